@@ -1,0 +1,453 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Every check here computes its expectation from a definition in the paper
+(Sec. 2 cut/balance/gain, Sec. 4.3 slots/penalties/Lemma 1, Sec. 4.4
+interleaving, Alg. 1 best prefix) by brute force, exact rationals or an
+invariant -- never by re-calling the oracle's own routine."""
+from __future__ import annotations
+
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import brute
+
+SMALL = [
+    dict(seed=1, n=40, avg_deg=4, k=3),
+    dict(seed=2, n=64, avg_deg=6, k=4, hubs=2, isolated=3),
+    dict(seed=3, n=100, avg_deg=3, k=5, isolated=10),
+    dict(seed=4, n=200, avg_deg=8, k=8, hubs=3),
+    dict(seed=5, n=150, avg_deg=5, k=2, weighted=False),
+    dict(seed=6, n=300, avg_deg=10, k=16, hubs=1, max_vw=30, max_ew=64),
+    dict(seed=7, n=9, avg_deg=2, k=12),                     # k > n
+]
+
+
+def small(i):
+    return synth.random_small(**SMALL[i])
+
+
+@pytest.fixture(params=range(len(SMALL)))
+def w(request):
+    return small(request.param)
+
+
+# ---------------------------------------------------------------- step 0/1
+def test_cut_and_block_weights_closed_form(w):
+    c, bw = oracle.cut(w, w.part)
+    assert c == brute.cut(w, w.part)
+    assert np.array_equal(bw, brute.block_weights(w, w.part))
+
+
+def test_gain_table_brute_force(w):
+    W, wI = oracle.gain_table(w, w.part)
+    assert np.array_equal(W.astype(np.int64), brute.table(w, w.part))
+    # omega(I(v)) is the row sum; cut = (sum omega(I(v)) - sum omega(v, P(v))) / 2
+    assert np.array_equal(wI, brute.table(w, w.part).sum(axis=1))
+    own = W[np.arange(w.n), w.part].astype(np.int64)
+    assert (wI.sum() - own.sum()) // 2 == brute.cut(w, w.part)
+
+
+def test_lmax_definition():
+    for tot, k, eps in [(16384, 8, 0.03), (4194304, 64, 0.03), (100, 3, 0.03), (7, 2, 0.5), (1, 2, 0.03),
+                        (103000000, 256, 0.03), (12, 2, 0.2)]:
+        avg = -(-tot // k)
+        assert oracle.lmax(tot, k, eps) == int((1 + Fraction(round(eps * 1e6), 10**6)) * avg)
+    assert oracle.lmax(16384, 8, 0.03) == 2109            # 1.03 * 2048 = 2109.44
+
+
+# ---------------------------------------------------------------- step 2
+def test_slot_defining_inequality():
+    rng = np.random.default_rng(11)
+    cases = [(0, 1), (1, 1), (2, 1), (3, 2), (9, 4), (27, 8), (81, 16), (1, 2**30), (2**31 - 1, 1),
+             (2**31 - 1, 2**31 - 1), (5, 7), (1000, 3)]
+    cases += [(int(a), int(b)) for a, b in zip(rng.integers(0, 10**6, 300), rng.integers(1, 2000, 300))]
+    for om, c in cases:
+        assert oracle.slot(om, c) == brute.slot(om, c), (om, c)
+    # hand values: (3/2)^0 = 1, (3/2)^1 = 1.5, (3/2)^2 = 2.25
+    assert oracle.slot(1, 1) == 0 and oracle.slot(3, 2) == 1 and oracle.slot(2, 1) == 2
+    assert oracle.slot(0, 5) == -32 and oracle.slot(2**31 - 1, 1) == 40
+
+
+def test_penalty_factors_exact():
+    for r, R in [(1, 1), (1, 8), (4, 8), (8, 8), (2, 4), (3, 3)]:
+        F = oracle.factors(r, R)
+        t = brute.tau(r, R)
+        assert list(F) == [brute.factor(l, t) for l in range(-32, 41)]
+    assert brute.tau(1, 8) == Fraction(1, 4) and brute.tau(8, 8) == 1
+    assert oracle.factors(8, 8)[32] == 2**20              # tau = 1, l = 0
+
+
+def test_buckets_from_definition(w):
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 3)
+    assert rc == oracle.OK
+    W = brute.table(w, w.part)
+    c = brute.node_w(w)
+    own = W[np.arange(w.n), w.part]
+    wI = W.sum(axis=1)
+    avail = 10 * own >= 7 * wI                            # omega(v, P(v)) >= t omega(I(v)), t = 0.7
+    assert np.array_equal(tr["avail"].astype(bool), avail)
+    slots = np.array([brute.slot(int(o), int(cc)) for o, cc in zip(own, c)])
+    assert np.array_equal(tr["slot"], slots)
+    B = np.zeros((w.k, 73), np.int64)
+    for v in np.nonzero(avail)[0]:
+        B[w.part[v], slots[v] + 32] += c[v]
+    assert np.array_equal(tr["bucket"], B)
+
+
+# ---------------------------------------------------------------- Lemma 1
+def _lemma_instance(seed, slack):
+    """Unit weights, k blocks; block 0 holds exactly L_max - slack nodes."""
+    rng = np.random.default_rng(seed)
+    n, k = 120, 4
+    w = synth.random_small(seed, n, 5.0, k, weighted=False)
+    L = brute.lmax(w)
+    part = np.full(n, -1, np.int32)
+    order = rng.permutation(n)
+    part[order[: L - slack]] = 0
+    rest = order[L - slack:]
+    part[rest] = 1 + (np.arange(len(rest)) % (k - 1))
+    w.part = part
+    return w, L
+
+
+@pytest.mark.parametrize("seed,slack", [(21, 0), (22, 0), (23, 3), (24, 0)])
+def test_lemma1_penalty_bound(seed, slack):
+    """Lemma 1 (Sec. 4.3): with unit weights, the i-th node moved into V_1 is
+    penalised at the slot of the i-th cheapest available node of V_1, and
+    moving those nodes out again costs at most (1/t) sum (3/2)^l_i."""
+    w, L = _lemma_instance(seed, slack)
+    W = brute.table(w, w.part)
+    own = W[np.arange(w.n), w.part]
+    wI = W.sum(axis=1)
+    in1 = np.nonzero(w.part == 0)[0]
+    avail = [v for v in in1 if 10 * own[v] >= 7 * wI[v]]
+    slots = sorted(brute.slot(int(own[v]), 1) for v in avail)
+    U = np.nonzero(w.part != 0)[0][:25]
+    pen, lvl = oracle.penalty_sequence(w, w.part, 0, U, p=oracle.params(tau1=(1, 1)))
+    for i in range(len(U)):
+        if i < slack:
+            assert pen[i] == 0
+        elif i - slack < len(slots):
+            assert lvl[i] == slots[i - slack]
+            assert pen[i] == brute.factor(int(lvl[i]), Fraction(1)) >> 20   # c(u) = 1, tau = 1
+        else:
+            assert pen[i] == -1                                       # forbidden: no slot covers the excess
+    # the constructive rebalancing of the proof
+    j = min(len(U), slack + len(slots)) - slack
+    if j <= 0:
+        return
+    U = U[: slack + j]
+    P1 = brute.apply(w.part, U, 0)
+    cheapest = sorted(avail, key=lambda v: (brute.slot(int(own[v]), 1), v))[:j]
+    P2 = brute.apply(P1, cheapest, 1)
+    increase = brute.cut(w, P2) - brute.cut(w, P1)
+    bound = Fraction(10, 7) * sum(Fraction(3, 2) ** int(l) for l in lvl[slack: slack + j])
+    assert increase <= bound
+    assert np.all(brute.block_weights(w, P2)[0] <= L)
+
+
+# ---------------------------------------------------------------- step 3 / 4
+def _penalty_bruteforce(B, b, x, cu, F):
+    if x <= 0:
+        return 0
+    acc = 0
+    for l in range(73):
+        acc += int(B[b, l])
+        if acc >= x:
+            return (cu * int(F[l])) >> 20
+    return None
+
+
+def test_selection_bruteforce(w):
+    r, R = 1, 3
+    rc, _, _, tr = oracle.run_round(w, w.part, r, R)
+    edges = brute.coo(w)
+    c = brute.node_w(w)
+    C = brute.block_weights(w, w.part)
+    L = brute.lmax(w)
+    W = brute.table(w, w.part)
+    F = [brute.factor(l, brute.tau(r, R)) for l in range(-32, 41)]
+    cut0 = brute.cut(w, w.part, edges)
+    B = tr["bucket"]
+    for v in range(w.n):
+        a = w.part[v]
+        best = None
+        if W[v, a] < W[v].sum():                                   # boundary node
+            for b in range(w.k):
+                if b == a or W[v, b] == 0:
+                    continue
+                gain = cut0 - brute.cut(w, brute.apply(w.part, [v], b), edges)
+                pen = _penalty_bruteforce(B, b, int(C[b] + c[v] - L), int(c[v]), F)
+                if pen is None:
+                    continue
+                s0 = gain - pen
+                if best is None or s0 > best[0]:
+                    best = (s0, b, gain)
+        if best is not None and best[0] > 0:
+            assert (tr["cand_target"][v], tr["cand_s0"][v], tr["cand_gain"][v]) == (best[1], best[0], best[2])
+        else:
+            assert tr["cand_target"][v] == -1
+
+
+def test_move_list_inflow(w):
+    r, R = 1, 2
+    rc, _, _, tr = oracle.run_round(w, w.part, r, R)
+    c = brute.node_w(w)
+    C = brute.block_weights(w, w.part)
+    L = brute.lmax(w)
+    F = [brute.factor(l, brute.tau(r, R)) for l in range(-32, 41)]
+    tgt, s0, g = tr["cand_target"], tr["cand_s0"], tr["cand_gain"]
+    expect = {}
+    for t in range(w.k):
+        cands = sorted([v for v in range(w.n) if tgt[v] == t], key=lambda v: (-s0[v], v))
+        inflow = 0
+        for v in cands:
+            pen = _penalty_bruteforce(tr["bucket"], t, int(C[t] + inflow + c[v] - L), int(c[v]), F)
+            inflow += int(c[v])
+            if pen is not None and g[v] - pen > 0:
+                expect[v] = (t, g[v] - pen)
+    Mn, Mt, Ms = tr["M"]
+    assert {int(v): (int(t), int(s)) for v, t, s in zip(Mn, Mt, Ms)} == expect
+    keys = [(-int(s), int(v)) for v, s in zip(Mn, Ms)]
+    assert keys == sorted(keys)                                    # M ordered by (score desc, id asc)
+
+
+# ---------------------------------------------------------------- step 6-10
+def _after_M(w, tr):
+    Mn, Mt, _ = tr["M"]
+    return brute.apply(w.part, Mn, Mt)
+
+
+def test_rebalance_postconditions(w):
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 2)
+    L = brute.lmax(w)
+    P1 = _after_M(w, tr)
+    C1 = brute.block_weights(w, P1)
+    over1 = set(np.nonzero(C1 > L)[0])
+    Rn, Rf, Rt, Rs = tr["R"]
+    assert len(set(Rn.tolist())) == len(Rn)                        # each node rebalanced at most once
+    P = P1.copy()
+    for h in sorted(set(Rs.tolist())):
+        sel = Rs == h
+        Ch = brute.block_weights(w, P)
+        for v, a, b in zip(Rn[sel], Rf[sel], Rt[sel]):
+            assert P[v] == a and Ch[a] > L                         # evicted from an overloaded block
+            assert b not in over1                                  # into a block that was never overloaded
+        P = brute.apply(P, Rn[sel], Rt[sel])
+        assert np.all(brute.block_weights(w, P)[list(set(range(w.k)) - over1)] <= L)
+        # minimal per-source prefix: without its last admitted move a source is still overloaded
+        Cn = brute.block_weights(w, P)
+        c = brute.node_w(w)
+        for a in set(Rf[sel].tolist()):
+            last = Rn[sel][Rf[sel] == a][-1]
+            assert Cn[a] + c[last] > L
+    if tr["n_rebal"] or over1:
+        assert np.all(brute.block_weights(w, P) <= L) or tr["subrounds"] > 0
+
+
+def test_interleave_rule(w):
+    """Sec. 4.4: after each move of M into block b, exactly the minimal prefix of
+    the remaining R_b that makes b balanced follows (as far as R_b reaches)."""
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 2)
+    L = brute.lmax(w)
+    c = brute.node_w(w)
+    Mn, Mt, _ = tr["M"]
+    Rn, Rf, Rt, _ = tr["R"]
+    Xn, Xf, Xt = tr["X"]
+    assert len(Xn) == len(Mn) + len(Rn)
+    rset = {(int(v), int(a), int(b)) for v, a, b in zip(Rn, Rf, Rt)}
+    isR = np.array([(int(v), int(a), int(b)) in rset for v, a, b in zip(Xn, Xf, Xt)], dtype=bool)
+    assert list(Xn[~isR]) == list(Mn)                             # M keeps its order
+    for b in range(w.k):                                           # each R_b keeps its order
+        assert list(Xn[isR & (Xf == b)]) == list(Rn[Rf == b])
+    Cw = brute.block_weights(w, w.part)
+    i, nM = 0, 0
+    while i < len(Xn) and nM < len(Mn):
+        assert not isR[i]
+        v, a, b = int(Xn[i]), int(Xf[i]), int(Xt[i])
+        Cw[a] -= c[v]; Cw[b] += c[v]
+        nM += 1
+        i += 1
+        while i < len(Xn) and isR[i]:
+            assert int(Xf[i]) == b and Cw[b] > L                   # only while the target is overloaded
+            Cw[b] -= c[Xn[i]]; Cw[int(Xt[i])] += c[Xn[i]]
+            i += 1
+        remaining_b = [j for j in range(i, len(Xn)) if isR[j] and int(Xf[j]) == b]
+        if remaining_b and nM < len(Mn):
+            assert Cw[b] <= L                                      # stopped early only once balanced
+
+
+def test_merge_double_moves(w):
+    """Sec. 4.4 footnote: a node moved twice becomes one move.  Applying the whole
+    merged sequence I gives the partition after M and R; I is the interleaved
+    sequence with each folded R move removed (the merged move sits at the M
+    position) and no-op moves dropped."""
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 2)
+    Mn, Mt, _ = tr["M"]
+    Rn, Rf, Rt, _ = tr["R"]
+    Xn, Xf, Xt = tr["X"]
+    In, If, It, _ = tr["I"]
+    after = brute.apply(brute.apply(w.part, Mn, Mt), Rn, Rt)
+    assert np.array_equal(brute.apply(w.part, In, It), after)
+    mset = set(Mn.tolist())
+    rset = {(int(v), int(a), int(b)) for v, a, b in zip(Rn, Rf, Rt)}
+    expect = [int(v) for v, a, b in zip(Xn, Xf, Xt)
+              if not ((int(v), int(a), int(b)) in rset and int(v) in mset) and after[v] != w.part[v]]
+    assert [int(v) for v in In] == expect
+
+
+def test_exact_gains_and_best_prefix(w, samples=None):
+    """G(j) == cut(P) - cut(P o I^j) by brute force (all j, or `samples` evenly
+    spaced j on larger graphs), eligibility from block weights, and the best
+    prefix as the max over balanced prefixes (ties: shortest)."""
+    for r, R in [(1, 3), (3, 3)]:
+        rc, newp, cut_after, tr = oracle.run_round(w, w.part, r, R)
+        assert rc == oracle.OK
+        edges = brute.coo(w)
+        L = brute.lmax(w)
+        c = brute.node_w(w)
+        In, If, It, Ig = tr["I"]
+        assert len(set(In.tolist())) == len(In)                    # every node at most once after merging
+        assert np.all(If == w.part[In]) and np.all(If != It)
+        cut0 = brute.cut(w, w.part, edges)
+        check = set(range(1, len(In) + 1)) if samples is None else \
+            set(np.linspace(1, len(In), min(samples, len(In)), dtype=np.int64).tolist())
+        P = w.part.copy()
+        Cw = brute.block_weights(w, w.part)
+        Gs = np.concatenate([[0], np.cumsum(Ig)])
+        best = (0, 0)
+        for j in range(1, len(In) + 1):
+            v = In[j - 1]
+            P[v] = It[j - 1]
+            Cw[If[j - 1]] -= c[v]; Cw[It[j - 1]] += c[v]
+            if j in check:
+                assert Gs[j] == cut0 - brute.cut(w, P, edges)      # exact prefix gains
+            bal = bool(np.all(Cw <= L))
+            assert bal == bool(tr["eligible"][j])
+            if bal and Gs[j] > best[0]:
+                best = (int(Gs[j]), j)
+        assert (tr["best_gain"], tr["best_len"]) == best
+        assert cut_after == cut0 - best[0] == brute.cut(w, newp, edges) <= cut0
+        assert np.all(brute.block_weights(w, newp) <= L)
+
+
+# ---------------------------------------------------------------- whole round
+def _exhaustive_opt(w):
+    L = brute.lmax(w)
+    edges = brute.coo(w)
+    c = brute.node_w(w)
+    best = None
+    for assign in itertools.product(range(w.k), repeat=w.n):
+        p = np.array(assign)
+        if np.any(np.bincount(p, weights=c, minlength=w.k) > L):
+            continue
+        cc = brute.cut(w, p, edges)
+        best = cc if best is None else min(best, cc)
+    return best
+
+
+@pytest.mark.parametrize("seed,n,k", [(31, 10, 2), (32, 12, 2), (33, 8, 3), (34, 11, 2), (35, 7, 3), (36, 12, 2)])
+def test_never_below_exhaustive_optimum(seed, n, k):
+    w = synth.random_small(seed, n, 3.0, k, weighted=(seed % 2 == 0), max_vw=2)
+    w.eps = 0.25
+    rc, newp, cutv, rcuts = oracle.refine(w, w.part, rounds=4)
+    assert rc == oracle.OK
+    opt = _exhaustive_opt(w)
+    assert cutv >= opt
+    assert cutv == brute.cut(w, newp)
+    assert np.all(np.diff(rcuts) <= 0)                            # cut never worse (Sec. 3 rollback)
+
+
+def _two_cliques(size, misplaced_pairs, eps):
+    n = 2 * size
+    src, dst = [], []
+    for base in (0, size):
+        for i in range(size):
+            for j in range(i + 1, size):
+                src.append(base + i); dst.append(base + j)
+    xadj, adj = synth.csr_from_edges(n, np.array(src), np.array(dst))
+    part = np.array([0] * size + [1] * size, np.int32)
+    for i in range(misplaced_pairs):
+        part[i], part[size + i] = 1, 0
+    return synth.Workload("cliques", n, xadj, adj, None, None, 2, eps, part, 1)
+
+
+def test_two_cliques_one_misplaced_node():
+    """Two disjoint K6, one node of the first clique in the second block (eps =
+    0.2 gives the slack): its move has gain 5 and no penalty, so round 1 reaches cut 0."""
+    w = _two_cliques(6, 0, 0.2)
+    w.part[0] = 1
+    rc, newp, cutv, _ = oracle.refine(w, w.part, rounds=1)
+    assert rc == oracle.OK and cutv == 0 and brute.cut(w, newp) == 0
+
+
+def test_two_cliques_swapped_pair_needs_penalty_and_prefix():
+    """Two disjoint K6, eps = 0.03 (L_max = 6), one node of each clique swapped.
+    Each move has gain 5; the target block would hold 7 > L_max, so the penalty
+    is taken at slot 4 of the five available clique nodes (omega = 4,
+    (3/2)^3 < 4 <= (3/2)^4): floor(tau_1 (3/2)^4 2^20) >> 20 = 1 at tau_1 = 1/4.
+    Both moves stay (score 4); the 1-prefix is imbalanced, the 2-prefix is
+    balanced with gain 10, so the cut drops from 10 to 0."""
+    w = _two_cliques(6, 1, 0.03)
+    assert brute.cut(w, w.part) == 10
+    rc, newp, cutv, tr = oracle.run_round(w, w.part, 1, 2)
+    Mn, Mt, Ms = tr["M"]
+    assert list(Mn) == [0, 6] and list(Ms) == [4, 4]
+    assert list(tr["eligible"]) == [True, False, True]
+    assert cutv == 0 and tr["best_len"] == 2
+
+
+def test_split_resume_equals_one_call():
+    w = small(3)
+    rc, p8, c8, _ = oracle.refine(w, w.part, rounds=8, total_rounds=8)
+    rc1, p3, c3, _ = oracle.refine(w, w.part, rounds=3, round_offset=0, total_rounds=8)
+    rc2, p35, c35, _ = oracle.refine(w, p3, rounds=5, round_offset=3, total_rounds=8)
+    assert rc == rc1 == rc2 == oracle.OK
+    assert np.array_equal(p8, p35) and c8 == c35
+
+
+def test_imbalanced_input_is_repaired():
+    w = synth.random_small(41, 120, 4.0, 4, balanced=False)
+    L = brute.lmax(w)
+    assert np.any(brute.block_weights(w, w.part) > L)
+    rc, newp, cutv, rcuts = oracle.refine(w, w.part, rounds=2)
+    assert rc == oracle.OK
+    assert np.all(brute.block_weights(w, newp) <= L)
+    assert cutv == brute.cut(w, newp)
+
+
+def test_tiny_config_improves_and_stays_balanced():
+    w = synth.plain_tiny()
+    rc, newp, cutv, rcuts = oracle.refine(w, w.part)
+    assert rc == oracle.OK
+    assert cutv == brute.cut(w, newp) < brute.cut(w, w.part)
+    assert np.all(brute.block_weights(w, newp) <= brute.lmax(w))
+    assert np.all(np.diff(rcuts) <= 0)
+
+
+def _medium(name):
+    if name == "rmat":
+        return synth.plain_large(10)
+    w = synth.plain_weighted(6)                  # strip split is imbalanced at this size: repair it first
+    rc, p, _, _ = oracle.refine(w, w.part, rounds=0, total_rounds=1)
+    assert rc == oracle.OK
+    w.part = p
+    return w
+
+
+@pytest.mark.parametrize("name", ["rmat", "rgg"])
+def test_round_pins_on_skewed_and_weighted_graphs(name):
+    w = _medium(name)
+    test_rebalance_postconditions(w)
+    test_interleave_rule(w)
+    test_merge_double_moves(w)
+    test_exact_gains_and_best_prefix(w, samples=200)
+    rc, newp, cutv, rcuts = oracle.refine(w, w.part, rounds=3, total_rounds=8)
+    assert rc == oracle.OK and cutv == brute.cut(w, newp)
+    assert np.all(np.diff(rcuts) <= 0)
+    assert np.all(brute.block_weights(w, newp) <= brute.lmax(w))
