@@ -1,0 +1,209 @@
+/*
+ * upr.h -- unconstrained FM refinement for balanced k-way graph partitioning
+ * on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The library refines a k-way partition of an undirected graph G = (V, E,
+ * c, omega) with integer node weights c > 0 and edge weights omega > 0 (Sec. 2
+ * of Maas, Gottesbueren, Seemaier, "Parallel Unconstrained Local Search for
+ * Partitioning Irregular Graphs", arXiv 2308.15494).  One round is the
+ * deterministic synchronous form of Algorithm 1:
+ *   (a) gain table omega(v, V_b) (Sec. 6.1),
+ *   (b) selection of moves that may violate the balance constraint, scored by
+ *       gain minus the rebalancing-cost penalty of Sec. 4.3, scaled by the
+ *       tau schedule of Sec. 4.4,
+ *   (d) rebalancing by gain-per-weight priority (Sec. 6),
+ *   (c) interleaving of the moves with the rebalancing moves, exact gain
+ *       recalculation and application of the best balanced prefix (Sec. 4.4,
+ *       Alg. 1 line 19), so the cut never increases,
+ *   (e) exact cut and block weights (Sec. 2).
+ * Every quantity is an integer and every tie is broken by node or block id,
+ * so results are bit-for-bit reproducible and equal those of the sequential
+ * reference definition of the round.
+ *
+ * Conventions for every entry point:
+ *  - Return value: UPR_OK (0) on success, UPR_PENDING (1) for a job that is not
+ *    finished, a negative upr_status on error.  On error no output argument
+ *    is modified and the context stays usable unless the status is
+ *    UPR_ERR_CUDA (a CUDA error that may have left the device unusable).
+ *  - Pointers to graph or partition data may be host or device memory; the
+ *    library detects which (cudaPointerGetAttributes).  Device pointers must
+ *    be on the device that was current when the context was created.
+ *  - All device work of a context runs on the stream given in upr_params
+ *    (NULL = the legacy default stream); every call returns after its results
+ *    are in the caller's buffers (it synchronises that stream).
+ *  - Contexts are not thread-safe: one thread at a time per context.
+ */
+#ifndef UPR_H
+#define UPR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t upr_status;
+#define UPR_OK               0
+#define UPR_PENDING          1
+#define UPR_ERR_INVALID     (-1)  /* malformed graph, partition or parameter            */
+#define UPR_ERR_OOM         (-2)  /* device or host allocation failed                   */
+#define UPR_ERR_CUDA        (-3)  /* a CUDA runtime call failed                          */
+#define UPR_ERR_INFEASIBLE  (-4)  /* an imbalanced input could not be rebalanced         */
+#define UPR_ERR_BUSY        (-5)  /* server queue full                                  */
+#define UPR_ERR_TIMEOUT     (-6)  /* a bounded wait expired                              */
+#define UPR_ERR_NOT_FOUND   (-7)  /* unknown ticket                                      */
+
+typedef struct upr_ctx upr_ctx;
+typedef struct upr_server upr_server;
+
+/* An undirected graph in CSR form (Sec. 2).  Every edge {u,v} appears twice,
+ * as v in u's list and u in v's list, with equal weight.  n < 2^31, m < 2^31.
+ * on_device: ignored (the library inspects the pointers); kept for callers
+ * that want to state it. */
+typedef struct {
+    int64_t        n;        /* number of nodes                                      */
+    int64_t        m;        /* number of adjacency entries (= 2|E|)                 */
+    const int64_t *xadj;     /* [n+1], xadj[0] = 0, non-decreasing, xadj[n] = m      */
+    const int32_t *adjncy;   /* [m], neighbour ids in [0, n), no self loops          */
+    const int32_t *vwgt;     /* [n] node weights c(v) > 0, or NULL for unit weights  */
+    const int32_t *adjwgt;   /* [m] edge weights omega > 0, or NULL for unit weights */
+    int32_t        on_device;
+} upr_graph;
+
+typedef struct {
+    int32_t t_num, t_den;        /* rebalancing-availability threshold t (Sec. 4.3): a node v
+                                    is available if omega(v, P(v)) >= t * omega(I(v)). 7/10  */
+    int32_t tau1_num, tau1_den;  /* tau_1, the penalty factor of round 1 (Sec. 4.4); rounds
+                                    interpolate linearly to 1. 1/4; tau1_den <= 65536       */
+    int32_t max_subrounds;       /* rebalancing sub-rounds per round. 64                      */
+    int32_t validate;            /* 1: check the graph in upr_create (symmetry by a 64-bit
+                                    multiset hash, ranges, weights). 1                      */
+    int32_t round_offset;        /* rounds already run of a longer schedule (resume). 0       */
+    int32_t total_rounds;        /* length of the tau schedule; 0 = the rounds of each call   */
+    void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
+} upr_params;
+
+/* Per-call statistics (all optional). */
+typedef struct {
+    int64_t cut_in, cut_out;     /* cut before and after the call                       */
+    int32_t rounds_run;          /* refinement rounds executed                          */
+    int32_t repaired_input;      /* 1 if an imbalanced input was rebalanced first       */
+    int64_t n_candidates;        /* sum over rounds: nodes with a positive scored move  */
+    int64_t n_moves;             /* sum over rounds: |M|                                */
+    int64_t n_rebalance_moves;   /* sum over rounds: |R|                                */
+    int64_t n_sequence;          /* sum over rounds: |I| after merging                  */
+    int64_t n_applied;           /* sum over rounds: length of the applied prefix       */
+    int32_t subrounds;           /* sum over rounds: rebalancing sub-rounds             */
+    int32_t kernel_launches;     /* kernels launched by the call                        */
+    double  ms_device;           /* device time of the call (CUDA events)               */
+    double  ms_gain_table;       /* device time of gain-table builds                    */
+    int32_t gain_table_builds;   /* number of full gain-table builds                    */
+    int64_t gain_table_bytes;    /* algorithmic DRAM bytes of one build                 */
+} upr_stats;
+
+/* Fills *p with the defaults documented in upr_params. */
+void upr_params_default(upr_params *p);
+
+/* Human-readable name of a status code (static string). */
+const char *upr_status_str(upr_status s);
+
+/* Creates a refinement context for graph g, k blocks (2 <= k <= 4096) and
+ * imbalance eps > 0 (L_max = floor((1 + eps) * ceil(c(V)/k)) with eps rounded
+ * to parts per million; Sec. 2).  Copies the graph to the device (the caller
+ * may free it on return), computes omega(I(v)) and allocates all workspace
+ * for later calls, so upr_refine allocates nothing.  params may be NULL.
+ * Errors: UPR_ERR_INVALID (bad sizes, k, eps, params, or with validate=1 a
+ * graph that is not a symmetric positive-weight CSR without self loops, or
+ * weights so large that omega(I(v)) >= 2^31 or the exact rebalancing key
+ * would exceed 63 bits); UPR_ERR_OOM; UPR_ERR_CUDA. */
+upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_params *params,
+                      upr_ctx **out);
+
+/* Refines part (n entries, host or device, values in [0, k)) in place with
+ * `rounds` rounds (the tau schedule of Sec. 4.4 runs over rounds
+ * round_offset+1 .. round_offset+rounds of total_rounds).  An imbalanced
+ * input is first rebalanced (round 0: Sec. 6 rebalancing and best balanced
+ * prefix).  The cut never increases.  seed is recorded only: results depend
+ * on (graph, k, eps, part, rounds, params) alone.  part is written only on
+ * UPR_OK.  Errors: UPR_ERR_INVALID (part out of range, rounds < 0, schedule
+ * out of range), UPR_ERR_INFEASIBLE (imbalanced input that cannot be
+ * rebalanced), UPR_ERR_CUDA. */
+upr_status upr_refine(upr_ctx *ctx, int32_t *part, int32_t rounds, uint64_t seed, upr_stats *stats);
+
+/* Exact cut and block weights (Sec. 2) of part (host or device, n entries).
+ * *cut receives sum of omega over cut edges; block_weights (k entries, host,
+ * may be NULL) receives c(V_b). Errors: UPR_ERR_INVALID, UPR_ERR_CUDA. */
+upr_status upr_cut(upr_ctx *ctx, const int32_t *part, int64_t *cut, int64_t *block_weights);
+
+/* Releases the context and all its device memory. NULL is ignored. */
+void upr_destroy(upr_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Serving: a host worker thread admits refinement jobs while device memory
+ * and job slots allow, runs each job on its own stream and context so jobs of
+ * different sizes overlap on the device, and keeps each job's state resident
+ * until it is polled.  Results are identical to upr_create + upr_refine on the
+ * same inputs. */
+typedef struct {
+    int32_t max_jobs;           /* jobs resident on the device at once (slots). 8          */
+    int32_t queue_capacity;     /* submitted-but-not-admitted jobs before UPR_ERR_BUSY. 4096 */
+    int64_t memory_budget;      /* device bytes the server may hold; 0 = 80% of free memory */
+    upr_params params;          /* per-job parameters (stream ignored: each slot owns one) */
+} upr_server_params;
+
+void upr_server_params_default(upr_server_params *p);
+
+upr_status upr_server_create(const upr_server_params *p, upr_server **out);
+
+/* Queues a job.  The graph and part (host memory) are copied before the call
+ * returns.  *ticket identifies the job.  Errors: UPR_ERR_INVALID, UPR_ERR_BUSY,
+ * UPR_ERR_OOM. */
+upr_status upr_submit(upr_server *s, const upr_graph *g, int32_t k, double eps, const int32_t *part,
+                      int32_t rounds, uint64_t seed, uint64_t *ticket);
+
+/* UPR_PENDING while the job runs; on completion writes part_out (n entries,
+ * host), *cut_out and stats (each may be NULL), forgets the ticket and returns
+ * the job's status.  Errors: UPR_ERR_NOT_FOUND. */
+upr_status upr_poll(upr_server *s, uint64_t ticket, int32_t *part_out, int64_t *cut_out,
+                    upr_stats *stats);
+
+/* Waits up to timeout_ms for a job (same outputs as upr_poll); UPR_ERR_TIMEOUT
+ * if it is still running afterwards. */
+upr_status upr_wait(upr_server *s, uint64_t ticket, int64_t timeout_ms, int32_t *part_out,
+                    int64_t *cut_out, upr_stats *stats);
+
+/* Stops the worker after finishing admitted jobs and frees everything. */
+void upr_server_destroy(upr_server *s);
+
+/* ------------------------------------------------------------------------
+ * Inspection entry points used by the parity tests; each runs one step or
+ * one round and copies intermediate results to host buffers. */
+
+/* Dense gain table W[v*k + b] = omega(v, V_b) (Sec. 2, Sec. 6.1) of part, and
+ * omega(I(v)).  W (n*k int32) and wI (n int64) are host buffers (NULL to skip). */
+upr_status upr_debug_gain_table(upr_ctx *ctx, const int32_t *part, int32_t *W, int64_t *wI);
+
+/* Trace of one round (host buffers; any pointer may be NULL).  Capacities:
+ * node-indexed arrays n, the pre-merge sequence 2n, I_eligible n+1, bucket
+ * k*73 (slot s in column s+32), factor 73. */
+typedef struct {
+    int8_t  *avail;        int32_t *slot;        int64_t *bucket;      int64_t *factor;
+    int32_t *cand_target;  int64_t *cand_s0;     int64_t *cand_gain;   int64_t  n_cand;
+    int64_t  n_moves;      int32_t *M_node;      int32_t *M_to;        int64_t *M_score;
+    int64_t  n_rebal;      int32_t  subrounds;
+    int32_t *R_node;       int32_t *R_from;      int32_t *R_to;        int32_t *R_subround;
+    int64_t  n_inter;      int32_t *X_node;      int32_t *X_from;      int32_t *X_to;
+    int64_t  n_seq;        int32_t *I_node;      int32_t *I_from;      int32_t *I_to;
+    int64_t *I_gain;       int8_t  *I_eligible;
+    int64_t  best_len;     int64_t  best_gain;   int64_t  cut_before;  int64_t  cut_after;
+} upr_trace;
+
+/* Runs round r of R (rebalance_only = 1: the round-0 repair) on part (host,
+ * in/out, written only on UPR_OK) and fills *trace. */
+upr_status upr_debug_round(upr_ctx *ctx, int32_t *part, int32_t r, int32_t R, int32_t rebalance_only,
+                           upr_trace *trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UPR_H */

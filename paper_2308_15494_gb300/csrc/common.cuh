@@ -1,0 +1,71 @@
+// Shared definitions of the CUDA library: integer types, launch helpers,
+// error propagation and warp-level primitives.  Everything here is
+// integer-only; no floating point reaches a result.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "../../include/upr.h"
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+namespace upr {
+
+constexpr int kSlotLo = -32;                 // bucket slots are clamped to [-32, 40]
+constexpr int kSlotHi = 40;
+constexpr int kSlots = kSlotHi - kSlotLo + 1; // 73
+constexpr int kQ = 20;                       // fixed-point bits of the penalty factors
+constexpr int kMaxK = 4096;
+constexpr int kHubDegree = 4096;             // nodes above this degree get CTA-wide treatment
+
+// A failing CUDA call is turned into UPR_ERR_CUDA by the entry points.
+struct CudaError { cudaError_t e; const char *what; };
+
+#define UPR_CUDA(call)                                                     \
+    do {                                                                   \
+        cudaError_t _e = (call);                                           \
+        if (_e != cudaSuccess) throw ::upr::CudaError{_e, #call};          \
+    } while (0)
+
+// Counts kernel launches of this library (reported in upr_stats).
+extern std::atomic<long long> g_upr_launches;
+#define UPR_LAUNCH_CHECK()                                                 \
+    do {                                                                   \
+        g_upr_launches.fetch_add(1, std::memory_order_relaxed);            \
+        UPR_CUDA(cudaGetLastError());                                      \
+    } while (0)
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over an aligned group of G lanes (G a power of two <= 32).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lexicographic max of (score, -id) over an aligned group of G lanes: the
+// larger score wins, equal scores go to the smaller id; id < 0 marks "none".
+template <int G>
+__device__ __forceinline__ void group_argmax(int64_t &score, int32_t &id) {
+    for (int o = G / 2; o > 0; o >>= 1) {
+        int64_t s2 = __shfl_xor_sync(0xffffffffu, score, o);
+        int32_t i2 = __shfl_xor_sync(0xffffffffu, id, o);
+        bool take = (i2 >= 0) && (id < 0 || s2 > score || (s2 == score && i2 < id));
+        if (take) { score = s2; id = i2; }
+    }
+}
+
+}  // namespace upr

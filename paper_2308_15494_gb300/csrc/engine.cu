@@ -1,0 +1,769 @@
+// The C ABI of include/upr.h: context creation, the round driver and the
+// inspection entry points.  The driver enqueues the kernels of one round on
+// the context's stream; it reads back a few counters per step (list lengths,
+// block weights between rebalancing sub-rounds) to size the next launches.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace upr;
+
+namespace {
+
+int bit_length(uint64_t x) { int b = 0; while (x) { b++; x >>= 1; } return b; }
+
+// Bump allocator over one cudaMalloc; a first pass with base == nullptr sizes it.
+struct Arena {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename T> T *take(size_t count) {
+        size_t a = (off + 255) & ~size_t(255);
+        off = a + count * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + a) : nullptr;
+    }
+};
+
+struct SortBuf {
+    uint64_t *k, *ka;
+    uint32_t *v, *va;
+    // sorts (k, v) on `bits` bits; returns the buffers holding the result
+    void run(int64_t n, int bits, void *tmp, cudaStream_t s, uint64_t **ko, uint32_t **vo) {
+        bool alt = radix_sort_pairs(k, v, ka, va, n, bits, tmp, s);
+        *ko = alt ? ka : k;
+        *vo = alt ? va : v;
+    }
+};
+
+// Host-side F_r[l] = floor(tau_r * (3/2)^l * 2^Q), tau_r = tau_1 + (1 - tau_1)(r-1)/max(R-1,1)
+void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F) {
+    const int64_t D = R > 1 ? (int64_t)R - 1 : 1;
+    const u128 num = (u128)(t1n * D + (t1d - t1n) * (int64_t)(r - 1));
+    const u128 den = (u128)(t1d * D);
+    for (int l = kSlotLo; l <= kSlotHi; l++) {
+        u128 p3 = 1, p2 = 1;
+        for (int i = 0; i < (l >= 0 ? l : -l); i++) { p3 *= 3; p2 *= 2; }
+        u128 a = l >= 0 ? num * p3 : num * p2;
+        u128 b = l >= 0 ? den * p2 : den * p3;
+        F[l - kSlotLo] = (int64_t)((a << kQ) / b);
+    }
+}
+
+}  // namespace
+
+std::atomic<long long> upr::g_upr_launches{0};
+
+struct upr_ctx {
+    int device = 0;
+    int64_t n = 0, m = 0;
+    int32_t k = 0;
+    int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;
+    int gbits = 1, cbits = 1;
+    upr_params prm{};
+    cudaStream_t s = nullptr;
+    GraphDev G{};
+
+    void *mem = nullptr;
+    // graph
+    int64_t *xadj; int32_t *adj, *adjw, *vwgt, *wI;
+    HubChunk *hub_chunks; int64_t n_chunks = 0;
+    // state
+    int32_t *part0, *part; int64_t *C0, *C, *cut; int32_t *W;
+    int64_t *BW, *PW, *F;
+    // node-indexed
+    int32_t *cand_tgt, *cand_gain, *flags, *flags2, *excl_i, *m_pos, *r_to, *pos, *dest, *prop_tgt, *prop_gain;
+    int64_t *cand_s0;
+    // lists
+    int32_t *idxA, *idxB, *idxC, *idxD;
+    int64_t *score;
+    int32_t *M_node, *M_from, *M_to; int64_t *M_score;
+    int32_t *R_node, *R_from, *R_to, *R_sub;
+    int32_t *X_node, *X_from, *X_to, *final_to; int8_t *X_isr;
+    int32_t *I_node, *I_from, *I_to; int64_t *I_gain, *Gsum;
+    SortBuf sb[3];
+    int64_t *c_sorted, *c_excl, *delta, *d_excl;
+    uint64_t *packed, *qmax;
+    int32_t *emit, *qbefore, *em_excl, *pos_m;
+    int32_t *diff, *diff_excl;
+    int32_t *hub_flag, *hub_excl, *hubs;
+    int32_t *seg_first, *rbeg, *rend, *ebeg, *eend, *qfin, *left, *left_excl;
+    long long *best_parts, *best;
+    int8_t *over_d, *excl_d, *reject_d;
+    int32_t *counts;          // small device counters
+    uint64_t *vacc; int32_t *vflags; int64_t *scal;
+    void *tmp;                // scan / sort temporaries
+    // host pinned mirror
+    int64_t *h = nullptr;     // pinned scratch
+    int8_t *h8 = nullptr;
+    cudaEvent_t ev[4] = {};
+};
+
+namespace {
+
+void layout(upr_ctx *c, Arena &A) {
+    const size_t n = (size_t)std::max<int64_t>(c->n, 1), m = (size_t)std::max<int64_t>(c->m, 1), k = (size_t)c->k;
+    const size_t n2 = 2 * n;
+    c->xadj = A.take<int64_t>(n + 1);
+    c->adj = A.take<int32_t>(m);
+    c->adjw = A.take<int32_t>(m);
+    c->vwgt = A.take<int32_t>(n);
+    c->wI = A.take<int32_t>(n);
+    c->hub_chunks = A.take<HubChunk>((size_t)std::max<int64_t>(c->n_chunks, 1));
+    c->part0 = A.take<int32_t>(n);
+    c->part = A.take<int32_t>(n);
+    c->C0 = A.take<int64_t>(k);
+    c->C = A.take<int64_t>(k);
+    c->cut = A.take<int64_t>(4);
+    c->W = A.take<int32_t>(n * k);
+    c->BW = A.take<int64_t>(k * kSlots);
+    c->PW = A.take<int64_t>(k * kSlots);
+    c->F = A.take<int64_t>(kSlots);
+    for (int32_t **p : {&c->cand_tgt, &c->cand_gain, &c->flags, &c->m_pos, &c->r_to, &c->pos, &c->dest, &c->prop_tgt,
+                        &c->prop_gain, &c->idxA, &c->idxB, &c->idxC, &c->M_node, &c->M_from, &c->M_to, &c->R_node,
+                        &c->R_from, &c->R_to, &c->R_sub, &c->I_node, &c->I_from, &c->I_to, &c->emit, &c->qbefore,
+                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs})
+        *p = A.take<int32_t>(n);
+    for (int32_t **p : {&c->flags2, &c->excl_i, &c->idxD, &c->X_node, &c->X_from, &c->X_to, &c->final_to})
+        *p = A.take<int32_t>(n2 + 1);
+    c->diff = A.take<int32_t>(n + 2);
+    c->diff_excl = A.take<int32_t>(n + 2);
+    c->X_isr = A.take<int8_t>(n2);
+    c->cand_s0 = A.take<int64_t>(n);
+    c->score = A.take<int64_t>(n);
+    c->M_score = A.take<int64_t>(n);
+    c->I_gain = A.take<int64_t>(n);
+    c->Gsum = A.take<int64_t>(n);
+    for (int i = 0; i < 3; i++) {
+        c->sb[i].k = A.take<uint64_t>(n2);
+        c->sb[i].ka = A.take<uint64_t>(n2);
+        c->sb[i].v = A.take<uint32_t>(n2);
+        c->sb[i].va = A.take<uint32_t>(n2);
+    }
+    c->c_sorted = A.take<int64_t>(n2);
+    c->c_excl = A.take<int64_t>(n2);
+    c->delta = A.take<int64_t>(n2);
+    c->d_excl = A.take<int64_t>(n2);
+    c->packed = A.take<uint64_t>(n2);
+    c->qmax = A.take<uint64_t>(n2);
+    for (int32_t **p : {&c->seg_first, &c->rbeg, &c->rend, &c->ebeg, &c->eend, &c->qfin, &c->left, &c->left_excl})
+        *p = A.take<int32_t>(k);
+    c->best_parts = A.take<long long>(2048);
+    c->best = A.take<long long>(2);
+    c->over_d = A.take<int8_t>(k);
+    c->excl_d = A.take<int8_t>(k);
+    c->reject_d = A.take<int8_t>(k);
+    c->counts = A.take<int32_t>(16);
+    c->vacc = A.take<uint64_t>(2);
+    c->vflags = A.take<int32_t>(2);
+    c->scal = A.take<int64_t>(4);
+    c->tmp = A.take<char>(std::max(radix_temp_bytes((int64_t)n2), scan_temp_bytes((int64_t)n2 + 1)) + 1024);
+}
+
+enum MemKind { kHost = 0, kDevice = 1 };
+
+MemKind mem_kind(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return kHost; }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? kDevice : kHost;
+}
+
+void copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    UPR_CUDA(cudaMemcpyAsync(dst, src, bytes, mem_kind(src) == kDevice ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    UPR_CUDA(cudaMemcpyAsync(dst, src, bytes, mem_kind(dst) == kDevice ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+int32_t read_count(upr_ctx *c, int slot) {
+    UPR_CUDA(cudaMemcpyAsync(c->h, c->counts + slot, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+    UPR_CUDA(cudaStreamSynchronize(c->s));
+    return *reinterpret_cast<int32_t *>(c->h);
+}
+
+void read_i64(upr_ctx *c, const int64_t *src, int64_t cnt, int64_t *dst) {
+    UPR_CUDA(cudaMemcpyAsync(c->h, src, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, c->s));
+    UPR_CUDA(cudaStreamSynchronize(c->s));
+    memcpy(dst, c->h, sizeof(int64_t) * cnt);
+}
+
+struct RoundInfo {
+    int64_t n_cand = 0, n_moves = 0, n_rebal = 0, n_inter = 0, n_seq = 0, best_len = 0, best_gain = 0;
+    int32_t subrounds = 0;
+    float ms_table = 0;
+    int tables = 0;
+};
+
+// Trace destinations on the host (debug entry only).
+struct TraceSink { upr_trace *t; int8_t *avail_d; int32_t *slot_d; };
+
+void d2h(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (dst && bytes) UPR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+}
+
+void build_table(upr_ctx *c, const int32_t *part, RoundInfo &ri) {
+    UPR_CUDA(cudaEventRecord(c->ev[0], c->s));
+    gain_table(c->G, part, c->W, c->hub_chunks, c->n_chunks, c->s);
+    UPR_CUDA(cudaEventRecord(c->ev[1], c->s));
+    UPR_CUDA(cudaEventSynchronize(c->ev[1]));
+    float ms = 0;
+    UPR_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    ri.ms_table += ms;
+    ri.tables++;
+}
+
+/*
+ * One round on c->part0 / c->C0 / c->cut (device state).  Returns UPR_OK or
+ * UPR_ERR_INFEASIBLE (state unchanged).  rebalance_only: the round-0 repair.
+ */
+upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
+    cudaStream_t s = c->s;
+    const GraphDev &G = c->G;
+    const int64_t n = c->n;
+    const int32_t k = c->k;
+    const int kbits = std::max(1, bit_length((uint64_t)(k - 1)));
+    upr_trace *T = tr ? tr->t : nullptr;
+
+    UPR_CUDA(cudaMemcpyAsync(c->part, c->part0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * k, cudaMemcpyDeviceToDevice, s));
+    build_table(c, c->part0, ri);
+
+    int64_t nM = 0;
+    if (!rebalance_only) {
+        // ---- (b1) availability, slots, bucket weights; F_r
+        buckets(G, c->part0, c->W, c->prm.t_num, c->prm.t_den, c->BW, c->PW, tr ? tr->avail_d : nullptr,
+                tr ? tr->slot_d : nullptr, s);
+        penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->h);
+        UPR_CUDA(cudaMemcpyAsync(c->F, c->h, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
+        if (T) {
+            d2h(T->avail, tr->avail_d, n, s);
+            d2h(T->slot, tr->slot_d, sizeof(int32_t) * n, s);
+            d2h(T->bucket, c->BW, sizeof(int64_t) * k * kSlots, s);
+            if (T->factor) memcpy(T->factor, c->h, sizeof(int64_t) * kSlots);
+        }
+        Penalty pen{c->PW, c->F, c->C0, c->Lmax};
+        // ---- (b2) best move per boundary node
+        select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, s);
+        select_flags(c->flags, c->excl_i, c->idxA, c->counts + 0, n, c->tmp, s);
+        const int64_t nc = read_count(c, 0);
+        ri.n_cand = nc;
+        if (T) {
+            d2h(T->cand_target, c->cand_tgt, sizeof(int32_t) * n, s);
+            d2h(T->cand_s0, c->cand_s0, sizeof(int64_t) * n, s);
+            if (T->cand_gain) {
+                // cand_gain is int32 on the device; widen on the host
+                std::vector<int32_t> tmp(n);
+                UPR_CUDA(cudaMemcpyAsync(tmp.data(), c->cand_gain, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+                UPR_CUDA(cudaStreamSynchronize(s));
+                for (int64_t v = 0; v < n; v++) T->cand_gain[v] = tmp[v];
+            }
+        }
+        if (nc > 0) {
+            // ---- (b3) inflow penalties: order by (target, s0 desc, id)
+            uint64_t *ko; uint32_t *vo;
+            cand_keys(c->idxA, c->counts + 0, c->cand_tgt, c->cand_s0, c->sb[0].k, c->sb[0].v, nc, s);
+            c->sb[0].run(nc, 31 + kbits, c->tmp, s, &ko, &vo);
+            cand_gather(G, c->idxA, vo, c->counts + 0, c->cand_tgt, c->c_sorted, c->seg_first, nc, s);
+            exclusive_sum_i64(c->c_sorted, c->c_excl, nc, c->tmp, s);
+            inflow_filter(G, c->idxA, vo, c->counts + 0, c->cand_tgt, c->cand_gain, c->c_excl, c->seg_first, pen,
+                          c->flags2, c->score, nc, s);
+            select_flags(c->flags2, c->excl_i, c->idxB, c->counts + 1, nc, c->tmp, s);
+            nM = read_count(c, 1);
+            if (nM > 0) {
+                // ---- M ordered by (score desc, id)
+                uint64_t *k2; uint32_t *v2;
+                move_keys(c->idxB, c->counts + 1, c->score, c->sb[1].k, c->sb[1].v, nM, s);
+                c->sb[1].run(nM, 31, c->tmp, s, &k2, &v2);
+                apply_moves(G, c->idxA, c->idxB, v2, c->counts + 1, c->cand_tgt, c->score, c->part0, c->part, c->C,
+                            c->M_node, c->M_from, c->M_to, c->M_score, c->m_pos, nM, s);
+                // W' for P o M: delta update when M is small, rebuild otherwise
+                if (nM * 8 < n) {
+                    table_move(G, c->W, c->M_node, c->M_from, c->M_to, c->counts + 1, nM, s);
+                } else {
+                    build_table(c, c->part, ri);
+                }
+            }
+        }
+    }
+    ri.n_moves = nM;
+    if (T && T->M_node) {
+        d2h(T->M_node, c->M_node, sizeof(int32_t) * nM, s);
+        d2h(T->M_to, c->M_to, sizeof(int32_t) * nM, s);
+        d2h(T->M_score, c->M_score, sizeof(int64_t) * nM, s);
+    }
+
+    // ---- (d) rebalancing sub-rounds
+    std::vector<int64_t> Ch(k);
+    read_i64(c, c->C, k, Ch.data());
+    std::vector<int8_t> excl(k, 0), over(k, 0);
+    for (int32_t b = 0; b < k; b++) excl[b] = Ch[b] > c->Lmax;
+    int64_t nR = 0;
+    for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
+        bool any = false;
+        for (int32_t b = 0; b < k; b++) { over[b] = Ch[b] > c->Lmax; any = any || over[b]; }
+        if (!any) break;
+        ri.subrounds = h;
+        int32_t light = -1;
+        for (int32_t b = 0; b < k; b++)
+            if (!excl[b] && (light < 0 || Ch[b] < Ch[light])) light = b;
+        memcpy(c->h8, over.data(), k);
+        memcpy(c->h8 + k, excl.data(), k);
+        UPR_CUDA(cudaMemcpyAsync(c->over_d, c->h8, k, cudaMemcpyHostToDevice, s));
+        UPR_CUDA(cudaMemcpyAsync(c->excl_d, c->h8 + k, k, cudaMemcpyHostToDevice, s));
+        UPR_CUDA(cudaMemsetAsync(c->reject_d, 0, k, s));
+        RebalState st{c->C, c->over_d, c->excl_d, light, c->Lmax};
+        rebalance_propose(G, c->part, c->W, st, c->prop_tgt, c->prop_gain, c->flags, s);
+        select_flags(c->flags, c->excl_i, c->idxA, c->counts + 2, n, c->tmp, s);
+        const int64_t np = read_count(c, 2);
+        int64_t na = 0;
+        bool grew = false;
+        if (np > 0) {
+            uint64_t *kA; uint32_t *A;
+            rebalance_prio_keys(G, c->idxA, c->counts + 2, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v,
+                                np, s);
+            c->sb[0].run(np, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
+            // per source: the minimal prefix covering the excess
+            uint64_t *kB; uint32_t *B;
+            rebalance_block_keys(c->idxA, A, nullptr, c->counts + 2, c->part, c->sb[1].k, c->sb[1].v, np, s);
+            c->sb[1].run(np, kbits, c->tmp, s, &kB, &B);
+            rebalance_seg_weights(G, c->idxA, A, nullptr, B, kB, c->counts + 2, c->c_sorted, c->seg_first, np, s);
+            exclusive_sum_i64(c->c_sorted, c->c_excl, np, c->tmp, s);
+            rebalance_mark_selected(B, kB, c->counts + 2, c->c_excl, c->seg_first, st, c->flags2, np, s);
+            select_flags(c->flags2, c->excl_i, c->idxB, c->counts + 3, np, c->tmp, s);
+            const int64_t ns = read_count(c, 3);
+            if (ns > 0) {
+                // per target: the longest prefix that fits
+                uint64_t *kT; uint32_t *Tq;
+                rebalance_block_keys(c->idxA, A, c->idxB, c->counts + 3, c->prop_tgt, c->sb[2].k, c->sb[2].v, ns, s);
+                c->sb[2].run(ns, kbits, c->tmp, s, &kT, &Tq);
+                rebalance_seg_weights(G, c->idxA, A, c->idxB, Tq, kT, c->counts + 3, c->c_sorted, c->seg_first, ns, s);
+                exclusive_sum_i64(c->c_sorted, c->c_excl, ns, c->tmp, s);
+                rebalance_mark_admitted(Tq, kT, c->counts + 3, c->c_sorted, c->c_excl, c->seg_first, st, c->flags2,
+                                        c->reject_d, ns, s);
+                select_flags(c->flags2, c->excl_i, c->idxC, c->counts + 4, ns, c->tmp, s);
+                na = read_count(c, 4);
+                if (na > 0) {
+                    rebalance_apply(G, c->idxA, A, c->idxB, c->idxC, c->counts + 4, c->prop_tgt, c->part, c->C, h,
+                                    c->R_node + nR, c->R_from + nR, c->R_to + nR, c->R_sub + nR, c->r_to, na, s);
+                    table_move(G, c->W, c->R_node + nR, c->R_from + nR, c->R_to + nR, c->counts + 4, na, s);
+                }
+            }
+            UPR_CUDA(cudaMemcpyAsync(c->h8, c->reject_d, k, cudaMemcpyDeviceToHost, s));
+            read_i64(c, c->C, k, Ch.data());   // synchronises
+            for (int32_t b = 0; b < k; b++)
+                if (c->h8[b] && !excl[b]) { excl[b] = 1; grew = true; }
+        }
+        nR += na;
+        if (na == 0 && !grew) break;
+    }
+    ri.n_rebal = nR;
+    if (T && T->R_node) {
+        d2h(T->R_node, c->R_node, sizeof(int32_t) * nR, s);
+        d2h(T->R_from, c->R_from, sizeof(int32_t) * nR, s);
+        d2h(T->R_to, c->R_to, sizeof(int32_t) * nR, s);
+        d2h(T->R_subround, c->R_sub, sizeof(int32_t) * nR, s);
+    }
+
+    // ---- (c1) interleave M and R_1..R_k
+    UPR_CUDA(cudaMemsetAsync(c->rbeg, 0, sizeof(int32_t) * k, s));
+    UPR_CUDA(cudaMemsetAsync(c->rend, 0, sizeof(int32_t) * k, s));
+    UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
+    UPR_CUDA(cudaMemsetAsync(c->eend, 0, sizeof(int32_t) * k, s));
+    uint64_t *kRB = nullptr; uint32_t *RB = nullptr;
+    if (nR > 0) {
+        seq_rb_keys(c->R_from, nR, c->sb[0].k, c->sb[0].v, s);
+        c->sb[0].run(nR, kbits, c->tmp, s, &kRB, &RB);
+        seq_rb_bounds(c->R_node, c->R_from, RB, nR, G.vwgt, c->c_sorted, c->rbeg, c->rend, s);
+        exclusive_sum_i64(c->c_sorted, c->c_excl, nR, c->tmp, s);
+    }
+    uint64_t *kEV = nullptr; uint32_t *EV = nullptr;
+    if (nM > 0) {
+        const int64_t nev = 2 * nM;
+        seq_ev_keys(c->M_from, c->M_to, nM, c->sb[1].k, c->sb[1].v, s);
+        c->sb[1].run(nev, kbits, c->tmp, s, &kEV, &EV);
+        seq_ev_delta(c->M_node, EV, kEV, nev, G.vwgt, c->delta, c->ebeg, c->eend, s);
+        exclusive_sum_i64(c->delta, c->d_excl, nev, c->tmp, s);
+        seq_ev_need(EV, kEV, nev, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->rbeg, c->rend, c->c_excl,
+                    c->c_sorted, c->packed, s);
+        inclusive_max_u64(c->packed, c->qmax, nev, c->tmp, s);
+        seq_ev_emit(EV, kEV, nev, c->qmax, c->ebeg, c->emit, c->qbefore, s);
+        exclusive_sum_i32(c->emit, c->em_excl, nM, c->tmp, s);
+    }
+    seq_block_final(k, c->ebeg, c->eend, c->qmax, c->rbeg, c->rend, c->qfin, c->left, s);
+    exclusive_sum_i32(c->left, c->left_excl, k, c->tmp, s);
+    const int64_t nX = nM + nR;
+    seq_place_m(c->M_node, c->M_from, c->M_to, nM, c->em_excl, c->pos_m, c->X_node, c->X_from, c->X_to, c->X_isr, s);
+    seq_place_r(c->R_node, c->R_from, c->R_to, RB, nR, c->rbeg, EV, c->ebeg, c->eend, c->qmax, c->pos_m, c->qfin,
+                c->left_excl, c->em_excl, c->emit, nM, c->X_node, c->X_from, c->X_to, c->X_isr, s);
+    ri.n_inter = nX;
+    if (T && T->X_node) {
+        d2h(T->X_node, c->X_node, sizeof(int32_t) * nX, s);
+        d2h(T->X_from, c->X_from, sizeof(int32_t) * nX, s);
+        d2h(T->X_to, c->X_to, sizeof(int32_t) * nX, s);
+    }
+
+    // ---- (c1) merge double moves
+    int64_t nI = 0;
+    if (nX > 0) {
+        seq_merge_flags(c->X_node, c->X_to, c->X_isr, nX, c->m_pos, c->r_to, c->part0, c->flags2, c->final_to, s);
+        select_flags(c->flags2, c->excl_i, c->idxD, c->counts + 5, nX, c->tmp, s);
+        nI = read_count(c, 5);
+        seq_build_I(c->idxD, c->counts + 5, nI, c->X_node, c->final_to, c->part0, c->I_node, c->I_from, c->I_to,
+                    c->pos, c->dest, s);
+    }
+    ri.n_seq = nI;
+
+    // ---- (c2) exact gains, balanced prefixes, best prefix
+    int32_t over0 = 0;
+    {
+        std::vector<int64_t> C0h(k);
+        read_i64(c, c->C0, k, C0h.data());
+        for (int32_t b = 0; b < k; b++) over0 += C0h[b] > c->Lmax;
+    }
+    UPR_CUDA(cudaMemsetAsync(c->diff, 0, sizeof(int32_t) * (nI + 1), s));
+    if (nI > 0) {
+        seq_gains(G, c->I_node, c->I_from, c->I_to, nI, c->pos, c->dest, c->part0, c->I_gain, c->hub_flag,
+                  c->hub_excl, c->hubs, c->counts + 6, c->tmp, s);
+        inclusive_sum_i64(c->I_gain, c->Gsum, nI, c->tmp, s);
+        uint64_t *kE; uint32_t *E;
+        seq_iev_keys(c->I_from, c->I_to, nI, c->sb[2].k, c->sb[2].v, s);
+        c->sb[2].run(2 * nI, kbits, c->tmp, s, &kE, &E);
+        UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
+        seq_iev_delta(c->I_node, E, kE, 2 * nI, G.vwgt, c->delta, c->ebeg, s);
+        exclusive_sum_i64(c->delta, c->d_excl, 2 * nI, c->tmp, s);
+        seq_iev_transitions(E, kE, 2 * nI, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->diff, s);
+    }
+    exclusive_sum_i32(c->diff, c->diff_excl, nI + 1, c->tmp, s);
+    seq_best(c->Gsum, c->diff, c->diff_excl, nI, over0, c->best_parts, c->best, s);
+    long long best[2];
+    UPR_CUDA(cudaMemcpyAsync(c->h, c->best, sizeof(best), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    memcpy(best, c->h, sizeof(best));
+    if (T) {
+        T->n_cand = ri.n_cand; T->n_moves = nM; T->n_rebal = nR; T->subrounds = ri.subrounds; T->n_inter = nX;
+        T->n_seq = nI;
+        d2h(T->I_node, c->I_node, sizeof(int32_t) * nI, s);
+        d2h(T->I_from, c->I_from, sizeof(int32_t) * nI, s);
+        d2h(T->I_to, c->I_to, sizeof(int32_t) * nI, s);
+        d2h(T->I_gain, c->I_gain, sizeof(int64_t) * nI, s);
+        if (T->I_eligible) {
+            std::vector<int32_t> df(nI + 1), de(nI + 1);
+            UPR_CUDA(cudaMemcpyAsync(df.data(), c->diff, sizeof(int32_t) * (nI + 1), cudaMemcpyDeviceToHost, s));
+            UPR_CUDA(cudaMemcpyAsync(de.data(), c->diff_excl, sizeof(int32_t) * (nI + 1), cudaMemcpyDeviceToHost, s));
+            UPR_CUDA(cudaStreamSynchronize(s));
+            for (int64_t j = 0; j <= nI; j++) T->I_eligible[j] = (over0 + de[j] + df[j]) == 0;
+        }
+        int64_t cb;
+        read_i64(c, c->cut, 1, &cb);
+        T->cut_before = cb;
+    }
+    // reset node-indexed markers for the next round
+    reset_nodes(c->I_node, nI, c->pos, INT32_MAX, s);
+    reset_nodes(c->M_node, nM, c->m_pos, -1, s);
+    reset_nodes(c->R_node, nR, c->r_to, -1, s);
+    if (best[1] < 0) {
+        UPR_CUDA(cudaStreamSynchronize(s));
+        return UPR_ERR_INFEASIBLE;
+    }
+    seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, nI, c->best, c->part0, c->C0, c->cut, s);
+    ri.best_len = best[1];
+    ri.best_gain = best[0];
+    if (T) {
+        T->best_len = best[1];
+        T->best_gain = best[0];
+        int64_t ca;
+        read_i64(c, c->cut, 1, &ca);
+        T->cut_after = ca;
+    }
+    return UPR_OK;
+}
+
+void free_ctx(upr_ctx *c) {
+    if (!c) return;
+    if (c->mem) cudaFree(c->mem);
+    if (c->h) cudaFreeHost(c->h);
+    if (c->h8) cudaFreeHost(c->h8);
+    for (auto &e : c->ev) if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+// part in [0, k)?
+__global__ void k_check_part(const int32_t *part, int64_t n, int32_t k, int32_t *bad) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n && (part[v] < 0 || part[v] >= k)) atomicOr(bad, 1);
+}
+
+upr_status load_part(upr_ctx *c, const int32_t *part) {
+    copy_in(c->part0, part, sizeof(int32_t) * c->n, c->s);
+    UPR_CUDA(cudaMemsetAsync(c->counts + 7, 0, sizeof(int32_t), c->s));
+    if (c->n > 0) {
+        k_check_part<<<(unsigned)ceil_div(c->n, 256), 256, 0, c->s>>>(c->part0, c->n, c->k, c->counts + 7);
+        UPR_LAUNCH_CHECK();
+    }
+    if (read_count(c, 7)) return UPR_ERR_INVALID;
+    block_weights(c->G, c->part0, c->C0, c->s);
+    edge_cut(c->G, c->part0, c->cut, c->s);
+    return UPR_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void upr_params_default(upr_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->t_num = 7; p->t_den = 10;
+    p->tau1_num = 1; p->tau1_den = 4;
+    p->max_subrounds = 64;
+    p->validate = 1;
+    p->round_offset = 0;
+    p->total_rounds = 0;
+    p->stream = nullptr;
+}
+
+const char *upr_status_str(upr_status s) {
+    switch (s) {
+        case UPR_OK: return "UPR_OK";
+        case UPR_PENDING: return "UPR_PENDING";
+        case UPR_ERR_INVALID: return "UPR_ERR_INVALID";
+        case UPR_ERR_OOM: return "UPR_ERR_OOM";
+        case UPR_ERR_CUDA: return "UPR_ERR_CUDA";
+        case UPR_ERR_INFEASIBLE: return "UPR_ERR_INFEASIBLE";
+        case UPR_ERR_BUSY: return "UPR_ERR_BUSY";
+        case UPR_ERR_TIMEOUT: return "UPR_ERR_TIMEOUT";
+        case UPR_ERR_NOT_FOUND: return "UPR_ERR_NOT_FOUND";
+        default: return "UPR_UNKNOWN";
+    }
+}
+
+static bool params_ok(const upr_params &p) {
+    return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
+           p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
+           p.total_rounds >= 0 && p.total_rounds <= 65536;
+}
+
+upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_params *params, upr_ctx **out) {
+    if (!g || !out || g->n < 0 || g->m < 0 || g->n >= (1LL << 31) || g->m >= (1LL << 31) || k < 2 || k > kMaxK ||
+        !(eps > 0) || eps > 1000.0 || (g->n > 0 && !g->xadj) || (g->m > 0 && !g->adjncy))
+        return UPR_ERR_INVALID;
+    upr_params prm;
+    upr_params_default(&prm);
+    if (params) prm = *params;
+    if (!params_ok(prm)) return UPR_ERR_INVALID;
+    upr_ctx *c = new (std::nothrow) upr_ctx();
+    if (!c) return UPR_ERR_OOM;
+    try {
+        UPR_CUDA(cudaGetDevice(&c->device));
+        c->n = g->n; c->m = g->m; c->k = k; c->prm = prm;
+        c->s = (cudaStream_t)prm.stream;
+        c->eps_ppm = (int64_t)(eps * 1e6 + 0.5);
+        // host copies of xadj / vwgt for create-time decisions
+        std::vector<int64_t> xadj_h(c->n + 1, 0);
+        if (c->n > 0) {
+            UPR_CUDA(cudaMemcpy(xadj_h.data(), g->xadj, sizeof(int64_t) * (c->n + 1),
+                                mem_kind(g->xadj) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        }
+        if (c->n > 0 && (xadj_h[0] != 0 || xadj_h[c->n] != c->m)) { free_ctx(c); return UPR_ERR_INVALID; }
+        for (int64_t v = 0; v < c->n; v++)
+            if (xadj_h[v + 1] < xadj_h[v]) { free_ctx(c); return UPR_ERR_INVALID; }
+        int64_t cmax = 1, total = c->n;
+        if (g->vwgt && c->n > 0) {
+            std::vector<int32_t> vw(c->n);
+            UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * c->n,
+                                mem_kind(g->vwgt) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+            total = 0;
+            for (int32_t w : vw) {
+                if (w <= 0) { free_ctx(c); return UPR_ERR_INVALID; }
+                total += w;
+                cmax = std::max<int64_t>(cmax, w);
+            }
+        }
+        c->total_w = total;
+        c->cbits = bit_length((uint64_t)cmax);
+        const int64_t avg = (total + k - 1) / k;
+        c->Lmax = (int64_t)(((i128)avg * (1000000 + c->eps_ppm)) / 1000000);
+        std::vector<HubChunk> chunks;
+        for (int64_t v = 0; v < c->n; v++) {
+            const int64_t d = xadj_h[v + 1] - xadj_h[v];
+            if (d > kHubDegree)
+                for (int64_t b = xadj_h[v]; b < xadj_h[v + 1]; b += 8192)
+                    chunks.push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
+        }
+        c->n_chunks = (int64_t)chunks.size();
+        Arena A;
+        layout(c, A);
+        if (cudaMalloc(&c->mem, A.off) != cudaSuccess) { cudaGetLastError(); free_ctx(c); return UPR_ERR_OOM; }
+        A.base = (char *)c->mem; A.off = 0;
+        layout(c, A);
+        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * std::max<int64_t>(4 * k, 2 * kSlots + 64)));
+        UPR_CUDA(cudaMallocHost((void **)&c->h8, 2 * (size_t)k + 64));
+        for (auto &e : c->ev) UPR_CUDA(cudaEventCreate(&e));
+        cudaStream_t s = c->s;
+        copy_in(c->xadj, g->xadj, sizeof(int64_t) * (c->n + 1), s);
+        copy_in(c->adj, g->adjncy, sizeof(int32_t) * c->m, s);
+        if (g->adjwgt) copy_in(c->adjw, g->adjwgt, sizeof(int32_t) * c->m, s);
+        if (g->vwgt) copy_in(c->vwgt, g->vwgt, sizeof(int32_t) * c->n, s);
+        if (!chunks.empty())
+            UPR_CUDA(cudaMemcpyAsync(c->hub_chunks, chunks.data(), sizeof(HubChunk) * chunks.size(),
+                                     cudaMemcpyHostToDevice, s));
+        c->G = GraphDev{c->n, c->m, k, c->xadj, c->adj, g->adjwgt ? c->adjw : nullptr, g->vwgt ? c->vwgt : nullptr,
+                        c->wI};
+        if (prm.validate) {
+            validate_graph(c->G, c->vacc, c->vflags, s);
+            uint64_t acc[2]; int32_t flags;
+            UPR_CUDA(cudaMemcpyAsync(acc, c->vacc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+            UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+            UPR_CUDA(cudaStreamSynchronize(s));
+            if (flags != 0 || acc[0] != acc[1]) { free_ctx(c); return UPR_ERR_INVALID; }
+        }
+        incident_weights(c->G, c->wI, c->scal, s);
+        read_i64(c, c->scal, 1, &c->wmax);
+        if (c->wmax > 0x7fffffffLL) { free_ctx(c); return UPR_ERR_INVALID; }
+        c->gbits = std::max(1, bit_length((uint64_t)c->wmax));
+        if (1 + c->gbits + 2 * c->cbits > 63) { free_ctx(c); return UPR_ERR_INVALID; }
+        fill_i32(c->pos, c->n, INT32_MAX, s);
+        fill_i32(c->m_pos, c->n, -1, s);
+        fill_i32(c->r_to, c->n, -1, s);
+        UPR_CUDA(cudaStreamSynchronize(s));
+    } catch (const CudaError &) {
+        free_ctx(c);
+        return UPR_ERR_CUDA;
+    } catch (const std::bad_alloc &) {
+        free_ctx(c);
+        return UPR_ERR_OOM;
+    }
+    *out = c;
+    return UPR_OK;
+}
+
+void upr_destroy(upr_ctx *c) { free_ctx(c); }
+
+upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
+    if (!c || !part || !cut) return UPR_ERR_INVALID;
+    try {
+        upr_status st = load_part(c, part);
+        if (st != UPR_OK) return st;
+        int64_t tmp[1];
+        read_i64(c, c->cut, 1, tmp);
+        *cut = tmp[0];
+        if (block_weights_out) read_i64(c, c->C0, c->k, block_weights_out);
+    } catch (const CudaError &) {
+        return UPR_ERR_CUDA;
+    }
+    return UPR_OK;
+}
+
+upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_stats *stats) {
+    (void)seed;
+    if (!c || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
+    const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
+    if (c->prm.round_offset + rounds > total) return UPR_ERR_INVALID;
+    upr_stats st{};
+    const long long launches0 = g_upr_launches.load();
+    try {
+        UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
+        upr_status rc = load_part(c, part);
+        if (rc != UPR_OK) return rc;
+        read_i64(c, c->cut, 1, &st.cut_in);
+        std::vector<int64_t> C0h(c->k);
+        read_i64(c, c->C0, c->k, C0h.data());
+        bool balanced = true;
+        for (int32_t b = 0; b < c->k; b++) balanced = balanced && C0h[b] <= c->Lmax;
+        if (!balanced) {
+            RoundInfo ri;
+            rc = run_round(c, 0, total, true, ri, nullptr);
+            st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
+            st.n_rebalance_moves += ri.n_rebal; st.subrounds += ri.subrounds; st.n_sequence += ri.n_seq;
+            st.n_applied += ri.best_len;
+            if (rc != UPR_OK) return rc;
+            st.repaired_input = 1;
+        }
+        for (int32_t i = 1; i <= rounds; i++) {
+            RoundInfo ri;
+            rc = run_round(c, c->prm.round_offset + i, total, false, ri, nullptr);
+            if (rc != UPR_OK) return rc;
+            st.rounds_run++;
+            st.n_candidates += ri.n_cand; st.n_moves += ri.n_moves; st.n_rebalance_moves += ri.n_rebal;
+            st.n_sequence += ri.n_seq; st.n_applied += ri.best_len; st.subrounds += ri.subrounds;
+            st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
+        }
+        copy_out(part, c->part0, sizeof(int32_t) * c->n, c->s);
+        read_i64(c, c->cut, 1, &st.cut_out);
+        UPR_CUDA(cudaEventRecord(c->ev[3], c->s));
+        UPR_CUDA(cudaEventSynchronize(c->ev[3]));
+        float ms = 0;
+        UPR_CUDA(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+        st.ms_device = ms;
+    } catch (const CudaError &) {
+        return UPR_ERR_CUDA;
+    }
+    st.kernel_launches = (int32_t)(g_upr_launches.load() - launches0);
+    st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
+                          4 * c->n * (int64_t)c->k;
+    if (stats) *stats = st;
+    return UPR_OK;
+}
+
+upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int64_t *wI) {
+    if (!c || !part) return UPR_ERR_INVALID;
+    try {
+        upr_status rc = load_part(c, part);
+        if (rc != UPR_OK) return rc;
+        RoundInfo ri;
+        build_table(c, c->part0, ri);
+        if (W) UPR_CUDA(cudaMemcpyAsync(W, c->W, sizeof(int32_t) * c->n * c->k, cudaMemcpyDeviceToHost, c->s));
+        if (wI && c->n > 0) {
+            std::vector<int32_t> w(c->n);
+            UPR_CUDA(cudaMemcpyAsync(w.data(), c->wI, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->s));
+            UPR_CUDA(cudaStreamSynchronize(c->s));
+            for (int64_t v = 0; v < c->n; v++) wI[v] = w[v];
+        }
+        UPR_CUDA(cudaStreamSynchronize(c->s));
+    } catch (const CudaError &) {
+        return UPR_ERR_CUDA;
+    }
+    return UPR_OK;
+}
+
+upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int32_t rebalance_only, upr_trace *trace) {
+    if (!c || !part || !trace || R < 1 || R > 65536 || (!rebalance_only && (r < 1 || r > R))) return UPR_ERR_INVALID;
+    int8_t *avail_d = nullptr;
+    int32_t *slot_d = nullptr;
+    upr_status rc = UPR_OK;
+    try {
+        rc = load_part(c, part);
+        if (rc != UPR_OK) return rc;
+        UPR_CUDA(cudaMalloc(&avail_d, std::max<int64_t>(c->n, 1)));
+        UPR_CUDA(cudaMalloc(&slot_d, sizeof(int32_t) * std::max<int64_t>(c->n, 1)));
+        TraceSink ts{trace, avail_d, slot_d};
+        RoundInfo ri;
+        rc = run_round(c, r, R, rebalance_only != 0, ri, &ts);
+        if (rc == UPR_OK) copy_out(part, c->part0, sizeof(int32_t) * c->n, c->s);
+        UPR_CUDA(cudaStreamSynchronize(c->s));
+    } catch (const CudaError &) {
+        rc = UPR_ERR_CUDA;
+    }
+    if (avail_d) cudaFree(avail_d);
+    if (slot_d) cudaFree(slot_d);
+    return rc;
+}
+
+}  // extern "C"
+
+// Device bytes a context for (n, m, k) allocates (used by the server's admission).
+size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k) {
+    upr_ctx c;
+    c.n = n; c.m = m; c.k = k;
+    c.n_chunks = m / 4096 + 1;
+    Arena A;
+    layout(&c, A);
+    return A.off + ((size_t)1 << 20);
+}

@@ -1,0 +1,299 @@
+// Step (e): block weights and edge cut (Sec. 2); step (a): the gain table
+// omega(v, V_b) (Sec. 2, Sec. 6.1) and its delta update; create-time graph
+// checks and incident weights omega(I(v)).
+#include "kernels.h"
+
+namespace upr {
+namespace {
+
+constexpr int kChunk = 1024;   // adjacency entries per warp in entry-parallel passes
+
+// Owner of adjacency entry e: the v with xadj[v] <= e < xadj[v+1] (rows may be empty).
+__device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ xadj, int64_t n, int64_t e) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (xadj[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block weights: per-CTA shared accumulators, lanes with the same block
+// combined with __match_any_sync before the shared atomic.
+__global__ void k_block_weights(const int32_t *__restrict__ part, const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
+                                int64_t *__restrict__ C) {
+    extern __shared__ unsigned long long s_c[];
+    for (int b = threadIdx.x; b < k; b += blockDim.x) s_c[b] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = base + threadIdx.x;
+        int32_t b = v < n ? part[v] : -1;
+        long long c = v < n ? (vwgt ? vwgt[v] : 1) : 0;
+        unsigned peers = __match_any_sync(0xffffffffu, b);
+        // sum c over the peers (the leader adds the group's total)
+        long long tot = 0;
+        for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, c, __ffs(m) - 1);
+        if (b >= 0 && (peers & lt) == 0) atomicAdd(&s_c[b], (unsigned long long)tot);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < k; b += blockDim.x)
+        if (s_c[b]) atomicAdd((unsigned long long *)&C[b], s_c[b]);
+}
+
+__global__ void k_edge_cut(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                           const int32_t *__restrict__ adjw, const int32_t *__restrict__ part, int64_t n, int64_t m,
+                           unsigned long long *__restrict__ out) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = warp * kChunk, e1 = min(m, e0 + kChunk);
+    long long acc = 0;
+    if (e0 < m) {
+        int64_t e = e0 + lane;
+        int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
+        for (; e < e1; e += 32) {
+            while (xadj[v + 1] <= e) v++;
+            if (part[v] != part[adj[e]]) acc += adjw ? adjw[e] : 1;
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0 && acc) atomicAdd(out, (unsigned long long)acc);
+}
+
+// omega(I(v)) per node (warp per node); records the maximum and overflow.
+__global__ void k_incident(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adjw, int64_t n,
+                           int32_t *__restrict__ wI, unsigned long long *__restrict__ wmax) {
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n) return;
+    long long acc = 0;
+    for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) acc += adjw ? adjw[e] : 1;
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        wI[v] = acc > 0x7fffffffLL ? 0x7fffffff : (int32_t)acc;
+        atomicMax(wmax, (unsigned long long)acc);
+    }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t entry_hash(uint64_t a, uint64_t b, uint64_t w) {
+    return mix64(mix64(mix64(a + 0x1234567ull) ^ b) + w);
+}
+
+// Validation bits: 1 xadj, 2 neighbour range, 4 self loop, 8 edge weight, 16 node
+// weight, 64 asymmetric (sum of hash(v,u,w) over entries != sum of hash(u,v,w)).
+__global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                                   const int32_t *__restrict__ adjw, int64_t n, int64_t m,
+                                   unsigned long long *__restrict__ acc, int32_t *__restrict__ flags) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = warp * kChunk, e1 = min(m, e0 + kChunk);
+    unsigned long long h1 = 0, h2 = 0;
+    int32_t f = 0;
+    if (e0 < m) {
+        int64_t e = e0 + lane;
+        int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
+        for (; e < e1; e += 32) {
+            while (xadj[v + 1] <= e) v++;
+            int32_t u = adj[e];
+            int32_t w = adjw ? adjw[e] : 1;
+            if (u < 0 || u >= n) { f |= 2; continue; }
+            if (u == v) f |= 4;
+            if (w <= 0) f |= 8;
+            h1 += entry_hash((uint64_t)v, (uint64_t)u, (uint64_t)(uint32_t)w);
+            h2 += entry_hash((uint64_t)u, (uint64_t)v, (uint64_t)(uint32_t)w);
+        }
+    }
+    h1 = warp_sum(h1);
+    h2 = warp_sum(h2);
+    for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) {
+        if (h1) atomicAdd(&acc[0], h1);
+        if (h2) atomicAdd(&acc[1], h2);
+        if (f) atomicOr(flags, f);
+    }
+}
+
+__global__ void k_validate_nodes(const int64_t *__restrict__ xadj, const int32_t *__restrict__ vwgt, int64_t n, int64_t m,
+                                 int32_t *__restrict__ flags) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v > n) return;
+    int32_t f = 0;
+    if (v == 0 && xadj[0] != 0) f |= 1;
+    if (v == n && xadj[n] != m) f |= 1;
+    if (v < n && xadj[v + 1] < xadj[v]) f |= 1;
+    if (v < n && vwgt && vwgt[v] <= 0) f |= 16;
+    if (f) atomicOr(flags, f);
+}
+
+// Dense gain table: G lanes per node, a k-int row per group in shared memory,
+// shared atomics per adjacency entry, one coalesced row store (int4 when
+// k % 4 == 0).  Nodes of degree > kHubDegree get a zero row here; their rows
+// are accumulated by k_table_hub_chunks afterwards.
+template <int G>
+__global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                                                     const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
+                                                     int64_t n, int32_t k, int32_t *__restrict__ W) {
+    extern __shared__ int s_rows[];
+    constexpr int kGroups = 256 / G;
+    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    int *row = s_rows + gid * k;
+    const bool vec = (k & 3) == 0;
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t v = base + gid;
+        const bool active = v < n;
+        for (int b = gl; b < k; b += G) row[b] = 0;
+        __syncwarp();
+        if (active) {
+            const int64_t b0 = xadj[v], b1 = xadj[v + 1];
+            if (b1 - b0 <= kHubDegree) {
+                if (adjw) {
+                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[adj[e]]], adjw[e]);
+                } else {
+                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[adj[e]]], 1);
+                }
+            }
+        }
+        __syncwarp();
+        if (active) {
+            int32_t *dst = W + v * (int64_t)k;
+            if (vec) {
+                for (int b = gl * 4; b < k; b += G * 4)
+                    *reinterpret_cast<int4 *>(dst + b) = *reinterpret_cast<const int4 *>(row + b);
+            } else {
+                for (int b = gl; b < k; b += G) dst[b] = row[b];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Hub rows: one CTA per chunk of a hub's adjacency, shared-memory row, then
+// atomic adds of the non-zero entries into the (zeroed) global row.
+__global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__restrict__ chunks, const int32_t *__restrict__ adj,
+                                                          const int32_t *__restrict__ adjw,
+                                                          const int32_t *__restrict__ part, int32_t k,
+                                                          int32_t *__restrict__ W) {
+    extern __shared__ int s_row[];
+    const HubChunk ch = chunks[blockIdx.x];
+    for (int b = threadIdx.x; b < k; b += blockDim.x) s_row[b] = 0;
+    __syncthreads();
+    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x)
+        atomicAdd(&s_row[part[adj[e]]], adjw ? adjw[e] : 1);
+    __syncthreads();
+    int32_t *dst = W + (int64_t)ch.v * k;
+    for (int b = threadIdx.x; b < k; b += blockDim.x)
+        if (s_row[b]) atomicAdd(&dst[b], s_row[b]);
+}
+
+// Delta update: warp per moved node.
+__global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                             const int32_t *__restrict__ adjw, int32_t k, int32_t *__restrict__ W,
+                             const int32_t *__restrict__ nodes, const int32_t *__restrict__ from,
+                             const int32_t *__restrict__ to, const int32_t *__restrict__ d_count) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t cnt = *d_count;
+    for (int64_t j = i; j < cnt; j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t v = nodes[j], a = from[j], b = to[j];
+        for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) {
+            const int32_t w = adjw ? adjw[e] : 1;
+            int32_t *row = W + (int64_t)adj[e] * k;
+            atomicSub(&row[a], w);
+            atomicAdd(&row[b], w);
+        }
+    }
+}
+
+int sm_count() {
+    static int cnt = 0;
+    if (!cnt) {
+        int dev = 0;
+        UPR_CUDA(cudaGetDevice(&dev));
+        UPR_CUDA(cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return cnt;
+}
+
+}  // namespace
+
+void block_weights(const GraphDev &g, const int32_t *part, int64_t *C, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(C, 0, sizeof(int64_t) * g.k, s));
+    if (g.n == 0) return;
+    int64_t blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count() * 8);
+    k_block_weights<<<(unsigned)blocks, 256, sizeof(int64_t) * g.k, s>>>(part, g.vwgt, g.n, g.k, C);
+    UPR_LAUNCH_CHECK();
+}
+
+void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(cut, 0, sizeof(int64_t), s));
+    if (g.m == 0) return;
+    int64_t warps = ceil_div(g.m, kChunk);
+    k_edge_cut<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(g.xadj, g.adj, g.adjw, part, g.n, g.m,
+                                                                   (unsigned long long *)cut);
+    UPR_LAUNCH_CHECK();
+}
+
+void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(wmax, 0, sizeof(int64_t), s));
+    if (g.n == 0) return;
+    k_incident<<<(unsigned)ceil_div(g.n * 32, 256), 256, 0, s>>>(g.xadj, g.adjw, g.n, wI, (unsigned long long *)wmax);
+    UPR_LAUNCH_CHECK();
+}
+
+void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(d_acc, 0, 2 * sizeof(uint64_t), s));
+    UPR_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int32_t), s));
+    k_validate_nodes<<<(unsigned)ceil_div(g.n + 1, 256), 256, 0, s>>>(g.xadj, g.vwgt, g.n, g.m, d_flags);
+    UPR_LAUNCH_CHECK();
+    if (g.m > 0 && g.n > 0) {
+        int64_t warps = ceil_div(g.m, kChunk);
+        k_validate_entries<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(
+            g.xadj, g.adj, g.adjw, g.n, g.m, (unsigned long long *)d_acc, d_flags);
+        UPR_LAUNCH_CHECK();
+    }
+}
+
+void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
+                cudaStream_t s) {
+    if (g.n == 0) return;
+    const int k = g.k;
+    int G = k / 4;
+    G = G < 4 ? 4 : (G > 32 ? 32 : G);
+    G = G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
+    const size_t shm = (size_t)(256 / G) * k * sizeof(int);
+    const int64_t groups = 256 / G;
+    const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count() * 16);
+    if (shm > 48 * 1024) {
+        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    }
+    switch (G) {
+        case 4: k_table_dense<4><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
+        case 8: k_table_dense<8><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
+        case 16: k_table_dense<16><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
+        default: k_table_dense<32><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
+    }
+    UPR_LAUNCH_CHECK();
+    if (n_chunks > 0) {
+        k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * k, s>>>(hub_chunks, g.adj, g.adjw, part, k, W);
+        UPR_LAUNCH_CHECK();
+    }
+}
+
+void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
+                const int32_t *d_count, int64_t max_count, cudaStream_t s) {
+    if (max_count <= 0) return;
+    int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
+    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, W, nodes, from, to, d_count);
+    UPR_LAUNCH_CHECK();
+}
+
+}  // namespace upr

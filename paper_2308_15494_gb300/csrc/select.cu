@@ -1,0 +1,309 @@
+// Step (b): rebalancing availability, slots and bucket weights (Alg. 1 lines
+// 1-2, Sec. 4.3), each boundary node's best move by gain minus penalty
+// (Alg. 1 line 8), penalties with the inflow of better-ranked candidates,
+// the global move order M (Sec. 4.4), and the application of M.
+#include "kernels.h"
+
+namespace upr {
+namespace {
+
+// 3^i for i = 0..40 (3^40 < 2^64).
+__constant__ uint64_t c_pow3[41];
+
+int sm_count_sel() {
+    static int cnt = 0;
+    if (!cnt) {
+        int dev = 0;
+        UPR_CUDA(cudaGetDevice(&dev));
+        UPR_CUDA(cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return cnt;
+}
+
+void ensure_pow3() {
+    static int done_dev = -1;
+    int dev = 0;
+    UPR_CUDA(cudaGetDevice(&dev));
+    if (done_dev == dev) return;
+    uint64_t p[41];
+    p[0] = 1;
+    for (int i = 1; i <= 40; i++) p[i] = p[i - 1] * 3;
+    UPR_CUDA(cudaMemcpyToSymbol(c_pow3, p, sizeof(p)));
+    done_dev = dev;
+}
+
+// (3/2)^s * c >= omega, exactly.
+__device__ __forceinline__ bool slot_ok(int s, uint64_t omega, uint64_t c) {
+    if (s >= 0) return (u128)c_pow3[s] * c >= ((u128)omega << s);
+    return ((u128)c << (-s)) >= (u128)c_pow3[-s] * omega;
+}
+
+// Smallest s in [kSlotLo, kSlotHi] with (3/2)^s >= omega / c (kSlotHi if none).
+__device__ __forceinline__ int slot_of(uint64_t omega, uint64_t c) {
+    int lo = kSlotLo, hi = kSlotHi;
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (slot_ok(mid, omega, c)) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Penalty of moving weight cu into block b that would then exceed L_max by x;
+// -1 = forbidden (no slot's cumulative weight covers x).
+__device__ __forceinline__ int64_t penalty(const Penalty &p, int32_t b, int64_t x, int64_t cu) {
+    if (x <= 0) return 0;
+    const int64_t *row = p.PW + (int64_t)b * kSlots;
+    if (row[kSlots - 1] < x) return -1;
+    int lo = 0, hi = kSlots - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (row[mid] >= x) hi = mid; else lo = mid + 1;
+    }
+    return (int64_t)(((u128)(uint64_t)cu * (uint64_t)p.F[lo]) >> kQ);
+}
+
+__global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
+                          const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
+                          int32_t t_num, int32_t t_den, unsigned long long *__restrict__ BW, int use_shared,
+                          int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out) {
+    extern __shared__ unsigned long long s_bw[];
+    const int bins = k * kSlots;
+    if (use_shared) {
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) s_bw[i] = 0;
+        __syncthreads();
+    }
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = part[v];
+        const int64_t own = W[v * (int64_t)k + a];
+        const int64_t c = vwgt ? vwgt[v] : 1;
+        const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wI[v];
+        const int s = slot_of((uint64_t)own, (uint64_t)c);
+        if (av) {
+            unsigned long long *dst = use_shared ? s_bw : BW;
+            atomicAdd(&dst[a * kSlots + (s - kSlotLo)], (unsigned long long)c);
+        }
+        if (avail_out) avail_out[v] = av ? 1 : 0;
+        if (slot_out) slot_out[v] = s;
+    }
+    if (use_shared) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < bins; i += blockDim.x)
+            if (s_bw[i]) atomicAdd(&BW[i], s_bw[i]);
+    }
+}
+
+__global__ void k_bucket_prefix(const int64_t *__restrict__ BW, int64_t *__restrict__ PW, int32_t k) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= k) return;
+    int64_t acc = 0;
+    for (int l = 0; l < kSlots; l++) { acc += BW[b * kSlots + l]; PW[b * kSlots + l] = acc; }
+}
+
+// G lanes per node: best target by (gain - penalty) among adjacent blocks,
+// ties to the smaller block id; candidate iff the score is positive and v is
+// a boundary node.
+template <int G>
+__global__ void __launch_bounds__(256) k_select(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
+                                                const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt,
+                                                int64_t n, int32_t k, Penalty pen, int32_t *__restrict__ cand_tgt,
+                                                int64_t *__restrict__ cand_s0, int32_t *__restrict__ cand_gain,
+                                                int32_t *__restrict__ flags) {
+    constexpr int kGroups = 256 / G;
+    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t v = base + gid;
+        const bool active = v < n;
+        int64_t best = 0;
+        int32_t bt = -1, bg = 0;
+        if (active) {
+            const int32_t a = part[v];
+            const int32_t *row = W + v * (int64_t)k;
+            const int32_t own = row[a];
+            if (own < wI[v]) {
+                const int64_t c = vwgt ? vwgt[v] : 1;
+                for (int b = gl; b < k; b += G) {
+                    const int32_t w = row[b];
+                    if (b == a || w <= 0) continue;
+                    const int64_t gain = (int64_t)w - own;
+                    const int64_t p = penalty(pen, b, pen.C[b] + c - pen.Lmax, c);
+                    if (p < 0) continue;
+                    const int64_t sc = gain - p;
+                    if (bt < 0 || sc > best) { best = sc; bt = b; bg = (int32_t)gain; }
+                }
+            }
+        }
+        int64_t s = best;
+        int32_t id = bt;
+        group_argmax<G>(s, id);
+        // lanes own disjoint blocks, so exactly one lane holds the winner's gain
+        const int32_t gsel = group_sum<G>((id >= 0 && bt == id) ? bg : 0);
+        if (active && gl == 0) {
+            const bool cand = id >= 0 && s > 0;
+            cand_tgt[v] = cand ? id : -1;
+            cand_s0[v] = cand ? s : 0;
+            cand_gain[v] = cand ? gsel : 0;
+            flags[v] = cand ? 1 : 0;
+        }
+    }
+}
+
+__global__ void k_cand_keys(const int32_t *__restrict__ cand_idx, const int32_t *__restrict__ d_count,
+                            const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ cand_s0,
+                            uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *d_count) return;
+    const int32_t v = cand_idx[i];
+    keys[i] = ((uint64_t)cand_tgt[v] << 31) | (uint64_t)(0x7fffffffLL - cand_s0[v]);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_cand_gather(const int32_t *__restrict__ cand_idx, const uint32_t *__restrict__ order,
+                              const int32_t *__restrict__ d_count, const int32_t *__restrict__ cand_tgt,
+                              const int32_t *__restrict__ vwgt, int64_t *__restrict__ c_sorted,
+                              int32_t *__restrict__ seg_first) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *d_count) return;
+    const int32_t v = cand_idx[order[j]];
+    c_sorted[j] = vwgt ? vwgt[v] : 1;
+    const int32_t t = cand_tgt[v];
+    if (j == 0 || cand_tgt[cand_idx[order[j - 1]]] != t) seg_first[t] = (int32_t)j;
+}
+
+__global__ void k_inflow(const int32_t *__restrict__ cand_idx, const uint32_t *__restrict__ order,
+                         const int32_t *__restrict__ d_count, const int32_t *__restrict__ cand_tgt,
+                         const int32_t *__restrict__ cand_gain, const int32_t *__restrict__ vwgt,
+                         const int64_t *__restrict__ c_excl, const int32_t *__restrict__ seg_first, Penalty pen,
+                         int32_t *__restrict__ keep, int64_t *__restrict__ score) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *d_count) return;
+    const uint32_t i = order[j];
+    const int32_t v = cand_idx[i];
+    const int32_t t = cand_tgt[v];
+    const int64_t c = vwgt ? vwgt[v] : 1;
+    const int64_t inflow = c_excl[j] - c_excl[seg_first[t]];
+    const int64_t p = penalty(pen, t, pen.C[t] + inflow + c - pen.Lmax, c);
+    const int64_t s = (int64_t)cand_gain[v] - p;
+    const bool kp = p >= 0 && s > 0;
+    keep[i] = kp ? 1 : 0;
+    score[i] = kp ? s : 0;
+}
+
+__global__ void k_move_keys(const int32_t *__restrict__ m_idx, const int32_t *__restrict__ d_count,
+                            const int64_t *__restrict__ score, uint64_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *d_count) return;
+    keys[j] = (uint64_t)(0x7fffffffLL - score[m_idx[j]]);
+    vals[j] = (uint32_t)j;
+}
+
+__global__ void k_apply_moves(const int32_t *__restrict__ cand_idx, const int32_t *__restrict__ m_idx,
+                              const uint32_t *__restrict__ order, const int32_t *__restrict__ d_count,
+                              const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ score,
+                              const int32_t *__restrict__ vwgt, const int32_t *__restrict__ part0,
+                              int32_t *__restrict__ part, unsigned long long *__restrict__ C,
+                              int32_t *__restrict__ M_node, int32_t *__restrict__ M_from, int32_t *__restrict__ M_to,
+                              int64_t *__restrict__ M_score, int32_t *__restrict__ m_pos) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= *d_count) return;
+    const int32_t i = m_idx[order[p]];
+    const int32_t v = cand_idx[i];
+    const int32_t a = part0[v], b = cand_tgt[v];
+    const unsigned long long c = vwgt ? (unsigned long long)vwgt[v] : 1ull;
+    M_node[p] = v;
+    M_from[p] = a;
+    M_to[p] = b;
+    M_score[p] = score[i];
+    m_pos[v] = (int32_t)p;
+    part[v] = b;
+    atomicAdd(&C[a], (unsigned long long)(-(long long)c));
+    atomicAdd(&C[b], c);
+}
+
+}  // namespace
+
+void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
+             int64_t *PW, int8_t *avail_out, int32_t *slot_out, cudaStream_t s) {
+    ensure_pow3();
+    UPR_CUDA(cudaMemsetAsync(BW, 0, sizeof(int64_t) * g.k * kSlots, s));
+    if (g.n > 0) {
+        const size_t shm = sizeof(unsigned long long) * (size_t)g.k * kSlots;
+        const int use_shared = shm <= 200 * 1024;
+        if (use_shared && shm > 48 * 1024)
+            UPR_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        int64_t blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * (shm > 48 * 1024 ? 1 : 4));
+        k_buckets<<<(unsigned)blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, t_num, t_den,
+                                                                      (unsigned long long *)BW, use_shared,
+                                                                      avail_out, slot_out);
+        UPR_LAUNCH_CHECK();
+    }
+    k_bucket_prefix<<<(unsigned)ceil_div(g.k, 128), 128, 0, s>>>(BW, PW, g.k);
+    UPR_LAUNCH_CHECK();
+}
+
+int select_group(int k) {
+    int G = k / 4;
+    return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
+}
+
+void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Penalty pen, int32_t *cand_tgt,
+                  int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s) {
+    if (g.n == 0) return;
+    const int G = select_group(g.k);
+    const int64_t groups = 256 / G;
+    const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 16);
+#define UPR_SEL(GG) k_select<GG><<<(unsigned)blocks, 256, 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, pen, cand_tgt, \
+                                                                  cand_s0, cand_gain, flags)
+    switch (G) {
+        case 4: UPR_SEL(4); break;
+        case 8: UPR_SEL(8); break;
+        case 16: UPR_SEL(16); break;
+        default: UPR_SEL(32); break;
+    }
+#undef UPR_SEL
+    UPR_LAUNCH_CHECK();
+}
+
+void cand_keys(const int32_t *cand_idx, const int32_t *d_count, const int32_t *cand_tgt, const int64_t *cand_s0,
+               uint64_t *keys, uint32_t *vals, int64_t max_count, cudaStream_t s) {
+    if (max_count <= 0) return;
+    k_cand_keys<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, d_count, cand_tgt, cand_s0, keys, vals);
+    UPR_LAUNCH_CHECK();
+}
+
+void cand_gather(const GraphDev &g, const int32_t *cand_idx, const uint32_t *order, const int32_t *d_count,
+                 const int32_t *cand_tgt, int64_t *c_sorted, int32_t *seg_first, int64_t max_count, cudaStream_t s) {
+    if (max_count <= 0) return;
+    k_cand_gather<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, order, d_count, cand_tgt, g.vwgt,
+                                                                     c_sorted, seg_first);
+    UPR_LAUNCH_CHECK();
+}
+
+void inflow_filter(const GraphDev &g, const int32_t *cand_idx, const uint32_t *order, const int32_t *d_count,
+                   const int32_t *cand_tgt, const int32_t *cand_gain, const int64_t *c_excl, const int32_t *seg_first,
+                   Penalty pen, int32_t *keep_flag, int64_t *score, int64_t max_count, cudaStream_t s) {
+    if (max_count <= 0) return;
+    k_inflow<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, order, d_count, cand_tgt, cand_gain, g.vwgt,
+                                                                c_excl, seg_first, pen, keep_flag, score);
+    UPR_LAUNCH_CHECK();
+}
+
+void move_keys(const int32_t *m_idx, const int32_t *d_count, const int64_t *score, uint64_t *keys, uint32_t *vals,
+               int64_t max_count, cudaStream_t s) {
+    if (max_count <= 0) return;
+    k_move_keys<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(m_idx, d_count, score, keys, vals);
+    UPR_LAUNCH_CHECK();
+}
+
+void apply_moves(const GraphDev &g, const int32_t *cand_idx, const int32_t *m_idx, const uint32_t *order,
+                 const int32_t *d_count, const int32_t *cand_tgt, const int64_t *score, const int32_t *part0,
+                 int32_t *part, int64_t *C, int32_t *M_node, int32_t *M_from, int32_t *M_to, int64_t *M_score,
+                 int32_t *m_pos, int64_t max_count, cudaStream_t s) {
+    if (max_count <= 0) return;
+    k_apply_moves<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, m_idx, order, d_count, cand_tgt, score,
+                                                                     g.vwgt, part0, part, (unsigned long long *)C,
+                                                                     M_node, M_from, M_to, M_score, m_pos);
+    UPR_LAUNCH_CHECK();
+}
+
+}  // namespace upr

@@ -1,0 +1,250 @@
+"""Parity of the CUDA library with the CPU oracle, through the C ABI.
+
+Everything the round computes is an integer, so the bar is bit-exact: the
+gain table, availability, slots, bucket weights, penalty factors, candidate
+targets and scores, the move list M, the rebalancing moves R with their
+sub-rounds, the interleaved sequence, the merged sequence I with its exact
+gains and balanced prefixes, the applied prefix, the partition, the cut and
+the block weights."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import brute
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def upr():
+    from paper_2308_15494_gb300 import build
+    build.build()
+    import paper_2308_15494_gb300 as m
+    m.load()
+    return m
+
+
+def _star_plus(seed, n=6000, k=8):
+    """A hub adjacent to every other node (degree above the hub threshold) plus random edges."""
+    rng = np.random.default_rng(seed)
+    src = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(0, n, 3 * n)])
+    dst = np.concatenate([np.arange(1, n), rng.integers(0, n, 3 * n)])
+    xadj, adj = synth.csr_from_edges(n, src.astype(np.int32), dst.astype(np.int32))
+    part = synth.part_random_balanced(n, k, seed)
+    return synth.Workload(f"star{n}", n, xadj, adj, None, None, k, 0.03, part, 3)
+
+
+def _isolated(n=100, k=4):
+    xadj = np.zeros(n + 1, np.int64)
+    adj = np.zeros(0, np.int32)
+    return synth.Workload("isolated", n, xadj, adj, None, None, k, 0.03, synth.part_random_balanced(n, k, 3), 2)
+
+
+def _heavy(seed=9, n=300, k=4):
+    """Node weights up to 2^20 (wide exact rebalancing keys)."""
+    w = synth.random_small(seed, n, 4.0, k, max_vw=(1 << 20) - 1, max_ew=100)
+    return w
+
+
+CASES = {
+    "small1": lambda: synth.random_small(1, 40, 4, 3),
+    "small2_hubs_isolated": lambda: synth.random_small(2, 64, 6, 4, hubs=2, isolated=3),
+    "small3_isolated": lambda: synth.random_small(3, 100, 3, 5, isolated=10),
+    "small4_hubs": lambda: synth.random_small(4, 200, 8, 8, hubs=3),
+    "small5_unit": lambda: synth.random_small(5, 150, 5, 2, weighted=False),
+    "small6_wide": lambda: synth.random_small(6, 300, 10, 16, hubs=1, max_vw=30, max_ew=64),
+    "small7_k_gt_n": lambda: synth.random_small(7, 9, 2, 12),
+    "k11_odd": lambda: synth.random_small(8, 500, 6, 11, max_vw=5),
+    "star_hub": lambda: _star_plus(10),
+    "isolated": _isolated,
+    "heavy_weights": _heavy,
+    "chung_lu_1k": lambda: synth.plain_tiny(4),
+    "rmat_s12_k64": lambda: synth.plain_large(10),
+}
+
+
+def _repaired(w):
+    """Imbalanced inputs get the round-0 repair first (as upr_refine does)."""
+    rc, p, _, _ = oracle.refine(w, w.part, rounds=0, total_rounds=1)
+    if rc == oracle.OK:
+        w.part = p
+    return w
+
+
+@pytest.fixture(params=sorted(CASES))
+def case(request):
+    return _repaired(CASES[request.param]())
+
+
+def test_cut_and_block_weights(upr, case):
+    ctx = upr.create_from_workload(case)
+    c, bw = upr.upr_cut(ctx, case.part)
+    c0, bw0 = oracle.cut(case, case.part)
+    assert c == c0 and np.array_equal(bw, bw0)
+
+
+def test_gain_table(upr, case):
+    ctx = upr.create_from_workload(case)
+    W, wI = upr.upr_debug_gain_table(ctx, case.part)
+    W0, wI0 = oracle.gain_table(case, case.part)
+    assert np.array_equal(W, W0) and np.array_equal(wI, wI0)
+
+
+def _compare_traces(t, o):
+    for key in ("n_cand", "n_moves", "n_rebal", "subrounds", "n_inter", "n_seq", "best_len", "best_gain",
+                "cut_before", "cut_after"):
+        assert t[key] == o[key], key
+    for key in ("avail", "slot", "bucket", "factor", "cand_target", "cand_s0", "cand_gain", "eligible"):
+        assert np.array_equal(np.asarray(t[key]), np.asarray(o[key])), key
+    for key in ("M", "R", "X", "I"):
+        for a, b in zip(t[key], o[key]):
+            assert np.array_equal(a, b), key
+
+
+@pytest.mark.parametrize("r,R", [(1, 4), (4, 4), (1, 1)])
+def test_round_trace(upr, case, r, R):
+    ctx = upr.create_from_workload(case)
+    rc, p, t = upr.upr_debug_round(ctx, case.part, r, R)
+    rc0, p0, c0, o = oracle.run_round(case, case.part, r, R)
+    assert rc == rc0
+    _compare_traces(t, o)
+    assert np.array_equal(p, p0)
+
+
+def test_round_zero_repair_trace(upr):
+    w = synth.random_small(41, 400, 5.0, 4, balanced=False)
+    assert np.any(brute.block_weights(w, w.part) > brute.lmax(w))
+    ctx = upr.create_from_workload(w)
+    rc, p, t = upr.upr_debug_round(ctx, w.part, 0, 4, rebalance_only=True)
+    rc0, p0, c0, o = oracle.run_round(w, w.part, 0, 4, rebalance_only=True)
+    assert rc == rc0 == oracle.OK
+    _compare_traces(t, o)
+    assert np.array_equal(p, p0)
+
+
+def test_refine(upr, case):
+    ctx = upr.create_from_workload(case)
+    part = case.part.copy()
+    st = upr.upr_refine(ctx, part, case.rounds)
+    rc0, p0, c0, _ = oracle.refine(case, case.part, rounds=case.rounds)
+    assert rc0 == oracle.OK
+    assert np.array_equal(part, p0) and st.cut_out == c0
+    assert st.cut_out <= st.cut_in
+
+
+@pytest.mark.parametrize("builder,shrink", [("plain_tiny", 0), ("plain_large", 6), ("plain_weighted", 6)])
+def test_refine_configs_scaled(upr, builder, shrink):
+    w = _repaired(synth.cached(getattr(synth, builder), shrink))
+    ctx = upr.create_from_workload(w)
+    part = w.part.copy()
+    st = upr.upr_refine(ctx, part, w.rounds)
+    rc0, p0, c0, rcuts = oracle.refine(w, w.part, rounds=w.rounds)
+    assert np.array_equal(part, p0) and st.cut_out == c0 == rcuts[-1]
+    c, bw = upr.upr_cut(ctx, part)
+    assert c == c0 and np.array_equal(bw, oracle.cut(w, p0)[1])
+
+
+def test_device_pointers_match_host(upr):
+    import torch
+    w = synth.plain_tiny(2)
+    host = upr.create_from_workload(w)
+    dev = upr.create_from_workload(w, device=True)
+    p_host = w.part.copy()
+    upr.upr_refine(host, p_host, 3)
+    p_dev = torch.from_numpy(w.part.copy()).cuda()
+    upr.upr_refine(dev, p_dev, 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(p_dev.cpu().numpy(), p_host)
+
+
+def test_imbalanced_input_repaired(upr):
+    w = synth.random_small(42, 500, 5.0, 6, balanced=False)
+    ctx = upr.create_from_workload(w)
+    part = w.part.copy()
+    st = upr.upr_refine(ctx, part, 2)
+    rc0, p0, c0, _ = oracle.refine(w, w.part, rounds=2)
+    assert st.repaired_input == 1 and np.array_equal(part, p0) and st.cut_out == c0
+
+
+def test_infeasible_input_leaves_part_unchanged(upr):
+    xadj, adj = synth.csr_from_edges(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    vw = np.array([10, 1, 1], np.int32)
+    w = synth.Workload("heavy", 3, xadj, adj, None, vw, 2, 0.03, np.array([0, 0, 1], np.int32), 1)
+    ctx = upr.create_from_workload(w)
+    part = w.part.copy()
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_refine(ctx, part, 1)
+    assert e.value.status == upr.UPR_ERR_INFEASIBLE
+    assert np.array_equal(part, w.part)
+    assert oracle.refine(w, w.part, rounds=1)[0] == oracle.ERR_INFEASIBLE
+
+
+def test_invalid_inputs_rejected(upr):
+    w = synth.random_small(43, 50, 4.0, 3)
+    # asymmetric: drop one direction of an edge by editing a neighbour id
+    adj = w.adj.copy()
+    adj[0] = (adj[0] + 1) % w.n if (adj[0] + 1) % w.n != 0 else 2
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_create(w.xadj, adj, w.k, w.eps, vwgt=w.vwgt, adjw=w.adjw)
+    assert e.value.status == upr.UPR_ERR_INVALID
+    # self loop
+    xadj, adj2 = synth.csr_from_edges(3, np.array([0], np.int32), np.array([1], np.int32))
+    adj_self = np.array([0, 0], np.int32)
+    with pytest.raises(upr.UprError):
+        upr.upr_create(xadj, adj_self, 2, 0.03)
+    # partition out of range: part untouched
+    ctx = upr.create_from_workload(w)
+    part = w.part.copy()
+    part[3] = w.k
+    keep = part.copy()
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_refine(ctx, part, 1)
+    assert e.value.status == upr.UPR_ERR_INVALID and np.array_equal(part, keep)
+    with pytest.raises(upr.UprError):
+        upr.upr_create(w.xadj, w.adj, 1, 0.03)            # k < 2
+
+
+def test_split_resume_and_seed_independence(upr):
+    w = synth.plain_tiny(3)
+    full = upr.create_from_workload(w)
+    p8 = w.part.copy()
+    upr.upr_refine(full, p8, 8, seed=1)
+    p8b = w.part.copy()
+    upr.upr_refine(full, p8b, 8, seed=12345)
+    assert np.array_equal(p8, p8b)
+    prm = upr.upr_params_default()
+    prm.round_offset, prm.total_rounds = 0, 8
+    a = upr.create_from_workload(w, params=prm)
+    p = w.part.copy()
+    upr.upr_refine(a, p, 3)
+    prm2 = upr.upr_params_default()
+    prm2.round_offset, prm2.total_rounds = 3, 8
+    b = upr.create_from_workload(w, params=prm2)
+    upr.upr_refine(b, p, 5)
+    assert np.array_equal(p, p8)
+    rc0, p0, c0, _ = oracle.refine(w, w.part, rounds=8)
+    assert np.array_equal(p8, p0)
+
+
+def test_server_results_equal_alone_and_in_mix(upr):
+    ws = [synth.random_small(50 + i, 200 + 97 * i, 5.0, 2 + (i % 5)) for i in range(6)]
+    ws += [synth.plain_tiny(2), synth.plain_large(11)]
+    alone = []
+    for w in ws:
+        ctx = upr.create_from_workload(w)
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, w.rounds)
+        alone.append((p, st.cut_out))
+    srv = upr.Server(max_jobs=4)
+    try:
+        tickets = [srv.submit(w) for w in ws]
+        for t, (p, c), w in zip(tickets, alone, ws):
+            p2, c2, st = srv.wait(t)
+            assert np.array_equal(p2, p) and c2 == c
+            rc0, p0, c0, _ = oracle.refine(w, w.part, rounds=w.rounds)
+            assert np.array_equal(p2, p0)
+    finally:
+        srv.close()
