@@ -1,0 +1,303 @@
+"""Benchmark of the refinement hot path: edges refined per second.
+
+One step = one upr_refine call (all rounds of the workload: gain table,
+selection, rebalancing, interleaving, exact gains, best prefix) on the R-MAT
+scale-22 workload (4,194,304 nodes, 128.3M adjacency entries after
+symmetrisation and deduplication, unit weights, k = 64, eps = 0.03, seeded
+random balanced initial partition, 8 rounds).  value = rounds * |E| / step
+time, with the graph and the initial partition resident in HBM; e2e = the
+same metric through the C ABI from pinned host buffers (graph upload and
+checks, refinement, partition read-back) per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+N > 1 runs under torch.distributed.run: every rank refines its own replica
+(the single-graph path does not shard), scaling "weak".  --impl reference
+times the CPU oracle on one round of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "plain_large"
+METRIC = "edges refined/s"
+UNIT = "edges/s"
+
+
+def _config(w):
+    E = w.m // 2
+    return {"workload": f"{w.name}: R-MAT scale 22 (a=0.57, b=c=0.19), edge factor 16, symmetrised + dedup, "
+                        f"unit weights, k={w.k}, eps={w.eps}, seeded random balanced initial partition, "
+                        f"{w.rounds} rounds",
+            "n": w.n, "m": w.m, "edges": E, "k": w.k, "rounds": w.rounds,
+            "l2": "inputs larger than L2 (CSR 0.55 GB, gain table 1.07 GB per build)"}
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _traffic(kernel_src: str, profile: str):
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu summary,
+    only if it was taken on the current kernel source."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
+    m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    if not m1 or not m2 or m1.group(1) != sha:
+        return None
+    return int(m2.group(1))
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    w = synth.cached(getattr(synth, WORKLOAD))
+    oracle.build()
+    E = w.m // 2
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rc, p, c, tr = oracle.run_round(w, w.part, 1, w.rounds)
+        t = time.perf_counter() - t0
+        assert rc == oracle.OK
+        if i >= args.warmup:
+            times.append(t)
+    per = sum(times) / len(times)
+    value = E / per
+    sample = f"one round (round 1 of {w.rounds}) of the full workload per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": _config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(w):
+    """The oracle as it stands, single-threaded, on one round of the same workload."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    rc, p, c, tr = oracle.run_round(w, w.part, 1, w.rounds)
+    t = time.perf_counter() - t0
+    return {"value": (w.m // 2) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"round 1 of {w.rounds} on the full workload, {t:.1f} s, 1 of {os.cpu_count()} host cores"}
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2308_15494_gb300 import build as cuda_build
+    cuda_build.build()
+    import paper_2308_15494_gb300 as upr
+    upr.load()
+
+    w = synth.cached(getattr(synth, WORKLOAD))
+    E = w.m // 2
+    stream = torch.cuda.current_stream()
+    ctx = upr.create_from_workload(w, device=True)
+    part_init = torch.from_numpy(w.part.copy()).cuda()
+    part = torch.empty_like(part_init)
+
+    def step():
+        part.copy_(part_init)
+        return upr.upr_refine(ctx, part, w.rounds)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stats = []
+    barrier()
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step())
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * w.rounds * E / (ms_step / 1e3)
+
+    # roofline of the dominant kernel: the gain-table build (device time from
+    # CUDA events on the context's stream around every build)
+    builds = sum(s.gain_table_builds for s in stats)
+    t_build = sum(s.ms_gain_table for s in stats) / max(builds, 1) / 1e3
+    bytes_build = stats[0].gain_table_bytes
+    peak, peak_kind = _peaks()
+    achieved = bytes_build / t_build / 1e9
+    roofline = {"bound": "hbm", "kernel": "gain table build (k_table_dense + hub chunks)",
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak, "bytes_per_launch": bytes_build, "ms_per_launch": t_build * 1e3,
+                "traffic": _traffic("paper_2308_15494_gb300/csrc/graph.cu", "gain_table_rmat_s22_k64.md")}
+
+    # end to end through the C ABI from pinned host buffers
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+              for k, a in (("xadj", w.xadj), ("adj", w.adj), ("part", w.part), ("work", w.part))}
+    pin = {k: t.numpy() for k, t in pinned.items()}
+    h2d = pin["xadj"].nbytes + pin["adj"].nbytes + pin["part"].nbytes
+    d2h = pin["part"].nbytes + 8
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        c = upr.upr_create(pin["xadj"], pin["adj"], w.k, w.eps)
+        pin["work"][:] = pin["part"]
+        st = upr.upr_refine(c, pin["work"], w.rounds)
+        upr.upr_destroy(c)
+        return st
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": ws * w.rounds * E / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": t_e2e * 1e3, "steps": e2e_steps}
+
+    if rank == 0:
+        cb = cpu_baseline(w) if ws == 1 and not args.no_cpu_baseline else None
+        s0 = stats[-1]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": _config(w),
+                "e2e": e2e, "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+                "roofline": roofline, "cpu_baseline": cb, "clocks": clk.summary(),
+                "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
+                           "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
+                           "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds}}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

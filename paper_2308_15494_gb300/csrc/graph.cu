@@ -53,7 +53,8 @@ __global__ void k_edge_cut(const int64_t *__restrict__ xadj, const int32_t *__re
         int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
         for (; e < e1; e += 32) {
             while (xadj[v + 1] <= e) v++;
-            if (part[v] != part[adj[e]]) acc += adjw ? adjw[e] : 1;
+            const int32_t u = adj[e];
+            if (v < u && part[v] != part[u]) acc += adjw ? adjw[e] : 1;   // each undirected edge once
         }
     }
     acc = warp_sum(acc);
