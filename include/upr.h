@@ -138,6 +138,29 @@ upr_status upr_cut(upr_ctx *ctx, const int32_t *part, int64_t *cut, int64_t *blo
 /* Releases the context and all its device memory. NULL is ignored. */
 void upr_destroy(upr_ctx *ctx);
 
+/* Cut and block weights of part, like upr_cut, for callers that cannot
+ * allocate: code whose device memory is owned by another allocator or
+ * budget (a host framework's pool, a fixed-footprint embedded deployment),
+ * or latency-critical loops that must not pay the implicit device
+ * synchronisation and locking of cudaMalloc / cudaFree.  The paper has no
+ * counterpart; it is an operational variant of step (e).
+ * It allocates nothing: no context, no cudaMalloc / cudaFree, no allocating
+ * library call.  The graph arrays of g and part must be device memory (the
+ * caller's); cut (one int64) and block_weights (k int64, may be NULL) may be
+ * host or device memory.  The kernels' scratch is one static device array of
+ * 4096 + 8 int64 that every GPU loading the library holds until exit, so
+ * k must be in [2, 4096] (UPR_ERR_INVALID otherwise).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * it before any stream capture.  Every call on a device shares the one
+ * array and clears what it accumulates into, so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.  The call runs on `stream` (cudaStream_t, NULL = default) and
+ * returns after synchronising it.  Errors: UPR_ERR_INVALID (sizes, k, host
+ * graph pointers, part values outside [0, k)), UPR_ERR_CUDA.  The graph is
+ * not validated beyond that (see upr_create's validate). */
+upr_status upr_cut_noalloc(const upr_graph *g, int32_t k, const int32_t *part, void *stream, int64_t *cut,
+                           int64_t *block_weights);
+
 /* ------------------------------------------------------------------------
  * Serving: a host worker thread admits refinement jobs while device memory
  * and job slots allow, runs each job on its own stream and context so jobs of

@@ -70,6 +70,7 @@ SIGNATURES = {
     "upr_refine": (I32, [P, P, I32, U64, ctypes.POINTER(Stats)]),
     "upr_cut": (I32, [P, P, ctypes.POINTER(I64), P]),
     "upr_destroy": (None, [P]),
+    "upr_cut_noalloc": (I32, [ctypes.POINTER(Graph), I32, P, P, ctypes.POINTER(I64), P]),
     "upr_server_params_default": (None, [ctypes.POINTER(ServerParams)]),
     "upr_server_create": (I32, [ctypes.POINTER(ServerParams), ctypes.POINTER(P)]),
     "upr_submit": (I32, [P, ctypes.POINTER(Graph), I32, D, P, I32, U64, ctypes.POINTER(U64)]),
@@ -202,6 +203,20 @@ def upr_cut(ctx: Context, part) -> tuple[int, np.ndarray]:
     rc = load().upr_cut(ctx.handle, _ptr(part), ctypes.byref(cut), _ptr(bw))
     if rc != UPR_OK:
         raise UprError(rc, "upr_cut")
+    return int(cut.value), bw
+
+
+def upr_cut_noalloc(xadj, adj, part, k: int, vwgt=None, adjw=None, stream=None) -> tuple[int, np.ndarray]:
+    """upr_cut_noalloc: graph arrays and part are torch CUDA tensors (the
+    caller's memory); returns (cut, block weights) without any allocation in
+    the library."""
+    g, n, m = _graph_struct(xadj, adj, vwgt, adjw)
+    cut = ctypes.c_int64()
+    bw = np.zeros(k, np.int64)
+    s = stream if stream is not None else _current_stream()
+    rc = load().upr_cut_noalloc(ctypes.byref(g), k, _ptr(part), s, ctypes.byref(cut), _ptr(bw))
+    if rc != UPR_OK:
+        raise UprError(rc, "upr_cut_noalloc")
     return int(cut.value), bw
 
 

@@ -35,7 +35,7 @@ struct CudaError { cudaError_t e; const char *what; };
 extern std::atomic<long long> g_upr_launches;
 #define UPR_LAUNCH_CHECK()                                                 \
     do {                                                                   \
-        g_upr_launches.fetch_add(1, std::memory_order_relaxed);            \
+        ::upr::g_upr_launches.fetch_add(1, std::memory_order_relaxed);     \
         UPR_CUDA(cudaGetLastError());                                      \
     } while (0)
 
