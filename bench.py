@@ -186,7 +186,7 @@ def run_gpu(args):
     import paper_2308_15494_gb300 as upr
     upr.load()
 
-    w = synth.cached(getattr(synth, WORKLOAD))
+    w = synth.cached(getattr(synth, WORKLOAD), args.shrink)
     E = w.m // 2
     stream = torch.cuda.current_stream()
     ctx = upr.create_from_workload(w, device=True)
@@ -212,12 +212,19 @@ def run_gpu(args):
     with Clocks(local) as clk:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
             stats.append(step())
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         barrier()
     ms = e0.elapsed_time(e1)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "ms_per_step": ms / args.steps,
+                              "launches_per_step": stats[-1].kernel_launches}))
+        return 0
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device="cuda")
@@ -276,6 +283,9 @@ def run_gpu(args):
                 "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": _config(w),
                 "e2e": e2e, "gpu_launches": int(sum(s.kernel_launches for s in stats)),
                 "roofline": roofline, "cpu_baseline": cb, "clocks": clk.summary(),
+                "phases_ms_per_step": {"gain_table": s0.ms_gain_table, "select": s0.ms_select,
+                                       "rebalance": s0.ms_rebalance, "sequence": s0.ms_sequence,
+                                       "host_wall": s0.ms_host},
                 "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
                            "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
                            "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds}}
@@ -293,6 +303,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shrink", type=int, default=0,
+                    help="profiling only: the same workload family with 2^-shrink of the nodes")
+    ap.add_argument("--profile", action="store_true",
+                    help="device loop only (for ncu launch lists): no e2e, no CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

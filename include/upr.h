@@ -99,6 +99,11 @@ typedef struct {
     double  ms_gain_table;       /* device time of gain-table builds                    */
     int32_t gain_table_builds;   /* number of full gain-table builds                    */
     int64_t gain_table_bytes;    /* algorithmic DRAM bytes of one build                 */
+    double  ms_select;           /* device time of step (b) and applying M (with the
+                                    table update after M)                               */
+    double  ms_rebalance;        /* device time of step (d)                             */
+    double  ms_sequence;         /* device time of step (c): interleave to apply        */
+    double  ms_host;             /* wall-clock time of the call on the host             */
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */

@@ -40,7 +40,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("cut_in", I64), ("cut_out", I64), ("rounds_run", I32), ("repaired_input", I32),
                 ("n_candidates", I64), ("n_moves", I64), ("n_rebalance_moves", I64), ("n_sequence", I64),
                 ("n_applied", I64), ("subrounds", I32), ("kernel_launches", I32), ("ms_device", D),
-                ("ms_gain_table", D), ("gain_table_builds", I32), ("gain_table_bytes", I64)]
+                ("ms_gain_table", D), ("gain_table_builds", I32), ("gain_table_bytes", I64),
+                ("ms_select", D), ("ms_rebalance", D), ("ms_sequence", D), ("ms_host", D)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

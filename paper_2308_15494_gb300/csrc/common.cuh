@@ -68,4 +68,52 @@ __device__ __forceinline__ void group_argmax(int64_t &score, int32_t &id) {
     }
 }
 
+// Per-CTA accumulation of block-weight changes.  Every lane of every warp
+// calls add() (key < 0 = nothing to add); lanes with equal keys are combined
+// with __match_any_sync and their leader adds the group's total to shared
+// memory; flush() adds the CTA's non-zero totals to the global counters.
+// Integer additions commute, so the result is independent of scheduling.
+struct BlockDelta {
+    unsigned long long *s;
+    int k;
+    __device__ __forceinline__ void init() {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) s[i] = 0;
+        __syncthreads();
+    }
+    __device__ __forceinline__ void add(int key, long long d) {
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        long long tot = 0;
+        for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, d, __ffs(m) - 1);
+        if (key >= 0 && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0 && tot != 0)
+            atomicAdd(&s[key], (unsigned long long)tot);
+    }
+    __device__ __forceinline__ void flush(unsigned long long *C) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x)
+            if (s[i]) atomicAdd(&C[i], s[i]);
+    }
+};
+
+inline int device_sm_count() {
+    static thread_local int cnt = 0, dev_cached = -1;
+    int dev = 0;
+    UPR_CUDA(cudaGetDevice(&dev));
+    if (dev != dev_cached) {
+        UPR_CUDA(cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev));
+        dev_cached = dev;
+    }
+    return cnt;
+}
+
+// 32-bit form of group_argmax.
+template <int G>
+__device__ __forceinline__ void group_argmax32(int32_t &score, int32_t &id) {
+    for (int o = G / 2; o > 0; o >>= 1) {
+        int32_t s2 = __shfl_xor_sync(0xffffffffu, score, o);
+        int32_t i2 = __shfl_xor_sync(0xffffffffu, id, o);
+        bool take = (i2 >= 0) && (id < 0 || s2 > score || (s2 == score && i2 < id));
+        if (take) { score = s2; id = i2; }
+    }
+}
+
 }  // namespace upr

@@ -4,6 +4,9 @@
 // block weights between rebalancing sub-rounds) to size the next launches.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -15,6 +18,13 @@ using namespace upr;
 namespace {
 
 int bit_length(uint64_t x) { int b = 0; while (x) { b++; x >>= 1; } return b; }
+
+// UPR_LOG=1 in the environment prints list sizes per round and sub-round to stderr.
+bool log_enabled() {
+    static int on = -1;
+    if (on < 0) { const char *v = getenv("UPR_LOG"); on = (v && *v && *v != '0') ? 1 : 0; }
+    return on == 1;
+}
 
 // Bump allocator over one cudaMalloc; a first pass with base == nullptr sizes it.
 struct Arena {
@@ -31,7 +41,7 @@ struct SortBuf {
     uint64_t *k, *ka;
     uint32_t *v, *va;
     // sorts (k, v) on `bits` bits; returns the buffers holding the result
-    void run(int64_t n, int bits, void *tmp, cudaStream_t s, uint64_t **ko, uint32_t **vo) {
+    void run(Count n, int bits, void *tmp, cudaStream_t s, uint64_t **ko, uint32_t **vo) {
         bool alt = radix_sort_pairs(k, v, ka, va, n, bits, tmp, s);
         *ko = alt ? ka : k;
         *vo = alt ? va : v;
@@ -70,6 +80,7 @@ struct upr_ctx {
     // graph
     int64_t *xadj; int32_t *adj, *adjw, *vwgt, *wI;
     HubChunk *hub_chunks; int64_t n_chunks = 0;
+    TableTile *tiles = nullptr; int64_t n_tiles = 0; int32_t tile_nodes = 0;
     // state
     int32_t *part0, *part; int64_t *C0, *C, *cut; int32_t *W;
     int64_t *BW, *PW, *F;
@@ -77,7 +88,7 @@ struct upr_ctx {
     int32_t *cand_tgt, *cand_gain, *flags, *flags2, *excl_i, *m_pos, *r_to, *pos, *dest, *prop_tgt, *prop_gain;
     int64_t *cand_s0;
     // lists
-    int32_t *idxA, *idxB, *idxC, *idxD;
+    int32_t *idxA, *idxB, *idxC, *idxD, *L1;
     int64_t *score;
     int32_t *M_node, *M_from, *M_to; int64_t *M_score;
     int32_t *R_node, *R_from, *R_to, *R_sub;
@@ -92,13 +103,18 @@ struct upr_ctx {
     int32_t *seg_first, *rbeg, *rend, *ebeg, *eend, *qfin, *left, *left_excl;
     long long *best_parts, *best;
     int8_t *over_d, *excl_d, *reject_d;
-    int32_t *counts;          // small device counters
+    int32_t *counts;          // device counters (CNT_* slots)
+    RebalCtl *ctl;            // rebalancing loop control block
     uint64_t *vacc; int32_t *vflags; int64_t *scal;
     void *tmp;                // scan / sort temporaries
-    // host pinned mirror
+    // pinned host mirrors
     int64_t *h = nullptr;     // pinned scratch
     int8_t *h8 = nullptr;
-    cudaEvent_t ev[4] = {};
+    int64_t *hF = nullptr, *hcut = nullptr;
+    int32_t *hcnt = nullptr;
+    long long *hbest = nullptr;
+    RebalCtl *hctl = nullptr;
+    cudaEvent_t ev[8] = {};
 };
 
 namespace {
@@ -112,6 +128,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->vwgt = A.take<int32_t>(n);
     c->wI = A.take<int32_t>(n);
     c->hub_chunks = A.take<HubChunk>((size_t)std::max<int64_t>(c->n_chunks, 1));
+    c->tiles = A.take<TableTile>((size_t)std::max<int64_t>(c->n_tiles, 1));
     c->part0 = A.take<int32_t>(n);
     c->part = A.take<int32_t>(n);
     c->C0 = A.take<int64_t>(k);
@@ -124,7 +141,7 @@ void layout(upr_ctx *c, Arena &A) {
     for (int32_t **p : {&c->cand_tgt, &c->cand_gain, &c->flags, &c->m_pos, &c->r_to, &c->pos, &c->dest, &c->prop_tgt,
                         &c->prop_gain, &c->idxA, &c->idxB, &c->idxC, &c->M_node, &c->M_from, &c->M_to, &c->R_node,
                         &c->R_from, &c->R_to, &c->R_sub, &c->I_node, &c->I_from, &c->I_to, &c->emit, &c->qbefore,
-                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs})
+                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs, &c->L1})
         *p = A.take<int32_t>(n);
     for (int32_t **p : {&c->flags2, &c->excl_i, &c->idxD, &c->X_node, &c->X_from, &c->X_to, &c->final_to})
         *p = A.take<int32_t>(n2 + 1);
@@ -155,7 +172,8 @@ void layout(upr_ctx *c, Arena &A) {
     c->over_d = A.take<int8_t>(k);
     c->excl_d = A.take<int8_t>(k);
     c->reject_d = A.take<int8_t>(k);
-    c->counts = A.take<int32_t>(16);
+    c->counts = A.take<int32_t>(64);
+    c->ctl = A.take<RebalCtl>(1);
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
     c->scal = A.take<int64_t>(4);
@@ -196,7 +214,7 @@ void read_i64(upr_ctx *c, const int64_t *src, int64_t cnt, int64_t *dst) {
 struct RoundInfo {
     int64_t n_cand = 0, n_moves = 0, n_rebal = 0, n_inter = 0, n_seq = 0, best_len = 0, best_gain = 0;
     int32_t subrounds = 0;
-    float ms_table = 0;
+    float ms_table = 0, ms_select = 0, ms_rebalance = 0, ms_sequence = 0;
     int tables = 0;
 };
 
@@ -207,20 +225,18 @@ void d2h(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (dst && bytes) UPR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
 }
 
-void build_table(upr_ctx *c, const int32_t *part, RoundInfo &ri) {
-    UPR_CUDA(cudaEventRecord(c->ev[0], c->s));
-    gain_table(c->G, part, c->W, c->hub_chunks, c->n_chunks, c->s);
-    UPR_CUDA(cudaEventRecord(c->ev[1], c->s));
-    UPR_CUDA(cudaEventSynchronize(c->ev[1]));
-    float ms = 0;
-    UPR_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-    ri.ms_table += ms;
-    ri.tables++;
-}
+// Slots of the device counters (upr_ctx::counts).
+enum {
+    CNT_CAND = 0, CNT_M, CNT_P, CNT_S, CNT_A, CNT_I, CNT_HUB, CNT_BADPART, CNT_L1, CNT_X, CNT_EVM, CNT_EVI,
+    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_SLOTS = 32
+};
 
 /*
- * One round on c->part0 / c->C0 / c->cut (device state).  Returns UPR_OK or
- * UPR_ERR_INFEASIBLE (state unchanged).  rebalance_only: the round-0 repair.
+ * One round on c->part0 / c->C0 / c->cut (device state).  Every step is
+ * enqueued on c->s with its list lengths in device memory; the host waits
+ * only for the rebalancing loop's stop flag after each sub-round and for the
+ * end of the round.  Returns UPR_OK or UPR_ERR_INFEASIBLE (state unchanged).
+ * rebalance_only: the round-0 repair.
  */
 upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
     cudaStream_t s = c->s;
@@ -229,259 +245,231 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     const int32_t k = c->k;
     const int kbits = std::max(1, bit_length((uint64_t)(k - 1)));
     upr_trace *T = tr ? tr->t : nullptr;
+    int32_t *cnt = c->counts;
+    RebalCtl *ctl = c->ctl;
+    const Count cN{nullptr, n};
+    uint64_t *ko; uint32_t *vo;
 
+    UPR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * CNT_SLOTS, s));
     UPR_CUDA(cudaMemcpyAsync(c->part, c->part0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * k, cudaMemcpyDeviceToDevice, s));
-    build_table(c, c->part0, ri);
-
-    int64_t nM = 0;
+    // ---- (a) gain table of the round-start partition
+    UPR_CUDA(cudaEventRecord(c->ev[0], s));
+    gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+               c->tile_nodes, nullptr, s);
+    UPR_CUDA(cudaEventRecord(c->ev[1], s));
+    UPR_CUDA(cudaEventRecord(c->ev[4], s));
     if (!rebalance_only) {
         // ---- (b1) availability, slots, bucket weights; F_r
         buckets(G, c->part0, c->W, c->prm.t_num, c->prm.t_den, c->BW, c->PW, tr ? tr->avail_d : nullptr,
                 tr ? tr->slot_d : nullptr, s);
-        penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->h);
-        UPR_CUDA(cudaMemcpyAsync(c->F, c->h, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
-        if (T) {
-            d2h(T->avail, tr->avail_d, n, s);
-            d2h(T->slot, tr->slot_d, sizeof(int32_t) * n, s);
-            d2h(T->bucket, c->BW, sizeof(int64_t) * k * kSlots, s);
-            if (T->factor) memcpy(T->factor, c->h, sizeof(int64_t) * kSlots);
-        }
+        penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
+        UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
         Penalty pen{c->PW, c->F, c->C0, c->Lmax};
         // ---- (b2) best move per boundary node
         select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, s);
-        select_flags(c->flags, c->excl_i, c->idxA, c->counts + 0, n, c->tmp, s);
-        const int64_t nc = read_count(c, 0);
-        ri.n_cand = nc;
-        if (T) {
-            d2h(T->cand_target, c->cand_tgt, sizeof(int32_t) * n, s);
-            d2h(T->cand_s0, c->cand_s0, sizeof(int64_t) * n, s);
-            if (T->cand_gain) {
-                // cand_gain is int32 on the device; widen on the host
-                std::vector<int32_t> tmp(n);
-                UPR_CUDA(cudaMemcpyAsync(tmp.data(), c->cand_gain, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-                UPR_CUDA(cudaStreamSynchronize(s));
-                for (int64_t v = 0; v < n; v++) T->cand_gain[v] = tmp[v];
-            }
-        }
-        if (nc > 0) {
-            // ---- (b3) inflow penalties: order by (target, s0 desc, id)
-            uint64_t *ko; uint32_t *vo;
-            cand_keys(c->idxA, c->counts + 0, c->cand_tgt, c->cand_s0, c->sb[0].k, c->sb[0].v, nc, s);
-            c->sb[0].run(nc, 31 + kbits, c->tmp, s, &ko, &vo);
-            cand_gather(G, c->idxA, vo, c->counts + 0, c->cand_tgt, c->c_sorted, c->seg_first, nc, s);
-            exclusive_sum_i64(c->c_sorted, c->c_excl, nc, c->tmp, s);
-            inflow_filter(G, c->idxA, vo, c->counts + 0, c->cand_tgt, c->cand_gain, c->c_excl, c->seg_first, pen,
-                          c->flags2, c->score, nc, s);
-            select_flags(c->flags2, c->excl_i, c->idxB, c->counts + 1, nc, c->tmp, s);
-            nM = read_count(c, 1);
-            if (nM > 0) {
-                // ---- M ordered by (score desc, id)
-                uint64_t *k2; uint32_t *v2;
-                move_keys(c->idxB, c->counts + 1, c->score, c->sb[1].k, c->sb[1].v, nM, s);
-                c->sb[1].run(nM, 31, c->tmp, s, &k2, &v2);
-                apply_moves(G, c->idxA, c->idxB, v2, c->counts + 1, c->cand_tgt, c->score, c->part0, c->part, c->C,
-                            c->M_node, c->M_from, c->M_to, c->M_score, c->m_pos, nM, s);
-                // W' for P o M: delta update when M is small, rebuild otherwise
-                if (nM * 8 < n) {
-                    table_move(G, c->W, c->M_node, c->M_from, c->M_to, c->counts + 1, nM, s);
-                } else {
-                    build_table(c, c->part, ri);
-                }
-            }
-        }
+        select_flags(c->flags, c->idxA, cnt + CNT_CAND, cN, c->tmp, s);
+        const Count cC{cnt + CNT_CAND, n};
+        // ---- (b3) inflow penalties: order by (target, s0 desc, id)
+        cand_keys(c->idxA, cnt + CNT_CAND, c->cand_tgt, c->cand_s0, c->gbits, c->sb[0].k, c->sb[0].v, n, s);
+        c->sb[0].run(cC, c->gbits + kbits, c->tmp, s, &ko, &vo);
+        cand_gather(G, c->idxA, vo, cnt + CNT_CAND, c->cand_tgt, c->c_sorted, c->seg_first, n, s);
+        exclusive_sum_i64(c->c_sorted, c->c_excl, cC, c->tmp, s);
+        inflow_filter(G, c->idxA, vo, cnt + CNT_CAND, c->cand_tgt, c->cand_gain, c->c_excl, c->seg_first, pen,
+                      c->flags2, c->score, n, s);
+        select_flags(c->flags2, c->idxB, cnt + CNT_M, cC, c->tmp, s);
+        // ---- M ordered by (score desc, id), applied
+        uint64_t *k2; uint32_t *v2;
+        move_keys(c->idxB, cnt + CNT_M, c->score, c->gbits, c->sb[1].k, c->sb[1].v, n, s);
+        c->sb[1].run(Count{cnt + CNT_M, n}, c->gbits, c->tmp, s, &k2, &v2);
+        apply_moves(G, c->idxA, c->idxB, v2, cnt + CNT_M, c->cand_tgt, c->score, c->part0, c->part, c->C, c->M_node,
+                    c->M_from, c->M_to, c->M_score, c->m_pos, c->scal + 1, n, s);
+        // W' for P o M: the delta update costs two atomics per adjacency entry of a
+        // moved node, a rebuild streams the graph and the table once; each kernel
+        // checks on the device which of the two applies
+        table_move(G, c->W, c->M_node, c->M_from, c->M_to, cnt + CNT_M, nullptr, c->scal + 1, n, s);
+        gain_table(G, c->part, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, c->scal + 1, s);
     }
-    ri.n_moves = nM;
-    if (T && T->M_node) {
-        d2h(T->M_node, c->M_node, sizeof(int32_t) * nM, s);
-        d2h(T->M_to, c->M_to, sizeof(int32_t) * nM, s);
-        d2h(T->M_score, c->M_score, sizeof(int64_t) * nM, s);
-    }
+    UPR_CUDA(cudaEventRecord(c->ev[5], s));
 
     // ---- (d) rebalancing sub-rounds
-    std::vector<int64_t> Ch(k);
-    read_i64(c, c->C, k, Ch.data());
-    std::vector<int8_t> excl(k, 0), over(k, 0);
-    for (int32_t b = 0; b < k; b++) excl[b] = Ch[b] > c->Lmax;
-    int64_t nR = 0;
+    rebalance_init(c->C, k, c->Lmax, c->excl_d, ctl, s);
+    rebalance_flag_in_blocks(c->part, n, c->excl_d, c->flags, s);
+    select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
+    const RebalState st{c->C, c->over_d, c->excl_d, &ctl->light, c->Lmax};
+    const Count cP{cnt + CNT_P, n}, cS{cnt + CNT_S, n};
     for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
-        bool any = false;
-        for (int32_t b = 0; b < k; b++) { over[b] = Ch[b] > c->Lmax; any = any || over[b]; }
-        if (!any) break;
-        ri.subrounds = h;
-        int32_t light = -1;
-        for (int32_t b = 0; b < k; b++)
-            if (!excl[b] && (light < 0 || Ch[b] < Ch[light])) light = b;
-        memcpy(c->h8, over.data(), k);
-        memcpy(c->h8 + k, excl.data(), k);
-        UPR_CUDA(cudaMemcpyAsync(c->over_d, c->h8, k, cudaMemcpyHostToDevice, s));
-        UPR_CUDA(cudaMemcpyAsync(c->excl_d, c->h8 + k, k, cudaMemcpyHostToDevice, s));
-        UPR_CUDA(cudaMemsetAsync(c->reject_d, 0, k, s));
-        RebalState st{c->C, c->over_d, c->excl_d, light, c->Lmax};
-        rebalance_propose(G, c->part, c->W, st, c->prop_tgt, c->prop_gain, c->flags, s);
-        select_flags(c->flags, c->excl_i, c->idxA, c->counts + 2, n, c->tmp, s);
-        const int64_t np = read_count(c, 2);
-        int64_t na = 0;
-        bool grew = false;
-        if (np > 0) {
-            uint64_t *kA; uint32_t *A;
-            rebalance_prio_keys(G, c->idxA, c->counts + 2, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v,
-                                np, s);
-            c->sb[0].run(np, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
-            // per source: the minimal prefix covering the excess
-            uint64_t *kB; uint32_t *B;
-            rebalance_block_keys(c->idxA, A, nullptr, c->counts + 2, c->part, c->sb[1].k, c->sb[1].v, np, s);
-            c->sb[1].run(np, kbits, c->tmp, s, &kB, &B);
-            rebalance_seg_weights(G, c->idxA, A, nullptr, B, kB, c->counts + 2, c->c_sorted, c->seg_first, np, s);
-            exclusive_sum_i64(c->c_sorted, c->c_excl, np, c->tmp, s);
-            rebalance_mark_selected(B, kB, c->counts + 2, c->c_excl, c->seg_first, st, c->flags2, np, s);
-            select_flags(c->flags2, c->excl_i, c->idxB, c->counts + 3, np, c->tmp, s);
-            const int64_t ns = read_count(c, 3);
-            if (ns > 0) {
-                // per target: the longest prefix that fits
-                uint64_t *kT; uint32_t *Tq;
-                rebalance_block_keys(c->idxA, A, c->idxB, c->counts + 3, c->prop_tgt, c->sb[2].k, c->sb[2].v, ns, s);
-                c->sb[2].run(ns, kbits, c->tmp, s, &kT, &Tq);
-                rebalance_seg_weights(G, c->idxA, A, c->idxB, Tq, kT, c->counts + 3, c->c_sorted, c->seg_first, ns, s);
-                exclusive_sum_i64(c->c_sorted, c->c_excl, ns, c->tmp, s);
-                rebalance_mark_admitted(Tq, kT, c->counts + 3, c->c_sorted, c->c_excl, c->seg_first, st, c->flags2,
-                                        c->reject_d, ns, s);
-                select_flags(c->flags2, c->excl_i, c->idxC, c->counts + 4, ns, c->tmp, s);
-                na = read_count(c, 4);
-                if (na > 0) {
-                    rebalance_apply(G, c->idxA, A, c->idxB, c->idxC, c->counts + 4, c->prop_tgt, c->part, c->C, h,
-                                    c->R_node + nR, c->R_from + nR, c->R_to + nR, c->R_sub + nR, c->r_to, na, s);
-                    table_move(G, c->W, c->R_node + nR, c->R_from + nR, c->R_to + nR, c->counts + 4, na, s);
-                }
-            }
-            UPR_CUDA(cudaMemcpyAsync(c->h8, c->reject_d, k, cudaMemcpyDeviceToHost, s));
-            read_i64(c, c->C, k, Ch.data());   // synchronises
-            for (int32_t b = 0; b < k; b++)
-                if (c->h8[b] && !excl[b]) { excl[b] = 1; grew = true; }
-        }
-        nR += na;
-        if (na == 0 && !grew) break;
+        rebalance_begin(c->C, k, c->Lmax, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, h, c->prm.max_subrounds, ctl,
+                        s);
+        rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain, c->flags, s);
+        select_flags(c->flags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
+        rebalance_gather_list(c->L1, c->idxD, cnt + CNT_P, c->idxA, n, s);
+        uint64_t *kA; uint32_t *A;
+        rebalance_prio_keys(G, c->idxA, cnt + CNT_P, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v, n, s);
+        c->sb[0].run(cP, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
+        // per source: the minimal prefix covering the excess
+        uint64_t *kB; uint32_t *B;
+        rebalance_block_keys(c->idxA, A, nullptr, cnt + CNT_P, c->part, c->sb[1].k, c->sb[1].v, n, s);
+        c->sb[1].run(cP, kbits, c->tmp, s, &kB, &B);
+        rebalance_seg_weights(G, c->idxA, A, nullptr, B, kB, cnt + CNT_P, c->c_sorted, c->seg_first, n, s);
+        exclusive_sum_i64(c->c_sorted, c->c_excl, cP, c->tmp, s);
+        rebalance_mark_selected(B, kB, cnt + CNT_P, c->c_excl, c->seg_first, st, c->flags2, n, s);
+        select_flags(c->flags2, c->idxB, cnt + CNT_S, cP, c->tmp, s);
+        // per target: the longest prefix that fits
+        uint64_t *kT; uint32_t *Tq;
+        rebalance_block_keys(c->idxA, A, c->idxB, cnt + CNT_S, c->prop_tgt, c->sb[2].k, c->sb[2].v, n, s);
+        c->sb[2].run(cS, kbits, c->tmp, s, &kT, &Tq);
+        rebalance_seg_weights(G, c->idxA, A, c->idxB, Tq, kT, cnt + CNT_S, c->c_sorted, c->seg_first, n, s);
+        exclusive_sum_i64(c->c_sorted, c->c_excl, cS, c->tmp, s);
+        rebalance_mark_admitted(Tq, kT, cnt + CNT_S, c->c_sorted, c->c_excl, c->seg_first, st, c->flags2, c->reject_d,
+                                n, s);
+        select_flags(c->flags2, c->idxC, cnt + CNT_A, cS, c->tmp, s);
+        rebalance_apply(G, c->idxA, A, c->idxB, c->idxC, cnt + CNT_A, c->prop_tgt, c->part, c->C, ctl, c->R_node,
+                        c->R_from, c->R_to, c->R_sub, c->r_to, n, s);
+        table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, s);
+        rebalance_end(k, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
+        UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
+        UPR_CUDA(cudaStreamSynchronize(s));
+        if (c->hctl->stopped) break;
     }
-    ri.n_rebal = nR;
-    if (T && T->R_node) {
-        d2h(T->R_node, c->R_node, sizeof(int32_t) * nR, s);
-        d2h(T->R_from, c->R_from, sizeof(int32_t) * nR, s);
-        d2h(T->R_to, c->R_to, sizeof(int32_t) * nR, s);
-        d2h(T->R_subround, c->R_sub, sizeof(int32_t) * nR, s);
-    }
+    UPR_CUDA(cudaEventRecord(c->ev[6], s));
 
     // ---- (c1) interleave M and R_1..R_k
+    const int32_t *dM = cnt + CNT_M, *dR = &ctl->nR;
+    count_affine(dM, 2, nullptr, 0, cnt + CNT_EVM, s);
+    count_affine(dM, 1, dR, 0, cnt + CNT_X, s);
     UPR_CUDA(cudaMemsetAsync(c->rbeg, 0, sizeof(int32_t) * k, s));
     UPR_CUDA(cudaMemsetAsync(c->rend, 0, sizeof(int32_t) * k, s));
     UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
     UPR_CUDA(cudaMemsetAsync(c->eend, 0, sizeof(int32_t) * k, s));
-    uint64_t *kRB = nullptr; uint32_t *RB = nullptr;
-    if (nR > 0) {
-        seq_rb_keys(c->R_from, nR, c->sb[0].k, c->sb[0].v, s);
-        c->sb[0].run(nR, kbits, c->tmp, s, &kRB, &RB);
-        seq_rb_bounds(c->R_node, c->R_from, RB, nR, G.vwgt, c->c_sorted, c->rbeg, c->rend, s);
-        exclusive_sum_i64(c->c_sorted, c->c_excl, nR, c->tmp, s);
-    }
-    uint64_t *kEV = nullptr; uint32_t *EV = nullptr;
-    if (nM > 0) {
-        const int64_t nev = 2 * nM;
-        seq_ev_keys(c->M_from, c->M_to, nM, c->sb[1].k, c->sb[1].v, s);
-        c->sb[1].run(nev, kbits, c->tmp, s, &kEV, &EV);
-        seq_ev_delta(c->M_node, EV, kEV, nev, G.vwgt, c->delta, c->ebeg, c->eend, s);
-        exclusive_sum_i64(c->delta, c->d_excl, nev, c->tmp, s);
-        seq_ev_need(EV, kEV, nev, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->rbeg, c->rend, c->c_excl,
-                    c->c_sorted, c->packed, s);
-        inclusive_max_u64(c->packed, c->qmax, nev, c->tmp, s);
-        seq_ev_emit(EV, kEV, nev, c->qmax, c->ebeg, c->emit, c->qbefore, s);
-        exclusive_sum_i32(c->emit, c->em_excl, nM, c->tmp, s);
-    }
+    uint64_t *kRB; uint32_t *RB;
+    seq_rb_keys(c->R_from, dR, n, c->sb[0].k, c->sb[0].v, s);
+    c->sb[0].run(Count{dR, n}, kbits, c->tmp, s, &kRB, &RB);
+    seq_rb_bounds(c->R_node, c->R_from, RB, dR, n, G.vwgt, c->c_sorted, c->rbeg, c->rend, s);
+    exclusive_sum_i64(c->c_sorted, c->c_excl, Count{dR, n}, c->tmp, s);
+    uint64_t *kEV; uint32_t *EV;
+    const Count cEVM{cnt + CNT_EVM, 2 * n};
+    seq_ev_keys(c->M_from, c->M_to, dM, n, c->sb[1].k, c->sb[1].v, s);
+    c->sb[1].run(cEVM, kbits, c->tmp, s, &kEV, &EV);
+    seq_ev_delta(c->M_node, EV, kEV, dM, n, G.vwgt, c->delta, c->ebeg, c->eend, s);
+    exclusive_sum_i64(c->delta, c->d_excl, cEVM, c->tmp, s);
+    seq_ev_need(EV, kEV, dM, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->rbeg, c->rend, c->c_excl,
+                c->c_sorted, c->packed, s);
+    inclusive_max_u64(c->packed, c->qmax, cEVM, c->tmp, s);
+    seq_ev_emit(EV, kEV, dM, n, c->qmax, c->ebeg, c->emit, c->qbefore, s);
+    exclusive_sum_i32(c->emit, c->em_excl, Count{dM, n}, c->tmp, s);
     seq_block_final(k, c->ebeg, c->eend, c->qmax, c->rbeg, c->rend, c->qfin, c->left, s);
-    exclusive_sum_i32(c->left, c->left_excl, k, c->tmp, s);
-    const int64_t nX = nM + nR;
-    seq_place_m(c->M_node, c->M_from, c->M_to, nM, c->em_excl, c->pos_m, c->X_node, c->X_from, c->X_to, c->X_isr, s);
-    seq_place_r(c->R_node, c->R_from, c->R_to, RB, nR, c->rbeg, EV, c->ebeg, c->eend, c->qmax, c->pos_m, c->qfin,
-                c->left_excl, c->em_excl, c->emit, nM, c->X_node, c->X_from, c->X_to, c->X_isr, s);
-    ri.n_inter = nX;
-    if (T && T->X_node) {
+    exclusive_sum_i32(c->left, c->left_excl, fixed(k), c->tmp, s);
+    seq_place_m(c->M_node, c->M_from, c->M_to, dM, n, c->em_excl, c->pos_m, c->X_node, c->X_from, c->X_to, c->X_isr,
+                s);
+    seq_place_r(c->R_node, c->R_from, c->R_to, RB, dR, n, c->rbeg, EV, c->ebeg, c->eend, c->qmax, c->pos_m, c->qfin,
+                c->left_excl, c->em_excl, c->emit, dM, c->X_node, c->X_from, c->X_to, c->X_isr, s);
+
+    // ---- (c1) merge double moves
+    const Count cX{cnt + CNT_X, 2 * n};
+    seq_merge_flags(c->X_node, c->X_to, c->X_isr, cnt + CNT_X, 2 * n, c->m_pos, c->r_to, c->part0, c->flags2,
+                    c->final_to, s);
+    select_flags(c->flags2, c->idxD, cnt + CNT_I, cX, c->tmp, s);
+    const int32_t *dI = cnt + CNT_I;
+    seq_build_I(c->idxD, dI, n, c->X_node, c->final_to, c->part0, c->I_node, c->I_from, c->I_to, c->pos, c->dest, s);
+
+    // ---- (c2) exact gains, balanced prefixes, best prefix
+    seq_gains(G, c->I_node, c->I_from, c->I_to, dI, n, c->pos, c->dest, c->part0, c->I_gain, c->hub_flag, c->hubs,
+              cnt + CNT_HUB, c->tmp, s);
+    inclusive_sum_i64(c->I_gain, c->Gsum, Count{dI, n}, c->tmp, s);
+    count_affine(dI, 2, nullptr, 0, cnt + CNT_EVI, s);
+    count_affine(dI, 1, nullptr, 1, cnt + CNT_I1, s);
+    uint64_t *kE; uint32_t *E;
+    const Count cEVI{cnt + CNT_EVI, 2 * n};
+    seq_iev_keys(c->I_from, c->I_to, dI, n, c->sb[2].k, c->sb[2].v, s);
+    c->sb[2].run(cEVI, kbits, c->tmp, s, &kE, &E);
+    UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
+    seq_iev_delta(c->I_node, E, kE, dI, n, G.vwgt, c->delta, c->ebeg, s);
+    exclusive_sum_i64(c->delta, c->d_excl, cEVI, c->tmp, s);
+    clear_count(c->diff, dI, 1, n, s);
+    seq_iev_transitions(E, kE, dI, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->diff, s);
+    exclusive_sum_i32(c->diff, c->diff_excl, Count{cnt + CNT_I1, n + 1}, c->tmp, s);
+    count_over(c->C0, k, c->Lmax, cnt + CNT_OVER0, s);
+    seq_best(c->Gsum, c->diff, c->diff_excl, dI, n, cnt + CNT_OVER0, c->best_parts, c->best, cnt + CNT_INFEAS, s);
+    UPR_CUDA(cudaMemcpyAsync(c->hcut, c->cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));   // cut before the round
+    // reset node-indexed markers for the next round
+    reset_nodes(c->I_node, dI, n, c->pos, INT32_MAX, s);
+    reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
+    reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
+    seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
+    UPR_CUDA(cudaEventRecord(c->ev[7], s));
+    UPR_CUDA(cudaMemcpyAsync(c->hcnt, cnt, sizeof(int32_t) * CNT_SLOTS, cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaMemcpyAsync(c->hbest, c->best, sizeof(long long) * 2, cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    {
+        float a = 0, b = 0, d = 0, t = 0;
+        UPR_CUDA(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+        UPR_CUDA(cudaEventElapsedTime(&a, c->ev[4], c->ev[5]));
+        UPR_CUDA(cudaEventElapsedTime(&b, c->ev[5], c->ev[6]));
+        UPR_CUDA(cudaEventElapsedTime(&d, c->ev[6], c->ev[7]));
+        ri.ms_table += t; ri.tables++;
+        ri.ms_select = a; ri.ms_rebalance = b; ri.ms_sequence = d;
+    }
+    const int32_t *hc = c->hcnt;
+    ri.n_cand = rebalance_only ? 0 : hc[CNT_CAND];
+    ri.n_moves = hc[CNT_M];
+    ri.n_rebal = c->hctl->nR;
+    ri.subrounds = c->hctl->subrounds;
+    ri.n_inter = hc[CNT_X];
+    ri.n_seq = hc[CNT_I];
+    const bool infeasible = hc[CNT_INFEAS] != 0;
+    ri.best_len = infeasible ? 0 : c->hbest[1];
+    ri.best_gain = infeasible ? 0 : c->hbest[0];
+    if (log_enabled())
+        fprintf(stderr, "upr round %d: candidates %lld moves %lld rebalance moves %lld in %d sub-rounds, "
+                        "sequence %lld, applied %lld (gain %lld)\n",
+                r, (long long)ri.n_cand, (long long)ri.n_moves, (long long)ri.n_rebal, ri.subrounds,
+                (long long)ri.n_seq, (long long)ri.best_len, (long long)ri.best_gain);
+    if (T) {
+        const int64_t nM = ri.n_moves, nR = ri.n_rebal, nX = ri.n_inter, nI = ri.n_seq;
+        T->n_cand = ri.n_cand; T->n_moves = nM; T->n_rebal = nR; T->subrounds = ri.subrounds; T->n_inter = nX;
+        T->n_seq = nI;
+        if (!rebalance_only) {
+            d2h(T->avail, tr->avail_d, n, s);
+            d2h(T->slot, tr->slot_d, sizeof(int32_t) * n, s);
+            d2h(T->bucket, c->BW, sizeof(int64_t) * k * kSlots, s);
+            if (T->factor) memcpy(T->factor, c->hF, sizeof(int64_t) * kSlots);
+            d2h(T->cand_target, c->cand_tgt, sizeof(int32_t) * n, s);
+            d2h(T->cand_s0, c->cand_s0, sizeof(int64_t) * n, s);
+        }
+        std::vector<int32_t> tmp(rebalance_only ? 0 : n);
+        if (T->cand_gain && !rebalance_only)
+            UPR_CUDA(cudaMemcpyAsync(tmp.data(), c->cand_gain, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        d2h(T->M_node, c->M_node, sizeof(int32_t) * nM, s);
+        d2h(T->M_to, c->M_to, sizeof(int32_t) * nM, s);
+        d2h(T->M_score, c->M_score, sizeof(int64_t) * nM, s);
+        d2h(T->R_node, c->R_node, sizeof(int32_t) * nR, s);
+        d2h(T->R_from, c->R_from, sizeof(int32_t) * nR, s);
+        d2h(T->R_to, c->R_to, sizeof(int32_t) * nR, s);
+        d2h(T->R_subround, c->R_sub, sizeof(int32_t) * nR, s);
         d2h(T->X_node, c->X_node, sizeof(int32_t) * nX, s);
         d2h(T->X_from, c->X_from, sizeof(int32_t) * nX, s);
         d2h(T->X_to, c->X_to, sizeof(int32_t) * nX, s);
-    }
-
-    // ---- (c1) merge double moves
-    int64_t nI = 0;
-    if (nX > 0) {
-        seq_merge_flags(c->X_node, c->X_to, c->X_isr, nX, c->m_pos, c->r_to, c->part0, c->flags2, c->final_to, s);
-        select_flags(c->flags2, c->excl_i, c->idxD, c->counts + 5, nX, c->tmp, s);
-        nI = read_count(c, 5);
-        seq_build_I(c->idxD, c->counts + 5, nI, c->X_node, c->final_to, c->part0, c->I_node, c->I_from, c->I_to,
-                    c->pos, c->dest, s);
-    }
-    ri.n_seq = nI;
-
-    // ---- (c2) exact gains, balanced prefixes, best prefix
-    int32_t over0 = 0;
-    {
-        std::vector<int64_t> C0h(k);
-        read_i64(c, c->C0, k, C0h.data());
-        for (int32_t b = 0; b < k; b++) over0 += C0h[b] > c->Lmax;
-    }
-    UPR_CUDA(cudaMemsetAsync(c->diff, 0, sizeof(int32_t) * (nI + 1), s));
-    if (nI > 0) {
-        seq_gains(G, c->I_node, c->I_from, c->I_to, nI, c->pos, c->dest, c->part0, c->I_gain, c->hub_flag,
-                  c->hub_excl, c->hubs, c->counts + 6, c->tmp, s);
-        inclusive_sum_i64(c->I_gain, c->Gsum, nI, c->tmp, s);
-        uint64_t *kE; uint32_t *E;
-        seq_iev_keys(c->I_from, c->I_to, nI, c->sb[2].k, c->sb[2].v, s);
-        c->sb[2].run(2 * nI, kbits, c->tmp, s, &kE, &E);
-        UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
-        seq_iev_delta(c->I_node, E, kE, 2 * nI, G.vwgt, c->delta, c->ebeg, s);
-        exclusive_sum_i64(c->delta, c->d_excl, 2 * nI, c->tmp, s);
-        seq_iev_transitions(E, kE, 2 * nI, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->diff, s);
-    }
-    exclusive_sum_i32(c->diff, c->diff_excl, nI + 1, c->tmp, s);
-    seq_best(c->Gsum, c->diff, c->diff_excl, nI, over0, c->best_parts, c->best, s);
-    long long best[2];
-    UPR_CUDA(cudaMemcpyAsync(c->h, c->best, sizeof(best), cudaMemcpyDeviceToHost, s));
-    UPR_CUDA(cudaStreamSynchronize(s));
-    memcpy(best, c->h, sizeof(best));
-    if (T) {
-        T->n_cand = ri.n_cand; T->n_moves = nM; T->n_rebal = nR; T->subrounds = ri.subrounds; T->n_inter = nX;
-        T->n_seq = nI;
         d2h(T->I_node, c->I_node, sizeof(int32_t) * nI, s);
         d2h(T->I_from, c->I_from, sizeof(int32_t) * nI, s);
         d2h(T->I_to, c->I_to, sizeof(int32_t) * nI, s);
         d2h(T->I_gain, c->I_gain, sizeof(int64_t) * nI, s);
-        if (T->I_eligible) {
-            std::vector<int32_t> df(nI + 1), de(nI + 1);
-            UPR_CUDA(cudaMemcpyAsync(df.data(), c->diff, sizeof(int32_t) * (nI + 1), cudaMemcpyDeviceToHost, s));
-            UPR_CUDA(cudaMemcpyAsync(de.data(), c->diff_excl, sizeof(int32_t) * (nI + 1), cudaMemcpyDeviceToHost, s));
-            UPR_CUDA(cudaStreamSynchronize(s));
-            for (int64_t j = 0; j <= nI; j++) T->I_eligible[j] = (over0 + de[j] + df[j]) == 0;
-        }
-        int64_t cb;
-        read_i64(c, c->cut, 1, &cb);
-        T->cut_before = cb;
-    }
-    // reset node-indexed markers for the next round
-    reset_nodes(c->I_node, nI, c->pos, INT32_MAX, s);
-    reset_nodes(c->M_node, nM, c->m_pos, -1, s);
-    reset_nodes(c->R_node, nR, c->r_to, -1, s);
-    if (best[1] < 0) {
+        std::vector<int32_t> df(nI + 1), de(nI + 1);
+        UPR_CUDA(cudaMemcpyAsync(df.data(), c->diff, sizeof(int32_t) * (nI + 1), cudaMemcpyDeviceToHost, s));
+        UPR_CUDA(cudaMemcpyAsync(de.data(), c->diff_excl, sizeof(int32_t) * (nI + 1), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
-        return UPR_ERR_INFEASIBLE;
+        if (T->cand_gain && !rebalance_only)
+            for (int64_t v = 0; v < n; v++) T->cand_gain[v] = tmp[v];
+        if (T->I_eligible)
+            for (int64_t j = 0; j <= nI; j++) T->I_eligible[j] = (hc[CNT_OVER0] + de[j] + df[j]) == 0;
+        T->cut_before = *c->hcut;
+        T->best_len = infeasible ? 0 : c->hbest[1];
+        T->best_gain = infeasible ? 0 : c->hbest[0];
+        T->cut_after = *c->hcut - T->best_gain;
     }
-    seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, nI, c->best, c->part0, c->C0, c->cut, s);
-    ri.best_len = best[1];
-    ri.best_gain = best[0];
-    if (T) {
-        T->best_len = best[1];
-        T->best_gain = best[0];
-        int64_t ca;
-        read_i64(c, c->cut, 1, &ca);
-        T->cut_after = ca;
-    }
-    return UPR_OK;
+    return infeasible ? UPR_ERR_INFEASIBLE : UPR_OK;
 }
 
 void free_ctx(upr_ctx *c) {
@@ -598,12 +586,41 @@ upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_param
                     chunks.push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
         }
         c->n_chunks = (int64_t)chunks.size();
+        // static schedule of the tiled table build: runs of consecutive nodes
+        // with at most tile_nodes rows (<= 64 KB of shared memory) and at most
+        // kTileEntries non-hub adjacency entries; a hub closes its tile
+        std::vector<TableTile> tiles;
+        if (k % 4 == 0) {
+            const int64_t kTileEntries = 4096;
+            c->tile_nodes = (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k));
+            int64_t v = 0;
+            while (v < c->n) {
+                TableTile t{xadj_h[v], xadj_h[v], (int32_t)v, (int32_t)v};
+                while (v < c->n && t.v1 - t.v0 < c->tile_nodes) {
+                    const int64_t d = xadj_h[v + 1] - xadj_h[v];
+                    if (d > kHubDegree) { t.v1 = (int32_t)(++v); break; }     // hub: row zero here, last in tile
+                    if (t.e1 + d - t.e0 > kTileEntries && t.v1 > t.v0) break;
+                    t.e1 += d;
+                    t.v1 = (int32_t)(++v);
+                }
+                tiles.push_back(t);
+            }
+        }
+        c->n_tiles = (int64_t)tiles.size();
         Arena A;
         layout(c, A);
         if (cudaMalloc(&c->mem, A.off) != cudaSuccess) { cudaGetLastError(); free_ctx(c); return UPR_ERR_OOM; }
         A.base = (char *)c->mem; A.off = 0;
         layout(c, A);
-        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * std::max<int64_t>(4 * k, 2 * kSlots + 64)));
+        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * (std::max<int64_t>(4 * k, 2 * kSlots + 64) + 256)));
+        {
+            int64_t *base = c->h + std::max<int64_t>(4 * k, 2 * kSlots + 64);
+            c->hF = base;                                           // 73
+            c->hcut = base + 80;                                    // 1
+            c->hbest = reinterpret_cast<long long *>(base + 88);    // 2
+            c->hctl = reinterpret_cast<RebalCtl *>(base + 96);      // 4
+            c->hcnt = reinterpret_cast<int32_t *>(base + 112);      // 64 ints
+        }
         UPR_CUDA(cudaMallocHost((void **)&c->h8, 2 * (size_t)k + 64));
         for (auto &e : c->ev) UPR_CUDA(cudaEventCreate(&e));
         cudaStream_t s = c->s;
@@ -614,6 +631,8 @@ upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_param
         if (!chunks.empty())
             UPR_CUDA(cudaMemcpyAsync(c->hub_chunks, chunks.data(), sizeof(HubChunk) * chunks.size(),
                                      cudaMemcpyHostToDevice, s));
+        if (!tiles.empty())
+            UPR_CUDA(cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(TableTile) * tiles.size(), cudaMemcpyHostToDevice, s));
         c->G = GraphDev{c->n, c->m, k, c->xadj, c->adj, g->adjwgt ? c->adjw : nullptr, g->vwgt ? c->vwgt : nullptr,
                         c->wI};
         if (prm.validate) {
@@ -667,6 +686,7 @@ upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, 
     const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
     if (c->prm.round_offset + rounds > total) return UPR_ERR_INVALID;
     upr_stats st{};
+    const auto t_host0 = std::chrono::steady_clock::now();
     const long long launches0 = g_upr_launches.load();
     try {
         UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
@@ -694,6 +714,7 @@ upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, 
             st.n_candidates += ri.n_cand; st.n_moves += ri.n_moves; st.n_rebalance_moves += ri.n_rebal;
             st.n_sequence += ri.n_seq; st.n_applied += ri.best_len; st.subrounds += ri.subrounds;
             st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
+            st.ms_select += ri.ms_select; st.ms_rebalance += ri.ms_rebalance; st.ms_sequence += ri.ms_sequence;
         }
         copy_out(part, c->part0, sizeof(int32_t) * c->n, c->s);
         read_i64(c, c->cut, 1, &st.cut_out);
@@ -706,6 +727,7 @@ upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, 
         return UPR_ERR_CUDA;
     }
     st.kernel_launches = (int32_t)(g_upr_launches.load() - launches0);
+    st.ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
     st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
                           4 * c->n * (int64_t)c->k;
     if (stats) *stats = st;
@@ -717,8 +739,8 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
     try {
         upr_status rc = load_part(c, part);
         if (rc != UPR_OK) return rc;
-        RoundInfo ri;
-        build_table(c, c->part0, ri);
+        gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, nullptr, c->s);
         if (W) UPR_CUDA(cudaMemcpyAsync(W, c->W, sizeof(int32_t) * c->n * c->k, cudaMemcpyDeviceToHost, c->s));
         if (wI && c->n > 0) {
             std::vector<int32_t> w(c->n);
@@ -763,6 +785,7 @@ size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k) {
     upr_ctx c;
     c.n = n; c.m = m; c.k = k;
     c.n_chunks = m / 4096 + 1;
+    c.n_tiles = n + 1;
     Arena A;
     layout(&c, A);
     return A.off + ((size_t)1 << 20);

@@ -139,7 +139,9 @@ __global__ void k_validate_nodes(const int64_t *__restrict__ xadj, const int32_t
 template <int G>
 __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                                                      const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
-                                                     int64_t n, int32_t k, int32_t *__restrict__ W) {
+                                                     int64_t n, int32_t k, int32_t *__restrict__ W,
+                                                     const int64_t *__restrict__ deg_sum, int64_t m) {
+    if (deg_sum && *deg_sum * 4 < m) return;
     extern __shared__ int s_rows[];
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
@@ -153,10 +155,12 @@ __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__
         if (active) {
             const int64_t b0 = xadj[v], b1 = xadj[v + 1];
             if (b1 - b0 <= kHubDegree) {
+                // adjacency is read once per build: stream it past L2 so the
+                // gathered partition array stays cached
                 if (adjw) {
-                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[adj[e]]], adjw[e]);
+                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[__ldcs(adj + e)]], __ldcs(adjw + e));
                 } else {
-                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[adj[e]]], 1);
+                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[__ldcs(adj + e)]], 1);
                 }
             }
         }
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__
             int32_t *dst = W + v * (int64_t)k;
             if (vec) {
                 for (int b = gl * 4; b < k; b += G * 4)
-                    *reinterpret_cast<int4 *>(dst + b) = *reinterpret_cast<const int4 *>(row + b);
+                    __stcs(reinterpret_cast<int4 *>(dst + b), *reinterpret_cast<const int4 *>(row + b));
             } else {
                 for (int b = gl; b < k; b += G) dst[b] = row[b];
             }
@@ -174,12 +178,97 @@ __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__
     }
 }
 
+// Dense gain table, tiled: one CTA per tile of consecutive nodes whose
+// adjacency (without hubs) is one contiguous range of entries.  The CTA
+// streams that range with 16-byte loads (16 entries in flight per thread),
+// gathers the neighbours' blocks, finds each entry's owner (binary search in
+// the tile's xadj slice for the first of four consecutive entries, then a
+// forward walk), accumulates all rows of the tile in shared memory and writes
+// them as one contiguous block with streaming stores.  Hub rows stay zero.
+constexpr int kTableUnroll = 4;
+
+__device__ __forceinline__ int tile_owner(const int64_t *s_x, int nn, int64_t e) {
+    int lo = 0, hi = nn - 1;            // last i with s_x[i] <= e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_x[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict__ tiles,
+                                                     const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                                                     const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
+                                                     int32_t k, int32_t *__restrict__ W,
+                                                     const int64_t *__restrict__ deg_sum, int64_t m) {
+    if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
+    extern __shared__ int4 s_raw[];
+    const TableTile t = tiles[blockIdx.x];
+    const int nn = t.v1 - t.v0;
+    int64_t *s_x = reinterpret_cast<int64_t *>(s_raw);           // nn + 1 row starts
+    int *rows = reinterpret_cast<int *>(s_x + ((nn + 2) & ~1));    // nn * k
+    for (int i = threadIdx.x; i <= nn; i += blockDim.x) s_x[i] = xadj[t.v0 + i];
+    const int words4 = nn * k / 4;
+    const int4 z = make_int4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < words4; i += blockDim.x) reinterpret_cast<int4 *>(rows)[i] = z;
+    __syncthreads();
+    // ragged head and tail (fewer than 4 entries each) element by element
+    const int64_t qa = (t.e0 + 3) >> 2, qb = t.e1 >> 2;     // aligned quads [qa, qb)
+    if (threadIdx.x < 8) {
+        const int64_t e = threadIdx.x < 4 ? t.e0 + threadIdx.x : (qb << 2) + (threadIdx.x - 4);
+        const bool in_head = threadIdx.x < 4 && e < min(qa << 2, t.e1);
+        const bool in_tail = threadIdx.x >= 4 && qb >= qa && e < t.e1;
+        if (in_head || in_tail) {
+            const int o = tile_owner(s_x, nn, e);
+            atomicAdd(&rows[o * k + part[adj[e]]], adjw ? adjw[e] : 1);
+        }
+    }
+    const int4 *adj4 = reinterpret_cast<const int4 *>(adj);
+    const int4 *adjw4 = reinterpret_cast<const int4 *>(adjw);
+    for (int64_t q0 = qa + threadIdx.x; q0 < qb; q0 += (int64_t)blockDim.x * kTableUnroll) {
+        int4 u[kTableUnroll], w[kTableUnroll];
+#pragma unroll
+        for (int r = 0; r < kTableUnroll; r++) {
+            const int64_t q = q0 + (int64_t)r * blockDim.x;
+            u[r] = q < qb ? __ldcs(adj4 + q) : make_int4(0, 0, 0, 0);
+            w[r] = (q < qb && adjw) ? __ldcs(adjw4 + q) : make_int4(1, 1, 1, 1);
+        }
+        int pb[kTableUnroll][4];
+#pragma unroll
+        for (int r = 0; r < kTableUnroll; r++) {
+            const bool ok = q0 + (int64_t)r * blockDim.x < qb;
+            pb[r][0] = ok ? part[u[r].x] : 0;
+            pb[r][1] = ok ? part[u[r].y] : 0;
+            pb[r][2] = ok ? part[u[r].z] : 0;
+            pb[r][3] = ok ? part[u[r].w] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kTableUnroll; r++) {
+            const int64_t q = q0 + (int64_t)r * blockDim.x;
+            if (q >= qb) continue;
+            const int64_t e = q << 2;
+            int o = tile_owner(s_x, nn, e);
+            const int ww[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                while (s_x[o + 1] <= e + j) o++;
+                atomicAdd(&rows[o * k + pb[r][j]], ww[j]);
+            }
+        }
+    }
+    __syncthreads();
+    int4 *dst = reinterpret_cast<int4 *>(W + (int64_t)t.v0 * k);
+    for (int i = threadIdx.x; i < words4; i += blockDim.x) __stcs(dst + i, reinterpret_cast<const int4 *>(rows)[i]);
+}
+
 // Hub rows: one CTA per chunk of a hub's adjacency, shared-memory row, then
 // atomic adds of the non-zero entries into the (zeroed) global row.
 __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__restrict__ chunks, const int32_t *__restrict__ adj,
                                                           const int32_t *__restrict__ adjw,
                                                           const int32_t *__restrict__ part, int32_t k,
-                                                          int32_t *__restrict__ W) {
+                                                          int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
+                                                          int64_t m) {
+    if (deg_sum && *deg_sum * 4 < m) return;
     extern __shared__ int s_row[];
     const HubChunk ch = chunks[blockIdx.x];
     for (int b = threadIdx.x; b < k; b += blockDim.x) s_row[b] = 0;
@@ -196,12 +285,15 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
 __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                              const int32_t *__restrict__ adjw, int32_t k, int32_t *__restrict__ W,
                              const int32_t *__restrict__ nodes, const int32_t *__restrict__ from,
-                             const int32_t *__restrict__ to, const int32_t *__restrict__ d_count) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                             const int32_t *__restrict__ to, const int32_t *__restrict__ d_count,
+                             const int32_t *__restrict__ d_offset, const int64_t *__restrict__ deg_sum, int64_t m) {
+    if (deg_sum && *deg_sum * 4 >= m) return;     // a rebuild handles this case
     const int lane = threadIdx.x & 31;
     const int64_t cnt = *d_count;
-    for (int64_t j = i; j < cnt; j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int32_t v = nodes[j], a = from[j], b = to[j];
+    const int64_t off = d_offset ? *d_offset : 0;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
+         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t v = nodes[off + j], a = from[off + j], b = to[off + j];
         for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) {
             const int32_t w = adjw ? adjw[e] : 1;
             int32_t *row = W + (int64_t)adj[e] * k;
@@ -260,40 +352,60 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaSt
     }
 }
 
+size_t table_tile_smem(int32_t k, int32_t nodes) {
+    return sizeof(int64_t) * (size_t)((nodes + 2) & ~1) + sizeof(int) * (size_t)nodes * k;
+}
+
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
-                cudaStream_t s) {
+                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s) {
     if (g.n == 0) return;
-    const int k = g.k;
-    int G = k / 4;
-    G = G < 4 ? 4 : (G > 32 ? 32 : G);
-    G = G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
-    const size_t shm = (size_t)(256 / G) * k * sizeof(int);
-    const int64_t groups = 256 / G;
-    const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count() * 16);
-    if (shm > 48 * 1024) {
-        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        UPR_CUDA(cudaFuncSetAttribute(k_table_dense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    if (tiles && n_tiles > 0) {
+        const size_t shm = table_tile_smem(g.k, tile_nodes);
+        static thread_local size_t attr_set = 0;
+        if (shm > 48 * 1024 && attr_set < shm) {
+            UPR_CUDA(cudaFuncSetAttribute(k_table_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            attr_set = shm;
+        }
+        k_table_tiles<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, W, deg_sum, g.m);
+        UPR_LAUNCH_CHECK();
+    } else {
+        const int k = g.k;
+        int G = k / 4;
+        G = G < 4 ? 4 : (G > 32 ? 32 : G);
+        G = G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
+        const size_t shm = (size_t)(256 / G) * k * sizeof(int);
+        const int64_t groups = 256 / G;
+        const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count() * 16);
+        if (shm > 48 * 1024) {
+            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        }
+#define UPR_TD(GG) k_table_dense<GG><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W, deg_sum, g.m)
+        switch (G) {
+            case 4: UPR_TD(4); break;
+            case 8: UPR_TD(8); break;
+            case 16: UPR_TD(16); break;
+            default: UPR_TD(32); break;
+        }
+#undef UPR_TD
+        UPR_LAUNCH_CHECK();
     }
-    switch (G) {
-        case 4: k_table_dense<4><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
-        case 8: k_table_dense<8><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
-        case 16: k_table_dense<16><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
-        default: k_table_dense<32><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W); break;
-    }
-    UPR_LAUNCH_CHECK();
     if (n_chunks > 0) {
-        k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * k, s>>>(hub_chunks, g.adj, g.adjw, part, k, W);
+        k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k, W,
+                                                                             deg_sum, g.m);
         UPR_LAUNCH_CHECK();
     }
 }
 
 void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
-                const int32_t *d_count, int64_t max_count, cudaStream_t s) {
+                const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
+                cudaStream_t s) {
     if (max_count <= 0) return;
     int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
-    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, W, nodes, from, to, d_count);
+    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, W, nodes, from, to, d_count, d_offset,
+                                                  deg_sum, g.m);
     UPR_LAUNCH_CHECK();
 }
 

@@ -20,33 +20,61 @@ struct GraphDev {
 __device__ __forceinline__ int64_t node_c(const GraphDev &g, int64_t v) { return g.vwgt ? (int64_t)g.vwgt[v] : 1; }
 __device__ __forceinline__ int32_t edge_w(const GraphDev &g, int64_t e) { return g.adjw ? g.adjw[e] : 1; }
 
+// An element count that may live in device memory: d (nullable) holds the
+// actual count, max is a static upper bound used to size grids and buffers.
+struct Count {
+    const int32_t *d;
+    int64_t max;
+};
+inline Count fixed(int64_t n) { return Count{nullptr, n}; }
+
+// Grid-stride loop over a device-held count (all threads of the grid).
+#define UPR_FOR(i, cnt) \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (cnt); i += (int64_t)gridDim.x * blockDim.x)
+
+// A grid of 256-thread blocks for up to `max` items, at most 8 blocks per SM.
+inline unsigned grid_for(int64_t max) {
+    const int64_t b = ceil_div(max > 0 ? max : 1, 256);
+    return (unsigned)std::min<int64_t>(b, (int64_t)device_sm_count() * 8);
+}
+
 // ---- prim.cu
 size_t scan_temp_bytes(int64_t n);
 size_t radix_temp_bytes(int64_t n);
-void exclusive_sum_i32(const int32_t *in, int32_t *out, int64_t n, void *tmp, cudaStream_t s);
-void exclusive_sum_i64(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
-void inclusive_sum_i64(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
-void exclusive_sum_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
-void inclusive_max_u64(const uint64_t *in, uint64_t *out, int64_t n, void *tmp, cudaStream_t s);
+void exclusive_sum_i32(const int32_t *in, int32_t *out, Count n, void *tmp, cudaStream_t s);
+void exclusive_sum_i64(const int64_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s);
+void inclusive_sum_i64(const int64_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s);
+void exclusive_sum_i32_to_i64(const int32_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s);
+void inclusive_max_u64(const uint64_t *in, uint64_t *out, Count n, void *tmp, cudaStream_t s);
 void iota_u32(uint32_t *v, int64_t n, cudaStream_t s);
-// Stable LSD sort on key bits [0, bits); returns true if the result is in the *_alt buffers.
-bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, int64_t n, int bits,
+// Stable LSD sort on key bits [0, bits); returns true if the result is in the *_alt buffers
+// (a property of `bits` alone, known when the launches are enqueued).
+bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, Count n, int bits,
                       void *tmp, cudaStream_t s);
-// out_idx[0..*d_count) = indices i with flags[i] != 0, ascending.  excl: n scratch ints.
-void select_flags(const int32_t *flags, int32_t *excl, int32_t *out_idx, int32_t *d_count, int64_t n, void *tmp,
-                  cudaStream_t s);
+// out_idx[0..*d_count) = indices i < n with flags[i] != 0, ascending.
+void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, void *tmp, cudaStream_t s);
 
 // ---- graph.cu: step (e), step (a), create-time work
 struct HubChunk { int32_t v; int32_t pad; int64_t begin, end; };
 void block_weights(const GraphDev &g, const int32_t *part, int64_t *C, cudaStream_t s);
 void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t s);
 void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_t s);
+// A tile of the table build: nodes [v0, v1) and the adjacency entries [e0, e1)
+// of its non-hub nodes (a hub, if any, is the tile's last node).
+struct TableTile { int64_t e0, e1; int32_t v0, v1; };
+// Shared memory of one tile of `nodes` rows.
+size_t table_tile_smem(int32_t k, int32_t nodes);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
+// With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
+// With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
-                cudaStream_t s);
-// For each listed node v moving from[i] -> to[i]: W[u][from] -= w, W[u][to] += w for every neighbour u.
+                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s);
+// For each listed node v moving from[i] -> to[i] (i < *d_count, entries start at
+// *d_offset when given): W[u][from] -= w, W[u][to] += w for every neighbour u.
+// With deg_sum: runs only when 4 * (*deg_sum) < m (otherwise a rebuild is cheaper).
 void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
-                const int32_t *d_count, int64_t max_count, cudaStream_t s);
+                const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
+                cudaStream_t s);
 // Graph checks; writes a bitmask of violations into *d_flags (see engine.cu).
 void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s);
 
@@ -62,88 +90,117 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
 void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Penalty pen, int32_t *cand_tgt,
                   int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s);
 void cand_keys(const int32_t *cand_idx, const int32_t *d_count, const int32_t *cand_tgt, const int64_t *cand_s0,
-               uint64_t *keys, uint32_t *vals, int64_t max_count, cudaStream_t s);
+               int gbits, uint64_t *keys, uint32_t *vals, int64_t max_count, cudaStream_t s);
 void cand_gather(const GraphDev &g, const int32_t *cand_idx, const uint32_t *order, const int32_t *d_count,
                  const int32_t *cand_tgt, int64_t *c_sorted, int32_t *seg_first, int64_t max_count, cudaStream_t s);
 void inflow_filter(const GraphDev &g, const int32_t *cand_idx, const uint32_t *order, const int32_t *d_count,
                    const int32_t *cand_tgt, const int32_t *cand_gain, const int64_t *c_excl, const int32_t *seg_first,
                    Penalty pen, int32_t *keep_flag, int64_t *score, int64_t max_count, cudaStream_t s);
-void move_keys(const int32_t *m_idx, const int32_t *d_count, const int64_t *score, uint64_t *keys, uint32_t *vals,
-               int64_t max_count, cudaStream_t s);
+void move_keys(const int32_t *m_idx, const int32_t *d_count, const int64_t *score, int gbits, uint64_t *keys,
+               uint32_t *vals, int64_t max_count, cudaStream_t s);
 void apply_moves(const GraphDev &g, const int32_t *cand_idx, const int32_t *m_idx, const uint32_t *order,
                  const int32_t *d_count, const int32_t *cand_tgt, const int64_t *score, const int32_t *part0,
                  int32_t *part, int64_t *C, int32_t *M_node, int32_t *M_from, int32_t *M_to, int64_t *M_score,
-                 int32_t *m_pos, int64_t max_count, cudaStream_t s);
+                 int32_t *m_pos, int64_t *deg_sum, int64_t max_count, cudaStream_t s);
 
 // ---- rebalance.cu: step (d)
+// Device-resident control block of the rebalancing loop.
+struct RebalCtl {
+    int32_t active;      // the current sub-round runs
+    int32_t stopped;     // the loop has finished
+    int32_t light;       // lightest block that may receive moves, or -1
+    int32_t subrounds;   // sub-rounds that ran
+    int32_t nR;          // rebalancing moves so far (length of R)
+    int32_t n1_active;   // length of the node list if this sub-round runs, else 0
+    int32_t pad[2];
+};
 struct RebalState {
     const int64_t *C;     // current block weights
     const int8_t *over;   // [k] overloaded now
     const int8_t *excl;   // [k] not a target: overloaded at the first sub-round, or rejected a move
-    int32_t light;        // lightest non-excluded block, or -1
+    const int32_t *light; // lightest non-excluded block, or -1
     int64_t Lmax;
 };
-void rebalance_propose(const GraphDev &g, const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
-                       int32_t *prop_gain, int32_t *flags, cudaStream_t s);
+// flags[v] = 1 for the nodes of the marked blocks
+void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s);
+void rebalance_gather_list(const int32_t *list, const int32_t *pos, const int32_t *d_cnt, int32_t *out, int64_t cnt_max,
+                           cudaStream_t s);
+// Proposals of the listed nodes in overloaded blocks: prop_tgt/prop_gain by node, flags by list position.
+void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
+                                   const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
+                                   int32_t *prop_gain, int32_t *flags, cudaStream_t s);
+void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
+                            const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
+                            int32_t *prop_gain, int32_t *flags, cudaStream_t s);
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
-                         int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np, cudaStream_t s);
+                         int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s);
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,
-                          const int32_t *blk_of_node, uint64_t *keys, uint32_t *vals, int64_t cnt, cudaStream_t s);
+                          const int32_t *blk_of_node, uint64_t *keys, uint32_t *vals, int64_t cnt_max, cudaStream_t s);
 void rebalance_seg_weights(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S,
                            const uint32_t *B, const uint64_t *bkeys, const int32_t *d_cnt, int64_t *c_sorted,
-                           int32_t *seg_first, int64_t cnt, cudaStream_t s);
+                           int32_t *seg_first, int64_t cnt_max, cudaStream_t s);
 void rebalance_mark_selected(const uint32_t *B, const uint64_t *bkeys, const int32_t *d_cnt, const int64_t *c_excl,
-                             const int32_t *seg_first, RebalState st, int32_t *sel, int64_t cnt, cudaStream_t s);
+                             const int32_t *seg_first, RebalState st, int32_t *sel, int64_t cnt_max, cudaStream_t s);
 void rebalance_mark_admitted(const uint32_t *T, const uint64_t *bkeys, const int32_t *d_cnt, const int64_t *c_sorted,
                              const int64_t *c_excl, const int32_t *seg_first, RebalState st, int32_t *adm,
-                             int8_t *reject, int64_t cnt, cudaStream_t s);
+                             int8_t *reject, int64_t cnt_max, cudaStream_t s);
 void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *Adm,
-                     const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, int32_t subround,
-                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int64_t na,
+                     const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, const RebalCtl *ctl,
+                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int64_t na_max,
                      cudaStream_t s);
+void rebalance_init(const int64_t *C, int32_t k, int64_t Lmax, int8_t *excl, RebalCtl *ctl, cudaStream_t s);
+void rebalance_begin(const int64_t *C, int32_t k, int64_t Lmax, const int8_t *excl, int8_t *over, int8_t *reject,
+                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, cudaStream_t s);
+void rebalance_end(int32_t k, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl, cudaStream_t s);
 
-// ---- sequence.cu: step (c)
+// ---- sequence.cu: step (c); every count lives in device memory, `max` bounds it
+void count_affine(const int32_t *a, int32_t a_mul, const int32_t *b, int32_t add, int32_t *out, cudaStream_t s);
 void fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t s);
-void reset_nodes(const int32_t *nodes, int64_t cnt, int32_t *arr, int32_t val, cudaStream_t s);
-void seq_rb_keys(const int32_t *R_from, int64_t nR, uint64_t *keys, uint32_t *vals, cudaStream_t s);
-void seq_rb_bounds(const int32_t *R_node, const int32_t *R_from, const uint32_t *RB, int64_t nR, const int32_t *vwgt,
-                   int64_t *rc, int32_t *rbeg, int32_t *rend, cudaStream_t s);
-void seq_ev_keys(const int32_t *M_from, const int32_t *M_to, int64_t nM, uint64_t *keys, uint32_t *vals,
+void clear_count(int32_t *a, const int32_t *d_n, int32_t extra, int64_t max, cudaStream_t s);
+void reset_nodes(const int32_t *nodes, const int32_t *d_cnt, int64_t max, int32_t *arr, int32_t val, cudaStream_t s);
+void count_over(const int64_t *C, int32_t k, int64_t Lmax, int32_t *out, cudaStream_t s);
+void seq_rb_keys(const int32_t *R_from, const int32_t *d_nR, int64_t max, uint64_t *keys, uint32_t *vals,
                  cudaStream_t s);
-void seq_ev_delta(const int32_t *M_node, const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int32_t *vwgt,
-                  int64_t *delta, int32_t *ebeg, int32_t *eend, cudaStream_t s);
-void seq_ev_need(const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int64_t *delta, const int64_t *d_excl,
-                 const int32_t *ebeg, const int64_t *C0, int64_t Lmax, const int32_t *rbeg, const int32_t *rend,
-                 const int64_t *rc_excl, const int64_t *rc, uint64_t *packed, cudaStream_t s);
-void seq_ev_emit(const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const uint64_t *qmax, const int32_t *ebeg,
-                 int32_t *emit, int32_t *qbefore_m, cudaStream_t s);
+void seq_rb_bounds(const int32_t *R_node, const int32_t *R_from, const uint32_t *RB, const int32_t *d_nR, int64_t max,
+                   const int32_t *vwgt, int64_t *rc, int32_t *rbeg, int32_t *rend, cudaStream_t s);
+void seq_ev_keys(const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM, int64_t max, uint64_t *keys,
+                 uint32_t *vals, cudaStream_t s);
+void seq_ev_delta(const int32_t *M_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max,
+                  const int32_t *vwgt, int64_t *delta, int32_t *ebeg, int32_t *eend, cudaStream_t s);
+void seq_ev_need(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const int64_t *delta,
+                 const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, int64_t Lmax, const int32_t *rbeg,
+                 const int32_t *rend, const int64_t *rc_excl, const int64_t *rc, uint64_t *packed, cudaStream_t s);
+void seq_ev_emit(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const uint64_t *qmax,
+                 const int32_t *ebeg, int32_t *emit, int32_t *qbefore_m, cudaStream_t s);
 void seq_block_final(int32_t k, const int32_t *ebeg, const int32_t *eend, const uint64_t *qmax, const int32_t *rbeg,
                      const int32_t *rend, int32_t *qfin, int32_t *left, cudaStream_t s);
-void seq_place_m(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, int64_t nM, const int32_t *em_excl,
-                 int32_t *pos_m, int32_t *X_node, int32_t *X_from, int32_t *X_to, int8_t *X_isr, cudaStream_t s);
-void seq_place_r(const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const uint32_t *RB, int64_t nR,
-                 const int32_t *rbeg, const uint32_t *EV, const int32_t *ebeg, const int32_t *eend,
-                 const uint64_t *qmax, const int32_t *pos_m, const int32_t *qfin, const int32_t *left_excl,
-                 const int32_t *em_excl, const int32_t *emit, int64_t nM, int32_t *X_node, int32_t *X_from,
-                 int32_t *X_to, int8_t *X_isr, cudaStream_t s);
-void seq_merge_flags(const int32_t *X_node, const int32_t *X_to, const int8_t *X_isr, int64_t nX, const int32_t *m_pos,
-                     const int32_t *r_to, const int32_t *part0, int32_t *keep, int32_t *final_to, cudaStream_t s);
-void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t nI_max, const int32_t *X_node, const int32_t *final_to,
+void seq_place_m(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM, int64_t max,
+                 const int32_t *em_excl, int32_t *pos_m, int32_t *X_node, int32_t *X_from, int32_t *X_to,
+                 int8_t *X_isr, cudaStream_t s);
+void seq_place_r(const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const uint32_t *RB,
+                 const int32_t *d_nR, int64_t max, const int32_t *rbeg, const uint32_t *EV, const int32_t *ebeg,
+                 const int32_t *eend, const uint64_t *qmax, const int32_t *pos_m, const int32_t *qfin,
+                 const int32_t *left_excl, const int32_t *em_excl, const int32_t *emit, const int32_t *d_nM,
+                 int32_t *X_node, int32_t *X_from, int32_t *X_to, int8_t *X_isr, cudaStream_t s);
+void seq_merge_flags(const int32_t *X_node, const int32_t *X_to, const int8_t *X_isr, const int32_t *d_nX, int64_t max,
+                     const int32_t *m_pos, const int32_t *r_to, const int32_t *part0, int32_t *keep, int32_t *final_to,
+                     cudaStream_t s);
+void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int32_t *X_node, const int32_t *final_to,
                  const int32_t *part0, int32_t *I_node, int32_t *I_from, int32_t *I_to, int32_t *pos, int32_t *dest,
                  cudaStream_t s);
-void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to, int64_t nI,
-               const int32_t *pos, const int32_t *dest, const int32_t *part0, int64_t *gain, int32_t *hub_flag,
-               int32_t *hub_excl, int32_t *hubs, int32_t *d_nh, void *tmp, cudaStream_t s);
-void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, int64_t nI, uint64_t *keys, uint32_t *vals,
-                  cudaStream_t s);
-void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int32_t *vwgt,
-                   int64_t *delta, int32_t *ebeg, cudaStream_t s);
-void seq_iev_transitions(const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int64_t *delta,
-                         const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, int64_t Lmax, int32_t *diff,
-                         cudaStream_t s);
-void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, int64_t nI, int32_t over0,
-              long long *parts, long long *out, cudaStream_t s);
-void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to, int64_t nI,
-                      const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s);
+void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+               const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
+               int64_t *gain, int32_t *hub_flag, int32_t *hubs, int32_t *d_nh, void *tmp, cudaStream_t s);
+void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, const int32_t *d_nI, int64_t max, uint64_t *keys,
+                  uint32_t *vals, cudaStream_t s);
+void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,
+                   const int32_t *vwgt, int64_t *delta, int32_t *ebeg, cudaStream_t s);
+void seq_iev_transitions(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,
+                         const int64_t *delta, const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0,
+                         int64_t Lmax, int32_t *diff, cudaStream_t s);
+void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, const int32_t *d_nI, int64_t max,
+              const int32_t *d_over0, long long *parts, long long *out, int32_t *infeasible, cudaStream_t s);
+void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+                      int64_t max, const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s);
 
 }  // namespace upr

@@ -21,23 +21,26 @@ int sm_count_reb() {
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
-                                                 const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
-                                                 RebalState st, int32_t *__restrict__ prop_tgt,
-                                                 int32_t *__restrict__ prop_gain, int32_t *__restrict__ flags) {
+__global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
+                                                 const int32_t *__restrict__ part, const int32_t *__restrict__ W,
+                                                 const int32_t *__restrict__ vwgt, int32_t k, RebalState st,
+                                                 int32_t *__restrict__ prop_tgt, int32_t *__restrict__ prop_gain,
+                                                 int32_t *__restrict__ flags) {
+    const int64_t n1 = *d_n1;
+    const int32_t light = *st.light;
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
-    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
-        const int64_t v = base + gid;
-        const bool active = v < n;
-        const int32_t a = active ? part[v] : 0;
-        const bool src = active && st.over[a];
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t i = base + gid;
+        const int32_t v = i < n1 ? list[i] : 0;
+        const int32_t a = i < n1 ? part[v] : 0;
+        const bool src = i < n1 && st.over[a];
         int64_t best = 0;
         int32_t bt = -1;
         int32_t own = 0;
         int64_t c = 1;
         if (src) {
-            const int32_t *row = W + v * (int64_t)k;
+            const int32_t *row = W + (int64_t)v * k;
             own = row[a];
             c = vwgt ? vwgt[v] : 1;
             for (int b = gl; b < k; b += G) {
@@ -50,16 +53,191 @@ __global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ par
         int64_t s = best;
         int32_t id = bt;
         group_argmax<G>(s, id);
-        if (src && gl == 0) {
-            int32_t tgt = id;
+        if (i < n1 && gl == 0) {
+            int32_t tgt = src ? id : -1;
             int64_t gain = s;
-            if (tgt < 0 && st.light >= 0 && st.C[st.light] + c <= st.Lmax) { tgt = st.light; gain = -(int64_t)own; }
-            prop_tgt[v] = tgt;
-            prop_gain[v] = (int32_t)gain;
-            flags[v] = tgt >= 0 ? 1 : 0;
-        } else if (active && gl == 0) {
-            flags[v] = 0;
+            if (src && tgt < 0 && light >= 0 && st.C[light] + c <= st.Lmax) { tgt = light; gain = -(int64_t)own; }
+            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = (int32_t)gain; }
+            flags[i] = tgt >= 0 ? 1 : 0;
         }
+    }
+}
+
+__device__ __forceinline__ int32_t int4_at(const int4 &x, int c) {
+    return c == 0 ? x.x : c == 1 ? x.y : c == 2 ? x.z : x.w;
+}
+
+// Proposals of the listed nodes (the nodes of blocks overloaded when
+// rebalancing started; those that left them are skipped).  Vectorised rows
+// as in selection; s_room[b] = L_max - C[b] for an allowed target, -1 for an
+// excluded one, so one comparison c <= s_room[b] tests validity.
+template <int G, int CH>
+__global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
+                                                     const int32_t *__restrict__ part, const int32_t *__restrict__ W,
+                                                     const int32_t *__restrict__ vwgt, int32_t k, RebalState st,
+                                                     int32_t *__restrict__ prop_tgt, int32_t *__restrict__ prop_gain,
+                                                     int32_t *__restrict__ flags) {
+    const int64_t n1 = *d_n1;
+    if (n1 == 0) return;
+    extern __shared__ int64_t s_room[];
+    int8_t *s_over = reinterpret_cast<int8_t *>(s_room + k);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        s_room[i] = st.excl[i] ? -1 : st.Lmax - st.C[i];
+        s_over[i] = st.over[i];
+    }
+    __syncthreads();
+    constexpr int kGroups = 256 / G;
+    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const int32_t light = *st.light;
+    const int64_t light_room = light >= 0 ? st.Lmax - st.C[light] : -1;
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t i = base + gid;
+        const int32_t v = i < n1 ? list[i] : 0;
+        const int32_t a = i < n1 ? part[v] : 0;
+        const bool src = i < n1 && s_over[a];
+        const int4 zero = make_int4(0, 0, 0, 0);
+        int4 r[CH];
+        if (src) {
+            const int4 *row4 = reinterpret_cast<const int4 *>(W + (int64_t)v * k);
+#pragma unroll
+            for (int j = 0; j < CH; j++) {
+                const int q = gl + G * j;
+                r[j] = 4 * q < k ? row4[q] : zero;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CH; j++) r[j] = zero;
+        }
+        const int q4 = a >> 2;
+        int32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < CH; j++)
+            if (j == q4 / G) mine = int4_at(r[j], a & 3);
+        const int32_t own = __shfl_sync(0xffffffffu, mine, gbase + (q4 % G));
+        const int64_t c = src ? (vwgt ? vwgt[v] : 1) : 1;
+        int64_t best = 0;
+        int32_t bt = -1;
+        if (src) {
+#pragma unroll
+            for (int j = 0; j < CH; j++) {
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) {
+                    const int b = 4 * (gl + G * j) + cc;
+                    const int32_t w = int4_at(r[j], cc);
+                    if (b >= k || b == a || w <= 0 || c > s_room[b]) continue;
+                    const int64_t gain = (int64_t)w - own;
+                    if (bt < 0 || gain > best) { best = gain; bt = b; }
+                }
+            }
+        }
+        int64_t sb = best;
+        int32_t id = bt;
+        group_argmax<G>(sb, id);
+        if (i < n1 && gl == 0) {
+            int32_t tgt = src ? id : -1;
+            int64_t gain = sb;
+            if (src && tgt < 0 && c <= light_room) { tgt = light; gain = -(int64_t)own; }
+            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = (int32_t)gain; }
+            flags[i] = tgt >= 0 ? 1 : 0;
+        }
+    }
+}
+
+// list[i] = nodes of the blocks marked in `mark`
+__global__ void k_flag_in_blocks(const int32_t *__restrict__ part, int64_t n, const int8_t *__restrict__ mark,
+                                 int32_t *__restrict__ flags) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flags[v] = mark[part[v]] ? 1 : 0;
+}
+
+__global__ void k_gather_list(const int32_t *__restrict__ list, const int32_t *__restrict__ pos,
+                              const int32_t *__restrict__ d_cnt, int32_t *__restrict__ out) {
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(i, cnt) out[i] = list[pos[i]];
+}
+
+// ---- loop control: one CTA each, k <= 4096 blocks
+// Start of rebalancing: the blocks overloaded now are never targets.
+__global__ void k_reb_init(const int64_t *__restrict__ C, int32_t k, int64_t Lmax, int8_t *__restrict__ excl,
+                           RebalCtl *__restrict__ ctl) {
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < k; b += blockDim.x) {
+        const bool o = C[b] > Lmax;
+        excl[b] = o ? 1 : 0;
+        if (o) s_any = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->active = 0;
+        ctl->stopped = s_any ? 0 : 1;
+        ctl->light = -1;
+        ctl->subrounds = 0;
+        ctl->nR = 0;
+        ctl->n1_active = 0;
+    }
+}
+
+// Start of sub-round h: overloaded set, lightest allowed block, activity.
+__global__ void k_reb_begin(const int64_t *__restrict__ C, int32_t k, int64_t Lmax, const int8_t *__restrict__ excl,
+                            int8_t *__restrict__ over, int8_t *__restrict__ reject, const int32_t *__restrict__ d_n1,
+                            int32_t h, int32_t max_subrounds, RebalCtl *__restrict__ ctl) {
+    __shared__ int s_any;
+    __shared__ long long s_w[256];
+    __shared__ int s_b[256];
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    long long bw = 0;
+    int bb = -1;
+    for (int b = threadIdx.x; b < k; b += blockDim.x) {
+        const bool o = C[b] > Lmax;
+        over[b] = o ? 1 : 0;
+        reject[b] = 0;
+        if (o) s_any = 1;
+        if (!excl[b] && (bb < 0 || C[b] < bw)) { bw = C[b]; bb = b; }
+    }
+    s_w[threadIdx.x] = bw;
+    s_b[threadIdx.x] = bb;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const int b2 = s_b[threadIdx.x + o];
+            const long long w2 = s_w[threadIdx.x + o];
+            const int b1 = s_b[threadIdx.x];
+            if (b2 >= 0 && (b1 < 0 || w2 < s_w[threadIdx.x] || (w2 == s_w[threadIdx.x] && b2 < b1))) {
+                s_b[threadIdx.x] = b2;
+                s_w[threadIdx.x] = w2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool run = !ctl->stopped && s_any && h <= max_subrounds;
+        ctl->active = run ? 1 : 0;
+        if (!run) ctl->stopped = 1;
+        if (run) ctl->subrounds = h;
+        ctl->light = s_b[0];
+        ctl->n1_active = run ? *d_n1 : 0;
+    }
+}
+
+// End of a sub-round: targets that rejected a move are excluded from now on;
+// stop when nothing was admitted and no target was newly excluded.
+__global__ void k_reb_end(int32_t k, int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
+                          const int32_t *__restrict__ d_na, RebalCtl *__restrict__ ctl) {
+    __shared__ int s_grew;
+    if (threadIdx.x == 0) s_grew = 0;
+    __syncthreads();
+    if (!ctl->active) return;
+    for (int b = threadIdx.x; b < k; b += blockDim.x)
+        if (reject[b] && !excl[b]) { excl[b] = 1; s_grew = 1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int32_t na = *d_na;
+        ctl->nR += na;
+        if (na == 0 && !s_grew) ctl->stopped = 1;
     }
 }
 
@@ -69,20 +247,18 @@ __global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ par
 __global__ void k_prio_keys(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
                             const int32_t *__restrict__ prop_gain, const int32_t *__restrict__ vwgt, int gbits,
                             int cbits, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *d_np) return;
-    const int32_t u = P[i];
-    const int64_t g = prop_gain[u];
-    const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
+    const int64_t cnt = *d_np;
     const int S = 2 * cbits;
-    uint64_t key;
-    if (g >= 0) {
-        key = ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
-    } else {
-        key = (1ull << (gbits + S)) | ((((uint64_t)(-g)) << S) / c);
+    UPR_FOR(i, cnt) {
+        const int32_t u = P[i];
+        const int64_t g = prop_gain[u];
+        const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
+        uint64_t key;
+        if (g >= 0) key = ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
+        else key = (1ull << (gbits + S)) | ((((uint64_t)(-g)) << S) / c);
+        keys[i] = key;
+        vals[i] = (uint32_t)i;
     }
-    keys[i] = key;
-    vals[i] = (uint32_t)i;
 }
 
 // Block-id key (source or target) of the entries listed through idx/order.
@@ -90,12 +266,13 @@ __global__ void k_block_keys(const int32_t *__restrict__ P, const uint32_t *__re
                              const int32_t *__restrict__ S, const int32_t *__restrict__ d_cnt,
                              const int32_t *__restrict__ blk_of_node, uint64_t *__restrict__ keys,
                              uint32_t *__restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *d_cnt) return;
-    const int64_t j = S ? S[i] : i;
-    const int32_t u = P[A[j]];
-    keys[i] = (uint64_t)blk_of_node[u];
-    vals[i] = (uint32_t)i;
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(i, cnt) {
+        const int64_t j = S ? S[i] : i;
+        const int32_t u = P[A[j]];
+        keys[i] = (uint64_t)blk_of_node[u];
+        vals[i] = (uint32_t)i;
+    }
 }
 
 // For entries in block-sorted order: weights, and the first position of each block.
@@ -104,14 +281,15 @@ __global__ void k_seg_weights(const int32_t *__restrict__ P, const uint32_t *__r
                               const uint64_t *__restrict__ bkeys, const int32_t *__restrict__ d_cnt,
                               const int32_t *__restrict__ vwgt, int64_t *__restrict__ c_sorted,
                               int32_t *__restrict__ seg_first) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= *d_cnt) return;
-    const int64_t i = B[q];
-    const int64_t j = S ? S[i] : i;
-    const int32_t u = P[A[j]];
-    c_sorted[q] = vwgt ? vwgt[u] : 1;
-    const int32_t b = (int32_t)bkeys[q];
-    if (q == 0 || (int32_t)bkeys[q - 1] != b) seg_first[b] = (int32_t)q;
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(q, cnt) {
+        const int64_t i = B[q];
+        const int64_t j = S ? S[i] : i;
+        const int32_t u = P[A[j]];
+        c_sorted[q] = vwgt ? vwgt[u] : 1;
+        const int32_t b = (int32_t)bkeys[q];
+        if (q == 0 || (int32_t)bkeys[q - 1] != b) seg_first[b] = (int32_t)q;
+    }
 }
 
 // Minimal prefix per source: entry selected iff the weight before it in its
@@ -119,11 +297,12 @@ __global__ void k_seg_weights(const int32_t *__restrict__ P, const uint32_t *__r
 __global__ void k_mark_selected(const uint32_t *__restrict__ B, const uint64_t *__restrict__ bkeys,
                                 const int32_t *__restrict__ d_cnt, const int64_t *__restrict__ c_excl,
                                 const int32_t *__restrict__ seg_first, RebalState st, int32_t *__restrict__ sel) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= *d_cnt) return;
-    const int32_t b = (int32_t)bkeys[q];
-    const int64_t before = c_excl[q] - c_excl[seg_first[b]];
-    sel[B[q]] = before < st.C[b] - st.Lmax ? 1 : 0;
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(q, cnt) {
+        const int32_t b = (int32_t)bkeys[q];
+        const int64_t before = c_excl[q] - c_excl[seg_first[b]];
+        sel[B[q]] = before < st.C[b] - st.Lmax ? 1 : 0;
+    }
 }
 
 // Longest fitting prefix per target; a rejected entry marks its target.
@@ -131,35 +310,50 @@ __global__ void k_mark_admitted(const uint32_t *__restrict__ T, const uint64_t *
                                 const int32_t *__restrict__ d_cnt, const int64_t *__restrict__ c_sorted,
                                 const int64_t *__restrict__ c_excl, const int32_t *__restrict__ seg_first,
                                 RebalState st, int32_t *__restrict__ adm, int8_t *__restrict__ reject) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= *d_cnt) return;
-    const int32_t t = (int32_t)bkeys[q];
-    const int64_t incl = c_excl[q] - c_excl[seg_first[t]] + c_sorted[q];
-    const bool ok = st.C[t] + incl <= st.Lmax;
-    adm[T[q]] = ok ? 1 : 0;
-    if (!ok) reject[t] = 1;
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(q, cnt) {
+        const int32_t t = (int32_t)bkeys[q];
+        const int64_t incl = c_excl[q] - c_excl[seg_first[t]] + c_sorted[q];
+        const bool ok = st.C[t] + incl <= st.Lmax;
+        adm[T[q]] = ok ? 1 : 0;
+        if (!ok) reject[t] = 1;
+    }
 }
 
 __global__ void k_apply_rebal(const int32_t *__restrict__ P, const uint32_t *__restrict__ A,
                               const int32_t *__restrict__ S, const int32_t *__restrict__ Adm,
                               const int32_t *__restrict__ d_na, const int32_t *__restrict__ prop_tgt,
                               const int32_t *__restrict__ vwgt, int32_t *__restrict__ part,
-                              unsigned long long *__restrict__ C, int32_t subround, int32_t *__restrict__ R_node,
-                              int32_t *__restrict__ R_from, int32_t *__restrict__ R_to,
-                              int32_t *__restrict__ R_sub, int32_t *__restrict__ r_to) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *d_na) return;
-    const int32_t u = P[A[S[Adm[p]]]];
-    const int32_t a = part[u], b = prop_tgt[u];
-    const unsigned long long c = vwgt ? (unsigned long long)vwgt[u] : 1ull;
-    R_node[p] = u;
-    R_from[p] = a;
-    R_to[p] = b;
-    R_sub[p] = subround;
-    r_to[u] = b;
-    part[u] = b;
-    atomicAdd(&C[a], (unsigned long long)(-(long long)c));
-    atomicAdd(&C[b], c);
+                              unsigned long long *__restrict__ C, int32_t k, const RebalCtl *__restrict__ ctl,
+                              int32_t *__restrict__ R_node, int32_t *__restrict__ R_from,
+                              int32_t *__restrict__ R_to, int32_t *__restrict__ R_sub, int32_t *__restrict__ r_to) {
+    extern __shared__ unsigned long long s_delta[];
+    BlockDelta bd{s_delta, k};
+    bd.init();
+    const int64_t cnt = *d_na;
+    const int64_t off = ctl->nR;
+    const int32_t subround = ctl->subrounds;
+    R_node += off; R_from += off; R_to += off; R_sub += off;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < cnt; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        int32_t a = -1, b = -1;
+        long long c = 0;
+        if (p < cnt) {
+            const int32_t u = P[A[S[Adm[p]]]];
+            a = part[u];
+            b = prop_tgt[u];
+            c = vwgt ? vwgt[u] : 1;
+            R_node[p] = u;
+            R_from[p] = a;
+            R_to[p] = b;
+            R_sub[p] = subround;
+            r_to[u] = b;
+            part[u] = b;
+        }
+        bd.add(a, -c);
+        bd.add(b, c);
+    }
+    bd.flush(C);
 }
 
 inline unsigned grid1(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, 256); }
@@ -171,13 +365,15 @@ int rebalance_group(int k) {
     return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
 }
 
-void rebalance_propose(const GraphDev &g, const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
-                       int32_t *prop_gain, int32_t *flags, cudaStream_t s) {
-    if (g.n == 0) return;
+void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
+                                   const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
+                                   int32_t *prop_gain, int32_t *flags, cudaStream_t s) {
+    if (n1_max <= 0) return;
     const int G = rebalance_group(g.k);
     const int64_t groups = 256 / G;
-    const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_reb() * 16);
-#define UPR_PROP(GG) k_propose<GG><<<(unsigned)blocks, 256, 0, s>>>(part, W, g.vwgt, g.n, g.k, st, prop_tgt, prop_gain, flags)
+    const int64_t blocks = std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 16);
+#define UPR_PROP(GG) k_propose<GG><<<(unsigned)blocks, 256, 0, s>>>(list, d_n1, part, W, g.vwgt, g.k, st, prop_tgt, \
+                                                                    prop_gain, flags)
     switch (G) {
         case 4: UPR_PROP(4); break;
         case 8: UPR_PROP(8); break;
@@ -188,50 +384,114 @@ void rebalance_propose(const GraphDev &g, const int32_t *part, const int32_t *W,
     UPR_LAUNCH_CHECK();
 }
 
+void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s) {
+    if (n <= 0) return;
+    k_flag_in_blocks<<<grid1(n), 256, 0, s>>>(part, n, mark, flags);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_gather_list(const int32_t *list, const int32_t *pos, const int32_t *d_cnt, int32_t *out, int64_t cnt_max,
+                           cudaStream_t s) {
+    if (cnt_max <= 0) return;
+    k_gather_list<<<grid_for(cnt_max), 256, 0, s>>>(list, pos, d_cnt, out);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
+                            const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
+                            int32_t *prop_gain, int32_t *flags, cudaStream_t s) {
+    if (n1_max <= 0) return;
+    const int k = g.k;
+    const size_t shm = sizeof(int64_t) * (size_t)k + (size_t)k + 16;
+    if (k % 4 == 0 && k <= 256) {
+        int G = 1;
+        while (G < 32 && 4 * G < k) G <<= 1;
+        const int CH = (k + 4 * G - 1) / (4 * G);
+        const int64_t groups = 256 / G;
+        const int64_t blocks = std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 8);
+#define UPR_PV(GG, CC) k_propose_vec<GG, CC><<<(unsigned)blocks, 256, shm, s>>>(list, d_n1, part, W, g.vwgt, k, st, \
+                                                                            prop_tgt, prop_gain, flags)
+        if (CH == 1) {
+            switch (G) {
+                case 1: UPR_PV(1, 1); break;
+                case 2: UPR_PV(2, 1); break;
+                case 4: UPR_PV(4, 1); break;
+                case 8: UPR_PV(8, 1); break;
+                case 16: UPR_PV(16, 1); break;
+                default: UPR_PV(32, 1); break;
+            }
+        } else {
+            UPR_PV(32, 2);
+        }
+#undef UPR_PV
+        UPR_LAUNCH_CHECK();
+        return;
+    }
+    rebalance_propose_scalar_list(g, list, d_n1, n1_max, part, W, st, prop_tgt, prop_gain, flags, s);
+}
+
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
-                         int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np, cudaStream_t s) {
-    if (np <= 0) return;
-    k_prio_keys<<<grid1(np), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, gbits, cbits, keys, vals);
+                         int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s) {
+    if (np_max <= 0) return;
+    k_prio_keys<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, gbits, cbits, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,
-                          const int32_t *blk_of_node, uint64_t *keys, uint32_t *vals, int64_t cnt, cudaStream_t s) {
-    if (cnt <= 0) return;
-    k_block_keys<<<grid1(cnt), 256, 0, s>>>(P, A, S, d_cnt, blk_of_node, keys, vals);
+                          const int32_t *blk_of_node, uint64_t *keys, uint32_t *vals, int64_t cnt_max, cudaStream_t s) {
+    if (cnt_max <= 0) return;
+    k_block_keys<<<grid_for(cnt_max), 256, 0, s>>>(P, A, S, d_cnt, blk_of_node, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_seg_weights(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S,
                            const uint32_t *B, const uint64_t *bkeys, const int32_t *d_cnt, int64_t *c_sorted,
-                           int32_t *seg_first, int64_t cnt, cudaStream_t s) {
-    if (cnt <= 0) return;
-    k_seg_weights<<<grid1(cnt), 256, 0, s>>>(P, A, S, B, bkeys, d_cnt, g.vwgt, c_sorted, seg_first);
+                           int32_t *seg_first, int64_t cnt_max, cudaStream_t s) {
+    if (cnt_max <= 0) return;
+    k_seg_weights<<<grid_for(cnt_max), 256, 0, s>>>(P, A, S, B, bkeys, d_cnt, g.vwgt, c_sorted, seg_first);
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_mark_selected(const uint32_t *B, const uint64_t *bkeys, const int32_t *d_cnt, const int64_t *c_excl,
-                             const int32_t *seg_first, RebalState st, int32_t *sel, int64_t cnt, cudaStream_t s) {
-    if (cnt <= 0) return;
-    k_mark_selected<<<grid1(cnt), 256, 0, s>>>(B, bkeys, d_cnt, c_excl, seg_first, st, sel);
+                             const int32_t *seg_first, RebalState st, int32_t *sel, int64_t cnt_max, cudaStream_t s) {
+    if (cnt_max <= 0) return;
+    k_mark_selected<<<grid_for(cnt_max), 256, 0, s>>>(B, bkeys, d_cnt, c_excl, seg_first, st, sel);
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_mark_admitted(const uint32_t *T, const uint64_t *bkeys, const int32_t *d_cnt, const int64_t *c_sorted,
                              const int64_t *c_excl, const int32_t *seg_first, RebalState st, int32_t *adm,
-                             int8_t *reject, int64_t cnt, cudaStream_t s) {
-    if (cnt <= 0) return;
-    k_mark_admitted<<<grid1(cnt), 256, 0, s>>>(T, bkeys, d_cnt, c_sorted, c_excl, seg_first, st, adm, reject);
+                             int8_t *reject, int64_t cnt_max, cudaStream_t s) {
+    if (cnt_max <= 0) return;
+    k_mark_admitted<<<grid_for(cnt_max), 256, 0, s>>>(T, bkeys, d_cnt, c_sorted, c_excl, seg_first, st, adm, reject);
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *Adm,
-                     const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, int32_t subround,
-                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int64_t na,
+                     const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, const RebalCtl *ctl,
+                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int64_t na_max,
                      cudaStream_t s) {
-    if (na <= 0) return;
-    k_apply_rebal<<<grid1(na), 256, 0, s>>>(P, A, S, Adm, d_na, prop_tgt, g.vwgt, part, (unsigned long long *)C,
-                                            subround, R_node, R_from, R_to, R_sub, r_to);
+    if (na_max <= 0) return;
+    const int64_t blocks = std::min<int64_t>(ceil_div(na_max, 256), (int64_t)device_sm_count() * 4);
+    k_apply_rebal<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
+        P, A, S, Adm, d_na, prop_tgt, g.vwgt, part, (unsigned long long *)C, g.k, ctl, R_node, R_from, R_to, R_sub,
+        r_to);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_init(const int64_t *C, int32_t k, int64_t Lmax, int8_t *excl, RebalCtl *ctl, cudaStream_t s) {
+    k_reb_init<<<1, 256, 0, s>>>(C, k, Lmax, excl, ctl);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_begin(const int64_t *C, int32_t k, int64_t Lmax, const int8_t *excl, int8_t *over, int8_t *reject,
+                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, cudaStream_t s) {
+    k_reb_begin<<<1, 256, 0, s>>>(C, k, Lmax, excl, over, reject, d_n1, h, max_subrounds, ctl);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_end(int32_t k, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl, cudaStream_t s) {
+    k_reb_end<<<1, 256, 0, s>>>(k, excl, reject, d_na, ctl);
     UPR_LAUNCH_CHECK();
 }
 

@@ -147,26 +147,130 @@ __global__ void __launch_bounds__(256) k_select(const int32_t *__restrict__ part
     }
 }
 
+__device__ __forceinline__ int32_t int4_get(const int4 &x, int c) {
+    return c == 0 ? x.x : c == 1 ? x.y : c == 2 ? x.z : x.w;
+}
+
+// Vectorised form of k_select for k % 4 == 0, k <= 4*G*CH: lane gl of a group
+// holds blocks [4(gl + G j), 4(gl + G j) + 4) of the row in one int4 per j.
+// The per-block slack L_max - C[b] and the factors F_r (and, when they fit,
+// the bucket prefixes) are staged in shared memory; a move into a block with
+// room for it costs no penalty and needs no search.
+template <int G, int CH>
+__global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
+                                                    const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt,
+                                                    int64_t n, int32_t k, Penalty pen, int smem_pw,
+                                                    int32_t *__restrict__ cand_tgt, int64_t *__restrict__ cand_s0,
+                                                    int32_t *__restrict__ cand_gain, int32_t *__restrict__ flags) {
+    extern __shared__ int64_t s_mem[];
+    int64_t *s_slack = s_mem;
+    int64_t *s_F = s_mem + k;
+    int64_t *s_PW = s_mem + k + kSlots;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s_slack[i] = pen.Lmax - pen.C[i];
+    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) s_F[i] = pen.F[i];
+    if (smem_pw)
+        for (int i = threadIdx.x; i < k * kSlots; i += blockDim.x) s_PW[i] = pen.PW[i];
+    __syncthreads();
+    const int64_t *PW = smem_pw ? s_PW : pen.PW;
+    constexpr int kGroups = 256 / G;
+    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t v = base + gid;
+        const bool active = v < n;
+        int4 r[CH];
+        int32_t a = 0;
+        const int4 zero = make_int4(0, 0, 0, 0);
+        if (active) {
+            a = part[v];
+            const int4 *row4 = reinterpret_cast<const int4 *>(W + v * (int64_t)k);
+#pragma unroll
+            for (int j = 0; j < CH; j++) {
+                const int q = gl + G * j;
+                r[j] = 4 * q < k ? __ldcs(row4 + q) : zero;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CH; j++) r[j] = zero;
+        }
+        const int q4 = a >> 2;
+        int32_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < CH; j++)
+            if (j == q4 / G) mine = int4_get(r[j], a & 3);
+        const int32_t own = __shfl_sync(0xffffffffu, mine, gbase + (q4 % G));
+        // Only a positive score makes a candidate and the penalty is never
+        // negative, so blocks with gain <= 0 are skipped and every score kept
+        // lies in [1, 2^31).
+        int32_t best = 0;
+        int32_t bt = -1, bg = 0;
+        if (active && own < wI[v]) {
+            const int64_t c = vwgt ? vwgt[v] : 1;
+#pragma unroll
+            for (int j = 0; j < CH; j++) {
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) {
+                    const int b = 4 * (gl + G * j) + cc;
+                    const int32_t w = int4_get(r[j], cc);
+                    if (b >= k || b == a || w <= own) continue;
+                    const int32_t gain = w - own;
+                    const int64_t x = c - s_slack[b];
+                    int64_t p = 0;
+                    if (x > 0) {
+                        const int64_t *row = PW + (int64_t)b * kSlots;
+                        if (row[kSlots - 1] < x) continue;          // no slot covers the excess: forbidden
+                        int lo = 0, hi = kSlots - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (row[mid] >= x) hi = mid; else lo = mid + 1;
+                        }
+                        p = (int64_t)(((u128)(uint64_t)c * (uint64_t)s_F[lo]) >> kQ);
+                        if (p >= gain) continue;
+                    }
+                    const int32_t sc = gain - (int32_t)p;
+                    if (bt < 0 || sc > best) { best = sc; bt = b; bg = gain; }
+                }
+            }
+        }
+        int32_t sbest = best;
+        int32_t id = bt;
+        group_argmax32<G>(sbest, id);
+        const int32_t gsel = group_sum<G>((id >= 0 && bt == id) ? bg : 0);
+        if (active && gl == 0) {
+            const bool cand = id >= 0 && sbest > 0;
+            cand_tgt[v] = cand ? id : -1;
+            cand_s0[v] = cand ? sbest : 0;
+            cand_gain[v] = cand ? gsel : 0;
+            flags[v] = cand ? 1 : 0;
+        }
+    }
+}
+
+// Ascending (target, s0 descending): scores lie in [1, 2^gbits) because a
+// score never exceeds its gain, which never exceeds omega(I(v)) < 2^gbits.
 __global__ void k_cand_keys(const int32_t *__restrict__ cand_idx, const int32_t *__restrict__ d_count,
-                            const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ cand_s0,
+                            const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ cand_s0, int gbits,
                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *d_count) return;
-    const int32_t v = cand_idx[i];
-    keys[i] = ((uint64_t)cand_tgt[v] << 31) | (uint64_t)(0x7fffffffLL - cand_s0[v]);
-    vals[i] = (uint32_t)i;
+    const int64_t cnt = *d_count;
+    const uint64_t top = (1ull << gbits) - 1ull;
+    UPR_FOR(i, cnt) {
+        const int32_t v = cand_idx[i];
+        keys[i] = ((uint64_t)cand_tgt[v] << gbits) | (top - (uint64_t)cand_s0[v]);
+        vals[i] = (uint32_t)i;
+    }
 }
 
 __global__ void k_cand_gather(const int32_t *__restrict__ cand_idx, const uint32_t *__restrict__ order,
                               const int32_t *__restrict__ d_count, const int32_t *__restrict__ cand_tgt,
                               const int32_t *__restrict__ vwgt, int64_t *__restrict__ c_sorted,
                               int32_t *__restrict__ seg_first) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *d_count) return;
-    const int32_t v = cand_idx[order[j]];
-    c_sorted[j] = vwgt ? vwgt[v] : 1;
-    const int32_t t = cand_tgt[v];
-    if (j == 0 || cand_tgt[cand_idx[order[j - 1]]] != t) seg_first[t] = (int32_t)j;
+    const int64_t cnt = *d_count;
+    UPR_FOR(j, cnt) {
+        const int32_t v = cand_idx[order[j]];
+        c_sorted[j] = vwgt ? vwgt[v] : 1;
+        const int32_t t = cand_tgt[v];
+        if (j == 0 || cand_tgt[cand_idx[order[j - 1]]] != t) seg_first[t] = (int32_t)j;
+    }
 }
 
 __global__ void k_inflow(const int32_t *__restrict__ cand_idx, const uint32_t *__restrict__ order,
@@ -174,50 +278,69 @@ __global__ void k_inflow(const int32_t *__restrict__ cand_idx, const uint32_t *_
                          const int32_t *__restrict__ cand_gain, const int32_t *__restrict__ vwgt,
                          const int64_t *__restrict__ c_excl, const int32_t *__restrict__ seg_first, Penalty pen,
                          int32_t *__restrict__ keep, int64_t *__restrict__ score) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *d_count) return;
-    const uint32_t i = order[j];
-    const int32_t v = cand_idx[i];
-    const int32_t t = cand_tgt[v];
-    const int64_t c = vwgt ? vwgt[v] : 1;
-    const int64_t inflow = c_excl[j] - c_excl[seg_first[t]];
-    const int64_t p = penalty(pen, t, pen.C[t] + inflow + c - pen.Lmax, c);
-    const int64_t s = (int64_t)cand_gain[v] - p;
-    const bool kp = p >= 0 && s > 0;
-    keep[i] = kp ? 1 : 0;
-    score[i] = kp ? s : 0;
+    const int64_t cnt = *d_count;
+    UPR_FOR(j, cnt) {
+        const uint32_t i = order[j];
+        const int32_t v = cand_idx[i];
+        const int32_t t = cand_tgt[v];
+        const int64_t c = vwgt ? vwgt[v] : 1;
+        const int64_t inflow = c_excl[j] - c_excl[seg_first[t]];
+        const int64_t p = penalty(pen, t, pen.C[t] + inflow + c - pen.Lmax, c);
+        const int64_t s = (int64_t)cand_gain[v] - p;
+        const bool kp = p >= 0 && s > 0;
+        keep[i] = kp ? 1 : 0;
+        score[i] = kp ? s : 0;
+    }
 }
 
 __global__ void k_move_keys(const int32_t *__restrict__ m_idx, const int32_t *__restrict__ d_count,
-                            const int64_t *__restrict__ score, uint64_t *__restrict__ keys,
+                            const int64_t *__restrict__ score, int gbits, uint64_t *__restrict__ keys,
                             uint32_t *__restrict__ vals) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= *d_count) return;
-    keys[j] = (uint64_t)(0x7fffffffLL - score[m_idx[j]]);
-    vals[j] = (uint32_t)j;
+    const int64_t cnt = *d_count;
+    UPR_FOR(j, cnt) {
+        keys[j] = ((1ull << gbits) - 1ull) - (uint64_t)score[m_idx[j]];
+        vals[j] = (uint32_t)j;
+    }
 }
 
 __global__ void k_apply_moves(const int32_t *__restrict__ cand_idx, const int32_t *__restrict__ m_idx,
                               const uint32_t *__restrict__ order, const int32_t *__restrict__ d_count,
                               const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ score,
-                              const int32_t *__restrict__ vwgt, const int32_t *__restrict__ part0,
-                              int32_t *__restrict__ part, unsigned long long *__restrict__ C,
-                              int32_t *__restrict__ M_node, int32_t *__restrict__ M_from, int32_t *__restrict__ M_to,
-                              int64_t *__restrict__ M_score, int32_t *__restrict__ m_pos) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *d_count) return;
-    const int32_t i = m_idx[order[p]];
-    const int32_t v = cand_idx[i];
-    const int32_t a = part0[v], b = cand_tgt[v];
-    const unsigned long long c = vwgt ? (unsigned long long)vwgt[v] : 1ull;
-    M_node[p] = v;
-    M_from[p] = a;
-    M_to[p] = b;
-    M_score[p] = score[i];
-    m_pos[v] = (int32_t)p;
-    part[v] = b;
-    atomicAdd(&C[a], (unsigned long long)(-(long long)c));
-    atomicAdd(&C[b], c);
+                              const int32_t *__restrict__ vwgt, const int64_t *__restrict__ xadj,
+                              const int32_t *__restrict__ part0, int32_t *__restrict__ part,
+                              unsigned long long *__restrict__ C, int32_t k, int32_t *__restrict__ M_node,
+                              int32_t *__restrict__ M_from, int32_t *__restrict__ M_to,
+                              int64_t *__restrict__ M_score, int32_t *__restrict__ m_pos,
+                              unsigned long long *__restrict__ deg_sum) {
+    extern __shared__ unsigned long long s_delta[];
+    BlockDelta bd{s_delta, k};
+    bd.init();
+    const int64_t cnt = *d_count;
+    long long degs = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < cnt; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        int32_t a = -1, b = -1;
+        long long c = 0;
+        if (p < cnt) {
+            const int32_t i = m_idx[order[p]];
+            const int32_t v = cand_idx[i];
+            a = part0[v];
+            b = cand_tgt[v];
+            c = vwgt ? vwgt[v] : 1;
+            M_node[p] = v;
+            M_from[p] = a;
+            M_to[p] = b;
+            M_score[p] = score[i];
+            m_pos[v] = (int32_t)p;
+            part[v] = b;
+            degs += xadj[v + 1] - xadj[v];
+        }
+        bd.add(a, -c);
+        bd.add(b, c);
+    }
+    bd.flush(C);
+    degs = warp_sum(degs);
+    if ((threadIdx.x & 31) == 0 && degs) atomicAdd(deg_sum, (unsigned long long)degs);
 }
 
 }  // namespace
@@ -249,7 +372,34 @@ int select_group(int k) {
 void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Penalty pen, int32_t *cand_tgt,
                   int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s) {
     if (g.n == 0) return;
-    const int G = select_group(g.k);
+    const int k = g.k;
+    if (k % 4 == 0 && k <= 256) {
+        int G = 1;
+        while (G < 32 && 4 * G < k) G <<= 1;
+        const int CH = (k + 4 * G - 1) / (4 * G);
+        const int smem_pw = (size_t)k * kSlots * 8 <= 40 * 1024;
+        const size_t shm = sizeof(int64_t) * ((size_t)k + kSlots + (smem_pw ? (size_t)k * kSlots : 0));
+        const int64_t groups = 256 / G;
+        const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
+#define UPR_SELV(GG, CC) k_select_vec<GG, CC><<<(unsigned)blocks, 256, shm, s>>>(part, W, g.wI, g.vwgt, g.n, k, pen, \
+                                                                             smem_pw, cand_tgt, cand_s0, cand_gain, flags)
+        if (CH == 1) {
+            switch (G) {
+                case 1: UPR_SELV(1, 1); break;
+                case 2: UPR_SELV(2, 1); break;
+                case 4: UPR_SELV(4, 1); break;
+                case 8: UPR_SELV(8, 1); break;
+                case 16: UPR_SELV(16, 1); break;
+                default: UPR_SELV(32, 1); break;
+            }
+        } else {
+            UPR_SELV(32, 2);
+        }
+#undef UPR_SELV
+        UPR_LAUNCH_CHECK();
+        return;
+    }
+    const int G = select_group(k);
     const int64_t groups = 256 / G;
     const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 16);
 #define UPR_SEL(GG) k_select<GG><<<(unsigned)blocks, 256, 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, pen, cand_tgt, \
@@ -265,16 +415,17 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
 }
 
 void cand_keys(const int32_t *cand_idx, const int32_t *d_count, const int32_t *cand_tgt, const int64_t *cand_s0,
-               uint64_t *keys, uint32_t *vals, int64_t max_count, cudaStream_t s) {
+               int gbits, uint64_t *keys, uint32_t *vals, int64_t max_count, cudaStream_t s) {
     if (max_count <= 0) return;
-    k_cand_keys<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, d_count, cand_tgt, cand_s0, keys, vals);
+    k_cand_keys<<<grid_for(max_count), 256, 0, s>>>(cand_idx, d_count, cand_tgt, cand_s0, gbits, keys,
+                                                                   vals);
     UPR_LAUNCH_CHECK();
 }
 
 void cand_gather(const GraphDev &g, const int32_t *cand_idx, const uint32_t *order, const int32_t *d_count,
                  const int32_t *cand_tgt, int64_t *c_sorted, int32_t *seg_first, int64_t max_count, cudaStream_t s) {
     if (max_count <= 0) return;
-    k_cand_gather<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, order, d_count, cand_tgt, g.vwgt,
+    k_cand_gather<<<grid_for(max_count), 256, 0, s>>>(cand_idx, order, d_count, cand_tgt, g.vwgt,
                                                                      c_sorted, seg_first);
     UPR_LAUNCH_CHECK();
 }
@@ -283,26 +434,28 @@ void inflow_filter(const GraphDev &g, const int32_t *cand_idx, const uint32_t *o
                    const int32_t *cand_tgt, const int32_t *cand_gain, const int64_t *c_excl, const int32_t *seg_first,
                    Penalty pen, int32_t *keep_flag, int64_t *score, int64_t max_count, cudaStream_t s) {
     if (max_count <= 0) return;
-    k_inflow<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, order, d_count, cand_tgt, cand_gain, g.vwgt,
+    k_inflow<<<grid_for(max_count), 256, 0, s>>>(cand_idx, order, d_count, cand_tgt, cand_gain, g.vwgt,
                                                                 c_excl, seg_first, pen, keep_flag, score);
     UPR_LAUNCH_CHECK();
 }
 
-void move_keys(const int32_t *m_idx, const int32_t *d_count, const int64_t *score, uint64_t *keys, uint32_t *vals,
-               int64_t max_count, cudaStream_t s) {
+void move_keys(const int32_t *m_idx, const int32_t *d_count, const int64_t *score, int gbits, uint64_t *keys,
+               uint32_t *vals, int64_t max_count, cudaStream_t s) {
     if (max_count <= 0) return;
-    k_move_keys<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(m_idx, d_count, score, keys, vals);
+    k_move_keys<<<grid_for(max_count), 256, 0, s>>>(m_idx, d_count, score, gbits, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 
 void apply_moves(const GraphDev &g, const int32_t *cand_idx, const int32_t *m_idx, const uint32_t *order,
                  const int32_t *d_count, const int32_t *cand_tgt, const int64_t *score, const int32_t *part0,
                  int32_t *part, int64_t *C, int32_t *M_node, int32_t *M_from, int32_t *M_to, int64_t *M_score,
-                 int32_t *m_pos, int64_t max_count, cudaStream_t s) {
+                 int32_t *m_pos, int64_t *deg_sum, int64_t max_count, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(deg_sum, 0, sizeof(int64_t), s));
     if (max_count <= 0) return;
-    k_apply_moves<<<(unsigned)ceil_div(max_count, 256), 256, 0, s>>>(cand_idx, m_idx, order, d_count, cand_tgt, score,
-                                                                     g.vwgt, part0, part, (unsigned long long *)C,
-                                                                     M_node, M_from, M_to, M_score, m_pos);
+    const int64_t blocks = std::min<int64_t>(ceil_div(max_count, 256), (int64_t)device_sm_count() * 4);
+    k_apply_moves<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
+        cand_idx, m_idx, order, d_count, cand_tgt, score, g.vwgt, g.xadj, part0, part, (unsigned long long *)C, g.k,
+        M_node, M_from, M_to, M_score, m_pos, (unsigned long long *)deg_sum);
     UPR_LAUNCH_CHECK();
 }
 

@@ -13,113 +13,118 @@
 // becomes two block events (-c at its source, +c at its target); events are
 // sorted by block (stable, so M order within a block), D_b is a segmented
 // sum and the running maximum of need a segmented max-scan.
+//
+// All list lengths (|M|, |R|, |I|) are read from device memory.
 #include "kernels.h"
 
 namespace upr {
 namespace {
 
-inline unsigned grid1(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, 256); }
-
-int sm_count_seq() {
-    static int cnt = 0;
-    if (!cnt) {
-        int dev = 0;
-        UPR_CUDA(cudaGetDevice(&dev));
-        UPR_CUDA(cudaDeviceGetAttribute(&cnt, cudaDevAttrMultiProcessorCount, dev));
-    }
-    return cnt;
-}
-
 __device__ __forceinline__ int64_t cw(const int32_t *vwgt, int32_t v) { return vwgt ? (int64_t)vwgt[v] : 1; }
 
+// out = a_mul * (*a) + (b ? *b : 0) + add
+__global__ void k_count_affine(const int32_t *__restrict__ a, int32_t a_mul, const int32_t *__restrict__ b,
+                               int32_t add, int32_t *__restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = a_mul * (*a) + (b ? *b : 0) + add;
+}
+
 // keys/vals for R grouped by source block
-__global__ void k_rb_keys(const int32_t *__restrict__ R_from, int64_t nR, uint64_t *__restrict__ keys,
-                          uint32_t *__restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nR) return;
-    keys[i] = (uint64_t)R_from[i];
-    vals[i] = (uint32_t)i;
+__global__ void k_rb_keys(const int32_t *__restrict__ R_from, const int32_t *__restrict__ d_nR,
+                          uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t nR = *d_nR;
+    UPR_FOR(i, nR) {
+        keys[i] = (uint64_t)R_from[i];
+        vals[i] = (uint32_t)i;
+    }
 }
 
 // per R_b position: node weight; block bounds [rbeg[b], rend[b])
 __global__ void k_rb_bounds(const int32_t *__restrict__ R_node, const int32_t *__restrict__ R_from,
-                            const uint32_t *__restrict__ RB, int64_t nR, const int32_t *__restrict__ vwgt,
-                            int64_t *__restrict__ rc, int32_t *__restrict__ rbeg, int32_t *__restrict__ rend) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nR) return;
-    const uint32_t i = RB[q];
-    rc[q] = cw(vwgt, R_node[i]);
-    const int32_t b = R_from[i];
-    if (q == 0 || R_from[RB[q - 1]] != b) rbeg[b] = (int32_t)q;
-    if (q == nR - 1 || R_from[RB[q + 1]] != b) rend[b] = (int32_t)(q + 1);
+                            const uint32_t *__restrict__ RB, const int32_t *__restrict__ d_nR,
+                            const int32_t *__restrict__ vwgt, int64_t *__restrict__ rc, int32_t *__restrict__ rbeg,
+                            int32_t *__restrict__ rend) {
+    const int64_t nR = *d_nR;
+    UPR_FOR(q, nR) {
+        const uint32_t i = RB[q];
+        rc[q] = cw(vwgt, R_node[i]);
+        const int32_t b = R_from[i];
+        if (q == 0 || R_from[RB[q - 1]] != b) rbeg[b] = (int32_t)q;
+        if (q == nR - 1 || R_from[RB[q + 1]] != b) rend[b] = (int32_t)(q + 1);
+    }
 }
 
 // events of M: 2i = leave M_from[i], 2i+1 = enter M_to[i]
-__global__ void k_ev_keys(const int32_t *__restrict__ M_from, const int32_t *__restrict__ M_to, int64_t nM,
-                          uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * nM) return;
-    const int64_t i = e >> 1;
-    keys[e] = (uint64_t)((e & 1) ? M_to[i] : M_from[i]);
-    vals[e] = (uint32_t)e;
+__global__ void k_ev_keys(const int32_t *__restrict__ M_from, const int32_t *__restrict__ M_to,
+                          const int32_t *__restrict__ d_nM, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t nev = 2 * (int64_t)*d_nM;
+    UPR_FOR(e, nev) {
+        const int64_t i = e >> 1;
+        keys[e] = (uint64_t)((e & 1) ? M_to[i] : M_from[i]);
+        vals[e] = (uint32_t)e;
+    }
 }
 
 __global__ void k_ev_delta(const int32_t *__restrict__ M_node, const uint32_t *__restrict__ EV,
-                           const uint64_t *__restrict__ ekeys, int64_t nev, const int32_t *__restrict__ vwgt,
-                           int64_t *__restrict__ delta, int32_t *__restrict__ ebeg, int32_t *__restrict__ eend) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nev) return;
-    const uint32_t e = EV[q];
-    const int64_t c = cw(vwgt, M_node[e >> 1]);
-    delta[q] = (e & 1) ? c : -c;
-    const int32_t b = (int32_t)ekeys[q];
-    if (q == 0 || (int32_t)ekeys[q - 1] != b) ebeg[b] = (int32_t)q;
-    if (q == nev - 1 || (int32_t)ekeys[q + 1] != b) eend[b] = (int32_t)(q + 1);
+                           const uint64_t *__restrict__ ekeys, const int32_t *__restrict__ d_nM,
+                           const int32_t *__restrict__ vwgt, int64_t *__restrict__ delta, int32_t *__restrict__ ebeg,
+                           int32_t *__restrict__ eend) {
+    const int64_t nev = 2 * (int64_t)*d_nM;
+    UPR_FOR(q, nev) {
+        const uint32_t e = EV[q];
+        const int64_t c = cw(vwgt, M_node[e >> 1]);
+        delta[q] = (e & 1) ? c : -c;
+        const int32_t b = (int32_t)ekeys[q];
+        if (q == 0 || (int32_t)ekeys[q - 1] != b) ebeg[b] = (int32_t)q;
+        if (q == nev - 1 || (int32_t)ekeys[q + 1] != b) eend[b] = (int32_t)(q + 1);
+    }
 }
 
 // need(q) for inflow events into blocks with R_b non-empty; packed with the block for the max-scan
-__global__ void k_ev_need(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys, int64_t nev,
-                          const int64_t *__restrict__ delta, const int64_t *__restrict__ d_excl,
-                          const int32_t *__restrict__ ebeg, const int64_t *__restrict__ C0, int64_t Lmax,
-                          const int32_t *__restrict__ rbeg, const int32_t *__restrict__ rend,
-                          const int64_t *__restrict__ rc_excl, const int64_t *__restrict__ rc,
-                          uint64_t *__restrict__ packed) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nev) return;
-    const uint32_t e = EV[q];
-    const int32_t b = (int32_t)ekeys[q];
-    uint32_t need = 0;
-    const int32_t r0 = rbeg[b], r1 = rend[b];
-    if ((e & 1) && r1 > r0) {
-        const int64_t D = C0[b] + (d_excl[q] + delta[q]) - d_excl[ebeg[b]];
-        if (D > Lmax) {
-            // smallest x in [1, |R_b|] with D - (weight of R_b[0..x)) <= L_max, else |R_b|
-            const int64_t base = rc_excl[r0];
-            int lo = 1, hi = r1 - r0;
-            while (lo < hi) {
-                int mid = lo + ((hi - lo) >> 1);
-                int64_t w = rc_excl[r0 + mid - 1] + rc[r0 + mid - 1] - base;
-                if (D - w <= Lmax) hi = mid; else lo = mid + 1;
+__global__ void k_ev_need(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys,
+                          const int32_t *__restrict__ d_nM, const int64_t *__restrict__ delta,
+                          const int64_t *__restrict__ d_excl, const int32_t *__restrict__ ebeg,
+                          const int64_t *__restrict__ C0, int64_t Lmax, const int32_t *__restrict__ rbeg,
+                          const int32_t *__restrict__ rend, const int64_t *__restrict__ rc_excl,
+                          const int64_t *__restrict__ rc, uint64_t *__restrict__ packed) {
+    const int64_t nev = 2 * (int64_t)*d_nM;
+    UPR_FOR(q, nev) {
+        const uint32_t e = EV[q];
+        const int32_t b = (int32_t)ekeys[q];
+        uint32_t need = 0;
+        const int32_t r0 = rbeg[b], r1 = rend[b];
+        if ((e & 1) && r1 > r0) {
+            const int64_t D = C0[b] + (d_excl[q] + delta[q]) - d_excl[ebeg[b]];
+            if (D > Lmax) {
+                // smallest x in [1, |R_b|] with D - (weight of R_b[0..x)) <= L_max, else |R_b|
+                const int64_t base = rc_excl[r0];
+                int lo = 1, hi = r1 - r0;
+                while (lo < hi) {
+                    const int mid = lo + ((hi - lo) >> 1);
+                    const int64_t w = rc_excl[r0 + mid - 1] + rc[r0 + mid - 1] - base;
+                    if (D - w <= Lmax) hi = mid; else lo = mid + 1;
+                }
+                need = (uint32_t)lo;
             }
-            need = (uint32_t)lo;
         }
+        packed[q] = ((uint64_t)(uint32_t)b << 32) | need;
     }
-    packed[q] = ((uint64_t)(uint32_t)b << 32) | need;
 }
 
 // per M move: emissions after it (e_i) and the R_b count before them
-__global__ void k_ev_emit(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys, int64_t nev,
-                          const uint64_t *__restrict__ qmax, const int32_t *__restrict__ ebeg,
-                          int32_t *__restrict__ emit, int32_t *__restrict__ qbefore_m) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nev) return;
-    const uint32_t e = EV[q];
-    if (!(e & 1)) return;
-    const int32_t b = (int32_t)ekeys[q];
-    const uint32_t after = (uint32_t)qmax[q];
-    const uint32_t before = q == ebeg[b] ? 0u : (uint32_t)qmax[q - 1];
-    emit[e >> 1] = (int32_t)(after - before);
-    qbefore_m[e >> 1] = (int32_t)before;
+__global__ void k_ev_emit(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys,
+                          const int32_t *__restrict__ d_nM, const uint64_t *__restrict__ qmax,
+                          const int32_t *__restrict__ ebeg, int32_t *__restrict__ emit,
+                          int32_t *__restrict__ qbefore_m) {
+    const int64_t nev = 2 * (int64_t)*d_nM;
+    UPR_FOR(q, nev) {
+        const uint32_t e = EV[q];
+        if (!(e & 1)) continue;
+        const int32_t b = (int32_t)ekeys[q];
+        const uint32_t after = (uint32_t)qmax[q];
+        const uint32_t before = q == ebeg[b] ? 0u : (uint32_t)qmax[q - 1];
+        emit[e >> 1] = (int32_t)(after - before);
+        qbefore_m[e >> 1] = (int32_t)before;
+    }
 }
 
 // per block: final emitted count and leftover count
@@ -136,72 +141,78 @@ __global__ void k_block_final(int32_t k, const int32_t *__restrict__ ebeg, const
 
 // positions of M moves in X
 __global__ void k_place_m(const int32_t *__restrict__ M_node, const int32_t *__restrict__ M_from,
-                          const int32_t *__restrict__ M_to, int64_t nM, const int32_t *__restrict__ em_excl,
-                          int32_t *__restrict__ pos_m, int32_t *__restrict__ X_node, int32_t *__restrict__ X_from,
-                          int32_t *__restrict__ X_to, int8_t *__restrict__ X_isr) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nM) return;
-    const int32_t p = (int32_t)i + em_excl[i];
-    pos_m[i] = p;
-    X_node[p] = M_node[i];
-    X_from[p] = M_from[i];
-    X_to[p] = M_to[i];
-    X_isr[p] = 0;
+                          const int32_t *__restrict__ M_to, const int32_t *__restrict__ d_nM,
+                          const int32_t *__restrict__ em_excl, int32_t *__restrict__ pos_m,
+                          int32_t *__restrict__ X_node, int32_t *__restrict__ X_from, int32_t *__restrict__ X_to,
+                          int8_t *__restrict__ X_isr) {
+    const int64_t nM = *d_nM;
+    UPR_FOR(i, nM) {
+        const int32_t p = (int32_t)i + em_excl[i];
+        pos_m[i] = p;
+        X_node[p] = M_node[i];
+        X_from[p] = M_from[i];
+        X_to[p] = M_to[i];
+        X_isr[p] = 0;
+    }
 }
 
 // positions of R moves in X
 __global__ void k_place_r(const int32_t *__restrict__ R_node, const int32_t *__restrict__ R_from,
-                          const int32_t *__restrict__ R_to, const uint32_t *__restrict__ RB, int64_t nR,
-                          const int32_t *__restrict__ rbeg, const uint32_t *__restrict__ EV,
-                          const int32_t *__restrict__ ebeg, const int32_t *__restrict__ eend,
-                          const uint64_t *__restrict__ qmax, const int32_t *__restrict__ pos_m,
-                          const int32_t *__restrict__ qfin, const int32_t *__restrict__ left_excl,
-                          const int32_t *__restrict__ em_excl, const int32_t *__restrict__ emit, int64_t nM,
+                          const int32_t *__restrict__ R_to, const uint32_t *__restrict__ RB,
+                          const int32_t *__restrict__ d_nR, const int32_t *__restrict__ rbeg,
+                          const uint32_t *__restrict__ EV, const int32_t *__restrict__ ebeg,
+                          const int32_t *__restrict__ eend, const uint64_t *__restrict__ qmax,
+                          const int32_t *__restrict__ pos_m, const int32_t *__restrict__ qfin,
+                          const int32_t *__restrict__ left_excl, const int32_t *__restrict__ em_excl,
+                          const int32_t *__restrict__ emit, const int32_t *__restrict__ d_nM,
                           int32_t *__restrict__ X_node, int32_t *__restrict__ X_from, int32_t *__restrict__ X_to,
                           int8_t *__restrict__ X_isr) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nR) return;
-    const uint32_t i = RB[q];
-    const int32_t b = R_from[i];
-    const uint32_t r = (uint32_t)(q - rbeg[b]);
-    int64_t p;
-    if ((int32_t)r < qfin[b]) {
-        // first event of b with running max > r (an inflow event)
-        int lo = ebeg[b], hi = eend[b] - 1;
-        while (lo < hi) {
-            int mid = lo + ((hi - lo) >> 1);
-            if ((uint32_t)qmax[mid] > r) hi = mid; else lo = mid + 1;
+    const int64_t nR = *d_nR, nM = *d_nM;
+    const int64_t tail0 = nM + (nM > 0 ? (int64_t)em_excl[nM - 1] + emit[nM - 1] : 0);
+    UPR_FOR(q, nR) {
+        const uint32_t i = RB[q];
+        const int32_t b = R_from[i];
+        const uint32_t r = (uint32_t)(q - rbeg[b]);
+        int64_t p;
+        if ((int32_t)r < qfin[b]) {
+            // first event of b with running max > r (an inflow event)
+            int lo = ebeg[b], hi = eend[b] - 1;
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if ((uint32_t)qmax[mid] > r) hi = mid; else lo = mid + 1;
+            }
+            const uint32_t before = lo == ebeg[b] ? 0u : (uint32_t)qmax[lo - 1];
+            p = (int64_t)pos_m[EV[lo] >> 1] + 1 + (r - before);
+        } else {
+            p = tail0 + left_excl[b] + (r - (uint32_t)qfin[b]);
         }
-        const uint32_t before = lo == ebeg[b] ? 0u : (uint32_t)qmax[lo - 1];
-        p = (int64_t)pos_m[EV[lo] >> 1] + 1 + (r - before);
-    } else {
-        const int64_t tail0 = nM + (nM > 0 ? (int64_t)em_excl[nM - 1] + emit[nM - 1] : 0);
-        p = tail0 + left_excl[b] + (r - (uint32_t)qfin[b]);
+        X_node[p] = R_node[i];
+        X_from[p] = R_from[i];
+        X_to[p] = R_to[i];
+        X_isr[p] = 1;
     }
-    X_node[p] = R_node[i];
-    X_from[p] = R_from[i];
-    X_to[p] = R_to[i];
-    X_isr[p] = 1;
 }
 
 // merging: an R move of a node that also has an M move folds into the M move
 __global__ void k_merge_flags(const int32_t *__restrict__ X_node, const int32_t *__restrict__ X_to,
-                              const int8_t *__restrict__ X_isr, int64_t nX, const int32_t *__restrict__ m_pos,
-                              const int32_t *__restrict__ r_to, const int32_t *__restrict__ part0,
-                              int32_t *__restrict__ keep, int32_t *__restrict__ final_to) {
-    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nX) return;
-    const int32_t v = X_node[x];
-    int32_t to = X_to[x];
-    bool k = true;
-    if (X_isr[x]) {
-        if (m_pos[v] >= 0) k = false;
-    } else if (r_to[v] >= 0) {
-        to = r_to[v];
+                              const int8_t *__restrict__ X_isr, const int32_t *__restrict__ d_nX,
+                              const int32_t *__restrict__ m_pos, const int32_t *__restrict__ r_to,
+                              const int32_t *__restrict__ part0, int32_t *__restrict__ keep,
+                              int32_t *__restrict__ final_to) {
+    const int64_t nX = *d_nX;
+    UPR_FOR(x, nX) {
+        const int32_t v = X_node[x];
+        int32_t to = X_to[x];
+        bool k = true;
+        if (X_isr[x]) {
+            if (m_pos[v] >= 0) k = false;
+        } else if (r_to[v] >= 0) {
+            to = r_to[v];
+        }
+        if (k && to == part0[v]) k = false;
+        keep[x] = k ? 1 : 0;
+        final_to[x] = to;
     }
-    if (k && to == part0[v]) k = false;
-    keep[x] = k ? 1 : 0;
-    final_to[x] = to;
 }
 
 __global__ void k_build_I(const int32_t *__restrict__ Ix, const int32_t *__restrict__ d_nI,
@@ -209,15 +220,16 @@ __global__ void k_build_I(const int32_t *__restrict__ Ix, const int32_t *__restr
                           const int32_t *__restrict__ part0, int32_t *__restrict__ I_node,
                           int32_t *__restrict__ I_from, int32_t *__restrict__ I_to, int32_t *__restrict__ pos,
                           int32_t *__restrict__ dest) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *d_nI) return;
-    const int32_t x = Ix[i];
-    const int32_t v = X_node[x];
-    I_node[i] = v;
-    I_from[i] = part0[v];
-    I_to[i] = final_to[x];
-    pos[v] = (int32_t)i;
-    dest[v] = final_to[x];
+    const int64_t nI = *d_nI;
+    UPR_FOR(i, nI) {
+        const int32_t x = Ix[i];
+        const int32_t v = X_node[x];
+        I_node[i] = v;
+        I_from[i] = part0[v];
+        I_to[i] = final_to[x];
+        pos[v] = (int32_t)i;
+        dest[v] = final_to[x];
+    }
 }
 
 // Exact gain of the i-th move of I: neighbours moved earlier in I count in
@@ -225,11 +237,12 @@ __global__ void k_build_I(const int32_t *__restrict__ Ix, const int32_t *__restr
 // hub moves (degree > kHubDegree) are left to k_gains_hub.
 __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                              const int32_t *__restrict__ adjw, const int32_t *__restrict__ I_node,
-                             const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to, int64_t nI,
-                             const int32_t *__restrict__ pos, const int32_t *__restrict__ dest,
-                             const int32_t *__restrict__ part0, int64_t *__restrict__ gain,
-                             int32_t *__restrict__ hub_flag) {
+                             const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to,
+                             const int32_t *__restrict__ d_nI, const int32_t *__restrict__ pos,
+                             const int32_t *__restrict__ dest, const int32_t *__restrict__ part0,
+                             int64_t *__restrict__ gain, int32_t *__restrict__ hub_flag) {
     const int lane = threadIdx.x & 31;
+    const int64_t nI = *d_nI;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nI;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t v = I_node[i], a = I_from[i], b = I_to[i];
@@ -280,39 +293,56 @@ __global__ void __launch_bounds__(512) k_gains_hub(const int64_t *__restrict__ x
 }
 
 // block events of I for the weight trajectory: 2i = leave I_from[i], 2i+1 = enter I_to[i]
-__global__ void k_iev_keys(const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to, int64_t nI,
-                           uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 2 * nI) return;
-    const int64_t i = e >> 1;
-    keys[e] = (uint64_t)((e & 1) ? I_to[i] : I_from[i]);
-    vals[e] = (uint32_t)e;
+__global__ void k_iev_keys(const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to,
+                           const int32_t *__restrict__ d_nI, uint64_t *__restrict__ keys,
+                           uint32_t *__restrict__ vals) {
+    const int64_t nev = 2 * (int64_t)*d_nI;
+    UPR_FOR(e, nev) {
+        const int64_t i = e >> 1;
+        keys[e] = (uint64_t)((e & 1) ? I_to[i] : I_from[i]);
+        vals[e] = (uint32_t)e;
+    }
 }
 
 __global__ void k_iev_delta(const int32_t *__restrict__ I_node, const uint32_t *__restrict__ EV,
-                            const uint64_t *__restrict__ ekeys, int64_t nev, const int32_t *__restrict__ vwgt,
-                            int64_t *__restrict__ delta, int32_t *__restrict__ ebeg) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nev) return;
-    const uint32_t e = EV[q];
-    const int64_t c = cw(vwgt, I_node[e >> 1]);
-    delta[q] = (e & 1) ? c : -c;
-    const int32_t b = (int32_t)ekeys[q];
-    if (q == 0 || (int32_t)ekeys[q - 1] != b) ebeg[b] = (int32_t)q;
+                            const uint64_t *__restrict__ ekeys, const int32_t *__restrict__ d_nI,
+                            const int32_t *__restrict__ vwgt, int64_t *__restrict__ delta,
+                            int32_t *__restrict__ ebeg) {
+    const int64_t nev = 2 * (int64_t)*d_nI;
+    UPR_FOR(q, nev) {
+        const uint32_t e = EV[q];
+        const int64_t c = cw(vwgt, I_node[e >> 1]);
+        delta[q] = (e & 1) ? c : -c;
+        const int32_t b = (int32_t)ekeys[q];
+        if (q == 0 || (int32_t)ekeys[q - 1] != b) ebeg[b] = (int32_t)q;
+    }
 }
 
 // Changes of the number of overloaded blocks, at prefix length j = i + 1.
-__global__ void k_iev_transitions(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys, int64_t nev,
-                                  const int64_t *__restrict__ delta, const int64_t *__restrict__ d_excl,
-                                  const int32_t *__restrict__ ebeg, const int64_t *__restrict__ C0, int64_t Lmax,
-                                  int32_t *__restrict__ diff) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nev) return;
-    const int32_t b = (int32_t)ekeys[q];
-    const int64_t before = C0[b] + d_excl[q] - d_excl[ebeg[b]];
-    const int64_t after = before + delta[q];
-    const int t = (after > Lmax ? 1 : 0) - (before > Lmax ? 1 : 0);
-    if (t) atomicAdd(&diff[(EV[q] >> 1) + 1], t);
+__global__ void k_iev_transitions(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys,
+                                  const int32_t *__restrict__ d_nI, const int64_t *__restrict__ delta,
+                                  const int64_t *__restrict__ d_excl, const int32_t *__restrict__ ebeg,
+                                  const int64_t *__restrict__ C0, int64_t Lmax, int32_t *__restrict__ diff) {
+    const int64_t nev = 2 * (int64_t)*d_nI;
+    UPR_FOR(q, nev) {
+        const int32_t b = (int32_t)ekeys[q];
+        const int64_t before = C0[b] + d_excl[q] - d_excl[ebeg[b]];
+        const int64_t after = before + delta[q];
+        const int t = (after > Lmax ? 1 : 0) - (before > Lmax ? 1 : 0);
+        if (t) atomicAdd(&diff[(EV[q] >> 1) + 1], t);
+    }
+}
+
+// number of blocks above L_max
+__global__ void k_count_over(const int64_t *__restrict__ C, int32_t k, int64_t Lmax, int32_t *__restrict__ out) {
+    __shared__ int s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    int c = 0;
+    for (int b = threadIdx.x; b < k; b += blockDim.x) c += C[b] > Lmax;
+    if (c) atomicAdd(&s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = s;
 }
 
 // best prefix: max G(j) over eligible j (ties: smallest j); G(0) = 0, eligible(0) = (over0 == 0)
@@ -326,12 +356,15 @@ __device__ __forceinline__ Best better(Best x, Best y) {
 }
 
 __global__ void k_best_partial(const int64_t *__restrict__ Gsum, const int32_t *__restrict__ diff,
-                               const int32_t *__restrict__ diff_excl, int64_t nI, int32_t over0,
-                               long long *__restrict__ part_g, long long *__restrict__ part_j) {
+                               const int32_t *__restrict__ diff_excl, const int32_t *__restrict__ d_nI,
+                               const int32_t *__restrict__ d_over0, long long *__restrict__ part_g,
+                               long long *__restrict__ part_j) {
     __shared__ long long s_g[8], s_j[8];
+    const int64_t nI = *d_nI;
+    const int32_t over0 = *d_over0;
     Best b{0, -1};
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= nI; j += (int64_t)gridDim.x * blockDim.x) {
-        bool elig = over0 + diff_excl[j] + diff[j] == 0;
+        const bool elig = over0 + diff_excl[j] + diff[j] == 0;
         if (elig) b = better(b, Best{j == 0 ? 0 : Gsum[j - 1], j});
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -348,186 +381,220 @@ __global__ void k_best_partial(const int64_t *__restrict__ Gsum, const int32_t *
     }
 }
 
-__global__ void k_best_final(const long long *__restrict__ part_g, const long long *__restrict__ part_j, int parts,
-                             long long *__restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    Best t{0, -1};
-    for (int p = 0; p < parts; p++) t = better(t, Best{part_g[p], part_j[p]});
-    out[0] = t.g;
-    out[1] = t.j;
+__global__ void __launch_bounds__(1024) k_best_final(const long long *__restrict__ part_g,
+                                                    const long long *__restrict__ part_j, int parts,
+                                                    long long *__restrict__ out, int32_t *__restrict__ infeasible) {
+    __shared__ long long s_g[32], s_j[32];
+    Best b{0, -1};
+    for (int p = threadIdx.x; p < parts; p += blockDim.x) b = better(b, Best{part_g[p], part_j[p]});
+    for (int o = 16; o > 0; o >>= 1) {
+        Best y{__shfl_xor_sync(0xffffffffu, b.g, o), __shfl_xor_sync(0xffffffffu, b.j, o)};
+        b = better(b, y);
+    }
+    if ((threadIdx.x & 31) == 0) { s_g[threadIdx.x >> 5] = b.g; s_j[threadIdx.x >> 5] = b.j; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Best t{0, -1};
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = better(t, Best{s_g[w], s_j[w]});
+        out[0] = t.g;
+        out[1] = t.j;
+        if (t.j < 0) *infeasible = 1;
+    }
 }
 
 __global__ void k_apply_prefix(const int32_t *__restrict__ I_node, const int32_t *__restrict__ I_from,
                                const int32_t *__restrict__ I_to, const long long *__restrict__ best,
                                const int32_t *__restrict__ vwgt, int32_t *__restrict__ part0,
-                               unsigned long long *__restrict__ C0, long long *__restrict__ cut) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                               unsigned long long *__restrict__ C0, int32_t k, long long *__restrict__ cut) {
+    extern __shared__ unsigned long long s_delta[];
+    BlockDelta bd{s_delta, k};
+    bd.init();
     const long long len = best[1];
-    if (j == 0 && len >= 0) atomicAdd((unsigned long long *)cut, (unsigned long long)(-best[0]));
-    if (len < 0 || j >= len) return;
-    const int32_t v = I_node[j];
-    const unsigned long long c = vwgt ? (unsigned long long)vwgt[v] : 1ull;
-    part0[v] = I_to[j];
-    atomicAdd(&C0[I_from[j]], (unsigned long long)(-(long long)c));
-    atomicAdd(&C0[I_to[j]], c);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && len >= 0) atomicAdd((unsigned long long *)cut, (unsigned long long)(-best[0]));
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < len; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = base + threadIdx.x;
+        int32_t a = -1, b = -1;
+        long long c = 0;
+        if (j < len) {
+            const int32_t v = I_node[j];
+            a = I_from[j];
+            b = I_to[j];
+            c = vwgt ? vwgt[v] : 1;
+            part0[v] = b;
+        }
+        bd.add(a, -c);
+        bd.add(b, c);
+    }
+    bd.flush(C0);
 }
 
-__global__ void k_reset_nodes(const int32_t *__restrict__ nodes, int64_t cnt, int32_t *__restrict__ arr, int32_t val) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < cnt) arr[nodes[i]] = val;
+__global__ void k_reset_nodes(const int32_t *__restrict__ nodes, const int32_t *__restrict__ d_cnt,
+                              int32_t *__restrict__ arr, int32_t val) {
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(i, cnt) arr[nodes[i]] = val;
 }
 
 __global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = v;
+    UPR_FOR(i, n) a[i] = v;
+}
+
+// a[0 .. *d_n + extra) = 0
+__global__ void k_clear_count(int32_t *a, const int32_t *__restrict__ d_n, int32_t extra) {
+    const int64_t n = (int64_t)*d_n + extra;
+    UPR_FOR(i, n) a[i] = 0;
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- wrappers
+void count_affine(const int32_t *a, int32_t a_mul, const int32_t *b, int32_t add, int32_t *out, cudaStream_t s) {
+    k_count_affine<<<1, 32, 0, s>>>(a, a_mul, b, add, out);
+    UPR_LAUNCH_CHECK();
+}
+
 void fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t s) {
     if (n <= 0) return;
-    k_fill_i32<<<grid1(n), 256, 0, s>>>(a, n, v);
+    k_fill_i32<<<grid_for(n), 256, 0, s>>>(a, n, v);
     UPR_LAUNCH_CHECK();
 }
 
-void reset_nodes(const int32_t *nodes, int64_t cnt, int32_t *arr, int32_t val, cudaStream_t s) {
-    if (cnt <= 0) return;
-    k_reset_nodes<<<grid1(cnt), 256, 0, s>>>(nodes, cnt, arr, val);
+void clear_count(int32_t *a, const int32_t *d_n, int32_t extra, int64_t max, cudaStream_t s) {
+    k_clear_count<<<grid_for(max + extra), 256, 0, s>>>(a, d_n, extra);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_rb_keys(const int32_t *R_from, int64_t nR, uint64_t *keys, uint32_t *vals, cudaStream_t s) {
-    if (nR <= 0) return;
-    k_rb_keys<<<grid1(nR), 256, 0, s>>>(R_from, nR, keys, vals);
+void reset_nodes(const int32_t *nodes, const int32_t *d_cnt, int64_t max, int32_t *arr, int32_t val, cudaStream_t s) {
+    if (max <= 0) return;
+    k_reset_nodes<<<grid_for(max), 256, 0, s>>>(nodes, d_cnt, arr, val);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_rb_bounds(const int32_t *R_node, const int32_t *R_from, const uint32_t *RB, int64_t nR, const int32_t *vwgt,
-                   int64_t *rc, int32_t *rbeg, int32_t *rend, cudaStream_t s) {
-    if (nR <= 0) return;
-    k_rb_bounds<<<grid1(nR), 256, 0, s>>>(R_node, R_from, RB, nR, vwgt, rc, rbeg, rend);
+void count_over(const int64_t *C, int32_t k, int64_t Lmax, int32_t *out, cudaStream_t s) {
+    k_count_over<<<1, 256, 0, s>>>(C, k, Lmax, out);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_ev_keys(const int32_t *M_from, const int32_t *M_to, int64_t nM, uint64_t *keys, uint32_t *vals,
+void seq_rb_keys(const int32_t *R_from, const int32_t *d_nR, int64_t max, uint64_t *keys, uint32_t *vals,
                  cudaStream_t s) {
-    if (nM <= 0) return;
-    k_ev_keys<<<grid1(2 * nM), 256, 0, s>>>(M_from, M_to, nM, keys, vals);
+    k_rb_keys<<<grid_for(max), 256, 0, s>>>(R_from, d_nR, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_ev_delta(const int32_t *M_node, const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int32_t *vwgt,
-                  int64_t *delta, int32_t *ebeg, int32_t *eend, cudaStream_t s) {
-    if (nev <= 0) return;
-    k_ev_delta<<<grid1(nev), 256, 0, s>>>(M_node, EV, ekeys, nev, vwgt, delta, ebeg, eend);
+void seq_rb_bounds(const int32_t *R_node, const int32_t *R_from, const uint32_t *RB, const int32_t *d_nR, int64_t max,
+                   const int32_t *vwgt, int64_t *rc, int32_t *rbeg, int32_t *rend, cudaStream_t s) {
+    k_rb_bounds<<<grid_for(max), 256, 0, s>>>(R_node, R_from, RB, d_nR, vwgt, rc, rbeg, rend);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_ev_need(const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int64_t *delta, const int64_t *d_excl,
-                 const int32_t *ebeg, const int64_t *C0, int64_t Lmax, const int32_t *rbeg, const int32_t *rend,
-                 const int64_t *rc_excl, const int64_t *rc, uint64_t *packed, cudaStream_t s) {
-    if (nev <= 0) return;
-    k_ev_need<<<grid1(nev), 256, 0, s>>>(EV, ekeys, nev, delta, d_excl, ebeg, C0, Lmax, rbeg, rend, rc_excl, rc,
-                                         packed);
+void seq_ev_keys(const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM, int64_t max, uint64_t *keys,
+                 uint32_t *vals, cudaStream_t s) {
+    k_ev_keys<<<grid_for(2 * max), 256, 0, s>>>(M_from, M_to, d_nM, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_ev_emit(const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const uint64_t *qmax, const int32_t *ebeg,
-                 int32_t *emit, int32_t *qbefore_m, cudaStream_t s) {
-    if (nev <= 0) return;
-    k_ev_emit<<<grid1(nev), 256, 0, s>>>(EV, ekeys, nev, qmax, ebeg, emit, qbefore_m);
+void seq_ev_delta(const int32_t *M_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max,
+                  const int32_t *vwgt, int64_t *delta, int32_t *ebeg, int32_t *eend, cudaStream_t s) {
+    k_ev_delta<<<grid_for(2 * max), 256, 0, s>>>(M_node, EV, ekeys, d_nM, vwgt, delta, ebeg, eend);
+    UPR_LAUNCH_CHECK();
+}
+
+void seq_ev_need(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const int64_t *delta,
+                 const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, int64_t Lmax, const int32_t *rbeg,
+                 const int32_t *rend, const int64_t *rc_excl, const int64_t *rc, uint64_t *packed, cudaStream_t s) {
+    k_ev_need<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nM, delta, d_excl, ebeg, C0, Lmax, rbeg, rend, rc_excl,
+                                                rc, packed);
+    UPR_LAUNCH_CHECK();
+}
+
+void seq_ev_emit(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const uint64_t *qmax,
+                 const int32_t *ebeg, int32_t *emit, int32_t *qbefore_m, cudaStream_t s) {
+    k_ev_emit<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nM, qmax, ebeg, emit, qbefore_m);
     UPR_LAUNCH_CHECK();
 }
 
 void seq_block_final(int32_t k, const int32_t *ebeg, const int32_t *eend, const uint64_t *qmax, const int32_t *rbeg,
                      const int32_t *rend, int32_t *qfin, int32_t *left, cudaStream_t s) {
-    k_block_final<<<grid1(k), 256, 0, s>>>(k, ebeg, eend, qmax, rbeg, rend, qfin, left);
+    k_block_final<<<(unsigned)ceil_div(k, 256), 256, 0, s>>>(k, ebeg, eend, qmax, rbeg, rend, qfin, left);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_place_m(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, int64_t nM, const int32_t *em_excl,
-                 int32_t *pos_m, int32_t *X_node, int32_t *X_from, int32_t *X_to, int8_t *X_isr, cudaStream_t s) {
-    if (nM <= 0) return;
-    k_place_m<<<grid1(nM), 256, 0, s>>>(M_node, M_from, M_to, nM, em_excl, pos_m, X_node, X_from, X_to, X_isr);
+void seq_place_m(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM, int64_t max,
+                 const int32_t *em_excl, int32_t *pos_m, int32_t *X_node, int32_t *X_from, int32_t *X_to,
+                 int8_t *X_isr, cudaStream_t s) {
+    k_place_m<<<grid_for(max), 256, 0, s>>>(M_node, M_from, M_to, d_nM, em_excl, pos_m, X_node, X_from, X_to, X_isr);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_place_r(const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const uint32_t *RB, int64_t nR,
-                 const int32_t *rbeg, const uint32_t *EV, const int32_t *ebeg, const int32_t *eend,
-                 const uint64_t *qmax, const int32_t *pos_m, const int32_t *qfin, const int32_t *left_excl,
-                 const int32_t *em_excl, const int32_t *emit, int64_t nM, int32_t *X_node, int32_t *X_from,
-                 int32_t *X_to, int8_t *X_isr, cudaStream_t s) {
-    if (nR <= 0) return;
-    k_place_r<<<grid1(nR), 256, 0, s>>>(R_node, R_from, R_to, RB, nR, rbeg, EV, ebeg, eend, qmax, pos_m, qfin,
-                                        left_excl, em_excl, emit, nM, X_node, X_from, X_to, X_isr);
+void seq_place_r(const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const uint32_t *RB,
+                 const int32_t *d_nR, int64_t max, const int32_t *rbeg, const uint32_t *EV, const int32_t *ebeg,
+                 const int32_t *eend, const uint64_t *qmax, const int32_t *pos_m, const int32_t *qfin,
+                 const int32_t *left_excl, const int32_t *em_excl, const int32_t *emit, const int32_t *d_nM,
+                 int32_t *X_node, int32_t *X_from, int32_t *X_to, int8_t *X_isr, cudaStream_t s) {
+    k_place_r<<<grid_for(max), 256, 0, s>>>(R_node, R_from, R_to, RB, d_nR, rbeg, EV, ebeg, eend, qmax, pos_m, qfin,
+                                            left_excl, em_excl, emit, d_nM, X_node, X_from, X_to, X_isr);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_merge_flags(const int32_t *X_node, const int32_t *X_to, const int8_t *X_isr, int64_t nX, const int32_t *m_pos,
-                     const int32_t *r_to, const int32_t *part0, int32_t *keep, int32_t *final_to, cudaStream_t s) {
-    if (nX <= 0) return;
-    k_merge_flags<<<grid1(nX), 256, 0, s>>>(X_node, X_to, X_isr, nX, m_pos, r_to, part0, keep, final_to);
+void seq_merge_flags(const int32_t *X_node, const int32_t *X_to, const int8_t *X_isr, const int32_t *d_nX, int64_t max,
+                     const int32_t *m_pos, const int32_t *r_to, const int32_t *part0, int32_t *keep, int32_t *final_to,
+                     cudaStream_t s) {
+    k_merge_flags<<<grid_for(max), 256, 0, s>>>(X_node, X_to, X_isr, d_nX, m_pos, r_to, part0, keep, final_to);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t nI_max, const int32_t *X_node, const int32_t *final_to,
+void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int32_t *X_node, const int32_t *final_to,
                  const int32_t *part0, int32_t *I_node, int32_t *I_from, int32_t *I_to, int32_t *pos, int32_t *dest,
                  cudaStream_t s) {
-    if (nI_max <= 0) return;
-    k_build_I<<<grid1(nI_max), 256, 0, s>>>(Ix, d_nI, X_node, final_to, part0, I_node, I_from, I_to, pos, dest);
+    k_build_I<<<grid_for(max), 256, 0, s>>>(Ix, d_nI, X_node, final_to, part0, I_node, I_from, I_to, pos, dest);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to, int64_t nI,
-               const int32_t *pos, const int32_t *dest, const int32_t *part0, int64_t *gain, int32_t *hub_flag,
-               int32_t *hub_excl, int32_t *hubs, int32_t *d_nh, void *tmp, cudaStream_t s) {
-    if (nI <= 0) return;
-    const int64_t blocks = std::min<int64_t>(ceil_div(nI * 32, 256), (int64_t)sm_count_seq() * 16);
-    k_gains_warp<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to, nI, pos, dest, part0,
-                                                  gain, hub_flag);
+void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+               const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
+               int64_t *gain, int32_t *hub_flag, int32_t *hubs, int32_t *d_nh, void *tmp, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16);
+    k_gains_warp<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to,
+                                                                       d_nI, pos, dest, part0, gain, hub_flag);
     UPR_LAUNCH_CHECK();
-    select_flags(hub_flag, hub_excl, hubs, d_nh, nI, tmp, s);
-    k_gains_hub<<<(unsigned)sm_count_seq(), 512, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to, hubs, d_nh, pos,
-                                                         dest, part0, gain);
-    UPR_LAUNCH_CHECK();
-}
-
-void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, int64_t nI, uint64_t *keys, uint32_t *vals,
-                  cudaStream_t s) {
-    if (nI <= 0) return;
-    k_iev_keys<<<grid1(2 * nI), 256, 0, s>>>(I_from, I_to, nI, keys, vals);
+    select_flags(hub_flag, hubs, d_nh, Count{d_nI, max}, tmp, s);
+    k_gains_hub<<<(unsigned)device_sm_count(), 512, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to, hubs, d_nh,
+                                                            pos, dest, part0, gain);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int32_t *vwgt,
-                   int64_t *delta, int32_t *ebeg, cudaStream_t s) {
-    if (nev <= 0) return;
-    k_iev_delta<<<grid1(nev), 256, 0, s>>>(I_node, EV, ekeys, nev, vwgt, delta, ebeg);
+void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, const int32_t *d_nI, int64_t max, uint64_t *keys,
+                  uint32_t *vals, cudaStream_t s) {
+    k_iev_keys<<<grid_for(2 * max), 256, 0, s>>>(I_from, I_to, d_nI, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_iev_transitions(const uint32_t *EV, const uint64_t *ekeys, int64_t nev, const int64_t *delta,
-                         const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, int64_t Lmax, int32_t *diff,
-                         cudaStream_t s) {
-    if (nev <= 0) return;
-    k_iev_transitions<<<grid1(nev), 256, 0, s>>>(EV, ekeys, nev, delta, d_excl, ebeg, C0, Lmax, diff);
+void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,
+                   const int32_t *vwgt, int64_t *delta, int32_t *ebeg, cudaStream_t s) {
+    k_iev_delta<<<grid_for(2 * max), 256, 0, s>>>(I_node, EV, ekeys, d_nI, vwgt, delta, ebeg);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, int64_t nI, int32_t over0,
-              long long *parts, long long *out, cudaStream_t s) {
-    const int nparts = (int)std::min<int64_t>(ceil_div(nI + 1, 256), 1024);
-    k_best_partial<<<nparts, 256, 0, s>>>(Gsum, diff, diff_excl, nI, over0, parts, parts + 1024);
-    UPR_LAUNCH_CHECK();
-    k_best_final<<<1, 32, 0, s>>>(parts, parts + 1024, nparts, out);
+void seq_iev_transitions(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,
+                         const int64_t *delta, const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0,
+                         int64_t Lmax, int32_t *diff, cudaStream_t s) {
+    k_iev_transitions<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nI, delta, d_excl, ebeg, C0, Lmax, diff);
     UPR_LAUNCH_CHECK();
 }
 
-void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to, int64_t nI,
-                      const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s) {
-    k_apply_prefix<<<grid1(nI), 256, 0, s>>>(I_node, I_from, I_to, best, g.vwgt, part0, (unsigned long long *)C0,
-                                             (long long *)cut);
+void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, const int32_t *d_nI, int64_t max,
+              const int32_t *d_over0, long long *parts, long long *out, int32_t *infeasible, cudaStream_t s) {
+    const int nparts = (int)std::min<int64_t>(ceil_div(max + 1, 256), 1024);
+    k_best_partial<<<nparts, 256, 0, s>>>(Gsum, diff, diff_excl, d_nI, d_over0, parts, parts + 1024);
+    UPR_LAUNCH_CHECK();
+    k_best_final<<<1, 1024, 0, s>>>(parts, parts + 1024, nparts, out, infeasible);
+    UPR_LAUNCH_CHECK();
+}
+
+void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+                      int64_t max, const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>(ceil_div(max > 0 ? max : 1, 256), (int64_t)device_sm_count() * 4);
+    k_apply_prefix<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
+        I_node, I_from, I_to, best, g.vwgt, part0, (unsigned long long *)C0, g.k, (long long *)cut);
     UPR_LAUNCH_CHECK();
 }
 

@@ -37,6 +37,18 @@ def _star_plus(seed, n=6000, k=8):
     return synth.Workload(f"star{n}", n, xadj, adj, None, None, k, 0.03, part, 3)
 
 
+def _near_hubs(seed=11, n=9000, k=8, heavy=12, deg=4090):
+    """Several nodes of degree just below the hub threshold next to low-degree nodes,
+    so tiles of the table build close on their entry budget."""
+    rng = np.random.default_rng(seed)
+    src = [np.repeat(np.arange(heavy), deg)]
+    dst = [np.concatenate([rng.choice(np.arange(heavy, n), size=deg, replace=False) for _ in range(heavy)])]
+    src.append(rng.integers(0, n, 2 * n)); dst.append(rng.integers(0, n, 2 * n))
+    xadj, adj = synth.csr_from_edges(n, np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32))
+    part = synth.part_random_balanced(n, k, seed)
+    return synth.Workload("near_hubs", n, xadj, adj, None, None, k, 0.03, part, 3)
+
+
 def _isolated(n=100, k=4):
     xadj = np.zeros(n + 1, np.int64)
     adj = np.zeros(0, np.int32)
@@ -59,6 +71,7 @@ CASES = {
     "small7_k_gt_n": lambda: synth.random_small(7, 9, 2, 12),
     "k11_odd": lambda: synth.random_small(8, 500, 6, 11, max_vw=5),
     "star_hub": lambda: _star_plus(10),
+    "near_hubs": _near_hubs,
     "isolated": _isolated,
     "heavy_weights": _heavy,
     "chung_lu_1k": lambda: synth.plain_tiny(4),
