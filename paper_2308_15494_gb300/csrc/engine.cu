@@ -41,7 +41,7 @@ struct SortBuf {
     uint64_t *k, *ka;
     uint32_t *v, *va;
     // sorts (k, v) on `bits` bits; returns the buffers holding the result
-    void run(Count n, int bits, void *tmp, cudaStream_t s, uint64_t **ko, uint32_t **vo) {
+    void run(Count n, int bits, Scratch tmp, cudaStream_t s, uint64_t **ko, uint32_t **vo) {
         bool alt = radix_sort_pairs(k, v, ka, va, n, bits, tmp, s);
         *ko = alt ? ka : k;
         *vo = alt ? va : v;
@@ -85,7 +85,7 @@ struct upr_ctx {
     int32_t *part0, *part; int64_t *C0, *C, *cut; int32_t *W;
     int64_t *BW, *PW, *F;
     // node-indexed
-    int32_t *cand_tgt, *cand_gain, *flags, *flags2, *excl_i, *m_pos, *r_to, *pos, *dest, *prop_tgt, *prop_gain;
+    int32_t *cand_tgt, *cand_gain, *flags, *flags2, *excl_i, *m_pos, *r_to, *r_at, *pos, *dest, *prop_tgt, *prop_gain;
     int64_t *cand_s0;
     // lists
     int32_t *idxA, *idxB, *idxC, *idxD, *L1;
@@ -106,7 +106,7 @@ struct upr_ctx {
     int32_t *counts;          // device counters (CNT_* slots)
     RebalCtl *ctl;            // rebalancing loop control block
     uint64_t *vacc; int32_t *vflags; int64_t *scal;
-    void *tmp;                // scan / sort temporaries
+    Scratch tmp;              // scan / sort temporaries
     // pinned host mirrors
     int64_t *h = nullptr;     // pinned scratch
     int8_t *h8 = nullptr;
@@ -141,7 +141,7 @@ void layout(upr_ctx *c, Arena &A) {
     for (int32_t **p : {&c->cand_tgt, &c->cand_gain, &c->flags, &c->m_pos, &c->r_to, &c->pos, &c->dest, &c->prop_tgt,
                         &c->prop_gain, &c->idxA, &c->idxB, &c->idxC, &c->M_node, &c->M_from, &c->M_to, &c->R_node,
                         &c->R_from, &c->R_to, &c->R_sub, &c->I_node, &c->I_from, &c->I_to, &c->emit, &c->qbefore,
-                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs, &c->L1})
+                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs, &c->L1, &c->r_at})
         *p = A.take<int32_t>(n);
     for (int32_t **p : {&c->flags2, &c->excl_i, &c->idxD, &c->X_node, &c->X_from, &c->X_to, &c->final_to})
         *p = A.take<int32_t>(n2 + 1);
@@ -177,7 +177,8 @@ void layout(upr_ctx *c, Arena &A) {
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
     c->scal = A.take<int64_t>(4);
-    c->tmp = A.take<char>(std::max(radix_temp_bytes((int64_t)n2), scan_temp_bytes((int64_t)n2 + 1)) + 1024);
+    c->tmp.mem = A.take<char>(std::max(radix_temp_bytes((int64_t)n2), scan_temp_bytes((int64_t)n2 + 1)) + 1024);
+    c->tmp.ticket = A.take<unsigned int>(64);
 }
 
 enum MemKind { kHost = 0, kDevice = 1 };
@@ -287,7 +288,8 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         // W' for P o M: the delta update costs two atomics per adjacency entry of a
         // moved node, a rebuild streams the graph and the table once; each kernel
         // checks on the device which of the two applies
-        table_move(G, c->W, c->M_node, c->M_from, c->M_to, cnt + CNT_M, nullptr, c->scal + 1, n, s);
+        table_move(G, c->W, c->M_node, c->M_from, c->M_to, cnt + CNT_M, nullptr, c->scal + 1, n, c->hub_chunks,
+                   c->n_chunks, HubMoves{c->m_pos, nullptr, nullptr, nullptr, nullptr, c->M_from, c->M_to}, s);
         gain_table(G, c->part, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, c->scal + 1, s);
     }
@@ -326,8 +328,9 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
                                 n, s);
         select_flags(c->flags2, c->idxC, cnt + CNT_A, cS, c->tmp, s);
         rebalance_apply(G, c->idxA, A, c->idxB, c->idxC, cnt + CNT_A, c->prop_tgt, c->part, c->C, ctl, c->R_node,
-                        c->R_from, c->R_to, c->R_sub, c->r_to, n, s);
-        table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, s);
+                        c->R_from, c->R_to, c->R_sub, c->r_to, c->r_at, n, s);
+        table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
+                   c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
         rebalance_end(k, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
         UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
@@ -375,8 +378,8 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     seq_build_I(c->idxD, dI, n, c->X_node, c->final_to, c->part0, c->I_node, c->I_from, c->I_to, c->pos, c->dest, s);
 
     // ---- (c2) exact gains, balanced prefixes, best prefix
-    seq_gains(G, c->I_node, c->I_from, c->I_to, dI, n, c->pos, c->dest, c->part0, c->I_gain, c->hub_flag, c->hubs,
-              cnt + CNT_HUB, c->tmp, s);
+    seq_gains(G, c->I_node, c->I_from, c->I_to, dI, n, c->pos, c->dest, c->part0, c->I_gain, c->hub_chunks,
+              c->n_chunks, s);
     inclusive_sum_i64(c->I_gain, c->Gsum, Count{dI, n}, c->tmp, s);
     count_affine(dI, 2, nullptr, 0, cnt + CNT_EVI, s);
     count_affine(dI, 1, nullptr, 1, cnt + CNT_I1, s);
@@ -648,6 +651,7 @@ upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_param
         if (c->wmax > 0x7fffffffLL) { free_ctx(c); return UPR_ERR_INVALID; }
         c->gbits = std::max(1, bit_length((uint64_t)c->wmax));
         if (1 + c->gbits + 2 * c->cbits > 63) { free_ctx(c); return UPR_ERR_INVALID; }
+        UPR_CUDA(cudaMemsetAsync(c->tmp.ticket, 0, 64 * sizeof(unsigned int), s));
         fill_i32(c->pos, c->n, INT32_MAX, s);
         fill_i32(c->m_pos, c->n, -1, s);
         fill_i32(c->r_to, c->n, -1, s);

@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
         if (s_row[b]) atomicAdd(&dst[b], s_row[b]);
 }
 
-// Delta update: warp per moved node.
+// Delta update: warp per moved node; hubs (degree > kHubDegree) are left to
+// k_table_move_hubs, which splits them into the static chunks.
 __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                              const int32_t *__restrict__ adjw, int32_t k, int32_t *__restrict__ W,
                              const int32_t *__restrict__ nodes, const int32_t *__restrict__ from,
@@ -294,12 +295,46 @@ __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
          j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t v = nodes[off + j], a = from[off + j], b = to[off + j];
-        for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) {
+        const int64_t e0 = xadj[v], e1 = xadj[v + 1];
+        if (e1 - e0 > kHubDegree) continue;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int32_t w = adjw ? adjw[e] : 1;
             int32_t *row = W + (int64_t)adj[e] * k;
             atomicSub(&row[a], w);
             atomicAdd(&row[b], w);
         }
+    }
+}
+
+// Moved hubs, one CTA per static chunk.  A hub moved in M has m_pos >= 0 (from
+// its round-start block to its M target); a hub moved in the current
+// rebalancing sub-round has an R index in [*r_base, *r_base + *r_count).
+__global__ void __launch_bounds__(512) k_table_move_hubs(const HubChunk *__restrict__ chunks,
+                                                         const int32_t *__restrict__ adj,
+                                                         const int32_t *__restrict__ adjw, int32_t k,
+                                                         int32_t *__restrict__ W, HubMoves hm,
+                                                         const int64_t *__restrict__ deg_sum, int64_t m) {
+    if (deg_sum && *deg_sum * 4 >= m) return;
+    const HubChunk ch = chunks[blockIdx.x];
+    const int32_t v = ch.v;
+    int32_t a, b;
+    if (hm.m_pos) {
+        const int32_t p = hm.m_pos[v];
+        if (p < 0) return;
+        a = hm.from[p];
+        b = hm.to[p];
+    } else {
+        if (hm.r_to[v] < 0) return;
+        const int32_t ri = hm.r_at[v], base = *hm.r_base;
+        if (ri < base || ri >= base + *hm.r_count) return;
+        a = hm.from[ri];
+        b = hm.to[ri];
+    }
+    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
+        const int32_t w = adjw ? adjw[e] : 1;
+        int32_t *row = W + (int64_t)adj[e] * k;
+        atomicSub(&row[a], w);
+        atomicAdd(&row[b], w);
     }
 }
 
@@ -401,12 +436,16 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
 
 void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
                 const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
-                cudaStream_t s) {
+                const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s) {
     if (max_count <= 0) return;
     int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
     k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, W, nodes, from, to, d_count, d_offset,
                                                   deg_sum, g.m);
     UPR_LAUNCH_CHECK();
+    if (n_chunks > 0) {
+        k_table_move_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, g.k, W, hm, deg_sum, g.m);
+        UPR_LAUNCH_CHECK();
+    }
 }
 
 }  // namespace upr

@@ -28,6 +28,14 @@ struct Count {
 };
 inline Count fixed(int64_t n) { return Count{nullptr, n}; }
 
+// Scratch memory of the primitives and the word their last-finishing CTA
+// takes a ticket from (zero between calls; calls on one scratch are
+// serialised by their stream).
+struct Scratch {
+    char *mem;
+    unsigned int *ticket;
+};
+
 // Grid-stride loop over a device-held count (all threads of the grid).
 #define UPR_FOR(i, cnt) \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (cnt); i += (int64_t)gridDim.x * blockDim.x)
@@ -41,18 +49,18 @@ inline unsigned grid_for(int64_t max) {
 // ---- prim.cu
 size_t scan_temp_bytes(int64_t n);
 size_t radix_temp_bytes(int64_t n);
-void exclusive_sum_i32(const int32_t *in, int32_t *out, Count n, void *tmp, cudaStream_t s);
-void exclusive_sum_i64(const int64_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s);
-void inclusive_sum_i64(const int64_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s);
-void exclusive_sum_i32_to_i64(const int32_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s);
-void inclusive_max_u64(const uint64_t *in, uint64_t *out, Count n, void *tmp, cudaStream_t s);
+void exclusive_sum_i32(const int32_t *in, int32_t *out, Count n, Scratch tmp, cudaStream_t s);
+void exclusive_sum_i64(const int64_t *in, int64_t *out, Count n, Scratch tmp, cudaStream_t s);
+void inclusive_sum_i64(const int64_t *in, int64_t *out, Count n, Scratch tmp, cudaStream_t s);
+void exclusive_sum_i32_to_i64(const int32_t *in, int64_t *out, Count n, Scratch tmp, cudaStream_t s);
+void inclusive_max_u64(const uint64_t *in, uint64_t *out, Count n, Scratch tmp, cudaStream_t s);
 void iota_u32(uint32_t *v, int64_t n, cudaStream_t s);
 // Stable LSD sort on key bits [0, bits); returns true if the result is in the *_alt buffers
 // (a property of `bits` alone, known when the launches are enqueued).
 bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, Count n, int bits,
-                      void *tmp, cudaStream_t s);
+                      Scratch tmp, cudaStream_t s);
 // out_idx[0..*d_count) = indices i < n with flags[i] != 0, ascending.
-void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, void *tmp, cudaStream_t s);
+void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, Scratch tmp, cudaStream_t s);
 
 // ---- graph.cu: step (e), step (a), create-time work
 struct HubChunk { int32_t v; int32_t pad; int64_t begin, end; };
@@ -69,12 +77,22 @@ size_t table_tile_smem(int32_t k, int32_t nodes);
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
                 const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s);
+// How moved hubs are found for the chunked delta update: through m_pos (moves
+// of M: from/to are M_from/M_to) or, when m_pos is null, through r_to/r_at
+// (moves of the current rebalancing sub-round: R indices in [*r_base,
+// *r_base + *r_count), from/to are R_from/R_to).
+struct HubMoves {
+    const int32_t *m_pos;
+    const int32_t *r_to, *r_at, *r_base, *r_count;
+    const int32_t *from, *to;
+};
 // For each listed node v moving from[i] -> to[i] (i < *d_count, entries start at
 // *d_offset when given): W[u][from] -= w, W[u][to] += w for every neighbour u.
 // With deg_sum: runs only when 4 * (*deg_sum) < m (otherwise a rebuild is cheaper).
+// Hubs are handled chunk by chunk through hub_chunks and hm.
 void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
                 const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
-                cudaStream_t s);
+                const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s);
 // Graph checks; writes a bitmask of violations into *d_flags (see engine.cu).
 void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s);
 
@@ -146,8 +164,8 @@ void rebalance_mark_admitted(const uint32_t *T, const uint64_t *bkeys, const int
                              int8_t *reject, int64_t cnt_max, cudaStream_t s);
 void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *Adm,
                      const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, const RebalCtl *ctl,
-                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int64_t na_max,
-                     cudaStream_t s);
+                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int32_t *r_at,
+                     int64_t na_max, cudaStream_t s);
 void rebalance_init(const int64_t *C, int32_t k, int64_t Lmax, int8_t *excl, RebalCtl *ctl, cudaStream_t s);
 void rebalance_begin(const int64_t *C, int32_t k, int64_t Lmax, const int8_t *excl, int8_t *over, int8_t *reject,
                      const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, cudaStream_t s);
@@ -190,7 +208,7 @@ void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int3
                  cudaStream_t s);
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
-               int64_t *gain, int32_t *hub_flag, int32_t *hubs, int32_t *d_nh, void *tmp, cudaStream_t s);
+               int64_t *gain, const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s);
 void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, const int32_t *d_nI, int64_t max, uint64_t *keys,
                   uint32_t *vals, cudaStream_t s);
 void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,

@@ -101,10 +101,40 @@ __device__ __forceinline__ void store_items(T *__restrict__ out, int64_t base, i
     }
 }
 
+// Exclusive scan of the tile totals part[0 .. tiles) by one CTA, in chunks of
+// 2048 with a carry; optionally writes the grand total (as int32) to *d_total.
+template <typename Op, typename T>
+__device__ void scan_partials(T *part, int64_t tiles, int32_t *d_total, T *s_warp) {
+    T carry = Op::template identity<T>();
+    for (int64_t c0 = 0; c0 < tiles; c0 += kTile) {
+        T x[kItems];
+        const int64_t first = c0 + (int64_t)threadIdx.x * kItems;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) x[j] = first + j < tiles ? __ldcg(part + first + j) : Op::template identity<T>();
+        T acc = Op::template identity<T>();
+#pragma unroll
+        for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, x[j]);
+        T total;
+        T run = Op::template apply<T>(carry, block_exclusive<Op>(acc, s_warp, &total));
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const T nxt = Op::template apply<T>(run, x[j]);
+            if (first + j < tiles) part[first + j] = run;
+            run = nxt;
+        }
+        carry = Op::template apply<T>(carry, total);
+    }
+    if (d_total && threadIdx.x == 0) *d_total = (int32_t)carry;
+}
+
+// Per-tile totals; the CTA that finishes last (ticket counter, no waiting)
+// scans them and resets the ticket.
 template <typename Op, typename T, typename TIn>
 __global__ void __launch_bounds__(kThreads) k_tile_reduce(const TIn *__restrict__ in, const int32_t *__restrict__ d_n,
-                                                          int64_t n_max, T *__restrict__ part, int vec) {
+                                                          int64_t n_max, T *__restrict__ part, int vec,
+                                                          unsigned int *__restrict__ ticket) {
     __shared__ T s_warp[kWarps];
+    __shared__ bool s_last;
     const int64_t n = count_of(d_n, n_max);
     for (int64_t tile = blockIdx.x; tile < tiles_of(n); tile += gridDim.x) {
         TIn x[kItems];
@@ -116,34 +146,14 @@ __global__ void __launch_bounds__(kThreads) k_tile_reduce(const TIn *__restrict_
         block_exclusive<Op>(acc, s_warp, &total);
         if (threadIdx.x == 0) part[tile] = total;
     }
-}
-
-// One CTA: exclusive scan of the per-tile totals in chunks of 2048 with a
-// carry; optionally writes the grand total (as int32) to *d_total.
-template <typename Op, typename T>
-__global__ void __launch_bounds__(kThreads) k_partials_scan(T *__restrict__ part, const int32_t *__restrict__ d_n,
-                                                            int64_t n_max, int32_t *__restrict__ d_total) {
-    __shared__ T s_warp[kWarps];
-    const int64_t tiles = tiles_of(count_of(d_n, n_max));
-    T carry = Op::template identity<T>();
-    for (int64_t c0 = 0; c0 < tiles; c0 += kTile) {
-        T x[kItems];
-        load_items(part, c0, tiles, false, x);
-        T acc = Op::template identity<T>();
-#pragma unroll
-        for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, x[j]);
-        T total;
-        T run = Op::template apply<T>(carry, block_exclusive<Op>(acc, s_warp, &total));
-#pragma unroll
-        for (int j = 0; j < kItems; j++) {
-            const T nxt = Op::template apply<T>(run, x[j]);
-            x[j] = run;
-            run = nxt;
-        }
-        store_items(part, c0, tiles, false, x);
-        carry = Op::template apply<T>(carry, total);
-    }
-    if (d_total && threadIdx.x == 0) *d_total = (int32_t)carry;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    scan_partials<Op, T>(part, tiles_of(n), nullptr, s_warp);
+    if (threadIdx.x == 0) *ticket = 0;
 }
 
 // Scans every tile with the offset from part[] (exclusive-scanned totals; null = one tile).
@@ -180,7 +190,7 @@ inline unsigned tile_grid(int64_t tiles_max) {
 }
 
 template <typename Op, typename T, typename TIn>
-void scan_impl(const TIn *in, T *out, Count n, bool inclusive, void *tmp, cudaStream_t s) {
+void scan_impl(const TIn *in, T *out, Count n, bool inclusive, Scratch tmp, cudaStream_t s) {
     if (n.max <= 0) return;
     const int vin = aligned16(in) ? 1 : 0;
     const int vio = vin | (aligned16(out) ? 2 : 0);
@@ -190,10 +200,8 @@ void scan_impl(const TIn *in, T *out, Count n, bool inclusive, void *tmp, cudaSt
         UPR_LAUNCH_CHECK();
         return;
     }
-    T *part = (T *)tmp;
-    k_tile_reduce<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, n.d, n.max, part, vin);
-    UPR_LAUNCH_CHECK();
-    k_partials_scan<Op, T><<<1, kThreads, 0, s>>>(part, n.d, n.max, nullptr);
+    T *part = (T *)tmp.mem;
+    k_tile_reduce<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, n.d, n.max, part, vin, tmp.ticket);
     UPR_LAUNCH_CHECK();
     k_tile_scan<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, part, inclusive ? 1 : 0,
                                                                       vio);
@@ -205,8 +213,10 @@ void scan_impl(const TIn *in, T *out, Count n, bool inclusive, void *tmp, cudaSt
 // thread ranks its 8 flags in registers and writes the indices of the set
 // ones; tile order, then thread order, then item order = index order.
 __global__ void __launch_bounds__(kThreads) k_flag_count(const int32_t *__restrict__ flags, const int32_t *__restrict__ d_n,
-                                                         int64_t n_max, int32_t *__restrict__ counts, int vec) {
+                                                         int64_t n_max, int32_t *__restrict__ counts, int vec,
+                                                         int32_t *__restrict__ d_count, unsigned int *__restrict__ ticket) {
     __shared__ int32_t s_warp[kWarps];
+    __shared__ bool s_last;
     const int64_t n = count_of(d_n, n_max);
     for (int64_t tile = blockIdx.x; tile < tiles_of(n); tile += gridDim.x) {
         int32_t x[kItems];
@@ -218,6 +228,14 @@ __global__ void __launch_bounds__(kThreads) k_flag_count(const int32_t *__restri
         block_exclusive<OpSum>(c, s_warp, &total);
         if (threadIdx.x == 0) counts[tile] = total;
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    scan_partials<OpSum, int32_t>(counts, tiles_of(n), d_count, s_warp);
+    if (threadIdx.x == 0) *ticket = 0;
 }
 
 __global__ void __launch_bounds__(kThreads) k_flag_scatter(const int32_t *__restrict__ flags, const int32_t *__restrict__ d_n,
@@ -408,19 +426,19 @@ size_t radix_temp_bytes(int64_t n) {
     return hist * sizeof(int32_t) + 256 + scan_temp_bytes((int64_t)hist);
 }
 
-void exclusive_sum_i32(const int32_t *in, int32_t *out, Count n, void *tmp, cudaStream_t s) {
+void exclusive_sum_i32(const int32_t *in, int32_t *out, Count n, Scratch tmp, cudaStream_t s) {
     scan_impl<OpSum, int32_t, int32_t>(in, out, n, false, tmp, s);
 }
-void exclusive_sum_i64(const int64_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s) {
+void exclusive_sum_i64(const int64_t *in, int64_t *out, Count n, Scratch tmp, cudaStream_t s) {
     scan_impl<OpSum, int64_t, int64_t>(in, out, n, false, tmp, s);
 }
-void inclusive_sum_i64(const int64_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s) {
+void inclusive_sum_i64(const int64_t *in, int64_t *out, Count n, Scratch tmp, cudaStream_t s) {
     scan_impl<OpSum, int64_t, int64_t>(in, out, n, true, tmp, s);
 }
-void exclusive_sum_i32_to_i64(const int32_t *in, int64_t *out, Count n, void *tmp, cudaStream_t s) {
+void exclusive_sum_i32_to_i64(const int32_t *in, int64_t *out, Count n, Scratch tmp, cudaStream_t s) {
     scan_impl<OpSum, int64_t, int32_t>(in, out, n, false, tmp, s);
 }
-void inclusive_max_u64(const uint64_t *in, uint64_t *out, Count n, void *tmp, cudaStream_t s) {
+void inclusive_max_u64(const uint64_t *in, uint64_t *out, Count n, Scratch tmp, cudaStream_t s) {
     scan_impl<OpMax, uint64_t, uint64_t>(in, out, n, true, tmp, s);
 }
 
@@ -431,7 +449,7 @@ void iota_u32(uint32_t *v, int64_t n, cudaStream_t s) {
 }
 
 bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, Count n, int bits,
-                      void *tmp, cudaStream_t s) {
+                      Scratch tmp, cudaStream_t s) {
     if (n.max <= 0 || bits <= 0) return false;
     const int passes = (bits + 7) / 8;
     const bool alt = passes & 1;
@@ -440,9 +458,9 @@ bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     UPR_LAUNCH_CHECK();
     if (n.max <= kTile) return alt;
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    int32_t *hist = (int32_t *)tmp;
-    int32_t *d_hist_n = (int32_t *)((char *)tmp + (size_t)kBins * tiles_max * sizeof(int32_t));
-    void *stmp = (char *)tmp + (size_t)kBins * tiles_max * sizeof(int32_t) + 256;
+    int32_t *hist = (int32_t *)tmp.mem;
+    int32_t *d_hist_n = (int32_t *)(tmp.mem + (size_t)kBins * tiles_max * sizeof(int32_t));
+    const Scratch stmp{tmp.mem + (size_t)kBins * tiles_max * sizeof(int32_t) + 256, tmp.ticket};
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     for (int p = 0; p < passes; p++) {
@@ -457,7 +475,7 @@ bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     return alt;
 }
 
-void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, void *tmp, cudaStream_t s) {
+void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, Scratch tmp, cudaStream_t s) {
     if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
     const int vec = aligned16(flags) ? 1 : 0;
     const int64_t tiles_max = ceil_div(n.max, kTile);
@@ -466,10 +484,8 @@ void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Coun
         UPR_LAUNCH_CHECK();
         return;
     }
-    int32_t *counts = (int32_t *)tmp;
-    k_flag_count<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, counts, vec);
-    UPR_LAUNCH_CHECK();
-    k_partials_scan<OpSum, int32_t><<<1, kThreads, 0, s>>>(counts, n.d, n.max, d_count);
+    int32_t *counts = (int32_t *)tmp.mem;
+    k_flag_count<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, counts, vec, d_count, tmp.ticket);
     UPR_LAUNCH_CHECK();
     k_flag_scatter<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, counts, out_idx, d_count, vec);
     UPR_LAUNCH_CHECK();

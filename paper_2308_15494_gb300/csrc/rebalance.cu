@@ -71,18 +71,23 @@ __device__ __forceinline__ int32_t int4_at(const int4 &x, int c) {
 // rebalancing started; those that left them are skipped).  Vectorised rows
 // as in selection; s_room[b] = L_max - C[b] for an allowed target, -1 for an
 // excluded one, so one comparison c <= s_room[b] tests validity.
-template <int G, int CH>
+template <int G, int CH, bool EXACT>
 __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
                                                      const int32_t *__restrict__ part, const int32_t *__restrict__ W,
                                                      const int32_t *__restrict__ vwgt, int32_t k, RebalState st,
                                                      int32_t *__restrict__ prop_tgt, int32_t *__restrict__ prop_gain,
                                                      int32_t *__restrict__ flags) {
+    // EXACT: k == 4 * G * CH, every lane's four blocks exist.  The room of an
+    // excluded block (which includes every overloaded block, so the node's own
+    // block) is -1, so "c <= room" alone decides whether a block may receive
+    // the node; room is clamped to 2^31 - 1 since c < 2^31.
     const int64_t n1 = *d_n1;
     if (n1 == 0) return;
-    extern __shared__ int64_t s_room[];
+    extern __shared__ int32_t s_room[];
     int8_t *s_over = reinterpret_cast<int8_t *>(s_room + k);
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        s_room[i] = st.excl[i] ? -1 : st.Lmax - st.C[i];
+        const int64_t room = st.Lmax - st.C[i];
+        s_room[i] = st.excl[i] ? -1 : (int32_t)(room > 0x7fffffffLL ? 0x7fffffffLL : room);
         s_over[i] = st.over[i];
     }
     __syncthreads();
@@ -90,7 +95,8 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
     const int32_t light = *st.light;
-    const int64_t light_room = light >= 0 ? st.Lmax - st.C[light] : -1;
+    const int64_t lroom = light >= 0 ? st.Lmax - st.C[light] : -1;
+    const int32_t light_room = (int32_t)(lroom > 0x7fffffffLL ? 0x7fffffffLL : lroom);
     for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
         const int64_t i = base + gid;
         const int32_t v = i < n1 ? list[i] : 0;
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
 #pragma unroll
             for (int j = 0; j < CH; j++) {
                 const int q = gl + G * j;
-                r[j] = 4 * q < k ? row4[q] : zero;
+                r[j] = (EXACT || 4 * q < k) ? row4[q] : zero;
             }
         } else {
 #pragma unroll
@@ -115,9 +121,9 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
         for (int j = 0; j < CH; j++)
             if (j == q4 / G) mine = int4_at(r[j], a & 3);
         const int32_t own = __shfl_sync(0xffffffffu, mine, gbase + (q4 % G));
-        const int64_t c = src ? (vwgt ? vwgt[v] : 1) : 1;
-        int64_t best = 0;
-        int32_t bt = -1;
+        const int32_t c = src ? (vwgt ? vwgt[v] : 1) : 1;
+        // best valid block: the largest omega(v, V_b) (gain = omega - own), ties to the smaller b
+        int32_t bw = 0, bt = -1;
         if (src) {
 #pragma unroll
             for (int j = 0; j < CH; j++) {
@@ -125,20 +131,18 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
                 for (int cc = 0; cc < 4; cc++) {
                     const int b = 4 * (gl + G * j) + cc;
                     const int32_t w = int4_at(r[j], cc);
-                    if (b >= k || b == a || w <= 0 || c > s_room[b]) continue;
-                    const int64_t gain = (int64_t)w - own;
-                    if (bt < 0 || gain > best) { best = gain; bt = b; }
+                    if ((!EXACT && b >= k) || w <= 0 || c > s_room[b]) continue;
+                    if (bt < 0 || w > bw) { bw = w; bt = b; }
                 }
             }
         }
-        int64_t sb = best;
         int32_t id = bt;
-        group_argmax<G>(sb, id);
+        group_argmax32<G>(bw, id);
         if (i < n1 && gl == 0) {
             int32_t tgt = src ? id : -1;
-            int64_t gain = sb;
-            if (src && tgt < 0 && c <= light_room) { tgt = light; gain = -(int64_t)own; }
-            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = (int32_t)gain; }
+            int32_t gain = bw - own;
+            if (src && tgt < 0 && c <= light_room) { tgt = light; gain = -own; }
+            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = gain; }
             flags[i] = tgt >= 0 ? 1 : 0;
         }
     }
@@ -326,7 +330,8 @@ __global__ void k_apply_rebal(const int32_t *__restrict__ P, const uint32_t *__r
                               const int32_t *__restrict__ vwgt, int32_t *__restrict__ part,
                               unsigned long long *__restrict__ C, int32_t k, const RebalCtl *__restrict__ ctl,
                               int32_t *__restrict__ R_node, int32_t *__restrict__ R_from,
-                              int32_t *__restrict__ R_to, int32_t *__restrict__ R_sub, int32_t *__restrict__ r_to) {
+                              int32_t *__restrict__ R_to, int32_t *__restrict__ R_sub, int32_t *__restrict__ r_to,
+                              int32_t *__restrict__ r_at) {
     extern __shared__ unsigned long long s_delta[];
     BlockDelta bd{s_delta, k};
     bd.init();
@@ -348,6 +353,7 @@ __global__ void k_apply_rebal(const int32_t *__restrict__ P, const uint32_t *__r
             R_to[p] = b;
             R_sub[p] = subround;
             r_to[u] = b;
+            r_at[u] = (int32_t)(off + p);
             part[u] = b;
         }
         bd.add(a, -c);
@@ -402,27 +408,30 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
                             int32_t *prop_gain, int32_t *flags, cudaStream_t s) {
     if (n1_max <= 0) return;
     const int k = g.k;
-    const size_t shm = sizeof(int64_t) * (size_t)k + (size_t)k + 16;
+    const size_t shm = sizeof(int32_t) * (size_t)k + (size_t)k + 16;
     if (k % 4 == 0 && k <= 256) {
         int G = 1;
         while (G < 32 && 4 * G < k) G <<= 1;
         const int CH = (k + 4 * G - 1) / (4 * G);
+        const bool exact = k == 4 * G * CH;
         const int64_t groups = 256 / G;
         const int64_t blocks = std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 8);
-#define UPR_PV(GG, CC) k_propose_vec<GG, CC><<<(unsigned)blocks, 256, shm, s>>>(list, d_n1, part, W, g.vwgt, k, st, \
-                                                                            prop_tgt, prop_gain, flags)
+#define UPR_PV(GG, CC, EX) k_propose_vec<GG, CC, EX><<<(unsigned)blocks, 256, shm, s>>>(list, d_n1, part, W, g.vwgt, \
+                                                                                    k, st, prop_tgt, prop_gain, flags)
+#define UPR_PVE(GG, CC) do { if (exact) UPR_PV(GG, CC, true); else UPR_PV(GG, CC, false); } while (0)
         if (CH == 1) {
             switch (G) {
-                case 1: UPR_PV(1, 1); break;
-                case 2: UPR_PV(2, 1); break;
-                case 4: UPR_PV(4, 1); break;
-                case 8: UPR_PV(8, 1); break;
-                case 16: UPR_PV(16, 1); break;
-                default: UPR_PV(32, 1); break;
+                case 1: UPR_PVE(1, 1); break;
+                case 2: UPR_PVE(2, 1); break;
+                case 4: UPR_PVE(4, 1); break;
+                case 8: UPR_PVE(8, 1); break;
+                case 16: UPR_PVE(16, 1); break;
+                default: UPR_PVE(32, 1); break;
             }
         } else {
-            UPR_PV(32, 2);
+            UPR_PVE(32, 2);
         }
+#undef UPR_PVE
 #undef UPR_PV
         UPR_LAUNCH_CHECK();
         return;
@@ -469,13 +478,13 @@ void rebalance_mark_admitted(const uint32_t *T, const uint64_t *bkeys, const int
 
 void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *Adm,
                      const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, const RebalCtl *ctl,
-                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int64_t na_max,
-                     cudaStream_t s) {
+                     int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int32_t *r_at,
+                     int64_t na_max, cudaStream_t s) {
     if (na_max <= 0) return;
     const int64_t blocks = std::min<int64_t>(ceil_div(na_max, 256), (int64_t)device_sm_count() * 4);
     k_apply_rebal<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
         P, A, S, Adm, d_na, prop_tgt, g.vwgt, part, (unsigned long long *)C, g.k, ctl, R_node, R_from, R_to, R_sub,
-        r_to);
+        r_to, r_at);
     UPR_LAUNCH_CHECK();
 }
 

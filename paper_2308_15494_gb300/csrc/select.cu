@@ -156,17 +156,23 @@ __device__ __forceinline__ int32_t int4_get(const int4 &x, int c) {
 // The per-block slack L_max - C[b] and the factors F_r (and, when they fit,
 // the bucket prefixes) are staged in shared memory; a move into a block with
 // room for it costs no penalty and needs no search.
-template <int G, int CH>
+template <int G, int CH, bool EXACT>
 __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
                                                     const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt,
                                                     int64_t n, int32_t k, Penalty pen, int smem_pw,
                                                     int32_t *__restrict__ cand_tgt, int64_t *__restrict__ cand_s0,
                                                     int32_t *__restrict__ cand_gain, int32_t *__restrict__ flags) {
+    // s_slack[b] = L_max - C[b] clamped to 2^31 - 1 (blocks start balanced, so
+    // it is >= 0): a node of weight c < 2^31 overfills b iff c > s_slack[b],
+    // and then x = c - s_slack[b] is exact.
     extern __shared__ int64_t s_mem[];
-    int64_t *s_slack = s_mem;
-    int64_t *s_F = s_mem + k;
-    int64_t *s_PW = s_mem + k + kSlots;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) s_slack[i] = pen.Lmax - pen.C[i];
+    int64_t *s_F = s_mem;
+    int64_t *s_PW = s_mem + kSlots;
+    int32_t *s_slack = reinterpret_cast<int32_t *>(s_mem + kSlots + (smem_pw ? (size_t)k * kSlots : 0));
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int64_t sl = pen.Lmax - pen.C[i];
+        s_slack[i] = (int32_t)(sl > 0x7fffffffLL ? 0x7fffffffLL : sl);
+    }
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) s_F[i] = pen.F[i];
     if (smem_pw)
         for (int i = threadIdx.x; i < k * kSlots; i += blockDim.x) s_PW[i] = pen.PW[i];
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
 #pragma unroll
             for (int j = 0; j < CH; j++) {
                 const int q = gl + G * j;
-                r[j] = 4 * q < k ? __ldcs(row4 + q) : zero;
+                r[j] = (EXACT || 4 * q < k) ? __ldcs(row4 + q) : zero;
             }
         } else {
 #pragma unroll
@@ -200,23 +206,23 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
             if (j == q4 / G) mine = int4_get(r[j], a & 3);
         const int32_t own = __shfl_sync(0xffffffffu, mine, gbase + (q4 % G));
         // Only a positive score makes a candidate and the penalty is never
-        // negative, so blocks with gain <= 0 are skipped and every score kept
-        // lies in [1, 2^31).
+        // negative, so blocks with gain <= 0 (the own block among them) are
+        // skipped and every score kept lies in [1, 2^31).
         int32_t best = 0;
         int32_t bt = -1, bg = 0;
         if (active && own < wI[v]) {
-            const int64_t c = vwgt ? vwgt[v] : 1;
+            const int32_t c = vwgt ? vwgt[v] : 1;
 #pragma unroll
             for (int j = 0; j < CH; j++) {
 #pragma unroll
                 for (int cc = 0; cc < 4; cc++) {
                     const int b = 4 * (gl + G * j) + cc;
                     const int32_t w = int4_get(r[j], cc);
-                    if (b >= k || b == a || w <= own) continue;
+                    if ((!EXACT && b >= k) || w <= own) continue;
                     const int32_t gain = w - own;
-                    const int64_t x = c - s_slack[b];
-                    int64_t p = 0;
-                    if (x > 0) {
+                    int32_t sc = gain;
+                    if (c > s_slack[b]) {
+                        const int64_t x = (int64_t)c - s_slack[b];
                         const int64_t *row = PW + (int64_t)b * kSlots;
                         if (row[kSlots - 1] < x) continue;          // no slot covers the excess: forbidden
                         int lo = 0, hi = kSlots - 1;
@@ -224,10 +230,10 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
                             const int mid = (lo + hi) >> 1;
                             if (row[mid] >= x) hi = mid; else lo = mid + 1;
                         }
-                        p = (int64_t)(((u128)(uint64_t)c * (uint64_t)s_F[lo]) >> kQ);
+                        const int64_t p = (int64_t)(((u128)(uint64_t)c * (uint64_t)s_F[lo]) >> kQ);
                         if (p >= gain) continue;
+                        sc = gain - (int32_t)p;
                     }
-                    const int32_t sc = gain - (int32_t)p;
                     if (bt < 0 || sc > best) { best = sc; bt = b; bg = gain; }
                 }
             }
@@ -246,8 +252,6 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
     }
 }
 
-// Ascending (target, s0 descending): scores lie in [1, 2^gbits) because a
-// score never exceeds its gain, which never exceeds omega(I(v)) < 2^gbits.
 __global__ void k_cand_keys(const int32_t *__restrict__ cand_idx, const int32_t *__restrict__ d_count,
                             const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ cand_s0, int gbits,
                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
@@ -377,24 +381,28 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
         int G = 1;
         while (G < 32 && 4 * G < k) G <<= 1;
         const int CH = (k + 4 * G - 1) / (4 * G);
+        const bool exact = k == 4 * G * CH;
         const int smem_pw = (size_t)k * kSlots * 8 <= 40 * 1024;
-        const size_t shm = sizeof(int64_t) * ((size_t)k + kSlots + (smem_pw ? (size_t)k * kSlots : 0));
+        const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) + sizeof(int32_t) * k;
         const int64_t groups = 256 / G;
         const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
-#define UPR_SELV(GG, CC) k_select_vec<GG, CC><<<(unsigned)blocks, 256, shm, s>>>(part, W, g.wI, g.vwgt, g.n, k, pen, \
-                                                                             smem_pw, cand_tgt, cand_s0, cand_gain, flags)
+#define UPR_SELV(GG, CC, EX) k_select_vec<GG, CC, EX><<<(unsigned)blocks, 256, shm, s>>>(part, W, g.wI, g.vwgt, g.n, k, \
+                                                                                     pen, smem_pw, cand_tgt, cand_s0, \
+                                                                                     cand_gain, flags)
+#define UPR_SELVE(GG, CC) do { if (exact) UPR_SELV(GG, CC, true); else UPR_SELV(GG, CC, false); } while (0)
         if (CH == 1) {
             switch (G) {
-                case 1: UPR_SELV(1, 1); break;
-                case 2: UPR_SELV(2, 1); break;
-                case 4: UPR_SELV(4, 1); break;
-                case 8: UPR_SELV(8, 1); break;
-                case 16: UPR_SELV(16, 1); break;
-                default: UPR_SELV(32, 1); break;
+                case 1: UPR_SELVE(1, 1); break;
+                case 2: UPR_SELVE(2, 1); break;
+                case 4: UPR_SELVE(4, 1); break;
+                case 8: UPR_SELVE(8, 1); break;
+                case 16: UPR_SELVE(16, 1); break;
+                default: UPR_SELVE(32, 1); break;
             }
         } else {
-            UPR_SELV(32, 2);
+            UPR_SELVE(32, 2);
         }
+#undef UPR_SELVE
 #undef UPR_SELV
         UPR_LAUNCH_CHECK();
         return;

@@ -240,7 +240,7 @@ __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__
                              const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to,
                              const int32_t *__restrict__ d_nI, const int32_t *__restrict__ pos,
                              const int32_t *__restrict__ dest, const int32_t *__restrict__ part0,
-                             int64_t *__restrict__ gain, int32_t *__restrict__ hub_flag) {
+                             int64_t *__restrict__ gain) {
     const int lane = threadIdx.x & 31;
     const int64_t nI = *d_nI;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nI;
@@ -248,7 +248,7 @@ __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__
         const int32_t v = I_node[i], a = I_from[i], b = I_to[i];
         const int64_t e0 = xadj[v], e1 = xadj[v + 1];
         if (e1 - e0 > kHubDegree) {
-            if (lane == 0) { gain[i] = 0; hub_flag[i] = 1; }
+            if (lane == 0) gain[i] = 0;
             continue;
         }
         long long acc = 0;
@@ -259,36 +259,40 @@ __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__
             acc += (bu == b ? w : 0) - (bu == a ? w : 0);
         }
         acc = warp_sum(acc);
-        if (lane == 0) { gain[i] = acc; hub_flag[i] = 0; }
+        if (lane == 0) gain[i] = acc;
     }
 }
 
-__global__ void __launch_bounds__(512) k_gains_hub(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                                                   const int32_t *__restrict__ adjw, const int32_t *__restrict__ I_node,
-                                                   const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to,
-                                                   const int32_t *__restrict__ hubs, const int32_t *__restrict__ d_nh,
-                                                   const int32_t *__restrict__ pos, const int32_t *__restrict__ dest,
-                                                   const int32_t *__restrict__ part0, int64_t *__restrict__ gain) {
+// Exact gains of hub moves, one CTA per static chunk of a hub's adjacency:
+// partial sums added to gain[i] (set to 0 by k_gains_warp) with 64-bit
+// integer atomics, whose result does not depend on their order.
+__global__ void __launch_bounds__(512) k_gains_hub_chunks(const HubChunk *__restrict__ chunks,
+                                                          const int32_t *__restrict__ adj,
+                                                          const int32_t *__restrict__ adjw,
+                                                          const int32_t *__restrict__ I_from,
+                                                          const int32_t *__restrict__ I_to,
+                                                          const int32_t *__restrict__ pos,
+                                                          const int32_t *__restrict__ dest,
+                                                          const int32_t *__restrict__ part0, int64_t *__restrict__ gain) {
     __shared__ long long s_w[16];
-    for (int64_t h = blockIdx.x; h < *d_nh; h += gridDim.x) {
-        const int64_t i = hubs[h];
-        const int32_t v = I_node[i], a = I_from[i], b = I_to[i];
-        long long acc = 0;
-        for (int64_t e = xadj[v] + threadIdx.x; e < xadj[v + 1]; e += blockDim.x) {
-            const int32_t u = adj[e];
-            const int32_t bu = pos[u] < i ? dest[u] : part0[u];
-            const int32_t w = adjw ? adjw[e] : 1;
-            acc += (bu == b ? w : 0) - (bu == a ? w : 0);
-        }
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long t = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
-            gain[i] = t;
-        }
-        __syncthreads();
+    const HubChunk ch = chunks[blockIdx.x];
+    const int32_t i = pos[ch.v];
+    if (i == INT32_MAX) return;                  // this hub is not in I
+    const int32_t a = I_from[i], b = I_to[i];
+    long long acc = 0;
+    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
+        const int32_t u = adj[e];
+        const int32_t bu = pos[u] < i ? dest[u] : part0[u];
+        const int32_t w = adjw ? adjw[e] : 1;
+        acc += (bu == b ? w : 0) - (bu == a ? w : 0);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long *>(&gain[i]), (unsigned long long)t);
     }
 }
 
@@ -551,15 +555,16 @@ void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int3
 
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
-               int64_t *gain, int32_t *hub_flag, int32_t *hubs, int32_t *d_nh, void *tmp, cudaStream_t s) {
+               int64_t *gain, const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s) {
     const int64_t blocks = std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16);
     k_gains_warp<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to,
-                                                                       d_nI, pos, dest, part0, gain, hub_flag);
+                                                                       d_nI, pos, dest, part0, gain);
     UPR_LAUNCH_CHECK();
-    select_flags(hub_flag, hubs, d_nh, Count{d_nI, max}, tmp, s);
-    k_gains_hub<<<(unsigned)device_sm_count(), 512, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to, hubs, d_nh,
-                                                            pos, dest, part0, gain);
-    UPR_LAUNCH_CHECK();
+    if (n_chunks > 0) {
+        k_gains_hub_chunks<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, I_from, I_to, pos, dest, part0,
+                                                              gain);
+        UPR_LAUNCH_CHECK();
+    }
 }
 
 void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, const int32_t *d_nI, int64_t max, uint64_t *keys,
