@@ -77,6 +77,7 @@ struct upr_ctx {
     GraphDev G{};
 
     void *mem = nullptr;
+    size_t mem_bytes = 0;
     // graph
     int64_t *xadj; int32_t *adj, *adjw, *vwgt, *wI;
     HubChunk *hub_chunks; int64_t n_chunks = 0;
@@ -541,128 +542,161 @@ static bool params_ok(const upr_params &p) {
            p.total_rounds >= 0 && p.total_rounds <= 65536;
 }
 
-upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_params *params, upr_ctx **out) {
-    if (!g || !out || g->n < 0 || g->m < 0 || g->n >= (1LL << 31) || g->m >= (1LL << 31) || k < 2 || k > kMaxK ||
-        !(eps > 0) || eps > 1000.0 || (g->n > 0 && !g->xadj) || (g->m > 0 && !g->adjncy))
+}  // extern "C"
+
+namespace upr {
+
+// (Re)binds a context to a graph: checks it, lays out the workspace (reusing
+// the context's device arena when it is large enough), copies the graph and
+// computes omega(I(v)).  Pinned host buffers and events are created once per
+// context.  On error the context is left unbound (n = -1) but reusable.
+upr_status bind_graph(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params &prm) {
+    if (!g || g->n < 0 || g->m < 0 || g->n >= (1LL << 31) || g->m >= (1LL << 31) || k < 2 || k > kMaxK ||
+        !(eps > 0) || eps > 1000.0 || (g->n > 0 && !g->xadj) || (g->m > 0 && !g->adjncy) || !params_ok(prm))
         return UPR_ERR_INVALID;
+    c->n = -1;
+    UPR_CUDA(cudaGetDevice(&c->device));
+    c->prm = prm;
+    c->s = (cudaStream_t)prm.stream;
+    c->eps_ppm = (int64_t)(eps * 1e6 + 0.5);
+    const int64_t n = g->n, m = g->m;
+    // host copies of xadj / vwgt for create-time decisions
+    std::vector<int64_t> xadj_h(n + 1, 0);
+    if (n > 0)
+        UPR_CUDA(cudaMemcpy(xadj_h.data(), g->xadj, sizeof(int64_t) * (n + 1),
+                            mem_kind(g->xadj) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    if (n > 0 && (xadj_h[0] != 0 || xadj_h[n] != m)) return UPR_ERR_INVALID;
+    for (int64_t v = 0; v < n; v++)
+        if (xadj_h[v + 1] < xadj_h[v]) return UPR_ERR_INVALID;
+    int64_t cmax = 1, total = n;
+    if (g->vwgt && n > 0) {
+        std::vector<int32_t> vw(n);
+        UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * n,
+                            mem_kind(g->vwgt) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        total = 0;
+        for (int32_t w : vw) {
+            if (w <= 0) return UPR_ERR_INVALID;
+            total += w;
+            cmax = std::max<int64_t>(cmax, w);
+        }
+    }
+    c->total_w = total;
+    c->cbits = bit_length((uint64_t)cmax);
+    const int64_t avg = (total + k - 1) / k;
+    c->Lmax = (int64_t)(((i128)avg * (1000000 + c->eps_ppm)) / 1000000);
+    std::vector<HubChunk> chunks;
+    for (int64_t v = 0; v < n; v++) {
+        const int64_t d = xadj_h[v + 1] - xadj_h[v];
+        if (d > kHubDegree)
+            for (int64_t b = xadj_h[v]; b < xadj_h[v + 1]; b += 8192)
+                chunks.push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
+    }
+    // static schedule of the tiled table build: runs of consecutive nodes
+    // with at most tile_nodes rows (<= 32 KB of shared memory) and at most
+    // kTileEntries non-hub adjacency entries; a hub closes its tile
+    std::vector<TableTile> tiles;
+    int32_t tile_nodes = 0;
+    if (k % 4 == 0) {
+        const int64_t kTileEntries = 4096;
+        tile_nodes = (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k));
+        int64_t v = 0;
+        while (v < n) {
+            TableTile t{xadj_h[v], xadj_h[v], (int32_t)v, (int32_t)v};
+            while (v < n && t.v1 - t.v0 < tile_nodes) {
+                const int64_t d = xadj_h[v + 1] - xadj_h[v];
+                if (d > kHubDegree) { t.v1 = (int32_t)(++v); break; }     // hub: row zero here, last in tile
+                if (t.e1 + d - t.e0 > kTileEntries && t.v1 > t.v0) break;
+                t.e1 += d;
+                t.v1 = (int32_t)(++v);
+            }
+            tiles.push_back(t);
+        }
+    }
+    c->m = m; c->k = k;
+    c->n = n;                       // layout needs the sizes
+    c->n_chunks = (int64_t)chunks.size();
+    c->n_tiles = (int64_t)tiles.size();
+    c->tile_nodes = tile_nodes;
+    Arena A;
+    layout(c, A);
+    if (!c->mem || c->mem_bytes < A.off) {
+        if (c->mem) { cudaFree(c->mem); c->mem = nullptr; c->mem_bytes = 0; }
+        if (cudaMalloc(&c->mem, A.off) != cudaSuccess) { cudaGetLastError(); c->n = -1; return UPR_ERR_OOM; }
+        c->mem_bytes = A.off;
+    }
+    A.base = (char *)c->mem; A.off = 0;
+    layout(c, A);
+    // pinned buffers and events are sized for kMaxK blocks, so a context
+    // re-bound to another graph keeps them
+    if (!c->h) {
+        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * (4 * (int64_t)kMaxK + 256)));
+        int64_t *base = c->h + 4 * (int64_t)kMaxK;
+        c->hF = base;                                           // 73
+        c->hcut = base + 80;                                    // 1
+        c->hbest = reinterpret_cast<long long *>(base + 88);    // 2
+        c->hctl = reinterpret_cast<RebalCtl *>(base + 96);      // 4
+        c->hcnt = reinterpret_cast<int32_t *>(base + 112);      // 64 ints
+    }
+    if (!c->h8) UPR_CUDA(cudaMallocHost((void **)&c->h8, 2 * (size_t)kMaxK + 64));
+    for (auto &ev : c->ev)
+        if (!ev) UPR_CUDA(cudaEventCreate(&ev));
+    cudaStream_t s = c->s;
+    copy_in(c->xadj, g->xadj, sizeof(int64_t) * (n + 1), s);
+    copy_in(c->adj, g->adjncy, sizeof(int32_t) * m, s);
+    if (g->adjwgt) copy_in(c->adjw, g->adjwgt, sizeof(int32_t) * m, s);
+    if (g->vwgt) copy_in(c->vwgt, g->vwgt, sizeof(int32_t) * n, s);
+    if (!chunks.empty())
+        UPR_CUDA(cudaMemcpyAsync(c->hub_chunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice,
+                                 s));
+    if (!tiles.empty())
+        UPR_CUDA(cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(TableTile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    c->G = GraphDev{n, m, k, c->xadj, c->adj, g->adjwgt ? c->adjw : nullptr, g->vwgt ? c->vwgt : nullptr, c->wI};
+    if (prm.validate) {
+        validate_graph(c->G, c->vacc, c->vflags, s);
+        uint64_t acc[2]; int32_t flags;
+        UPR_CUDA(cudaMemcpyAsync(acc, c->vacc, sizeof(acc), cudaMemcpyDeviceToHost, s));
+        UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+        UPR_CUDA(cudaStreamSynchronize(s));
+        if (flags != 0 || acc[0] != acc[1]) { c->n = -1; return UPR_ERR_INVALID; }
+    }
+    incident_weights(c->G, c->wI, c->scal, s);
+    read_i64(c, c->scal, 1, &c->wmax);
+    if (c->wmax > 0x7fffffffLL) { c->n = -1; return UPR_ERR_INVALID; }
+    c->gbits = std::max(1, bit_length((uint64_t)c->wmax));
+    if (1 + c->gbits + 2 * c->cbits > 63) { c->n = -1; return UPR_ERR_INVALID; }
+    UPR_CUDA(cudaMemsetAsync(c->tmp.ticket, 0, 64 * sizeof(unsigned int), s));
+    fill_i32(c->pos, n, INT32_MAX, s);
+    fill_i32(c->m_pos, n, -1, s);
+    fill_i32(c->r_to, n, -1, s);
+    UPR_CUDA(cudaStreamSynchronize(s));
+    return UPR_OK;
+}
+
+upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params *params) {
     upr_params prm;
     upr_params_default(&prm);
     if (params) prm = *params;
-    if (!params_ok(prm)) return UPR_ERR_INVALID;
-    upr_ctx *c = new (std::nothrow) upr_ctx();
-    if (!c) return UPR_ERR_OOM;
     try {
-        UPR_CUDA(cudaGetDevice(&c->device));
-        c->n = g->n; c->m = g->m; c->k = k; c->prm = prm;
-        c->s = (cudaStream_t)prm.stream;
-        c->eps_ppm = (int64_t)(eps * 1e6 + 0.5);
-        // host copies of xadj / vwgt for create-time decisions
-        std::vector<int64_t> xadj_h(c->n + 1, 0);
-        if (c->n > 0) {
-            UPR_CUDA(cudaMemcpy(xadj_h.data(), g->xadj, sizeof(int64_t) * (c->n + 1),
-                                mem_kind(g->xadj) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-        }
-        if (c->n > 0 && (xadj_h[0] != 0 || xadj_h[c->n] != c->m)) { free_ctx(c); return UPR_ERR_INVALID; }
-        for (int64_t v = 0; v < c->n; v++)
-            if (xadj_h[v + 1] < xadj_h[v]) { free_ctx(c); return UPR_ERR_INVALID; }
-        int64_t cmax = 1, total = c->n;
-        if (g->vwgt && c->n > 0) {
-            std::vector<int32_t> vw(c->n);
-            UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * c->n,
-                                mem_kind(g->vwgt) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-            total = 0;
-            for (int32_t w : vw) {
-                if (w <= 0) { free_ctx(c); return UPR_ERR_INVALID; }
-                total += w;
-                cmax = std::max<int64_t>(cmax, w);
-            }
-        }
-        c->total_w = total;
-        c->cbits = bit_length((uint64_t)cmax);
-        const int64_t avg = (total + k - 1) / k;
-        c->Lmax = (int64_t)(((i128)avg * (1000000 + c->eps_ppm)) / 1000000);
-        std::vector<HubChunk> chunks;
-        for (int64_t v = 0; v < c->n; v++) {
-            const int64_t d = xadj_h[v + 1] - xadj_h[v];
-            if (d > kHubDegree)
-                for (int64_t b = xadj_h[v]; b < xadj_h[v + 1]; b += 8192)
-                    chunks.push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
-        }
-        c->n_chunks = (int64_t)chunks.size();
-        // static schedule of the tiled table build: runs of consecutive nodes
-        // with at most tile_nodes rows (<= 64 KB of shared memory) and at most
-        // kTileEntries non-hub adjacency entries; a hub closes its tile
-        std::vector<TableTile> tiles;
-        if (k % 4 == 0) {
-            const int64_t kTileEntries = 4096;
-            c->tile_nodes = (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k));
-            int64_t v = 0;
-            while (v < c->n) {
-                TableTile t{xadj_h[v], xadj_h[v], (int32_t)v, (int32_t)v};
-                while (v < c->n && t.v1 - t.v0 < c->tile_nodes) {
-                    const int64_t d = xadj_h[v + 1] - xadj_h[v];
-                    if (d > kHubDegree) { t.v1 = (int32_t)(++v); break; }     // hub: row zero here, last in tile
-                    if (t.e1 + d - t.e0 > kTileEntries && t.v1 > t.v0) break;
-                    t.e1 += d;
-                    t.v1 = (int32_t)(++v);
-                }
-                tiles.push_back(t);
-            }
-        }
-        c->n_tiles = (int64_t)tiles.size();
-        Arena A;
-        layout(c, A);
-        if (cudaMalloc(&c->mem, A.off) != cudaSuccess) { cudaGetLastError(); free_ctx(c); return UPR_ERR_OOM; }
-        A.base = (char *)c->mem; A.off = 0;
-        layout(c, A);
-        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * (std::max<int64_t>(4 * k, 2 * kSlots + 64) + 256)));
-        {
-            int64_t *base = c->h + std::max<int64_t>(4 * k, 2 * kSlots + 64);
-            c->hF = base;                                           // 73
-            c->hcut = base + 80;                                    // 1
-            c->hbest = reinterpret_cast<long long *>(base + 88);    // 2
-            c->hctl = reinterpret_cast<RebalCtl *>(base + 96);      // 4
-            c->hcnt = reinterpret_cast<int32_t *>(base + 112);      // 64 ints
-        }
-        UPR_CUDA(cudaMallocHost((void **)&c->h8, 2 * (size_t)k + 64));
-        for (auto &e : c->ev) UPR_CUDA(cudaEventCreate(&e));
-        cudaStream_t s = c->s;
-        copy_in(c->xadj, g->xadj, sizeof(int64_t) * (c->n + 1), s);
-        copy_in(c->adj, g->adjncy, sizeof(int32_t) * c->m, s);
-        if (g->adjwgt) copy_in(c->adjw, g->adjwgt, sizeof(int32_t) * c->m, s);
-        if (g->vwgt) copy_in(c->vwgt, g->vwgt, sizeof(int32_t) * c->n, s);
-        if (!chunks.empty())
-            UPR_CUDA(cudaMemcpyAsync(c->hub_chunks, chunks.data(), sizeof(HubChunk) * chunks.size(),
-                                     cudaMemcpyHostToDevice, s));
-        if (!tiles.empty())
-            UPR_CUDA(cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(TableTile) * tiles.size(), cudaMemcpyHostToDevice, s));
-        c->G = GraphDev{c->n, c->m, k, c->xadj, c->adj, g->adjwgt ? c->adjw : nullptr, g->vwgt ? c->vwgt : nullptr,
-                        c->wI};
-        if (prm.validate) {
-            validate_graph(c->G, c->vacc, c->vflags, s);
-            uint64_t acc[2]; int32_t flags;
-            UPR_CUDA(cudaMemcpyAsync(acc, c->vacc, sizeof(acc), cudaMemcpyDeviceToHost, s));
-            UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
-            UPR_CUDA(cudaStreamSynchronize(s));
-            if (flags != 0 || acc[0] != acc[1]) { free_ctx(c); return UPR_ERR_INVALID; }
-        }
-        incident_weights(c->G, c->wI, c->scal, s);
-        read_i64(c, c->scal, 1, &c->wmax);
-        if (c->wmax > 0x7fffffffLL) { free_ctx(c); return UPR_ERR_INVALID; }
-        c->gbits = std::max(1, bit_length((uint64_t)c->wmax));
-        if (1 + c->gbits + 2 * c->cbits > 63) { free_ctx(c); return UPR_ERR_INVALID; }
-        UPR_CUDA(cudaMemsetAsync(c->tmp.ticket, 0, 64 * sizeof(unsigned int), s));
-        fill_i32(c->pos, c->n, INT32_MAX, s);
-        fill_i32(c->m_pos, c->n, -1, s);
-        fill_i32(c->r_to, c->n, -1, s);
-        UPR_CUDA(cudaStreamSynchronize(s));
+        return bind_graph(c, g, k, eps, prm);
     } catch (const CudaError &) {
-        free_ctx(c);
+        c->n = -1;
         return UPR_ERR_CUDA;
     } catch (const std::bad_alloc &) {
-        free_ctx(c);
+        c->n = -1;
         return UPR_ERR_OOM;
     }
+}
+
+}  // namespace upr
+
+extern "C" {
+
+upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_params *params, upr_ctx **out) {
+    if (!out) return UPR_ERR_INVALID;
+    upr_ctx *c = new (std::nothrow) upr_ctx();
+    if (!c) return UPR_ERR_OOM;
+    const upr_status st = upr::ctx_rebind(c, g, k, eps, params);
+    if (st != UPR_OK) { free_ctx(c); return st; }
     *out = c;
     return UPR_OK;
 }
@@ -670,7 +704,7 @@ upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_param
 void upr_destroy(upr_ctx *c) { free_ctx(c); }
 
 upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
-    if (!c || !part || !cut) return UPR_ERR_INVALID;
+    if (!c || c->n < 0 || !part || !cut) return UPR_ERR_INVALID;
     try {
         upr_status st = load_part(c, part);
         if (st != UPR_OK) return st;
@@ -686,7 +720,7 @@ upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block
 
 upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_stats *stats) {
     (void)seed;
-    if (!c || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
+    if (!c || c->n < 0 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
     const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
     if (c->prm.round_offset + rounds > total) return UPR_ERR_INVALID;
     upr_stats st{};
@@ -739,7 +773,7 @@ upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, 
 }
 
 upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int64_t *wI) {
-    if (!c || !part) return UPR_ERR_INVALID;
+    if (!c || c->n < 0 || !part) return UPR_ERR_INVALID;
     try {
         upr_status rc = load_part(c, part);
         if (rc != UPR_OK) return rc;
@@ -760,7 +794,8 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
 }
 
 upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int32_t rebalance_only, upr_trace *trace) {
-    if (!c || !part || !trace || R < 1 || R > 65536 || (!rebalance_only && (r < 1 || r > R))) return UPR_ERR_INVALID;
+    if (!c || c->n < 0 || !part || !trace || R < 1 || R > 65536 || (!rebalance_only && (r < 1 || r > R)))
+        return UPR_ERR_INVALID;
     int8_t *avail_d = nullptr;
     int32_t *slot_d = nullptr;
     upr_status rc = UPR_OK;

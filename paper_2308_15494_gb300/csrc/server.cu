@@ -44,6 +44,10 @@ struct Job {
 // Device bytes one context needs (the arena of engine.cu plus slack).
 size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k);
 
+namespace upr {
+upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params *params);
+}
+
 struct upr_server {
     upr_server_params p{};
     std::mutex mu;
@@ -60,6 +64,7 @@ struct upr_server {
         cudaSetDevice(device);
         cudaStream_t s = nullptr;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+        upr_ctx *ctx = nullptr;     // this slot's context, re-bound to every job it runs
         for (;;) {
             std::shared_ptr<Job> job;
             {
@@ -79,7 +84,7 @@ struct upr_server {
                 }
             }
             if (!job) break;
-            run(job.get(), s);
+            run(job.get(), s, &ctx);
             {
                 std::lock_guard<std::mutex> lk(mu);
                 in_use -= job->footprint;
@@ -88,10 +93,11 @@ struct upr_server {
             cv_work.notify_all();
             cv_done.notify_all();
         }
+        upr_destroy(ctx);
         if (s) cudaStreamDestroy(s);
     }
 
-    void run(Job *j, cudaStream_t s) {
+    void run(Job *j, cudaStream_t s, upr_ctx **ctx) {
         upr_graph g{};
         g.n = j->n; g.m = j->m;
         g.xadj = j->xadj.data();
@@ -100,12 +106,14 @@ struct upr_server {
         g.adjwgt = j->has_adjw ? j->adjw.data() : nullptr;
         upr_params prm = p.params;
         prm.stream = s;
-        upr_ctx *ctx = nullptr;
-        upr_status st = upr_create(&g, j->k, j->eps, &prm, &ctx);
+        // the slot's context keeps its device arena, pinned buffers and events
+        // between jobs, so admitting a job allocates only when it is larger
+        // than every job this slot ran before
+        upr_status st = *ctx ? upr::ctx_rebind(*ctx, &g, j->k, j->eps, &prm)
+                             : upr_create(&g, j->k, j->eps, &prm, ctx);
         if (st == UPR_OK) {
-            st = upr_refine(ctx, j->part.data(), j->rounds, j->seed, &j->stats);
+            st = upr_refine(*ctx, j->part.data(), j->rounds, j->seed, &j->stats);
             if (st == UPR_OK) j->cut = j->stats.cut_out;
-            upr_destroy(ctx);
         }
         // the graph copy is no longer needed
         std::vector<int64_t>().swap(j->xadj);
