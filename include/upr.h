@@ -137,7 +137,8 @@ upr_status upr_refine(upr_ctx *ctx, int32_t *part, int32_t rounds, uint64_t seed
 
 /* Exact cut and block weights (Sec. 2) of part (host or device, n entries).
  * *cut receives sum of omega over cut edges; block_weights (k entries, host,
- * may be NULL) receives c(V_b). Errors: UPR_ERR_INVALID, UPR_ERR_CUDA. */
+ * may be NULL) receives c(V_b). Errors: UPR_ERR_INVALID (also for a batch
+ * context: see upr_batch_cut), UPR_ERR_CUDA. */
 upr_status upr_cut(upr_ctx *ctx, const int32_t *part, int64_t *cut, int64_t *block_weights);
 
 /* Releases the context and all its device memory. NULL is ignored. */
@@ -165,6 +166,46 @@ void upr_destroy(upr_ctx *ctx);
  * not validated beyond that (see upr_create's validate). */
 upr_status upr_cut_noalloc(const upr_graph *g, int32_t k, const int32_t *part, void *stream, int64_t *cut,
                            int64_t *block_weights);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent graphs refined together.  The paper refines one
+ * graph; a batch runs the same synchronous rounds (Alg. 1, Sec. 4-6) on the
+ * disjoint union of its graphs with every step kept per graph: graph g owns
+ * its own k blocks and L_max, its candidates, penalties, rebalancing and move
+ * sequence involve its blocks only, and its best prefix (Sec. 4.1) is taken
+ * over its own moves.  So every graph's result equals upr_refine on that
+ * graph alone, while one launch of each step covers all graphs.
+ * ------------------------------------------------------------------------ */
+
+/* Creates one context for n_graphs graphs, all with k blocks (2 <= k <=
+ * 4096); eps[i] is graph i's imbalance.  The graphs are packed into one
+ * device CSR in order (graph i's nodes follow graph i-1's); each graph's
+ * arrays are read as in upr_create (host or device, local node ids) and may
+ * be freed on return.  Sums of n and of m must stay below 2^31 and
+ * n_graphs * k below 2^30.  Errors as upr_create (a graph with an invalid
+ * CSR makes the whole call fail). */
+upr_status upr_batch_create(const upr_graph *graphs, int32_t n_graphs, int32_t k, const double *eps,
+                            const upr_params *params, upr_ctx **out);
+
+/* Refines all graphs of a batch context.  part holds every graph's
+ * partition back to back (graph i at node offset sum of n of graphs < i,
+ * graph-local block ids in [0, k)), host or device, refined in place.
+ * status, cut_in and cut_out (n_graphs entries each, host, may be NULL)
+ * receive per graph: UPR_OK or UPR_ERR_INFEASIBLE (an imbalanced input that
+ * cannot be rebalanced: that graph's partition and cut stay as given), the
+ * cut before and after.  stats sums over graphs.  Returns UPR_OK unless the
+ * call itself fails (UPR_ERR_INVALID: a block id out of range, rounds < 0;
+ * UPR_ERR_CUDA).  Also accepts a one-graph context. */
+upr_status upr_batch_refine(upr_ctx *ctx, int32_t *part, int32_t rounds, uint64_t seed, upr_status *status,
+                            int64_t *cut_in, int64_t *cut_out, upr_stats *stats);
+
+/* Per-graph cut (n_graphs entries) and block weights (n_graphs * k entries,
+ * graph-major, may be NULL) of a packed partition as in upr_batch_refine. */
+upr_status upr_batch_cut(upr_ctx *ctx, const int32_t *part, int64_t *cut, int64_t *block_weights);
+
+/* Number of graphs, node offsets (n_graphs + 1 entries) and L_max of each
+ * graph (n_graphs entries); the pointers may be NULL. */
+upr_status upr_batch_info(const upr_ctx *ctx, int32_t *n_graphs, int64_t *node_offsets, int64_t *lmax);
 
 /* ------------------------------------------------------------------------
  * Serving: a host worker thread admits refinement jobs while device memory

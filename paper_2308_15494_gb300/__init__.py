@@ -80,6 +80,10 @@ SIGNATURES = {
     "upr_server_destroy": (None, [P]),
     "upr_debug_gain_table": (I32, [P, P, P, P]),
     "upr_debug_round": (I32, [P, P, I32, I32, I32, ctypes.POINTER(Trace)]),
+    "upr_batch_create": (I32, [ctypes.POINTER(Graph), I32, I32, P, ctypes.POINTER(Params), ctypes.POINTER(P)]),
+    "upr_batch_refine": (I32, [P, P, I32, U64, P, P, P, ctypes.POINTER(Stats)]),
+    "upr_batch_cut": (I32, [P, P, P, P]),
+    "upr_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),
 }
 
 _lib = None
@@ -263,6 +267,87 @@ def upr_debug_round(ctx: Context, part: np.ndarray, r: int, R: int, rebalance_on
     tr["I"] = (a["I_node"][:ns], a["I_from"][:ns], a["I_to"][:ns], a["I_gain"][:ns])
     tr["eligible"] = a["I_eligible"][: ns + 1].astype(bool)
     return rc, part, tr
+
+
+# --------------------------------------------------------------- batches
+@dataclass
+class BatchContext:
+    handle: ctypes.c_void_p
+    n_graphs: int
+    k: int
+    offsets: np.ndarray          # node offsets, n_graphs + 1
+    lmax: np.ndarray             # L_max per graph
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.upr_destroy(self.handle)
+            self.handle = None
+
+
+def upr_batch_create(graphs, k: int, eps, params: Optional[Params] = None, stream=None) -> BatchContext:
+    """upr_batch_create: graphs = [(xadj, adj, vwgt or None, adjw or None), ...]
+    (numpy or torch CUDA arrays, graph-local node ids), one eps or one per graph."""
+    lib = load()
+    ng = len(graphs)
+    arr = (Graph * max(ng, 1))()
+    for i, (xa, ad, vw, aw) in enumerate(graphs):
+        arr[i], _, _ = _graph_struct(xa, ad, vw, aw)
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (ng,)))
+    p = params if params is not None else upr_params_default()
+    if stream is not None:
+        p.stream = stream
+    elif not p.stream:
+        p.stream = _current_stream()
+    h = ctypes.c_void_p()
+    st = lib.upr_batch_create(arr, ng, k, _ptr(e), ctypes.byref(p), ctypes.byref(h))
+    if st != UPR_OK:
+        raise UprError(st, "upr_batch_create")
+    cnt = I32()
+    off = np.zeros(ng + 1, np.int64)
+    lm = np.zeros(max(ng, 1), np.int64)
+    lib.upr_batch_info(h, ctypes.byref(cnt), _ptr(off), _ptr(lm))
+    return BatchContext(h, ng, k, off, lm[:ng])
+
+
+def create_batch_from_workloads(ws, params: Optional[Params] = None, device: bool = False) -> BatchContext:
+    """One batch context for workloads that share k (their own eps each)."""
+    ks = {w.k for w in ws}
+    assert len(ks) == 1, "a batch holds graphs with one k"
+    graphs = []
+    for w in ws:
+        arrs = [w.xadj, w.adj, w.vwgt, w.adjw]
+        if device:
+            import torch
+            arrs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+        graphs.append(tuple(arrs))
+    return upr_batch_create(graphs, ws[0].k, [w.eps for w in ws], params=params)
+
+
+def upr_batch_refine(ctx: BatchContext, part, rounds: int, seed: int = 0):
+    """Refines the packed partition in place; returns (status, cut_in, cut_out, stats) arrays per graph."""
+    ng = ctx.n_graphs
+    status = np.zeros(max(ng, 1), np.int32)
+    cin = np.zeros(max(ng, 1), np.int64)
+    cout = np.zeros(max(ng, 1), np.int64)
+    st = Stats()
+    rc = load().upr_batch_refine(ctx.handle, _ptr(part), rounds, seed, _ptr(status), _ptr(cin), _ptr(cout),
+                                 ctypes.byref(st))
+    if rc != UPR_OK:
+        raise UprError(rc, "upr_batch_refine")
+    return status[:ng], cin[:ng], cout[:ng], st
+
+
+def upr_batch_cut(ctx: BatchContext, part) -> tuple[np.ndarray, np.ndarray]:
+    cut = np.zeros(max(ctx.n_graphs, 1), np.int64)
+    bw = np.zeros(max(ctx.n_graphs * ctx.k, 1), np.int64)
+    rc = load().upr_batch_cut(ctx.handle, _ptr(part), _ptr(cut), _ptr(bw))
+    if rc != UPR_OK:
+        raise UprError(rc, "upr_batch_cut")
+    return cut[: ctx.n_graphs], bw[: ctx.n_graphs * ctx.k].reshape(ctx.n_graphs, ctx.k)
 
 
 # --------------------------------------------------------------- serving

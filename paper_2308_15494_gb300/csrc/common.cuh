@@ -72,12 +72,16 @@ __device__ __forceinline__ void group_argmax(int64_t &score, int32_t &id) {
 // calls add() (key < 0 = nothing to add); lanes with equal keys are combined
 // with __match_any_sync and their leader adds the group's total to shared
 // memory; flush() adds the CTA's non-zero totals to the global counters.
+// With more than kMaxK blocks (a batch of graphs) the shared array would not
+// fit: `direct` then points at the global counters and the leaders add there.
 // Integer additions commute, so the result is independent of scheduling.
 struct BlockDelta {
     unsigned long long *s;
     int k;
+    unsigned long long *direct;
     __device__ __forceinline__ void init() {
-        for (int i = threadIdx.x; i < k; i += blockDim.x) s[i] = 0;
+        if (!direct)
+            for (int i = threadIdx.x; i < k; i += blockDim.x) s[i] = 0;
         __syncthreads();
     }
     __device__ __forceinline__ void add(int key, long long d) {
@@ -85,14 +89,20 @@ struct BlockDelta {
         long long tot = 0;
         for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, d, __ffs(m) - 1);
         if (key >= 0 && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0 && tot != 0)
-            atomicAdd(&s[key], (unsigned long long)tot);
+            atomicAdd(direct ? &direct[key] : &s[key], (unsigned long long)tot);
     }
     __device__ __forceinline__ void flush(unsigned long long *C) {
+        if (direct) return;
         __syncthreads();
         for (int i = threadIdx.x; i < k; i += blockDim.x)
             if (s[i]) atomicAdd(&C[i], s[i]);
     }
 };
+// Shared memory of a BlockDelta over K blocks, and the CTA's accumulator.
+inline size_t block_delta_smem(int64_t K) { return K <= kMaxK ? sizeof(unsigned long long) * (size_t)K : 0; }
+__device__ __forceinline__ BlockDelta make_block_delta(unsigned long long *smem, int K, unsigned long long *C) {
+    return K <= kMaxK ? BlockDelta{smem, K, nullptr} : BlockDelta{nullptr, K, C};
+}
 
 inline int device_sm_count() {
     static thread_local int cnt = 0, dev_cached = -1;

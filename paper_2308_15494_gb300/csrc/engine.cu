@@ -70,7 +70,9 @@ struct upr_ctx {
     int device = 0;
     int64_t n = 0, m = 0;
     int32_t k = 0;
-    int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;
+    int32_t ng = 1;                   // graphs bound (a batch when > 1)
+    int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
+    std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
     upr_params prm{};
     cudaStream_t s = nullptr;
@@ -82,6 +84,10 @@ struct upr_ctx {
     int64_t *xadj; int32_t *adj, *adjw, *vwgt, *wI;
     HubChunk *hub_chunks; int64_t n_chunks = 0;
     TableTile *tiles = nullptr; int64_t n_tiles = 0; int32_t tile_nodes = 0;
+    int64_t *Lb; int32_t *gid;          // [K] L_max per block; [n] graph of each node (batches)
+    int32_t *seg_beg, *seg_end, *over0_g, *light_g, *infeas_g, *inf0_g; long long *best_g, *best_j; int64_t *tot;
+    int32_t *part_in;                   // batches: the input partition (global ids)
+    int64_t *noff_d;                    // batches: [ng + 1] first node of each graph
     // state
     int32_t *part0, *part; int64_t *C0, *C, *cut; int32_t *W;
     int64_t *BW, *PW, *F;
@@ -121,8 +127,20 @@ struct upr_ctx {
 namespace {
 
 void layout(upr_ctx *c, Arena &A) {
-    const size_t n = (size_t)std::max<int64_t>(c->n, 1), m = (size_t)std::max<int64_t>(c->m, 1), k = (size_t)c->k;
+    const size_t n = (size_t)std::max<int64_t>(c->n, 1), m = (size_t)std::max<int64_t>(c->m, 1);
+    const size_t kr = (size_t)c->k;                   // table row width
+    const size_t k = (size_t)c->k * (size_t)c->ng;    // blocks (K)
+    const size_t ng = (size_t)c->ng;
     const size_t n2 = 2 * n;
+    c->Lb = A.take<int64_t>(k);
+    c->gid = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
+    c->part_in = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
+    c->noff_d = A.take<int64_t>(ng + 1);
+    for (int32_t **p : {&c->seg_beg, &c->seg_end, &c->over0_g, &c->light_g, &c->infeas_g, &c->inf0_g})
+        *p = A.take<int32_t>(ng);
+    c->best_g = A.take<long long>(ng);
+    c->best_j = A.take<long long>(ng);
+    c->tot = A.take<int64_t>(4);
     c->xadj = A.take<int64_t>(n + 1);
     c->adj = A.take<int32_t>(m);
     c->adjw = A.take<int32_t>(m);
@@ -134,8 +152,8 @@ void layout(upr_ctx *c, Arena &A) {
     c->part = A.take<int32_t>(n);
     c->C0 = A.take<int64_t>(k);
     c->C = A.take<int64_t>(k);
-    c->cut = A.take<int64_t>(4);
-    c->W = A.take<int32_t>(n * k);
+    c->cut = A.take<int64_t>(std::max<size_t>(ng, 4));
+    c->W = A.take<int32_t>(n * kr);
     c->BW = A.take<int64_t>(k * kSlots);
     c->PW = A.take<int64_t>(k * kSlots);
     c->F = A.take<int64_t>(kSlots);
@@ -208,9 +226,19 @@ int32_t read_count(upr_ctx *c, int slot) {
 }
 
 void read_i64(upr_ctx *c, const int64_t *src, int64_t cnt, int64_t *dst) {
-    UPR_CUDA(cudaMemcpyAsync(c->h, src, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, c->s));
+    if (cnt <= 4 * (int64_t)kMaxK) {           // through the pinned buffer
+        UPR_CUDA(cudaMemcpyAsync(c->h, src, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, c->s));
+        UPR_CUDA(cudaStreamSynchronize(c->s));
+        memcpy(dst, c->h, sizeof(int64_t) * cnt);
+    } else {
+        UPR_CUDA(cudaMemcpyAsync(dst, src, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, c->s));
+        UPR_CUDA(cudaStreamSynchronize(c->s));
+    }
+}
+
+void read_i32(upr_ctx *c, const int32_t *src, int64_t cnt, int32_t *dst) {
+    UPR_CUDA(cudaMemcpyAsync(dst, src, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, c->s));
     UPR_CUDA(cudaStreamSynchronize(c->s));
-    memcpy(dst, c->h, sizeof(int64_t) * cnt);
 }
 
 struct RoundInfo {
@@ -244,8 +272,9 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     cudaStream_t s = c->s;
     const GraphDev &G = c->G;
     const int64_t n = c->n;
-    const int32_t k = c->k;
-    const int kbits = std::max(1, bit_length((uint64_t)(k - 1)));
+    const int32_t K = G.K();
+    const bool batch = c->ng > 1;
+    const int kbits = std::max(1, bit_length((uint64_t)(K - 1)));
     upr_trace *T = tr ? tr->t : nullptr;
     int32_t *cnt = c->counts;
     RebalCtl *ctl = c->ctl;
@@ -254,7 +283,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
 
     UPR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * CNT_SLOTS, s));
     UPR_CUDA(cudaMemcpyAsync(c->part, c->part0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-    UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * k, cudaMemcpyDeviceToDevice, s));
+    UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
     // ---- (a) gain table of the round-start partition
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
     gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
@@ -267,7 +296,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
                 tr ? tr->slot_d : nullptr, s);
         penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
         UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
-        Penalty pen{c->PW, c->F, c->C0, c->Lmax};
+        Penalty pen{c->PW, c->F, c->C0, c->Lb};
         // ---- (b2) best move per boundary node
         select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, s);
         select_flags(c->flags, c->idxA, cnt + CNT_CAND, cN, c->tmp, s);
@@ -297,13 +326,14 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     UPR_CUDA(cudaEventRecord(c->ev[5], s));
 
     // ---- (d) rebalancing sub-rounds
-    rebalance_init(c->C, k, c->Lmax, c->excl_d, ctl, s);
+    rebalance_init(G, c->C, c->excl_d, ctl, s);
     rebalance_flag_in_blocks(c->part, n, c->excl_d, c->flags, s);
     select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
-    const RebalState st{c->C, c->over_d, c->excl_d, &ctl->light, c->Lmax};
+    int32_t *light = batch ? c->light_g : &ctl->light;
+    const RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
     const Count cP{cnt + CNT_P, n}, cS{cnt + CNT_S, n};
     for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
-        rebalance_begin(c->C, k, c->Lmax, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, h, c->prm.max_subrounds, ctl,
+        rebalance_begin(G, c->C, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, h, c->prm.max_subrounds, ctl, light,
                         s);
         rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain, c->flags, s);
         select_flags(c->flags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
@@ -332,7 +362,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
                         c->R_from, c->R_to, c->R_sub, c->r_to, c->r_at, n, s);
         table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
                    c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
-        rebalance_end(k, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
+        rebalance_end(G, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
         UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
         if (c->hctl->stopped) break;
@@ -343,10 +373,10 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     const int32_t *dM = cnt + CNT_M, *dR = &ctl->nR;
     count_affine(dM, 2, nullptr, 0, cnt + CNT_EVM, s);
     count_affine(dM, 1, dR, 0, cnt + CNT_X, s);
-    UPR_CUDA(cudaMemsetAsync(c->rbeg, 0, sizeof(int32_t) * k, s));
-    UPR_CUDA(cudaMemsetAsync(c->rend, 0, sizeof(int32_t) * k, s));
-    UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
-    UPR_CUDA(cudaMemsetAsync(c->eend, 0, sizeof(int32_t) * k, s));
+    UPR_CUDA(cudaMemsetAsync(c->rbeg, 0, sizeof(int32_t) * K, s));
+    UPR_CUDA(cudaMemsetAsync(c->rend, 0, sizeof(int32_t) * K, s));
+    UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * K, s));
+    UPR_CUDA(cudaMemsetAsync(c->eend, 0, sizeof(int32_t) * K, s));
     uint64_t *kRB; uint32_t *RB;
     seq_rb_keys(c->R_from, dR, n, c->sb[0].k, c->sb[0].v, s);
     c->sb[0].run(Count{dR, n}, kbits, c->tmp, s, &kRB, &RB);
@@ -358,13 +388,13 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     c->sb[1].run(cEVM, kbits, c->tmp, s, &kEV, &EV);
     seq_ev_delta(c->M_node, EV, kEV, dM, n, G.vwgt, c->delta, c->ebeg, c->eend, s);
     exclusive_sum_i64(c->delta, c->d_excl, cEVM, c->tmp, s);
-    seq_ev_need(EV, kEV, dM, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->rbeg, c->rend, c->c_excl,
+    seq_ev_need(EV, kEV, dM, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lb, c->rbeg, c->rend, c->c_excl,
                 c->c_sorted, c->packed, s);
     inclusive_max_u64(c->packed, c->qmax, cEVM, c->tmp, s);
     seq_ev_emit(EV, kEV, dM, n, c->qmax, c->ebeg, c->emit, c->qbefore, s);
     exclusive_sum_i32(c->emit, c->em_excl, Count{dM, n}, c->tmp, s);
-    seq_block_final(k, c->ebeg, c->eend, c->qmax, c->rbeg, c->rend, c->qfin, c->left, s);
-    exclusive_sum_i32(c->left, c->left_excl, fixed(k), c->tmp, s);
+    seq_block_final(K, c->ebeg, c->eend, c->qmax, c->rbeg, c->rend, c->qfin, c->left, s);
+    exclusive_sum_i32(c->left, c->left_excl, fixed(K), c->tmp, s);
     seq_place_m(c->M_node, c->M_from, c->M_to, dM, n, c->em_excl, c->pos_m, c->X_node, c->X_from, c->X_to, c->X_isr,
                 s);
     seq_place_r(c->R_node, c->R_from, c->R_to, RB, dR, n, c->rbeg, EV, c->ebeg, c->eend, c->qmax, c->pos_m, c->qfin,
@@ -377,35 +407,50 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     select_flags(c->flags2, c->idxD, cnt + CNT_I, cX, c->tmp, s);
     const int32_t *dI = cnt + CNT_I;
     seq_build_I(c->idxD, dI, n, c->X_node, c->final_to, c->part0, c->I_node, c->I_from, c->I_to, c->pos, c->dest, s);
+    // a batch: each graph's moves are a subsequence of I in its own order;
+    // a stable sort by graph makes them contiguous (X_* are free by now)
+    const int32_t *Iv = c->I_node, *If = c->I_from, *It = c->I_to;
+    if (batch) {
+        seq_sort_by_graph(G, c->I_node, c->I_from, c->I_to, dI, n, c->sb[0].k, c->sb[0].v, c->sb[0].ka, c->sb[0].va,
+                          c->tmp, c->X_node, c->X_from, c->X_to, c->pos, c->dest, c->seg_beg, c->seg_end, s);
+        Iv = c->X_node; If = c->X_from; It = c->X_to;
+    }
 
     // ---- (c2) exact gains, balanced prefixes, best prefix
-    seq_gains(G, c->I_node, c->I_from, c->I_to, dI, n, c->pos, c->dest, c->part0, c->I_gain, c->hub_chunks,
-              c->n_chunks, s);
+    seq_gains(G, Iv, If, It, dI, n, c->pos, c->dest, c->part0, c->I_gain, c->hub_chunks, c->n_chunks, s);
     inclusive_sum_i64(c->I_gain, c->Gsum, Count{dI, n}, c->tmp, s);
     count_affine(dI, 2, nullptr, 0, cnt + CNT_EVI, s);
     count_affine(dI, 1, nullptr, 1, cnt + CNT_I1, s);
     uint64_t *kE; uint32_t *E;
     const Count cEVI{cnt + CNT_EVI, 2 * n};
-    seq_iev_keys(c->I_from, c->I_to, dI, n, c->sb[2].k, c->sb[2].v, s);
+    seq_iev_keys(If, It, dI, n, c->sb[2].k, c->sb[2].v, s);
     c->sb[2].run(cEVI, kbits, c->tmp, s, &kE, &E);
-    UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * k, s));
-    seq_iev_delta(c->I_node, E, kE, dI, n, G.vwgt, c->delta, c->ebeg, s);
+    UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * K, s));
+    seq_iev_delta(Iv, E, kE, dI, n, G.vwgt, c->delta, c->ebeg, s);
     exclusive_sum_i64(c->delta, c->d_excl, cEVI, c->tmp, s);
     clear_count(c->diff, dI, 1, n, s);
-    seq_iev_transitions(E, kE, dI, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lmax, c->diff, s);
+    seq_iev_transitions(E, kE, dI, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lb, c->diff, s);
     exclusive_sum_i32(c->diff, c->diff_excl, Count{cnt + CNT_I1, n + 1}, c->tmp, s);
-    count_over(c->C0, k, c->Lmax, cnt + CNT_OVER0, s);
-    seq_best(c->Gsum, c->diff, c->diff_excl, dI, n, cnt + CNT_OVER0, c->best_parts, c->best, cnt + CNT_INFEAS, s);
     UPR_CUDA(cudaMemcpyAsync(c->hcut, c->cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));   // cut before the round
+    if (!batch) {
+        count_over(G, c->C0, cnt + CNT_OVER0, s);
+        seq_best(c->Gsum, c->diff, c->diff_excl, dI, n, cnt + CNT_OVER0, c->best_parts, c->best, cnt + CNT_INFEAS, s);
+    } else {
+        count_over(G, c->C0, c->over0_g, s);
+        seq_best_seg(G, Iv, dI, n, c->seg_beg, c->Gsum, c->diff, c->diff_excl, c->over0_g, c->best_g, c->best_j, c->cut,
+                     c->infeas_g, c->tot, s);
+    }
     // reset node-indexed markers for the next round
     reset_nodes(c->I_node, dI, n, c->pos, INT32_MAX, s);
     reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
     reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
-    seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
+    if (!batch) seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
+    else seq_apply_prefix_seg(G, Iv, If, It, dI, n, c->seg_beg, c->best_j, c->part0, c->C0, s);
     UPR_CUDA(cudaEventRecord(c->ev[7], s));
     UPR_CUDA(cudaMemcpyAsync(c->hcnt, cnt, sizeof(int32_t) * CNT_SLOTS, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
-    UPR_CUDA(cudaMemcpyAsync(c->hbest, c->best, sizeof(long long) * 2, cudaMemcpyDeviceToHost, s));
+    if (!batch) UPR_CUDA(cudaMemcpyAsync(c->hbest, c->best, sizeof(long long) * 2, cudaMemcpyDeviceToHost, s));
+    else UPR_CUDA(cudaMemcpyAsync(c->hbest, c->tot, sizeof(long long) * 3, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaStreamSynchronize(s));
     {
         float a = 0, b = 0, d = 0, t = 0;
@@ -423,9 +468,11 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     ri.subrounds = c->hctl->subrounds;
     ri.n_inter = hc[CNT_X];
     ri.n_seq = hc[CNT_I];
-    const bool infeasible = hc[CNT_INFEAS] != 0;
-    ri.best_len = infeasible ? 0 : c->hbest[1];
-    ri.best_gain = infeasible ? 0 : c->hbest[0];
+    // one graph: an infeasible round applies nothing and is an error; a
+    // batch records it per graph (infeas_g) and the round goes on
+    const bool infeasible = !batch && hc[CNT_INFEAS] != 0;
+    ri.best_len = infeasible ? 0 : batch ? c->hbest[0] : c->hbest[1];
+    ri.best_gain = infeasible ? 0 : batch ? c->hbest[1] : c->hbest[0];
     if (log_enabled())
         fprintf(stderr, "upr round %d: candidates %lld moves %lld rebalance moves %lld in %d sub-rounds, "
                         "sequence %lld, applied %lld (gain %lld)\n",
@@ -438,7 +485,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         if (!rebalance_only) {
             d2h(T->avail, tr->avail_d, n, s);
             d2h(T->slot, tr->slot_d, sizeof(int32_t) * n, s);
-            d2h(T->bucket, c->BW, sizeof(int64_t) * k * kSlots, s);
+            d2h(T->bucket, c->BW, sizeof(int64_t) * K * kSlots, s);
             if (T->factor) memcpy(T->factor, c->hF, sizeof(int64_t) * kSlots);
             d2h(T->cand_target, c->cand_tgt, sizeof(int32_t) * n, s);
             d2h(T->cand_s0, c->cand_s0, sizeof(int64_t) * n, s);
@@ -491,6 +538,24 @@ __global__ void k_check_part(const int32_t *part, int64_t n, int32_t k, int32_t 
     if (v < n && (part[v] < 0 || part[v] >= k)) atomicOr(bad, 1);
 }
 
+// batches: graph-local block ids -> global ids (and a copy of the input)
+__global__ void k_part_to_global(int32_t *part, const int32_t *gid, int64_t n, int32_t k, int32_t *copy) {
+    UPR_FOR(v, n) {
+        const int32_t p = part[v] + gid[v] * k;
+        part[v] = p;
+        copy[v] = p;
+    }
+}
+
+// batches: global -> graph-local ids; graphs flagged in keep_input get their input back
+__global__ void k_part_to_local(const int32_t *part, const int32_t *part_in, const int32_t *gid,
+                                const int32_t *keep_input, int64_t n, int32_t k, int32_t *out) {
+    UPR_FOR(v, n) {
+        const int32_t g = gid[v];
+        out[v] = (keep_input[g] ? part_in[v] : part[v]) - g * k;
+    }
+}
+
 upr_status load_part(upr_ctx *c, const int32_t *part) {
     copy_in(c->part0, part, sizeof(int32_t) * c->n, c->s);
     UPR_CUDA(cudaMemsetAsync(c->counts + 7, 0, sizeof(int32_t), c->s));
@@ -499,8 +564,100 @@ upr_status load_part(upr_ctx *c, const int32_t *part) {
         UPR_LAUNCH_CHECK();
     }
     if (read_count(c, 7)) return UPR_ERR_INVALID;
+    if (c->ng > 1 && c->n > 0) {
+        k_part_to_global<<<grid_for(c->n), 256, 0, c->s>>>(c->part0, c->gid, c->n, c->k, c->part_in);
+        UPR_LAUNCH_CHECK();
+    }
     block_weights(c->G, c->part0, c->C0, c->s);
     edge_cut(c->G, c->part0, c->cut, c->s);
+    return UPR_OK;
+}
+
+// Writes the partition (graph-local ids) to `part`; in a batch, graphs with
+// keep_input[g] != 0 (host array) get their input partition back.
+void store_part(upr_ctx *c, int32_t *part, const std::vector<int32_t> &keep_input) {
+    if (c->ng == 1) {
+        copy_out(part, c->part0, sizeof(int32_t) * c->n, c->s);
+        return;
+    }
+    UPR_CUDA(cudaMemcpyAsync(c->inf0_g, keep_input.data(), sizeof(int32_t) * c->ng, cudaMemcpyHostToDevice, c->s));
+    if (c->n > 0) {
+        k_part_to_local<<<grid_for(c->n), 256, 0, c->s>>>(c->part0, c->part_in, c->gid, c->inf0_g, c->n, c->k, c->part);
+        UPR_LAUNCH_CHECK();
+    }
+    copy_out(part, c->part, sizeof(int32_t) * c->n, c->s);
+    UPR_CUDA(cudaStreamSynchronize(c->s));      // keep_input is host memory
+}
+
+void add_round(upr_stats &st, const RoundInfo &ri, bool repair) {
+    st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
+    st.n_rebalance_moves += ri.n_rebal; st.subrounds += ri.subrounds; st.n_sequence += ri.n_seq;
+    st.n_applied += ri.best_len;
+    if (repair) return;
+    st.rounds_run++;
+    st.n_candidates += ri.n_cand; st.n_moves += ri.n_moves;
+    st.ms_select += ri.ms_select; st.ms_rebalance += ri.ms_rebalance; st.ms_sequence += ri.ms_sequence;
+}
+
+/*
+ * upr_refine and upr_batch_refine.  One graph: an infeasible input is an
+ * error (part unchanged).  A batch: per-graph status; an infeasible graph
+ * keeps its input partition and cut, the others go on.  cut_in / cut_out /
+ * status (nullable) have ng entries.
+ */
+upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *stats, upr_status *status,
+                       int64_t *cut_in, int64_t *cut_out) {
+    const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
+    if (c->prm.round_offset + rounds > total) return UPR_ERR_INVALID;
+    const int32_t ng = c->ng, K = c->G.K();
+    upr_stats st{};
+    const auto t_host0 = std::chrono::steady_clock::now();
+    const long long launches0 = g_upr_launches.load();
+    UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
+    upr_status rc = load_part(c, part);
+    if (rc != UPR_OK) return rc;
+    std::vector<int64_t> cin(ng), cout(ng), C0h(K);
+    read_i64(c, c->cut, ng, cin.data());
+    read_i64(c, c->C0, K, C0h.data());
+    st.cut_in = 0;
+    for (int64_t x : cin) st.cut_in += x;
+    bool balanced = true;
+    for (int32_t b = 0; b < K; b++) balanced = balanced && C0h[b] <= c->Lmax_g[b / c->k];
+    std::vector<int32_t> keep(ng, 0);
+    if (!balanced) {
+        RoundInfo ri;
+        rc = run_round(c, 0, total, true, ri, nullptr);
+        add_round(st, ri, true);
+        if (rc != UPR_OK) return rc;
+        if (ng > 1) read_i32(c, c->infeas_g, ng, keep.data());
+        st.repaired_input = 1;
+    }
+    for (int32_t i = 1; i <= rounds; i++) {
+        RoundInfo ri;
+        rc = run_round(c, c->prm.round_offset + i, total, false, ri, nullptr);
+        if (rc != UPR_OK) return rc;
+        add_round(st, ri, false);
+    }
+    store_part(c, part, keep);
+    read_i64(c, c->cut, ng, cout.data());
+    st.cut_out = 0;
+    for (int32_t g = 0; g < ng; g++) {
+        if (keep[g]) cout[g] = cin[g];
+        st.cut_out += cout[g];
+        if (status) status[g] = keep[g] ? UPR_ERR_INFEASIBLE : UPR_OK;
+        if (cut_in) cut_in[g] = cin[g];
+        if (cut_out) cut_out[g] = cout[g];
+    }
+    UPR_CUDA(cudaEventRecord(c->ev[3], c->s));
+    UPR_CUDA(cudaEventSynchronize(c->ev[3]));
+    float ms = 0;
+    UPR_CUDA(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+    st.ms_device = ms;
+    st.kernel_launches = (int32_t)(g_upr_launches.load() - launches0);
+    st.ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
+    st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
+                          4 * c->n * (int64_t)c->k;
+    if (stats) *stats = st;
     return UPR_OK;
 }
 
@@ -546,44 +703,73 @@ static bool params_ok(const upr_params &p) {
 
 namespace upr {
 
-// (Re)binds a context to a graph: checks it, lays out the workspace (reusing
-// the context's device arena when it is large enough), copies the graph and
-// computes omega(I(v)).  Pinned host buffers and events are created once per
-// context.  On error the context is left unbound (n = -1) but reusable.
-upr_status bind_graph(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params &prm) {
-    if (!g || g->n < 0 || g->m < 0 || g->n >= (1LL << 31) || g->m >= (1LL << 31) || k < 2 || k > kMaxK ||
-        !(eps > 0) || eps > 1000.0 || (g->n > 0 && !g->xadj) || (g->m > 0 && !g->adjncy) || !params_ok(prm))
+// (Re)binds a context to one graph (ng = 1) or to a batch of ng graphs packed
+// into one CSR: checks them, lays out the workspace (reusing the context's
+// device arena when it is large enough), copies the graphs and computes
+// omega(I(v)).  Pinned host buffers and events are created once per context.
+// On error the context is left unbound (n = -1) but reusable.
+upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
+                       const upr_params &prm) {
+    if (!gs || !eps || ng < 1 || k < 2 || k > kMaxK || (int64_t)ng * k >= (1LL << 30) || !params_ok(prm))
         return UPR_ERR_INVALID;
+    int64_t n = 0, m = 0;
+    bool any_adjw = false, any_vwgt = false;
+    for (int32_t i = 0; i < ng; i++) {
+        const upr_graph *g = &gs[i];
+        if (g->n < 0 || g->m < 0 || !(eps[i] > 0) || eps[i] > 1000.0 || (g->n > 0 && !g->xadj) ||
+            (g->m > 0 && !g->adjncy))
+            return UPR_ERR_INVALID;
+        n += g->n;
+        m += g->m;
+        any_adjw = any_adjw || g->adjwgt;
+        any_vwgt = any_vwgt || g->vwgt;
+    }
+    if (n >= (1LL << 31) || m >= (1LL << 31)) return UPR_ERR_INVALID;
     c->n = -1;
     UPR_CUDA(cudaGetDevice(&c->device));
     c->prm = prm;
     c->s = (cudaStream_t)prm.stream;
-    c->eps_ppm = (int64_t)(eps * 1e6 + 0.5);
-    const int64_t n = g->n, m = g->m;
-    // host copies of xadj / vwgt for create-time decisions
+    c->ng = ng;
+    c->eps_ppm = (int64_t)(eps[0] * 1e6 + 0.5);
+    // host copy of the packed xadj and the per-graph sums for create-time decisions
     std::vector<int64_t> xadj_h(n + 1, 0);
-    if (n > 0)
-        UPR_CUDA(cudaMemcpy(xadj_h.data(), g->xadj, sizeof(int64_t) * (n + 1),
-                            mem_kind(g->xadj) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-    if (n > 0 && (xadj_h[0] != 0 || xadj_h[n] != m)) return UPR_ERR_INVALID;
-    for (int64_t v = 0; v < n; v++)
-        if (xadj_h[v + 1] < xadj_h[v]) return UPR_ERR_INVALID;
-    int64_t cmax = 1, total = n;
-    if (g->vwgt && n > 0) {
-        std::vector<int32_t> vw(n);
-        UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * n,
-                            mem_kind(g->vwgt) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-        total = 0;
-        for (int32_t w : vw) {
-            if (w <= 0) return UPR_ERR_INVALID;
-            total += w;
-            cmax = std::max<int64_t>(cmax, w);
+    c->noff.assign(ng + 1, 0);
+    c->Lmax_g.assign(ng, 0);
+    std::vector<int64_t> eoff(ng + 1, 0);
+    int64_t cmax = 1;
+    for (int32_t i = 0; i < ng; i++) {
+        const upr_graph *g = &gs[i];
+        const int64_t gn = g->n, v0 = c->noff[i], e0 = eoff[i];
+        c->noff[i + 1] = v0 + gn;
+        eoff[i + 1] = e0 + g->m;
+        if (gn > 0) {
+            UPR_CUDA(cudaMemcpy(xadj_h.data() + v0, g->xadj, sizeof(int64_t) * (gn + 1),
+                                mem_kind(g->xadj) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+            if (xadj_h[v0] != 0 || xadj_h[v0 + gn] != g->m) return UPR_ERR_INVALID;
+            for (int64_t v = v0; v < v0 + gn; v++)
+                if (xadj_h[v + 1] < xadj_h[v]) return UPR_ERR_INVALID;
+            for (int64_t v = v0; v <= v0 + gn; v++) xadj_h[v] += e0;
         }
+        xadj_h[v0 + gn] = e0 + g->m;
+        int64_t total = gn;
+        if (g->vwgt && gn > 0) {
+            std::vector<int32_t> vw(gn);
+            UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * gn,
+                                mem_kind(g->vwgt) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+            total = 0;
+            for (int32_t w : vw) {
+                if (w <= 0) return UPR_ERR_INVALID;
+                total += w;
+                cmax = std::max<int64_t>(cmax, w);
+            }
+        }
+        const int64_t eps_ppm = (int64_t)(eps[i] * 1e6 + 0.5);
+        const int64_t avg = (total + k - 1) / k;
+        c->Lmax_g[i] = (int64_t)(((i128)avg * (1000000 + eps_ppm)) / 1000000);
+        if (i == 0) c->total_w = total;
     }
-    c->total_w = total;
+    c->Lmax = c->Lmax_g[0];
     c->cbits = bit_length((uint64_t)cmax);
-    const int64_t avg = (total + k - 1) / k;
-    c->Lmax = (int64_t)(((i128)avg * (1000000 + c->eps_ppm)) / 1000000);
     std::vector<HubChunk> chunks;
     for (int64_t v = 0; v < n; v++) {
         const int64_t d = xadj_h[v + 1] - xadj_h[v];
@@ -593,7 +779,8 @@ upr_status bind_graph(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
     }
     // static schedule of the tiled table build: runs of consecutive nodes
     // with at most tile_nodes rows (<= 32 KB of shared memory) and at most
-    // kTileEntries non-hub adjacency entries; a hub closes its tile
+    // kTileEntries non-hub adjacency entries; a hub closes its tile.  Rows
+    // are independent, so a tile may span two graphs of a batch.
     std::vector<TableTile> tiles;
     int32_t tile_nodes = 0;
     if (k % 4 == 0) {
@@ -633,7 +820,7 @@ upr_status bind_graph(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
         int64_t *base = c->h + 4 * (int64_t)kMaxK;
         c->hF = base;                                           // 73
         c->hcut = base + 80;                                    // 1
-        c->hbest = reinterpret_cast<long long *>(base + 88);    // 2
+        c->hbest = reinterpret_cast<long long *>(base + 88);    // 3
         c->hctl = reinterpret_cast<RebalCtl *>(base + 96);      // 4
         c->hcnt = reinterpret_cast<int32_t *>(base + 112);      // 64 ints
     }
@@ -641,16 +828,41 @@ upr_status bind_graph(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
     for (auto &ev : c->ev)
         if (!ev) UPR_CUDA(cudaEventCreate(&ev));
     cudaStream_t s = c->s;
-    copy_in(c->xadj, g->xadj, sizeof(int64_t) * (n + 1), s);
-    copy_in(c->adj, g->adjncy, sizeof(int32_t) * m, s);
-    if (g->adjwgt) copy_in(c->adjw, g->adjwgt, sizeof(int32_t) * m, s);
-    if (g->vwgt) copy_in(c->vwgt, g->vwgt, sizeof(int32_t) * n, s);
+    if (ng == 1) {
+        copy_in(c->xadj, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
+    } else {
+        UPR_CUDA(cudaMemcpyAsync(c->xadj, xadj_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    }
+    for (int32_t i = 0; i < ng; i++) {
+        const upr_graph *g = &gs[i];
+        const int64_t v0 = c->noff[i], e0 = eoff[i];
+        copy_in(c->adj + e0, g->adjncy, sizeof(int32_t) * g->m, s);
+        if (g->adjwgt) copy_in(c->adjw + e0, g->adjwgt, sizeof(int32_t) * g->m, s);
+        else if (any_adjw) fill_i32(c->adjw + e0, g->m, 1, s);
+        if (g->vwgt) copy_in(c->vwgt + v0, g->vwgt, sizeof(int32_t) * g->n, s);
+        else if (any_vwgt) fill_i32(c->vwgt + v0, g->n, 1, s);
+    }
+    {
+        std::vector<int64_t> Lb((size_t)ng * k);
+        for (int32_t i = 0; i < ng; i++)
+            for (int32_t b = 0; b < k; b++) Lb[(size_t)i * k + b] = c->Lmax_g[i];
+        UPR_CUDA(cudaMemcpyAsync(c->Lb, Lb.data(), sizeof(int64_t) * Lb.size(), cudaMemcpyHostToDevice, s));
+        UPR_CUDA(cudaStreamSynchronize(s));     // Lb is a local vector
+    }
     if (!chunks.empty())
         UPR_CUDA(cudaMemcpyAsync(c->hub_chunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice,
                                  s));
     if (!tiles.empty())
         UPR_CUDA(cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(TableTile) * tiles.size(), cudaMemcpyHostToDevice, s));
-    c->G = GraphDev{n, m, k, c->xadj, c->adj, g->adjwgt ? c->adjw : nullptr, g->vwgt ? c->vwgt : nullptr, c->wI};
+    const int32_t kmask = ng == 1 ? -1 : ((k & (k - 1)) == 0 ? k - 1 : 0);
+    c->G = GraphDev{n,      m,        k,       ng,   kmask, c->xadj, c->adj, any_adjw ? c->adjw : nullptr,
+                    any_vwgt ? c->vwgt : nullptr, c->wI, c->Lb, c->gid};
+    if (ng > 1) {
+        // node -> graph, and graph-local neighbour ids made global
+        UPR_CUDA(cudaMemcpyAsync(c->noff_d, c->noff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
+        pack_batch(c->G, c->noff_d, c->gid, c->adj, s);
+        UPR_CUDA(cudaStreamSynchronize(s));     // noff is host memory that may be re-assigned
+    }
     if (prm.validate) {
         validate_graph(c->G, c->vacc, c->vflags, s);
         uint64_t acc[2]; int32_t flags;
@@ -672,12 +884,10 @@ upr_status bind_graph(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
     return UPR_OK;
 }
 
-upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params *params) {
-    upr_params prm;
-    upr_params_default(&prm);
-    if (params) prm = *params;
+template <typename F>
+upr_status guarded(upr_ctx *c, F f) {
     try {
-        return bind_graph(c, g, k, eps, prm);
+        return f();
     } catch (const CudaError &) {
         c->n = -1;
         return UPR_ERR_CUDA;
@@ -685,6 +895,23 @@ upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
         c->n = -1;
         return UPR_ERR_OOM;
     }
+}
+
+upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params *params) {
+    upr_params prm;
+    upr_params_default(&prm);
+    if (params) prm = *params;
+    if (!g) return UPR_ERR_INVALID;
+    if (g->n >= (1LL << 31) || g->m >= (1LL << 31)) return UPR_ERR_INVALID;
+    return guarded(c, [&] { return bind_graphs(c, g, 1, k, &eps, prm); });
+}
+
+upr_status ctx_rebind_batch(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
+                            const upr_params *params) {
+    upr_params prm;
+    upr_params_default(&prm);
+    if (params) prm = *params;
+    return guarded(c, [&] { return bind_graphs(c, gs, ng, k, eps, prm); });
 }
 
 }  // namespace upr
@@ -704,7 +931,7 @@ upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_param
 void upr_destroy(upr_ctx *c) { free_ctx(c); }
 
 upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
-    if (!c || c->n < 0 || !part || !cut) return UPR_ERR_INVALID;
+    if (!c || c->n < 0 || c->ng != 1 || !part || !cut) return UPR_ERR_INVALID;
     try {
         upr_status st = load_part(c, part);
         if (st != UPR_OK) return st;
@@ -720,60 +947,70 @@ upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block
 
 upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_stats *stats) {
     (void)seed;
-    if (!c || c->n < 0 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
-    const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
-    if (c->prm.round_offset + rounds > total) return UPR_ERR_INVALID;
-    upr_stats st{};
-    const auto t_host0 = std::chrono::steady_clock::now();
-    const long long launches0 = g_upr_launches.load();
+    if (!c || c->n < 0 || c->ng != 1 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
     try {
-        UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
-        upr_status rc = load_part(c, part);
-        if (rc != UPR_OK) return rc;
-        read_i64(c, c->cut, 1, &st.cut_in);
-        std::vector<int64_t> C0h(c->k);
-        read_i64(c, c->C0, c->k, C0h.data());
-        bool balanced = true;
-        for (int32_t b = 0; b < c->k; b++) balanced = balanced && C0h[b] <= c->Lmax;
-        if (!balanced) {
-            RoundInfo ri;
-            rc = run_round(c, 0, total, true, ri, nullptr);
-            st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
-            st.n_rebalance_moves += ri.n_rebal; st.subrounds += ri.subrounds; st.n_sequence += ri.n_seq;
-            st.n_applied += ri.best_len;
-            if (rc != UPR_OK) return rc;
-            st.repaired_input = 1;
-        }
-        for (int32_t i = 1; i <= rounds; i++) {
-            RoundInfo ri;
-            rc = run_round(c, c->prm.round_offset + i, total, false, ri, nullptr);
-            if (rc != UPR_OK) return rc;
-            st.rounds_run++;
-            st.n_candidates += ri.n_cand; st.n_moves += ri.n_moves; st.n_rebalance_moves += ri.n_rebal;
-            st.n_sequence += ri.n_seq; st.n_applied += ri.best_len; st.subrounds += ri.subrounds;
-            st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
-            st.ms_select += ri.ms_select; st.ms_rebalance += ri.ms_rebalance; st.ms_sequence += ri.ms_sequence;
-        }
-        copy_out(part, c->part0, sizeof(int32_t) * c->n, c->s);
-        read_i64(c, c->cut, 1, &st.cut_out);
-        UPR_CUDA(cudaEventRecord(c->ev[3], c->s));
-        UPR_CUDA(cudaEventSynchronize(c->ev[3]));
-        float ms = 0;
-        UPR_CUDA(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
-        st.ms_device = ms;
+        return refine_impl(c, part, rounds, stats, nullptr, nullptr, nullptr);
     } catch (const CudaError &) {
         return UPR_ERR_CUDA;
     }
-    st.kernel_launches = (int32_t)(g_upr_launches.load() - launches0);
-    st.ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
-    st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
-                          4 * c->n * (int64_t)c->k;
-    if (stats) *stats = st;
+}
+
+upr_status upr_batch_create(const upr_graph *graphs, int32_t n_graphs, int32_t k, const double *eps,
+                            const upr_params *params, upr_ctx **out) {
+    if (!out || !graphs || !eps || n_graphs < 1) return UPR_ERR_INVALID;
+    upr_ctx *c = new (std::nothrow) upr_ctx();
+    if (!c) return UPR_ERR_OOM;
+    const upr_status st = upr::ctx_rebind_batch(c, graphs, n_graphs, k, eps, params);
+    if (st != UPR_OK) { free_ctx(c); return st; }
+    *out = c;
+    return UPR_OK;
+}
+
+upr_status upr_batch_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_status *status,
+                            int64_t *cut_in, int64_t *cut_out, upr_stats *stats) {
+    (void)seed;
+    if (!c || c->n < 0 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
+    try {
+        upr_status rc = refine_impl(c, part, rounds, stats, status, cut_in, cut_out);
+        if (rc == UPR_ERR_INFEASIBLE && c->ng == 1) {
+            // one graph through the batch entry: a per-graph status, input kept
+            int64_t cut = 0;
+            read_i64(c, c->cut, 1, &cut);
+            if (status) status[0] = UPR_ERR_INFEASIBLE;
+            if (cut_in) cut_in[0] = cut;
+            if (cut_out) cut_out[0] = cut;
+            if (stats) { *stats = upr_stats{}; stats->cut_in = stats->cut_out = cut; }
+            rc = UPR_OK;
+        }
+        return rc;
+    } catch (const CudaError &) {
+        return UPR_ERR_CUDA;
+    }
+}
+
+upr_status upr_batch_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
+    if (!c || c->n < 0 || !part || !cut) return UPR_ERR_INVALID;
+    try {
+        upr_status st = load_part(c, part);
+        if (st != UPR_OK) return st;
+        read_i64(c, c->cut, c->ng, cut);
+        if (block_weights_out) read_i64(c, c->C0, c->G.K(), block_weights_out);
+    } catch (const CudaError &) {
+        return UPR_ERR_CUDA;
+    }
+    return UPR_OK;
+}
+
+upr_status upr_batch_info(const upr_ctx *c, int32_t *n_graphs, int64_t *node_offsets, int64_t *lmax) {
+    if (!c || c->n < 0) return UPR_ERR_INVALID;
+    if (n_graphs) *n_graphs = c->ng;
+    if (node_offsets) memcpy(node_offsets, c->noff.data(), sizeof(int64_t) * (c->ng + 1));
+    if (lmax) memcpy(lmax, c->Lmax_g.data(), sizeof(int64_t) * c->ng);
     return UPR_OK;
 }
 
 upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int64_t *wI) {
-    if (!c || c->n < 0 || !part) return UPR_ERR_INVALID;
+    if (!c || c->n < 0 || c->ng != 1 || !part) return UPR_ERR_INVALID;
     try {
         upr_status rc = load_part(c, part);
         if (rc != UPR_OK) return rc;
@@ -794,7 +1031,8 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
 }
 
 upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int32_t rebalance_only, upr_trace *trace) {
-    if (!c || c->n < 0 || !part || !trace || R < 1 || R > 65536 || (!rebalance_only && (r < 1 || r > R)))
+    if (!c || c->n < 0 || c->ng != 1 || !part || !trace || R < 1 || R > 65536 ||
+        (!rebalance_only && (r < 1 || r > R)))
         return UPR_ERR_INVALID;
     int8_t *avail_d = nullptr;
     int32_t *slot_d = nullptr;
@@ -822,7 +1060,7 @@ upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int3
 // Device bytes a context for (n, m, k) allocates (used by the server's admission).
 size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k) {
     upr_ctx c;
-    c.n = n; c.m = m; c.k = k;
+    c.n = n; c.m = m; c.k = k; c.ng = 1;
     c.n_chunks = m / 4096 + 1;
     c.n_tiles = n + 1;
     Arena A;

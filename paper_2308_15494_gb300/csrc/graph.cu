@@ -18,47 +18,47 @@ __device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ xadj, in
     return lo;
 }
 
-// Block weights: per-CTA shared accumulators, lanes with the same block
-// combined with __match_any_sync before the shared atomic.
-__global__ void k_block_weights(const int32_t *__restrict__ part, const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
+// Block weights: per-CTA accumulators (BlockDelta), lanes with the same
+// block combined with __match_any_sync first.
+__global__ void k_block_weights(const int32_t *__restrict__ part, const int32_t *__restrict__ vwgt, int64_t n, int32_t K,
                                 int64_t *__restrict__ C) {
     extern __shared__ unsigned long long s_c[];
-    for (int b = threadIdx.x; b < k; b += blockDim.x) s_c[b] = 0;
-    __syncthreads();
-    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    BlockDelta bd = make_block_delta(s_c, K, (unsigned long long *)C);
+    bd.init();
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t v = base + threadIdx.x;
-        int32_t b = v < n ? part[v] : -1;
-        long long c = v < n ? (vwgt ? vwgt[v] : 1) : 0;
-        unsigned peers = __match_any_sync(0xffffffffu, b);
-        // sum c over the peers (the leader adds the group's total)
-        long long tot = 0;
-        for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, c, __ffs(m) - 1);
-        if (b >= 0 && (peers & lt) == 0) atomicAdd(&s_c[b], (unsigned long long)tot);
+        const int64_t v = base + threadIdx.x;
+        bd.add(v < n ? part[v] : -1, v < n ? (vwgt ? vwgt[v] : 1) : 0);
     }
-    __syncthreads();
-    for (int b = threadIdx.x; b < k; b += blockDim.x)
-        if (s_c[b]) atomicAdd((unsigned long long *)&C[b], s_c[b]);
+    bd.flush((unsigned long long *)C);
 }
 
+// Edge cut per graph: warp per chunk of adjacency entries; a warp whose
+// entries all belong to one graph adds once, otherwise each lane adds its own.
 __global__ void k_edge_cut(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                           const int32_t *__restrict__ adjw, const int32_t *__restrict__ part, int64_t n, int64_t m,
-                           unsigned long long *__restrict__ out) {
+                           const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
+                           const int32_t *__restrict__ gid, int64_t n, int64_t m, unsigned long long *__restrict__ out) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t e0 = warp * kChunk, e1 = min(m, e0 + kChunk);
+    if (e0 >= m) return;                          // whole warp: e0 is warp-uniform
+    int64_t e = e0 + lane;
+    int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
+    const int32_t g0 = gid ? gid[owner_of(xadj, n, e0)] : 0;
+    const int32_t g1 = gid ? gid[owner_of(xadj, n, e1 - 1)] : 0;
     long long acc = 0;
-    if (e0 < m) {
-        int64_t e = e0 + lane;
-        int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
-        for (; e < e1; e += 32) {
-            while (xadj[v + 1] <= e) v++;
-            const int32_t u = adj[e];
-            if (v < u && part[v] != part[u]) acc += adjw ? adjw[e] : 1;   // each undirected edge once
+    for (; e < e1; e += 32) {
+        while (xadj[v + 1] <= e) v++;
+        const int32_t u = adj[e];
+        if (v < u && part[v] != part[u]) {        // each undirected edge once
+            const long long w = adjw ? adjw[e] : 1;
+            if (g0 == g1) acc += w;
+            else atomicAdd(&out[gid[v]], (unsigned long long)w);
         }
     }
-    acc = warp_sum(acc);
-    if (lane == 0 && acc) atomicAdd(out, (unsigned long long)acc);
+    if (g0 == g1) {
+        acc = warp_sum(acc);
+        if (lane == 0 && acc) atomicAdd(&out[g0], (unsigned long long)acc);
+    }
 }
 
 // omega(I(v)) per node (warp per node); records the maximum and overflow.
@@ -86,11 +86,12 @@ __device__ __forceinline__ uint64_t entry_hash(uint64_t a, uint64_t b, uint64_t 
     return mix64(mix64(mix64(a + 0x1234567ull) ^ b) + w);
 }
 
-// Validation bits: 1 xadj, 2 neighbour range, 4 self loop, 8 edge weight, 16 node
-// weight, 64 asymmetric (sum of hash(v,u,w) over entries != sum of hash(u,v,w)).
+// Validation bits: 1 xadj, 2 neighbour range (or, in a batch, a neighbour in
+// another graph), 4 self loop, 8 edge weight, 16 node weight, 64 asymmetric
+// (sum of hash(v,u,w) over entries != sum of hash(u,v,w)).
 __global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                                   const int32_t *__restrict__ adjw, int64_t n, int64_t m,
-                                   unsigned long long *__restrict__ acc, int32_t *__restrict__ flags) {
+                                   const int32_t *__restrict__ adjw, const int32_t *__restrict__ gid, int64_t n,
+                                   int64_t m, unsigned long long *__restrict__ acc, int32_t *__restrict__ flags) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t e0 = warp * kChunk, e1 = min(m, e0 + kChunk);
@@ -103,7 +104,7 @@ __global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32
             while (xadj[v + 1] <= e) v++;
             int32_t u = adj[e];
             int32_t w = adjw ? adjw[e] : 1;
-            if (u < 0 || u >= n) { f |= 2; continue; }
+            if (u < 0 || u >= n || (gid && gid[u] != gid[v])) { f |= 2; continue; }
             if (u == v) f |= 4;
             if (w <= 0) f |= 8;
             h1 += entry_hash((uint64_t)v, (uint64_t)u, (uint64_t)(uint32_t)w);
@@ -139,7 +140,7 @@ __global__ void k_validate_nodes(const int64_t *__restrict__ xadj, const int32_t
 template <int G>
 __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                                                      const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
-                                                     int64_t n, int32_t k, int32_t *__restrict__ W,
+                                                     int64_t n, int32_t k, int32_t kmask, int32_t *__restrict__ W,
                                                      const int64_t *__restrict__ deg_sum, int64_t m) {
     if (deg_sum && *deg_sum * 4 < m) return;
     extern __shared__ int s_rows[];
@@ -158,9 +159,10 @@ __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__
                 // adjacency is read once per build: stream it past L2 so the
                 // gathered partition array stays cached
                 if (adjw) {
-                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[__ldcs(adj + e)]], __ldcs(adjw + e));
+                    for (int64_t e = b0 + gl; e < b1; e += G)
+                        atomicAdd(&row[blk_local(part[__ldcs(adj + e)], k, kmask)], __ldcs(adjw + e));
                 } else {
-                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[part[__ldcs(adj + e)]], 1);
+                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[blk_local(part[__ldcs(adj + e)], k, kmask)], 1);
                 }
             }
         }
@@ -199,7 +201,7 @@ __device__ __forceinline__ int tile_owner(const int64_t *s_x, int nn, int64_t e)
 __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict__ tiles,
                                                      const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                                                      const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
-                                                     int32_t k, int32_t *__restrict__ W,
+                                                     int32_t k, int32_t kmask, int32_t *__restrict__ W,
                                                      const int64_t *__restrict__ deg_sum, int64_t m) {
     if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
     extern __shared__ int4 s_raw[];
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         const bool in_tail = threadIdx.x >= 4 && qb >= qa && e < t.e1;
         if (in_head || in_tail) {
             const int o = tile_owner(s_x, nn, e);
-            atomicAdd(&rows[o * k + part[adj[e]]], adjw ? adjw[e] : 1);
+            atomicAdd(&rows[o * k + blk_local(part[adj[e]], k, kmask)], adjw ? adjw[e] : 1);
         }
     }
     const int4 *adj4 = reinterpret_cast<const int4 *>(adj);
@@ -237,10 +239,10 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
 #pragma unroll
         for (int r = 0; r < kTableUnroll; r++) {
             const bool ok = q0 + (int64_t)r * blockDim.x < qb;
-            pb[r][0] = ok ? part[u[r].x] : 0;
-            pb[r][1] = ok ? part[u[r].y] : 0;
-            pb[r][2] = ok ? part[u[r].z] : 0;
-            pb[r][3] = ok ? part[u[r].w] : 0;
+            pb[r][0] = ok ? blk_local(part[u[r].x], k, kmask) : 0;
+            pb[r][1] = ok ? blk_local(part[u[r].y], k, kmask) : 0;
+            pb[r][2] = ok ? blk_local(part[u[r].z], k, kmask) : 0;
+            pb[r][3] = ok ? blk_local(part[u[r].w], k, kmask) : 0;
         }
 #pragma unroll
         for (int r = 0; r < kTableUnroll; r++) {
@@ -266,15 +268,15 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
 __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__restrict__ chunks, const int32_t *__restrict__ adj,
                                                           const int32_t *__restrict__ adjw,
                                                           const int32_t *__restrict__ part, int32_t k,
-                                                          int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
-                                                          int64_t m) {
+                                                          int32_t kmask, int32_t *__restrict__ W,
+                                                          const int64_t *__restrict__ deg_sum, int64_t m) {
     if (deg_sum && *deg_sum * 4 < m) return;
     extern __shared__ int s_row[];
     const HubChunk ch = chunks[blockIdx.x];
     for (int b = threadIdx.x; b < k; b += blockDim.x) s_row[b] = 0;
     __syncthreads();
     for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x)
-        atomicAdd(&s_row[part[adj[e]]], adjw ? adjw[e] : 1);
+        atomicAdd(&s_row[blk_local(part[adj[e]], k, kmask)], adjw ? adjw[e] : 1);
     __syncthreads();
     int32_t *dst = W + (int64_t)ch.v * k;
     for (int b = threadIdx.x; b < k; b += blockDim.x)
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
 // Delta update: warp per moved node; hubs (degree > kHubDegree) are left to
 // k_table_move_hubs, which splits them into the static chunks.
 __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                             const int32_t *__restrict__ adjw, int32_t k, int32_t *__restrict__ W,
+                             const int32_t *__restrict__ adjw, int32_t k, int32_t kmask, int32_t *__restrict__ W,
                              const int32_t *__restrict__ nodes, const int32_t *__restrict__ from,
                              const int32_t *__restrict__ to, const int32_t *__restrict__ d_count,
                              const int32_t *__restrict__ d_offset, const int64_t *__restrict__ deg_sum, int64_t m) {
@@ -294,7 +296,8 @@ __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__
     const int64_t off = d_offset ? *d_offset : 0;
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
          j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int32_t v = nodes[off + j], a = from[off + j], b = to[off + j];
+        const int32_t v = nodes[off + j];
+        const int32_t a = blk_local(from[off + j], k, kmask), b = blk_local(to[off + j], k, kmask);
         const int64_t e0 = xadj[v], e1 = xadj[v + 1];
         if (e1 - e0 > kHubDegree) continue;
         for (int64_t e = e0 + lane; e < e1; e += 32) {
@@ -312,7 +315,7 @@ __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__
 __global__ void __launch_bounds__(512) k_table_move_hubs(const HubChunk *__restrict__ chunks,
                                                          const int32_t *__restrict__ adj,
                                                          const int32_t *__restrict__ adjw, int32_t k,
-                                                         int32_t *__restrict__ W, HubMoves hm,
+                                                         int32_t kmask, int32_t *__restrict__ W, HubMoves hm,
                                                          const int64_t *__restrict__ deg_sum, int64_t m) {
     if (deg_sum && *deg_sum * 4 >= m) return;
     const HubChunk ch = chunks[blockIdx.x];
@@ -321,20 +324,44 @@ __global__ void __launch_bounds__(512) k_table_move_hubs(const HubChunk *__restr
     if (hm.m_pos) {
         const int32_t p = hm.m_pos[v];
         if (p < 0) return;
-        a = hm.from[p];
-        b = hm.to[p];
+        a = blk_local(hm.from[p], k, kmask);
+        b = blk_local(hm.to[p], k, kmask);
     } else {
         if (hm.r_to[v] < 0) return;
         const int32_t ri = hm.r_at[v], base = *hm.r_base;
         if (ri < base || ri >= base + *hm.r_count) return;
-        a = hm.from[ri];
-        b = hm.to[ri];
+        a = blk_local(hm.from[ri], k, kmask);
+        b = blk_local(hm.to[ri], k, kmask);
     }
     for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
         const int32_t w = adjw ? adjw[e] : 1;
         int32_t *row = W + (int64_t)adj[e] * k;
         atomicSub(&row[a], w);
         atomicAdd(&row[b], w);
+    }
+}
+
+__global__ void k_node_graph(const int64_t *__restrict__ noff, int32_t ng, int64_t n, int32_t *__restrict__ gid) {
+    UPR_FOR(v, n) {
+        int32_t lo = 0, hi = ng - 1;            // last g with noff[g] <= v
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (noff[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        gid[v] = lo;
+    }
+}
+
+__global__ void k_shift_adj(const int64_t *__restrict__ xadj, const int64_t *__restrict__ noff,
+                            const int32_t *__restrict__ gid, int64_t n, int32_t *__restrict__ adj) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n;
+         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t off = noff[gid[v]];
+        for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) {
+            const int64_t u = (int64_t)adj[e] + off;
+            adj[e] = (u < 0 || u >= n) ? -1 : (int32_t)u;
+        }
     }
 }
 
@@ -351,18 +378,18 @@ int sm_count() {
 }  // namespace
 
 void block_weights(const GraphDev &g, const int32_t *part, int64_t *C, cudaStream_t s) {
-    UPR_CUDA(cudaMemsetAsync(C, 0, sizeof(int64_t) * g.k, s));
+    UPR_CUDA(cudaMemsetAsync(C, 0, sizeof(int64_t) * g.K(), s));
     if (g.n == 0) return;
     int64_t blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count() * 8);
-    k_block_weights<<<(unsigned)blocks, 256, sizeof(int64_t) * g.k, s>>>(part, g.vwgt, g.n, g.k, C);
+    k_block_weights<<<(unsigned)blocks, 256, block_delta_smem(g.K()), s>>>(part, g.vwgt, g.n, g.K(), C);
     UPR_LAUNCH_CHECK();
 }
 
 void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t s) {
-    UPR_CUDA(cudaMemsetAsync(cut, 0, sizeof(int64_t), s));
+    UPR_CUDA(cudaMemsetAsync(cut, 0, sizeof(int64_t) * g.ng, s));
     if (g.m == 0) return;
     int64_t warps = ceil_div(g.m, kChunk);
-    k_edge_cut<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(g.xadj, g.adj, g.adjw, part, g.n, g.m,
+    k_edge_cut<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(g.xadj, g.adj, g.adjw, part, g.gid, g.n, g.m,
                                                                    (unsigned long long *)cut);
     UPR_LAUNCH_CHECK();
 }
@@ -374,6 +401,15 @@ void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_
     UPR_LAUNCH_CHECK();
 }
 
+void pack_batch(const GraphDev &g, const int64_t *noff, int32_t *gid, int32_t *adj, cudaStream_t s) {
+    if (g.n == 0) return;
+    k_node_graph<<<grid_for(g.n), 256, 0, s>>>(noff, g.ng, g.n, gid);
+    UPR_LAUNCH_CHECK();
+    const int64_t blocks = std::min<int64_t>(ceil_div(g.n * 32, 256), (int64_t)sm_count() * 16);
+    k_shift_adj<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, noff, gid, g.n, adj);
+    UPR_LAUNCH_CHECK();
+}
+
 void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s) {
     UPR_CUDA(cudaMemsetAsync(d_acc, 0, 2 * sizeof(uint64_t), s));
     UPR_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int32_t), s));
@@ -382,7 +418,7 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaSt
     if (g.m > 0 && g.n > 0) {
         int64_t warps = ceil_div(g.m, kChunk);
         k_validate_entries<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(
-            g.xadj, g.adj, g.adjw, g.n, g.m, (unsigned long long *)d_acc, d_flags);
+            g.xadj, g.adj, g.adjw, g.gid, g.n, g.m, (unsigned long long *)d_acc, d_flags);
         UPR_LAUNCH_CHECK();
     }
 }
@@ -401,7 +437,8 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
             UPR_CUDA(cudaFuncSetAttribute(k_table_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
             attr_set = shm;
         }
-        k_table_tiles<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, W, deg_sum, g.m);
+        k_table_tiles<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum,
+                                                          g.m);
         UPR_LAUNCH_CHECK();
     } else {
         const int k = g.k;
@@ -417,7 +454,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
             UPR_CUDA(cudaFuncSetAttribute(k_table_dense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
             UPR_CUDA(cudaFuncSetAttribute(k_table_dense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         }
-#define UPR_TD(GG) k_table_dense<GG><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, W, deg_sum, g.m)
+#define UPR_TD(GG) k_table_dense<GG><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, g.kmask, W, deg_sum, g.m)
         switch (G) {
             case 4: UPR_TD(4); break;
             case 8: UPR_TD(8); break;
@@ -428,8 +465,8 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
         UPR_LAUNCH_CHECK();
     }
     if (n_chunks > 0) {
-        k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k, W,
-                                                                             deg_sum, g.m);
+        k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k,
+                                                                             g.kmask, W, deg_sum, g.m);
         UPR_LAUNCH_CHECK();
     }
 }
@@ -439,11 +476,12 @@ void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32
                 const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s) {
     if (max_count <= 0) return;
     int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
-    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, W, nodes, from, to, d_count, d_offset,
-                                                  deg_sum, g.m);
+    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, g.kmask, W, nodes, from, to, d_count,
+                                                  d_offset, deg_sum, g.m);
     UPR_LAUNCH_CHECK();
     if (n_chunks > 0) {
-        k_table_move_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, g.k, W, hm, deg_sum, g.m);
+        k_table_move_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, g.k, g.kmask, W, hm, deg_sum,
+                                                             g.m);
         UPR_LAUNCH_CHECK();
     }
 }

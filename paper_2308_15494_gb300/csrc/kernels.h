@@ -7,15 +7,35 @@ namespace upr {
 
 // The graph as the kernels see it (device pointers; adjw / vwgt may be null =
 // unit weights).  wI[v] = omega(I(v)) < 2^31.
+//
+// A context holds one graph or a batch of ng independent graphs packed as one
+// CSR (graph g owns the nodes [noff[g], noff[g+1]) and no edge joins two
+// graphs).  Blocks are numbered globally: graph g owns blocks [g*k, g*k + k),
+// part[] holds global block ids, and everything indexed by block has K = ng*k
+// entries.  Gain-table rows keep k columns: the column of global block p is
+// p mod k (blk_local).  With one graph, global and local ids coincide.
 struct GraphDev {
     int64_t n, m;
-    int32_t k;
+    int32_t k;            // blocks per graph
+    int32_t ng;           // graphs in the context
+    int32_t kmask;        // blk_local(p) = p & kmask when non-zero (-1 for one graph, k-1 for k a power of two)
     const int64_t *xadj;
     const int32_t *adj;
     const int32_t *adjw;
     const int32_t *vwgt;
     const int32_t *wI;
+    const int64_t *Lb;    // [K] L_max of the graph each block belongs to
+    const int32_t *gid;   // [n] graph of each node (null for one graph)
+    __host__ __device__ int32_t K() const { return ng * k; }
 };
+
+__device__ __forceinline__ int32_t blk_local(int32_t p, int32_t k, int32_t kmask) {
+    return kmask ? (p & kmask) : p % k;
+}
+__device__ __forceinline__ int32_t blk_local(const GraphDev &g, int32_t p) { return blk_local(p, g.k, g.kmask); }
+// first global block of p's graph
+__device__ __forceinline__ int32_t blk_base(const GraphDev &g, int32_t p) { return p - blk_local(g, p); }
+__device__ __forceinline__ int32_t blk_graph(const GraphDev &g, int32_t p) { return g.ng == 1 ? 0 : p / g.k; }
 
 __device__ __forceinline__ int64_t node_c(const GraphDev &g, int64_t v) { return g.vwgt ? (int64_t)g.vwgt[v] : 1; }
 __device__ __forceinline__ int32_t edge_w(const GraphDev &g, int64_t e) { return g.adjw ? g.adjw[e] : 1; }
@@ -64,7 +84,9 @@ void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Coun
 
 // ---- graph.cu: step (e), step (a), create-time work
 struct HubChunk { int32_t v; int32_t pad; int64_t begin, end; };
+// C[0..K) = block weights of part.
 void block_weights(const GraphDev &g, const int32_t *part, int64_t *C, cudaStream_t s);
+// cut[0..ng) = edge cut of each graph.
 void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t s);
 void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_t s);
 // A tile of the table build: nodes [v0, v1) and the adjacency entries [e0, e1)
@@ -93,15 +115,19 @@ struct HubMoves {
 void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
                 const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
                 const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s);
+// Batches: gid[v] = graph of node v (noff: [ng + 1] first nodes), and each
+// graph's neighbour ids (local to the graph on input) shifted by its first
+// node; an id that leaves [0, n) becomes -1 for the checks to report.
+void pack_batch(const GraphDev &g, const int64_t *noff, int32_t *gid, int32_t *adj, cudaStream_t s);
 // Graph checks; writes a bitmask of violations into *d_flags (see engine.cu).
 void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s);
 
 // ---- select.cu: step (b) and applying M
 struct Penalty {
-    const int64_t *PW;    // [k][73] inclusive prefix over slots of available node weight
+    const int64_t *PW;    // [K][73] inclusive prefix over slots of available node weight
     const int64_t *F;     // [73] floor(tau_r * (3/2)^l * 2^Q)
-    const int64_t *C;     // [k] round-start block weights
-    int64_t Lmax;
+    const int64_t *C;     // [K] round-start block weights
+    const int64_t *Lb;    // [K] L_max of each block's graph
 };
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
              int64_t *PW, int8_t *avail_out, int32_t *slot_out, cudaStream_t s);
@@ -126,18 +152,19 @@ void apply_moves(const GraphDev &g, const int32_t *cand_idx, const int32_t *m_id
 struct RebalCtl {
     int32_t active;      // the current sub-round runs
     int32_t stopped;     // the loop has finished
-    int32_t light;       // lightest block that may receive moves, or -1
+    int32_t light;       // one graph: lightest block that may receive moves, or -1
     int32_t subrounds;   // sub-rounds that ran
     int32_t nR;          // rebalancing moves so far (length of R)
     int32_t n1_active;   // length of the node list if this sub-round runs, else 0
-    int32_t pad[2];
+    int32_t flag;        // batch controllers: "some block is overloaded" / "the excluded set grew"
+    uint32_t ticket;     // batch controllers: CTAs finished (the last one updates the control block)
 };
 struct RebalState {
-    const int64_t *C;     // current block weights
-    const int8_t *over;   // [k] overloaded now
-    const int8_t *excl;   // [k] not a target: overloaded at the first sub-round, or rejected a move
-    const int32_t *light; // lightest non-excluded block, or -1
-    int64_t Lmax;
+    const int64_t *C;     // [K] current block weights
+    const int8_t *over;   // [K] overloaded now
+    const int8_t *excl;   // [K] not a target: overloaded at the first sub-round, or rejected a move
+    const int32_t *light; // [ng] lightest non-excluded block of each graph, or -1
+    const int64_t *Lb;    // [K] L_max of each block's graph
 };
 // flags[v] = 1 for the nodes of the marked blocks
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s);
@@ -166,17 +193,22 @@ void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, con
                      const int32_t *d_na, const int32_t *prop_tgt, int32_t *part, int64_t *C, const RebalCtl *ctl,
                      int32_t *R_node, int32_t *R_from, int32_t *R_to, int32_t *R_sub, int32_t *r_to, int32_t *r_at,
                      int64_t na_max, cudaStream_t s);
-void rebalance_init(const int64_t *C, int32_t k, int64_t Lmax, int8_t *excl, RebalCtl *ctl, cudaStream_t s);
-void rebalance_begin(const int64_t *C, int32_t k, int64_t Lmax, const int8_t *excl, int8_t *over, int8_t *reject,
-                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, cudaStream_t s);
-void rebalance_end(int32_t k, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl, cudaStream_t s);
+// Loop control over the K blocks of g (C = current block weights).  light
+// receives each graph's lightest non-excluded block (&ctl->light for one graph).
+void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl *ctl, cudaStream_t s);
+void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
+                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, int32_t *light,
+                     cudaStream_t s);
+void rebalance_end(const GraphDev &g, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl,
+                   cudaStream_t s);
 
 // ---- sequence.cu: step (c); every count lives in device memory, `max` bounds it
 void count_affine(const int32_t *a, int32_t a_mul, const int32_t *b, int32_t add, int32_t *out, cudaStream_t s);
 void fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t s);
 void clear_count(int32_t *a, const int32_t *d_n, int32_t extra, int64_t max, cudaStream_t s);
 void reset_nodes(const int32_t *nodes, const int32_t *d_cnt, int64_t max, int32_t *arr, int32_t val, cudaStream_t s);
-void count_over(const int64_t *C, int32_t k, int64_t Lmax, int32_t *out, cudaStream_t s);
+// out[g] = number of blocks of graph g above L_max
+void count_over(const GraphDev &g, const int64_t *C, int32_t *out, cudaStream_t s);
 void seq_rb_keys(const int32_t *R_from, const int32_t *d_nR, int64_t max, uint64_t *keys, uint32_t *vals,
                  cudaStream_t s);
 void seq_rb_bounds(const int32_t *R_node, const int32_t *R_from, const uint32_t *RB, const int32_t *d_nR, int64_t max,
@@ -186,11 +218,12 @@ void seq_ev_keys(const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM
 void seq_ev_delta(const int32_t *M_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max,
                   const int32_t *vwgt, int64_t *delta, int32_t *ebeg, int32_t *eend, cudaStream_t s);
 void seq_ev_need(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const int64_t *delta,
-                 const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, int64_t Lmax, const int32_t *rbeg,
-                 const int32_t *rend, const int64_t *rc_excl, const int64_t *rc, uint64_t *packed, cudaStream_t s);
+                 const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, const int64_t *Lb,
+                 const int32_t *rbeg, const int32_t *rend, const int64_t *rc_excl, const int64_t *rc, uint64_t *packed,
+                 cudaStream_t s);
 void seq_ev_emit(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const uint64_t *qmax,
                  const int32_t *ebeg, int32_t *emit, int32_t *qbefore_m, cudaStream_t s);
-void seq_block_final(int32_t k, const int32_t *ebeg, const int32_t *eend, const uint64_t *qmax, const int32_t *rbeg,
+void seq_block_final(int32_t K, const int32_t *ebeg, const int32_t *eend, const uint64_t *qmax, const int32_t *rbeg,
                      const int32_t *rend, int32_t *qfin, int32_t *left, cudaStream_t s);
 void seq_place_m(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM, int64_t max,
                  const int32_t *em_excl, int32_t *pos_m, int32_t *X_node, int32_t *X_from, int32_t *X_to,
@@ -215,10 +248,26 @@ void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ek
                    const int32_t *vwgt, int64_t *delta, int32_t *ebeg, cudaStream_t s);
 void seq_iev_transitions(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,
                          const int64_t *delta, const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0,
-                         int64_t Lmax, int32_t *diff, cudaStream_t s);
+                         const int64_t *Lb, int32_t *diff, cudaStream_t s);
 void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, const int32_t *d_nI, int64_t max,
               const int32_t *d_over0, long long *parts, long long *out, int32_t *infeasible, cudaStream_t s);
 void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                       int64_t max, const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s);
+// Batches: I (length *d_nI) stably sorted by graph into O_*; pos/dest of the
+// moved nodes set from the sorted order; seg_beg/seg_end[g] bound graph g's
+// moves (both 0 for a graph without moves).
+void seq_sort_by_graph(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+                       const int32_t *d_nI, int64_t max, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                       uint32_t *vals_alt, Scratch tmp, int32_t *O_node, int32_t *O_from, int32_t *O_to, int32_t *pos,
+                       int32_t *dest, int32_t *seg_beg, int32_t *seg_end, cudaStream_t s);
+// Per graph: the best eligible prefix j* (ties: shortest; none: infeasible,
+// j* = 0), cut[g] -= G_g(j*); tot = (sum j*, sum G(j*), infeasible graphs).
+void seq_best_seg(const GraphDev &g, const int32_t *I_node, const int32_t *d_nI, int64_t max, const int32_t *seg_beg,
+                  const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, const int32_t *over0,
+                  long long *best_g, long long *best_j, int64_t *cut, int32_t *infeasible, int64_t *tot,
+                  cudaStream_t s);
+void seq_apply_prefix_seg(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+                          const int32_t *d_nI, int64_t max, const int32_t *seg_beg, const long long *best_j,
+                          int32_t *part0, int64_t *C0, cudaStream_t s);
 
 }  // namespace upr

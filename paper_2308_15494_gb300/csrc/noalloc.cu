@@ -63,7 +63,7 @@ extern "C" upr_status upr_cut_noalloc(const upr_graph *g, int32_t k, const int32
     int64_t *scratch = scratch_address(dev);
     if (!scratch) return UPR_ERR_CUDA;
     try {
-        upr::GraphDev G{g->n, g->m, k, g->xadj, g->adjncy, g->adjwgt, g->vwgt, nullptr};
+        upr::GraphDev G{g->n, g->m, k, 1, -1, g->xadj, g->adjncy, g->adjwgt, g->vwgt, nullptr, nullptr, nullptr};
         // the flag keeps the previous call's value: clear it first
         UPR_CUDA(cudaMemsetAsync(scratch + k + 1, 0, sizeof(int64_t), s));
         if (g->n > 0) {

@@ -21,20 +21,21 @@ int sm_count_reb() {
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
-                                                 const int32_t *__restrict__ part, const int32_t *__restrict__ W,
-                                                 const int32_t *__restrict__ vwgt, int32_t k, RebalState st,
+__global__ void __launch_bounds__(256) k_propose(const GraphDev g, const int32_t *__restrict__ list,
+                                                 const int32_t *__restrict__ d_n1, const int32_t *__restrict__ part,
+                                                 const int32_t *__restrict__ W, RebalState st,
                                                  int32_t *__restrict__ prop_tgt, int32_t *__restrict__ prop_gain,
                                                  int32_t *__restrict__ flags) {
     const int64_t n1 = *d_n1;
-    const int32_t light = *st.light;
+    const int32_t k = g.k;
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
         const int64_t i = base + gid;
         const int32_t v = i < n1 ? list[i] : 0;
-        const int32_t a = i < n1 ? part[v] : 0;
-        const bool src = i < n1 && st.over[a];
+        const int32_t ag = i < n1 ? part[v] : 0;
+        const bool src = i < n1 && st.over[ag];
+        const int32_t a = blk_local(g, ag), b0 = ag - a;
         int64_t best = 0;
         int32_t bt = -1;
         int32_t own = 0;
@@ -42,10 +43,11 @@ __global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ lis
         if (src) {
             const int32_t *row = W + (int64_t)v * k;
             own = row[a];
-            c = vwgt ? vwgt[v] : 1;
+            c = g.vwgt ? g.vwgt[v] : 1;
             for (int b = gl; b < k; b += G) {
                 const int32_t w = row[b];
-                if (b == a || w <= 0 || st.excl[b] || st.C[b] + c > st.Lmax) continue;
+                const int32_t gb = b0 + b;
+                if (b == a || w <= 0 || st.excl[gb] || st.C[gb] + c > st.Lb[gb]) continue;
                 const int64_t gain = (int64_t)w - own;
                 if (bt < 0 || gain > best) { best = gain; bt = b; }
             }
@@ -54,9 +56,10 @@ __global__ void __launch_bounds__(256) k_propose(const int32_t *__restrict__ lis
         int32_t id = bt;
         group_argmax<G>(s, id);
         if (i < n1 && gl == 0) {
-            int32_t tgt = src ? id : -1;
+            int32_t tgt = src && id >= 0 ? b0 + id : -1;
             int64_t gain = s;
-            if (src && tgt < 0 && light >= 0 && st.C[light] + c <= st.Lmax) { tgt = light; gain = -(int64_t)own; }
+            const int32_t light = src ? st.light[blk_graph(g, ag)] : -1;
+            if (src && tgt < 0 && light >= 0 && st.C[light] + c <= st.Lb[light]) { tgt = light; gain = -(int64_t)own; }
             if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = (int32_t)gain; }
             flags[i] = tgt >= 0 ? 1 : 0;
         }
@@ -69,39 +72,42 @@ __device__ __forceinline__ int32_t int4_at(const int4 &x, int c) {
 
 // Proposals of the listed nodes (the nodes of blocks overloaded when
 // rebalancing started; those that left them are skipped).  Vectorised rows
-// as in selection; s_room[b] = L_max - C[b] for an allowed target, -1 for an
-// excluded one, so one comparison c <= s_room[b] tests validity.
-template <int G, int CH, bool EXACT>
-__global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
+// as in selection; room(b) = L_max - C[b] for an allowed target, -1 for an
+// excluded one, so one comparison c <= room(b) tests validity.  With one
+// graph the rooms are staged in shared memory; in a batch each node reads its
+// graph's blocks from global memory.
+template <int G, int CH, bool EXACT, bool BATCH>
+__global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int32_t *__restrict__ list,
+                                                     const int32_t *__restrict__ d_n1,
                                                      const int32_t *__restrict__ part, const int32_t *__restrict__ W,
-                                                     const int32_t *__restrict__ vwgt, int32_t k, RebalState st,
-                                                     int32_t *__restrict__ prop_tgt, int32_t *__restrict__ prop_gain,
-                                                     int32_t *__restrict__ flags) {
+                                                     RebalState st, int32_t *__restrict__ prop_tgt,
+                                                     int32_t *__restrict__ prop_gain, int32_t *__restrict__ flags) {
     // EXACT: k == 4 * G * CH, every lane's four blocks exist.  The room of an
     // excluded block (which includes every overloaded block, so the node's own
     // block) is -1, so "c <= room" alone decides whether a block may receive
     // the node; room is clamped to 2^31 - 1 since c < 2^31.
     const int64_t n1 = *d_n1;
     if (n1 == 0) return;
+    const int32_t k = g.k;
     extern __shared__ int32_t s_room[];
     int8_t *s_over = reinterpret_cast<int8_t *>(s_room + k);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const int64_t room = st.Lmax - st.C[i];
-        s_room[i] = st.excl[i] ? -1 : (int32_t)(room > 0x7fffffffLL ? 0x7fffffffLL : room);
-        s_over[i] = st.over[i];
+    if (!BATCH) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            const int64_t room = st.Lb[i] - st.C[i];
+            s_room[i] = st.excl[i] ? -1 : (int32_t)(room > 0x7fffffffLL ? 0x7fffffffLL : room);
+            s_over[i] = st.over[i];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
-    const int32_t light = *st.light;
-    const int64_t lroom = light >= 0 ? st.Lmax - st.C[light] : -1;
-    const int32_t light_room = (int32_t)(lroom > 0x7fffffffLL ? 0x7fffffffLL : lroom);
     for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
         const int64_t i = base + gid;
         const int32_t v = i < n1 ? list[i] : 0;
-        const int32_t a = i < n1 ? part[v] : 0;
-        const bool src = i < n1 && s_over[a];
+        const int32_t ag = i < n1 ? part[v] : 0;
+        const int32_t a = BATCH ? blk_local(g, ag) : ag, b0 = ag - a;
+        const bool src = i < n1 && (BATCH ? st.over[ag] : s_over[a]);
         const int4 zero = make_int4(0, 0, 0, 0);
         int4 r[CH];
         if (src) {
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
         for (int j = 0; j < CH; j++)
             if (j == q4 / G) mine = int4_at(r[j], a & 3);
         const int32_t own = __shfl_sync(0xffffffffu, mine, gbase + (q4 % G));
-        const int32_t c = src ? (vwgt ? vwgt[v] : 1) : 1;
+        const int32_t c = src ? (g.vwgt ? g.vwgt[v] : 1) : 1;
         // best valid block: the largest omega(v, V_b) (gain = omega - own), ties to the smaller b
         int32_t bw = 0, bt = -1;
         if (src) {
@@ -131,7 +137,15 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
                 for (int cc = 0; cc < 4; cc++) {
                     const int b = 4 * (gl + G * j) + cc;
                     const int32_t w = int4_at(r[j], cc);
-                    if ((!EXACT && b >= k) || w <= 0 || c > s_room[b]) continue;
+                    if ((!EXACT && b >= k) || w <= 0) continue;
+                    int32_t room;
+                    if (BATCH) {
+                        const int64_t rm = st.Lb[b0 + b] - st.C[b0 + b];
+                        room = st.excl[b0 + b] ? -1 : (int32_t)(rm > 0x7fffffffLL ? 0x7fffffffLL : rm);
+                    } else {
+                        room = s_room[b];
+                    }
+                    if (c > room) continue;
                     if (bt < 0 || w > bw) { bw = w; bt = b; }
                 }
             }
@@ -139,9 +153,15 @@ __global__ void __launch_bounds__(256) k_propose_vec(const int32_t *__restrict__
         int32_t id = bt;
         group_argmax32<G>(bw, id);
         if (i < n1 && gl == 0) {
-            int32_t tgt = src ? id : -1;
+            int32_t tgt = src && id >= 0 ? b0 + id : -1;
             int32_t gain = bw - own;
-            if (src && tgt < 0 && c <= light_room) { tgt = light; gain = -own; }
+            if (src && tgt < 0) {
+                const int32_t light = st.light[BATCH ? blk_graph(g, ag) : 0];
+                if (light >= 0) {
+                    const int64_t lroom = st.Lb[light] - st.C[light];
+                    if ((int64_t)c <= lroom) { tgt = light; gain = -own; }
+                }
+            }
             if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = gain; }
             flags[i] = tgt >= 0 ? 1 : 0;
         }
@@ -161,15 +181,17 @@ __global__ void k_gather_list(const int32_t *__restrict__ list, const int32_t *_
     UPR_FOR(i, cnt) out[i] = list[pos[i]];
 }
 
-// ---- loop control: one CTA each, k <= 4096 blocks
+// ---- loop control.  One graph: one CTA each (K = k <= 4096).  A batch: a
+// grid over the graphs, warp per graph; the last CTA to finish (ticket)
+// updates the control block.
 // Start of rebalancing: the blocks overloaded now are never targets.
-__global__ void k_reb_init(const int64_t *__restrict__ C, int32_t k, int64_t Lmax, int8_t *__restrict__ excl,
-                           RebalCtl *__restrict__ ctl) {
+__global__ void k_reb_init(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t K,
+                           int8_t *__restrict__ excl, RebalCtl *__restrict__ ctl) {
     __shared__ int s_any;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
-    for (int b = threadIdx.x; b < k; b += blockDim.x) {
-        const bool o = C[b] > Lmax;
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
+        const bool o = C[b] > Lb[b];
         excl[b] = o ? 1 : 0;
         if (o) s_any = 1;
     }
@@ -181,13 +203,54 @@ __global__ void k_reb_init(const int64_t *__restrict__ C, int32_t k, int64_t Lma
         ctl->subrounds = 0;
         ctl->nR = 0;
         ctl->n1_active = 0;
+        ctl->flag = 0;
+        ctl->ticket = 0;
+    }
+}
+
+// The last CTA of a batch controller grid: true in thread 0 of that CTA.
+__device__ __forceinline__ bool last_cta(RebalCtl *ctl) {
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_last) {
+        __threadfence();
+        return true;
+    }
+    return false;
+}
+
+__global__ void k_reb_init_batch(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t K,
+                                 int8_t *__restrict__ excl, RebalCtl *__restrict__ ctl) {
+    int any = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K; b += gridDim.x * blockDim.x) {
+        const bool o = C[b] > Lb[b];
+        excl[b] = o ? 1 : 0;
+        any |= o;
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&ctl->flag, 1);
+    if (last_cta(ctl)) {
+        const int f = atomicAdd(&ctl->flag, 0);
+        ctl->active = 0;
+        ctl->stopped = f ? 0 : 1;
+        ctl->light = -1;
+        ctl->subrounds = 0;
+        ctl->nR = 0;
+        ctl->n1_active = 0;
+        ctl->flag = 0;
+        ctl->ticket = 0;
     }
 }
 
 // Start of sub-round h: overloaded set, lightest allowed block, activity.
-__global__ void k_reb_begin(const int64_t *__restrict__ C, int32_t k, int64_t Lmax, const int8_t *__restrict__ excl,
-                            int8_t *__restrict__ over, int8_t *__restrict__ reject, const int32_t *__restrict__ d_n1,
-                            int32_t h, int32_t max_subrounds, RebalCtl *__restrict__ ctl) {
+__global__ void k_reb_begin(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t k,
+                            const int8_t *__restrict__ excl, int8_t *__restrict__ over, int8_t *__restrict__ reject,
+                            const int32_t *__restrict__ d_n1, int32_t h, int32_t max_subrounds,
+                            RebalCtl *__restrict__ ctl) {
     __shared__ int s_any;
     __shared__ long long s_w[256];
     __shared__ int s_b[256];
@@ -196,7 +259,7 @@ __global__ void k_reb_begin(const int64_t *__restrict__ C, int32_t k, int64_t Lm
     long long bw = 0;
     int bb = -1;
     for (int b = threadIdx.x; b < k; b += blockDim.x) {
-        const bool o = C[b] > Lmax;
+        const bool o = C[b] > Lb[b];
         over[b] = o ? 1 : 0;
         reject[b] = 0;
         if (o) s_any = 1;
@@ -227,21 +290,76 @@ __global__ void k_reb_begin(const int64_t *__restrict__ C, int32_t k, int64_t Lm
     }
 }
 
+// Batch form: warp per graph.
+__global__ void k_reb_begin_batch(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t k,
+                                  int32_t ng, const int8_t *__restrict__ excl, int8_t *__restrict__ over,
+                                  int8_t *__restrict__ reject, const int32_t *__restrict__ d_n1, int32_t h,
+                                  int32_t max_subrounds, RebalCtl *__restrict__ ctl, int32_t *__restrict__ light) {
+    const int lane = threadIdx.x & 31;
+    int any = 0;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng;
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t bw = 0;
+        int32_t bb = -1;
+        for (int32_t j = lane; j < k; j += 32) {
+            const int32_t b = (int32_t)g * k + j;
+            const bool o = C[b] > Lb[b];
+            over[b] = o ? 1 : 0;
+            reject[b] = 0;
+            any |= o;
+            // lightest: smallest weight, ties to the smaller block (b grows with j)
+            if (!excl[b] && (bb < 0 || C[b] < bw)) { bw = C[b]; bb = b; }
+        }
+        // argmin over the warp: negate weights for group_argmax (larger score wins, ties to smaller id)
+        int64_t sc = -bw;
+        group_argmax<32>(sc, bb);
+        if (lane == 0) light[g] = bb;
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&ctl->flag, 1);
+    if (last_cta(ctl)) {
+        const int f = atomicAdd(&ctl->flag, 0);
+        const bool run = !ctl->stopped && f && h <= max_subrounds;
+        ctl->active = run ? 1 : 0;
+        if (!run) ctl->stopped = 1;
+        if (run) ctl->subrounds = h;
+        ctl->n1_active = run ? *d_n1 : 0;
+        ctl->flag = 0;
+        ctl->ticket = 0;
+    }
+}
+
 // End of a sub-round: targets that rejected a move are excluded from now on;
 // stop when nothing was admitted and no target was newly excluded.
-__global__ void k_reb_end(int32_t k, int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
+__global__ void k_reb_end(int32_t K, int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
                           const int32_t *__restrict__ d_na, RebalCtl *__restrict__ ctl) {
     __shared__ int s_grew;
     if (threadIdx.x == 0) s_grew = 0;
     __syncthreads();
     if (!ctl->active) return;
-    for (int b = threadIdx.x; b < k; b += blockDim.x)
+    for (int b = threadIdx.x; b < K; b += blockDim.x)
         if (reject[b] && !excl[b]) { excl[b] = 1; s_grew = 1; }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int32_t na = *d_na;
         ctl->nR += na;
         if (na == 0 && !s_grew) ctl->stopped = 1;
+    }
+}
+
+__global__ void k_reb_end_batch(int32_t K, int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
+                                const int32_t *__restrict__ d_na, RebalCtl *__restrict__ ctl) {
+    if (!ctl->active) return;                 // uniform over the grid: no CTA takes a ticket
+    int grew = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K; b += gridDim.x * blockDim.x)
+        if (reject[b] && !excl[b]) { excl[b] = 1; grew = 1; }
+    if (__syncthreads_or(grew) && threadIdx.x == 0) atomicOr(&ctl->flag, 1);
+    if (last_cta(ctl)) {
+        const int f = atomicAdd(&ctl->flag, 0);
+        const int32_t na = *d_na;
+        ctl->nR += na;
+        if (na == 0 && !f) ctl->stopped = 1;
+        ctl->flag = 0;
+        ctl->ticket = 0;
     }
 }
 
@@ -305,7 +423,7 @@ __global__ void k_mark_selected(const uint32_t *__restrict__ B, const uint64_t *
     UPR_FOR(q, cnt) {
         const int32_t b = (int32_t)bkeys[q];
         const int64_t before = c_excl[q] - c_excl[seg_first[b]];
-        sel[B[q]] = before < st.C[b] - st.Lmax ? 1 : 0;
+        sel[B[q]] = before < st.C[b] - st.Lb[b] ? 1 : 0;
     }
 }
 
@@ -318,7 +436,7 @@ __global__ void k_mark_admitted(const uint32_t *__restrict__ T, const uint64_t *
     UPR_FOR(q, cnt) {
         const int32_t t = (int32_t)bkeys[q];
         const int64_t incl = c_excl[q] - c_excl[seg_first[t]] + c_sorted[q];
-        const bool ok = st.C[t] + incl <= st.Lmax;
+        const bool ok = st.C[t] + incl <= st.Lb[t];
         adm[T[q]] = ok ? 1 : 0;
         if (!ok) reject[t] = 1;
     }
@@ -328,12 +446,12 @@ __global__ void k_apply_rebal(const int32_t *__restrict__ P, const uint32_t *__r
                               const int32_t *__restrict__ S, const int32_t *__restrict__ Adm,
                               const int32_t *__restrict__ d_na, const int32_t *__restrict__ prop_tgt,
                               const int32_t *__restrict__ vwgt, int32_t *__restrict__ part,
-                              unsigned long long *__restrict__ C, int32_t k, const RebalCtl *__restrict__ ctl,
+                              unsigned long long *__restrict__ C, int32_t K, const RebalCtl *__restrict__ ctl,
                               int32_t *__restrict__ R_node, int32_t *__restrict__ R_from,
                               int32_t *__restrict__ R_to, int32_t *__restrict__ R_sub, int32_t *__restrict__ r_to,
                               int32_t *__restrict__ r_at) {
     extern __shared__ unsigned long long s_delta[];
-    BlockDelta bd{s_delta, k};
+    BlockDelta bd = make_block_delta(s_delta, K, C);
     bd.init();
     const int64_t cnt = *d_na;
     const int64_t off = ctl->nR;
@@ -378,8 +496,8 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
     const int G = rebalance_group(g.k);
     const int64_t groups = 256 / G;
     const int64_t blocks = std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 16);
-#define UPR_PROP(GG) k_propose<GG><<<(unsigned)blocks, 256, 0, s>>>(list, d_n1, part, W, g.vwgt, g.k, st, prop_tgt, \
-                                                                    prop_gain, flags)
+#define UPR_PROP(GG) k_propose<GG><<<(unsigned)blocks, 256, 0, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, \
+                                                                    flags)
     switch (G) {
         case 4: UPR_PROP(4); break;
         case 8: UPR_PROP(8); break;
@@ -408,7 +526,8 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
                             int32_t *prop_gain, int32_t *flags, cudaStream_t s) {
     if (n1_max <= 0) return;
     const int k = g.k;
-    const size_t shm = sizeof(int32_t) * (size_t)k + (size_t)k + 16;
+    const bool batch = g.ng > 1;
+    const size_t shm = batch ? 0 : sizeof(int32_t) * (size_t)k + (size_t)k + 16;
     if (k % 4 == 0 && k <= 256) {
         int G = 1;
         while (G < 32 && 4 * G < k) G <<= 1;
@@ -416,9 +535,18 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
         const bool exact = k == 4 * G * CH;
         const int64_t groups = 256 / G;
         const int64_t blocks = std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 8);
-#define UPR_PV(GG, CC, EX) k_propose_vec<GG, CC, EX><<<(unsigned)blocks, 256, shm, s>>>(list, d_n1, part, W, g.vwgt, \
-                                                                                    k, st, prop_tgt, prop_gain, flags)
-#define UPR_PVE(GG, CC) do { if (exact) UPR_PV(GG, CC, true); else UPR_PV(GG, CC, false); } while (0)
+#define UPR_PV(GG, CC, EX, BA) k_propose_vec<GG, CC, EX, BA><<<(unsigned)blocks, 256, shm, s>>>( \
+        g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags)
+#define UPR_PVE(GG, CC)                                \
+    do {                                               \
+        if (batch) {                                   \
+            if (exact) UPR_PV(GG, CC, true, true);     \
+            else UPR_PV(GG, CC, false, true);          \
+        } else {                                       \
+            if (exact) UPR_PV(GG, CC, true, false);    \
+            else UPR_PV(GG, CC, false, false);         \
+        }                                              \
+    } while (0)
         if (CH == 1) {
             switch (G) {
                 case 1: UPR_PVE(1, 1); break;
@@ -482,25 +610,38 @@ void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, con
                      int64_t na_max, cudaStream_t s) {
     if (na_max <= 0) return;
     const int64_t blocks = std::min<int64_t>(ceil_div(na_max, 256), (int64_t)device_sm_count() * 4);
-    k_apply_rebal<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
-        P, A, S, Adm, d_na, prop_tgt, g.vwgt, part, (unsigned long long *)C, g.k, ctl, R_node, R_from, R_to, R_sub,
+    k_apply_rebal<<<(unsigned)blocks, 256, block_delta_smem(g.K()), s>>>(
+        P, A, S, Adm, d_na, prop_tgt, g.vwgt, part, (unsigned long long *)C, g.K(), ctl, R_node, R_from, R_to, R_sub,
         r_to, r_at);
     UPR_LAUNCH_CHECK();
 }
 
-void rebalance_init(const int64_t *C, int32_t k, int64_t Lmax, int8_t *excl, RebalCtl *ctl, cudaStream_t s) {
-    k_reb_init<<<1, 256, 0, s>>>(C, k, Lmax, excl, ctl);
+// Grid of a batch controller: warp per graph (begin) or thread per block.
+inline unsigned ctl_grid(int64_t items) {
+    return (unsigned)std::min<int64_t>(ceil_div(items > 0 ? items : 1, 256), (int64_t)sm_count_reb() * 2);
+}
+
+void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl *ctl, cudaStream_t s) {
+    if (g.ng == 1) k_reb_init<<<1, 256, 0, s>>>(C, g.Lb, g.K(), excl, ctl);
+    else k_reb_init_batch<<<ctl_grid(g.K()), 256, 0, s>>>(C, g.Lb, g.K(), excl, ctl);
     UPR_LAUNCH_CHECK();
 }
 
-void rebalance_begin(const int64_t *C, int32_t k, int64_t Lmax, const int8_t *excl, int8_t *over, int8_t *reject,
-                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, cudaStream_t s) {
-    k_reb_begin<<<1, 256, 0, s>>>(C, k, Lmax, excl, over, reject, d_n1, h, max_subrounds, ctl);
+void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
+                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, int32_t *light,
+                     cudaStream_t s) {
+    if (g.ng == 1)
+        k_reb_begin<<<1, 256, 0, s>>>(C, g.Lb, g.k, excl, over, reject, d_n1, h, max_subrounds, ctl);
+    else
+        k_reb_begin_batch<<<ctl_grid((int64_t)g.ng * 32), 256, 0, s>>>(C, g.Lb, g.k, g.ng, excl, over, reject, d_n1,
+                                                                       h, max_subrounds, ctl, light);
     UPR_LAUNCH_CHECK();
 }
 
-void rebalance_end(int32_t k, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl, cudaStream_t s) {
-    k_reb_end<<<1, 256, 0, s>>>(k, excl, reject, d_na, ctl);
+void rebalance_end(const GraphDev &g, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl,
+                   cudaStream_t s) {
+    if (g.ng == 1) k_reb_end<<<1, 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
+    else k_reb_end_batch<<<ctl_grid(g.K()), 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
     UPR_LAUNCH_CHECK();
 }
 

@@ -64,17 +64,17 @@ __device__ __forceinline__ int64_t penalty(const Penalty &p, int32_t b, int64_t 
 
 __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
                           const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
-                          int32_t t_num, int32_t t_den, unsigned long long *__restrict__ BW, int use_shared,
-                          int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out) {
+                          int32_t kmask, int32_t K, int32_t t_num, int32_t t_den, unsigned long long *__restrict__ BW,
+                          int use_shared, int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out) {
     extern __shared__ unsigned long long s_bw[];
-    const int bins = k * kSlots;
+    const int bins = K * kSlots;
     if (use_shared) {
         for (int i = threadIdx.x; i < bins; i += blockDim.x) s_bw[i] = 0;
         __syncthreads();
     }
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = part[v];
-        const int64_t own = W[v * (int64_t)k + a];
+        const int64_t own = W[v * (int64_t)k + blk_local(a, k, kmask)];
         const int64_t c = vwgt ? vwgt[v] : 1;
         const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wI[v];
         const int s = slot_of((uint64_t)own, (uint64_t)c);
@@ -92,9 +92,9 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
     }
 }
 
-__global__ void k_bucket_prefix(const int64_t *__restrict__ BW, int64_t *__restrict__ PW, int32_t k) {
+__global__ void k_bucket_prefix(const int64_t *__restrict__ BW, int64_t *__restrict__ PW, int32_t K) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= k) return;
+    if (b >= K) return;
     int64_t acc = 0;
     for (int l = 0; l < kSlots; l++) { acc += BW[b * kSlots + l]; PW[b * kSlots + l] = acc; }
 }
@@ -103,29 +103,33 @@ __global__ void k_bucket_prefix(const int64_t *__restrict__ BW, int64_t *__restr
 // ties to the smaller block id; candidate iff the score is positive and v is
 // a boundary node.
 template <int G>
-__global__ void __launch_bounds__(256) k_select(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
-                                                const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt,
-                                                int64_t n, int32_t k, Penalty pen, int32_t *__restrict__ cand_tgt,
-                                                int64_t *__restrict__ cand_s0, int32_t *__restrict__ cand_gain,
-                                                int32_t *__restrict__ flags) {
+__global__ void __launch_bounds__(256) k_select(const GraphDev g, const int32_t *__restrict__ part,
+                                                const int32_t *__restrict__ W, Penalty pen,
+                                                int32_t *__restrict__ cand_tgt, int64_t *__restrict__ cand_s0,
+                                                int32_t *__restrict__ cand_gain, int32_t *__restrict__ flags) {
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    const int64_t n = g.n;
+    const int32_t k = g.k;
     for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
         const int64_t v = base + gid;
         const bool active = v < n;
         int64_t best = 0;
-        int32_t bt = -1, bg = 0;
+        int32_t bt = -1, bg = 0, b0 = 0;
         if (active) {
-            const int32_t a = part[v];
+            const int32_t ag = part[v];
+            const int32_t a = blk_local(g, ag);
+            b0 = ag - a;
             const int32_t *row = W + v * (int64_t)k;
             const int32_t own = row[a];
-            if (own < wI[v]) {
-                const int64_t c = vwgt ? vwgt[v] : 1;
+            if (own < g.wI[v]) {
+                const int64_t c = g.vwgt ? g.vwgt[v] : 1;
                 for (int b = gl; b < k; b += G) {
                     const int32_t w = row[b];
                     if (b == a || w <= 0) continue;
                     const int64_t gain = (int64_t)w - own;
-                    const int64_t p = penalty(pen, b, pen.C[b] + c - pen.Lmax, c);
+                    const int32_t gb = b0 + b;
+                    const int64_t p = penalty(pen, gb, pen.C[gb] + c - pen.Lb[gb], c);
                     if (p < 0) continue;
                     const int64_t sc = gain - p;
                     if (bt < 0 || sc > best) { best = sc; bt = b; bg = (int32_t)gain; }
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(256) k_select(const int32_t *__restrict__ part
         const int32_t gsel = group_sum<G>((id >= 0 && bt == id) ? bg : 0);
         if (active && gl == 0) {
             const bool cand = id >= 0 && s > 0;
-            cand_tgt[v] = cand ? id : -1;
+            cand_tgt[v] = cand ? b0 + id : -1;
             cand_s0[v] = cand ? s : 0;
             cand_gain[v] = cand ? gsel : 0;
             flags[v] = cand ? 1 : 0;
@@ -153,31 +157,35 @@ __device__ __forceinline__ int32_t int4_get(const int4 &x, int c) {
 
 // Vectorised form of k_select for k % 4 == 0, k <= 4*G*CH: lane gl of a group
 // holds blocks [4(gl + G j), 4(gl + G j) + 4) of the row in one int4 per j.
-// The per-block slack L_max - C[b] and the factors F_r (and, when they fit,
-// the bucket prefixes) are staged in shared memory; a move into a block with
-// room for it costs no penalty and needs no search.
-template <int G, int CH, bool EXACT>
-__global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
-                                                    const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt,
-                                                    int64_t n, int32_t k, Penalty pen, int smem_pw,
+// With one graph (BATCH false) the per-block slack L_max - C[b] and the
+// factors F_r (and, when they fit, the bucket prefixes) are staged in shared
+// memory; in a batch each node reads its own graph's blocks from global
+// memory.  A move into a block with room for it costs no penalty and needs no
+// search.
+template <int G, int CH, bool EXACT, bool BATCH>
+__global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int32_t *__restrict__ part,
+                                                    const int32_t *__restrict__ W, Penalty pen, int smem_pw,
                                                     int32_t *__restrict__ cand_tgt, int64_t *__restrict__ cand_s0,
                                                     int32_t *__restrict__ cand_gain, int32_t *__restrict__ flags) {
     // s_slack[b] = L_max - C[b] clamped to 2^31 - 1 (blocks start balanced, so
     // it is >= 0): a node of weight c < 2^31 overfills b iff c > s_slack[b],
     // and then x = c - s_slack[b] is exact.
     extern __shared__ int64_t s_mem[];
+    const int64_t n = g.n;
+    const int32_t k = g.k;
     int64_t *s_F = s_mem;
     int64_t *s_PW = s_mem + kSlots;
     int32_t *s_slack = reinterpret_cast<int32_t *>(s_mem + kSlots + (smem_pw ? (size_t)k * kSlots : 0));
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const int64_t sl = pen.Lmax - pen.C[i];
-        s_slack[i] = (int32_t)(sl > 0x7fffffffLL ? 0x7fffffffLL : sl);
-    }
+    if (!BATCH)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            const int64_t sl = pen.Lb[i] - pen.C[i];
+            s_slack[i] = (int32_t)(sl > 0x7fffffffLL ? 0x7fffffffLL : sl);
+        }
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) s_F[i] = pen.F[i];
-    if (smem_pw)
+    if (!BATCH && smem_pw)
         for (int i = threadIdx.x; i < k * kSlots; i += blockDim.x) s_PW[i] = pen.PW[i];
     __syncthreads();
-    const int64_t *PW = smem_pw ? s_PW : pen.PW;
+    const int64_t *PW = (!BATCH && smem_pw) ? s_PW : pen.PW;
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
@@ -185,10 +193,12 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
         const int64_t v = base + gid;
         const bool active = v < n;
         int4 r[CH];
-        int32_t a = 0;
+        int32_t a = 0, b0 = 0;
         const int4 zero = make_int4(0, 0, 0, 0);
         if (active) {
-            a = part[v];
+            const int32_t ag = part[v];
+            a = BATCH ? blk_local(g, ag) : ag;
+            b0 = ag - a;
             const int4 *row4 = reinterpret_cast<const int4 *>(W + v * (int64_t)k);
 #pragma unroll
             for (int j = 0; j < CH; j++) {
@@ -210,8 +220,8 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
         // skipped and every score kept lies in [1, 2^31).
         int32_t best = 0;
         int32_t bt = -1, bg = 0;
-        if (active && own < wI[v]) {
-            const int32_t c = vwgt ? vwgt[v] : 1;
+        if (active && own < g.wI[v]) {
+            const int32_t c = g.vwgt ? g.vwgt[v] : 1;
 #pragma unroll
             for (int j = 0; j < CH; j++) {
 #pragma unroll
@@ -221,9 +231,16 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
                     if ((!EXACT && b >= k) || w <= own) continue;
                     const int32_t gain = w - own;
                     int32_t sc = gain;
-                    if (c > s_slack[b]) {
-                        const int64_t x = (int64_t)c - s_slack[b];
-                        const int64_t *row = PW + (int64_t)b * kSlots;
+                    int32_t slack;
+                    if (BATCH) {
+                        const int64_t sl = pen.Lb[b0 + b] - pen.C[b0 + b];
+                        slack = (int32_t)(sl > 0x7fffffffLL ? 0x7fffffffLL : sl);
+                    } else {
+                        slack = s_slack[b];
+                    }
+                    if (c > slack) {
+                        const int64_t x = (int64_t)c - slack;
+                        const int64_t *row = PW + (int64_t)(b0 + b) * kSlots;
                         if (row[kSlots - 1] < x) continue;          // no slot covers the excess: forbidden
                         int lo = 0, hi = kSlots - 1;
                         while (lo < hi) {
@@ -244,7 +261,7 @@ __global__ void __launch_bounds__(256) k_select_vec(const int32_t *__restrict__ 
         const int32_t gsel = group_sum<G>((id >= 0 && bt == id) ? bg : 0);
         if (active && gl == 0) {
             const bool cand = id >= 0 && sbest > 0;
-            cand_tgt[v] = cand ? id : -1;
+            cand_tgt[v] = cand ? b0 + id : -1;
             cand_s0[v] = cand ? sbest : 0;
             cand_gain[v] = cand ? gsel : 0;
             flags[v] = cand ? 1 : 0;
@@ -289,7 +306,7 @@ __global__ void k_inflow(const int32_t *__restrict__ cand_idx, const uint32_t *_
         const int32_t t = cand_tgt[v];
         const int64_t c = vwgt ? vwgt[v] : 1;
         const int64_t inflow = c_excl[j] - c_excl[seg_first[t]];
-        const int64_t p = penalty(pen, t, pen.C[t] + inflow + c - pen.Lmax, c);
+        const int64_t p = penalty(pen, t, pen.C[t] + inflow + c - pen.Lb[t], c);
         const int64_t s = (int64_t)cand_gain[v] - p;
         const bool kp = p >= 0 && s > 0;
         keep[i] = kp ? 1 : 0;
@@ -312,12 +329,12 @@ __global__ void k_apply_moves(const int32_t *__restrict__ cand_idx, const int32_
                               const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ score,
                               const int32_t *__restrict__ vwgt, const int64_t *__restrict__ xadj,
                               const int32_t *__restrict__ part0, int32_t *__restrict__ part,
-                              unsigned long long *__restrict__ C, int32_t k, int32_t *__restrict__ M_node,
+                              unsigned long long *__restrict__ C, int32_t K, int32_t *__restrict__ M_node,
                               int32_t *__restrict__ M_from, int32_t *__restrict__ M_to,
                               int64_t *__restrict__ M_score, int32_t *__restrict__ m_pos,
                               unsigned long long *__restrict__ deg_sum) {
     extern __shared__ unsigned long long s_delta[];
-    BlockDelta bd{s_delta, k};
+    BlockDelta bd = make_block_delta(s_delta, K, C);
     bd.init();
     const int64_t cnt = *d_count;
     long long degs = 0;
@@ -352,19 +369,21 @@ __global__ void k_apply_moves(const int32_t *__restrict__ cand_idx, const int32_
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
              int64_t *PW, int8_t *avail_out, int32_t *slot_out, cudaStream_t s) {
     ensure_pow3();
-    UPR_CUDA(cudaMemsetAsync(BW, 0, sizeof(int64_t) * g.k * kSlots, s));
+    const int32_t K = g.K();
+    UPR_CUDA(cudaMemsetAsync(BW, 0, sizeof(int64_t) * K * kSlots, s));
     if (g.n > 0) {
-        const size_t shm = sizeof(unsigned long long) * (size_t)g.k * kSlots;
+        const size_t shm = sizeof(unsigned long long) * (size_t)K * kSlots;
         const int use_shared = shm <= 200 * 1024;
         if (use_shared && shm > 48 * 1024)
             UPR_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         int64_t blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * (shm > 48 * 1024 ? 1 : 4));
-        k_buckets<<<(unsigned)blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, t_num, t_den,
-                                                                      (unsigned long long *)BW, use_shared,
-                                                                      avail_out, slot_out);
+        if (!use_shared) blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * 8);
+        k_buckets<<<(unsigned)blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, g.kmask, K,
+                                                                      t_num, t_den, (unsigned long long *)BW,
+                                                                      use_shared, avail_out, slot_out);
         UPR_LAUNCH_CHECK();
     }
-    k_bucket_prefix<<<(unsigned)ceil_div(g.k, 128), 128, 0, s>>>(BW, PW, g.k);
+    k_bucket_prefix<<<(unsigned)ceil_div(K, 128), 128, 0, s>>>(BW, PW, K);
     UPR_LAUNCH_CHECK();
 }
 
@@ -377,19 +396,29 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
                   int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s) {
     if (g.n == 0) return;
     const int k = g.k;
+    const bool batch = g.ng > 1;
     if (k % 4 == 0 && k <= 256) {
         int G = 1;
         while (G < 32 && 4 * G < k) G <<= 1;
         const int CH = (k + 4 * G - 1) / (4 * G);
         const bool exact = k == 4 * G * CH;
-        const int smem_pw = (size_t)k * kSlots * 8 <= 40 * 1024;
-        const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) + sizeof(int32_t) * k;
+        const int smem_pw = !batch && (size_t)k * kSlots * 8 <= 40 * 1024;
+        const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) +
+                           (batch ? 0 : sizeof(int32_t) * k);
         const int64_t groups = 256 / G;
         const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
-#define UPR_SELV(GG, CC, EX) k_select_vec<GG, CC, EX><<<(unsigned)blocks, 256, shm, s>>>(part, W, g.wI, g.vwgt, g.n, k, \
-                                                                                     pen, smem_pw, cand_tgt, cand_s0, \
-                                                                                     cand_gain, flags)
-#define UPR_SELVE(GG, CC) do { if (exact) UPR_SELV(GG, CC, true); else UPR_SELV(GG, CC, false); } while (0)
+#define UPR_SELV(GG, CC, EX, BA) k_select_vec<GG, CC, EX, BA><<<(unsigned)blocks, 256, shm, s>>>( \
+        g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags)
+#define UPR_SELVE(GG, CC)                                          \
+    do {                                                           \
+        if (batch) {                                               \
+            if (exact) UPR_SELV(GG, CC, true, true);               \
+            else UPR_SELV(GG, CC, false, true);                    \
+        } else {                                                   \
+            if (exact) UPR_SELV(GG, CC, true, false);              \
+            else UPR_SELV(GG, CC, false, false);                   \
+        }                                                          \
+    } while (0)
         if (CH == 1) {
             switch (G) {
                 case 1: UPR_SELVE(1, 1); break;
@@ -410,8 +439,7 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
     const int G = select_group(k);
     const int64_t groups = 256 / G;
     const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 16);
-#define UPR_SEL(GG) k_select<GG><<<(unsigned)blocks, 256, 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, pen, cand_tgt, \
-                                                                  cand_s0, cand_gain, flags)
+#define UPR_SEL(GG) k_select<GG><<<(unsigned)blocks, 256, 0, s>>>(g, part, W, pen, cand_tgt, cand_s0, cand_gain, flags)
     switch (G) {
         case 4: UPR_SEL(4); break;
         case 8: UPR_SEL(8); break;
@@ -461,8 +489,8 @@ void apply_moves(const GraphDev &g, const int32_t *cand_idx, const int32_t *m_id
     UPR_CUDA(cudaMemsetAsync(deg_sum, 0, sizeof(int64_t), s));
     if (max_count <= 0) return;
     const int64_t blocks = std::min<int64_t>(ceil_div(max_count, 256), (int64_t)device_sm_count() * 4);
-    k_apply_moves<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
-        cand_idx, m_idx, order, d_count, cand_tgt, score, g.vwgt, g.xadj, part0, part, (unsigned long long *)C, g.k,
+    k_apply_moves<<<(unsigned)blocks, 256, block_delta_smem(g.K()), s>>>(
+        cand_idx, m_idx, order, d_count, cand_tgt, score, g.vwgt, g.xadj, part0, part, (unsigned long long *)C, g.K(),
         M_node, M_from, M_to, M_score, m_pos, (unsigned long long *)deg_sum);
     UPR_LAUNCH_CHECK();
 }

@@ -15,6 +15,8 @@
 // sum and the running maximum of need a segmented max-scan.
 //
 // All list lengths (|M|, |R|, |I|) are read from device memory.
+#include <climits>
+
 #include "kernels.h"
 
 namespace upr {
@@ -83,9 +85,10 @@ __global__ void k_ev_delta(const int32_t *__restrict__ M_node, const uint32_t *_
 __global__ void k_ev_need(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys,
                           const int32_t *__restrict__ d_nM, const int64_t *__restrict__ delta,
                           const int64_t *__restrict__ d_excl, const int32_t *__restrict__ ebeg,
-                          const int64_t *__restrict__ C0, int64_t Lmax, const int32_t *__restrict__ rbeg,
-                          const int32_t *__restrict__ rend, const int64_t *__restrict__ rc_excl,
-                          const int64_t *__restrict__ rc, uint64_t *__restrict__ packed) {
+                          const int64_t *__restrict__ C0, const int64_t *__restrict__ Lb,
+                          const int32_t *__restrict__ rbeg, const int32_t *__restrict__ rend,
+                          const int64_t *__restrict__ rc_excl, const int64_t *__restrict__ rc,
+                          uint64_t *__restrict__ packed) {
     const int64_t nev = 2 * (int64_t)*d_nM;
     UPR_FOR(q, nev) {
         const uint32_t e = EV[q];
@@ -94,6 +97,7 @@ __global__ void k_ev_need(const uint32_t *__restrict__ EV, const uint64_t *__res
         const int32_t r0 = rbeg[b], r1 = rend[b];
         if ((e & 1) && r1 > r0) {
             const int64_t D = C0[b] + (d_excl[q] + delta[q]) - d_excl[ebeg[b]];
+            const int64_t Lmax = Lb[b];
             if (D > Lmax) {
                 // smallest x in [1, |R_b|] with D - (weight of R_b[0..x)) <= L_max, else |R_b|
                 const int64_t base = rc_excl[r0];
@@ -128,12 +132,12 @@ __global__ void k_ev_emit(const uint32_t *__restrict__ EV, const uint64_t *__res
 }
 
 // per block: final emitted count and leftover count
-__global__ void k_block_final(int32_t k, const int32_t *__restrict__ ebeg, const int32_t *__restrict__ eend,
+__global__ void k_block_final(int32_t K, const int32_t *__restrict__ ebeg, const int32_t *__restrict__ eend,
                               const uint64_t *__restrict__ qmax, const int32_t *__restrict__ rbeg,
                               const int32_t *__restrict__ rend, int32_t *__restrict__ qfin,
                               int32_t *__restrict__ left) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= k) return;
+    if (b >= K) return;
     const int32_t f = eend[b] > ebeg[b] ? (int32_t)(uint32_t)qmax[eend[b] - 1] : 0;
     qfin[b] = f;
     left[b] = (rend[b] - rbeg[b]) - f;
@@ -326,10 +330,12 @@ __global__ void k_iev_delta(const int32_t *__restrict__ I_node, const uint32_t *
 __global__ void k_iev_transitions(const uint32_t *__restrict__ EV, const uint64_t *__restrict__ ekeys,
                                   const int32_t *__restrict__ d_nI, const int64_t *__restrict__ delta,
                                   const int64_t *__restrict__ d_excl, const int32_t *__restrict__ ebeg,
-                                  const int64_t *__restrict__ C0, int64_t Lmax, int32_t *__restrict__ diff) {
+                                  const int64_t *__restrict__ C0, const int64_t *__restrict__ Lb,
+                                  int32_t *__restrict__ diff) {
     const int64_t nev = 2 * (int64_t)*d_nI;
     UPR_FOR(q, nev) {
         const int32_t b = (int32_t)ekeys[q];
+        const int64_t Lmax = Lb[b];
         const int64_t before = C0[b] + d_excl[q] - d_excl[ebeg[b]];
         const int64_t after = before + delta[q];
         const int t = (after > Lmax ? 1 : 0) - (before > Lmax ? 1 : 0);
@@ -337,16 +343,11 @@ __global__ void k_iev_transitions(const uint32_t *__restrict__ EV, const uint64_
     }
 }
 
-// number of blocks above L_max
-__global__ void k_count_over(const int64_t *__restrict__ C, int32_t k, int64_t Lmax, int32_t *__restrict__ out) {
-    __shared__ int s;
-    if (threadIdx.x == 0) s = 0;
-    __syncthreads();
-    int c = 0;
-    for (int b = threadIdx.x; b < k; b += blockDim.x) c += C[b] > Lmax;
-    if (c) atomicAdd(&s, c);
-    __syncthreads();
-    if (threadIdx.x == 0) *out = s;
+// number of blocks above L_max, per graph (out[0..ng) zeroed by the caller)
+__global__ void k_count_over(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t K, int32_t k,
+                             int32_t *__restrict__ out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K; b += gridDim.x * blockDim.x)
+        if (C[b] > Lb[b]) atomicAdd(&out[b / k], 1);
 }
 
 // best prefix: max G(j) over eligible j (ties: smallest j); G(0) = 0, eligible(0) = (over0 == 0)
@@ -409,9 +410,9 @@ __global__ void __launch_bounds__(1024) k_best_final(const long long *__restrict
 __global__ void k_apply_prefix(const int32_t *__restrict__ I_node, const int32_t *__restrict__ I_from,
                                const int32_t *__restrict__ I_to, const long long *__restrict__ best,
                                const int32_t *__restrict__ vwgt, int32_t *__restrict__ part0,
-                               unsigned long long *__restrict__ C0, int32_t k, long long *__restrict__ cut) {
+                               unsigned long long *__restrict__ C0, int32_t K, long long *__restrict__ cut) {
     extern __shared__ unsigned long long s_delta[];
-    BlockDelta bd{s_delta, k};
+    BlockDelta bd = make_block_delta(s_delta, K, C0);
     bd.init();
     const long long len = best[1];
     if (blockIdx.x == 0 && threadIdx.x == 0 && len >= 0) atomicAdd((unsigned long long *)cut, (unsigned long long)(-best[0]));
@@ -425,6 +426,169 @@ __global__ void k_apply_prefix(const int32_t *__restrict__ I_node, const int32_t
             b = I_to[j];
             c = vwgt ? vwgt[v] : 1;
             part0[v] = b;
+        }
+        bd.add(a, -c);
+        bd.add(b, c);
+    }
+    bd.flush(C0);
+}
+
+// ---- batches: I sorted by graph (stable), then per-graph segments
+// [seg_beg[g], seg_end[g]) of I; G_g(j) and eligibility are differences of
+// the global prefix sums taken at the segment start.
+
+// keys: graph of each move of I
+__global__ void k_i_graph_keys(const int32_t *__restrict__ I_node, const int32_t *__restrict__ d_nI,
+                               const int32_t *__restrict__ gid, uint64_t *__restrict__ keys,
+                               uint32_t *__restrict__ vals) {
+    const int64_t nI = *d_nI;
+    UPR_FOR(i, nI) {
+        keys[i] = (uint64_t)gid[I_node[i]];
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// I in graph order (out arrays), pos/dest of the moved nodes, segment bounds
+__global__ void k_i_permute(const uint32_t *__restrict__ order, const uint64_t *__restrict__ gkeys,
+                            const int32_t *__restrict__ d_nI, const int32_t *__restrict__ I_node,
+                            const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to,
+                            int32_t *__restrict__ O_node, int32_t *__restrict__ O_from, int32_t *__restrict__ O_to,
+                            int32_t *__restrict__ pos, int32_t *__restrict__ dest, int32_t *__restrict__ seg_beg,
+                            int32_t *__restrict__ seg_end) {
+    const int64_t nI = *d_nI;
+    UPR_FOR(q, nI) {
+        const uint32_t i = order[q];
+        const int32_t v = I_node[i];
+        O_node[q] = v;
+        O_from[q] = I_from[i];
+        O_to[q] = I_to[i];
+        pos[v] = (int32_t)q;
+        dest[v] = I_to[i];
+        const int32_t g = (int32_t)gkeys[q];
+        if (q == 0 || (int32_t)gkeys[q - 1] != g) seg_beg[g] = (int32_t)q;
+        if (q == nI - 1 || (int32_t)gkeys[q + 1] != g) seg_end[g] = (int32_t)(q + 1);
+    }
+}
+
+// per graph: best gain so far = 0 if the empty prefix is eligible, else "none"
+__global__ void k_best_seg_init(const int32_t *__restrict__ over0, int32_t ng, long long *__restrict__ best_g,
+                                long long *__restrict__ best_j) {
+    UPR_FOR(g, ng) {
+        best_g[g] = over0[g] == 0 ? 0 : LLONG_MIN;
+        best_j[g] = LLONG_MAX;
+    }
+}
+
+struct SegPoint { int32_t g; long long G; long long j; bool elig; };
+
+// Prefix of length j = i - seg_beg + 1 of move i's graph: its gain and eligibility.
+__device__ __forceinline__ SegPoint seg_point(int64_t i, const int32_t *I_node, const int32_t *gid,
+                                              const int32_t *seg_beg, const int64_t *Gsum, const int32_t *diff,
+                                              const int32_t *diff_excl, const int32_t *over0) {
+    const int32_t g = gid[I_node[i]];
+    const int32_t s = seg_beg[g];
+    const long long G = Gsum[i] - (s > 0 ? Gsum[s - 1] : 0);
+    const int32_t over = over0[g] + (diff_excl[i + 1] + diff[i + 1]) - (diff_excl[s] + diff[s]);
+    return SegPoint{g, G, (long long)(i - s + 1), over == 0};
+}
+
+__global__ void k_best_seg_max(const int32_t *__restrict__ I_node, const int32_t *__restrict__ d_nI,
+                               const int32_t *__restrict__ gid, const int32_t *__restrict__ seg_beg,
+                               const int64_t *__restrict__ Gsum, const int32_t *__restrict__ diff,
+                               const int32_t *__restrict__ diff_excl, const int32_t *__restrict__ over0,
+                               long long *__restrict__ best_g) {
+    const int64_t nI = *d_nI;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nI; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int32_t key = -1;
+        long long val = LLONG_MIN;
+        if (i < nI) {
+            const SegPoint p = seg_point(i, I_node, gid, seg_beg, Gsum, diff, diff_excl, over0);
+            if (p.elig) { key = p.g; val = p.G; }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        long long m = val;
+        for (unsigned r = peers; r; r &= r - 1) m = max(m, __shfl_sync(peers, val, __ffs(r) - 1));
+        if (key >= 0 && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0) atomicMax(&best_g[key], m);
+    }
+}
+
+__global__ void k_best_seg_min(const int32_t *__restrict__ I_node, const int32_t *__restrict__ d_nI,
+                               const int32_t *__restrict__ gid, const int32_t *__restrict__ seg_beg,
+                               const int64_t *__restrict__ Gsum, const int32_t *__restrict__ diff,
+                               const int32_t *__restrict__ diff_excl, const int32_t *__restrict__ over0,
+                               const long long *__restrict__ best_g, long long *__restrict__ best_j) {
+    const int64_t nI = *d_nI;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nI; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int32_t key = -1;
+        long long val = LLONG_MAX;
+        if (i < nI) {
+            const SegPoint p = seg_point(i, I_node, gid, seg_beg, Gsum, diff, diff_excl, over0);
+            if (p.elig && p.G == best_g[p.g]) { key = p.g; val = p.j; }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        long long m = val;
+        for (unsigned r = peers; r; r &= r - 1) m = min(m, __shfl_sync(peers, val, __ffs(r) - 1));
+        if (key >= 0 && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0) atomicMin(&best_j[key], m);
+    }
+}
+
+// per graph: j* (the empty prefix wins ties), cut update; totals for the
+// round statistics in tot[0..3) = (sum of j*, sum of gains, infeasible graphs)
+__global__ void k_best_seg_final(const int32_t *__restrict__ over0, int32_t ng, long long *__restrict__ best_g,
+                                 long long *__restrict__ best_j, long long *__restrict__ cut,
+                                 int32_t *__restrict__ infeasible, unsigned long long *__restrict__ tot) {
+    long long sj = 0, sg = 0, ninf = 0;
+    UPR_FOR(g, ng) {
+        long long G = best_g[g], j;
+        if (G == LLONG_MIN) {
+            infeasible[g] = 1;
+            G = 0;
+            j = 0;
+            ninf++;
+        } else {
+            infeasible[g] = 0;
+            j = (over0[g] == 0 && G == 0) ? 0 : best_j[g];
+            cut[g] -= G;
+        }
+        best_g[g] = G;
+        best_j[g] = j;
+        sj += j;
+        sg += G;
+    }
+    sj = warp_sum(sj);
+    sg = warp_sum(sg);
+    ninf = warp_sum(ninf);
+    if ((threadIdx.x & 31) == 0) {
+        if (sj) atomicAdd(&tot[0], (unsigned long long)sj);
+        if (sg) atomicAdd(&tot[1], (unsigned long long)sg);
+        if (ninf) atomicAdd(&tot[2], (unsigned long long)ninf);
+    }
+}
+
+__global__ void k_apply_prefix_seg(const int32_t *__restrict__ I_node, const int32_t *__restrict__ I_from,
+                                   const int32_t *__restrict__ I_to, const int32_t *__restrict__ d_nI,
+                                   const int32_t *__restrict__ gid, const int32_t *__restrict__ seg_beg,
+                                   const long long *__restrict__ best_j, const int32_t *__restrict__ vwgt,
+                                   int32_t *__restrict__ part0, unsigned long long *__restrict__ C0, int32_t K) {
+    extern __shared__ unsigned long long s_delta[];
+    BlockDelta bd = make_block_delta(s_delta, K, C0);
+    bd.init();
+    const int64_t nI = *d_nI;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nI; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int32_t a = -1, b = -1;
+        long long c = 0;
+        if (i < nI) {
+            const int32_t v = I_node[i];
+            const int32_t g = gid[v];
+            if (i - seg_beg[g] < best_j[g]) {
+                a = I_from[i];
+                b = I_to[i];
+                c = vwgt ? vwgt[v] : 1;
+                part0[v] = b;
+            }
         }
         bd.add(a, -c);
         bd.add(b, c);
@@ -473,8 +637,9 @@ void reset_nodes(const int32_t *nodes, const int32_t *d_cnt, int64_t max, int32_
     UPR_LAUNCH_CHECK();
 }
 
-void count_over(const int64_t *C, int32_t k, int64_t Lmax, int32_t *out, cudaStream_t s) {
-    k_count_over<<<1, 256, 0, s>>>(C, k, Lmax, out);
+void count_over(const GraphDev &g, const int64_t *C, int32_t *out, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t) * g.ng, s));
+    k_count_over<<<grid_for(g.K()), 256, 0, s>>>(C, g.Lb, g.K(), g.k, out);
     UPR_LAUNCH_CHECK();
 }
 
@@ -503,10 +668,11 @@ void seq_ev_delta(const int32_t *M_node, const uint32_t *EV, const uint64_t *eke
 }
 
 void seq_ev_need(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM, int64_t max, const int64_t *delta,
-                 const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, int64_t Lmax, const int32_t *rbeg,
-                 const int32_t *rend, const int64_t *rc_excl, const int64_t *rc, uint64_t *packed, cudaStream_t s) {
-    k_ev_need<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nM, delta, d_excl, ebeg, C0, Lmax, rbeg, rend, rc_excl,
-                                                rc, packed);
+                 const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0, const int64_t *Lb,
+                 const int32_t *rbeg, const int32_t *rend, const int64_t *rc_excl, const int64_t *rc, uint64_t *packed,
+                 cudaStream_t s) {
+    k_ev_need<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nM, delta, d_excl, ebeg, C0, Lb, rbeg, rend, rc_excl, rc,
+                                                packed);
     UPR_LAUNCH_CHECK();
 }
 
@@ -516,9 +682,9 @@ void seq_ev_emit(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nM,
     UPR_LAUNCH_CHECK();
 }
 
-void seq_block_final(int32_t k, const int32_t *ebeg, const int32_t *eend, const uint64_t *qmax, const int32_t *rbeg,
+void seq_block_final(int32_t K, const int32_t *ebeg, const int32_t *eend, const uint64_t *qmax, const int32_t *rbeg,
                      const int32_t *rend, int32_t *qfin, int32_t *left, cudaStream_t s) {
-    k_block_final<<<(unsigned)ceil_div(k, 256), 256, 0, s>>>(k, ebeg, eend, qmax, rbeg, rend, qfin, left);
+    k_block_final<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(K, ebeg, eend, qmax, rbeg, rend, qfin, left);
     UPR_LAUNCH_CHECK();
 }
 
@@ -581,8 +747,8 @@ void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ek
 
 void seq_iev_transitions(const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,
                          const int64_t *delta, const int64_t *d_excl, const int32_t *ebeg, const int64_t *C0,
-                         int64_t Lmax, int32_t *diff, cudaStream_t s) {
-    k_iev_transitions<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nI, delta, d_excl, ebeg, C0, Lmax, diff);
+                         const int64_t *Lb, int32_t *diff, cudaStream_t s) {
+    k_iev_transitions<<<grid_for(2 * max), 256, 0, s>>>(EV, ekeys, d_nI, delta, d_excl, ebeg, C0, Lb, diff);
     UPR_LAUNCH_CHECK();
 }
 
@@ -598,8 +764,54 @@ void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl
 void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                       int64_t max, const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s) {
     const int64_t blocks = std::min<int64_t>(ceil_div(max > 0 ? max : 1, 256), (int64_t)device_sm_count() * 4);
-    k_apply_prefix<<<(unsigned)blocks, 256, sizeof(unsigned long long) * g.k, s>>>(
-        I_node, I_from, I_to, best, g.vwgt, part0, (unsigned long long *)C0, g.k, (long long *)cut);
+    k_apply_prefix<<<(unsigned)blocks, 256, block_delta_smem(g.K()), s>>>(
+        I_node, I_from, I_to, best, g.vwgt, part0, (unsigned long long *)C0, g.K(), (long long *)cut);
+    UPR_LAUNCH_CHECK();
+}
+
+void seq_sort_by_graph(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+                       const int32_t *d_nI, int64_t max, uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                       uint32_t *vals_alt, Scratch tmp, int32_t *O_node, int32_t *O_from, int32_t *O_to, int32_t *pos,
+                       int32_t *dest, int32_t *seg_beg, int32_t *seg_end, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(seg_beg, 0, sizeof(int32_t) * g.ng, s));
+    UPR_CUDA(cudaMemsetAsync(seg_end, 0, sizeof(int32_t) * g.ng, s));
+    if (max <= 0) return;
+    k_i_graph_keys<<<grid_for(max), 256, 0, s>>>(I_node, d_nI, g.gid, keys, vals);
+    UPR_LAUNCH_CHECK();
+    int gbits = 1;
+    while ((1ll << gbits) < g.ng) gbits++;
+    const bool alt = radix_sort_pairs(keys, vals, keys_alt, vals_alt, Count{d_nI, max}, gbits, tmp, s);
+    k_i_permute<<<grid_for(max), 256, 0, s>>>(alt ? vals_alt : vals, alt ? keys_alt : keys, d_nI, I_node, I_from, I_to,
+                                              O_node, O_from, O_to, pos, dest, seg_beg, seg_end);
+    UPR_LAUNCH_CHECK();
+}
+
+void seq_best_seg(const GraphDev &g, const int32_t *I_node, const int32_t *d_nI, int64_t max, const int32_t *seg_beg,
+                  const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl, const int32_t *over0,
+                  long long *best_g, long long *best_j, int64_t *cut, int32_t *infeasible, int64_t *tot,
+                  cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(tot, 0, 3 * sizeof(int64_t), s));
+    k_best_seg_init<<<grid_for(g.ng), 256, 0, s>>>(over0, g.ng, best_g, best_j);
+    UPR_LAUNCH_CHECK();
+    if (max > 0) {
+        k_best_seg_max<<<grid_for(max), 256, 0, s>>>(I_node, d_nI, g.gid, seg_beg, Gsum, diff, diff_excl, over0, best_g);
+        UPR_LAUNCH_CHECK();
+        k_best_seg_min<<<grid_for(max), 256, 0, s>>>(I_node, d_nI, g.gid, seg_beg, Gsum, diff, diff_excl, over0, best_g,
+                                                     best_j);
+        UPR_LAUNCH_CHECK();
+    }
+    k_best_seg_final<<<grid_for(g.ng), 256, 0, s>>>(over0, g.ng, best_g, best_j, (long long *)cut, infeasible,
+                                                    (unsigned long long *)tot);
+    UPR_LAUNCH_CHECK();
+}
+
+void seq_apply_prefix_seg(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
+                          const int32_t *d_nI, int64_t max, const int32_t *seg_beg, const long long *best_j,
+                          int32_t *part0, int64_t *C0, cudaStream_t s) {
+    if (max <= 0) return;
+    const int64_t blocks = std::min<int64_t>(ceil_div(max, 256), (int64_t)device_sm_count() * 4);
+    k_apply_prefix_seg<<<(unsigned)blocks, 256, block_delta_smem(g.K()), s>>>(
+        I_node, I_from, I_to, d_nI, g.gid, seg_beg, best_j, g.vwgt, part0, (unsigned long long *)C0, g.K());
     UPR_LAUNCH_CHECK();
 }
 

@@ -1,0 +1,143 @@
+"""Batches through the C ABI: many graphs refined by one context must give,
+graph by graph, exactly what the oracle gives for that graph alone
+(partition, cut, block weights), and what the one-graph entry points give.
+
+The batch form keeps every step per graph (own blocks, own L_max, own move
+sequence and best prefix), so there is nothing approximate to allow for:
+the comparison is bit-exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def upr():
+    from paper_2308_15494_gb300 import build
+    build.build()
+    import paper_2308_15494_gb300 as m
+    m.load()
+    return m
+
+
+def _mixed(k: int, count: int, seed: int):
+    """Graphs of one k with different sizes, weights, hubs and isolated nodes."""
+    ws = []
+    for i in range(count):
+        s = seed * 1000 + i
+        n = [30, 200, 700, 64, 1500, 9][i % 6]
+        ws.append(synth.random_small(s, n, [3, 6, 4, 8, 5, 2][i % 6], k, weighted=i % 3 != 2,
+                                     hubs=i % 4 == 1 and 2 or 0, isolated=i % 5 == 3 and 4 or 0))
+    return ws
+
+
+def _packed(ws):
+    return np.concatenate([np.asarray(w.part, np.int32) for w in ws]) if ws else np.zeros(0, np.int32)
+
+
+def _check_batch(upr, ws, rounds, device):
+    import torch
+    ctx = upr.create_batch_from_workloads(ws, device=device)
+    part = _packed(ws)
+    buf = torch.from_numpy(part.copy()).cuda() if device else part.copy()
+    status, cin, cout, st = upr.upr_batch_refine(ctx, buf, rounds)
+    got = buf.cpu().numpy() if device else buf
+    off = ctx.offsets
+    cut_b, bw_b = upr.upr_batch_cut(ctx, got)
+    for i, w in enumerate(ws):
+        rc, ref, cut, _ = oracle.refine(w, w.part, rounds)
+        mine = got[off[i]:off[i + 1]]
+        if rc == 0:
+            assert status[i] == 0, (i, w.name)
+            assert np.array_equal(mine, ref), (i, w.name)
+            assert cout[i] == cut, (i, w.name)
+        else:
+            assert status[i] == rc, (i, w.name, status[i], rc)
+            assert np.array_equal(mine, w.part), (i, w.name)
+            assert cout[i] == cin[i]
+        assert cin[i] == oracle.cut(w, w.part)[0], (i, w.name)
+        assert cut_b[i] == cout[i]
+        bw = np.bincount(mine, weights=w.vwgt if w.vwgt is not None else None, minlength=w.k).astype(np.int64)
+        assert np.array_equal(bw_b[i], bw)
+    assert st.cut_out == int(cout.sum())
+    return ctx
+
+
+@pytest.mark.parametrize("k", [2, 4, 6, 8, 12, 32, 64])
+def test_batch_matches_oracle_per_graph(upr, k):
+    _check_batch(upr, _mixed(k, 12, k), rounds=3, device=False)
+
+
+@pytest.mark.parametrize("k", [8, 256])
+def test_batch_device_buffers(upr, k):
+    _check_batch(upr, _mixed(k, 7, 50 + k), rounds=2, device=True)
+
+
+def test_batch_repairs_and_infeasible(upr):
+    """Imbalanced inputs in the batch are repaired per graph; a graph that cannot
+    be balanced keeps its input and reports UPR_ERR_INFEASIBLE while the others
+    are refined as if alone."""
+    k = 4
+    ws = _mixed(k, 6, 77)
+    bad = synth.random_small(91, 120, 4, k, balanced=False)
+    # an infeasible graph: one node heavier than L_max allows
+    n = 12
+    xadj = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    adj = np.array([sorted(((v + 1) % n, (v - 1) % n)) for v in range(n)], np.int32).ravel()
+    vw = np.ones(n, np.int32)
+    vw[0] = 40
+    inf = synth.Workload("infeasible", n, xadj, adj, None, vw, k, 0.03, np.arange(n, dtype=np.int32) % k, 2)
+    ws = [ws[0], bad, ws[1], inf, ws[2]]
+    _check_batch(upr, ws, rounds=2, device=False)
+
+
+def test_batch_equals_single_graph_calls(upr):
+    ws = _mixed(16, 5, 5)
+    ctx = upr.create_batch_from_workloads(ws)
+    part = _packed(ws)
+    upr.upr_batch_refine(ctx, part, 3)
+    off = ctx.offsets
+    for i, w in enumerate(ws):
+        c1 = upr.create_from_workload(w)
+        p1 = np.asarray(w.part, np.int32).copy()
+        upr.upr_refine(c1, p1, 3)
+        assert np.array_equal(part[off[i]:off[i + 1]], p1)
+
+
+def test_batch_chung_lu_sample(upr):
+    """A sample of the 4096-graph Chung-Lu batch (n log-uniform in [2^10, 2^16]):
+    graphs grouped by k, one context per group, against the oracle."""
+    ws = [synth.cached(synth.batch_graph, i) for i in range(12)]
+    by_k = {}
+    for w in ws:
+        by_k.setdefault(w.k, []).append(w)
+    for k, group in sorted(by_k.items()):
+        _check_batch(upr, group, rounds=group[0].rounds, device=True)
+
+
+def test_one_graph_through_batch_entry(upr):
+    w = synth.random_small(3, 300, 5, 8)
+    _check_batch(upr, [w], rounds=2, device=False)
+
+
+def test_batch_rejects_bad_input(upr):
+    ws = _mixed(4, 3, 9)
+    ctx = upr.create_batch_from_workloads(ws)
+    part = _packed(ws)
+    part[5] = 4
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_batch_refine(ctx, part, 1)
+    assert e.value.status == upr.UPR_ERR_INVALID
+    # a neighbour id outside its own graph
+    w = ws[1]
+    adj = np.asarray(w.adj, np.int32).copy()
+    adj[0] = w.n
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_batch_create([(ws[0].xadj, ws[0].adj, ws[0].vwgt, ws[0].adjw), (w.xadj, adj, w.vwgt, w.adjw)], 4,
+                             0.03)
+    assert e.value.status == upr.UPR_ERR_INVALID
