@@ -18,6 +18,7 @@ times the CPU oracle on one round of the same workload per step.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -174,9 +175,129 @@ def cpu_baseline(w):
             "sample": f"round 1 of {w.rounds} on the full workload, {t:.1f} s, 1 of {os.cpu_count()} host cores"}
 
 
+def batched_leg(args, upr, rank, ws, local, graphs):
+    """The 4096-graph Chung-Lu batch: graphs grouped by k, one batch context per
+    group on its own stream (the groups run concurrently from host threads),
+    every graph refined for its 4 rounds per step; against the plain
+    one-graph-per-call form (upr_refine per graph, graph resident) on a sample
+    of the same graphs, whose cuts must be identical."""
+    import concurrent.futures as cf
+    import torch
+    by_k = {}
+    for i, w in enumerate(graphs):
+        by_k.setdefault(w.k, []).append(i)
+    rounds = graphs[0].rounds
+    groups = []
+    for k, idx in sorted(by_k.items()):
+        st = torch.cuda.Stream()
+        ctx = upr.upr_batch_create([(graphs[i].xadj, graphs[i].adj, graphs[i].vwgt, graphs[i].adjw) for i in idx], k,
+                                   [graphs[i].eps for i in idx], stream=ctypes.c_void_p(st.cuda_stream))
+        init = torch.from_numpy(np.concatenate([graphs[i].part for i in idx]).astype(np.int32)).cuda()
+        groups.append({"k": k, "idx": idx, "stream": st, "ctx": ctx, "init": init, "part": torch.empty_like(init)})
+    torch.cuda.synchronize()
+    pool = cf.ThreadPoolExecutor(len(groups), initializer=torch.cuda.set_device, initargs=(local,))
+
+    def run_group(gr):
+        with torch.cuda.stream(gr["stream"]):
+            gr["part"].copy_(gr["init"])
+        return upr.upr_batch_refine(gr["ctx"], gr["part"], rounds)
+
+    def step():
+        return list(pool.map(run_group, groups))
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        res = step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    main = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event() for _ in groups]
+    torch.cuda.synchronize()
+    e0.record(main)
+    for gr in groups:
+        gr["stream"].wait_event(e0)
+    for _ in range(steps):
+        res = step()
+    for gr, ev in zip(groups, ends):
+        ev.record(gr["stream"])
+        main.wait_event(ev)
+    e1.record(main)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / steps
+    ng = len(graphs)
+    cut_b = np.zeros(ng, np.int64)
+    stat_b = np.zeros(ng, np.int32)
+    launches = 0
+    for gr, (status, cin, cout, st) in zip(groups, res):
+        cut_b[gr["idx"]] = cout
+        stat_b[gr["idx"]] = status
+        launches += st.kernel_launches
+    E = sum(w.m // 2 for w in graphs)
+
+    # the plain form on a sample: one context and one upr_refine per graph
+    sample = list(range(0, ng, max(1, ng // args.plain_sample)))[: args.plain_sample]
+    plain = []
+    for i in sample:
+        w = graphs[i]
+        c = upr.create_from_workload(w, device=True)
+        plain.append((i, c, torch.from_numpy(w.part.copy()).cuda()))
+    work = [torch.empty_like(p) for _, _, p in plain]
+    for (i, c, p), q in zip(plain, work):       # warm-up
+        q.copy_(p)
+        upr.upr_refine(c, q, rounds)
+    torch.cuda.synchronize()
+    e0.record(main)
+    cut_p = {}
+    for (i, c, p), q in zip(plain, work):
+        q.copy_(p)
+        cut_p[i] = upr.upr_refine(c, q, rounds).cut_out
+    e1.record(main)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    identical = all(cut_p[i] == cut_b[i] for i in sample)
+    del plain, work
+
+    # end to end: upload from host arrays, refine, read back (one step)
+    t0 = time.perf_counter()
+    outs = []
+    for k, idx in sorted(by_k.items()):
+        ctx = upr.upr_batch_create([(graphs[i].xadj, graphs[i].adj, graphs[i].vwgt, graphs[i].adjw) for i in idx],
+                                   k, [graphs[i].eps for i in idx])
+        part = np.concatenate([graphs[i].part for i in idx]).astype(np.int32)
+        outs.append(upr.upr_batch_refine(ctx, part, rounds))
+        upr.upr_destroy(ctx)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    h2d = sum(w.xadj.nbytes + w.adj.nbytes + w.part.nbytes for w in graphs)
+    d2h = sum(w.part.nbytes for w in graphs)
+    for gr in groups:
+        upr.upr_destroy(gr["ctx"])
+    pool.shutdown()
+    return {
+        "workload": f"{ng} Chung-Lu graphs, n log-uniform in [2^10, 2^16], avg degree U[4,32], exponent U[2.0,2.8], "
+                    f"k from {{2,4,8,16,32}}, eps 0.03, unit weights, {rounds} rounds; grouped by k into "
+                    f"{len(groups)} batch contexts on concurrent streams",
+        "graphs": ng, "nodes": int(sum(w.n for w in graphs)), "edges": int(E),
+        "graphs_per_s": ng / t_batch, "edges_per_s": rounds * E / t_batch, "ms_per_step": t_batch * 1e3,
+        "steps": steps, "gpu_launches_per_step": int(launches),
+        "infeasible_graphs": int((stat_b != 0).sum()),
+        "plain": {"form": "one upr_refine per graph, graph resident on the device", "graphs": len(sample),
+                  "graphs_per_s": len(sample) / t_plain, "ms_per_graph": t_plain * 1e3 / len(sample)},
+        "speedup_vs_plain": (ng / t_batch) / (len(sample) / t_plain),
+        "identical_cuts_on_sample": bool(identical),
+        "e2e": {"graphs_per_s": ng / t_e2e, "ms": t_e2e * 1e3, "h2d_bytes": int(h2d), "d2h_bytes": int(d2h),
+                "includes": "batch creation from host arrays, refinement, partition read-back"},
+    }
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = _dist()
+    graphs = None
+    if args.batch_graphs > 0 and not args.profile:
+        # generated before CUDA starts (a spawned pool); rank r owns its own graphs
+        graphs = synth.batch_graphs(args.batch_graphs, start=rank * args.batch_graphs)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -275,6 +396,13 @@ def run_gpu(args):
     e2e = {"value": ws * w.rounds * E / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": t_e2e * 1e3, "steps": e2e_steps}
 
+    batched = batched_leg(args, upr, rank, ws, local, graphs) if graphs else None
+    if batched is not None and ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([batched["ms_per_step"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        batched["ms_per_step"] = float(t.item())
+        batched["graphs_per_s"] = ws * batched["graphs"] / (batched["ms_per_step"] / 1e3)
     if rank == 0:
         cb = cpu_baseline(w) if ws == 1 and not args.no_cpu_baseline else None
         s0 = stats[-1]
@@ -288,7 +416,8 @@ def run_gpu(args):
                                        "host_wall": s0.ms_host},
                 "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
                            "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
-                           "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds}}
+                           "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds},
+                "batched": batched}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -303,6 +432,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096,
+                    help="graphs of the Chung-Lu batch per GPU (0: skip the batched leg)")
+    ap.add_argument("--plain-sample", type=int, default=256,
+                    help="graphs of the batch timed in the one-graph-per-call form")
     ap.add_argument("--shrink", type=int, default=0,
                     help="profiling only: the same workload family with 2^-shrink of the nodes")
     ap.add_argument("--profile", action="store_true",

@@ -242,6 +242,23 @@ def batch_graph(i: int, seed: int = GRAPH_SEED + 3) -> Workload:
                     {"generator": "chung-lu", "avg_deg": d, "gamma": g})
 
 
+def _batch_graph_cached(i: int) -> None:
+    cached(batch_graph, i)
+
+
+def batch_graphs(count: int, start: int = 0, workers: Optional[int] = None) -> list:
+    """Graphs start .. start+count-1 of the Chung-Lu batch, generated in a
+    pool of spawned processes (safe after CUDA is initialised) through the
+    on-disk cache, then loaded in order."""
+    idx = list(range(start, start + count))
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers > 1 and count > 8:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_batch_graph_cached, idx, chunksize=8)
+    return [cached(batch_graph, i) for i in idx]
+
+
 def random_small(seed: int, n: int, avg_deg: float, k: int, weighted: bool = True,
                  hubs: int = 0, isolated: int = 0, max_vw: int = 8, max_ew: int = 9,
                  balanced: bool = True) -> Workload:
