@@ -288,16 +288,113 @@ def batched_leg(args, upr, rank, ws, local, graphs):
         "identical_cuts_on_sample": bool(identical),
         "e2e": {"graphs_per_s": ng / t_e2e, "ms": t_e2e * 1e3, "h2d_bytes": int(h2d), "d2h_bytes": int(d2h),
                 "includes": "batch creation from host arrays, refinement, partition read-back"},
+        "_cuts": cut_b,
+    }
+
+
+def _served_pool_cached(spec):
+    synth.cached(synth.served_rmat, *spec)
+
+
+SERVED_RMAT = [(18, 8, i) for i in range(4)] + [(18, 64, i) for i in range(4, 8)] + [(21, 8, 0), (21, 64, 1)]
+
+
+def served_inputs(small):
+    """Input pools of the served mix: the first Chung-Lu batch graphs, and
+    R-MAT scale-18 / scale-21 graphs with k from {8, 64} (generated in a
+    spawned pool before CUDA starts)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(SERVED_RMAT), os.cpu_count() or 1)) as pool:
+        pool.map(_served_pool_cached, SERVED_RMAT)
+    rm = [synth.cached(synth.served_rmat, *spec) for spec in SERVED_RMAT]
+    return {"small": small, "s18": [w for w in rm if w.info["scale"] == 18],
+            "s21": [w for w in rm if w.info["scale"] == 21]}
+
+
+def served_leg(args, upr, pools, batched_cuts):
+    """Poisson stream of requests (50% Chung-Lu batch graphs, 40% R-MAT scale
+    18, 10% R-MAT scale 21) into the continuous-batching server.  The arrival
+    rate is 0.7 x the capacity measured by a closed-loop burst of the same mix
+    just before; latency is arrival (scheduled submit time) to result."""
+    import concurrent.futures as cf
+    rng = np.random.default_rng(20230815)
+    kinds = ["small", "s18", "s21"]
+    probs = [0.5, 0.4, 0.1]
+
+    def draw():
+        kind = kinds[int(rng.choice(3, p=probs))]
+        pool = pools[kind]
+        return kind, int(rng.integers(len(pool)))
+
+    srv = upr.Server(max_jobs=args.serve_slots)
+    ex = cf.ThreadPoolExecutor(256)
+    results = []
+    lock = threading.Lock()
+
+    def request(kind, j, t_arrive, record):
+        w = pools[kind][j]
+        t = srv.submit(w)
+        part, cut, st = srv.wait(t, timeout_ms=600000)
+        t_done = time.perf_counter()
+        if record:
+            with lock:
+                results.append((kind, j, t_arrive, t_done, cut, st.batch_graphs))
+
+    # warm-up and closed-loop capacity: a burst of the mix submitted at once
+    burst = [draw() for _ in range(args.serve_burst)]
+    list(ex.map(lambda kj: request(kj[0], kj[1], 0.0, False), burst[:32]))
+    t0 = time.perf_counter()
+    list(ex.map(lambda kj: request(kj[0], kj[1], 0.0, False), burst))
+    capacity = len(burst) / (time.perf_counter() - t0)
+    lam = 0.7 * capacity
+    # open loop: Poisson arrivals for serve_seconds
+    futs = []
+    start = time.perf_counter()
+    t_next = start
+    while t_next - start < args.serve_seconds:
+        now = time.perf_counter()
+        if t_next > now:
+            time.sleep(t_next - now)
+        kind, j = draw()
+        futs.append(ex.submit(request, kind, j, t_next, True))
+        t_next += rng.exponential(1.0 / lam)
+    for f in futs:
+        f.result()
+    end = max(r[3] for r in results)
+    ex.shutdown()
+    srv.close()
+    lat = np.array([(r[3] - r[2]) * 1e3 for r in results])
+    # every request of one input must give one cut; Chung-Lu inputs also the batched leg's
+    cuts = {}
+    same = True
+    for kind, j, _, _, cut, _ in results:
+        same &= cuts.setdefault((kind, j), cut) == cut
+        if kind == "small" and batched_cuts is not None:
+            same &= int(batched_cuts[j]) == cut
+    by_kind = {k: int(sum(r[0] == k for r in results)) for k in kinds}
+    return {
+        "workload": "Poisson arrivals; 50% Chung-Lu batch graphs (their own k, 4 rounds), 40% R-MAT scale 18, "
+                    "10% R-MAT scale 21 (edge factor 16, k from {8, 64}, 8 rounds), eps 0.03; inputs drawn from "
+                    f"pools of {len(pools['small'])} / {len(pools['s18'])} / {len(pools['s21'])} graphs",
+        "slots": args.serve_slots, "seconds": args.serve_seconds, "requests": len(results), "by_kind": by_kind,
+        "capacity_closed_loop_per_s": capacity, "arrival_rate_per_s": lam,
+        "graphs_per_s": len(results) / (end - start),
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()), "max": float(lat.max())},
+        "batched_requests": int(sum(r[5] > 1 for r in results)),
+        "identical_results": bool(same),
     }
 
 
 def run_gpu(args):
     import torch
     ws, rank, local = _dist()
-    graphs = None
+    graphs = pools = None
     if args.batch_graphs > 0 and not args.profile:
         # generated before CUDA starts (a spawned pool); rank r owns its own graphs
         graphs = synth.batch_graphs(args.batch_graphs, start=rank * args.batch_graphs)
+        if args.serve_seconds > 0:
+            pools = served_inputs(graphs[:512])
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -397,6 +494,9 @@ def run_gpu(args):
            "ms_per_step": t_e2e * 1e3, "steps": e2e_steps}
 
     batched = batched_leg(args, upr, rank, ws, local, graphs) if graphs else None
+    served = served_leg(args, upr, pools, batched.get("_cuts") if batched else None) if pools else None
+    if batched is not None:
+        batched.pop("_cuts", None)
     if batched is not None and ws > 1:
         import torch.distributed as dist
         t = torch.tensor([batched["ms_per_step"]], device="cuda")
@@ -417,7 +517,7 @@ def run_gpu(args):
                 "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
                            "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
                            "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds},
-                "batched": batched}
+                "batched": batched, "served": served}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -436,6 +536,11 @@ def main():
                     help="graphs of the Chung-Lu batch per GPU (0: skip the batched leg)")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="graphs of the batch timed in the one-graph-per-call form")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the Poisson arrival window of the served leg (0: skip it)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-burst", type=int, default=400,
+                    help="requests of the closed-loop burst that measures capacity")
     ap.add_argument("--shrink", type=int, default=0,
                     help="profiling only: the same workload family with 2^-shrink of the nodes")
     ap.add_argument("--profile", action="store_true",

@@ -104,6 +104,9 @@ typedef struct {
     double  ms_rebalance;        /* device time of step (d)                             */
     double  ms_sequence;         /* device time of step (c): interleave to apply        */
     double  ms_host;             /* wall-clock time of the call on the host             */
+    int32_t batch_graphs;        /* graphs refined together in this call (batches and
+                                    batched server jobs; 1 = one graph)                 */
+    int32_t pad0;
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */
@@ -208,16 +211,25 @@ upr_status upr_batch_cut(upr_ctx *ctx, const int32_t *part, int64_t *cut, int64_
 upr_status upr_batch_info(const upr_ctx *ctx, int32_t *n_graphs, int64_t *node_offsets, int64_t *lmax);
 
 /* ------------------------------------------------------------------------
- * Serving: a host worker thread admits refinement jobs while device memory
- * and job slots allow, runs each job on its own stream and context so jobs of
- * different sizes overlap on the device, and keeps each job's state resident
- * until it is polled.  Results are identical to upr_create + upr_refine on the
- * same inputs. */
+ * Serving with continuous batching.  max_jobs slots, each with its own
+ * stream and context, take work from a FIFO queue while device memory
+ * allows (a job that does not fit yet may be overtaken by smaller ones).  A
+ * slot that takes a small job (n <= batch_max_nodes) also takes every other
+ * queued small job with the same k and rounds that fits the budget, up to
+ * batch_max_jobs graphs and batch_max_total_nodes nodes, and refines them as
+ * one batch (upr_batch_refine); jobs submitted while others run join the
+ * next batch a slot takes.  Slots run concurrently, so jobs of different
+ * sizes overlap on the device.  Each job's state stays on the device for all
+ * its rounds; its result stays in host memory until polled.  Every result is
+ * identical to upr_create + upr_refine on the same inputs. */
 typedef struct {
-    int32_t max_jobs;           /* jobs resident on the device at once (slots). 8          */
+    int32_t max_jobs;           /* slots: batches or jobs on the device at once. 8           */
     int32_t queue_capacity;     /* submitted-but-not-admitted jobs before UPR_ERR_BUSY. 4096 */
     int64_t memory_budget;      /* device bytes the server may hold; 0 = 80% of free memory */
     upr_params params;          /* per-job parameters (stream ignored: each slot owns one) */
+    int32_t batch_max_jobs;     /* graphs per batch; 1 = no batching. 4096                   */
+    int32_t batch_max_nodes;    /* largest graph (nodes) that joins batches. 131072          */
+    int64_t batch_max_total_nodes; /* nodes per batch. 2^25                                  */
 } upr_server_params;
 
 void upr_server_params_default(upr_server_params *p);

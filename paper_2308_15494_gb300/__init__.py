@@ -41,14 +41,16 @@ class Stats(ctypes.Structure):
                 ("n_candidates", I64), ("n_moves", I64), ("n_rebalance_moves", I64), ("n_sequence", I64),
                 ("n_applied", I64), ("subrounds", I32), ("kernel_launches", I32), ("ms_device", D),
                 ("ms_gain_table", D), ("gain_table_builds", I32), ("gain_table_bytes", I64),
-                ("ms_select", D), ("ms_rebalance", D), ("ms_sequence", D), ("ms_host", D)]
+                ("ms_select", D), ("ms_rebalance", D), ("ms_sequence", D), ("ms_host", D),
+                ("batch_graphs", I32), ("pad0", I32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ServerParams(ctypes.Structure):
-    _fields_ = [("max_jobs", I32), ("queue_capacity", I32), ("memory_budget", I64), ("params", Params)]
+    _fields_ = [("max_jobs", I32), ("queue_capacity", I32), ("memory_budget", I64), ("params", Params),
+                ("batch_max_jobs", I32), ("batch_max_nodes", I32), ("batch_max_total_nodes", I64)]
 
 
 class Trace(ctypes.Structure):
@@ -355,11 +357,16 @@ class Server:
     """upr_server_create / upr_submit / upr_poll / upr_wait / upr_server_destroy."""
 
     def __init__(self, max_jobs: int = 8, queue_capacity: int = 4096, memory_budget: int = 0,
-                 params: Optional[Params] = None):
+                 params: Optional[Params] = None, batch_max_jobs: Optional[int] = None,
+                 batch_max_nodes: Optional[int] = None):
         lib = load()
         sp = ServerParams()
         lib.upr_server_params_default(ctypes.byref(sp))
         sp.max_jobs, sp.queue_capacity, sp.memory_budget = max_jobs, queue_capacity, memory_budget
+        if batch_max_jobs is not None:
+            sp.batch_max_jobs = batch_max_jobs
+        if batch_max_nodes is not None:
+            sp.batch_max_nodes = batch_max_nodes
         if params is not None:
             sp.params = params
         h = ctypes.c_void_p()

@@ -657,6 +657,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     st.ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
     st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
                           4 * c->n * (int64_t)c->k;
+    st.batch_graphs = ng;
     if (stats) *stats = st;
     return UPR_OK;
 }
@@ -876,7 +877,11 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     if (c->wmax > 0x7fffffffLL) { c->n = -1; return UPR_ERR_INVALID; }
     c->gbits = std::max(1, bit_length((uint64_t)c->wmax));
     if (1 + c->gbits + 2 * c->cbits > 63) { c->n = -1; return UPR_ERR_INVALID; }
+    // the arena may hold another binding's data: clear every word a kernel
+    // reads before writing it
     UPR_CUDA(cudaMemsetAsync(c->tmp.ticket, 0, 64 * sizeof(unsigned int), s));
+    UPR_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(RebalCtl), s));
+    UPR_CUDA(cudaMemsetAsync(c->counts, 0, 64 * sizeof(int32_t), s));
     fill_i32(c->pos, n, INT32_MAX, s);
     fill_i32(c->m_pos, n, -1, s);
     fill_i32(c->r_to, n, -1, s);
@@ -905,6 +910,9 @@ upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
     if (g->n >= (1LL << 31) || g->m >= (1LL << 31)) return UPR_ERR_INVALID;
     return guarded(c, [&] { return bind_graphs(c, g, 1, k, &eps, prm); });
 }
+
+// Device bytes of the context's arena.
+size_t ctx_arena_bytes(const upr_ctx *c) { return c ? c->mem_bytes : 0; }
 
 upr_status ctx_rebind_batch(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
                             const upr_params *params) {
@@ -1057,10 +1065,11 @@ upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int3
 
 }  // extern "C"
 
-// Device bytes a context for (n, m, k) allocates (used by the server's admission).
-size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k) {
+// Device bytes a context for ng graphs with n nodes and m adjacency entries
+// in total and k blocks each allocates (used by the server's admission).
+size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k, int32_t ng) {
     upr_ctx c;
-    c.n = n; c.m = m; c.k = k; c.ng = 1;
+    c.n = n; c.m = m; c.k = k; c.ng = ng;
     c.n_chunks = m / 4096 + 1;
     c.n_tiles = n + 1;
     Arena A;

@@ -5,6 +5,8 @@
 // g / c(u) for g < 0, higher first, ties by node id) through an exact integer
 // key; each source keeps the minimal prefix that removes its excess; each
 // target admits the longest prefix that fits.  The host drives the loop.
+#include <cstddef>
+
 #include "kernels.h"
 
 namespace upr {
@@ -621,27 +623,45 @@ inline unsigned ctl_grid(int64_t items) {
     return (unsigned)std::min<int64_t>(ceil_div(items > 0 ? items : 1, 256), (int64_t)sm_count_reb() * 2);
 }
 
+// The batch controllers count finished CTAs in ctl->ticket and collect a flag
+// in ctl->flag; both are cleared before every such launch, so nothing
+// depends on what the control block held before.
+inline void clear_ticket(RebalCtl *ctl, cudaStream_t s) {
+    static_assert(offsetof(RebalCtl, ticket) == offsetof(RebalCtl, flag) + sizeof(int32_t), "flag, ticket adjacent");
+    UPR_CUDA(cudaMemsetAsync(&ctl->flag, 0, sizeof(int32_t) + sizeof(uint32_t), s));
+}
+
 void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl *ctl, cudaStream_t s) {
-    if (g.ng == 1) k_reb_init<<<1, 256, 0, s>>>(C, g.Lb, g.K(), excl, ctl);
-    else k_reb_init_batch<<<ctl_grid(g.K()), 256, 0, s>>>(C, g.Lb, g.K(), excl, ctl);
+    if (g.ng == 1) {
+        k_reb_init<<<1, 256, 0, s>>>(C, g.Lb, g.K(), excl, ctl);
+    } else {
+        clear_ticket(ctl, s);
+        k_reb_init_batch<<<ctl_grid(g.K()), 256, 0, s>>>(C, g.Lb, g.K(), excl, ctl);
+    }
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
                      const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, int32_t *light,
                      cudaStream_t s) {
-    if (g.ng == 1)
+    if (g.ng == 1) {
         k_reb_begin<<<1, 256, 0, s>>>(C, g.Lb, g.k, excl, over, reject, d_n1, h, max_subrounds, ctl);
-    else
+    } else {
+        clear_ticket(ctl, s);
         k_reb_begin_batch<<<ctl_grid((int64_t)g.ng * 32), 256, 0, s>>>(C, g.Lb, g.k, g.ng, excl, over, reject, d_n1,
                                                                        h, max_subrounds, ctl, light);
+    }
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_end(const GraphDev &g, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl,
                    cudaStream_t s) {
-    if (g.ng == 1) k_reb_end<<<1, 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
-    else k_reb_end_batch<<<ctl_grid(g.K()), 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
+    if (g.ng == 1) {
+        k_reb_end<<<1, 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
+    } else {
+        clear_ticket(ctl, s);
+        k_reb_end_batch<<<ctl_grid(g.K()), 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
+    }
     UPR_LAUNCH_CHECK();
 }
 

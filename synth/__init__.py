@@ -242,6 +242,16 @@ def batch_graph(i: int, seed: int = GRAPH_SEED + 3) -> Workload:
                     {"generator": "chung-lu", "avg_deg": d, "gamma": g})
 
 
+def served_rmat(scale: int, k: int, i: int) -> Workload:
+    """R-MAT graph i of the served mix: scale 18 or 21, edge factor 16,
+    symmetrised+dedup, unit weights, k from {8, 64}, 8 rounds."""
+    xadj, adj = rmat(scale, 16, 0.57, 0.19, 0.19, GRAPH_SEED + 5 + 7919 * i + 104729 * scale)
+    n = 1 << scale
+    part = part_random_balanced(n, k, PART_SEED + 5 + 7919 * i)
+    return Workload(f"served_rmat_s{scale}_k{k}_{i}", n, xadj, adj, None, None, k, 0.03, part, 8,
+                    {"generator": "r-mat", "scale": scale, "edge_factor": 16})
+
+
 def _batch_graph_cached(i: int) -> None:
     cached(batch_graph, i)
 
