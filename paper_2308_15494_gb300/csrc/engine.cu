@@ -90,7 +90,7 @@ struct upr_ctx {
     int64_t *noff_d;                    // batches: [ng + 1] first node of each graph
     // state
     int32_t *part0, *part; int64_t *C0, *C, *cut; int32_t *W;
-    int64_t *BW, *PW, *F;
+    int64_t *BW, *PW, *F; int8_t *first_slot;
     // node-indexed
     int32_t *cand_tgt, *cand_gain, *flags, *flags2, *excl_i, *m_pos, *r_to, *r_at, *pos, *dest, *prop_tgt, *prop_gain;
     int64_t *cand_s0;
@@ -157,6 +157,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->BW = A.take<int64_t>(k * kSlots);
     c->PW = A.take<int64_t>(k * kSlots);
     c->F = A.take<int64_t>(kSlots);
+    c->first_slot = A.take<int8_t>(k);
     for (int32_t **p : {&c->cand_tgt, &c->cand_gain, &c->flags, &c->m_pos, &c->r_to, &c->pos, &c->dest, &c->prop_tgt,
                         &c->prop_gain, &c->idxA, &c->idxB, &c->idxC, &c->M_node, &c->M_from, &c->M_to, &c->R_node,
                         &c->R_from, &c->R_to, &c->R_sub, &c->I_node, &c->I_from, &c->I_to, &c->emit, &c->qbefore,
@@ -292,11 +293,11 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     UPR_CUDA(cudaEventRecord(c->ev[4], s));
     if (!rebalance_only) {
         // ---- (b1) availability, slots, bucket weights; F_r
-        buckets(G, c->part0, c->W, c->prm.t_num, c->prm.t_den, c->BW, c->PW, tr ? tr->avail_d : nullptr,
-                tr ? tr->slot_d : nullptr, s);
+        buckets(G, c->part0, c->W, c->prm.t_num, c->prm.t_den, c->BW, c->PW, c->first_slot,
+                tr ? tr->avail_d : nullptr, tr ? tr->slot_d : nullptr, s);
         penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
         UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
-        Penalty pen{c->PW, c->F, c->C0, c->Lb};
+        Penalty pen{c->PW, c->F, c->C0, c->Lb, c->first_slot};
         // ---- (b2) best move per boundary node
         select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, s);
         select_flags(c->flags, c->idxA, cnt + CNT_CAND, cN, c->tmp, s);

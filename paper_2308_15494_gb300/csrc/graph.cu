@@ -182,12 +182,18 @@ __global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__
 
 // Dense gain table, tiled: one CTA per tile of consecutive nodes whose
 // adjacency (without hubs) is one contiguous range of entries.  The CTA
-// streams that range with 16-byte loads (16 entries in flight per thread),
-// gathers the neighbours' blocks, finds each entry's owner (binary search in
-// the tile's xadj slice for the first of four consecutive entries, then a
-// forward walk), accumulates all rows of the tile in shared memory and writes
-// them as one contiguous block with streaming stores.  Hub rows stay zero.
-constexpr int kTableUnroll = 4;
+// streams that range with 16-byte loads (4 * UNROLL entries in flight per
+// thread), gathers the neighbours' blocks, finds each entry's owner (binary
+// search in the tile's xadj slice for the first of four consecutive entries,
+// then a forward walk), accumulates all rows of the tile in shared memory and
+// writes them as one contiguous block with streaming stores.  WEIGHTED: edge
+// weights are read (else unit); LOCAL: 0 = one graph (block ids are
+// columns), 1 = a batch with k a power of two (mask), 2 = a batch with other
+// k (remainder).  Hub rows stay zero.
+template <int LOCAL>
+__device__ __forceinline__ int tile_col(int32_t p, int32_t k, int32_t kmask) {
+    return LOCAL == 0 ? p : LOCAL == 1 ? (p & kmask) : p % k;
+}
 
 __device__ __forceinline__ int tile_owner(const int64_t *s_x, int nn, int64_t e) {
     int lo = 0, hi = nn - 1;            // last i with s_x[i] <= e
@@ -198,11 +204,14 @@ __device__ __forceinline__ int tile_owner(const int64_t *s_x, int nn, int64_t e)
     return lo;
 }
 
+template <bool WEIGHTED, int LOCAL, int UNROLL>
 __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict__ tiles,
-                                                     const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                                                     const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
-                                                     int32_t k, int32_t kmask, int32_t *__restrict__ W,
-                                                     const int64_t *__restrict__ deg_sum, int64_t m) {
+                                                        const int64_t *__restrict__ xadj,
+                                                        const int32_t *__restrict__ adj,
+                                                        const int32_t *__restrict__ adjw,
+                                                        const int32_t *__restrict__ part, int32_t k, int32_t kmask,
+                                                        int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
+                                                        int64_t m) {
     if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
     extern __shared__ int4 s_raw[];
     const TableTile t = tiles[blockIdx.x];
@@ -222,35 +231,36 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         const bool in_tail = threadIdx.x >= 4 && qb >= qa && e < t.e1;
         if (in_head || in_tail) {
             const int o = tile_owner(s_x, nn, e);
-            atomicAdd(&rows[o * k + blk_local(part[adj[e]], k, kmask)], adjw ? adjw[e] : 1);
+            atomicAdd(&rows[o * k + tile_col<LOCAL>(part[adj[e]], k, kmask)], WEIGHTED ? adjw[e] : 1);
         }
     }
     const int4 *adj4 = reinterpret_cast<const int4 *>(adj);
     const int4 *adjw4 = reinterpret_cast<const int4 *>(adjw);
-    for (int64_t q0 = qa + threadIdx.x; q0 < qb; q0 += (int64_t)blockDim.x * kTableUnroll) {
-        int4 u[kTableUnroll], w[kTableUnroll];
+    for (int64_t q0 = qa + threadIdx.x; q0 < qb; q0 += (int64_t)blockDim.x * UNROLL) {
+        int4 u[UNROLL], w[UNROLL];
 #pragma unroll
-        for (int r = 0; r < kTableUnroll; r++) {
+        for (int r = 0; r < UNROLL; r++) {
             const int64_t q = q0 + (int64_t)r * blockDim.x;
             u[r] = q < qb ? __ldcs(adj4 + q) : make_int4(0, 0, 0, 0);
-            w[r] = (q < qb && adjw) ? __ldcs(adjw4 + q) : make_int4(1, 1, 1, 1);
+            if (WEIGHTED) w[r] = q < qb ? __ldcs(adjw4 + q) : make_int4(0, 0, 0, 0);
         }
-        int pb[kTableUnroll][4];
+        int pb[UNROLL][4];
 #pragma unroll
-        for (int r = 0; r < kTableUnroll; r++) {
+        for (int r = 0; r < UNROLL; r++) {
             const bool ok = q0 + (int64_t)r * blockDim.x < qb;
-            pb[r][0] = ok ? blk_local(part[u[r].x], k, kmask) : 0;
-            pb[r][1] = ok ? blk_local(part[u[r].y], k, kmask) : 0;
-            pb[r][2] = ok ? blk_local(part[u[r].z], k, kmask) : 0;
-            pb[r][3] = ok ? blk_local(part[u[r].w], k, kmask) : 0;
+            pb[r][0] = ok ? tile_col<LOCAL>(part[u[r].x], k, kmask) : 0;
+            pb[r][1] = ok ? tile_col<LOCAL>(part[u[r].y], k, kmask) : 0;
+            pb[r][2] = ok ? tile_col<LOCAL>(part[u[r].z], k, kmask) : 0;
+            pb[r][3] = ok ? tile_col<LOCAL>(part[u[r].w], k, kmask) : 0;
         }
 #pragma unroll
-        for (int r = 0; r < kTableUnroll; r++) {
+        for (int r = 0; r < UNROLL; r++) {
             const int64_t q = q0 + (int64_t)r * blockDim.x;
             if (q >= qb) continue;
             const int64_t e = q << 2;
             int o = tile_owner(s_x, nn, e);
-            const int ww[4] = {w[r].x, w[r].y, w[r].z, w[r].w};
+            int ww[4] = {1, 1, 1, 1};
+            if (WEIGHTED) { ww[0] = w[r].x; ww[1] = w[r].y; ww[2] = w[r].z; ww[3] = w[r].w; }
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 while (s_x[o + 1] <= e + j) o++;
@@ -432,13 +442,28 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
     if (g.n == 0) return;
     if (tiles && n_tiles > 0) {
         const size_t shm = table_tile_smem(g.k, tile_nodes);
-        static thread_local size_t attr_set = 0;
-        if (shm > 48 * 1024 && attr_set < shm) {
-            UPR_CUDA(cudaFuncSetAttribute(k_table_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-            attr_set = shm;
+        const int local = g.ng == 1 ? 0 : g.kmask ? 1 : 2;
+        auto launch = [&](auto kern) {
+            static thread_local size_t attr_set[8] = {};
+            const int slot = (g.adjw ? 4 : 0) + local;
+            if (shm > 48 * 1024 && attr_set[slot] < shm) {
+                UPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+                attr_set[slot] = shm;
+            }
+            kern<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum,
+                                                     g.m);
+        };
+        // 16 entries in flight per thread (8 with weights); the default
+        // shared/L1 split: a smaller L1 slows the gathers of part[] down
+        if (g.adjw) {
+            if (local == 0) launch(k_table_tiles<true, 0, 2>);
+            else if (local == 1) launch(k_table_tiles<true, 1, 2>);
+            else launch(k_table_tiles<true, 2, 2>);
+        } else {
+            if (local == 0) launch(k_table_tiles<false, 0, 4>);
+            else if (local == 1) launch(k_table_tiles<false, 1, 4>);
+            else launch(k_table_tiles<false, 2, 4>);
         }
-        k_table_tiles<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum,
-                                                          g.m);
         UPR_LAUNCH_CHECK();
     } else {
         const int k = g.k;

@@ -128,9 +128,10 @@ struct Penalty {
     const int64_t *F;     // [73] floor(tau_r * (3/2)^l * 2^Q)
     const int64_t *C;     // [K] round-start block weights
     const int64_t *Lb;    // [K] L_max of each block's graph
+    const int8_t *first;  // [K] smallest slot l with PW[b][l] >= 1, -1 if none (the excess-1 case)
 };
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
-             int64_t *PW, int8_t *avail_out, int32_t *slot_out, cudaStream_t s);
+             int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s);
 void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Penalty pen, int32_t *cand_tgt,
                   int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s);
 void cand_keys(const int32_t *cand_idx, const int32_t *d_count, const int32_t *cand_tgt, const int64_t *cand_s0,

@@ -50,14 +50,23 @@ __device__ __forceinline__ int slot_of(uint64_t omega, uint64_t c) {
 
 // Penalty of moving weight cu into block b that would then exceed L_max by x;
 // -1 = forbidden (no slot's cumulative weight covers x).
+// An excess of exactly 1 (every overfilling move of a unit-weight node) takes
+// the block's first non-empty slot without a search.
 __device__ __forceinline__ int64_t penalty(const Penalty &p, int32_t b, int64_t x, int64_t cu) {
     if (x <= 0) return 0;
-    const int64_t *row = p.PW + (int64_t)b * kSlots;
-    if (row[kSlots - 1] < x) return -1;
-    int lo = 0, hi = kSlots - 1;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (row[mid] >= x) hi = mid; else lo = mid + 1;
+    int lo;
+    if (x == 1) {
+        lo = p.first[b];
+        if (lo < 0) return -1;
+    } else {
+        const int64_t *row = p.PW + (int64_t)b * kSlots;
+        if (row[kSlots - 1] < x) return -1;
+        lo = 0;
+        int hi = kSlots - 1;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (row[mid] >= x) hi = mid; else lo = mid + 1;
+        }
     }
     return (int64_t)(((u128)(uint64_t)cu * (uint64_t)p.F[lo]) >> kQ);
 }
@@ -92,11 +101,18 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
     }
 }
 
-__global__ void k_bucket_prefix(const int64_t *__restrict__ BW, int64_t *__restrict__ PW, int32_t K) {
+__global__ void k_bucket_prefix(const int64_t *__restrict__ BW, int64_t *__restrict__ PW, int8_t *__restrict__ first,
+                                int32_t K) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= K) return;
     int64_t acc = 0;
-    for (int l = 0; l < kSlots; l++) { acc += BW[b * kSlots + l]; PW[b * kSlots + l] = acc; }
+    int f = -1;
+    for (int l = 0; l < kSlots; l++) {
+        acc += BW[b * kSlots + l];
+        PW[b * kSlots + l] = acc;
+        if (f < 0 && acc >= 1) f = l;
+    }
+    first[b] = (int8_t)f;
 }
 
 // G lanes per node: best target by (gain - penalty) among adjacent blocks,
@@ -176,10 +192,12 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
     int64_t *s_F = s_mem;
     int64_t *s_PW = s_mem + kSlots;
     int32_t *s_slack = reinterpret_cast<int32_t *>(s_mem + kSlots + (smem_pw ? (size_t)k * kSlots : 0));
+    int8_t *s_first = reinterpret_cast<int8_t *>(s_slack + k);
     if (!BATCH)
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             const int64_t sl = pen.Lb[i] - pen.C[i];
             s_slack[i] = (int32_t)(sl > 0x7fffffffLL ? 0x7fffffffLL : sl);
+            s_first[i] = pen.first[i];
         }
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) s_F[i] = pen.F[i];
     if (!BATCH && smem_pw)
@@ -240,12 +258,19 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
                     }
                     if (c > slack) {
                         const int64_t x = (int64_t)c - slack;
-                        const int64_t *row = PW + (int64_t)(b0 + b) * kSlots;
-                        if (row[kSlots - 1] < x) continue;          // no slot covers the excess: forbidden
-                        int lo = 0, hi = kSlots - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (row[mid] >= x) hi = mid; else lo = mid + 1;
+                        int lo;
+                        if (x == 1) {                               // first non-empty slot
+                            lo = BATCH ? pen.first[b0 + b] : s_first[b];
+                            if (lo < 0) continue;                   // forbidden
+                        } else {
+                            const int64_t *row = PW + (int64_t)(b0 + b) * kSlots;
+                            if (row[kSlots - 1] < x) continue;      // no slot covers the excess: forbidden
+                            lo = 0;
+                            int hi = kSlots - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (row[mid] >= x) hi = mid; else lo = mid + 1;
+                            }
                         }
                         const int64_t p = (int64_t)(((u128)(uint64_t)c * (uint64_t)s_F[lo]) >> kQ);
                         if (p >= gain) continue;
@@ -367,7 +392,7 @@ __global__ void k_apply_moves(const int32_t *__restrict__ cand_idx, const int32_
 }  // namespace
 
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
-             int64_t *PW, int8_t *avail_out, int32_t *slot_out, cudaStream_t s) {
+             int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s) {
     ensure_pow3();
     const int32_t K = g.K();
     UPR_CUDA(cudaMemsetAsync(BW, 0, sizeof(int64_t) * K * kSlots, s));
@@ -383,7 +408,7 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
                                                                       use_shared, avail_out, slot_out);
         UPR_LAUNCH_CHECK();
     }
-    k_bucket_prefix<<<(unsigned)ceil_div(K, 128), 128, 0, s>>>(BW, PW, K);
+    k_bucket_prefix<<<(unsigned)ceil_div(K, 128), 128, 0, s>>>(BW, PW, first, K);
     UPR_LAUNCH_CHECK();
 }
 
@@ -404,7 +429,7 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
         const bool exact = k == 4 * G * CH;
         const int smem_pw = !batch && (size_t)k * kSlots * 8 <= 40 * 1024;
         const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) +
-                           (batch ? 0 : sizeof(int32_t) * k);
+                           (batch ? 0 : (sizeof(int32_t) + 1) * k);
         const int64_t groups = 256 / G;
         const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
 #define UPR_SELV(GG, CC, EX, BA) k_select_vec<GG, CC, EX, BA><<<(unsigned)blocks, 256, shm, s>>>( \
