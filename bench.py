@@ -292,6 +292,44 @@ def batched_leg(args, upr, rank, ws, local, graphs):
     }
 
 
+def other_configs_leg(args, upr):
+    """The two other single-graph workloads, timed like the main one (graph and
+    partition resident, CUDA events around upr_refine): the Chung-Lu graph
+    with 16,384 nodes (k = 8, 4 rounds) and the weighted random geometric
+    graph with 2^22 nodes (k = 256, 8 rounds)."""
+    import torch
+    peak, _ = _peaks()
+    out = {}
+    for name, builder, steps in (("chung_lu_n16384_k8", "plain_tiny", 20), ("rgg_2^22_weighted_k256", "plain_weighted", 3)):
+        w = synth.cached(getattr(synth, builder))
+        ctx = upr.create_from_workload(w, device=True)
+        init = torch.from_numpy(w.part.copy()).cuda()
+        part = torch.empty_like(init)
+        for _ in range(2):
+            part.copy_(init)
+            upr.upr_refine(ctx, part, w.rounds)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sts = []
+        e0.record()
+        for _ in range(steps):
+            part.copy_(init)
+            sts.append(upr.upr_refine(ctx, part, w.rounds))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = sts[-1]
+        t_build = sum(x.ms_gain_table for x in sts) / max(1, sum(x.gain_table_builds for x in sts))
+        out[name] = {"n": w.n, "m": w.m, "k": w.k, "rounds": w.rounds, "weighted": w.adjw is not None,
+                     "ms_per_refine": ms, "edges_per_s": w.rounds * (w.m // 2) / (ms / 1e3),
+                     "cut_in": st.cut_in, "cut_out": st.cut_out,
+                     "gain_table_ms": t_build, "gain_table_gbs": st.gain_table_bytes / (t_build / 1e3) / 1e9,
+                     "gain_table_frac": st.gain_table_bytes / (t_build / 1e3) / 1e9 / peak}
+        del ctx
+    return out
+
+
 def _served_pool_cached(spec):
     synth.cached(synth.served_rmat, *spec)
 
@@ -458,7 +496,7 @@ def run_gpu(args):
     bytes_build = stats[0].gain_table_bytes
     peak, peak_kind = _peaks()
     achieved = bytes_build / t_build / 1e9
-    roofline = {"bound": "hbm", "kernel": "gain table build (k_table_dense + hub chunks)",
+    roofline = {"bound": "hbm", "kernel": "gain table build (k_table_tiles + k_table_hub_chunks)",
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak, "bytes_per_launch": bytes_build, "ms_per_launch": t_build * 1e3,
                 "traffic": _traffic("paper_2308_15494_gb300/csrc/graph.cu", "gain_table_rmat_s22_k64.md")}
@@ -493,6 +531,7 @@ def run_gpu(args):
     e2e = {"value": ws * w.rounds * E / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": t_e2e * 1e3, "steps": e2e_steps}
 
+    others = other_configs_leg(args, upr) if rank == 0 and not args.profile and args.other_configs else None
     batched = batched_leg(args, upr, rank, ws, local, graphs) if graphs else None
     served = served_leg(args, upr, pools, batched.get("_cuts") if batched else None) if pools else None
     if batched is not None:
@@ -517,7 +556,7 @@ def run_gpu(args):
                 "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
                            "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
                            "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds},
-                "batched": batched, "served": served}
+                "other_configs": others, "batched": batched, "served": served}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -536,6 +575,8 @@ def main():
                     help="graphs of the Chung-Lu batch per GPU (0: skip the batched leg)")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="graphs of the batch timed in the one-graph-per-call form")
+    ap.add_argument("--no-other-configs", dest="other_configs", action="store_false",
+                    help="skip timing the 16k Chung-Lu and weighted RGG workloads")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the Poisson arrival window of the served leg (0: skip it)")
     ap.add_argument("--serve-slots", type=int, default=8)
