@@ -71,6 +71,7 @@ struct upr_ctx {
     int64_t n = 0, m = 0;
     int32_t k = 0;
     int32_t ng = 1;                   // graphs bound (a batch when > 1)
+    bool table_valid = false;         // W holds the table of part0 (carried from the previous round)
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -196,7 +197,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->ctl = A.take<RebalCtl>(1);
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
-    c->scal = A.take<int64_t>(4);
+    c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves
     c->tmp.mem = A.take<char>(std::max(radix_temp_bytes((int64_t)n2), scan_temp_bytes((int64_t)n2 + 1)) + 1024);
     c->tmp.ticket = A.take<unsigned int>(64);
 }
@@ -285,10 +286,14 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     UPR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * CNT_SLOTS, s));
     UPR_CUDA(cudaMemcpyAsync(c->part, c->part0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
-    // ---- (a) gain table of the round-start partition
+    // ---- (a) gain table of the round-start partition (kept from the previous
+    // round of this call when it is valid)
+    const bool build = !c->table_valid || tr;
+    c->table_valid = false;
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
-    gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
-               c->tile_nodes, nullptr, s);
+    if (build)
+        gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, nullptr, s);
     UPR_CUDA(cudaEventRecord(c->ev[1], s));
     UPR_CUDA(cudaEventRecord(c->ev[4], s));
     if (!rebalance_only) {
@@ -441,12 +446,19 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         seq_best_seg(G, Iv, dI, n, c->seg_beg, c->Gsum, c->diff, c->diff_excl, c->over0_g, c->best_g, c->best_j, c->cut,
                      c->infeas_g, c->tot, s);
     }
+    if (!batch) seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
+    else seq_apply_prefix_seg(G, Iv, If, It, dI, n, c->seg_beg, c->best_j, c->part0, c->C0, s);
+    // the table goes from W(P o I) to W(P o I^{j*}) for the next round
+    {
+        const Rollback rb{Iv, If, It, dI, c->best, batch ? G.gid : nullptr, c->seg_beg, c->best_j};
+        table_rollback(G, rb, n, c->pos, c->W, c->hub_chunks, c->n_chunks, c->scal + 2, s);
+        gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, c->scal + 2, s);
+    }
     // reset node-indexed markers for the next round
     reset_nodes(c->I_node, dI, n, c->pos, INT32_MAX, s);
     reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
     reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
-    if (!batch) seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
-    else seq_apply_prefix_seg(G, Iv, If, It, dI, n, c->seg_beg, c->best_j, c->part0, c->C0, s);
     UPR_CUDA(cudaEventRecord(c->ev[7], s));
     UPR_CUDA(cudaMemcpyAsync(c->hcnt, cnt, sizeof(int32_t) * CNT_SLOTS, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
@@ -459,7 +471,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         UPR_CUDA(cudaEventElapsedTime(&a, c->ev[4], c->ev[5]));
         UPR_CUDA(cudaEventElapsedTime(&b, c->ev[5], c->ev[6]));
         UPR_CUDA(cudaEventElapsedTime(&d, c->ev[6], c->ev[7]));
-        ri.ms_table += t; ri.tables++;
+        if (build) { ri.ms_table += t; ri.tables++; }
         ri.ms_select = a; ri.ms_rebalance = b; ri.ms_sequence = d;
     }
     const int32_t *hc = c->hcnt;
@@ -472,6 +484,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     // one graph: an infeasible round applies nothing and is an error; a
     // batch records it per graph (infeas_g) and the round goes on
     const bool infeasible = !batch && hc[CNT_INFEAS] != 0;
+    c->table_valid = !infeasible;
     ri.best_len = infeasible ? 0 : batch ? c->hbest[0] : c->hbest[1];
     ri.best_gain = infeasible ? 0 : batch ? c->hbest[1] : c->hbest[0];
     if (log_enabled())
@@ -558,6 +571,7 @@ __global__ void k_part_to_local(const int32_t *part, const int32_t *part_in, con
 }
 
 upr_status load_part(upr_ctx *c, const int32_t *part) {
+    c->table_valid = false;
     copy_in(c->part0, part, sizeof(int32_t) * c->n, c->s);
     UPR_CUDA(cudaMemsetAsync(c->counts + 7, 0, sizeof(int32_t), c->s));
     if (c->n > 0) {
@@ -728,6 +742,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     }
     if (n >= (1LL << 31) || m >= (1LL << 31)) return UPR_ERR_INVALID;
     c->n = -1;
+    c->table_valid = false;
     UPR_CUDA(cudaGetDevice(&c->device));
     c->prm = prm;
     c->s = (cudaStream_t)prm.stream;

@@ -254,6 +254,20 @@ void seq_best(const int64_t *Gsum, const int32_t *diff, const int32_t *diff_excl
               const int32_t *d_over0, long long *parts, long long *out, int32_t *infeasible, cudaStream_t s);
 void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                       int64_t max, const long long *best, int32_t *part0, int64_t *C0, int64_t *cut, cudaStream_t s);
+// The moves of I undone after the best prefix: positions i >= j* (one graph,
+// best[1] = j*, -1 = none kept) or i - seg_beg[g] >= best_j[g] (a batch, gid set).
+struct Rollback {
+    const int32_t *I_node, *I_from, *I_to;
+    const int32_t *d_nI;
+    const long long *best;
+    const int32_t *gid, *seg_beg;
+    const long long *best_j;
+};
+// W(P o I) -> W(P o I^{j*}): delta updates of the undone moves (pos = positions
+// in I), or nothing when 4 * (their degree sum, left in *deg_sum) >= m, in which
+// case the caller rebuilds with gain_table(..., deg_sum).
+void table_rollback(const GraphDev &g, const Rollback &rb, int64_t max, const int32_t *pos, int32_t *W,
+                    const HubChunk *hub_chunks, int64_t n_chunks, int64_t *deg_sum, cudaStream_t s);
 // Batches: I (length *d_nI) stably sorted by graph into O_*; pos/dest of the
 // moved nodes set from the sorted order; seg_beg/seg_end[g] bound graph g's
 // moves (both 0 for a graph without moves).

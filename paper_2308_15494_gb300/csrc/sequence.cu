@@ -596,6 +596,74 @@ __global__ void k_apply_prefix_seg(const int32_t *__restrict__ I_node, const int
     bd.flush(C0);
 }
 
+// ---- carrying the gain table into the next round.  After rebalancing the
+// table is W(P o M o R) = W(P o I); the next round starts from P o I^{j*},
+// so the moves of I after the best prefix are undone in the table (delta
+// updates), or the table is rebuilt when they touch many entries.
+__device__ __forceinline__ bool rolled_back(const Rollback &rb, int64_t i) {
+    if (!rb.gid) {
+        const long long j = rb.best[1];
+        return i >= (j < 0 ? 0 : j);
+    }
+    const int32_t g = rb.gid[rb.I_node[i]];
+    return i - rb.seg_beg[g] >= rb.best_j[g];
+}
+
+__global__ void k_rollback_degsum(Rollback rb, const int64_t *__restrict__ xadj, unsigned long long *__restrict__ out) {
+    const int64_t nI = *rb.d_nI;
+    long long acc = 0;
+    UPR_FOR(i, nI) {
+        if (rolled_back(rb, i)) {
+            const int32_t v = rb.I_node[i];
+            acc += xadj[v + 1] - xadj[v];
+        }
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, (unsigned long long)acc);
+}
+
+// warp per move of I; hubs are left to k_table_rollback_hubs
+__global__ void k_table_rollback(Rollback rb, const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                                 const int32_t *__restrict__ adjw, int32_t k, int32_t kmask, int32_t *__restrict__ W,
+                                 const int64_t *__restrict__ deg_sum, int64_t m) {
+    if (*deg_sum * 4 >= m) return;          // the rebuild handles this case
+    const int lane = threadIdx.x & 31;
+    const int64_t nI = *rb.d_nI;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nI;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        if (!rolled_back(rb, i)) continue;
+        const int32_t v = rb.I_node[i];
+        const int64_t e0 = xadj[v], e1 = xadj[v + 1];
+        if (e1 - e0 > kHubDegree) continue;
+        const int32_t a = blk_local(rb.I_to[i], k, kmask), b = blk_local(rb.I_from[i], k, kmask);
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t w = adjw ? adjw[e] : 1;
+            int32_t *row = W + (int64_t)adj[e] * k;
+            atomicSub(&row[a], w);
+            atomicAdd(&row[b], w);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(512) k_table_rollback_hubs(Rollback rb, const HubChunk *__restrict__ chunks,
+                                                             const int32_t *__restrict__ pos,
+                                                             const int32_t *__restrict__ adj,
+                                                             const int32_t *__restrict__ adjw, int32_t k,
+                                                             int32_t kmask, int32_t *__restrict__ W,
+                                                             const int64_t *__restrict__ deg_sum, int64_t m) {
+    if (*deg_sum * 4 >= m) return;
+    const HubChunk ch = chunks[blockIdx.x];
+    const int32_t i = pos[ch.v];
+    if (i == INT32_MAX || !rolled_back(rb, i)) return;
+    const int32_t a = blk_local(rb.I_to[i], k, kmask), b = blk_local(rb.I_from[i], k, kmask);
+    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
+        const int32_t w = adjw ? adjw[e] : 1;
+        int32_t *row = W + (int64_t)adj[e] * k;
+        atomicSub(&row[a], w);
+        atomicAdd(&row[b], w);
+    }
+}
+
 __global__ void k_reset_nodes(const int32_t *__restrict__ nodes, const int32_t *__restrict__ d_cnt,
                               int32_t *__restrict__ arr, int32_t val) {
     const int64_t cnt = *d_cnt;
@@ -767,6 +835,22 @@ void seq_apply_prefix(const GraphDev &g, const int32_t *I_node, const int32_t *I
     k_apply_prefix<<<(unsigned)blocks, 256, block_delta_smem(g.K()), s>>>(
         I_node, I_from, I_to, best, g.vwgt, part0, (unsigned long long *)C0, g.K(), (long long *)cut);
     UPR_LAUNCH_CHECK();
+}
+
+void table_rollback(const GraphDev &g, const Rollback &rb, int64_t max, const int32_t *pos, int32_t *W,
+                    const HubChunk *hub_chunks, int64_t n_chunks, int64_t *deg_sum, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(deg_sum, 0, sizeof(int64_t), s));
+    if (max <= 0) return;
+    k_rollback_degsum<<<grid_for(max), 256, 0, s>>>(rb, g.xadj, (unsigned long long *)deg_sum);
+    UPR_LAUNCH_CHECK();
+    const int64_t blocks = std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16);
+    k_table_rollback<<<(unsigned)blocks, 256, 0, s>>>(rb, g.xadj, g.adj, g.adjw, g.k, g.kmask, W, deg_sum, g.m);
+    UPR_LAUNCH_CHECK();
+    if (n_chunks > 0) {
+        k_table_rollback_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(rb, hub_chunks, pos, g.adj, g.adjw, g.k, g.kmask, W,
+                                                                 deg_sum, g.m);
+        UPR_LAUNCH_CHECK();
+    }
 }
 
 void seq_sort_by_graph(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
