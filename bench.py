@@ -136,6 +136,29 @@ def _dist():
     return ws, rank, local
 
 
+# ---- multi-rank host logic (one process per GPU; gloo on CPU in the tests)
+def rank_graph_range(rank: int, per_rank: int):
+    """Graphs of the batch owned by a rank: ids [rank * per_rank, (rank + 1) * per_rank)
+    (each rank refines its own graphs: weak scaling, no collective on the data path)."""
+    return rank * per_rank, per_rank
+
+
+def allreduce_max(x: float, ws: int, device: str = "cuda") -> float:
+    """Maximum of x over the ranks (x itself when running alone)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / seconds_max
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -430,7 +453,8 @@ def run_gpu(args):
     graphs = pools = None
     if args.batch_graphs > 0 and not args.profile:
         # generated before CUDA starts (a spawned pool); rank r owns its own graphs
-        graphs = synth.batch_graphs(args.batch_graphs, start=rank * args.batch_graphs)
+        start, count = rank_graph_range(rank, args.batch_graphs)
+        graphs = synth.batch_graphs(count, start=start)
         if args.serve_seconds > 0:
             pools = served_inputs(graphs[:512])
     if ws > 1:
@@ -481,13 +505,9 @@ def run_gpu(args):
             print(json.dumps({"profile": True, "ms_per_step": ms / args.steps,
                               "launches_per_step": stats[-1].kernel_launches}))
         return 0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = allreduce_max(ms, ws)
     ms_step = ms / args.steps
-    value = ws * w.rounds * E / (ms_step / 1e3)
+    value = job_value(w.rounds * E, ws, ms_step / 1e3)
 
     # roofline of the dominant kernel: the gain-table build (device time from
     # CUDA events on the context's stream around every build)
@@ -523,12 +543,8 @@ def run_gpu(args):
         e2e_step()
     barrier()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": ws * w.rounds * E / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    t_e2e = allreduce_max(t_e2e, ws)
+    e2e = {"value": job_value(w.rounds * E, ws, t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": t_e2e * 1e3, "steps": e2e_steps}
 
     others = other_configs_leg(args, upr) if rank == 0 and not args.profile and args.other_configs else None
@@ -537,11 +553,8 @@ def run_gpu(args):
     if batched is not None:
         batched.pop("_cuts", None)
     if batched is not None and ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([batched["ms_per_step"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        batched["ms_per_step"] = float(t.item())
-        batched["graphs_per_s"] = ws * batched["graphs"] / (batched["ms_per_step"] / 1e3)
+        batched["ms_per_step"] = allreduce_max(batched["ms_per_step"], ws)
+        batched["graphs_per_s"] = job_value(batched["graphs"], ws, batched["ms_per_step"] / 1e3)
     if rank == 0:
         cb = cpu_baseline(w) if ws == 1 and not args.no_cpu_baseline else None
         s0 = stats[-1]
