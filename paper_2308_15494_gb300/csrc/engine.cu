@@ -72,6 +72,7 @@ struct upr_ctx {
     int32_t k = 0;
     int32_t ng = 1;                   // graphs bound (a batch when > 1)
     bool table_valid = false;         // W holds the table of part0 (carried from the previous round)
+    uint32_t epoch = 0;               // call tag of the primitives' status words (Scratch::epoch)
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -198,8 +199,14 @@ void layout(upr_ctx *c, Arena &A) {
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
     c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves
-    c->tmp.mem = A.take<char>(std::max(radix_temp_bytes((int64_t)n2), scan_temp_bytes((int64_t)n2 + 1)) + 1024);
+    c->tmp.tiles_cap = ceil_div(std::max<int64_t>((int64_t)n2 + 2, (int64_t)k + 2), 2048);   // lists of nodes, events, blocks
+    c->tmp.mem_bytes = radix_temp_bytes(c->tmp.tiles_cap * 2048);
+    c->tmp.scan_bytes = scan_temp_bytes(c->tmp.tiles_cap * 2048);
+    c->tmp.mem = A.take<char>(c->tmp.mem_bytes);
+    c->tmp.scan = A.take<char>(c->tmp.scan_bytes);
     c->tmp.ticket = A.take<unsigned int>(64);
+    c->tmp.err = A.take<int32_t>(1);
+    c->tmp.epoch = &c->epoch;
 }
 
 enum MemKind { kHost = 0, kDevice = 1 };
@@ -464,7 +471,10 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
     if (!batch) UPR_CUDA(cudaMemcpyAsync(c->hbest, c->best, sizeof(long long) * 2, cudaMemcpyDeviceToHost, s));
     else UPR_CUDA(cudaMemcpyAsync(c->hbest, c->tot, sizeof(long long) * 3, cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaMemcpyAsync(c->hcnt + 40, c->tmp.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaStreamSynchronize(s));
+    // a bounded wait of a primitive gave up: the round's lists are not trustworthy
+    if (c->hcnt[40] != 0) { c->table_valid = false; throw CudaError{cudaErrorLaunchTimeout, "primitive wait"}; }
     {
         float a = 0, b = 0, d = 0, t = 0;
         UPR_CUDA(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
@@ -896,6 +906,10 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     // the arena may hold another binding's data: clear every word a kernel
     // reads before writing it
     UPR_CUDA(cudaMemsetAsync(c->tmp.ticket, 0, 64 * sizeof(unsigned int), s));
+    UPR_CUDA(cudaMemsetAsync(c->tmp.mem, 0, c->tmp.mem_bytes, s));
+    UPR_CUDA(cudaMemsetAsync(c->tmp.scan, 0, c->tmp.scan_bytes, s));
+    UPR_CUDA(cudaMemsetAsync(c->tmp.err, 0, sizeof(int32_t), s));
+    c->epoch = 0;
     UPR_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(RebalCtl), s));
     UPR_CUDA(cudaMemsetAsync(c->counts, 0, 64 * sizeof(int32_t), s));
     fill_i32(c->pos, n, INT32_MAX, s);

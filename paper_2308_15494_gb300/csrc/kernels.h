@@ -48,12 +48,19 @@ struct Count {
 };
 inline Count fixed(int64_t n) { return Count{nullptr, n}; }
 
-// Scratch memory of the primitives and the word their last-finishing CTA
-// takes a ticket from (zero between calls; calls on one scratch are
-// serialised by their stream).
+// Scratch memory of the primitives: status words and partial results, tile
+// and ticket counters (zero between calls: the last CTA of a call resets
+// them), the call counter whose value tags status words (host memory,
+// advanced at every call; calls on one scratch are serialised by their
+// stream) and an error word set when a bounded wait gives up.
 struct Scratch {
-    char *mem;
-    unsigned int *ticket;
+    char *mem;              // radix status and digit counts (radix_temp_bytes(tiles_cap * 2048))
+    char *scan;             // scan / compaction status (scan_temp_bytes(tiles_cap * 2048)); never overlaps mem
+    size_t mem_bytes, scan_bytes;
+    int64_t tiles_cap;      // tiles of the longest list; fixes the layout of both regions
+    unsigned int *ticket;   // [0] next tile, [1] finished CTAs, [2] radix count ticket
+    uint32_t *epoch;
+    int32_t *err;
 };
 
 // Grid-stride loop over a device-held count (all threads of the grid).

@@ -1,4 +1,4 @@
-// Device-wide primitives written for this library: tile scans (sum / max),
+// Device-wide primitives written for this library: scans (sum / max),
 // stable LSD radix sort of (64-bit key, 32-bit value) pairs and stable flag
 // compaction.  Every ordered list the refinement produces comes out of these,
 // never out of the order of atomic operations, so results are deterministic.
@@ -8,12 +8,19 @@
 // actual count, so a step can be enqueued without the host knowing how long
 // the previous step's output was.
 //
-// Tiles are 2048 items: 256 threads x 8 items, grid-stride over tiles.  A scan
-// is reduce-then-scan (per-tile totals, a one-CTA scan of the totals, a
-// per-tile scan with its offset).  A radix pass is histogram -> scan of the
-// digit-major histogram -> stable scatter; inside a tile, equal digits are
-// ranked in item order with __match_any_sync per warp and a per-digit prefix
-// over the 8 warps.  Lists of at most one tile are sorted in one CTA.
+// Tiles are 2048 items (256 threads x 8 items).  Scans and compaction are
+// single-pass with decoupled look-back: a CTA takes the next tile index from
+// an atomic counter, publishes its tile total, then walks back over the
+// preceding tiles' published totals until it meets an inclusive prefix, and
+// publishes its own.  A tile only waits for tiles that running CTAs took
+// earlier, so the waits end whatever the scheduling; every wait is bounded
+// anyway and records a timeout in an error word instead of spinning on.
+// Status words carry the call's epoch (a per-scratch counter advanced by the
+// host at every call), so nothing has to be cleared between calls.  A radix
+// pass is histogram -> single-pass scan of the digit-major histogram ->
+// stable scatter; inside a tile, equal digits are ranked in item order with
+// __match_any_sync per warp and a per-digit prefix over the 8 warps.  Lists
+// of at most one tile are sorted in one CTA.
 #include "kernels.h"
 
 namespace upr {
@@ -101,92 +108,206 @@ __device__ __forceinline__ void store_items(T *__restrict__ out, int64_t base, i
     }
 }
 
-// Exclusive scan of the tile totals part[0 .. tiles) by one CTA, in chunks of
-// 2048 with a carry; optionally writes the grand total (as int32) to *d_total.
+// ---- decoupled look-back
+constexpr uint32_t kAgg = 1, kIncl = 2;
+constexpr int kMaxSpin = 1 << 22;            // polls before a wait gives up (error word set)
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Tile status of the scans: a flag word ((epoch << 2) | state) and separate
+// aggregate / inclusive values (a value is never overwritten after its flag).
+template <typename T>
+struct ScanState {
+    uint32_t *flag;
+    T *agg, *incl;
+    unsigned int *ctr;      // [0] next tile, [1] finished CTAs
+    int32_t *err;
+};
+
+// Waits (bounded) until tile j's flag carries this epoch; returns its state
+// (kAgg / kIncl), or 0 after a timeout (recorded in *err).
+__device__ __forceinline__ bool gave_up(const int32_t *err) { return *(volatile const int32_t *)err != 0; }
+
+__device__ __forceinline__ uint32_t wait_flag(const uint32_t *flag, uint32_t epoch, int32_t *err) {
+    for (int it = 0; it < kMaxSpin; it++) {
+        const uint32_t f = ld_acquire(flag);
+        if ((f >> 2) == epoch) return f & 3u;
+        if (it >= 32) {
+            if ((it & 1023) == 0 && gave_up(err)) return 0;   // another wait already timed out
+            __nanosleep(64);
+        }
+    }
+    atomicOr(err, 1);
+    return 0;
+}
+
+// The next tile for this CTA (all threads get it).
+__device__ __forceinline__ int64_t next_tile(unsigned int *ctr, uint32_t *s_tile) {
+    if (threadIdx.x == 0) *s_tile = atomicAdd(&ctr[0], 1u);
+    __syncthreads();
+    const int64_t t = *s_tile;
+    __syncthreads();
+    return t;
+}
+
+// CTAs that take part in a pass over `tiles` tiles: no more than there are
+// tiles; the others return at once without touching the counters.
+__device__ __forceinline__ unsigned participants(int64_t tiles) {
+    return (unsigned)min((int64_t)gridDim.x, tiles);
+}
+
+// Called by every taking-part CTA once it takes no more tiles: the last one
+// resets the counters.
+__device__ __forceinline__ void finish_tiles(unsigned int *ctr, unsigned parts) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1u) == parts - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+        }
+    }
+}
+
+// Exclusive prefix (over the preceding tiles) of `total` for tile t, computed
+// by warp 0 and published by its lane 0: the warp reads the status of 32
+// preceding tiles at a time (lane l: tile j - l), adds the published values
+// up to the nearest inclusive prefix, and goes on to the next 32 if there is
+// none among them.  Returns the prefix in every lane of warp 0.
 template <typename Op, typename T>
-__device__ void scan_partials(T *part, int64_t tiles, int32_t *d_total, T *s_warp) {
-    T carry = Op::template identity<T>();
-    for (int64_t c0 = 0; c0 < tiles; c0 += kTile) {
-        T x[kItems];
-        const int64_t first = c0 + (int64_t)threadIdx.x * kItems;
-#pragma unroll
-        for (int j = 0; j < kItems; j++) x[j] = first + j < tiles ? __ldcg(part + first + j) : Op::template identity<T>();
-        T acc = Op::template identity<T>();
-#pragma unroll
-        for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, x[j]);
-        T total;
-        T run = Op::template apply<T>(carry, block_exclusive<Op>(acc, s_warp, &total));
-#pragma unroll
-        for (int j = 0; j < kItems; j++) {
-            const T nxt = Op::template apply<T>(run, x[j]);
-            if (first + j < tiles) part[first + j] = run;
-            run = nxt;
+__device__ __forceinline__ T lookback(const ScanState<T> &st, int64_t t, T total, uint32_t epoch) {
+    const int lane = threadIdx.x & 31;
+    T excl = Op::template identity<T>();
+    if (t == 0) {
+        if (lane == 0) {
+            st.incl[0] = total;
+            st_release(&st.flag[0], (epoch << 2) | kIncl);
         }
-        carry = Op::template apply<T>(carry, total);
+        return excl;
     }
-    if (d_total && threadIdx.x == 0) *d_total = (int32_t)carry;
+    if (lane == 0) {
+        st.agg[t] = total;
+        st_release(&st.flag[t], (epoch << 2) | kAgg);
+    }
+    for (int64_t j = t - 1; j >= 0; j -= 32) {
+        const int64_t jj = j - lane;
+        uint32_t s = 0;
+        T v = Op::template identity<T>();
+        if (jj >= 0) {
+            s = wait_flag(&st.flag[jj], epoch, st.err);
+            if (s == kIncl) v = st.incl[jj];
+            else if (s == kAgg) v = st.agg[jj];
+        }
+        const unsigned incl = __ballot_sync(0xffffffffu, s == kIncl);
+        const unsigned bad = __ballot_sync(0xffffffffu, jj >= 0 && s == 0);
+        // lanes up to the nearest inclusive prefix (all lanes if none) contribute
+        const int stop = incl ? __ffs(incl) - 1 : 31;
+        if (lane > stop) v = Op::template identity<T>();
+        for (int o = 16; o > 0; o >>= 1) v = Op::template apply<T>(v, __shfl_xor_sync(0xffffffffu, v, o));
+        excl = Op::template apply<T>(excl, v);
+        if (incl || bad) break;                       // done (or a wait timed out: error recorded)
+    }
+    if (lane == 0) {
+        st.incl[t] = Op::template apply<T>(excl, total);
+        st_release(&st.flag[t], (epoch << 2) | kIncl);
+    }
+    return excl;
 }
 
-// Per-tile totals; the CTA that finishes last (ticket counter, no waiting)
-// scans them and resets the ticket.
+// Single-pass scan (see the top of the file).  A one-tile list needs neither
+// the tile counters nor the look-back.
 template <typename Op, typename T, typename TIn>
-__global__ void __launch_bounds__(kThreads) k_tile_reduce(const TIn *__restrict__ in, const int32_t *__restrict__ d_n,
-                                                          int64_t n_max, T *__restrict__ part, int vec,
-                                                          unsigned int *__restrict__ ticket) {
-    __shared__ T s_warp[kWarps];
-    __shared__ bool s_last;
-    const int64_t n = count_of(d_n, n_max);
-    for (int64_t tile = blockIdx.x; tile < tiles_of(n); tile += gridDim.x) {
-        TIn x[kItems];
-        load_items(in, tile * kTile, n, vec != 0, x);
-        T acc = Op::template identity<T>();
+__device__ __forceinline__ void scan_tile(const TIn *in, T *out, int64_t n, int inclusive, int vec,
+                                          const ScanState<T> &st, uint32_t epoch, int64_t tile, bool alone,
+                                          T *s_warp, T *s_excl) {
+    TIn x[kItems];
+    load_items(in, tile * kTile, n, (vec & 1) != 0, x);
+    T acc = Op::template identity<T>();
 #pragma unroll
-        for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, (T)x[j]);
-        T total;
-        block_exclusive<Op>(acc, s_warp, &total);
-        if (threadIdx.x == 0) part[tile] = total;
+    for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, (T)x[j]);
+    T total;
+    const T pre = block_exclusive<Op>(acc, s_warp, &total);
+    if (alone) {
+        if (threadIdx.x == 0) *s_excl = Op::template identity<T>();
+    } else if (threadIdx.x < 32) {
+        const T e = lookback<Op>(st, tile, total, epoch);
+        if (threadIdx.x == 0) *s_excl = e;
     }
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    T run = Op::template apply<T>(*s_excl, pre);
+    T y[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+        const T nxt = Op::template apply<T>(run, (T)x[j]);
+        y[j] = inclusive ? nxt : run;
+        run = nxt;
+    }
+    store_items(out, tile * kTile, n, (vec & 2) != 0, y);
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    scan_partials<Op, T>(part, tiles_of(n), nullptr, s_warp);
-    if (threadIdx.x == 0) *ticket = 0;
 }
 
-// Scans every tile with the offset from part[] (exclusive-scanned totals; null = one tile).
 template <typename Op, typename T, typename TIn>
-__global__ void __launch_bounds__(kThreads) k_tile_scan(const TIn *__restrict__ in, T *__restrict__ out,
-                                                        const int32_t *__restrict__ d_n, int64_t n_max,
-                                                        const T *__restrict__ part, int inclusive, int vec) {
+__global__ void __launch_bounds__(kThreads) k_scan(const TIn *in, T *out, const int32_t *__restrict__ d_n,
+                                                   int64_t n_max, int inclusive, int vec, ScanState<T> st,
+                                                   uint32_t epoch) {
     __shared__ T s_warp[kWarps];
+    __shared__ T s_excl;
+    __shared__ uint32_t s_tile;
     const int64_t n = count_of(d_n, n_max);
-    for (int64_t tile = blockIdx.x; tile < tiles_of(n); tile += gridDim.x) {
-        TIn x[kItems];
-        load_items(in, tile * kTile, n, (vec & 1) != 0, x);
-        T acc = Op::template identity<T>();
-#pragma unroll
-        for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, (T)x[j]);
-        T total;
-        const T pre = block_exclusive<Op>(acc, s_warp, &total);
-        T run = Op::template apply<T>(part ? part[tile] : Op::template identity<T>(), pre);
-        T y[kItems];
-#pragma unroll
-        for (int j = 0; j < kItems; j++) {
-            const T nxt = Op::template apply<T>(run, (T)x[j]);
-            y[j] = inclusive ? nxt : run;
-            run = nxt;
-        }
-        store_items(out, tile * kTile, n, (vec & 2) != 0, y);
+    const int64_t tiles = tiles_of(n);
+    const unsigned parts = participants(tiles);
+    if (blockIdx.x >= parts) return;
+    if (tiles == 1) {
+        scan_tile<Op>(in, out, n, inclusive, vec, st, epoch, 0, true, s_warp, &s_excl);
+        return;
     }
+    for (;;) {
+        const int64_t tile = next_tile(st.ctr, &s_tile);
+        if (tile >= tiles) break;
+        scan_tile<Op>(in, out, n, inclusive, vec, st, epoch, tile, false, s_warp, &s_excl);
+    }
+    finish_tiles(st.ctr, parts);
 }
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Persistent grid of the tile kernels: tiles are taken dynamically.
 inline unsigned tile_grid(int64_t tiles_max) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_max, (int64_t)device_sm_count() * 8));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_max, (int64_t)device_sm_count() * 4));
+}
+
+// Tag of a new call.  Tags live in 30 bits; when they run out (after about
+// 10^9 calls on one scratch), the status memory is cleared on the stream and
+// tags restart at 1, so no stale word can carry a current tag.
+inline uint32_t next_epoch(const Scratch &tmp, cudaStream_t s) {
+    uint32_t e = ++(*tmp.epoch);
+    if (e >= (1u << 30) - 1) {
+        UPR_CUDA(cudaMemsetAsync(tmp.mem, 0, tmp.mem_bytes, s));
+        UPR_CUDA(cudaMemsetAsync(tmp.scan, 0, tmp.scan_bytes, s));
+        *tmp.epoch = e = 1;
+    }
+    return e;
+}
+
+// The layout depends on the scratch's capacity only, never on the call, so a
+// status word is only ever read at a place where status words are written.
+template <typename T>
+ScanState<T> scan_state(const Scratch &tmp, int64_t tiles_max) {
+    if (tiles_max > tmp.tiles_cap) throw CudaError{cudaErrorInvalidValue, "scan longer than the scratch"};
+    const size_t stride = ((size_t)tmp.tiles_cap * sizeof(int64_t) + 255) & ~(size_t)255;
+    ScanState<T> st;
+    st.flag = reinterpret_cast<uint32_t *>(tmp.scan);
+    st.agg = reinterpret_cast<T *>(tmp.scan + stride);
+    st.incl = reinterpret_cast<T *>(tmp.scan + 2 * stride);
+    st.ctr = tmp.ticket;
+    st.err = tmp.err;
+    return st;
 }
 
 template <typename Op, typename T, typename TIn>
@@ -195,70 +316,65 @@ void scan_impl(const TIn *in, T *out, Count n, bool inclusive, Scratch tmp, cuda
     const int vin = aligned16(in) ? 1 : 0;
     const int vio = vin | (aligned16(out) ? 2 : 0);
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    if (tiles_max == 1) {
-        k_tile_scan<Op, T, TIn><<<1, kThreads, 0, s>>>(in, out, n.d, n.max, (const T *)nullptr, inclusive ? 1 : 0, vio);
-        UPR_LAUNCH_CHECK();
-        return;
-    }
-    T *part = (T *)tmp.mem;
-    k_tile_reduce<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, n.d, n.max, part, vin, tmp.ticket);
-    UPR_LAUNCH_CHECK();
-    k_tile_scan<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, part, inclusive ? 1 : 0,
-                                                                      vio);
+    const uint32_t epoch = next_epoch(tmp, s);
+    k_scan<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, inclusive ? 1 : 0, vio,
+                                                                  scan_state<T>(tmp, tiles_max), epoch);
     UPR_LAUNCH_CHECK();
 }
 
 // ------------------------------------------------------------------ compaction
-// Pass 1: number of set flags per tile.  One-CTA scan of those.  Pass 2: every
-// thread ranks its 8 flags in registers and writes the indices of the set
-// ones; tile order, then thread order, then item order = index order.
-__global__ void __launch_bounds__(kThreads) k_flag_count(const int32_t *__restrict__ flags, const int32_t *__restrict__ d_n,
-                                                         int64_t n_max, int32_t *__restrict__ counts, int vec,
-                                                         int32_t *__restrict__ d_count, unsigned int *__restrict__ ticket) {
-    __shared__ int32_t s_warp[kWarps];
-    __shared__ bool s_last;
-    const int64_t n = count_of(d_n, n_max);
-    for (int64_t tile = blockIdx.x; tile < tiles_of(n); tile += gridDim.x) {
-        int32_t x[kItems];
-        load_items(flags, tile * kTile, n, vec != 0, x);
-        int32_t c = 0;
+// Single pass: a tile counts its set flags, takes its offset by look-back and
+// every thread writes the indices of its set flags (tile order, then thread
+// order, then item order = index order); the last tile writes the total.
+__device__ __forceinline__ void compact_tile(const int32_t *flags, int64_t n, int64_t tiles, int32_t *out,
+                                             int32_t *d_count, int vec, const ScanState<int32_t> &st,
+                                             uint32_t epoch, int64_t tile, bool alone, int32_t *s_warp,
+                                             int32_t *s_excl) {
+    int32_t x[kItems];
+    load_items(flags, tile * kTile, n, vec != 0, x);
+    int32_t c = 0;
 #pragma unroll
-        for (int j = 0; j < kItems; j++) c += x[j] != 0;
-        int32_t total;
-        block_exclusive<OpSum>(c, s_warp, &total);
-        if (threadIdx.x == 0) counts[tile] = total;
+    for (int j = 0; j < kItems; j++) c += x[j] != 0;
+    int32_t total;
+    const int32_t pre = block_exclusive<OpSum>(c, s_warp, &total);
+    if (threadIdx.x < 32) {
+        const int32_t e = alone ? 0 : lookback<OpSum>(st, tile, total, epoch);
+        if (threadIdx.x == 0) {
+            *s_excl = e;
+            if (tile == tiles - 1) *d_count = e + total;
+        }
     }
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    int32_t pos = *s_excl + pre;
+    const int64_t first = tile * kTile + (int64_t)threadIdx.x * kItems;
+#pragma unroll
+    for (int j = 0; j < kItems; j++)
+        if (x[j]) out[pos++] = (int32_t)(first + j);
     __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    scan_partials<OpSum, int32_t>(counts, tiles_of(n), d_count, s_warp);
-    if (threadIdx.x == 0) *ticket = 0;
 }
 
-__global__ void __launch_bounds__(kThreads) k_flag_scatter(const int32_t *__restrict__ flags, const int32_t *__restrict__ d_n,
-                                                           int64_t n_max, const int32_t *__restrict__ offs,
-                                                           int32_t *__restrict__ out, int32_t *__restrict__ d_count,
-                                                           int vec) {
+__global__ void __launch_bounds__(kThreads) k_compact(const int32_t *__restrict__ flags, const int32_t *__restrict__ d_n,
+                                                      int64_t n_max, int32_t *__restrict__ out,
+                                                      int32_t *__restrict__ d_count, int vec, ScanState<int32_t> st,
+                                                      uint32_t epoch) {
     __shared__ int32_t s_warp[kWarps];
+    __shared__ int32_t s_excl;
+    __shared__ uint32_t s_tile;
     const int64_t n = count_of(d_n, n_max);
-    if (!offs && blockIdx.x == 0 && threadIdx.x == 0 && n == 0) *d_count = 0;
-    for (int64_t tile = blockIdx.x; tile < tiles_of(n); tile += gridDim.x) {
-        int32_t x[kItems];
-        load_items(flags, tile * kTile, n, vec != 0, x);
-        int32_t c = 0;
-#pragma unroll
-        for (int j = 0; j < kItems; j++) c += x[j] != 0;
-        int32_t total;
-        int32_t pos = block_exclusive<OpSum>(c, s_warp, &total) + (offs ? offs[tile] : 0);
-        const int64_t first = tile * kTile + (int64_t)threadIdx.x * kItems;
-#pragma unroll
-        for (int j = 0; j < kItems; j++)
-            if (x[j]) out[pos++] = (int32_t)(first + j);
-        if (!offs && threadIdx.x == 0) *d_count = total;   // single tile
+    const int64_t tiles = tiles_of(n);
+    if (tiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_count = 0;
+    const unsigned parts = participants(tiles);
+    if (blockIdx.x >= parts) return;
+    if (tiles == 1) {
+        compact_tile(flags, n, tiles, out, d_count, vec, st, epoch, 0, true, s_warp, &s_excl);
+        return;
     }
+    for (;;) {
+        const int64_t tile = next_tile(st.ctr, &s_tile);
+        if (tile >= tiles) break;
+        compact_tile(flags, n, tiles, out, d_count, vec, st, epoch, tile, false, s_warp, &s_excl);
+    }
+    finish_tiles(st.ctr, parts);
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -417,13 +533,13 @@ __global__ void k_iota_u32(uint32_t *v, int64_t n) {
 }  // namespace
 
 size_t scan_temp_bytes(int64_t n) {
-    return (size_t)(ceil_div(n > 0 ? n : 1, kTile) + 64) * sizeof(int64_t);
+    const size_t tiles = (size_t)ceil_div(n > 0 ? n : 1, kTile);
+    return 3 * ((tiles * sizeof(int64_t) + 255) & ~(size_t)255);
 }
 
 size_t radix_temp_bytes(int64_t n) {
-    const int64_t tiles = ceil_div(n > 0 ? n : 1, kTile);
-    const size_t hist = (size_t)kBins * tiles;
-    return hist * sizeof(int32_t) + 256 + scan_temp_bytes((int64_t)hist);
+    const size_t tiles = (size_t)ceil_div(n > 0 ? n : 1, kTile);
+    return ((tiles * kBins + 64) * sizeof(int32_t) + 255) & ~(size_t)255;
 }
 
 void exclusive_sum_i32(const int32_t *in, int32_t *out, Count n, Scratch tmp, cudaStream_t s) {
@@ -458,16 +574,18 @@ bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     UPR_LAUNCH_CHECK();
     if (n.max <= kTile) return alt;
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    int32_t *hist = (int32_t *)tmp.mem;
-    int32_t *d_hist_n = (int32_t *)(tmp.mem + (size_t)kBins * tiles_max * sizeof(int32_t));
-    const Scratch stmp{tmp.mem + (size_t)kBins * tiles_max * sizeof(int32_t) + 256, tmp.ticket};
+    if (tiles_max > tmp.tiles_cap) throw CudaError{cudaErrorInvalidValue, "sort longer than the scratch"};
+    // digit-major per-tile histograms (kBins x tiles), scanned in place
+    int32_t *hist = reinterpret_cast<int32_t *>(tmp.mem);
+    int32_t *d_hist_n = hist + (size_t)kBins * tmp.tiles_cap;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_max, (int64_t)device_sm_count() * 8));
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     for (int p = 0; p < passes; p++) {
-        k_radix_hist<<<tile_grid(tiles_max), kThreads, 0, s>>>(ka, n.d, n.max, 8 * p, hist, d_hist_n);
+        k_radix_hist<<<grid, kThreads, 0, s>>>(ka, n.d, n.max, 8 * p, hist, d_hist_n);
         UPR_LAUNCH_CHECK();
-        exclusive_sum_i32(hist, hist, Count{d_hist_n, (int64_t)kBins * tiles_max}, stmp, s);
-        k_radix_scatter<<<tile_grid(tiles_max), kThreads, 0, s>>>(ka, va, kb, vb, n.d, n.max, 8 * p, hist);
+        scan_impl<OpSum, int32_t, int32_t>(hist, hist, Count{d_hist_n, (int64_t)kBins * tiles_max}, false, tmp, s);
+        k_radix_scatter<<<grid, kThreads, 0, s>>>(ka, va, kb, vb, n.d, n.max, 8 * p, hist);
         UPR_LAUNCH_CHECK();
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -479,15 +597,9 @@ void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Coun
     if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
     const int vec = aligned16(flags) ? 1 : 0;
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    if (tiles_max == 1) {
-        k_flag_scatter<<<1, kThreads, 0, s>>>(flags, n.d, n.max, nullptr, out_idx, d_count, vec);
-        UPR_LAUNCH_CHECK();
-        return;
-    }
-    int32_t *counts = (int32_t *)tmp.mem;
-    k_flag_count<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, counts, vec, d_count, tmp.ticket);
-    UPR_LAUNCH_CHECK();
-    k_flag_scatter<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, counts, out_idx, d_count, vec);
+    const uint32_t epoch = next_epoch(tmp, s);
+    k_compact<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, out_idx, d_count, vec,
+                                                        scan_state<int32_t>(tmp, tiles_max), epoch);
     UPR_LAUNCH_CHECK();
 }
 
