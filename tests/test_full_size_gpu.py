@@ -70,3 +70,107 @@ def test_full_size_matches_oracle(upr, builder):
     assert cut == g["cut_out"] and list(bw) == g["block_weights"]
     L = (-(-int(np.sum(w.vwgt if w.vwgt is not None else np.ones(w.n))) // w.k) * (10**6 + round(w.eps * 1e6))) // 10**6
     assert max(g["block_weights"]) <= L
+
+
+def _oracle_job(args):
+    """One graph through the oracle (runs in a spawned worker)."""
+    import oracle as orc
+    import synth as syn
+    kind, spec = args
+    w = syn.cached(syn.batch_graph, spec) if kind == "batch" else syn.cached(syn.served_rmat, *spec)
+    orc.build()
+    rc, p, c, _ = orc.refine(w, w.part, w.rounds)
+    return rc, p, c
+
+
+def _oracle_pool(jobs):
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_oracle_job, jobs)
+
+
+def test_batch_4096_graphs_sampled(upr):
+    """The 4096-graph Chung-Lu batch in the bench's launch configuration (graphs
+    grouped by k, one batch context per group on its own stream, the groups
+    refined concurrently from host threads), every graph's status and cut
+    against its balance, and 32 graphs sampled across the groups against the
+    oracle bit for bit."""
+    import concurrent.futures as cf
+    import torch
+    graphs = synth.batch_graphs(4096)
+    by_k = {}
+    for i, w in enumerate(graphs):
+        by_k.setdefault(w.k, []).append(i)
+    groups = []
+    for k, idx in sorted(by_k.items()):
+        st = torch.cuda.Stream()
+        ctx = upr.upr_batch_create([(graphs[i].xadj, graphs[i].adj, graphs[i].vwgt, graphs[i].adjw) for i in idx], k,
+                                   [graphs[i].eps for i in idx], stream=upr.ctypes.c_void_p(st.cuda_stream))
+        part = torch.from_numpy(np.concatenate([graphs[i].part for i in idx]).astype(np.int32)).cuda()
+        groups.append((idx, st, ctx, part))
+    torch.cuda.synchronize()
+
+    def run(gr):
+        idx, st, ctx, part = gr
+        torch.cuda.set_device(0)
+        return upr.upr_batch_refine(ctx, part, graphs[idx[0]].rounds)
+
+    with cf.ThreadPoolExecutor(len(groups)) as ex:
+        results = list(ex.map(run, groups))
+    torch.cuda.synchronize()
+    parts = {}
+    for (idx, st, ctx, part), (status, cin, cout, stats) in zip(groups, results):
+        assert (status == 0).all()
+        assert (cout <= cin).all()
+        host = part.cpu().numpy()
+        for j, i in enumerate(idx):
+            o0, o1 = ctx.offsets[j], ctx.offsets[j + 1]
+            parts[i] = (host[o0:o1], int(cout[j]))
+            w = graphs[i]
+            bw = np.bincount(parts[i][0], minlength=w.k)
+            assert bw.max() <= ctx.lmax[j]
+    sample = sorted({int(x) for x in np.linspace(0, 4095, 32).round()})
+    for i, (rc, p, c) in zip(sample, _oracle_pool([("batch", i) for i in sample])):
+        assert rc == 0
+        assert np.array_equal(parts[i][0], p), i
+        assert parts[i][1] == c, i
+
+
+def test_served_mix_sampled(upr):
+    """A burst of the served mix (Chung-Lu batch graphs with their own k, R-MAT
+    scale-18 graphs with k from {8, 64}) into the continuous-batching server
+    with 8 slots, as the bench serves it: every repeat of an input gives the
+    same result, and sampled jobs equal the oracle bit for bit."""
+    small = [synth.cached(synth.batch_graph, i) for i in range(48)]
+    rmat = [synth.cached(synth.served_rmat, 18, 8 if i < 2 else 64, i) for i in range(4)]
+    rng = np.random.default_rng(5)
+    jobs = []
+    for _ in range(160):
+        if rng.random() < 0.55:
+            jobs.append(("batch", int(rng.integers(len(small)))))
+        else:
+            jobs.append(("rmat", int(rng.integers(len(rmat)))))
+    srv = upr.Server(max_jobs=8)
+    try:
+        tickets = [srv.submit(small[j] if kind == "batch" else rmat[j]) for kind, j in jobs]
+        out = [srv.wait(t) for t in tickets]
+    finally:
+        srv.close()
+    seen = {}
+    batched = 0
+    for (kind, j), (p, c, st) in zip(jobs, out):
+        key = (kind, j)
+        if key in seen:
+            assert np.array_equal(seen[key][0], p) and seen[key][1] == c
+        else:
+            seen[key] = (p, c)
+        batched += st.batch_graphs > 1
+    assert batched > 0
+    sample = sorted(seen)[:: max(1, len(seen) // 12)]
+    specs = [("batch", j) if kind == "batch" else ("rmat", (18, 8 if j < 2 else 64, j)) for kind, j in sample]
+    for key, (rc, p, c) in zip(sample, _oracle_pool(specs)):
+        assert rc == 0
+        assert np.array_equal(seen[key][0], p), key
+        assert seen[key][1] == c, key
