@@ -568,7 +568,8 @@ def run_gpu(args):
                                        "host_wall": s0.ms_host},
                 "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
                            "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
-                           "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds},
+                           "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds,
+                           "lanes_per_node": {"select": s0.select_lanes, "propose": s0.propose_lanes}},
                 "other_configs": others, "batched": batched, "served": served}
         print(json.dumps(line))
     if ws > 1:

@@ -80,6 +80,10 @@ typedef struct {
                                     multiset hash, ranges, weights). 1                      */
     int32_t round_offset;        /* rounds already run of a longer schedule (resume). 0       */
     int32_t total_rounds;        /* length of the tau schedule; 0 = the rounds of each call   */
+    int32_t autotune;            /* 1: on a context's first large calls, time the lane
+                                    schedules of the selection and proposal kernels on the
+                                    actual inputs and keep the fastest (results never depend
+                                    on the schedule). 1                                      */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 
@@ -106,6 +110,8 @@ typedef struct {
     double  ms_host;             /* wall-clock time of the call on the host             */
     int32_t batch_graphs;        /* graphs refined together in this call (batches and
                                     batched server jobs; 1 = one graph)                 */
+    int32_t select_lanes;        /* lanes per node of the selection kernel (0: scalar)  */
+    int32_t propose_lanes;       /* lanes per node of the proposal kernel (0: scalar)   */
     int32_t pad0;
 } upr_stats;
 

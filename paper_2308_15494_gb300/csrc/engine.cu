@@ -73,6 +73,13 @@ struct upr_ctx {
     int32_t ng = 1;                   // graphs bound (a batch when > 1)
     bool table_valid = false;         // W holds the table of part0 (carried from the previous round)
     uint32_t epoch = 0;               // call tag of the primitives' status words (Scratch::epoch)
+    // lane schedules of the selection / proposal kernels: chosen by timing the
+    // candidates on this binding's inputs (see tune_*), default until then
+    LaneCfg sel_cfg{0, 0}, prop_cfg{0, 0};
+    bool sel_tuned = false, prop_tuned = false;
+    int sel_pending = 0, prop_pending = 0;      // candidates timed in the current round / sub-round
+    LaneCfg sel_cands[3], prop_cands[3];
+    cudaEvent_t ev_tune[12] = {};
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -270,6 +277,49 @@ enum {
     CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_SLOTS = 32
 };
 
+// ---- lane-schedule tuning.  A kernel whose schedule is not chosen yet runs
+// every candidate back to back on the same inputs (each run rewrites the
+// same outputs, all equal), timed with events; the times are read after the
+// next synchronisation the round makes anyway.  Small inputs keep the
+// default (nothing to gain, and their timings would be launch noise).
+bool worth_tuning(const upr_ctx *c) { return c->prm.autotune && (int64_t)c->n * c->k >= ((int64_t)1 << 22); }
+
+template <typename F>
+void run_tuned(upr_ctx *c, bool tuned, LaneCfg cfg, LaneCfg *cands, int *pending, cudaEvent_t *ev, F launch) {
+    *pending = 0;
+    if (!tuned && worth_tuning(c)) {
+        const int nc = lane_candidates(c->k, cands);
+        if (nc > 1) {
+            for (int i = 0; i < nc; i++) {
+                UPR_CUDA(cudaEventRecord(ev[2 * i], c->s));
+                launch(cands[i]);
+                UPR_CUDA(cudaEventRecord(ev[2 * i + 1], c->s));
+            }
+            *pending = nc;
+            return;
+        }
+    }
+    launch(cfg);
+}
+
+// After a synchronisation: keep the fastest candidate if the work was large
+// enough to tell them apart (otherwise try again next time).
+void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands, cudaEvent_t *ev, float min_ms) {
+    if (*pending <= 1) return;
+    int best = 0;
+    float tbest = 0;
+    for (int i = 0; i < *pending; i++) {
+        float t = 0;
+        UPR_CUDA(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+        if (i == 0 || t < tbest) { tbest = t; best = i; }
+    }
+    if (tbest >= min_ms) {
+        *cfg = cands[best];
+        *tuned = true;
+    }
+    *pending = 0;
+}
+
 /*
  * One round on c->part0 / c->C0 / c->cut (device state).  Every step is
  * enqueued on c->s with its list lengths in device memory; the host waits
@@ -311,7 +361,9 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
         Penalty pen{c->PW, c->F, c->C0, c->Lb, c->first_slot};
         // ---- (b2) best move per boundary node
-        select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, s);
+        run_tuned(c, c->sel_tuned, c->sel_cfg, c->sel_cands, &c->sel_pending, c->ev_tune, [&](LaneCfg cfg) {
+            select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, cfg, s);
+        });
         select_flags(c->flags, c->idxA, cnt + CNT_CAND, cN, c->tmp, s);
         const Count cC{cnt + CNT_CAND, n};
         // ---- (b3) inflow penalties: order by (target, s0 desc, id)
@@ -348,7 +400,15 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
         rebalance_begin(G, c->C, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, h, c->prm.max_subrounds, ctl, light,
                         s);
-        rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain, c->flags, s);
+        if (h == 1)
+            run_tuned(c, c->prop_tuned, c->prop_cfg, c->prop_cands, &c->prop_pending, c->ev_tune + 6,
+                      [&](LaneCfg cfg) {
+                          rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt,
+                                                 c->prop_gain, c->flags, cfg, s);
+                      });
+        else
+            rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain,
+                                   c->flags, c->prop_cfg, s);
         select_flags(c->flags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
         rebalance_gather_list(c->L1, c->idxD, cnt + CNT_P, c->idxA, n, s);
         uint64_t *kA; uint32_t *A;
@@ -378,6 +438,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         rebalance_end(G, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
         UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
+        settle_tuning(&c->prop_cfg, &c->prop_tuned, &c->prop_pending, c->prop_cands, c->ev_tune + 6, 0.02f);
         if (c->hctl->stopped) break;
     }
     UPR_CUDA(cudaEventRecord(c->ev[6], s));
@@ -473,6 +534,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     else UPR_CUDA(cudaMemcpyAsync(c->hbest, c->tot, sizeof(long long) * 3, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaMemcpyAsync(c->hcnt + 40, c->tmp.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaStreamSynchronize(s));
+    settle_tuning(&c->sel_cfg, &c->sel_tuned, &c->sel_pending, c->sel_cands, c->ev_tune, 0.05f);
     // a bounded wait of a primitive gave up: the round's lists are not trustworthy
     if (c->hcnt[40] != 0) { c->table_valid = false; throw CudaError{cudaErrorLaunchTimeout, "primitive wait"}; }
     {
@@ -553,6 +615,7 @@ void free_ctx(upr_ctx *c) {
     if (c->h) cudaFreeHost(c->h);
     if (c->h8) cudaFreeHost(c->h8);
     for (auto &e : c->ev) if (e) cudaEventDestroy(e);
+    for (auto &e : c->ev_tune) if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -683,6 +746,12 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
                           4 * c->n * (int64_t)c->k;
     st.batch_graphs = ng;
+    {
+        LaneCfg d[3];
+        const int nd = lane_candidates(c->k, d);
+        st.select_lanes = nd ? (c->sel_cfg.G > 0 ? c->sel_cfg.G : d[0].G) : 0;
+        st.propose_lanes = nd ? (c->prop_cfg.G > 0 ? c->prop_cfg.G : d[0].G) : 0;
+    }
     if (stats) *stats = st;
     return UPR_OK;
 }
@@ -701,6 +770,7 @@ void upr_params_default(upr_params *p) {
     p->validate = 1;
     p->round_offset = 0;
     p->total_rounds = 0;
+    p->autotune = 1;
     p->stream = nullptr;
 }
 
@@ -722,7 +792,7 @@ const char *upr_status_str(upr_status s) {
 static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
-           p.total_rounds >= 0 && p.total_rounds <= 65536;
+           p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1);
 }
 
 }  // extern "C"
@@ -854,6 +924,11 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     if (!c->h8) UPR_CUDA(cudaMallocHost((void **)&c->h8, 2 * (size_t)kMaxK + 64));
     for (auto &ev : c->ev)
         if (!ev) UPR_CUDA(cudaEventCreate(&ev));
+    for (auto &ev : c->ev_tune)
+        if (!ev) UPR_CUDA(cudaEventCreate(&ev));
+    c->sel_cfg = c->prop_cfg = LaneCfg{0, 0};
+    c->sel_tuned = c->prop_tuned = false;
+    c->sel_pending = c->prop_pending = 0;
     cudaStream_t s = c->s;
     if (ng == 1) {
         copy_in(c->xadj, gs[0].xadj, sizeof(int64_t) * (n + 1), s);

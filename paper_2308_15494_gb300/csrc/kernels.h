@@ -139,8 +139,15 @@ struct Penalty {
 };
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
              int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s);
+// Lanes per node (G) and 16-byte chunks per lane (CH) of the vectorised
+// selection and proposal kernels (k % 4 == 0, k <= 256, 4*G*CH >= k).  A
+// schedule only decides how the work is spread over lanes, never the
+// result.  G = 0: the default (the fewest chunks per lane).
+struct LaneCfg { int32_t G, CH; };
+// The schedules worth timing for k (the default first); returns their number (0..3).
+int lane_candidates(int32_t k, LaneCfg *out);
 void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Penalty pen, int32_t *cand_tgt,
-                  int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s);
+                  int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s);
 void cand_keys(const int32_t *cand_idx, const int32_t *d_count, const int32_t *cand_tgt, const int64_t *cand_s0,
                int gbits, uint64_t *keys, uint32_t *vals, int64_t max_count, cudaStream_t s);
 void cand_gather(const GraphDev &g, const int32_t *cand_idx, const uint32_t *order, const int32_t *d_count,
@@ -184,7 +191,7 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
                                    int32_t *prop_gain, int32_t *flags, cudaStream_t s);
 void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                             const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
-                            int32_t *prop_gain, int32_t *flags, cudaStream_t s);
+                            int32_t *prop_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s);
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                          int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s);
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,

@@ -523,48 +523,51 @@ void rebalance_gather_list(const int32_t *list, const int32_t *pos, const int32_
     UPR_LAUNCH_CHECK();
 }
 
+namespace {
+
+template <int G, int CH>
+void launch_propose_vec(bool exact, bool batch, unsigned blocks, size_t shm, cudaStream_t s, const GraphDev &g,
+                        const int32_t *list, const int32_t *d_n1, const int32_t *part, const int32_t *W,
+                        const RebalState &st, int32_t *prop_tgt, int32_t *prop_gain, int32_t *flags) {
+    if constexpr (CH == 1 || (G == 32 && CH == 2)) {
+        if (!exact) {
+            if (batch) k_propose_vec<G, CH, false, true><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
+            else k_propose_vec<G, CH, false, false><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
+            return;
+        }
+    }
+    if (batch) k_propose_vec<G, CH, true, true><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
+    else k_propose_vec<G, CH, true, false><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
+}
+
+}  // namespace
+
 void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                             const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
-                            int32_t *prop_gain, int32_t *flags, cudaStream_t s) {
+                            int32_t *prop_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s) {
     if (n1_max <= 0) return;
     const int k = g.k;
     const bool batch = g.ng > 1;
     const size_t shm = batch ? 0 : sizeof(int32_t) * (size_t)k + (size_t)k + 16;
-    if (k % 4 == 0 && k <= 256) {
-        int G = 1;
-        while (G < 32 && 4 * G < k) G <<= 1;
-        const int CH = (k + 4 * G - 1) / (4 * G);
+    LaneCfg cands[3];
+    if (lane_candidates(k, cands) > 0) {
+        if (cfg.G <= 0) cfg = cands[0];
+        const int G = cfg.G, CH = cfg.CH;
         const bool exact = k == 4 * G * CH;
         const int64_t groups = 256 / G;
-        const int64_t blocks = std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 8);
-#define UPR_PV(GG, CC, EX, BA) k_propose_vec<GG, CC, EX, BA><<<(unsigned)blocks, 256, shm, s>>>( \
-        g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags)
-#define UPR_PVE(GG, CC)                                \
-    do {                                               \
-        if (batch) {                                   \
-            if (exact) UPR_PV(GG, CC, true, true);     \
-            else UPR_PV(GG, CC, false, true);          \
-        } else {                                       \
-            if (exact) UPR_PV(GG, CC, true, false);    \
-            else UPR_PV(GG, CC, false, false);         \
-        }                                              \
-    } while (0)
-        if (CH == 1) {
-            switch (G) {
-                case 1: UPR_PVE(1, 1); break;
-                case 2: UPR_PVE(2, 1); break;
-                case 4: UPR_PVE(4, 1); break;
-                case 8: UPR_PVE(8, 1); break;
-                case 16: UPR_PVE(16, 1); break;
-                default: UPR_PVE(32, 1); break;
-            }
-        } else {
-            UPR_PVE(32, 2);
-        }
-#undef UPR_PVE
-#undef UPR_PV
-        UPR_LAUNCH_CHECK();
-        return;
+        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n1_max, groups), (int64_t)sm_count_reb() * 8);
+#define UPR_PVC(GG, CC)                                                                                        \
+    if (G == GG && CH == CC) {                                                                                 \
+        launch_propose_vec<GG, CC>(exact, batch, blocks, shm, s, g, list, d_n1, part, W, st, prop_tgt,         \
+                                   prop_gain, flags);                                                          \
+        UPR_LAUNCH_CHECK();                                                                                    \
+        return;                                                                                                \
+    }
+        UPR_PVC(1, 1) UPR_PVC(2, 1) UPR_PVC(4, 1) UPR_PVC(8, 1) UPR_PVC(16, 1) UPR_PVC(32, 1)
+        UPR_PVC(1, 2) UPR_PVC(2, 2) UPR_PVC(4, 2) UPR_PVC(8, 2) UPR_PVC(16, 2) UPR_PVC(32, 2)
+        UPR_PVC(1, 4) UPR_PVC(2, 4) UPR_PVC(4, 4) UPR_PVC(8, 4) UPR_PVC(16, 4)
+#undef UPR_PVC
+        throw CudaError{cudaErrorInvalidValue, "rebalance_propose_list: unsupported lane schedule"};
     }
     rebalance_propose_scalar_list(g, list, d_n1, n1_max, part, W, st, prop_tgt, prop_gain, flags, s);
 }

@@ -417,49 +417,68 @@ int select_group(int k) {
     return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
 }
 
+int lane_candidates(int32_t k, LaneCfg *out) {
+    if (k % 4 != 0 || k > 256) return 0;
+    int G = 1;
+    while (G < 32 && 4 * G < k) G <<= 1;
+    int CH = (k + 4 * G - 1) / (4 * G);
+    int cnt = 0;
+    out[cnt++] = LaneCfg{G, CH};
+    // fewer lanes per node, more chunks per lane (exact fits only, at most 4 chunks)
+    while (cnt < 3 && G > 1 && CH * 2 <= 4 && 4 * (G / 2) * (CH * 2) == k) {
+        G /= 2;
+        CH *= 2;
+        out[cnt++] = LaneCfg{G, CH};
+    }
+    return cnt;
+}
+
+namespace {
+
+template <int G, int CH>
+void launch_select_vec(bool exact, bool batch, unsigned blocks, size_t shm, cudaStream_t s, const GraphDev &g,
+                       const int32_t *part, const int32_t *W, const Penalty &pen, int smem_pw, int32_t *cand_tgt,
+                       int64_t *cand_s0, int32_t *cand_gain, int32_t *flags) {
+    if constexpr (CH == 1 || (G == 32 && CH == 2)) {
+        if (!exact) {
+            if (batch) k_select_vec<G, CH, false, true><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
+            else k_select_vec<G, CH, false, false><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
+            return;
+        }
+    }
+    if (batch) k_select_vec<G, CH, true, true><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
+    else k_select_vec<G, CH, true, false><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
+}
+
+}  // namespace
+
 void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Penalty pen, int32_t *cand_tgt,
-                  int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, cudaStream_t s) {
+                  int64_t *cand_s0, int32_t *cand_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s) {
     if (g.n == 0) return;
     const int k = g.k;
     const bool batch = g.ng > 1;
-    if (k % 4 == 0 && k <= 256) {
-        int G = 1;
-        while (G < 32 && 4 * G < k) G <<= 1;
-        const int CH = (k + 4 * G - 1) / (4 * G);
+    LaneCfg cands[3];
+    if (lane_candidates(k, cands) > 0) {
+        if (cfg.G <= 0) cfg = cands[0];
+        const int G = cfg.G, CH = cfg.CH;
         const bool exact = k == 4 * G * CH;
         const int smem_pw = !batch && (size_t)k * kSlots * 8 <= 40 * 1024;
         const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) +
                            (batch ? 0 : (sizeof(int32_t) + 1) * k);
         const int64_t groups = 256 / G;
-        const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
-#define UPR_SELV(GG, CC, EX, BA) k_select_vec<GG, CC, EX, BA><<<(unsigned)blocks, 256, shm, s>>>( \
-        g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags)
-#define UPR_SELVE(GG, CC)                                          \
-    do {                                                           \
-        if (batch) {                                               \
-            if (exact) UPR_SELV(GG, CC, true, true);               \
-            else UPR_SELV(GG, CC, false, true);                    \
-        } else {                                                   \
-            if (exact) UPR_SELV(GG, CC, true, false);              \
-            else UPR_SELV(GG, CC, false, false);                   \
-        }                                                          \
-    } while (0)
-        if (CH == 1) {
-            switch (G) {
-                case 1: UPR_SELVE(1, 1); break;
-                case 2: UPR_SELVE(2, 1); break;
-                case 4: UPR_SELVE(4, 1); break;
-                case 8: UPR_SELVE(8, 1); break;
-                case 16: UPR_SELVE(16, 1); break;
-                default: UPR_SELVE(32, 1); break;
-            }
-        } else {
-            UPR_SELVE(32, 2);
-        }
-#undef UPR_SELVE
-#undef UPR_SELV
-        UPR_LAUNCH_CHECK();
-        return;
+        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
+#define UPR_SELC(GG, CC)                                                                                       \
+    if (G == GG && CH == CC) {                                                                                 \
+        launch_select_vec<GG, CC>(exact, batch, blocks, shm, s, g, part, W, pen, smem_pw, cand_tgt, cand_s0,   \
+                                  cand_gain, flags);                                                           \
+        UPR_LAUNCH_CHECK();                                                                                    \
+        return;                                                                                                \
+    }
+        UPR_SELC(1, 1) UPR_SELC(2, 1) UPR_SELC(4, 1) UPR_SELC(8, 1) UPR_SELC(16, 1) UPR_SELC(32, 1)
+        UPR_SELC(1, 2) UPR_SELC(2, 2) UPR_SELC(4, 2) UPR_SELC(8, 2) UPR_SELC(16, 2) UPR_SELC(32, 2)
+        UPR_SELC(1, 4) UPR_SELC(2, 4) UPR_SELC(4, 4) UPR_SELC(8, 4) UPR_SELC(16, 4)
+#undef UPR_SELC
+        throw CudaError{cudaErrorInvalidValue, "select_moves: unsupported lane schedule"};
     }
     const int G = select_group(k);
     const int64_t groups = 256 / G;
