@@ -323,9 +323,14 @@ def other_configs_leg(args, upr):
     import torch
     peak, _ = _peaks()
     out = {}
-    for name, builder, steps in (("chung_lu_n16384_k8", "plain_tiny", 20), ("rgg_2^22_weighted_k256", "plain_weighted", 3)):
+    legs = (("chung_lu_n16384_k8", "plain_tiny", 20, 0), ("rgg_2^22_weighted_k256", "plain_weighted", 3, 0),
+            ("rgg_2^22_weighted_k256_dense_table", "plain_weighted", 3, 1),
+            ("rgg_2^22_weighted_k256_hashed_table", "plain_weighted", 3, 2))
+    for name, builder, steps, table in legs:
         w = synth.cached(getattr(synth, builder))
-        ctx = upr.create_from_workload(w, device=True)
+        prm = upr.upr_params_default()
+        prm.table = table
+        ctx = upr.create_from_workload(w, params=prm, device=True)
         init = torch.from_numpy(w.part.copy()).cuda()
         part = torch.empty_like(init)
         for _ in range(2):
@@ -347,6 +352,8 @@ def other_configs_leg(args, upr):
         out[name] = {"n": w.n, "m": w.m, "k": w.k, "rounds": w.rounds, "weighted": w.adjw is not None,
                      "ms_per_refine": ms, "edges_per_s": w.rounds * (w.m // 2) / (ms / 1e3),
                      "cut_in": st.cut_in, "cut_out": st.cut_out,
+                     "table": ("hashed rows" if st.sparse_table else "dense n x k")
+                              + (" (chosen by size)" if table == 0 else ""),
                      "gain_table_ms": t_build, "gain_table_gbs": st.gain_table_bytes / (t_build / 1e3) / 1e9,
                      "gain_table_frac": st.gain_table_bytes / (t_build / 1e3) / 1e9 / peak}
         del ctx

@@ -84,6 +84,12 @@ typedef struct {
                                     schedules of the selection and proposal kernels on the
                                     actual inputs and keep the fastest (results never depend
                                     on the schedule). 1                                      */
+    int32_t table;               /* gain-table layout (results never depend on it): 0 auto
+                                    (the dense table), 1 dense, 2 hashed rows of
+                                    min(k, 2 deg) + 1 slots, 3 hashed rows of
+                                    min(k, deg) + 1 slots; hashed rows need k % 4 == 0 and
+                                    k <= 256, else the dense table is used, and a row that
+                                    overflows switches the round to the dense table. 0       */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 
@@ -112,7 +118,7 @@ typedef struct {
                                     batched server jobs; 1 = one graph)                 */
     int32_t select_lanes;        /* lanes per node of the selection kernel (0: scalar)  */
     int32_t propose_lanes;       /* lanes per node of the proposal kernel (0: scalar)   */
-    int32_t pad0;
+    int32_t sparse_table;        /* 1: the rounds ran on the sparse gain table            */
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */

@@ -104,6 +104,13 @@ __device__ __forceinline__ BlockDelta make_block_delta(unsigned long long *smem,
     return K <= kMaxK ? BlockDelta{smem, K, nullptr} : BlockDelta{nullptr, K, C};
 }
 
+// Kernel attributes are per process and device, shared by every host thread:
+// a kernel's dynamic shared-memory limit is raised once to the device's
+// opt-in maximum (a ceiling only: occupancy follows the launch's actual size)
+// and its shared/L1 split set, never changed afterwards, so no thread can
+// lower a limit another thread's launch relies on.
+void kernel_setup(const void *func, int carveout_percent);   // engine.cu; -1 = no carveout preference
+
 inline int device_sm_count() {
     static thread_local int cnt = 0, dev_cached = -1;
     int dev = 0;

@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 #include <vector>
 
 #include "kernels.h"
@@ -24,6 +26,12 @@ bool log_enabled() {
     static int on = -1;
     if (on < 0) { const char *v = getenv("UPR_LOG"); on = (v && *v && *v != '0') ? 1 : 0; }
     return on == 1;
+}
+
+// UPR_LOG: name the failing CUDA call and its error.
+upr_status cuda_failure(const CudaError &e) {
+    if (log_enabled()) fprintf(stderr, "upr: %s failed: %s\n", e.what, cudaGetErrorString(e.e));
+    return UPR_ERR_CUDA;
 }
 
 // Bump allocator over one cudaMalloc; a first pass with base == nullptr sizes it.
@@ -66,6 +74,21 @@ void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F)
 
 std::atomic<long long> upr::g_upr_launches{0};
 
+void upr::kernel_setup(const void *func, int carveout_percent) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    UPR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, func})) return;
+    int optin = 0;
+    UPR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    UPR_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    if (carveout_percent >= 0)
+        UPR_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent));
+    done.insert({dev, func});
+}
+
 struct upr_ctx {
     int device = 0;
     int64_t n = 0, m = 0;
@@ -80,6 +103,10 @@ struct upr_ctx {
     int sel_pending = 0, prop_pending = 0;      // candidates timed in the current round / sub-round
     LaneCfg sel_cands[3], prop_cands[3];
     cudaEvent_t ev_tune[12] = {};
+    // sparse gain table (GraphDev::sp): row offsets, slots, overflow word
+    int64_t sp_slots = 0;             // slots of all rows (0: dense only)
+    bool sparse_on = false;           // the rounds use the sparse table
+    int64_t *sp_off = nullptr; int2 *sp_slot = nullptr; int32_t *sp_over = nullptr;
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -157,6 +184,9 @@ void layout(upr_ctx *c, Arena &A) {
     c->wI = A.take<int32_t>(n);
     c->hub_chunks = A.take<HubChunk>((size_t)std::max<int64_t>(c->n_chunks, 1));
     c->tiles = A.take<TableTile>((size_t)std::max<int64_t>(c->n_tiles, 1));
+    c->sp_off = c->sp_slots ? A.take<int64_t>(n + 1) : nullptr;
+    c->sp_slot = c->sp_slots ? A.take<int2>((size_t)c->sp_slots) : nullptr;
+    c->sp_over = A.take<int32_t>(1);
     c->part0 = A.take<int32_t>(n);
     c->part = A.take<int32_t>(n);
     c->C0 = A.take<int64_t>(k);
@@ -327,7 +357,9 @@ void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands
  * end of the round.  Returns UPR_OK or UPR_ERR_INFEASIBLE (state unchanged).
  * rebalance_only: the round-0 repair.
  */
-upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
+constexpr upr_status kRedoDense = 100;     // internal: run the round again on the dense table
+
+upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
     cudaStream_t s = c->s;
     const GraphDev &G = c->G;
     const int64_t n = c->n;
@@ -345,7 +377,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
     // ---- (a) gain table of the round-start partition (kept from the previous
     // round of this call when it is valid)
-    const bool build = !c->table_valid || tr;
+    const bool build = !c->table_valid || tr || G.sp.on();     // sparse rows: rebuilt every round
     c->table_valid = false;
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
     if (build)
@@ -514,10 +546,25 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         seq_best_seg(G, Iv, dI, n, c->seg_beg, c->Gsum, c->diff, c->diff_excl, c->over0_g, c->best_g, c->best_j, c->cut,
                      c->infeas_g, c->tot, s);
     }
+    if (G.sp.on()) {
+        // a sparse row without room for a new block: nothing of the round is
+        // applied yet; the caller runs it again on the dense table
+        UPR_CUDA(cudaMemcpyAsync(c->hcnt + 41, c->sp_over, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        UPR_CUDA(cudaStreamSynchronize(s));
+        if (c->hcnt[41] != 0) {
+            reset_nodes(c->I_node, dI, n, c->pos, INT32_MAX, s);
+            reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
+            reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
+            UPR_CUDA(cudaMemsetAsync(c->sp_over, 0, sizeof(int32_t), s));
+            UPR_CUDA(cudaStreamSynchronize(s));
+            return kRedoDense;
+        }
+    }
     if (!batch) seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
     else seq_apply_prefix_seg(G, Iv, If, It, dI, n, c->seg_beg, c->best_j, c->part0, c->C0, s);
-    // the table goes from W(P o I) to W(P o I^{j*}) for the next round
-    {
+    // the table goes from W(P o I) to W(P o I^{j*}) for the next round (the
+    // sparse rows are rebuilt instead)
+    if (!G.sp.on()) {
         const Rollback rb{Iv, If, It, dI, c->best, batch ? G.gid : nullptr, c->seg_beg, c->best_j};
         table_rollback(G, rb, n, c->pos, c->W, c->hub_chunks, c->n_chunks, c->scal + 2, s);
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
@@ -556,7 +603,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
     // one graph: an infeasible round applies nothing and is an error; a
     // batch records it per graph (infeas_g) and the round goes on
     const bool infeasible = !batch && hc[CNT_INFEAS] != 0;
-    c->table_valid = !infeasible;
+    c->table_valid = !infeasible && !G.sp.on();
     ri.best_len = infeasible ? 0 : batch ? c->hbest[0] : c->hbest[1];
     ri.best_gain = infeasible ? 0 : batch ? c->hbest[1] : c->hbest[0];
     if (log_enabled())
@@ -607,6 +654,19 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         T->cut_after = *c->hcut - T->best_gain;
     }
     return infeasible ? UPR_ERR_INFEASIBLE : UPR_OK;
+}
+
+// A round; when a sparse row overflows, the context switches to the dense
+// table and the round runs again from the same state.
+upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
+    for (;;) {
+        ri = RoundInfo{};
+        const upr_status rc = run_round_once(c, r, R, rebalance_only, ri, tr);
+        if (rc != kRedoDense) return rc;
+        c->sparse_on = false;
+        c->G.sp.slot = nullptr;
+        c->table_valid = false;
+    }
 }
 
 void free_ctx(upr_ctx *c) {
@@ -751,6 +811,8 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
         const int nd = lane_candidates(c->k, d);
         st.select_lanes = nd ? (c->sel_cfg.G > 0 ? c->sel_cfg.G : d[0].G) : 0;
         st.propose_lanes = nd ? (c->prop_cfg.G > 0 ? c->prop_cfg.G : d[0].G) : 0;
+        st.sparse_table = c->G.sp.on() ? 1 : 0;
+        if (c->G.sp.on()) st.select_lanes = st.propose_lanes = 8;
     }
     if (stats) *stats = st;
     return UPR_OK;
@@ -771,6 +833,7 @@ void upr_params_default(upr_params *p) {
     p->round_offset = 0;
     p->total_rounds = 0;
     p->autotune = 1;
+    p->table = 0;
     p->stream = nullptr;
 }
 
@@ -792,7 +855,8 @@ const char *upr_status_str(upr_status s) {
 static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
-           p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1);
+           p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
+           p.table >= 0 && p.table <= 3;
 }
 
 }  // extern "C"
@@ -896,6 +960,26 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
             tiles.push_back(t);
         }
     }
+    // sparse rows (on request): a power of two >= min(k, 2 deg(v)) + 1 slots per
+    // row (mode 3: min(k, deg(v)) + 1)
+    std::vector<int64_t> sp_off_h;
+    {
+        const int mode = prm.table;
+        int64_t total = 0;
+        if (k % 4 == 0 && k <= kSparseRowMax / 2 && mode >= 2) {
+            sp_off_h.assign(n + 1, 0);
+            for (int64_t v = 0; v < n; v++) {
+                const int64_t d = xadj_h[v + 1] - xadj_h[v];
+                const int64_t want = std::min<int64_t>(k, mode == 3 ? d : 2 * d) + 1;
+                int64_t cap = 1;
+                while (cap < want) cap <<= 1;
+                sp_off_h[v] = total;
+                total += cap;
+            }
+            sp_off_h[n] = total;
+        }
+        c->sp_slots = total;
+    }
     c->m = m; c->k = k;
     c->n = n;                       // layout needs the sizes
     c->n_chunks = (int64_t)chunks.size();
@@ -957,8 +1041,13 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     if (!tiles.empty())
         UPR_CUDA(cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(TableTile) * tiles.size(), cudaMemcpyHostToDevice, s));
     const int32_t kmask = ng == 1 ? -1 : ((k & (k - 1)) == 0 ? k - 1 : 0);
+    c->sparse_on = c->sp_slots > 0;
+    if (c->sparse_on)
+        UPR_CUDA(cudaMemcpyAsync(c->sp_off, sp_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    UPR_CUDA(cudaMemsetAsync(c->sp_over, 0, sizeof(int32_t), s));
     c->G = GraphDev{n,      m,        k,       ng,   kmask, c->xadj, c->adj, any_adjw ? c->adjw : nullptr,
-                    any_vwgt ? c->vwgt : nullptr, c->wI, c->Lb, c->gid};
+                    any_vwgt ? c->vwgt : nullptr, c->wI, c->Lb, c->gid,
+                    SparseRows{c->sp_off, c->sparse_on ? c->sp_slot : nullptr, c->sp_over}};
     if (ng > 1) {
         // node -> graph, and graph-local neighbour ids made global
         UPR_CUDA(cudaMemcpyAsync(c->noff_d, c->noff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
@@ -998,9 +1087,9 @@ template <typename F>
 upr_status guarded(upr_ctx *c, F f) {
     try {
         return f();
-    } catch (const CudaError &) {
+    } catch (const CudaError &e) {
         c->n = -1;
-        return UPR_ERR_CUDA;
+        return cuda_failure(e);
     } catch (const std::bad_alloc &) {
         c->n = -1;
         return UPR_ERR_OOM;
@@ -1052,8 +1141,8 @@ upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block
         read_i64(c, c->cut, 1, tmp);
         *cut = tmp[0];
         if (block_weights_out) read_i64(c, c->C0, c->k, block_weights_out);
-    } catch (const CudaError &) {
-        return UPR_ERR_CUDA;
+    } catch (const CudaError &e) {
+        return cuda_failure(e);
     }
     return UPR_OK;
 }
@@ -1063,8 +1152,8 @@ upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, 
     if (!c || c->n < 0 || c->ng != 1 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
     try {
         return refine_impl(c, part, rounds, stats, nullptr, nullptr, nullptr);
-    } catch (const CudaError &) {
-        return UPR_ERR_CUDA;
+    } catch (const CudaError &e) {
+        return cuda_failure(e);
     }
 }
 
@@ -1096,8 +1185,8 @@ upr_status upr_batch_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t 
             rc = UPR_OK;
         }
         return rc;
-    } catch (const CudaError &) {
-        return UPR_ERR_CUDA;
+    } catch (const CudaError &e) {
+        return cuda_failure(e);
     }
 }
 
@@ -1108,8 +1197,8 @@ upr_status upr_batch_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t 
         if (st != UPR_OK) return st;
         read_i64(c, c->cut, c->ng, cut);
         if (block_weights_out) read_i64(c, c->C0, c->G.K(), block_weights_out);
-    } catch (const CudaError &) {
-        return UPR_ERR_CUDA;
+    } catch (const CudaError &e) {
+        return cuda_failure(e);
     }
     return UPR_OK;
 }
@@ -1129,6 +1218,7 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
         if (rc != UPR_OK) return rc;
         gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, nullptr, c->s);
+        sparse_to_dense(c->G, c->W, c->s);
         if (W) UPR_CUDA(cudaMemcpyAsync(W, c->W, sizeof(int32_t) * c->n * c->k, cudaMemcpyDeviceToHost, c->s));
         if (wI && c->n > 0) {
             std::vector<int32_t> w(c->n);
@@ -1137,8 +1227,8 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
             for (int64_t v = 0; v < c->n; v++) wI[v] = w[v];
         }
         UPR_CUDA(cudaStreamSynchronize(c->s));
-    } catch (const CudaError &) {
-        return UPR_ERR_CUDA;
+    } catch (const CudaError &e) {
+        return cuda_failure(e);
     }
     return UPR_OK;
 }
@@ -1160,8 +1250,8 @@ upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int3
         rc = run_round(c, r, R, rebalance_only != 0, ri, &ts);
         if (rc == UPR_OK) copy_out(part, c->part0, sizeof(int32_t) * c->n, c->s);
         UPR_CUDA(cudaStreamSynchronize(c->s));
-    } catch (const CudaError &) {
-        rc = UPR_ERR_CUDA;
+    } catch (const CudaError &e) {
+        rc = cuda_failure(e);
     }
     if (avail_d) cudaFree(avail_d);
     if (slot_d) cudaFree(slot_d);
@@ -1177,6 +1267,7 @@ size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k, int32_t ng) {
     c.n = n; c.m = m; c.k = k; c.ng = ng;
     c.n_chunks = m / 4096 + 1;
     c.n_tiles = n + 1;
+    c.sp_slots = 0;                                     // served contexts use the dense table
     Arena A;
     layout(&c, A);
     return A.off + ((size_t)1 << 20);

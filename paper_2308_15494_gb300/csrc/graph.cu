@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
                                                         const int32_t *__restrict__ adjw,
                                                         const int32_t *__restrict__ part, int32_t k, int32_t kmask,
                                                         int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
-                                                        int64_t m) {
+                                                        int64_t m, SparseRows sp) {
     if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
     extern __shared__ int4 s_raw[];
     const TableTile t = tiles[blockIdx.x];
@@ -269,6 +269,33 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         }
     }
     __syncthreads();
+    if (sp.on()) {
+        // sparse table: a warp per row fills the row's slots in its own shared
+        // buffer (each non-zero column is claimed once, by the lane that holds
+        // it), then stores them with coalesced 8-byte stores
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        int2 *buf = reinterpret_cast<int2 *>(rows + nn * k) + warp * kSparseRowMax;
+        for (int r = warp; r < nn; r += (int)(blockDim.x >> 5)) {
+            const int64_t v = t.v0 + r;
+            const int64_t o = sp.off[v];
+            const uint32_t cap = (uint32_t)(sp.off[v + 1] - o);
+            for (uint32_t i = lane; i < cap; i += 32) buf[i] = make_int2(kEmpty, 0);
+            __syncwarp();
+            for (int c = lane; c < k; c += 32) {
+                const int w = rows[r * k + c];
+                if (!w) continue;
+                uint32_t h = sp_home(c, cap);
+                for (uint32_t i = 0; i < cap; i++) {
+                    if (atomicCAS(&buf[h].x, kEmpty, c) == kEmpty) { buf[h].y = w; break; }
+                    h = (h + 1) & (cap - 1);
+                }
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < cap; i += 32) sp.slot[o + i] = buf[i];
+            __syncwarp();
+        }
+        return;
+    }
     int4 *dst = reinterpret_cast<int4 *>(W + (int64_t)t.v0 * k);
     for (int i = threadIdx.x; i < words4; i += blockDim.x) __stcs(dst + i, reinterpret_cast<const int4 *>(rows)[i]);
 }
@@ -279,7 +306,8 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
                                                           const int32_t *__restrict__ adjw,
                                                           const int32_t *__restrict__ part, int32_t k,
                                                           int32_t kmask, int32_t *__restrict__ W,
-                                                          const int64_t *__restrict__ deg_sum, int64_t m) {
+                                                          const int64_t *__restrict__ deg_sum, int64_t m,
+                                                          SparseRows sp) {
     if (deg_sum && *deg_sum * 4 < m) return;
     extern __shared__ int s_row[];
     const HubChunk ch = chunks[blockIdx.x];
@@ -288,6 +316,11 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
     for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x)
         atomicAdd(&s_row[blk_local(part[adj[e]], k, kmask)], adjw ? adjw[e] : 1);
     __syncthreads();
+    if (sp.on()) {
+        for (int b = threadIdx.x; b < k; b += blockDim.x)
+            if (s_row[b]) sp_add(sp, ch.v, b, s_row[b]);
+        return;
+    }
     int32_t *dst = W + (int64_t)ch.v * k;
     for (int b = threadIdx.x; b < k; b += blockDim.x)
         if (s_row[b]) atomicAdd(&dst[b], s_row[b]);
@@ -299,7 +332,8 @@ __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__
                              const int32_t *__restrict__ adjw, int32_t k, int32_t kmask, int32_t *__restrict__ W,
                              const int32_t *__restrict__ nodes, const int32_t *__restrict__ from,
                              const int32_t *__restrict__ to, const int32_t *__restrict__ d_count,
-                             const int32_t *__restrict__ d_offset, const int64_t *__restrict__ deg_sum, int64_t m) {
+                             const int32_t *__restrict__ d_offset, const int64_t *__restrict__ deg_sum, int64_t m,
+                             SparseRows sp) {
     if (deg_sum && *deg_sum * 4 >= m) return;     // a rebuild handles this case
     const int lane = threadIdx.x & 31;
     const int64_t cnt = *d_count;
@@ -312,6 +346,11 @@ __global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__
         if (e1 - e0 > kHubDegree) continue;
         for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int32_t w = adjw ? adjw[e] : 1;
+            if (sp.on()) {
+                sp_sub(sp, adj[e], a, w);
+                sp_add(sp, adj[e], b, w);
+                continue;
+            }
             int32_t *row = W + (int64_t)adj[e] * k;
             atomicSub(&row[a], w);
             atomicAdd(&row[b], w);
@@ -326,7 +365,8 @@ __global__ void __launch_bounds__(512) k_table_move_hubs(const HubChunk *__restr
                                                          const int32_t *__restrict__ adj,
                                                          const int32_t *__restrict__ adjw, int32_t k,
                                                          int32_t kmask, int32_t *__restrict__ W, HubMoves hm,
-                                                         const int64_t *__restrict__ deg_sum, int64_t m) {
+                                                         const int64_t *__restrict__ deg_sum, int64_t m,
+                                                         SparseRows sp) {
     if (deg_sum && *deg_sum * 4 >= m) return;
     const HubChunk ch = chunks[blockIdx.x];
     const int32_t v = ch.v;
@@ -345,6 +385,11 @@ __global__ void __launch_bounds__(512) k_table_move_hubs(const HubChunk *__restr
     }
     for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
         const int32_t w = adjw ? adjw[e] : 1;
+        if (sp.on()) {
+            sp_sub(sp, adj[e], a, w);
+            sp_add(sp, adj[e], b, w);
+            continue;
+        }
         int32_t *row = W + (int64_t)adj[e] * k;
         atomicSub(&row[a], w);
         atomicAdd(&row[b], w);
@@ -372,6 +417,22 @@ __global__ void k_shift_adj(const int64_t *__restrict__ xadj, const int64_t *__r
             const int64_t u = (int64_t)adj[e] + off;
             adj[e] = (u < 0 || u >= n) ? -1 : (int32_t)u;
         }
+    }
+}
+
+// Dense rows from the sparse table (inspection only): warp per row.
+__global__ void k_sparse_to_dense(SparseRows sp, int64_t n, int32_t k, int32_t *__restrict__ W) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n;
+         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int32_t *row = W + v * k;
+        for (int c = lane; c < k; c += 32) row[c] = 0;
+        __syncwarp();
+        for (int64_t i = sp.off[v] + lane; i < sp.off[v + 1]; i += 32) {
+            const int2 e = sp.slot[i];
+            if (e.x != kEmpty) row[e.x] = e.y;
+        }
+        __syncwarp();
     }
 }
 
@@ -420,6 +481,13 @@ void pack_batch(const GraphDev &g, const int64_t *noff, int32_t *gid, int32_t *a
     UPR_LAUNCH_CHECK();
 }
 
+void sparse_to_dense(const GraphDev &g, int32_t *W, cudaStream_t s) {
+    if (g.n == 0 || !g.sp.on()) return;
+    const int64_t blocks = std::min<int64_t>(ceil_div(g.n * 32, 256), (int64_t)sm_count() * 16);
+    k_sparse_to_dense<<<(unsigned)blocks, 256, 0, s>>>(g.sp, g.n, g.k, W);
+    UPR_LAUNCH_CHECK();
+}
+
 void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s) {
     UPR_CUDA(cudaMemsetAsync(d_acc, 0, 2 * sizeof(uint64_t), s));
     UPR_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int32_t), s));
@@ -433,25 +501,23 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaSt
     }
 }
 
-size_t table_tile_smem(int32_t k, int32_t nodes) {
-    return sizeof(int64_t) * (size_t)((nodes + 2) & ~1) + sizeof(int) * (size_t)nodes * k;
+size_t table_tile_smem(int32_t k, int32_t nodes, bool sparse) {
+    const size_t rows = sizeof(int64_t) * (size_t)((nodes + 2) & ~1) + sizeof(int) * (size_t)nodes * k;
+    return sparse ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * kSparseRowMax : rows;
 }
 
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
                 const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s) {
     if (g.n == 0) return;
     if (tiles && n_tiles > 0) {
-        const size_t shm = table_tile_smem(g.k, tile_nodes);
+        const size_t shm = table_tile_smem(g.k, tile_nodes, g.sp.on());
         const int local = g.ng == 1 ? 0 : g.kmask ? 1 : 2;
         auto launch = [&](auto kern) {
-            static thread_local size_t attr_set[8] = {};
-            const int slot = (g.adjw ? 4 : 0) + local;
-            if (shm > 48 * 1024 && attr_set[slot] < shm) {
-                UPR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-                attr_set[slot] = shm;
-            }
+            // about four tiles per SM and the rest of the unified memory as L1:
+            // the gathers of part[] need the L1 more than extra CTAs
+            kernel_setup((const void *)kern, 64);
             kern<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum,
-                                                     g.m);
+                                                     g.m, g.sp);
         };
         // 16 entries in flight per thread (8 with weights); the default
         // shared/L1 split: a smaller L1 slows the gathers of part[] down
@@ -474,10 +540,10 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
         const int64_t groups = 256 / G;
         const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count() * 16);
         if (shm > 48 * 1024) {
-            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-            UPR_CUDA(cudaFuncSetAttribute(k_table_dense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            kernel_setup((const void *)k_table_dense<4>, -1);
+            kernel_setup((const void *)k_table_dense<8>, -1);
+            kernel_setup((const void *)k_table_dense<16>, -1);
+            kernel_setup((const void *)k_table_dense<32>, -1);
         }
 #define UPR_TD(GG) k_table_dense<GG><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, g.kmask, W, deg_sum, g.m)
         switch (G) {
@@ -491,7 +557,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
     }
     if (n_chunks > 0) {
         k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k,
-                                                                             g.kmask, W, deg_sum, g.m);
+                                                                             g.kmask, W, deg_sum, g.m, g.sp);
         UPR_LAUNCH_CHECK();
     }
 }
@@ -502,11 +568,11 @@ void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32
     if (max_count <= 0) return;
     int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
     k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, g.kmask, W, nodes, from, to, d_count,
-                                                  d_offset, deg_sum, g.m);
+                                                  d_offset, deg_sum, g.m, g.sp);
     UPR_LAUNCH_CHECK();
     if (n_chunks > 0) {
         k_table_move_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, g.k, g.kmask, W, hm, deg_sum,
-                                                             g.m);
+                                                             g.m, g.sp);
         UPR_LAUNCH_CHECK();
     }
 }

@@ -8,6 +8,23 @@ namespace upr {
 // The graph as the kernels see it (device pointers; adjw / vwgt may be null =
 // unit weights).  wI[v] = omega(I(v)) < 2^31.
 //
+// Sparse form of the gain table for large k: row v holds the blocks adjacent
+// to v in off[v+1] - off[v] slots (a power of two, at least min(k, 2 deg(v))
+// + 1), each (local block or kEmpty, weight), open addressing with linear
+// probing from a hashed home slot.  Keys are only ever inserted (a weight may
+// drop to 0 and its key stays), so concurrent inserts of one block meet at
+// the same first free slot; the table is rebuilt at every round start.  A row
+// without a free slot for a new block sets *overflow, and the round is run
+// again with the dense table.
+constexpr int32_t kEmpty = -1;
+constexpr int kSparseRowMax = 512;   // slots of the largest sparse row (k <= 256: 2k rounded up)
+struct SparseRows {
+    const int64_t *off;   // [n+1] first slot of each row
+    int2 *slot;           // (local block or kEmpty, weight); null: the table is dense
+    int32_t *overflow;
+    __host__ __device__ bool on() const { return slot != nullptr; }
+};
+
 // A context holds one graph or a batch of ng independent graphs packed as one
 // CSR (graph g owns the nodes [noff[g], noff[g+1]) and no edge joins two
 // graphs).  Blocks are numbered globally: graph g owns blocks [g*k, g*k + k),
@@ -26,8 +43,62 @@ struct GraphDev {
     const int32_t *wI;
     const int64_t *Lb;    // [K] L_max of the graph each block belongs to
     const int32_t *gid;   // [n] graph of each node (null for one graph)
+    SparseRows sp;        // sparse gain table when sp.on(), else the dense W[n][k]
     __host__ __device__ int32_t K() const { return ng * k; }
 };
+
+__device__ __forceinline__ uint32_t sp_home(int32_t b, uint32_t cap) {
+    return (((uint32_t)b * 0x9E3779B1u) >> 8) & (cap - 1);
+}
+// omega(v, block column b)
+__device__ __forceinline__ int32_t sp_get(const SparseRows &t, int64_t v, int32_t b) {
+    const int64_t o = t.off[v];
+    const uint32_t cap = (uint32_t)(t.off[v + 1] - o);
+    uint32_t h = sp_home(b, cap);
+    for (uint32_t i = 0; i < cap; i++) {
+        const int2 e = t.slot[o + h];
+        if (e.x == b) return e.y;
+        if (e.x == kEmpty) return 0;
+        h = (h + 1) & (cap - 1);
+    }
+    return 0;
+}
+// omega(v, b) += w, inserting b at the first free slot of its probe sequence
+__device__ __forceinline__ void sp_add(const SparseRows &t, int64_t v, int32_t b, int32_t w) {
+    const int64_t o = t.off[v];
+    const uint32_t cap = (uint32_t)(t.off[v + 1] - o);
+    uint32_t h = sp_home(b, cap);
+    for (uint32_t i = 0; i < cap; i++) {
+        int *key = &t.slot[o + h].x;
+        int kk = *(volatile int *)key;
+        if (kk == kEmpty) {
+            kk = atomicCAS(key, kEmpty, b);
+            if (kk == kEmpty) kk = b;
+        }
+        if (kk == b) {
+            atomicAdd(&t.slot[o + h].y, w);
+            return;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    atomicOr(t.overflow, 1);
+}
+// omega(v, b) -= w for a block b that is in the row
+__device__ __forceinline__ void sp_sub(const SparseRows &t, int64_t v, int32_t b, int32_t w) {
+    const int64_t o = t.off[v];
+    const uint32_t cap = (uint32_t)(t.off[v + 1] - o);
+    uint32_t h = sp_home(b, cap);
+    for (uint32_t i = 0; i < cap; i++) {
+        const int kk = *(volatile int *)&t.slot[o + h].x;
+        if (kk == b) {
+            atomicSub(&t.slot[o + h].y, w);
+            return;
+        }
+        if (kk == kEmpty) break;
+        h = (h + 1) & (cap - 1);
+    }
+    atomicOr(t.overflow, 2);      // cannot happen: the block of a neighbour is always in the row
+}
 
 __device__ __forceinline__ int32_t blk_local(int32_t p, int32_t k, int32_t kmask) {
     return kmask ? (p & kmask) : p % k;
@@ -99,8 +170,8 @@ void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_
 // A tile of the table build: nodes [v0, v1) and the adjacency entries [e0, e1)
 // of its non-hub nodes (a hub, if any, is the tile's last node).
 struct TableTile { int64_t e0, e1; int32_t v0, v1; };
-// Shared memory of one tile of `nodes` rows.
-size_t table_tile_smem(int32_t k, int32_t nodes);
+// Shared memory of one tile of `nodes` rows (plus per-warp row buffers for the sparse table).
+size_t table_tile_smem(int32_t k, int32_t nodes, bool sparse);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
 // With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
@@ -126,6 +197,8 @@ void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32
 // graph's neighbour ids (local to the graph on input) shifted by its first
 // node; an id that leaves [0, n) becomes -1 for the checks to report.
 void pack_batch(const GraphDev &g, const int64_t *noff, int32_t *gid, int32_t *adj, cudaStream_t s);
+// W[v][b] = omega(v, V_b) from the sparse table (inspection only).
+void sparse_to_dense(const GraphDev &g, int32_t *W, cudaStream_t s);
 // Graph checks; writes a bitmask of violations into *d_flags (see engine.cu).
 void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s);
 

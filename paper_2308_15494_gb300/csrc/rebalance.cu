@@ -170,6 +170,51 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
     }
 }
 
+// Proposals over the sparse table: G lanes per node walk the node's slots;
+// the best valid block has the largest omega(v, V_b), ties to the smaller b.
+template <int G>
+__global__ void __launch_bounds__(256) k_propose_sparse(const GraphDev g, const int32_t *__restrict__ list,
+                                                        const int32_t *__restrict__ d_n1,
+                                                        const int32_t *__restrict__ part, RebalState st,
+                                                        int32_t *__restrict__ prop_tgt, int32_t *__restrict__ prop_gain,
+                                                        int32_t *__restrict__ flags) {
+    const int64_t n1 = *d_n1;
+    constexpr int kGroups = 256 / G;
+    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    const SparseRows &sp = g.sp;
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t i = base + gid;
+        const int32_t v = i < n1 ? list[i] : 0;
+        const int32_t ag = i < n1 ? part[v] : 0;
+        const bool src = i < n1 && st.over[ag];
+        const int32_t a = blk_local(g, ag), b0 = ag - a;
+        int32_t bw = 0, bt = -1, own = 0;
+        const int32_t c = src ? (g.vwgt ? g.vwgt[v] : 1) : 1;
+        if (src) {
+            own = sp_get(sp, v, a);
+            for (int64_t q = sp.off[v] + gl; q < sp.off[v + 1]; q += G) {
+                const int2 e = sp.slot[q];
+                if (e.x == kEmpty || e.y <= 0) continue;
+                const int32_t gb = b0 + e.x;
+                if (st.excl[gb] || st.C[gb] + c > st.Lb[gb]) continue;
+                if (bt < 0 || e.y > bw || (e.y == bw && e.x < bt)) { bw = e.y; bt = e.x; }
+            }
+        }
+        int32_t id = bt;
+        group_argmax32<G>(bw, id);
+        if (i < n1 && gl == 0) {
+            int32_t tgt = src && id >= 0 ? b0 + id : -1;
+            int32_t gain = bw - own;
+            if (src && tgt < 0) {
+                const int32_t light = st.light[blk_graph(g, ag)];
+                if (light >= 0 && (int64_t)c <= st.Lb[light] - st.C[light]) { tgt = light; gain = -own; }
+            }
+            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = gain; }
+            flags[i] = tgt >= 0 ? 1 : 0;
+        }
+    }
+}
+
 // list[i] = nodes of the blocks marked in `mark`
 __global__ void k_flag_in_blocks(const int32_t *__restrict__ part, int64_t n, const int8_t *__restrict__ mark,
                                  int32_t *__restrict__ flags) {
@@ -548,6 +593,12 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
     if (n1_max <= 0) return;
     const int k = g.k;
     const bool batch = g.ng > 1;
+    if (g.sp.on()) {
+        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n1_max, 256 / 8), (int64_t)sm_count_reb() * 8);
+        k_propose_sparse<8><<<blocks, 256, 0, s>>>(g, list, d_n1, part, st, prop_tgt, prop_gain, flags);
+        UPR_LAUNCH_CHECK();
+        return;
+    }
     const size_t shm = batch ? 0 : sizeof(int32_t) * (size_t)k + (size_t)k + 16;
     LaneCfg cands[3];
     if (lane_candidates(k, cands) > 0) {

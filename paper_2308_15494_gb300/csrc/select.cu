@@ -74,7 +74,8 @@ __device__ __forceinline__ int64_t penalty(const Penalty &p, int32_t b, int64_t 
 __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__restrict__ W,
                           const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
                           int32_t kmask, int32_t K, int32_t t_num, int32_t t_den, unsigned long long *__restrict__ BW,
-                          int use_shared, int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out) {
+                          int use_shared, int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out,
+                          SparseRows sp) {
     extern __shared__ unsigned long long s_bw[];
     const int bins = K * kSlots;
     if (use_shared) {
@@ -83,7 +84,7 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
     }
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = part[v];
-        const int64_t own = W[v * (int64_t)k + blk_local(a, k, kmask)];
+        const int64_t own = sp.on() ? sp_get(sp, v, blk_local(a, k, kmask)) : W[v * (int64_t)k + blk_local(a, k, kmask)];
         const int64_t c = vwgt ? vwgt[v] : 1;
         const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wI[v];
         const int s = slot_of((uint64_t)own, (uint64_t)c);
@@ -294,6 +295,73 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
     }
 }
 
+// Selection over the sparse table: G lanes per node walk the node's slots
+// (hash order, so ties compare block ids explicitly); penalties as in
+// k_select_vec with the per-block values read from global memory.
+template <int G>
+__global__ void __launch_bounds__(256) k_select_sparse(const GraphDev g, const int32_t *__restrict__ part,
+                                                       Penalty pen, int32_t *__restrict__ cand_tgt,
+                                                       int64_t *__restrict__ cand_s0, int32_t *__restrict__ cand_gain,
+                                                       int32_t *__restrict__ flags) {
+    constexpr int kGroups = 256 / G;
+    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
+    const int64_t n = g.n;
+    const SparseRows &sp = g.sp;
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t v = base + gid;
+        const bool active = v < n;
+        int32_t best = 0, bt = -1, bg = 0, b0 = 0;
+        if (active) {
+            const int32_t ag = part[v];
+            const int32_t a = blk_local(g, ag);
+            b0 = ag - a;
+            const int32_t own = sp_get(sp, v, a);
+            if (own < g.wI[v]) {
+                const int32_t c = g.vwgt ? g.vwgt[v] : 1;
+                for (int64_t i = sp.off[v] + gl; i < sp.off[v + 1]; i += G) {
+                    const int2 e = sp.slot[i];
+                    if (e.x == kEmpty || e.y <= own) continue;      // gain <= 0 (the own block among them)
+                    const int32_t b = e.x, gain = e.y - own;
+                    const int64_t sl = pen.Lb[b0 + b] - pen.C[b0 + b];
+                    const int32_t slack = (int32_t)(sl > 0x7fffffffLL ? 0x7fffffffLL : sl);
+                    int32_t sc = gain;
+                    if (c > slack) {
+                        const int64_t x = (int64_t)c - slack;
+                        int lo;
+                        if (x == 1) {
+                            lo = pen.first[b0 + b];
+                            if (lo < 0) continue;
+                        } else {
+                            const int64_t *row = pen.PW + (int64_t)(b0 + b) * kSlots;
+                            if (row[kSlots - 1] < x) continue;
+                            lo = 0;
+                            int hi = kSlots - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (row[mid] >= x) hi = mid; else lo = mid + 1;
+                            }
+                        }
+                        const int64_t p = (int64_t)(((u128)(uint64_t)c * (uint64_t)pen.F[lo]) >> kQ);
+                        if (p >= gain) continue;
+                        sc = gain - (int32_t)p;
+                    }
+                    if (bt < 0 || sc > best || (sc == best && b < bt)) { best = sc; bt = b; bg = gain; }
+                }
+            }
+        }
+        int32_t sbest = best, id = bt;
+        group_argmax32<G>(sbest, id);
+        const int32_t gsel = group_sum<G>((id >= 0 && bt == id) ? bg : 0);
+        if (active && gl == 0) {
+            const bool cand = id >= 0 && sbest > 0;
+            cand_tgt[v] = cand ? b0 + id : -1;
+            cand_s0[v] = cand ? sbest : 0;
+            cand_gain[v] = cand ? gsel : 0;
+            flags[v] = cand ? 1 : 0;
+        }
+    }
+}
+
 __global__ void k_cand_keys(const int32_t *__restrict__ cand_idx, const int32_t *__restrict__ d_count,
                             const int32_t *__restrict__ cand_tgt, const int64_t *__restrict__ cand_s0, int gbits,
                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
@@ -400,12 +468,12 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
         const size_t shm = sizeof(unsigned long long) * (size_t)K * kSlots;
         const int use_shared = shm <= 200 * 1024;
         if (use_shared && shm > 48 * 1024)
-            UPR_CUDA(cudaFuncSetAttribute(k_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            kernel_setup((const void *)k_buckets, -1);
         int64_t blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * (shm > 48 * 1024 ? 1 : 4));
         if (!use_shared) blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * 8);
         k_buckets<<<(unsigned)blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, g.kmask, K,
                                                                       t_num, t_den, (unsigned long long *)BW,
-                                                                      use_shared, avail_out, slot_out);
+                                                                      use_shared, avail_out, slot_out, g.sp);
         UPR_LAUNCH_CHECK();
     }
     k_bucket_prefix<<<(unsigned)ceil_div(K, 128), 128, 0, s>>>(BW, PW, first, K);
@@ -457,6 +525,12 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
     if (g.n == 0) return;
     const int k = g.k;
     const bool batch = g.ng > 1;
+    if (g.sp.on()) {
+        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(g.n, 256 / 8), (int64_t)sm_count_sel() * 8);
+        k_select_sparse<8><<<blocks, 256, 0, s>>>(g, part, pen, cand_tgt, cand_s0, cand_gain, flags);
+        UPR_LAUNCH_CHECK();
+        return;
+    }
     LaneCfg cands[3];
     if (lane_candidates(k, cands) > 0) {
         if (cfg.G <= 0) cfg = cands[0];

@@ -261,3 +261,46 @@ def test_server_results_equal_alone_and_in_mix(upr):
             assert np.array_equal(p2, p0)
     finally:
         srv.close()
+
+
+def _params(upr, table):
+    p = upr.upr_params_default()
+    p.table = table
+    return p
+
+
+@pytest.mark.parametrize("table", [2, 3])
+@pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "star_hub", "chung_lu_1k",
+                                  "rmat_s12_k64", "heavy_weights"])
+def test_sparse_table_same_results(upr, name, table):
+    """The sparse gain table (2: rows of min(k, 2 deg) + 1 slots; 3: rows of
+    min(k, deg) + 1 slots, which overflow in busy rounds and send the round
+    back to the dense table) changes nothing: table, partition and cut equal
+    the oracle's."""
+    w = CASES[name]()
+    ctx = upr.create_from_workload(w, params=_params(upr, table))
+    if w.k % 4 == 0:
+        W, _ = upr.upr_debug_gain_table(ctx, w.part)
+        Wo, _ = oracle.gain_table(w, w.part)
+        assert np.array_equal(W, Wo)
+    p = w.part.copy()
+    st = upr.upr_refine(ctx, p, w.rounds)
+    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=w.rounds)
+    assert np.array_equal(p, p0)
+    assert st.cut_out == c0
+
+
+def test_sparse_table_by_request_only(upr):
+    w = synth.random_small(21, 3000, 6, 256, max_vw=20)
+    ctx = upr.create_from_workload(w)
+    p = w.part.copy()
+    st = upr.upr_refine(ctx, p, 3)
+    assert st.sparse_table == 0
+    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=3)
+    assert np.array_equal(p, p0) and st.cut_out == c0
+    ctx = upr.create_from_workload(w, params=_params(upr, 2))
+    p = w.part.copy()
+    st = upr.upr_refine(ctx, p, 3)
+    assert st.sparse_table == 1
+    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=3)
+    assert np.array_equal(p, p0) and st.cut_out == c0
