@@ -14,7 +14,7 @@
  *   (d) rebalancing by gain-per-weight priority (Sec. 6),
  *   (c) interleaving of the moves with the rebalancing moves, exact gain
  *       recalculation and application of the best balanced prefix (Sec. 4.4,
- *       Alg. 1 line 19), so the cut never increases,
+ *       Alg. 1), so the cut never increases,
  *   (e) exact cut and block weights (Sec. 2).
  * Every quantity is an integer and every tie is broken by node or block id,
  * so results are bit-for-bit reproducible and equal those of the sequential
@@ -85,11 +85,15 @@ typedef struct {
                                     actual inputs and keep the fastest (results never depend
                                     on the schedule). 1                                      */
     int32_t table;               /* gain-table layout (results never depend on it): 0 auto
-                                    (the dense table), 1 dense, 2 hashed rows of
+                                    (hashed rows of min(k, 2 deg) + 1 slots when k >= 128
+                                    and they take at most half the bytes of the dense
+                                    table, else dense), 1 dense, 2 hashed rows of
                                     min(k, 2 deg) + 1 slots, 3 hashed rows of
-                                    min(k, deg) + 1 slots; hashed rows need k % 4 == 0 and
-                                    k <= 256, else the dense table is used, and a row that
-                                    overflows switches the round to the dense table. 0       */
+                                    min(k, deg) + 1 slots.  Hashed rows need k % 4 == 0 and
+                                    k <= 256 (else the dense table is used); they carry no
+                                    dense table: a round whose rows run out of slots runs
+                                    again on rows built afresh, and if those run out too,
+                                    on a dense table allocated then. 0                       */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 

@@ -16,18 +16,18 @@
  *   0. block weights c(V_b) and cut (Sec. 2)
  *   1. gain table omega(v, V_b) and omega(I(v)) (Sec. 2, Sec. 6.1)
  *   2. rebalancing-availability, slots, bucket weights, penalty factors
- *      (Alg. 1 lines 1-2, Sec. 4.3, Sec. 4.4 for the tau schedule)
- *   3. per boundary node, the best target by gain minus penalty (Alg. 1
- *      line 8, Sec. 4.3)
+ *      (Alg. 1, Sec. 4.3, Sec. 4.4 for the tau schedule)
+ *   3. per boundary node, the best target by gain minus penalty (Alg. 1,
+ *      Sec. 4.3)
  *   4. penalties including the inflow of better-ranked candidates into the
- *      same block, keep gain - penalty > 0, global move order M (Alg. 1
- *      lines 13-15, Sec. 4.4 first paragraph, Lemma 1's sequence)
- *   5. apply M (Alg. 1 line 15)
- *   6. rebalancing into R_1..R_k (Alg. 1 lines 17-18, Sec. 6)
+ *      same block, keep gain - penalty > 0, global move order M (Alg. 1,
+ *      Sec. 4.4 first paragraph, Lemma 1's sequence)
+ *   5. apply M (Alg. 1)
+ *   6. rebalancing into R_1..R_k (Alg. 1, Sec. 6)
  *   7. interleaving of M and R (Sec. 4.4)
  *   8. merging of a node's two moves into one (Sec. 4.4 footnote)
  *   9. exact gains of the interleaved sequence (Sec. 4.4; gains per Sec. 2)
- *  10. best balanced prefix and its application (Alg. 1 line 19, Sec. 4.1)
+ *  10. best balanced prefix and its application (Alg. 1, Sec. 4.1)
  * Parity status of each step is listed in the oracle's package docstring.
  */
 #include <stdint.h>
@@ -257,7 +257,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
     std::vector<int64_t> Cp(C);
 
     if (!rebalance_only) {
-        /* ---- step 2: V_r, slots, buckets B_{i,j} (Alg. 1 lines 1-2, Sec. 4.3) ---- */
+        /* ---- step 2: V_r, slots, buckets B_{i,j} (Alg. 1, Sec. 4.3) ---- */
         std::vector<int64_t> BW((size_t)k * NSLOT, 0);
         for (int64_t v = 0; v < n; v++) {
             int64_t own = T.at(v, part[v]);
@@ -273,7 +273,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
         if (tr && tr->bucket) memcpy(tr->bucket, BW.data(), sizeof(int64_t) * BW.size());
         if (tr && tr->factor) memcpy(tr->factor, F, sizeof(F));
 
-        /* ---- step 3: best target of every boundary node (Alg. 1 line 8) ---- */
+        /* ---- step 3: best target of every boundary node (Alg. 1, Sec. 4.3) ---- */
         std::vector<int32_t> tgt(n, -1);
         std::vector<int64_t> s0(n, 0), gain(n, 0);
         for (int64_t v = 0; v < n; v++) {
@@ -327,7 +327,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
         }
         out->n_moves = (int64_t)M.size();
 
-        /* ---- step 5: apply M (P' = P o M, Alg. 1 line 15) ---- */
+        /* ---- step 5: apply M (P' = P o M, Alg. 1) ---- */
         for (const Move &mv : M) {
             Pp[mv.v] = mv.to;
             Cp[mv.from] -= g.c(mv.v);
@@ -336,7 +336,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
         }
     }
 
-    /* ---- step 6: rebalancing (Alg. 1 lines 17-18, Sec. 6) ---- */
+    /* ---- step 6: rebalancing (Alg. 1, Sec. 6) ---- */
     std::vector<Move> Rseq;
     std::vector<int32_t> Rsub;
     std::vector<char> over1(k, 0), forb(k, 0);
@@ -469,7 +469,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
         gI[i] = gsum;
     }
 
-    /* ---- step 10: best balanced prefix (Alg. 1 line 19, Sec. 4.1) ---- */
+    /* ---- step 10: best balanced prefix (Alg. 1, Sec. 4.1) ---- */
     std::vector<int64_t> Xw(C);
     int64_t overloaded = 0;
     for (int32_t b = 0; b < k; b++) overloaded += Xw[b] > Lmax;

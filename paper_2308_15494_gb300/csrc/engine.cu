@@ -31,7 +31,7 @@ bool log_enabled() {
 // UPR_LOG: name the failing CUDA call and its error.
 upr_status cuda_failure(const CudaError &e) {
     if (log_enabled()) fprintf(stderr, "upr: %s failed: %s\n", e.what, cudaGetErrorString(e.e));
-    return UPR_ERR_CUDA;
+    return e.e == cudaErrorMemoryAllocation ? UPR_ERR_OOM : UPR_ERR_CUDA;
 }
 
 // Bump allocator over one cudaMalloc; a first pass with base == nullptr sizes it.
@@ -107,6 +107,10 @@ struct upr_ctx {
     int64_t sp_slots = 0;             // slots of all rows (0: dense only)
     bool sparse_on = false;           // the rounds use the sparse table
     int64_t *sp_off = nullptr; int2 *sp_slot = nullptr; int32_t *sp_over = nullptr;
+    // with sparse rows there is no dense table in the arena: one is allocated
+    // here only if a round falls back to it (or for the debug entry point)
+    int32_t *W_own = nullptr; size_t W_own_bytes = 0;
+    int32_t sp_buf_cap = 1;
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -192,7 +196,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->C0 = A.take<int64_t>(k);
     c->C = A.take<int64_t>(k);
     c->cut = A.take<int64_t>(std::max<size_t>(ng, 4));
-    c->W = A.take<int32_t>(n * kr);
+    c->W = c->sp_slots ? nullptr : A.take<int32_t>(n * kr);
     c->BW = A.take<int64_t>(k * kSlots);
     c->PW = A.take<int64_t>(k * kSlots);
     c->F = A.take<int64_t>(kSlots);
@@ -358,6 +362,7 @@ void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands
  * rebalance_only: the round-0 repair.
  */
 constexpr upr_status kRedoDense = 100;     // internal: run the round again on the dense table
+constexpr upr_status kRedoFresh = 101;     // internal: run the round again on freshly built sparse rows
 
 upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
     cudaStream_t s = c->s;
@@ -377,7 +382,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
     // ---- (a) gain table of the round-start partition (kept from the previous
     // round of this call when it is valid)
-    const bool build = !c->table_valid || tr || G.sp.on();     // sparse rows: rebuilt every round
+    const bool build = !c->table_valid || tr;
     c->table_valid = false;
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
     if (build)
@@ -548,7 +553,9 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     }
     if (G.sp.on()) {
         // a sparse row without room for a new block: nothing of the round is
-        // applied yet; the caller runs it again on the dense table
+        // applied yet; the caller runs it again on rows built afresh (which
+        // drop the blocks whose weight went back to zero) or, if these were
+        // fresh already, on the dense table
         UPR_CUDA(cudaMemcpyAsync(c->hcnt + 41, c->sp_over, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
         if (c->hcnt[41] != 0) {
@@ -557,14 +564,13 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
             reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
             UPR_CUDA(cudaMemsetAsync(c->sp_over, 0, sizeof(int32_t), s));
             UPR_CUDA(cudaStreamSynchronize(s));
-            return kRedoDense;
+            return build ? kRedoDense : kRedoFresh;
         }
     }
     if (!batch) seq_apply_prefix(G, c->I_node, c->I_from, c->I_to, n, c->best, c->part0, c->C0, c->cut, s);
     else seq_apply_prefix_seg(G, Iv, If, It, dI, n, c->seg_beg, c->best_j, c->part0, c->C0, s);
-    // the table goes from W(P o I) to W(P o I^{j*}) for the next round (the
-    // sparse rows are rebuilt instead)
-    if (!G.sp.on()) {
+    // the table goes from W(P o I) to W(P o I^{j*}) for the next round
+    {
         const Rollback rb{Iv, If, It, dI, c->best, batch ? G.gid : nullptr, c->seg_beg, c->best_j};
         table_rollback(G, rb, n, c->pos, c->W, c->hub_chunks, c->n_chunks, c->scal + 2, s);
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
@@ -603,7 +609,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     // one graph: an infeasible round applies nothing and is an error; a
     // batch records it per graph (infeas_g) and the round goes on
     const bool infeasible = !batch && hc[CNT_INFEAS] != 0;
-    c->table_valid = !infeasible && !G.sp.on();
+    c->table_valid = !infeasible;
     ri.best_len = infeasible ? 0 : batch ? c->hbest[0] : c->hbest[1];
     ri.best_gain = infeasible ? 0 : batch ? c->hbest[1] : c->hbest[0];
     if (log_enabled())
@@ -656,13 +662,35 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     return infeasible ? UPR_ERR_INFEASIBLE : UPR_OK;
 }
 
-// A round; when a sparse row overflows, the context switches to the dense
-// table and the round runs again from the same state.
+// The dense table of a context bound with sparse rows (allocated on first use).
+void ensure_dense(upr_ctx *c) {
+    if (c->W) return;
+    const size_t bytes = sizeof(int32_t) * (size_t)std::max<int64_t>(c->n, 1) * (size_t)c->k;
+    if (c->W_own_bytes < bytes) {
+        if (c->W_own) cudaFree(c->W_own);
+        c->W_own = nullptr;
+        c->W_own_bytes = 0;
+        if (cudaMalloc(&c->W_own, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            throw CudaError{cudaErrorMemoryAllocation, "dense gain table"};
+        }
+        c->W_own_bytes = bytes;
+    }
+    c->W = c->W_own;
+}
+
+// A round; when a sparse row overflows, the round runs again from the same
+// state on rows built afresh, and when fresh rows overflow, on the dense table.
 upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
     for (;;) {
         ri = RoundInfo{};
         const upr_status rc = run_round_once(c, r, R, rebalance_only, ri, tr);
+        if (rc == kRedoFresh) {
+            c->table_valid = false;
+            continue;
+        }
         if (rc != kRedoDense) return rc;
+        ensure_dense(c);
         c->sparse_on = false;
         c->G.sp.slot = nullptr;
         c->table_valid = false;
@@ -672,6 +700,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
 void free_ctx(upr_ctx *c) {
     if (!c) return;
     if (c->mem) cudaFree(c->mem);
+    if (c->W_own) cudaFree(c->W_own);
     if (c->h) cudaFreeHost(c->h);
     if (c->h8) cudaFreeHost(c->h8);
     for (auto &e : c->ev) if (e) cudaEventDestroy(e);
@@ -960,13 +989,14 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
             tiles.push_back(t);
         }
     }
-    // sparse rows (on request): a power of two >= min(k, 2 deg(v)) + 1 slots per
-    // row (mode 3: min(k, deg(v)) + 1)
+    // sparse rows: a power of two >= min(k, 2 deg(v)) + 1 slots per row (mode 3:
+    // min(k, deg(v)) + 1); chosen by size (mode 0) when k >= 128 and the rows
+    // take at most half the bytes of the dense table
     std::vector<int64_t> sp_off_h;
     {
         const int mode = prm.table;
-        int64_t total = 0;
-        if (k % 4 == 0 && k <= kSparseRowMax / 2 && mode >= 2) {
+        int64_t total = 0, buf_cap = 1;
+        if (k % 4 == 0 && k <= kSparseRowMax / 2 && (mode >= 2 || (mode == 0 && k >= 128))) {
             sp_off_h.assign(n + 1, 0);
             for (int64_t v = 0; v < n; v++) {
                 const int64_t d = xadj_h[v + 1] - xadj_h[v];
@@ -975,10 +1005,14 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
                 while (cap < want) cap <<= 1;
                 sp_off_h[v] = total;
                 total += cap;
+                if (d <= kHubDegree) buf_cap = std::max<int64_t>(buf_cap, cap);
             }
             sp_off_h[n] = total;
+            if (mode == 0 && total * (int64_t)sizeof(int2) * 2 > n * (int64_t)k * (int64_t)sizeof(int32_t))
+                total = 0, buf_cap = 1, sp_off_h.clear();
         }
         c->sp_slots = total;
+        c->sp_buf_cap = (int32_t)buf_cap;
     }
     c->m = m; c->k = k;
     c->n = n;                       // layout needs the sizes
@@ -986,6 +1020,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->n_tiles = (int64_t)tiles.size();
     c->tile_nodes = tile_nodes;
     Arena A;
+    if (c->W_own) { cudaFree(c->W_own); c->W_own = nullptr; c->W_own_bytes = 0; }
     layout(c, A);
     if (!c->mem || c->mem_bytes < A.off) {
         if (c->mem) { cudaFree(c->mem); c->mem = nullptr; c->mem_bytes = 0; }
@@ -1047,7 +1082,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     UPR_CUDA(cudaMemsetAsync(c->sp_over, 0, sizeof(int32_t), s));
     c->G = GraphDev{n,      m,        k,       ng,   kmask, c->xadj, c->adj, any_adjw ? c->adjw : nullptr,
                     any_vwgt ? c->vwgt : nullptr, c->wI, c->Lb, c->gid,
-                    SparseRows{c->sp_off, c->sparse_on ? c->sp_slot : nullptr, c->sp_over}};
+                    SparseRows{c->sp_off, c->sparse_on ? c->sp_slot : nullptr, c->sp_over, c->sp_buf_cap}};
     if (ng > 1) {
         // node -> graph, and graph-local neighbour ids made global
         UPR_CUDA(cudaMemcpyAsync(c->noff_d, c->noff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
@@ -1216,6 +1251,7 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
     try {
         upr_status rc = load_part(c, part);
         if (rc != UPR_OK) return rc;
+        ensure_dense(c);
         gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, nullptr, c->s);
         sparse_to_dense(c->G, c->W, c->s);
@@ -1267,7 +1303,7 @@ size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k, int32_t ng) {
     c.n = n; c.m = m; c.k = k; c.ng = ng;
     c.n_chunks = m / 4096 + 1;
     c.n_tiles = n + 1;
-    c.sp_slots = 0;                                     // served contexts use the dense table
+    c.sp_slots = 0;     // the dense layout bounds the sparse one (rows chosen by size take half as many bytes)
     Arena A;
     layout(&c, A);
     return A.off + ((size_t)1 << 20);

@@ -274,11 +274,16 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         // buffer (each non-zero column is claimed once, by the lane that holds
         // it), then stores them with coalesced 8-byte stores
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        int2 *buf = reinterpret_cast<int2 *>(rows + nn * k) + warp * kSparseRowMax;
+        int2 *buf = reinterpret_cast<int2 *>(rows + nn * k) + warp * sp.buf_cap;
         for (int r = warp; r < nn; r += (int)(blockDim.x >> 5)) {
             const int64_t v = t.v0 + r;
             const int64_t o = sp.off[v];
             const uint32_t cap = (uint32_t)(sp.off[v + 1] - o);
+            if (cap > (uint32_t)sp.buf_cap) {
+                // a hub: its row is empty here, the chunk pass fills it
+                for (uint32_t i = lane; i < cap; i += 32) sp.slot[o + i] = make_int2(kEmpty, 0);
+                continue;
+            }
             for (uint32_t i = lane; i < cap; i += 32) buf[i] = make_int2(kEmpty, 0);
             __syncwarp();
             for (int c = lane; c < k; c += 32) {
@@ -501,16 +506,16 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaSt
     }
 }
 
-size_t table_tile_smem(int32_t k, int32_t nodes, bool sparse) {
+size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap) {
     const size_t rows = sizeof(int64_t) * (size_t)((nodes + 2) & ~1) + sizeof(int) * (size_t)nodes * k;
-    return sparse ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * kSparseRowMax : rows;
+    return sparse_buf_cap > 0 ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * (size_t)sparse_buf_cap : rows;
 }
 
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
                 const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s) {
     if (g.n == 0) return;
     if (tiles && n_tiles > 0) {
-        const size_t shm = table_tile_smem(g.k, tile_nodes, g.sp.on());
+        const size_t shm = table_tile_smem(g.k, tile_nodes, g.sp.on() ? g.sp.buf_cap : 0);
         const int local = g.ng == 1 ? 0 : g.kmask ? 1 : 2;
         auto launch = [&](auto kern) {
             // about four tiles per SM and the rest of the unified memory as L1:

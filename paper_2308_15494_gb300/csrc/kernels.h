@@ -22,6 +22,7 @@ struct SparseRows {
     const int64_t *off;   // [n+1] first slot of each row
     int2 *slot;           // (local block or kEmpty, weight); null: the table is dense
     int32_t *overflow;
+    int32_t buf_cap;      // largest row of a node of degree <= kHubDegree (the build's staging buffer)
     __host__ __device__ bool on() const { return slot != nullptr; }
 };
 
@@ -171,7 +172,7 @@ void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_
 // of its non-hub nodes (a hub, if any, is the tile's last node).
 struct TableTile { int64_t e0, e1; int32_t v0, v1; };
 // Shared memory of one tile of `nodes` rows (plus per-warp row buffers for the sparse table).
-size_t table_tile_smem(int32_t k, int32_t nodes, bool sparse);
+size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
 // With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).

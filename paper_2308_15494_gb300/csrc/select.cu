@@ -1,6 +1,6 @@
-// Step (b): rebalancing availability, slots and bucket weights (Alg. 1 lines
-// 1-2, Sec. 4.3), each boundary node's best move by gain minus penalty
-// (Alg. 1 line 8), penalties with the inflow of better-ranked candidates,
+// Step (b): rebalancing availability, slots and bucket weights (Alg. 1,
+// Sec. 4.3), each boundary node's best move by gain minus penalty
+// (Alg. 1), penalties with the inflow of better-ranked candidates,
 // the global move order M (Sec. 4.4), and the application of M.
 #include "kernels.h"
 

@@ -1,6 +1,6 @@
 // Step (c): the interleaved move sequence I of M and R_1..R_k (Sec. 4.4),
 // merging of a node's two moves (Sec. 4.4 footnote), exact gains of I, the
-// balanced prefixes and the best one (Alg. 1 line 19, Sec. 4.1).
+// balanced prefixes and the best one (Alg. 1, Sec. 4.1).
 //
 // Interleaving in parallel.  Walking M, after each move into block b the
 // sequential rule emits the shortest further prefix of R_b that brings b to
@@ -623,9 +623,10 @@ __global__ void k_rollback_degsum(Rollback rb, const int64_t *__restrict__ xadj,
 }
 
 // warp per move of I; hubs are left to k_table_rollback_hubs
+// (sparse rows: both blocks are keys of the row already, so nothing is inserted)
 __global__ void k_table_rollback(Rollback rb, const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                                  const int32_t *__restrict__ adjw, int32_t k, int32_t kmask, int32_t *__restrict__ W,
-                                 const int64_t *__restrict__ deg_sum, int64_t m) {
+                                 const int64_t *__restrict__ deg_sum, int64_t m, SparseRows sp) {
     if (*deg_sum * 4 >= m) return;          // the rebuild handles this case
     const int lane = threadIdx.x & 31;
     const int64_t nI = *rb.d_nI;
@@ -638,6 +639,11 @@ __global__ void k_table_rollback(Rollback rb, const int64_t *__restrict__ xadj, 
         const int32_t a = blk_local(rb.I_to[i], k, kmask), b = blk_local(rb.I_from[i], k, kmask);
         for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int32_t w = adjw ? adjw[e] : 1;
+            if (sp.on()) {
+                sp_sub(sp, adj[e], a, w);
+                sp_add(sp, adj[e], b, w);
+                continue;
+            }
             int32_t *row = W + (int64_t)adj[e] * k;
             atomicSub(&row[a], w);
             atomicAdd(&row[b], w);
@@ -650,7 +656,8 @@ __global__ void __launch_bounds__(512) k_table_rollback_hubs(Rollback rb, const 
                                                              const int32_t *__restrict__ adj,
                                                              const int32_t *__restrict__ adjw, int32_t k,
                                                              int32_t kmask, int32_t *__restrict__ W,
-                                                             const int64_t *__restrict__ deg_sum, int64_t m) {
+                                                             const int64_t *__restrict__ deg_sum, int64_t m,
+                                                             SparseRows sp) {
     if (*deg_sum * 4 >= m) return;
     const HubChunk ch = chunks[blockIdx.x];
     const int32_t i = pos[ch.v];
@@ -658,6 +665,11 @@ __global__ void __launch_bounds__(512) k_table_rollback_hubs(Rollback rb, const 
     const int32_t a = blk_local(rb.I_to[i], k, kmask), b = blk_local(rb.I_from[i], k, kmask);
     for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
         const int32_t w = adjw ? adjw[e] : 1;
+        if (sp.on()) {
+            sp_sub(sp, adj[e], a, w);
+            sp_add(sp, adj[e], b, w);
+            continue;
+        }
         int32_t *row = W + (int64_t)adj[e] * k;
         atomicSub(&row[a], w);
         atomicAdd(&row[b], w);
@@ -844,11 +856,12 @@ void table_rollback(const GraphDev &g, const Rollback &rb, int64_t max, const in
     k_rollback_degsum<<<grid_for(max), 256, 0, s>>>(rb, g.xadj, (unsigned long long *)deg_sum);
     UPR_LAUNCH_CHECK();
     const int64_t blocks = std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16);
-    k_table_rollback<<<(unsigned)blocks, 256, 0, s>>>(rb, g.xadj, g.adj, g.adjw, g.k, g.kmask, W, deg_sum, g.m);
+    k_table_rollback<<<(unsigned)blocks, 256, 0, s>>>(rb, g.xadj, g.adj, g.adjw, g.k, g.kmask, W, deg_sum, g.m,
+                                                      g.sp);
     UPR_LAUNCH_CHECK();
     if (n_chunks > 0) {
         k_table_rollback_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(rb, hub_chunks, pos, g.adj, g.adjw, g.k, g.kmask, W,
-                                                                 deg_sum, g.m);
+                                                                 deg_sum, g.m, g.sp);
         UPR_LAUNCH_CHECK();
     }
 }

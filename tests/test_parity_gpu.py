@@ -290,17 +290,51 @@ def test_sparse_table_same_results(upr, name, table):
     assert st.cut_out == c0
 
 
-def test_sparse_table_by_request_only(upr):
-    w = synth.random_small(21, 3000, 6, 256, max_vw=20)
-    ctx = upr.create_from_workload(w)
-    p = w.part.copy()
-    st = upr.upr_refine(ctx, p, 3)
-    assert st.sparse_table == 0
-    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=3)
-    assert np.array_equal(p, p0) and st.cut_out == c0
-    ctx = upr.create_from_workload(w, params=_params(upr, 2))
-    p = w.part.copy()
-    st = upr.upr_refine(ctx, p, 3)
+@pytest.mark.parametrize("table", [2, 3])
+def test_sparse_rows_carried_over_rounds(upr, table):
+    """Hashed rows are built once and then follow the moves, the rebalancing
+    moves and the end-of-round rollback as delta updates, round after round
+    and across calls on one context; a row that runs out of slots sends the
+    round back to rows built afresh (then to the dense table).  Nothing of
+    this shows in the results."""
+    for w in (CASES["rmat_s12_k64"](), synth.random_small(23, 4000, 9, 256, weighted=True, hubs=2)):
+        ctx = upr.create_from_workload(w, params=_params(upr, table))
+        rounds = 6
+        rc, p0, c0, _ = oracle.refine(w, w.part, rounds=rounds)
+        for _ in range(2):
+            p = w.part.copy()
+            st = upr.upr_refine(ctx, p, rounds)
+            assert np.array_equal(p, p0), w.name
+            assert st.cut_out == c0
+        if table == 2:
+            assert st.sparse_table == 1
+            assert st.gain_table_builds < rounds
+
+
+def test_sparse_rows_in_a_batch(upr):
+    ws = [synth.random_small(40 + i, [300, 900, 50, 2000][i % 4], [5, 9, 3, 7][i % 4], 128,
+                             weighted=i % 2 == 0, hubs=1 if i == 1 else 0) for i in range(6)]
+    ctx = upr.create_batch_from_workloads(ws, params=_params(upr, 2))
+    part = np.concatenate([w.part for w in ws]).astype(np.int32)
+    status, cin, cout, st = upr.upr_batch_refine(ctx, part, 4)
     assert st.sparse_table == 1
-    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=3)
-    assert np.array_equal(p, p0) and st.cut_out == c0
+    off = ctx.offsets
+    for i, w in enumerate(ws):
+        rc, ref, cut, _ = oracle.refine(w, w.part, rounds=4)
+        assert status[i] == rc
+        if rc == 0:
+            assert np.array_equal(part[off[i]:off[i + 1]], ref), i
+            assert cout[i] == cut
+
+
+def test_sparse_table_chosen_by_size(upr):
+    """Auto layout: hashed rows for k >= 128 when they take at most half the
+    dense table's bytes (sparse graphs), the dense table otherwise."""
+    for k, deg, want in ((256, 6, 1), (64, 6, 0), (128, 200, 0)):
+        w = synth.random_small(21, 3000, deg, k, max_vw=20)
+        ctx = upr.create_from_workload(w)
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, 3)
+        assert st.sparse_table == want, (k, deg)
+        rc, p0, c0, _ = oracle.refine(w, w.part, rounds=3)
+        assert np.array_equal(p, p0) and st.cut_out == c0
