@@ -94,6 +94,11 @@ typedef struct {
                                     dense table: a round whose rows run out of slots runs
                                     again on rows built afresh, and if those run out too,
                                     on a dense table allocated then. 0                       */
+    int32_t graphs;              /* 1: once the proposal schedule is settled, each round's
+                                    rebalancing loop runs as one CUDA graph launch (a while
+                                    node over one sub-round, the stop test on the device);
+                                    0: the host launches every sub-round and reads its stop
+                                    flag.  Results never depend on it. 1                     */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 
@@ -123,6 +128,7 @@ typedef struct {
     int32_t select_lanes;        /* lanes per node of the selection kernel (0: scalar)  */
     int32_t propose_lanes;       /* lanes per node of the proposal kernel (0: scalar)   */
     int32_t sparse_table;        /* 1: the rounds ran on the sparse gain table            */
+    int32_t rebalance_graphs;    /* rounds whose rebalancing loop ran as one graph launch */
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */

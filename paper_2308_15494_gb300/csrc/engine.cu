@@ -95,7 +95,6 @@ struct upr_ctx {
     int32_t k = 0;
     int32_t ng = 1;                   // graphs bound (a batch when > 1)
     bool table_valid = false;         // W holds the table of part0 (carried from the previous round)
-    uint32_t epoch = 0;               // call tag of the primitives' status words (Scratch::epoch)
     // lane schedules of the selection / proposal kernels: chosen by timing the
     // candidates on this binding's inputs (see tune_*), default until then
     LaneCfg sel_cfg{0, 0}, prop_cfg{0, 0};
@@ -111,6 +110,15 @@ struct upr_ctx {
     // here only if a round falls back to it (or for the debug entry point)
     int32_t *W_own = nullptr; size_t W_own_bytes = 0;
     int32_t sp_buf_cap = 1;
+    // the rebalancing loop as one CUDA graph (a while node over one sub-round),
+    // built for the binding and the proposal schedule it was captured with
+    cudaStream_t s_cap = nullptr;     // capture stream (non-blocking)
+    cudaGraphExec_t reb_exec = nullptr;
+    uint64_t gen = 0, reb_gen = ~0ull;  // binding generation; the one reb_exec belongs to
+    LaneCfg reb_cfg{};
+    int reb_body_kernels = 0;
+    int64_t rounds_bound = 0;         // rounds run since the binding
+    bool reb_failed = false;          // capture or instantiation failed: host-driven loop
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -150,6 +158,8 @@ struct upr_ctx {
     int32_t *seg_first, *rbeg, *rend, *ebeg, *eend, *qfin, *left, *left_excl;
     long long *best_parts, *best;
     int8_t *over_d, *excl_d, *reject_d;
+    unsigned long long *prio_hist;   // [K][kPrioBins] proposal prefilter (null: K too large, no prefilter)
+    int32_t *prio_cut;               // [K]
     int32_t *counts;          // device counters (CNT_* slots)
     RebalCtl *ctl;            // rebalancing loop control block
     uint64_t *vacc; int32_t *vflags; int64_t *scal;
@@ -235,6 +245,9 @@ void layout(upr_ctx *c, Arena &A) {
     c->over_d = A.take<int8_t>(k);
     c->excl_d = A.take<int8_t>(k);
     c->reject_d = A.take<int8_t>(k);
+    const bool prefilter = k * (size_t)kPrioBins <= ((size_t)1 << 22);
+    c->prio_hist = prefilter ? A.take<unsigned long long>(k * kPrioBins) : nullptr;
+    c->prio_cut = prefilter ? A.take<int32_t>(k) : nullptr;
     c->counts = A.take<int32_t>(64);
     c->ctl = A.take<RebalCtl>(1);
     c->vacc = A.take<uint64_t>(2);
@@ -247,7 +260,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->tmp.scan = A.take<char>(c->tmp.scan_bytes);
     c->tmp.ticket = A.take<unsigned int>(64);
     c->tmp.err = A.take<int32_t>(1);
-    c->tmp.epoch = &c->epoch;
+    c->tmp.epoch = A.take<uint32_t>(1);
 }
 
 enum MemKind { kHost = 0, kDevice = 1 };
@@ -296,6 +309,7 @@ struct RoundInfo {
     int32_t subrounds = 0;
     float ms_table = 0, ms_select = 0, ms_rebalance = 0, ms_sequence = 0;
     int tables = 0;
+    bool graph = false;         // the rebalancing loop ran as one graph launch
 };
 
 // Trace destinations on the host (debug entry only).
@@ -308,7 +322,7 @@ void d2h(void *dst, const void *src, size_t bytes, cudaStream_t s) {
 // Slots of the device counters (upr_ctx::counts).
 enum {
     CNT_CAND = 0, CNT_M, CNT_P, CNT_S, CNT_A, CNT_I, CNT_HUB, CNT_BADPART, CNT_L1, CNT_X, CNT_EVM, CNT_EVI,
-    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_SLOTS = 32
+    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_Q, CNT_SLOTS = 32
 };
 
 // ---- lane-schedule tuning.  A kernel whose schedule is not chosen yet runs
@@ -352,6 +366,134 @@ void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands
         *tuned = true;
     }
     *pending = 0;
+}
+
+// One rebalancing sub-round (Sec. 6), enqueued on s.  Every argument is fixed
+// for the binding (the sub-round number and every list length live in device
+// memory), so the same launches can be captured once and replayed.  first:
+// the round's first sub-round, which may time the proposal kernel's lane
+// schedules (host-driven loop only).
+void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool first, cudaStream_t s) {
+    const GraphDev &G = c->G;
+    const int64_t n = c->n;
+    const int kbits = std::max(1, bit_length((uint64_t)(G.K() - 1)));
+    int32_t *cnt = c->counts;
+    RebalCtl *ctl = c->ctl;
+    const Count cS{cnt + CNT_S, n};
+    rebalance_begin(G, c->C, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, c->prm.max_subrounds, ctl, light, s);
+    if (first)
+        run_tuned(c, c->prop_tuned, c->prop_cfg, c->prop_cands, &c->prop_pending, c->ev_tune + 6,
+                  [&](LaneCfg cfg) {
+                      rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt,
+                                             c->prop_gain, c->flags, cfg, s);
+                  });
+    else
+        rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain,
+                               c->flags, c->prop_cfg, s);
+    select_flags(c->flags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
+    rebalance_gather_list(c->L1, c->idxD, cnt + CNT_P, c->idxA, n, s);
+    // proposals that cannot be in their source's minimal prefix are
+    // dropped before the ordering (node order kept)
+    const int32_t *Pn = c->idxA;
+    int32_t *dP = cnt + CNT_P;
+    if (c->prio_hist) {
+        rebalance_prefilter(G, c->idxA, cnt + CNT_P, c->prop_gain, c->part, c->over_d, c->C, c->gbits, c->cbits,
+                            c->sb[2].k, c->prio_hist, c->prio_cut, c->flags2, n, s);
+        select_flags(c->flags2, c->idxB, cnt + CNT_Q, Count{cnt + CNT_P, n}, c->tmp, s);
+        rebalance_gather_list(c->idxA, c->idxB, cnt + CNT_Q, c->idxD, n, s);
+        Pn = c->idxD;
+        dP = cnt + CNT_Q;
+    }
+    const Count cP{dP, n};
+    uint64_t *kA; uint32_t *A;
+    rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v, n, s);
+    c->sb[0].run(cP, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
+    // per source: the minimal prefix covering the excess
+    uint64_t *kB; uint32_t *B;
+    rebalance_block_keys(Pn, A, nullptr, dP, c->part, c->sb[1].k, c->sb[1].v, n, s);
+    c->sb[1].run(cP, kbits, c->tmp, s, &kB, &B);
+    rebalance_seg_weights(G, Pn, A, nullptr, B, kB, dP, c->c_sorted, c->seg_first, n, s);
+    exclusive_sum_i64(c->c_sorted, c->c_excl, cP, c->tmp, s);
+    rebalance_mark_selected(B, kB, dP, c->c_excl, c->seg_first, st, c->flags2, n, s);
+    select_flags(c->flags2, c->idxB, cnt + CNT_S, cP, c->tmp, s);
+    // per target: the longest prefix that fits
+    uint64_t *kT; uint32_t *Tq;
+    rebalance_block_keys(Pn, A, c->idxB, cnt + CNT_S, c->prop_tgt, c->sb[2].k, c->sb[2].v, n, s);
+    c->sb[2].run(cS, kbits, c->tmp, s, &kT, &Tq);
+    rebalance_seg_weights(G, Pn, A, c->idxB, Tq, kT, cnt + CNT_S, c->c_sorted, c->seg_first, n, s);
+    exclusive_sum_i64(c->c_sorted, c->c_excl, cS, c->tmp, s);
+    rebalance_mark_admitted(Tq, kT, cnt + CNT_S, c->c_sorted, c->c_excl, c->seg_first, st, c->flags2, c->reject_d,
+                            n, s);
+    select_flags(c->flags2, c->idxC, cnt + CNT_A, cS, c->tmp, s);
+    rebalance_apply(G, Pn, A, c->idxB, c->idxC, cnt + CNT_A, c->prop_tgt, c->part, c->C, ctl, c->R_node,
+                    c->R_from, c->R_to, c->R_sub, c->r_to, c->r_at, n, s);
+    table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
+               c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
+    rebalance_end(G, c->C, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
+}
+
+// The rebalancing loop as a graph: a kernel sets the condition of a while
+// node whose body is one sub-round followed by the same kernel.  Built on
+// first use for the binding and the proposal schedule, then replayed; false
+// if the graph cannot be built (the host-driven loop is used instead).
+bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
+    if (c->reb_failed) return false;
+    if (c->reb_exec && c->reb_gen == c->gen && c->reb_cfg.G == c->prop_cfg.G && c->reb_cfg.CH == c->prop_cfg.CH)
+        return true;
+    if (c->reb_exec) { cudaGraphExecDestroy(c->reb_exec); c->reb_exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    bool capturing = false;
+    long long captured = 0;
+    try {
+        if (!c->s_cap) UPR_CUDA(cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
+        UPR_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle cond;
+        UPR_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+        UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        rebalance_continue(c->ctl, c->prm.max_subrounds, cond, c->s_cap);
+        captured++;
+        cudaGraph_t out = nullptr;
+        capturing = false;
+        UPR_CUDA(cudaStreamEndCapture(c->s_cap, &out));
+        cudaGraphNode_t head[1];
+        size_t n_head = 1;
+        UPR_CUDA(cudaGraphGetNodes(g, head, &n_head));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop;
+        UPR_CUDA(cudaGraphAddNode(&loop, g, head, nullptr, n_head, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        const long long b0 = g_upr_launches.load();
+        enqueue_subround(c, st, light, false, c->s_cap);
+        rebalance_continue(c->ctl, c->prm.max_subrounds, cond, c->s_cap);
+        c->reb_body_kernels = (int)(g_upr_launches.load() - b0);
+        captured += c->reb_body_kernels;
+        capturing = false;
+        UPR_CUDA(cudaStreamEndCapture(c->s_cap, &out));
+        UPR_CUDA(cudaGraphInstantiate(&c->reb_exec, g, 0));
+        cudaGraphDestroy(g);
+    } catch (const CudaError &e) {
+        if (capturing) {
+            cudaGraph_t out = nullptr;
+            cudaStreamEndCapture(c->s_cap, &out);
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (log_enabled()) fprintf(stderr, "upr: rebalancing graph not built (%s: %s)\n", e.what,
+                                   cudaGetErrorString(e.e));
+        c->reb_exec = nullptr;
+        c->reb_failed = true;
+    }
+    g_upr_launches.fetch_sub(captured);     // captured, not launched: counted when the graph runs
+    c->reb_gen = c->gen;
+    c->reb_cfg = c->prop_cfg;
+    return c->reb_exec != nullptr;
 }
 
 /*
@@ -428,54 +570,39 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     UPR_CUDA(cudaEventRecord(c->ev[5], s));
 
     // ---- (d) rebalancing sub-rounds
+    if (c->prio_hist)
+        UPR_CUDA(cudaMemsetAsync(c->prio_hist, 0, sizeof(unsigned long long) * K * kPrioBins, s));
     rebalance_init(G, c->C, c->excl_d, ctl, s);
     rebalance_flag_in_blocks(c->part, n, c->excl_d, c->flags, s);
     select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
     int32_t *light = batch ? c->light_g : &ctl->light;
     const RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
-    const Count cP{cnt + CNT_P, n}, cS{cnt + CNT_S, n};
-    for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
-        rebalance_begin(G, c->C, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, h, c->prm.max_subrounds, ctl, light,
-                        s);
-        if (h == 1)
-            run_tuned(c, c->prop_tuned, c->prop_cfg, c->prop_cands, &c->prop_pending, c->ev_tune + 6,
-                      [&](LaneCfg cfg) {
-                          rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt,
-                                                 c->prop_gain, c->flags, cfg, s);
-                      });
-        else
-            rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain,
-                                   c->flags, c->prop_cfg, s);
-        select_flags(c->flags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
-        rebalance_gather_list(c->L1, c->idxD, cnt + CNT_P, c->idxA, n, s);
-        uint64_t *kA; uint32_t *A;
-        rebalance_prio_keys(G, c->idxA, cnt + CNT_P, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v, n, s);
-        c->sb[0].run(cP, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
-        // per source: the minimal prefix covering the excess
-        uint64_t *kB; uint32_t *B;
-        rebalance_block_keys(c->idxA, A, nullptr, cnt + CNT_P, c->part, c->sb[1].k, c->sb[1].v, n, s);
-        c->sb[1].run(cP, kbits, c->tmp, s, &kB, &B);
-        rebalance_seg_weights(G, c->idxA, A, nullptr, B, kB, cnt + CNT_P, c->c_sorted, c->seg_first, n, s);
-        exclusive_sum_i64(c->c_sorted, c->c_excl, cP, c->tmp, s);
-        rebalance_mark_selected(B, kB, cnt + CNT_P, c->c_excl, c->seg_first, st, c->flags2, n, s);
-        select_flags(c->flags2, c->idxB, cnt + CNT_S, cP, c->tmp, s);
-        // per target: the longest prefix that fits
-        uint64_t *kT; uint32_t *Tq;
-        rebalance_block_keys(c->idxA, A, c->idxB, cnt + CNT_S, c->prop_tgt, c->sb[2].k, c->sb[2].v, n, s);
-        c->sb[2].run(cS, kbits, c->tmp, s, &kT, &Tq);
-        rebalance_seg_weights(G, c->idxA, A, c->idxB, Tq, kT, cnt + CNT_S, c->c_sorted, c->seg_first, n, s);
-        exclusive_sum_i64(c->c_sorted, c->c_excl, cS, c->tmp, s);
-        rebalance_mark_admitted(Tq, kT, cnt + CNT_S, c->c_sorted, c->c_excl, c->seg_first, st, c->flags2, c->reject_d,
-                                n, s);
-        select_flags(c->flags2, c->idxC, cnt + CNT_A, cS, c->tmp, s);
-        rebalance_apply(G, c->idxA, A, c->idxB, c->idxC, cnt + CNT_A, c->prop_tgt, c->part, c->C, ctl, c->R_node,
-                        c->R_from, c->R_to, c->R_sub, c->r_to, c->r_at, n, s);
-        table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
-                   c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
-        rebalance_end(G, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
+    auto t_sub = std::chrono::steady_clock::now();
+    // the loop runs on the device as one graph once the proposal schedule is
+    // settled (the host-driven form times the schedules, logs and traces);
+    // a small binding first has to run a few rounds to pay for the capture
+    const bool tuning = !c->prop_tuned && worth_tuning(c);
+    const bool pays = (int64_t)n * c->k >= ((int64_t)1 << 22) || c->rounds_bound >= 8;
+    c->rounds_bound++;
+    if (c->prm.graphs && pays && !tuning && !tr && !log_enabled() && rebalance_graph(c, st, light)) {
+        UPR_CUDA(cudaGraphLaunch(c->reb_exec, s));
+        ri.graph = true;
+    } else for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
+        enqueue_subround(c, st, light, h == 1, s);
         UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
         settle_tuning(&c->prop_cfg, &c->prop_tuned, &c->prop_pending, c->prop_cands, c->ev_tune + 6, 0.02f);
+        if (log_enabled()) {
+            int32_t hc[CNT_SLOTS];
+            UPR_CUDA(cudaMemcpy(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost));
+            const auto t1 = std::chrono::steady_clock::now();
+            fprintf(stderr, "upr round %d sub-round %d: listed %d active %d proposals %d kept %d selected %d "
+                            "admitted %d (%.3f ms)\n",
+                    r, h, hc[CNT_L1], c->hctl->n1_active, hc[CNT_P], c->prio_hist ? hc[CNT_Q] : hc[CNT_P],
+                    hc[CNT_S], hc[CNT_A],
+                    std::chrono::duration<double, std::milli>(t1 - t_sub).count());
+            t_sub = std::chrono::steady_clock::now();
+        }
         if (c->hctl->stopped) break;
     }
     UPR_CUDA(cudaEventRecord(c->ev[6], s));
@@ -604,6 +731,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     ri.n_moves = hc[CNT_M];
     ri.n_rebal = c->hctl->nR;
     ri.subrounds = c->hctl->subrounds;
+    if (ri.graph) g_upr_launches.fetch_add(1 + (long long)c->reb_body_kernels * ri.subrounds);
     ri.n_inter = hc[CNT_X];
     ri.n_seq = hc[CNT_I];
     // one graph: an infeasible round applies nothing and is an error; a
@@ -694,6 +822,7 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
         c->sparse_on = false;
         c->G.sp.slot = nullptr;
         c->table_valid = false;
+        c->gen++;
     }
 }
 
@@ -701,6 +830,8 @@ void free_ctx(upr_ctx *c) {
     if (!c) return;
     if (c->mem) cudaFree(c->mem);
     if (c->W_own) cudaFree(c->W_own);
+    if (c->reb_exec) cudaGraphExecDestroy(c->reb_exec);
+    if (c->s_cap) cudaStreamDestroy(c->s_cap);
     if (c->h) cudaFreeHost(c->h);
     if (c->h8) cudaFreeHost(c->h8);
     for (auto &e : c->ev) if (e) cudaEventDestroy(e);
@@ -769,6 +900,7 @@ void store_part(upr_ctx *c, int32_t *part, const std::vector<int32_t> &keep_inpu
 void add_round(upr_stats &st, const RoundInfo &ri, bool repair) {
     st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
     st.n_rebalance_moves += ri.n_rebal; st.subrounds += ri.subrounds; st.n_sequence += ri.n_seq;
+    st.rebalance_graphs += ri.graph ? 1 : 0;
     st.n_applied += ri.best_len;
     if (repair) return;
     st.rounds_run++;
@@ -863,6 +995,7 @@ void upr_params_default(upr_params *p) {
     p->total_rounds = 0;
     p->autotune = 1;
     p->table = 0;
+    p->graphs = 1;
     p->stream = nullptr;
 }
 
@@ -1021,6 +1154,8 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->tile_nodes = tile_nodes;
     Arena A;
     if (c->W_own) { cudaFree(c->W_own); c->W_own = nullptr; c->W_own_bytes = 0; }
+    c->gen++;                       // kernels captured for the previous binding are stale
+    c->rounds_bound = 0;
     layout(c, A);
     if (!c->mem || c->mem_bytes < A.off) {
         if (c->mem) { cudaFree(c->mem); c->mem = nullptr; c->mem_bytes = 0; }
@@ -1108,7 +1243,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     UPR_CUDA(cudaMemsetAsync(c->tmp.mem, 0, c->tmp.mem_bytes, s));
     UPR_CUDA(cudaMemsetAsync(c->tmp.scan, 0, c->tmp.scan_bytes, s));
     UPR_CUDA(cudaMemsetAsync(c->tmp.err, 0, sizeof(int32_t), s));
-    c->epoch = 0;
+    UPR_CUDA(cudaMemsetAsync(c->tmp.epoch, 0, sizeof(uint32_t), s));
     UPR_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(RebalCtl), s));
     UPR_CUDA(cudaMemsetAsync(c->counts, 0, 64 * sizeof(int32_t), s));
     fill_i32(c->pos, n, INT32_MAX, s);

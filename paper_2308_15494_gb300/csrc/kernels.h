@@ -131,7 +131,7 @@ struct Scratch {
     size_t mem_bytes, scan_bytes;
     int64_t tiles_cap;      // tiles of the longest list; fixes the layout of both regions
     unsigned int *ticket;   // [0] next tile, [1] finished CTAs, [2] radix count ticket
-    uint32_t *epoch;
+    uint32_t *epoch;        // device word: the primitives' last call tag
     int32_t *err;
 };
 
@@ -266,6 +266,15 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
 void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                             const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
                             int32_t *prop_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s);
+// Proposal prefilter (exact): per source block, the proposals of the priority
+// bins after the one where the cumulative weight reaches the excess can never
+// be selected; flags[i] = 1 for the others.  hist (K * kPrioBins, zero on entry)
+// is left zero.
+constexpr int kPrioBins = 256;
+void rebalance_prefilter(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
+                         const int32_t *part, const int8_t *over, const int64_t *C, int gbits, int cbits,
+                         uint64_t *keys, unsigned long long *hist, int32_t *cut, int32_t *flags, int64_t np_max,
+                         cudaStream_t s);
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                          int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s);
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,
@@ -286,10 +295,12 @@ void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, con
 // receives each graph's lightest non-excluded block (&ctl->light for one graph).
 void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl *ctl, cudaStream_t s);
 void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
-                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, int32_t *light,
-                     cudaStream_t s);
-void rebalance_end(const GraphDev &g, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl,
-                   cudaStream_t s);
+                     const int32_t *d_n1, int32_t max_subrounds, RebalCtl *ctl, int32_t *light, cudaStream_t s);
+// Sets the condition of a graph's while node: another sub-round is due.
+void rebalance_continue(const RebalCtl *ctl, int32_t max_subrounds, cudaGraphConditionalHandle handle,
+                        cudaStream_t s);
+void rebalance_end(const GraphDev &g, const int64_t *C, int8_t *excl, const int8_t *reject, const int32_t *d_na,
+                   RebalCtl *ctl, cudaStream_t s);
 
 // ---- sequence.cu: step (c); every count lives in device memory, `max` bounds it
 void count_affine(const int32_t *a, int32_t a_mul, const int32_t *b, int32_t add, int32_t *out, cudaStream_t s);

@@ -15,8 +15,10 @@
 // publishes its own.  A tile only waits for tiles that running CTAs took
 // earlier, so the waits end whatever the scheduling; every wait is bounded
 // anyway and records a timeout in an error word instead of spinning on.
-// Status words carry the call's epoch (a per-scratch counter advanced by the
-// host at every call), so nothing has to be cleared between calls.  A radix
+// Status words carry the call's epoch, so nothing has to be cleared between
+// calls: the epoch is a device word that the taking-part CTAs read when they
+// start and the last of them advances when it finishes, so calls replayed
+// from a CUDA graph get fresh epochs exactly like calls launched one by one.  A radix
 // pass is histogram -> single-pass scan of the digit-major histogram ->
 // stable scatter; inside a tile, equal digits are ranked in item order with
 // __match_any_sync per warp and a per-digit prefix over the 8 warps.  Lists
@@ -129,7 +131,18 @@ struct ScanState {
     T *agg, *incl;
     unsigned int *ctr;      // [0] next tile, [1] finished CTAs
     int32_t *err;
+    uint32_t *epoch;        // the last epoch used (0 after a clear)
+    int64_t flags_cap;      // status words in `flag`
 };
+
+// Epochs live in 30 bits; the call that reaches the limit clears every status
+// word and starts again from 1, so no stale word can carry a current epoch.
+constexpr uint32_t kEpochLimit = (1u << 30) - 1;
+
+template <typename T>
+__device__ __forceinline__ uint32_t call_epoch(const ScanState<T> &st) {
+    return *(volatile const uint32_t *)st.epoch + 1u;
+}
 
 // Waits (bounded) until tile j's flag carries this epoch; returns its state
 // (kAgg / kIncl), or 0 after a timeout (recorded in *err).
@@ -164,14 +177,26 @@ __device__ __forceinline__ unsigned participants(int64_t tiles) {
 }
 
 // Called by every taking-part CTA once it takes no more tiles: the last one
-// resets the counters.
-__device__ __forceinline__ void finish_tiles(unsigned int *ctr, unsigned parts) {
+// resets the counters and advances the epoch (all taking-part CTAs read it
+// before they got here).
+template <typename T>
+__device__ __forceinline__ void finish_tiles(const ScanState<T> &st, unsigned parts, uint32_t epoch) {
+    __shared__ bool s_last;
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&ctr[1], 1u) == parts - 1) {
-            ctr[0] = 0;
-            ctr[1] = 0;
-        }
+        s_last = atomicAdd(&st.ctr[1], 1u) == parts - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    if (epoch >= kEpochLimit) {
+        for (int64_t i = threadIdx.x; i < st.flags_cap; i += blockDim.x) st.flag[i] = 0;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st.ctr[0] = 0;
+        st.ctr[1] = 0;
+        *st.epoch = epoch >= kEpochLimit ? 0u : epoch;
+        __threadfence();
     }
 }
 
@@ -254,8 +279,7 @@ __device__ __forceinline__ void scan_tile(const TIn *in, T *out, int64_t n, int 
 
 template <typename Op, typename T, typename TIn>
 __global__ void __launch_bounds__(kThreads) k_scan(const TIn *in, T *out, const int32_t *__restrict__ d_n,
-                                                   int64_t n_max, int inclusive, int vec, ScanState<T> st,
-                                                   uint32_t epoch) {
+                                                   int64_t n_max, int inclusive, int vec, ScanState<T> st) {
     __shared__ T s_warp[kWarps];
     __shared__ T s_excl;
     __shared__ uint32_t s_tile;
@@ -264,15 +288,16 @@ __global__ void __launch_bounds__(kThreads) k_scan(const TIn *in, T *out, const 
     const unsigned parts = participants(tiles);
     if (blockIdx.x >= parts) return;
     if (tiles == 1) {
-        scan_tile<Op>(in, out, n, inclusive, vec, st, epoch, 0, true, s_warp, &s_excl);
+        scan_tile<Op>(in, out, n, inclusive, vec, st, 0u, 0, true, s_warp, &s_excl);
         return;
     }
+    const uint32_t epoch = call_epoch(st);
     for (;;) {
         const int64_t tile = next_tile(st.ctr, &s_tile);
         if (tile >= tiles) break;
         scan_tile<Op>(in, out, n, inclusive, vec, st, epoch, tile, false, s_warp, &s_excl);
     }
-    finish_tiles(st.ctr, parts);
+    finish_tiles(st, parts, epoch);
 }
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -280,19 +305,6 @@ inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // Persistent grid of the tile kernels: tiles are taken dynamically.
 inline unsigned tile_grid(int64_t tiles_max) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_max, (int64_t)device_sm_count() * 4));
-}
-
-// Tag of a new call.  Tags live in 30 bits; when they run out (after about
-// 10^9 calls on one scratch), the status memory is cleared on the stream and
-// tags restart at 1, so no stale word can carry a current tag.
-inline uint32_t next_epoch(const Scratch &tmp, cudaStream_t s) {
-    uint32_t e = ++(*tmp.epoch);
-    if (e >= (1u << 30) - 1) {
-        UPR_CUDA(cudaMemsetAsync(tmp.mem, 0, tmp.mem_bytes, s));
-        UPR_CUDA(cudaMemsetAsync(tmp.scan, 0, tmp.scan_bytes, s));
-        *tmp.epoch = e = 1;
-    }
-    return e;
 }
 
 // The layout depends on the scratch's capacity only, never on the call, so a
@@ -307,6 +319,8 @@ ScanState<T> scan_state(const Scratch &tmp, int64_t tiles_max) {
     st.incl = reinterpret_cast<T *>(tmp.scan + 2 * stride);
     st.ctr = tmp.ticket;
     st.err = tmp.err;
+    st.epoch = tmp.epoch;
+    st.flags_cap = tmp.tiles_cap;
     return st;
 }
 
@@ -316,9 +330,8 @@ void scan_impl(const TIn *in, T *out, Count n, bool inclusive, Scratch tmp, cuda
     const int vin = aligned16(in) ? 1 : 0;
     const int vio = vin | (aligned16(out) ? 2 : 0);
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    const uint32_t epoch = next_epoch(tmp, s);
     k_scan<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, inclusive ? 1 : 0, vio,
-                                                                  scan_state<T>(tmp, tiles_max), epoch);
+                                                                  scan_state<T>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
 }
 
@@ -355,8 +368,7 @@ __device__ __forceinline__ void compact_tile(const int32_t *flags, int64_t n, in
 
 __global__ void __launch_bounds__(kThreads) k_compact(const int32_t *__restrict__ flags, const int32_t *__restrict__ d_n,
                                                       int64_t n_max, int32_t *__restrict__ out,
-                                                      int32_t *__restrict__ d_count, int vec, ScanState<int32_t> st,
-                                                      uint32_t epoch) {
+                                                      int32_t *__restrict__ d_count, int vec, ScanState<int32_t> st) {
     __shared__ int32_t s_warp[kWarps];
     __shared__ int32_t s_excl;
     __shared__ uint32_t s_tile;
@@ -366,15 +378,16 @@ __global__ void __launch_bounds__(kThreads) k_compact(const int32_t *__restrict_
     const unsigned parts = participants(tiles);
     if (blockIdx.x >= parts) return;
     if (tiles == 1) {
-        compact_tile(flags, n, tiles, out, d_count, vec, st, epoch, 0, true, s_warp, &s_excl);
+        compact_tile(flags, n, tiles, out, d_count, vec, st, 0u, 0, true, s_warp, &s_excl);
         return;
     }
+    const uint32_t epoch = call_epoch(st);
     for (;;) {
         const int64_t tile = next_tile(st.ctr, &s_tile);
         if (tile >= tiles) break;
         compact_tile(flags, n, tiles, out, d_count, vec, st, epoch, tile, false, s_warp, &s_excl);
     }
-    finish_tiles(st.ctr, parts);
+    finish_tiles(st, parts, epoch);
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -597,9 +610,8 @@ void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Coun
     if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
     const int vec = aligned16(flags) ? 1 : 0;
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    const uint32_t epoch = next_epoch(tmp, s);
     k_compact<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, out_idx, d_count, vec,
-                                                        scan_state<int32_t>(tmp, tiles_max), epoch);
+                                                        scan_state<int32_t>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
 }
 

@@ -293,11 +293,11 @@ __global__ void k_reb_init_batch(const int64_t *__restrict__ C, const int64_t *_
     }
 }
 
-// Start of sub-round h: overloaded set, lightest allowed block, activity.
+// Start of the next sub-round (h = the number run so far + 1): overloaded
+// set, lightest allowed block, activity.
 __global__ void k_reb_begin(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t k,
                             const int8_t *__restrict__ excl, int8_t *__restrict__ over, int8_t *__restrict__ reject,
-                            const int32_t *__restrict__ d_n1, int32_t h, int32_t max_subrounds,
-                            RebalCtl *__restrict__ ctl) {
+                            const int32_t *__restrict__ d_n1, int32_t max_subrounds, RebalCtl *__restrict__ ctl) {
     __shared__ int s_any;
     __shared__ long long s_w[256];
     __shared__ int s_b[256];
@@ -328,6 +328,7 @@ __global__ void k_reb_begin(const int64_t *__restrict__ C, const int64_t *__rest
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        const int32_t h = ctl->subrounds + 1;
         const bool run = !ctl->stopped && s_any && h <= max_subrounds;
         ctl->active = run ? 1 : 0;
         if (!run) ctl->stopped = 1;
@@ -340,7 +341,7 @@ __global__ void k_reb_begin(const int64_t *__restrict__ C, const int64_t *__rest
 // Batch form: warp per graph.
 __global__ void k_reb_begin_batch(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t k,
                                   int32_t ng, const int8_t *__restrict__ excl, int8_t *__restrict__ over,
-                                  int8_t *__restrict__ reject, const int32_t *__restrict__ d_n1, int32_t h,
+                                  int8_t *__restrict__ reject, const int32_t *__restrict__ d_n1,
                                   int32_t max_subrounds, RebalCtl *__restrict__ ctl, int32_t *__restrict__ light) {
     const int lane = threadIdx.x & 31;
     int any = 0;
@@ -365,6 +366,7 @@ __global__ void k_reb_begin_batch(const int64_t *__restrict__ C, const int64_t *
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&ctl->flag, 1);
     if (last_cta(ctl)) {
         const int f = atomicAdd(&ctl->flag, 0);
+        const int32_t h = ctl->subrounds + 1;
         const bool run = !ctl->stopped && f && h <= max_subrounds;
         ctl->active = run ? 1 : 0;
         if (!run) ctl->stopped = 1;
@@ -376,35 +378,43 @@ __global__ void k_reb_begin_batch(const int64_t *__restrict__ C, const int64_t *
 }
 
 // End of a sub-round: targets that rejected a move are excluded from now on;
-// stop when nothing was admitted and no target was newly excluded.
-__global__ void k_reb_end(int32_t K, int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
+// stop when nothing was admitted and no target was newly excluded, or when no
+// block is overloaded any more (the next sub-round would find nothing to do).
+__global__ void k_reb_end(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t K,
+                          int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
                           const int32_t *__restrict__ d_na, RebalCtl *__restrict__ ctl) {
-    __shared__ int s_grew;
-    if (threadIdx.x == 0) s_grew = 0;
+    __shared__ int s_grew, s_over;
+    if (threadIdx.x == 0) s_grew = 0, s_over = 0;
     __syncthreads();
     if (!ctl->active) return;
-    for (int b = threadIdx.x; b < K; b += blockDim.x)
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
         if (reject[b] && !excl[b]) { excl[b] = 1; s_grew = 1; }
+        if (C[b] > Lb[b]) s_over = 1;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int32_t na = *d_na;
         ctl->nR += na;
-        if (na == 0 && !s_grew) ctl->stopped = 1;
+        if ((na == 0 && !s_grew) || !s_over) ctl->stopped = 1;
     }
 }
 
-__global__ void k_reb_end_batch(int32_t K, int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
+__global__ void k_reb_end_batch(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t K,
+                                int8_t *__restrict__ excl, const int8_t *__restrict__ reject,
                                 const int32_t *__restrict__ d_na, RebalCtl *__restrict__ ctl) {
     if (!ctl->active) return;                 // uniform over the grid: no CTA takes a ticket
-    int grew = 0;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K; b += gridDim.x * blockDim.x)
+    int grew = 0, over = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < K; b += gridDim.x * blockDim.x) {
         if (reject[b] && !excl[b]) { excl[b] = 1; grew = 1; }
+        if (C[b] > Lb[b]) over = 1;
+    }
     if (__syncthreads_or(grew) && threadIdx.x == 0) atomicOr(&ctl->flag, 1);
+    if (__syncthreads_or(over) && threadIdx.x == 0) atomicOr(&ctl->flag, 2);
     if (last_cta(ctl)) {
         const int f = atomicAdd(&ctl->flag, 0);
         const int32_t na = *d_na;
         ctl->nR += na;
-        if (na == 0 && !f) ctl->stopped = 1;
+        if ((na == 0 && !(f & 1)) || !(f & 2)) ctl->stopped = 1;
         ctl->flag = 0;
         ctl->ticket = 0;
     }
@@ -413,21 +423,93 @@ __global__ void k_reb_end_batch(int32_t K, int8_t *__restrict__ excl, const int8
 // Ascending key = descending priority.  Class 0 (g >= 0): (2^(gb+cb) - 1) - g*c.
 // Class 1 (g < 0): floor(|g| * 2^(2cb) / c), exact for c < 2^cb.  Equal
 // priorities give equal keys; the stable sort then keeps node order.
+__device__ __forceinline__ uint64_t prio_key(int64_t g, uint64_t c, int gbits, int cbits) {
+    const int S = 2 * cbits;
+    if (g >= 0) return ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
+    return (1ull << (gbits + S)) | ((((uint64_t)(-g)) << S) / c);
+}
+
 __global__ void k_prio_keys(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
                             const int32_t *__restrict__ prop_gain, const int32_t *__restrict__ vwgt, int gbits,
                             int cbits, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t cnt = *d_np;
-    const int S = 2 * cbits;
     UPR_FOR(i, cnt) {
         const int32_t u = P[i];
-        const int64_t g = prop_gain[u];
-        const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
-        uint64_t key;
-        if (g >= 0) key = ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
-        else key = (1ull << (gbits + S)) | ((((uint64_t)(-g)) << S) / c);
-        keys[i] = key;
+        keys[i] = prio_key(prop_gain[u], vwgt ? (uint64_t)vwgt[u] : 1ull, gbits, cbits);
         vals[i] = (uint32_t)i;
     }
+}
+
+// ---- prefilter of the proposals.  A source keeps the minimal prefix of its
+// proposals (priority order) that covers its excess; that prefix is usually a
+// few percent of them.  A coarse bin, non-decreasing in the key, splits each
+// source's proposals into ranges: every proposal in a bin below the bin where
+// the source's cumulative weight reaches the excess is in the prefix, none
+// above it is, so only the proposals up to that bin need the exact ordering.
+// Keeping them (in their order) and dropping the rest leaves every kept
+// proposal with the same weight before it in its source's order.
+__device__ __forceinline__ int prio_bin(uint64_t key, int gbits, int cbits) {
+    const uint64_t top = 1ull << (gbits + 2 * cbits);
+    if (key < top) {      // g >= 0: g*c from 127 down, larger values share bin 0
+        const uint64_t v = ((1ull << (gbits + cbits)) - 1ull) - key;
+        return 127 - (int)(v < 127ull ? v : 127ull);
+    }
+    const uint64_t r = (key - top) >> cbits;      // about |g| * 2^cb / c
+    return 128 + (int)(r < 127ull ? r : 127ull);
+}
+
+// Keys of the proposals and, per source block, their weight by bin.
+__global__ void k_prio_hist(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
+                            const int32_t *__restrict__ prop_gain, const int32_t *__restrict__ vwgt,
+                            const int32_t *__restrict__ part, int gbits, int cbits, uint64_t *__restrict__ keys,
+                            unsigned long long *__restrict__ hist) {
+    const int64_t cnt = *d_np;
+    UPR_FOR(i, cnt) {
+        const int32_t u = P[i];
+        const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
+        const uint64_t key = prio_key(prop_gain[u], c, gbits, cbits);
+        keys[i] = key;
+        atomicAdd(&hist[(int64_t)part[u] * kPrioBins + prio_bin(key, gbits, cbits)], (unsigned long long)c);
+    }
+}
+
+// Per overloaded source: the first bin where the cumulative weight reaches the
+// excess C - L_max (the last bin when it never does); the histogram row is
+// cleared for the next sub-round.  One CTA of kPrioBins threads per block.
+__global__ void __launch_bounds__(kPrioBins) k_prio_cut(int32_t K, const int8_t *__restrict__ over,
+                                                       const int64_t *__restrict__ C, const int64_t *__restrict__ Lb,
+                                                       unsigned long long *__restrict__ hist,
+                                                       int32_t *__restrict__ cut) {
+    __shared__ unsigned long long s_warp[kPrioBins / 32];
+    __shared__ int s_cut;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int32_t a = blockIdx.x; a < K; a += gridDim.x) {
+        if (!over[a]) continue;                       // uniform over the CTA
+        unsigned long long *row = hist + (int64_t)a * kPrioBins;
+        const unsigned long long v = row[t];
+        unsigned long long inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        if (t == 0) s_cut = kPrioBins - 1;
+        __syncthreads();
+        for (int w = 0; w < warp; w++) inc += s_warp[w];
+        const unsigned long long excess = (unsigned long long)(C[a] - Lb[a]);
+        if (inc >= excess) atomicMin(&s_cut, t);
+        row[t] = 0;
+        __syncthreads();
+        if (t == 0) cut[a] = s_cut;
+        __syncthreads();
+    }
+}
+
+__global__ void k_prio_keep(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
+                            const uint64_t *__restrict__ keys, const int32_t *__restrict__ part,
+                            const int32_t *__restrict__ cut, int gbits, int cbits, int32_t *__restrict__ flags) {
+    const int64_t cnt = *d_np;
+    UPR_FOR(i, cnt) flags[i] = prio_bin(keys[i], gbits, cbits) <= cut[part[P[i]]] ? 1 : 0;
 }
 
 // Block-id key (source or target) of the entries listed through idx/order.
@@ -623,6 +705,19 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
     rebalance_propose_scalar_list(g, list, d_n1, n1_max, part, W, st, prop_tgt, prop_gain, flags, s);
 }
 
+void rebalance_prefilter(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
+                         const int32_t *part, const int8_t *over, const int64_t *C, int gbits, int cbits,
+                         uint64_t *keys, unsigned long long *hist, int32_t *cut, int32_t *flags, int64_t np_max,
+                         cudaStream_t s) {
+    if (np_max <= 0) return;
+    k_prio_hist<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, part, gbits, cbits, keys, hist);
+    UPR_LAUNCH_CHECK();
+    k_prio_cut<<<(unsigned)std::min<int64_t>(g.K(), 4096), kPrioBins, 0, s>>>(g.K(), over, C, g.Lb, hist, cut);
+    UPR_LAUNCH_CHECK();
+    k_prio_keep<<<grid_for(np_max), 256, 0, s>>>(P, d_np, keys, part, cut, gbits, cbits, flags);
+    UPR_LAUNCH_CHECK();
+}
+
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                          int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s) {
     if (np_max <= 0) return;
@@ -696,25 +791,38 @@ void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl 
 }
 
 void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
-                     const int32_t *d_n1, int32_t h, int32_t max_subrounds, RebalCtl *ctl, int32_t *light,
-                     cudaStream_t s) {
+                     const int32_t *d_n1, int32_t max_subrounds, RebalCtl *ctl, int32_t *light, cudaStream_t s) {
     if (g.ng == 1) {
-        k_reb_begin<<<1, 256, 0, s>>>(C, g.Lb, g.k, excl, over, reject, d_n1, h, max_subrounds, ctl);
+        k_reb_begin<<<1, 256, 0, s>>>(C, g.Lb, g.k, excl, over, reject, d_n1, max_subrounds, ctl);
     } else {
         clear_ticket(ctl, s);
         k_reb_begin_batch<<<ctl_grid((int64_t)g.ng * 32), 256, 0, s>>>(C, g.Lb, g.k, g.ng, excl, over, reject, d_n1,
-                                                                       h, max_subrounds, ctl, light);
+                                                                       max_subrounds, ctl, light);
     }
     UPR_LAUNCH_CHECK();
 }
 
-void rebalance_end(const GraphDev &g, int8_t *excl, const int8_t *reject, const int32_t *d_na, RebalCtl *ctl,
-                   cudaStream_t s) {
+// The loop condition of the graph-resident rebalancing loop: run another
+// sub-round while the loop has not stopped and sub-rounds are left.
+__global__ void k_reb_continue(const RebalCtl *__restrict__ ctl, int32_t max_subrounds,
+                               cudaGraphConditionalHandle handle) {
+    if (threadIdx.x == 0)
+        cudaGraphSetConditional(handle, (!ctl->stopped && ctl->subrounds < max_subrounds) ? 1u : 0u);
+}
+
+void rebalance_continue(const RebalCtl *ctl, int32_t max_subrounds, cudaGraphConditionalHandle handle,
+                        cudaStream_t s) {
+    k_reb_continue<<<1, 32, 0, s>>>(ctl, max_subrounds, handle);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_end(const GraphDev &g, const int64_t *C, int8_t *excl, const int8_t *reject, const int32_t *d_na,
+                   RebalCtl *ctl, cudaStream_t s) {
     if (g.ng == 1) {
-        k_reb_end<<<1, 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
+        k_reb_end<<<1, 256, 0, s>>>(C, g.Lb, g.K(), excl, reject, d_na, ctl);
     } else {
         clear_ticket(ctl, s);
-        k_reb_end_batch<<<ctl_grid(g.K()), 256, 0, s>>>(g.K(), excl, reject, d_na, ctl);
+        k_reb_end_batch<<<ctl_grid(g.K()), 256, 0, s>>>(C, g.Lb, g.K(), excl, reject, d_na, ctl);
     }
     UPR_LAUNCH_CHECK();
 }

@@ -141,3 +141,24 @@ def test_batch_rejects_bad_input(upr):
         upr.upr_batch_create([(ws[0].xadj, ws[0].adj, ws[0].vwgt, ws[0].adjw), (w.xadj, adj, w.vwgt, w.adjw)], 4,
                              0.03)
     assert e.value.status == upr.UPR_ERR_INVALID
+
+
+def test_batch_repeated_calls_graph_loop(upr):
+    """A batch context refined again and again: from the ninth round of the
+    binding on, the rebalancing loop runs as a CUDA graph; every call still
+    equals the oracle graph by graph."""
+    ws = _mixed(16, 10, 77)
+    ctx = upr.create_batch_from_workloads(ws)
+    used = 0
+    for _ in range(3):
+        part = _packed(ws)
+        status, cin, cout, st = upr.upr_batch_refine(ctx, part, 4)
+        used += st.rebalance_graphs
+        off = ctx.offsets
+        for i, w in enumerate(ws):
+            rc, ref, cut, _ = oracle.refine(w, w.part, 4)
+            assert status[i] == rc
+            if rc == 0:
+                assert np.array_equal(part[off[i]:off[i + 1]], ref), i
+                assert cout[i] == cut
+    assert used > 0

@@ -327,6 +327,23 @@ def test_sparse_rows_in_a_batch(upr):
             assert cout[i] == cut
 
 
+def test_rebalancing_graph_same_results(upr):
+    """The rebalancing loop run as one CUDA graph launch per round (a while
+    node over one sub-round, the stop test on the device) gives what the
+    host-driven loop gives; a small binding switches to it after 8 rounds."""
+    for w in (CASES["rmat_s12_k64"](), synth.random_small(31, 3000, 6, 8, weighted=True, hubs=1)):
+        rc, p0, c0, _ = oracle.refine(w, w.part, rounds=12)
+        for graphs in (0, 1):
+            prm = upr.upr_params_default()
+            prm.graphs = graphs
+            ctx = upr.create_from_workload(w, params=prm)
+            p = w.part.copy()
+            st = upr.upr_refine(ctx, p, 12)
+            assert np.array_equal(p, p0), (w.name, graphs)
+            assert st.cut_out == c0
+            assert (st.rebalance_graphs > 0) == (graphs == 1)
+
+
 def test_sparse_table_chosen_by_size(upr):
     """Auto layout: hashed rows for k >= 128 when they take at most half the
     dense table's bytes (sparse graphs), the dense table otherwise."""
