@@ -476,7 +476,9 @@ def run_gpu(args):
     w = synth.cached(getattr(synth, WORKLOAD), args.shrink)
     E = w.m // 2
     stream = torch.cuda.current_stream()
-    ctx = upr.create_from_workload(w, device=True)
+    prm = upr.upr_params_default()
+    prm.graphs = 0 if args.no_graphs else 1
+    ctx = upr.create_from_workload(w, params=prm, device=True)
     part_init = torch.from_numpy(w.part.copy()).cuda()
     part = torch.empty_like(part_init)
 
@@ -576,6 +578,7 @@ def run_gpu(args):
                 "result": {"cut_in": s0.cut_in, "cut_out": s0.cut_out, "moves": s0.n_moves,
                            "rebalance_moves": s0.n_rebalance_moves, "applied": s0.n_applied,
                            "subrounds": s0.subrounds, "table_builds_per_step": s0.gain_table_builds,
+                           "rebalance_graph_rounds_per_step": s0.rebalance_graphs,
                            "lanes_per_node": {"select": s0.select_lanes, "propose": s0.propose_lanes}},
                 "other_configs": others, "batched": batched, "served": served}
         print(json.dumps(line))
@@ -605,6 +608,9 @@ def main():
                     help="requests of the closed-loop burst that measures capacity")
     ap.add_argument("--shrink", type=int, default=0,
                     help="profiling only: the same workload family with 2^-shrink of the nodes")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every rebalancing sub-round from the host instead of one CUDA graph per round "
+                         "(same kernels; ncu's NVTX filter does not see kernels launched by a graph)")
     ap.add_argument("--profile", action="store_true",
                     help="device loop only (for ncu launch lists): no e2e, no CPU baseline")
     args = ap.parse_args()

@@ -322,7 +322,7 @@ void d2h(void *dst, const void *src, size_t bytes, cudaStream_t s) {
 // Slots of the device counters (upr_ctx::counts).
 enum {
     CNT_CAND = 0, CNT_M, CNT_P, CNT_S, CNT_A, CNT_I, CNT_HUB, CNT_BADPART, CNT_L1, CNT_X, CNT_EVM, CNT_EVI,
-    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_Q, CNT_SLOTS = 32
+    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_SLOTS = 32
 };
 
 // ---- lane-schedule tuning.  A kernel whose schedule is not chosen yet runs
@@ -390,20 +390,18 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     else
         rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain,
                                c->flags, c->prop_cfg, s);
-    select_flags(c->flags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
+    // proposals that cannot be in their source's minimal prefix are dropped
+    // before the ordering; P lists the others in node order
+    const int32_t *pflags = c->flags;
+    if (c->prio_hist) {
+        rebalance_prefilter(G, c->L1, &ctl->n1_active, n, c->flags, c->prop_gain, c->part, c->over_d, c->C,
+                            c->gbits, c->cbits, c->prio_hist, c->prio_cut, c->flags2, s);
+        pflags = c->flags2;
+    }
+    select_flags(pflags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
     rebalance_gather_list(c->L1, c->idxD, cnt + CNT_P, c->idxA, n, s);
-    // proposals that cannot be in their source's minimal prefix are
-    // dropped before the ordering (node order kept)
     const int32_t *Pn = c->idxA;
     int32_t *dP = cnt + CNT_P;
-    if (c->prio_hist) {
-        rebalance_prefilter(G, c->idxA, cnt + CNT_P, c->prop_gain, c->part, c->over_d, c->C, c->gbits, c->cbits,
-                            c->sb[2].k, c->prio_hist, c->prio_cut, c->flags2, n, s);
-        select_flags(c->flags2, c->idxB, cnt + CNT_Q, Count{cnt + CNT_P, n}, c->tmp, s);
-        rebalance_gather_list(c->idxA, c->idxB, cnt + CNT_Q, c->idxD, n, s);
-        Pn = c->idxD;
-        dP = cnt + CNT_Q;
-    }
     const Count cP{dP, n};
     uint64_t *kA; uint32_t *A;
     rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v, n, s);
@@ -596,10 +594,9 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
             int32_t hc[CNT_SLOTS];
             UPR_CUDA(cudaMemcpy(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost));
             const auto t1 = std::chrono::steady_clock::now();
-            fprintf(stderr, "upr round %d sub-round %d: listed %d active %d proposals %d kept %d selected %d "
+            fprintf(stderr, "upr round %d sub-round %d: listed %d active %d proposals kept %d selected %d "
                             "admitted %d (%.3f ms)\n",
-                    r, h, hc[CNT_L1], c->hctl->n1_active, hc[CNT_P], c->prio_hist ? hc[CNT_Q] : hc[CNT_P],
-                    hc[CNT_S], hc[CNT_A],
+                    r, h, hc[CNT_L1], c->hctl->n1_active, hc[CNT_P], hc[CNT_S], hc[CNT_A],
                     std::chrono::duration<double, std::milli>(t1 - t_sub).count());
             t_sub = std::chrono::steady_clock::now();
         }

@@ -266,15 +266,16 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
 void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                             const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,
                             int32_t *prop_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s);
-// Proposal prefilter (exact): per source block, the proposals of the priority
-// bins after the one where the cumulative weight reaches the excess can never
-// be selected; flags[i] = 1 for the others.  hist (K * kPrioBins, zero on entry)
-// is left zero.
+// Proposal prefilter (exact): a source's proposals in the priority bins after
+// the one where its cumulative weight reaches the excess can never be in its
+// minimal prefix.  keep[i] = 1 for listed node i (list/d_n1, flags from the
+// proposal kernel) when it proposes and is not in such a bin.  hist
+// (K * kPrioBins, zero on entry) is left zero.
 constexpr int kPrioBins = 256;
-void rebalance_prefilter(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
-                         const int32_t *part, const int8_t *over, const int64_t *C, int gbits, int cbits,
-                         uint64_t *keys, unsigned long long *hist, int32_t *cut, int32_t *flags, int64_t np_max,
-                         cudaStream_t s);
+void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
+                         const int32_t *flags, const int32_t *prop_gain, const int32_t *part, const int8_t *over,
+                         const int64_t *C, int gbits, int cbits, unsigned long long *hist, int32_t *cut,
+                         int32_t *keep, cudaStream_t s);
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                          int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s);
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,

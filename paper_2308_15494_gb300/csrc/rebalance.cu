@@ -458,19 +458,47 @@ __device__ __forceinline__ int prio_bin(uint64_t key, int gbits, int cbits) {
     return 128 + (int)(r < 127ull ? r : 127ull);
 }
 
-// Keys of the proposals and, per source block, their weight by bin.
-__global__ void k_prio_hist(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
-                            const int32_t *__restrict__ prop_gain, const int32_t *__restrict__ vwgt,
-                            const int32_t *__restrict__ part, int gbits, int cbits, uint64_t *__restrict__ keys,
-                            unsigned long long *__restrict__ hist) {
-    const int64_t cnt = *d_np;
-    UPR_FOR(i, cnt) {
-        const int32_t u = P[i];
+// Per source block, the weight of its proposals by bin.  The proposals are
+// the listed nodes with a set flag.  Each CTA sums into a small shared hash
+// table keyed by (block, bin) first (the weight piles up on a few bins of each
+// block), then adds its entries to the global histogram.
+constexpr int kHistSlots = 2048;
+constexpr uint32_t kHistEmpty = 0xffffffffu;
+
+__global__ void __launch_bounds__(256) k_prio_hist(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
+                                                   const int32_t *__restrict__ flags,
+                                                   const int32_t *__restrict__ prop_gain,
+                                                   const int32_t *__restrict__ vwgt, const int32_t *__restrict__ part,
+                                                   int gbits, int cbits, unsigned long long *__restrict__ hist) {
+    __shared__ uint32_t s_key[kHistSlots];
+    __shared__ unsigned long long s_val[kHistSlots];
+    for (int i = threadIdx.x; i < kHistSlots; i += blockDim.x) { s_key[i] = kHistEmpty; s_val[i] = 0; }
+    __syncthreads();
+    const int64_t n1 = *d_n1;
+    UPR_FOR(i, n1) {
+        if (!flags[i]) continue;
+        const int32_t u = list[i];
         const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
-        const uint64_t key = prio_key(prop_gain[u], c, gbits, cbits);
-        keys[i] = key;
-        atomicAdd(&hist[(int64_t)part[u] * kPrioBins + prio_bin(key, gbits, cbits)], (unsigned long long)c);
+        const uint32_t key = (uint32_t)part[u] * kPrioBins + prio_bin(prio_key(prop_gain[u], c, gbits, cbits), gbits, cbits);
+        uint32_t h = (key * 0x9E3779B1u) >> 21;          // 11 bits: kHistSlots
+        bool done = false;
+        for (int probe = 0; probe < 32 && !done; probe++) {
+            uint32_t cur = s_key[h];
+            if (cur == kHistEmpty) {
+                cur = atomicCAS(&s_key[h], kHistEmpty, key);
+                if (cur == kHistEmpty) cur = key;
+            }
+            if (cur == key) {
+                atomicAdd(&s_val[h], (unsigned long long)c);
+                done = true;
+            }
+            h = (h + 1) & (kHistSlots - 1);
+        }
+        if (!done) atomicAdd(&hist[key], (unsigned long long)c);   // crowded table: straight to the histogram
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHistSlots; i += blockDim.x)
+        if (s_key[i] != kHistEmpty) atomicAdd(&hist[s_key[i]], s_val[i]);
 }
 
 // Per overloaded source: the first bin where the cumulative weight reaches the
@@ -505,11 +533,21 @@ __global__ void __launch_bounds__(kPrioBins) k_prio_cut(int32_t K, const int8_t 
     }
 }
 
-__global__ void k_prio_keep(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
-                            const uint64_t *__restrict__ keys, const int32_t *__restrict__ part,
-                            const int32_t *__restrict__ cut, int gbits, int cbits, int32_t *__restrict__ flags) {
-    const int64_t cnt = *d_np;
-    UPR_FOR(i, cnt) flags[i] = prio_bin(keys[i], gbits, cbits) <= cut[part[P[i]]] ? 1 : 0;
+// keep[i]: listed node i proposes and its bin is not after its source's cut
+__global__ void k_prio_keep(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
+                            const int32_t *__restrict__ flags, const int32_t *__restrict__ prop_gain,
+                            const int32_t *__restrict__ vwgt, const int32_t *__restrict__ part,
+                            const int32_t *__restrict__ cut, int gbits, int cbits, int32_t *__restrict__ keep) {
+    const int64_t n1 = *d_n1;
+    UPR_FOR(i, n1) {
+        int32_t k = 0;
+        if (flags[i]) {
+            const int32_t u = list[i];
+            const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
+            k = prio_bin(prio_key(prop_gain[u], c, gbits, cbits), gbits, cbits) <= cut[part[u]] ? 1 : 0;
+        }
+        keep[i] = k;
+    }
 }
 
 // Block-id key (source or target) of the entries listed through idx/order.
@@ -705,16 +743,17 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
     rebalance_propose_scalar_list(g, list, d_n1, n1_max, part, W, st, prop_tgt, prop_gain, flags, s);
 }
 
-void rebalance_prefilter(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
-                         const int32_t *part, const int8_t *over, const int64_t *C, int gbits, int cbits,
-                         uint64_t *keys, unsigned long long *hist, int32_t *cut, int32_t *flags, int64_t np_max,
-                         cudaStream_t s) {
-    if (np_max <= 0) return;
-    k_prio_hist<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, part, gbits, cbits, keys, hist);
+void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
+                         const int32_t *flags, const int32_t *prop_gain, const int32_t *part, const int8_t *over,
+                         const int64_t *C, int gbits, int cbits, unsigned long long *hist, int32_t *cut,
+                         int32_t *keep, cudaStream_t s) {
+    if (n1_max <= 0) return;
+    const unsigned hist_grid = (unsigned)std::min<int64_t>(ceil_div(n1_max, 256), (int64_t)device_sm_count() * 4);
+    k_prio_hist<<<hist_grid, 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, gbits, cbits, hist);
     UPR_LAUNCH_CHECK();
     k_prio_cut<<<(unsigned)std::min<int64_t>(g.K(), 4096), kPrioBins, 0, s>>>(g.K(), over, C, g.Lb, hist, cut);
     UPR_LAUNCH_CHECK();
-    k_prio_keep<<<grid_for(np_max), 256, 0, s>>>(P, d_np, keys, part, cut, gbits, cbits, flags);
+    k_prio_keep<<<grid_for(n1_max), 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, cut, gbits, cbits, keep);
     UPR_LAUNCH_CHECK();
 }
 
