@@ -106,10 +106,16 @@ __device__ __forceinline__ BlockDelta make_block_delta(unsigned long long *smem,
 
 // Kernel attributes are per process and device, shared by every host thread:
 // a kernel's dynamic shared-memory limit is raised once to the device's
-// opt-in maximum (a ceiling only: occupancy follows the launch's actual size)
+// opt-in maximum less its static shared memory (a ceiling only: occupancy
+// follows the launch's actual size)
 // and its shared/L1 split set, never changed afterwards, so no thread can
 // lower a limit another thread's launch relies on.
 void kernel_setup(const void *func, int carveout_percent);   // engine.cu; -1 = no carveout preference
+// CTAs of `threads` threads with `shm` bytes of dynamic shared memory that fit
+// on one SM at once (at least 1), cached per kernel and size (engine.cu).
+int resident_ctas(const void *func, int threads, size_t shm);
+// A grid for `want` CTAs of a grid-stride kernel: at most one full wave.
+inline unsigned wave_grid(const void *func, int threads, size_t shm, int64_t want);
 
 inline int device_sm_count() {
     static thread_local int cnt = 0, dev_cached = -1;
@@ -120,6 +126,11 @@ inline int device_sm_count() {
         dev_cached = dev;
     }
     return cnt;
+}
+
+inline unsigned wave_grid(const void *func, int threads, size_t shm, int64_t want) {
+    const int64_t wave = (int64_t)device_sm_count() * resident_ctas(func, threads, shm);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, wave));
 }
 
 // 32-bit form of group_argmax.

@@ -8,9 +8,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
@@ -74,6 +76,22 @@ void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F)
 
 std::atomic<long long> upr::g_upr_launches{0};
 
+int upr::resident_ctas(const void *func, int threads, size_t shm) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    UPR_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, func, threads, shm);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    UPR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, shm));
+    n = std::max(n, 1);
+    cache[key] = n;
+    return n;
+}
+
 void upr::kernel_setup(const void *func, int carveout_percent) {
     static std::mutex mu;
     static std::set<std::pair<int, const void *>> done;
@@ -83,7 +101,10 @@ void upr::kernel_setup(const void *func, int carveout_percent) {
     if (done.count({dev, func})) return;
     int optin = 0;
     UPR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    UPR_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    cudaFuncAttributes fa;
+    UPR_CUDA(cudaFuncGetAttributes(&fa, func));     // static shared memory counts against the same limit
+    UPR_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes));
     if (carveout_percent >= 0)
         UPR_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent));
     done.insert({dev, func});
@@ -118,6 +139,7 @@ struct upr_ctx {
     LaneCfg reb_cfg{};
     int reb_body_kernels = 0;
     int64_t rounds_bound = 0;         // rounds run since the binding
+    bool cut_pending = false;         // the next build also computes the cut of part0 (load_part skipped it)
     bool reb_failed = false;          // capture or instantiation failed: host-driven loop
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
@@ -252,7 +274,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->ctl = A.take<RebalCtl>(1);
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
-    c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves
+    c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves, [3] twice the input cut
     c->tmp.tiles_cap = ceil_div(std::max<int64_t>((int64_t)n2 + 2, (int64_t)k + 2), 2048);   // lists of nodes, events, blocks
     c->tmp.mem_bytes = radix_temp_bytes(c->tmp.tiles_cap * 2048);
     c->tmp.scan_bytes = scan_temp_bytes(c->tmp.tiles_cap * 2048);
@@ -525,9 +547,11 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     const bool build = !c->table_valid || tr;
     c->table_valid = false;
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
-    if (build)
+    if (build) {
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
-                   c->tile_nodes, nullptr, s);
+                   c->tile_nodes, nullptr, s, c->cut_pending ? c->scal + 3 : nullptr, c->cut);
+        c->cut_pending = false;
+    }
     UPR_CUDA(cudaEventRecord(c->ev[1], s));
     UPR_CUDA(cudaEventRecord(c->ev[4], s));
     if (!rebalance_only) {
@@ -860,7 +884,9 @@ __global__ void k_part_to_local(const int32_t *part, const int32_t *part_in, con
     }
 }
 
-upr_status load_part(upr_ctx *c, const int32_t *part) {
+// need_cut = false: the cut is left to the first table build (one graph with
+// tiles, a round follows).
+upr_status load_part(upr_ctx *c, const int32_t *part, bool need_cut = true) {
     c->table_valid = false;
     copy_in(c->part0, part, sizeof(int32_t) * c->n, c->s);
     UPR_CUDA(cudaMemsetAsync(c->counts + 7, 0, sizeof(int32_t), c->s));
@@ -874,7 +900,8 @@ upr_status load_part(upr_ctx *c, const int32_t *part) {
         UPR_LAUNCH_CHECK();
     }
     block_weights(c->G, c->part0, c->C0, c->s);
-    edge_cut(c->G, c->part0, c->cut, c->s);
+    c->cut_pending = !need_cut;
+    if (need_cut) edge_cut(c->G, c->part0, c->cut, c->s);
     return UPR_OK;
 }
 
@@ -920,10 +947,13 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     const auto t_host0 = std::chrono::steady_clock::now();
     const long long launches0 = g_upr_launches.load();
     UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
-    upr_status rc = load_part(c, part);
+    // one graph: the first round's table build gives the cut (the edges are
+    // read once instead of twice)
+    const bool defer_cut = ng == 1 && rounds >= 1 && c->n_tiles > 0;
+    upr_status rc = load_part(c, part, !defer_cut);
     if (rc != UPR_OK) return rc;
     std::vector<int64_t> cin(ng), cout(ng), C0h(K);
-    read_i64(c, c->cut, ng, cin.data());
+    if (!defer_cut) read_i64(c, c->cut, ng, cin.data());
     read_i64(c, c->C0, K, C0h.data());
     st.cut_in = 0;
     for (int64_t x : cin) st.cut_in += x;
@@ -946,6 +976,11 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     }
     store_part(c, part, keep);
     read_i64(c, c->cut, ng, cout.data());
+    if (defer_cut) {
+        read_i64(c, c->scal + 3, 1, cin.data());
+        cin[0] /= 2;
+        st.cut_in = cin[0];
+    }
     st.cut_out = 0;
     for (int32_t g = 0; g < ng; g++) {
         if (keep[g]) cout[g] = cin[g];

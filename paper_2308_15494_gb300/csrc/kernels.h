@@ -176,8 +176,11 @@ size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
 // With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
+// With cut2 (one graph, tiles only): the build also sums twice the cut of part
+// (Sec. 2) into *cut2 and writes the cut to *cut.
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
-                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s);
+                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s,
+                int64_t *cut2 = nullptr, int64_t *cut = nullptr);
 // How moved hubs are found for the chunked delta update: through m_pos (moves
 // of M: from/to are M_from/M_to) or, when m_pos is null, through r_to/r_at
 // (moves of the current rebalancing sub-round: R indices in [*r_base,

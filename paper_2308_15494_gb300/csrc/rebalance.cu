@@ -694,15 +694,20 @@ template <int G, int CH>
 void launch_propose_vec(bool exact, bool batch, unsigned blocks, size_t shm, cudaStream_t s, const GraphDev &g,
                         const int32_t *list, const int32_t *d_n1, const int32_t *part, const int32_t *W,
                         const RebalState &st, int32_t *prop_tgt, int32_t *prop_gain, int32_t *flags) {
+    // one full wave of CTAs at most (the kernel loops over the list)
+    auto go = [&](auto kern) {
+        kern<<<wave_grid((const void *)kern, 256, shm, blocks), 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt,
+                                                                             prop_gain, flags);
+    };
     if constexpr (CH == 1 || (G == 32 && CH == 2)) {
         if (!exact) {
-            if (batch) k_propose_vec<G, CH, false, true><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
-            else k_propose_vec<G, CH, false, false><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
+            if (batch) go(k_propose_vec<G, CH, false, true>);
+            else go(k_propose_vec<G, CH, false, false>);
             return;
         }
     }
-    if (batch) k_propose_vec<G, CH, true, true><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
-    else k_propose_vec<G, CH, true, false><<<blocks, 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, flags);
+    if (batch) go(k_propose_vec<G, CH, true, true>);
+    else go(k_propose_vec<G, CH, true, false>);
 }
 
 }  // namespace

@@ -469,9 +469,8 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
         const int use_shared = shm <= 200 * 1024;
         if (use_shared && shm > 48 * 1024)
             kernel_setup((const void *)k_buckets, -1);
-        int64_t blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * (shm > 48 * 1024 ? 1 : 4));
-        if (!use_shared) blocks = std::min<int64_t>(ceil_div(g.n, 256), (int64_t)sm_count_sel() * 8);
-        k_buckets<<<(unsigned)blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, g.kmask, K,
+        const unsigned blocks = wave_grid((const void *)k_buckets, 256, use_shared ? shm : 0, ceil_div(g.n, 256));
+        k_buckets<<<blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, g.kmask, K,
                                                                       t_num, t_den, (unsigned long long *)BW,
                                                                       use_shared, avail_out, slot_out, g.sp);
         UPR_LAUNCH_CHECK();
@@ -507,15 +506,20 @@ template <int G, int CH>
 void launch_select_vec(bool exact, bool batch, unsigned blocks, size_t shm, cudaStream_t s, const GraphDev &g,
                        const int32_t *part, const int32_t *W, const Penalty &pen, int smem_pw, int32_t *cand_tgt,
                        int64_t *cand_s0, int32_t *cand_gain, int32_t *flags) {
+    // one full wave of CTAs at most (the kernel loops over the nodes)
+    auto go = [&](auto kern) {
+        kern<<<wave_grid((const void *)kern, 256, shm, blocks), 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt,
+                                                                             cand_s0, cand_gain, flags);
+    };
     if constexpr (CH == 1 || (G == 32 && CH == 2)) {
         if (!exact) {
-            if (batch) k_select_vec<G, CH, false, true><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
-            else k_select_vec<G, CH, false, false><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
+            if (batch) go(k_select_vec<G, CH, false, true>);
+            else go(k_select_vec<G, CH, false, false>);
             return;
         }
     }
-    if (batch) k_select_vec<G, CH, true, true><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
-    else k_select_vec<G, CH, true, false><<<blocks, 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt, cand_s0, cand_gain, flags);
+    if (batch) go(k_select_vec<G, CH, true, true>);
+    else go(k_select_vec<G, CH, true, false>);
 }
 
 }  // namespace

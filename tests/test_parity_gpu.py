@@ -146,6 +146,8 @@ def test_refine(upr, case):
     assert rc0 == oracle.OK
     assert np.array_equal(part, p0) and st.cut_out == c0
     assert st.cut_out <= st.cut_in
+    # the input cut (from the first table build when the graph has tiles)
+    assert st.cut_in == oracle.cut(case, case.part)[0]
 
 
 @pytest.mark.parametrize("builder,shrink", [("plain_tiny", 0), ("plain_large", 6), ("plain_weighted", 6)])
