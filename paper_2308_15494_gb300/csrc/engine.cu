@@ -165,7 +165,7 @@ struct upr_ctx {
     int32_t *cand_tgt, *cand_gain, *flags, *flags2, *excl_i, *m_pos, *r_to, *r_at, *pos, *dest, *prop_tgt, *prop_gain;
     int64_t *cand_s0;
     // lists
-    int32_t *idxA, *idxB, *idxC, *idxD, *L1;
+    int32_t *idxA, *idxB, *idxC, *idxD, *L1, *Pq;
     int64_t *score;
     int32_t *M_node, *M_from, *M_to; int64_t *M_score;
     int32_t *R_node, *R_from, *R_to, *R_sub;
@@ -184,7 +184,7 @@ struct upr_ctx {
     int32_t *prio_cut;               // [K]
     int32_t *counts;          // device counters (CNT_* slots)
     RebalCtl *ctl;            // rebalancing loop control block
-    uint64_t *vacc; int32_t *vflags; int64_t *scal;
+    uint64_t *vacc; int32_t *vflags; int64_t *scal, *cut_parts;
     Scratch tmp;              // scan / sort temporaries
     // pinned host mirrors
     int64_t *h = nullptr;     // pinned scratch
@@ -236,7 +236,7 @@ void layout(upr_ctx *c, Arena &A) {
     for (int32_t **p : {&c->cand_tgt, &c->cand_gain, &c->flags, &c->m_pos, &c->r_to, &c->pos, &c->dest, &c->prop_tgt,
                         &c->prop_gain, &c->idxA, &c->idxB, &c->idxC, &c->M_node, &c->M_from, &c->M_to, &c->R_node,
                         &c->R_from, &c->R_to, &c->R_sub, &c->I_node, &c->I_from, &c->I_to, &c->emit, &c->qbefore,
-                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs, &c->L1, &c->r_at})
+                        &c->em_excl, &c->pos_m, &c->hub_flag, &c->hub_excl, &c->hubs, &c->L1, &c->r_at, &c->Pq})
         *p = A.take<int32_t>(n);
     for (int32_t **p : {&c->flags2, &c->excl_i, &c->idxD, &c->X_node, &c->X_from, &c->X_to, &c->final_to})
         *p = A.take<int32_t>(n2 + 1);
@@ -274,7 +274,8 @@ void layout(upr_ctx *c, Arena &A) {
     c->ctl = A.take<RebalCtl>(1);
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
-    c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves, [3] twice the input cut
+    c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves
+    c->cut_parts = A.take<int64_t>(kCutParts + 1);   // twice the input cut: partial sums, total
     c->tmp.tiles_cap = ceil_div(std::max<int64_t>((int64_t)n2 + 2, (int64_t)k + 2), 2048);   // lists of nodes, events, blocks
     c->tmp.mem_bytes = radix_temp_bytes(c->tmp.tiles_cap * 2048);
     c->tmp.scan_bytes = scan_temp_bytes(c->tmp.tiles_cap * 2048);
@@ -412,18 +413,25 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     else
         rebalance_propose_list(G, c->L1, &ctl->n1_active, n, c->part, c->W, st, c->prop_tgt, c->prop_gain,
                                c->flags, c->prop_cfg, s);
+    // the proposers, in node order, are the next sub-round's list: a listed
+    // node without a proposal has no block with room for it (the lightest
+    // allowed block has the most room, and rooms only shrink), so it never
+    // proposes again
+    select_flags(c->flags, c->idxD, cnt + CNT_L1, Count{&ctl->n1_active, n}, c->tmp, s);
+    rebalance_gather_list(c->L1, c->idxD, cnt + CNT_L1, c->idxA, n, s);
+    rebalance_copy_list(c->idxA, cnt + CNT_L1, c->L1, n, s);
     // proposals that cannot be in their source's minimal prefix are dropped
     // before the ordering; P lists the others in node order
-    const int32_t *pflags = c->flags;
-    if (c->prio_hist) {
-        rebalance_prefilter(G, c->L1, &ctl->n1_active, n, c->flags, c->prop_gain, c->part, c->over_d, c->C,
-                            c->gbits, c->cbits, c->prio_hist, c->prio_cut, c->flags2, s);
-        pflags = c->flags2;
-    }
-    select_flags(pflags, c->idxD, cnt + CNT_P, Count{&ctl->n1_active, n}, c->tmp, s);
-    rebalance_gather_list(c->L1, c->idxD, cnt + CNT_P, c->idxA, n, s);
     const int32_t *Pn = c->idxA;
-    int32_t *dP = cnt + CNT_P;
+    int32_t *dP = cnt + CNT_L1;
+    if (c->prio_hist) {
+        rebalance_prefilter(G, c->idxA, cnt + CNT_L1, n, nullptr, c->prop_gain, c->part, c->over_d, c->C, c->gbits,
+                            c->cbits, c->prio_hist, c->prio_cut, c->flags2, s);
+        select_flags(c->flags2, c->idxD, cnt + CNT_P, Count{cnt + CNT_L1, n}, c->tmp, s);
+        rebalance_gather_list(c->idxA, c->idxD, cnt + CNT_P, c->Pq, n, s);
+        Pn = c->Pq;
+        dP = cnt + CNT_P;
+    }
     const Count cP{dP, n};
     uint64_t *kA; uint32_t *A;
     rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v, n, s);
@@ -549,7 +557,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
     if (build) {
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
-                   c->tile_nodes, nullptr, s, c->cut_pending ? c->scal + 3 : nullptr, c->cut);
+                   c->tile_nodes, nullptr, s, c->cut_pending ? c->cut_parts : nullptr, c->cut);
         c->cut_pending = false;
     }
     UPR_CUDA(cudaEventRecord(c->ev[1], s));
@@ -618,9 +626,10 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
             int32_t hc[CNT_SLOTS];
             UPR_CUDA(cudaMemcpy(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost));
             const auto t1 = std::chrono::steady_clock::now();
-            fprintf(stderr, "upr round %d sub-round %d: listed %d active %d proposals kept %d selected %d "
+            fprintf(stderr, "upr round %d sub-round %d: listed %d proposals %d kept %d selected %d "
                             "admitted %d (%.3f ms)\n",
-                    r, h, hc[CNT_L1], c->hctl->n1_active, hc[CNT_P], hc[CNT_S], hc[CNT_A],
+                    r, h, c->hctl->n1_active, hc[CNT_L1], c->prio_hist ? hc[CNT_P] : hc[CNT_L1], hc[CNT_S],
+                    hc[CNT_A],
                     std::chrono::duration<double, std::milli>(t1 - t_sub).count());
             t_sub = std::chrono::steady_clock::now();
         }
@@ -977,7 +986,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     store_part(c, part, keep);
     read_i64(c, c->cut, ng, cout.data());
     if (defer_cut) {
-        read_i64(c, c->scal + 3, 1, cin.data());
+        read_i64(c, c->cut_parts + kCutParts, 1, cin.data());
         cin[0] /= 2;
         st.cut_in = cin[0];
     }

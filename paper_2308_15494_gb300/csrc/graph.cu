@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         if (threadIdx.x == 0) {
             long long tot = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_part[w];
-            if (tot) atomicAdd(cut2, (unsigned long long)tot);
+            if (tot) atomicAdd(&cut2[blockIdx.x % kCutParts], (unsigned long long)tot);
         }
     }
     if (sp.on()) {
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
             long long tot = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_part[w];
             tot -= s_row[blk_local(part[ch.v], k, kmask)];
-            if (tot) atomicAdd(cut2, (unsigned long long)tot);
+            if (tot) atomicAdd(&cut2[blockIdx.x % kCutParts], (unsigned long long)tot);
         }
     }
     if (sp.on()) {
@@ -549,8 +549,21 @@ size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap) {
     return sparse_buf_cap > 0 ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * (size_t)sparse_buf_cap : rows;
 }
 
-__global__ void k_half_cut(const unsigned long long *__restrict__ cut2, int64_t *__restrict__ cut) {
-    if (threadIdx.x == 0) cut[0] = (int64_t)(*cut2 / 2);
+// cut2[0 .. kCutParts): partial sums (spread over many words so that the
+// tiles' atomics do not queue on one address); cut2[kCutParts] = their total.
+__global__ void __launch_bounds__(kCutParts) k_half_cut(unsigned long long *__restrict__ cut2,
+                                                        int64_t *__restrict__ cut) {
+    __shared__ unsigned long long s_w[kCutParts / 32];
+    unsigned long long v = cut2[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kCutParts / 32; w++) t += s_w[w];
+        cut2[kCutParts] = t;
+        cut[0] = (int64_t)(t / 2);
+    }
 }
 
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
@@ -560,7 +573,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
     unsigned long long *c2 = nullptr;
     if (cut2) {
         if (!(tiles && n_tiles > 0 && g.ng == 1)) throw CudaError{cudaErrorInvalidValue, "gain_table: cut needs tiles"};
-        UPR_CUDA(cudaMemsetAsync(cut2, 0, sizeof(int64_t), s));
+        UPR_CUDA(cudaMemsetAsync(cut2, 0, sizeof(int64_t) * (kCutParts + 1), s));
         c2 = reinterpret_cast<unsigned long long *>(cut2);
     }
     if (tiles && n_tiles > 0) {
@@ -615,7 +628,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
         UPR_LAUNCH_CHECK();
     }
     if (c2) {
-        k_half_cut<<<1, 32, 0, s>>>(c2, cut);
+        k_half_cut<<<1, kCutParts, 0, s>>>(c2, cut);
         UPR_LAUNCH_CHECK();
     }
 }
@@ -624,7 +637,9 @@ void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32
                 const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
                 const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s) {
     if (max_count <= 0) return;
-    const unsigned blocks = wave_grid((const void *)k_table_move, 256, 0, ceil_div(max_count * 32, 256));
+    // two waves of CTAs: warps of the second wave take over from those of the
+    // first as they finish (moved nodes differ widely in degree)
+    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
     k_table_move<<<blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, g.kmask, W, nodes, from, to, d_count,
                                                   d_offset, deg_sum, g.m, g.sp);
     UPR_LAUNCH_CHECK();

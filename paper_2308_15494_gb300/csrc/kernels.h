@@ -176,8 +176,9 @@ size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
 // With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
-// With cut2 (one graph, tiles only): the build also sums twice the cut of part
-// (Sec. 2) into *cut2 and writes the cut to *cut.
+// With cut2 (kCutParts + 1 words; one graph, tiles only): the build also sums
+// twice the cut of part (Sec. 2) into cut2[kCutParts] and writes the cut to *cut.
+constexpr int kCutParts = 256;
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
                 const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s,
                 int64_t *cut2 = nullptr, int64_t *cut = nullptr);
@@ -260,6 +261,8 @@ struct RebalState {
 };
 // flags[v] = 1 for the nodes of the marked blocks
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s);
+// dst[i] = src[i] for i < *d_cnt
+void rebalance_copy_list(const int32_t *src, const int32_t *d_cnt, int32_t *dst, int64_t cnt_max, cudaStream_t s);
 void rebalance_gather_list(const int32_t *list, const int32_t *pos, const int32_t *d_cnt, int32_t *out, int64_t cnt_max,
                            cudaStream_t s);
 // Proposals of the listed nodes in overloaded blocks: prop_tgt/prop_gain by node, flags by list position.
@@ -271,9 +274,9 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
                             int32_t *prop_gain, int32_t *flags, LaneCfg cfg, cudaStream_t s);
 // Proposal prefilter (exact): a source's proposals in the priority bins after
 // the one where its cumulative weight reaches the excess can never be in its
-// minimal prefix.  keep[i] = 1 for listed node i (list/d_n1, flags from the
-// proposal kernel) when it proposes and is not in such a bin.  hist
-// (K * kPrioBins, zero on entry) is left zero.
+// minimal prefix.  keep[i] = 1 for listed node i (list/d_n1; flags from the
+// proposal kernel, or null when every listed node proposes) when it proposes
+// and is not in such a bin.  hist (K * kPrioBins, zero on entry) is left zero.
 constexpr int kPrioBins = 256;
 void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                          const int32_t *flags, const int32_t *prop_gain, const int32_t *part, const int8_t *over,

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(256) k_prio_hist(const int32_t *__restrict__ l
     __syncthreads();
     const int64_t n1 = *d_n1;
     UPR_FOR(i, n1) {
-        if (!flags[i]) continue;
+        if (flags && !flags[i]) continue;
         const int32_t u = list[i];
         const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
         const uint32_t key = (uint32_t)part[u] * kPrioBins + prio_bin(prio_key(prop_gain[u], c, gbits, cbits), gbits, cbits);
@@ -541,7 +541,7 @@ __global__ void k_prio_keep(const int32_t *__restrict__ list, const int32_t *__r
     const int64_t n1 = *d_n1;
     UPR_FOR(i, n1) {
         int32_t k = 0;
-        if (flags[i]) {
+        if (!flags || flags[i]) {
             const int32_t u = list[i];
             const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
             k = prio_bin(prio_key(prop_gain[u], c, gbits, cbits), gbits, cbits) <= cut[part[u]] ? 1 : 0;
@@ -678,6 +678,18 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
     k_flag_in_blocks<<<grid1(n), 256, 0, s>>>(part, n, mark, flags);
+    UPR_LAUNCH_CHECK();
+}
+
+__global__ void k_copy_list(const int32_t *__restrict__ src, const int32_t *__restrict__ d_cnt,
+                            int32_t *__restrict__ dst) {
+    const int64_t cnt = *d_cnt;
+    UPR_FOR(i, cnt) dst[i] = src[i];
+}
+
+void rebalance_copy_list(const int32_t *src, const int32_t *d_cnt, int32_t *dst, int64_t cnt_max, cudaStream_t s) {
+    if (cnt_max <= 0) return;
+    k_copy_list<<<grid_for(cnt_max), 256, 0, s>>>(src, d_cnt, dst);
     UPR_LAUNCH_CHECK();
 }
 

@@ -802,7 +802,9 @@ void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int3
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
                int64_t *gain, const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s) {
-    const unsigned blocks = wave_grid((const void *)k_gains_warp, 256, 0, ceil_div(max * 32, 256));
+    // two waves of CTAs (moved nodes differ widely in degree)
+    const unsigned blocks = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16));
     k_gains_warp<<<blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to,
                                                                        d_nI, pos, dest, part0, gain);
     UPR_LAUNCH_CHECK();
@@ -855,7 +857,7 @@ void table_rollback(const GraphDev &g, const Rollback &rb, int64_t max, const in
     if (max <= 0) return;
     k_rollback_degsum<<<grid_for(max), 256, 0, s>>>(rb, g.xadj, (unsigned long long *)deg_sum);
     UPR_LAUNCH_CHECK();
-    const unsigned blocks = wave_grid((const void *)k_table_rollback, 256, 0, ceil_div(max * 32, 256));
+    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16);
     k_table_rollback<<<blocks, 256, 0, s>>>(rb, g.xadj, g.adj, g.adjw, g.k, g.kmask, W, deg_sum, g.m,
                                                       g.sp);
     UPR_LAUNCH_CHECK();
