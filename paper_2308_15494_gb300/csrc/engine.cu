@@ -185,6 +185,7 @@ struct upr_ctx {
     int32_t *counts;          // device counters (CNT_* slots)
     RebalCtl *ctl;            // rebalancing loop control block
     uint64_t *vacc; int32_t *vflags; int64_t *scal, *cut_parts;
+    int2 *pk;                 // exact gains: position in I and blocks before/after, per node
     Scratch tmp;              // scan / sort temporaries
     // pinned host mirrors
     int64_t *h = nullptr;     // pinned scratch
@@ -276,6 +277,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->vflags = A.take<int32_t>(2);
     c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves
     c->cut_parts = A.take<int64_t>(kCutParts + 1);   // twice the input cut: partial sums, total
+    c->pk = A.take<int2>(n);
     c->tmp.tiles_cap = ceil_div(std::max<int64_t>((int64_t)n2 + 2, (int64_t)k + 2), 2048);   // lists of nodes, events, blocks
     c->tmp.mem_bytes = radix_temp_bytes(c->tmp.tiles_cap * 2048);
     c->tmp.scan_bytes = scan_temp_bytes(c->tmp.tiles_cap * 2048);
@@ -685,7 +687,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     }
 
     // ---- (c2) exact gains, balanced prefixes, best prefix
-    seq_gains(G, Iv, If, It, dI, n, c->pos, c->dest, c->part0, c->I_gain, c->hub_chunks, c->n_chunks, s);
+    seq_gains(G, Iv, If, It, dI, n, c->part0, c->pk, c->I_gain, c->hub_chunks, c->n_chunks, s);
     inclusive_sum_i64(c->I_gain, c->Gsum, Count{dI, n}, c->tmp, s);
     count_affine(dI, 2, nullptr, 0, cnt + CNT_EVI, s);
     count_affine(dI, 1, nullptr, 1, cnt + CNT_I1, s);

@@ -346,9 +346,10 @@ void seq_merge_flags(const int32_t *X_node, const int32_t *X_to, const int8_t *X
 void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int32_t *X_node, const int32_t *final_to,
                  const int32_t *part0, int32_t *I_node, int32_t *I_from, int32_t *I_to, int32_t *pos, int32_t *dest,
                  cudaStream_t s);
+// pk: n words of scratch (each node's position in I and blocks before/after)
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
-               const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
-               int64_t *gain, const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s);
+               const int32_t *d_nI, int64_t max, const int32_t *part0, int2 *pk, int64_t *gain,
+               const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s);
 void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, const int32_t *d_nI, int64_t max, uint64_t *keys,
                   uint32_t *vals, cudaStream_t s);
 void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,

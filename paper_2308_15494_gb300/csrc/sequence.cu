@@ -239,17 +239,46 @@ __global__ void k_build_I(const int32_t *__restrict__ Ix, const int32_t *__restr
 // Exact gain of the i-th move of I: neighbours moved earlier in I count in
 // their new block, all others in their round-start block.  Warp per move;
 // hub moves (degree > kHubDegree) are left to k_gains_hub.
+// Block of each node at every step of I, packed for one 8-byte gather per
+// adjacency entry: x = the node's position in I (INT32_MAX when it does not
+// move), y = (local block before its move) | (local block after it) << 16.
+// Before step i a neighbour u is in its later block iff x < i.
+__global__ void k_pk_fill(const int32_t *__restrict__ part0, int64_t n, int32_t k, int32_t kmask,
+                          int2 *__restrict__ pk) {
+    UPR_FOR(u, n) {
+        const uint32_t l = (uint32_t)blk_local(part0[u], k, kmask);
+        pk[u] = make_int2(INT32_MAX, (int32_t)(l | (l << 16)));
+    }
+}
+
+__global__ void k_pk_moves(const int32_t *__restrict__ I_node, const int32_t *__restrict__ I_from,
+                           const int32_t *__restrict__ I_to, const int32_t *__restrict__ d_nI, int32_t k,
+                           int32_t kmask, int2 *__restrict__ pk) {
+    const int64_t nI = *d_nI;
+    UPR_FOR(i, nI) {
+        const uint32_t a = (uint32_t)blk_local(I_from[i], k, kmask), b = (uint32_t)blk_local(I_to[i], k, kmask);
+        pk[I_node[i]] = make_int2((int32_t)i, (int32_t)(a | (b << 16)));
+    }
+}
+
+__device__ __forceinline__ uint32_t block_before(int2 p, int64_t i) {
+    const uint32_t code = (uint32_t)p.y;
+    return p.x < i ? (code >> 16) : (code & 0xffffu);
+}
+
+// Exact gain of every move of I against the partition just before it (Sec.
+// 4.4): warp per move, hubs (degree > kHubDegree) are left to the chunk kernel.
 __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                              const int32_t *__restrict__ adjw, const int32_t *__restrict__ I_node,
                              const int32_t *__restrict__ I_from, const int32_t *__restrict__ I_to,
-                             const int32_t *__restrict__ d_nI, const int32_t *__restrict__ pos,
-                             const int32_t *__restrict__ dest, const int32_t *__restrict__ part0,
+                             const int32_t *__restrict__ d_nI, const int2 *__restrict__ pk, int32_t k, int32_t kmask,
                              int64_t *__restrict__ gain) {
     const int lane = threadIdx.x & 31;
     const int64_t nI = *d_nI;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nI;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int32_t v = I_node[i], a = I_from[i], b = I_to[i];
+        const int32_t v = I_node[i];
+        const uint32_t a = (uint32_t)blk_local(I_from[i], k, kmask), b = (uint32_t)blk_local(I_to[i], k, kmask);
         const int64_t e0 = xadj[v], e1 = xadj[v + 1];
         if (e1 - e0 > kHubDegree) {
             if (lane == 0) gain[i] = 0;
@@ -257,8 +286,7 @@ __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__
         }
         long long acc = 0;
         for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int32_t u = adj[e];
-            const int32_t bu = pos[u] < i ? dest[u] : part0[u];
+            const uint32_t bu = block_before(pk[adj[e]], i);
             const int32_t w = adjw ? adjw[e] : 1;
             acc += (bu == b ? w : 0) - (bu == a ? w : 0);
         }
@@ -273,20 +301,17 @@ __global__ void k_gains_warp(const int64_t *__restrict__ xadj, const int32_t *__
 __global__ void __launch_bounds__(512) k_gains_hub_chunks(const HubChunk *__restrict__ chunks,
                                                           const int32_t *__restrict__ adj,
                                                           const int32_t *__restrict__ adjw,
-                                                          const int32_t *__restrict__ I_from,
-                                                          const int32_t *__restrict__ I_to,
-                                                          const int32_t *__restrict__ pos,
-                                                          const int32_t *__restrict__ dest,
-                                                          const int32_t *__restrict__ part0, int64_t *__restrict__ gain) {
+                                                          const int2 *__restrict__ pk,
+                                                          int64_t *__restrict__ gain) {
     __shared__ long long s_w[16];
     const HubChunk ch = chunks[blockIdx.x];
-    const int32_t i = pos[ch.v];
+    const int2 me = pk[ch.v];
+    const int32_t i = me.x;
     if (i == INT32_MAX) return;                  // this hub is not in I
-    const int32_t a = I_from[i], b = I_to[i];
+    const uint32_t a = (uint32_t)me.y & 0xffffu, b = (uint32_t)me.y >> 16;
     long long acc = 0;
     for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
-        const int32_t u = adj[e];
-        const int32_t bu = pos[u] < i ? dest[u] : part0[u];
+        const uint32_t bu = block_before(pk[adj[e]], i);
         const int32_t w = adjw ? adjw[e] : 1;
         acc += (bu == b ? w : 0) - (bu == a ? w : 0);
     }
@@ -800,17 +825,19 @@ void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int3
 }
 
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
-               const int32_t *d_nI, int64_t max, const int32_t *pos, const int32_t *dest, const int32_t *part0,
-               int64_t *gain, const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s) {
+               const int32_t *d_nI, int64_t max, const int32_t *part0, int2 *pk, int64_t *gain,
+               const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s) {
+    k_pk_fill<<<grid_for(g.n), 256, 0, s>>>(part0, g.n, g.k, g.kmask, pk);
+    UPR_LAUNCH_CHECK();
+    k_pk_moves<<<grid_for(max), 256, 0, s>>>(I_node, I_from, I_to, d_nI, g.k, g.kmask, pk);
+    UPR_LAUNCH_CHECK();
     // two waves of CTAs (moved nodes differ widely in degree)
     const unsigned blocks = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(ceil_div(max * 32, 256), (int64_t)device_sm_count() * 16));
-    k_gains_warp<<<blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to,
-                                                                       d_nI, pos, dest, part0, gain);
+    k_gains_warp<<<blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, I_node, I_from, I_to, d_nI, pk, g.k, g.kmask, gain);
     UPR_LAUNCH_CHECK();
     if (n_chunks > 0) {
-        k_gains_hub_chunks<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, I_from, I_to, pos, dest, part0,
-                                                              gain);
+        k_gains_hub_chunks<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, pk, gain);
         UPR_LAUNCH_CHECK();
     }
 }
