@@ -426,7 +426,8 @@ __global__ void k_reb_end_batch(const int64_t *__restrict__ C, const int64_t *__
 __device__ __forceinline__ uint64_t prio_key(int64_t g, uint64_t c, int gbits, int cbits) {
     const int S = 2 * cbits;
     if (g >= 0) return ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
-    return (1ull << (gbits + S)) | ((((uint64_t)(-g)) << S) / c);
+    const uint64_t num = ((uint64_t)(-g)) << S;
+    return (1ull << (gbits + S)) | (c == 1 ? num : num / c);     // unit weights need no division
 }
 
 __global__ void k_prio_keys(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,

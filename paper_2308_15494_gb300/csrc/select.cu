@@ -32,20 +32,22 @@ void ensure_pow3() {
     done_dev = dev;
 }
 
-// (3/2)^s * c >= omega, exactly.
-__device__ __forceinline__ bool slot_ok(int s, uint64_t omega, uint64_t c) {
-    if (s >= 0) return (u128)c_pow3[s] * c >= ((u128)omega << s);
-    return ((u128)c << (-s)) >= (u128)c_pow3[-s] * omega;
+// (3/2)^s * c >= omega, exactly (p3 = the powers of 3, in shared memory).
+__device__ __forceinline__ bool slot_ok(int s, uint64_t omega, uint64_t c, const uint64_t *p3) {
+    if (s >= 0) return (u128)p3[s] * c >= ((u128)omega << s);
+    return ((u128)c << (-s)) >= (u128)p3[-s] * omega;
 }
 
 // Smallest s in [kSlotLo, kSlotHi] with (3/2)^s >= omega / c (kSlotHi if none).
-__device__ __forceinline__ int slot_of(uint64_t omega, uint64_t c) {
-    int lo = kSlotLo, hi = kSlotHi;
-    while (lo < hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        if (slot_ok(mid, omega, c)) hi = mid; else lo = mid + 1;
-    }
-    return lo;
+// A single-precision logarithm gives a first guess; the exact test, monotone
+// in s, then moves it to the answer (one or two tests in practice).
+__device__ __forceinline__ int slot_of(uint64_t omega, uint64_t c, const uint64_t *p3) {
+    if (omega == 0) return kSlotLo;
+    const float guess = (log2f((float)omega) - log2f((float)c)) * 1.7095113f;   // 1 / log2(3/2)
+    int s = guess > (float)kSlotHi ? kSlotHi : guess < (float)kSlotLo ? kSlotLo : (int)ceilf(guess);
+    while (s > kSlotLo && slot_ok(s - 1, omega, c, p3)) s--;
+    while (s < kSlotHi && !slot_ok(s, omega, c, p3)) s++;
+    return s;
 }
 
 // Penalty of moving weight cu into block b that would then exceed L_max by x;
@@ -77,7 +79,10 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
                           int use_shared, int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out,
                           SparseRows sp) {
     extern __shared__ unsigned long long s_bw[];
+    __shared__ uint64_t s_p3[41];
+    for (int i = threadIdx.x; i < 41; i += blockDim.x) s_p3[i] = c_pow3[i];
     const int bins = K * kSlots;
+    __syncthreads();
     if (use_shared) {
         for (int i = threadIdx.x; i < bins; i += blockDim.x) s_bw[i] = 0;
         __syncthreads();
@@ -87,7 +92,7 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
         const int64_t own = sp.on() ? sp_get(sp, v, blk_local(a, k, kmask)) : W[v * (int64_t)k + blk_local(a, k, kmask)];
         const int64_t c = vwgt ? vwgt[v] : 1;
         const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wI[v];
-        const int s = slot_of((uint64_t)own, (uint64_t)c);
+        const int s = slot_of((uint64_t)own, (uint64_t)c, s_p3);
         if (av) {
             unsigned long long *dst = use_shared ? s_bw : BW;
             atomicAdd(&dst[a * kSlots + (s - kSlotLo)], (unsigned long long)c);
