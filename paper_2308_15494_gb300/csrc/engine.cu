@@ -557,17 +557,18 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     const bool build = !c->table_valid || tr;
     c->table_valid = false;
     UPR_CUDA(cudaEventRecord(c->ev[0], s));
-    if (build) {
+    if (build)
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
-                   c->tile_nodes, nullptr, s, c->cut_pending ? c->cut_parts : nullptr, c->cut);
-        c->cut_pending = false;
-    }
+                   c->tile_nodes, nullptr, s);
     UPR_CUDA(cudaEventRecord(c->ev[1], s));
     UPR_CUDA(cudaEventRecord(c->ev[4], s));
     if (!rebalance_only) {
         // ---- (b1) availability, slots, bucket weights; F_r
+        // (the first round of a call also sums the input cut here)
         buckets(G, c->part0, c->W, c->prm.t_num, c->prm.t_den, c->BW, c->PW, c->first_slot,
-                tr ? tr->avail_d : nullptr, tr ? tr->slot_d : nullptr, s);
+                tr ? tr->avail_d : nullptr, tr ? tr->slot_d : nullptr, s, c->cut_pending ? c->cut_parts : nullptr,
+                c->cut);
+        c->cut_pending = false;
         penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
         UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
         Penalty pen{c->PW, c->F, c->C0, c->Lb, c->first_slot};
@@ -895,8 +896,8 @@ __global__ void k_part_to_local(const int32_t *part, const int32_t *part_in, con
     }
 }
 
-// need_cut = false: the cut is left to the first table build (one graph with
-// tiles, a round follows).
+// need_cut = false: the cut is left to the first round's bucket pass (one
+// graph, a refinement round follows).
 upr_status load_part(upr_ctx *c, const int32_t *part, bool need_cut = true) {
     c->table_valid = false;
     copy_in(c->part0, part, sizeof(int32_t) * c->n, c->s);
@@ -958,14 +959,24 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     const auto t_host0 = std::chrono::steady_clock::now();
     const long long launches0 = g_upr_launches.load();
     UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
-    // one graph: the first round's table build gives the cut (the edges are
-    // read once instead of twice)
-    const bool defer_cut = ng == 1 && rounds >= 1 && c->n_tiles > 0;
+    // one graph with a balanced input: the first round's bucket pass, which
+    // reads omega(v, V_P(v)) and omega(I(v)) of every node anyway, gives the
+    // cut, instead of a pass over the edges
+    bool defer_cut = ng == 1 && rounds >= 1;
     upr_status rc = load_part(c, part, !defer_cut);
     if (rc != UPR_OK) return rc;
     std::vector<int64_t> cin(ng), cout(ng), C0h(K);
-    if (!defer_cut) read_i64(c, c->cut, ng, cin.data());
     read_i64(c, c->C0, K, C0h.data());
+    if (defer_cut) {
+        bool bal = true;
+        for (int32_t b = 0; b < K; b++) bal = bal && C0h[b] <= c->Lmax_g[b / c->k];
+        if (!bal) {             // the repair round comes first and has no bucket pass
+            edge_cut(c->G, c->part0, c->cut, c->s);
+            c->cut_pending = false;
+            defer_cut = false;
+        }
+    }
+    if (!defer_cut) read_i64(c, c->cut, ng, cin.data());
     st.cut_in = 0;
     for (int64_t x : cin) st.cut_in += x;
     bool balanced = true;

@@ -211,8 +211,7 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
                                                         const int32_t *__restrict__ adjw,
                                                         const int32_t *__restrict__ part, int32_t k, int32_t kmask,
                                                         int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
-                                                        int64_t m, SparseRows sp, const int32_t *__restrict__ wI,
-                                                        unsigned long long *__restrict__ cut2) {
+                                                        int64_t m, SparseRows sp) {
     if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
     extern __shared__ int4 s_raw[];
     const TableTile t = tiles[blockIdx.x];
@@ -270,26 +269,6 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         }
     }
     __syncthreads();
-    if (cut2) {
-        // twice the cut (Sec. 2), row by row: the weight of v's edges into
-        // other blocks is omega(I(v)) - omega(v, V_P(v)); hub rows are summed
-        // by the chunk pass
-        __shared__ long long s_part[8];
-        long long acc = 0;
-        for (int r = threadIdx.x; r < nn; r += blockDim.x) {
-            if (s_x[r + 1] - s_x[r] > kHubDegree) continue;
-            const int64_t v = t.v0 + r;
-            acc += (long long)wI[v] - rows[r * k + tile_col<LOCAL>(part[v], k, kmask)];
-        }
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_part[w];
-            if (tot) atomicAdd(&cut2[blockIdx.x % kCutParts], (unsigned long long)tot);
-        }
-    }
     if (sp.on()) {
         // sparse table: a warp per row fills the row's slots in its own shared
         // buffer (each non-zero column is claimed once, by the lane that holds
@@ -333,32 +312,15 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
                                                           const int32_t *__restrict__ part, int32_t k,
                                                           int32_t kmask, int32_t *__restrict__ W,
                                                           const int64_t *__restrict__ deg_sum, int64_t m,
-                                                          SparseRows sp, unsigned long long *__restrict__ cut2) {
+                                                          SparseRows sp) {
     if (deg_sum && *deg_sum * 4 < m) return;
     extern __shared__ int s_row[];
     const HubChunk ch = chunks[blockIdx.x];
     for (int b = threadIdx.x; b < k; b += blockDim.x) s_row[b] = 0;
     __syncthreads();
-    long long tw = 0;
-    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
-        const int32_t w = adjw ? adjw[e] : 1;
-        atomicAdd(&s_row[blk_local(part[adj[e]], k, kmask)], w);
-        tw += w;
-    }
+    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x)
+        atomicAdd(&s_row[blk_local(part[adj[e]], k, kmask)], adjw ? adjw[e] : 1);
     __syncthreads();
-    if (cut2) {
-        // the chunk's share of twice the cut: its weight outside the hub's block
-        __shared__ long long s_part[16];
-        tw = warp_sum(tw);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = tw;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += s_part[w];
-            tot -= s_row[blk_local(part[ch.v], k, kmask)];
-            if (tot) atomicAdd(&cut2[blockIdx.x % kCutParts], (unsigned long long)tot);
-        }
-    }
     if (sp.on()) {
         for (int b = threadIdx.x; b < k; b += blockDim.x)
             if (s_row[b]) sp_add(sp, ch.v, b, s_row[b]);
@@ -549,33 +511,9 @@ size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap) {
     return sparse_buf_cap > 0 ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * (size_t)sparse_buf_cap : rows;
 }
 
-// cut2[0 .. kCutParts): partial sums (spread over many words so that the
-// tiles' atomics do not queue on one address); cut2[kCutParts] = their total.
-__global__ void __launch_bounds__(kCutParts) k_half_cut(unsigned long long *__restrict__ cut2,
-                                                        int64_t *__restrict__ cut) {
-    __shared__ unsigned long long s_w[kCutParts / 32];
-    unsigned long long v = cut2[threadIdx.x];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < kCutParts / 32; w++) t += s_w[w];
-        cut2[kCutParts] = t;
-        cut[0] = (int64_t)(t / 2);
-    }
-}
-
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
-                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s,
-                int64_t *cut2, int64_t *cut) {
+                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s) {
     if (g.n == 0) return;
-    unsigned long long *c2 = nullptr;
-    if (cut2) {
-        if (!(tiles && n_tiles > 0 && g.ng == 1)) throw CudaError{cudaErrorInvalidValue, "gain_table: cut needs tiles"};
-        UPR_CUDA(cudaMemsetAsync(cut2, 0, sizeof(int64_t) * (kCutParts + 1), s));
-        c2 = reinterpret_cast<unsigned long long *>(cut2);
-    }
     if (tiles && n_tiles > 0) {
         const size_t shm = table_tile_smem(g.k, tile_nodes, g.sp.on() ? g.sp.buf_cap : 0);
         const int local = g.ng == 1 ? 0 : g.kmask ? 1 : 2;
@@ -584,7 +522,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
             // the gathers of part[] need the L1 more than extra CTAs
             kernel_setup((const void *)kern, 64);
             kern<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum,
-                                                     g.m, g.sp, g.wI, c2);
+                                                     g.m, g.sp);
         };
         // 16 entries in flight per thread (8 with weights); the default
         // shared/L1 split: a smaller L1 slows the gathers of part[] down
@@ -624,11 +562,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
     }
     if (n_chunks > 0) {
         k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k,
-                                                                             g.kmask, W, deg_sum, g.m, g.sp, c2);
-        UPR_LAUNCH_CHECK();
-    }
-    if (c2) {
-        k_half_cut<<<1, kCutParts, 0, s>>>(c2, cut);
+                                                                             g.kmask, W, deg_sum, g.m, g.sp);
         UPR_LAUNCH_CHECK();
     }
 }
@@ -637,10 +571,8 @@ void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32
                 const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
                 const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s) {
     if (max_count <= 0) return;
-    // two waves of CTAs: warps of the second wave take over from those of the
-    // first as they finish (moved nodes differ widely in degree)
-    const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
-    k_table_move<<<blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, g.kmask, W, nodes, from, to, d_count,
+    int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
+    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, g.kmask, W, nodes, from, to, d_count,
                                                   d_offset, deg_sum, g.m, g.sp);
     UPR_LAUNCH_CHECK();
     if (n_chunks > 0) {

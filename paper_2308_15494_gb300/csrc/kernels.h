@@ -176,12 +176,8 @@ size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
 // With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
-// With cut2 (kCutParts + 1 words; one graph, tiles only): the build also sums
-// twice the cut of part (Sec. 2) into cut2[kCutParts] and writes the cut to *cut.
-constexpr int kCutParts = 256;
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
-                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s,
-                int64_t *cut2 = nullptr, int64_t *cut = nullptr);
+                const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s);
 // How moved hubs are found for the chunked delta update: through m_pos (moves
 // of M: from/to are M_from/M_to) or, when m_pos is null, through r_to/r_at
 // (moves of the current rebalancing sub-round: R indices in [*r_base,
@@ -215,8 +211,13 @@ struct Penalty {
     const int64_t *Lb;    // [K] L_max of each block's graph
     const int8_t *first;  // [K] smallest slot l with PW[b][l] >= 1, -1 if none (the excess-1 case)
 };
+// With cut2 (kCutParts + 1 words; one graph): also sums twice the cut of part
+// (Sec. 2: the sum over v of omega(I(v)) - omega(v, V_P(v))) into
+// cut2[kCutParts] and writes the cut to *cut.
+constexpr int kCutParts = 256;
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
-             int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s);
+             int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s,
+             int64_t *cut2 = nullptr, int64_t *cut = nullptr);
 // Lanes per node (G) and 16-byte chunks per lane (CH) of the vectorised
 // selection and proposal kernels (k % 4 == 0, k <= 256, 4*G*CH >= k).  A
 // schedule only decides how the work is spread over lanes, never the

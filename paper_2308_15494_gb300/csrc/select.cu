@@ -77,7 +77,7 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
                           const int32_t *__restrict__ wI, const int32_t *__restrict__ vwgt, int64_t n, int32_t k,
                           int32_t kmask, int32_t K, int32_t t_num, int32_t t_den, unsigned long long *__restrict__ BW,
                           int use_shared, int8_t *__restrict__ avail_out, int32_t *__restrict__ slot_out,
-                          SparseRows sp) {
+                          SparseRows sp, unsigned long long *__restrict__ cut2) {
     extern __shared__ unsigned long long s_bw[];
     __shared__ uint64_t s_p3[41];
     for (int i = threadIdx.x; i < 41; i += blockDim.x) s_p3[i] = c_pow3[i];
@@ -87,11 +87,13 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
         for (int i = threadIdx.x; i < bins; i += blockDim.x) s_bw[i] = 0;
         __syncthreads();
     }
+    long long out_w = 0;      // weight of the edges leaving v's block, summed over this thread's nodes
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = part[v];
         const int64_t own = sp.on() ? sp_get(sp, v, blk_local(a, k, kmask)) : W[v * (int64_t)k + blk_local(a, k, kmask)];
         const int64_t c = vwgt ? vwgt[v] : 1;
         const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wI[v];
+        out_w += (long long)wI[v] - own;
         const int s = slot_of((uint64_t)own, (uint64_t)c, s_p3);
         if (av) {
             unsigned long long *dst = use_shared ? s_bw : BW;
@@ -104,6 +106,35 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
         __syncthreads();
         for (int i = threadIdx.x; i < bins; i += blockDim.x)
             if (s_bw[i]) atomicAdd(&BW[i], s_bw[i]);
+    }
+    if (cut2) {
+        __shared__ long long s_cw[8];
+        out_w = warp_sum(out_w);
+        if ((threadIdx.x & 31) == 0) s_cw[threadIdx.x >> 5] = out_w;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_cw[w];
+            if (t) atomicAdd(&cut2[blockIdx.x % kCutParts], (unsigned long long)t);
+        }
+    }
+}
+
+// cut2[0 .. kCutParts): partial sums of twice the cut (spread over many words
+// so that the CTAs' atomics do not queue on one address); cut2[kCutParts] =
+// their total; cut = half of it.
+__global__ void __launch_bounds__(kCutParts) k_half_cut(unsigned long long *__restrict__ cut2,
+                                                        int64_t *__restrict__ cut) {
+    __shared__ unsigned long long s_w[kCutParts / 32];
+    unsigned long long v = cut2[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kCutParts / 32; w++) t += s_w[w];
+        cut2[kCutParts] = t;
+        cut[0] = (int64_t)(t / 2);
     }
 }
 
@@ -465,10 +496,17 @@ __global__ void k_apply_moves(const int32_t *__restrict__ cand_idx, const int32_
 }  // namespace
 
 void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t_num, int32_t t_den, int64_t *BW,
-             int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s) {
+             int64_t *PW, int8_t *first, int8_t *avail_out, int32_t *slot_out, cudaStream_t s, int64_t *cut2,
+             int64_t *cut) {
     ensure_pow3();
     const int32_t K = g.K();
     UPR_CUDA(cudaMemsetAsync(BW, 0, sizeof(int64_t) * K * kSlots, s));
+    unsigned long long *c2 = nullptr;
+    if (cut2) {
+        if (g.ng != 1) throw CudaError{cudaErrorInvalidValue, "buckets: the cut is summed for one graph"};
+        UPR_CUDA(cudaMemsetAsync(cut2, 0, sizeof(int64_t) * (kCutParts + 1), s));
+        c2 = reinterpret_cast<unsigned long long *>(cut2);
+    }
     if (g.n > 0) {
         const size_t shm = sizeof(unsigned long long) * (size_t)K * kSlots;
         const int use_shared = shm <= 200 * 1024;
@@ -477,7 +515,11 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
         const unsigned blocks = wave_grid((const void *)k_buckets, 256, use_shared ? shm : 0, ceil_div(g.n, 256));
         k_buckets<<<blocks, 256, use_shared ? shm : 0, s>>>(part, W, g.wI, g.vwgt, g.n, g.k, g.kmask, K,
                                                                       t_num, t_den, (unsigned long long *)BW,
-                                                                      use_shared, avail_out, slot_out, g.sp);
+                                                                      use_shared, avail_out, slot_out, g.sp, c2);
+        UPR_LAUNCH_CHECK();
+    }
+    if (c2) {
+        k_half_cut<<<1, kCutParts, 0, s>>>(c2, cut);
         UPR_LAUNCH_CHECK();
     }
     k_bucket_prefix<<<(unsigned)ceil_div(K, 128), 128, 0, s>>>(BW, PW, first, K);
