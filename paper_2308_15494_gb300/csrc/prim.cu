@@ -302,9 +302,10 @@ __global__ void __launch_bounds__(kThreads) k_scan(const TIn *in, T *out, const 
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Persistent grid of the tile kernels: tiles are taken dynamically.
-inline unsigned tile_grid(int64_t tiles_max) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_max, (int64_t)device_sm_count() * 4));
+// Persistent grid of the tile kernels (tiles are taken dynamically): as many
+// CTAs as fit on the GPU at once, no more than there are tiles.
+inline unsigned tile_grid(const void *func, int64_t tiles_max) {
+    return wave_grid(func, kThreads, 0, tiles_max);
 }
 
 // The layout depends on the scratch's capacity only, never on the call, so a
@@ -330,7 +331,7 @@ void scan_impl(const TIn *in, T *out, Count n, bool inclusive, Scratch tmp, cuda
     const int vin = aligned16(in) ? 1 : 0;
     const int vio = vin | (aligned16(out) ? 2 : 0);
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    k_scan<Op, T, TIn><<<tile_grid(tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, inclusive ? 1 : 0, vio,
+    k_scan<Op, T, TIn><<<tile_grid((const void *)k_scan<Op, T, TIn>, tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, inclusive ? 1 : 0, vio,
                                                                   scan_state<T>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
 }
@@ -591,14 +592,16 @@ bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     // digit-major per-tile histograms (kBins x tiles), scanned in place
     int32_t *hist = reinterpret_cast<int32_t *>(tmp.mem);
     int32_t *d_hist_n = hist + (size_t)kBins * tmp.tiles_cap;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles_max, (int64_t)device_sm_count() * 8));
+    // one full wave each (tiles are assigned by CTA index)
+    const unsigned grid_h = wave_grid((const void *)k_radix_hist, kThreads, 0, tiles_max);
+    const unsigned grid_s = wave_grid((const void *)k_radix_scatter, kThreads, 0, tiles_max);
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     for (int p = 0; p < passes; p++) {
-        k_radix_hist<<<grid, kThreads, 0, s>>>(ka, n.d, n.max, 8 * p, hist, d_hist_n);
+        k_radix_hist<<<grid_h, kThreads, 0, s>>>(ka, n.d, n.max, 8 * p, hist, d_hist_n);
         UPR_LAUNCH_CHECK();
         scan_impl<OpSum, int32_t, int32_t>(hist, hist, Count{d_hist_n, (int64_t)kBins * tiles_max}, false, tmp, s);
-        k_radix_scatter<<<grid, kThreads, 0, s>>>(ka, va, kb, vb, n.d, n.max, 8 * p, hist);
+        k_radix_scatter<<<grid_s, kThreads, 0, s>>>(ka, va, kb, vb, n.d, n.max, 8 * p, hist);
         UPR_LAUNCH_CHECK();
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
@@ -610,7 +613,7 @@ void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Coun
     if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
     const int vec = aligned16(flags) ? 1 : 0;
     const int64_t tiles_max = ceil_div(n.max, kTile);
-    k_compact<<<tile_grid(tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, out_idx, d_count, vec,
+    k_compact<<<tile_grid((const void *)k_compact, tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, out_idx, d_count, vec,
                                                         scan_state<int32_t>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
 }
