@@ -12,6 +12,7 @@
 #include <mutex>
 #include <new>
 #include <set>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -375,6 +376,36 @@ void run_tuned(upr_ctx *c, bool tuned, LaneCfg cfg, LaneCfg *cands, int *pending
     launch(cfg);
 }
 
+// Schedules found by tuning, shared by the contexts of the process: keyed by
+// device, k, the table layout, one graph or a batch, and the size class
+// (log2 of n), so a context bound to a graph like one tuned before starts
+// with its schedules instead of timing the candidates again.
+struct TuneKey {
+    int dev, k, sparse, batch, size_class, which;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, k, sparse, batch, size_class, which) <
+               std::tie(o.dev, o.k, o.sparse, o.batch, o.size_class, o.which);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LaneCfg> g_tuned;
+
+TuneKey tune_key(const upr_ctx *c, int which) {
+    return TuneKey{c->device, c->k, c->G.sp.on() ? 1 : 0, c->ng > 1 ? 1 : 0, bit_length((uint64_t)c->n), which};
+}
+
+void remember_tuning(const upr_ctx *c, int which, LaneCfg cfg) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[tune_key(c, which)] = cfg;
+}
+
+void recall_tuning(upr_ctx *c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto a = g_tuned.find(tune_key(c, 0)), b = g_tuned.find(tune_key(c, 1));
+    if (a != g_tuned.end()) { c->sel_cfg = a->second; c->sel_tuned = true; }
+    if (b != g_tuned.end()) { c->prop_cfg = b->second; c->prop_tuned = true; }
+}
+
 // After a synchronisation: keep the fastest candidate if the work was large
 // enough to tell them apart (otherwise try again next time).
 void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands, cudaEvent_t *ev, float min_ms) {
@@ -624,7 +655,10 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
         enqueue_subround(c, st, light, h == 1, s);
         UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
-        settle_tuning(&c->prop_cfg, &c->prop_tuned, &c->prop_pending, c->prop_cands, c->ev_tune + 6, 0.02f);
+        if (c->prop_pending) {
+            settle_tuning(&c->prop_cfg, &c->prop_tuned, &c->prop_pending, c->prop_cands, c->ev_tune + 6, 0.02f);
+            if (c->prop_tuned) remember_tuning(c, 1, c->prop_cfg);
+        }
         if (log_enabled()) {
             int32_t hc[CNT_SLOTS];
             UPR_CUDA(cudaMemcpy(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost));
@@ -747,7 +781,10 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     else UPR_CUDA(cudaMemcpyAsync(c->hbest, c->tot, sizeof(long long) * 3, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaMemcpyAsync(c->hcnt + 40, c->tmp.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaStreamSynchronize(s));
-    settle_tuning(&c->sel_cfg, &c->sel_tuned, &c->sel_pending, c->sel_cands, c->ev_tune, 0.05f);
+    if (c->sel_pending) {
+        settle_tuning(&c->sel_cfg, &c->sel_tuned, &c->sel_pending, c->sel_cands, c->ev_tune, 0.05f);
+        if (c->sel_tuned) remember_tuning(c, 0, c->sel_cfg);
+    }
     // a bounded wait of a primitive gave up: the round's lists are not trustworthy
     if (c->hcnt[40] != 0) { c->table_valid = false; throw CudaError{cudaErrorLaunchTimeout, "primitive wait"}; }
     {
@@ -1084,6 +1121,26 @@ namespace upr {
 // device arena when it is large enough), copies the graphs and computes
 // omega(I(v)).  Pinned host buffers and events are created once per context.
 // On error the context is left unbound (n = -1) but reusable.
+// Host threads for a pass over n nodes: one per 2^18 nodes, at most 16.
+int host_threads(int64_t n) {
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    return (int)std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)16, n >> 18}));
+}
+
+// fn(t, v0, v1) on [0, n) split into `parts` contiguous segments, segment t on
+// its own thread (the calling thread takes segment 0).
+template <typename F>
+void parallel_segments(int64_t n, int parts, F fn) {
+    if (parts <= 1 || n <= 0) {
+        fn(0, 0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 1; t < parts; t++) th.emplace_back(fn, t, n * t / parts, n * (t + 1) / parts);
+    fn(0, 0, n / parts);
+    for (auto &x : th) x.join();
+}
+
 upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
                        const upr_params &prm) {
     if (!gs || !eps || ng < 1 || k < 2 || k > kMaxK || (int64_t)ng * k >= (1LL << 30) || !params_ok(prm))
@@ -1101,6 +1158,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         any_vwgt = any_vwgt || g->vwgt;
     }
     if (n >= (1LL << 31) || m >= (1LL << 31)) return UPR_ERR_INVALID;
+    const auto t_bind0 = std::chrono::steady_clock::now();
     c->n = -1;
     c->table_valid = false;
     UPR_CUDA(cudaGetDevice(&c->device));
@@ -1108,31 +1166,81 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->s = (cudaStream_t)prm.stream;
     c->ng = ng;
     c->eps_ppm = (int64_t)(eps[0] * 1e6 + 0.5);
-    // host copy of the packed xadj and the per-graph sums for create-time decisions
-    std::vector<int64_t> xadj_h(n + 1, 0);
+    // the packed xadj on the host (the caller's array itself for one graph in
+    // host memory) and the per-graph sums for create-time decisions; the
+    // passes over the nodes run on several host threads
     c->noff.assign(ng + 1, 0);
     c->Lmax_g.assign(ng, 0);
     std::vector<int64_t> eoff(ng + 1, 0);
+    for (int32_t i = 0; i < ng; i++) {
+        c->noff[i + 1] = c->noff[i] + gs[i].n;
+        eoff[i + 1] = eoff[i] + gs[i].m;
+    }
+    std::vector<int64_t> xadj_store;
+    const int64_t *xadj_h;
+    if (ng == 1 && (n == 0 || mem_kind(gs[0].xadj) == kHost)) {
+        static const int64_t zero = 0;
+        xadj_h = n > 0 ? gs[0].xadj : &zero;
+        if (n > 0 && (xadj_h[0] != 0 || xadj_h[n] != m)) return UPR_ERR_INVALID;
+    } else {
+        xadj_store.assign(n + 1, 0);
+        for (int32_t i = 0; i < ng; i++) {
+            const upr_graph *g = &gs[i];
+            const int64_t gn = g->n, v0 = c->noff[i];
+            if (gn == 0) continue;
+            if (mem_kind(g->xadj) == kDevice)
+                UPR_CUDA(cudaMemcpy(xadj_store.data() + v0, g->xadj, sizeof(int64_t) * (gn + 1), cudaMemcpyDeviceToHost));
+            else
+                memcpy(xadj_store.data() + v0, g->xadj, sizeof(int64_t) * (gn + 1));
+            if (xadj_store[v0] != 0 || xadj_store[v0 + gn] != g->m) return UPR_ERR_INVALID;
+        }
+        xadj_store[n] = m;
+        xadj_h = xadj_store.data();
+    }
+    const int nthreads = host_threads(n);
+    // monotone rows; batches: graph-local offsets made global
+    {
+        std::vector<char> bad(nthreads, 0);
+        parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
+            if (ng == 1) {
+                for (int64_t v = v0; v < v1; v++)
+                    if (xadj_h[v + 1] < xadj_h[v]) { bad[t] = 1; return; }
+                return;
+            }
+            // v in [v0, v1): graph of v by search, then its offset
+            int32_t gi = (int32_t)(std::upper_bound(c->noff.begin(), c->noff.end(), v0) - c->noff.begin()) - 1;
+            for (int64_t v = v0; v < v1; v++) {
+                while (v >= c->noff[gi + 1]) gi++;
+                const bool last = v + 1 == c->noff[gi + 1];
+                const int64_t nxt = last ? gs[gi].m : xadj_store[v + 1];
+                if (nxt < xadj_store[v]) { bad[t] = 1; return; }
+            }
+        });
+        for (char x : bad)
+            if (x) return UPR_ERR_INVALID;
+        if (ng > 1) {
+            // every entry of graph g gains eoff[g] (the last one of a graph is the next graph's 0 + its offset)
+            parallel_segments(n, nthreads, [&](int, int64_t v0, int64_t v1) {
+                int32_t gi = (int32_t)(std::upper_bound(c->noff.begin(), c->noff.end(), v0) - c->noff.begin()) - 1;
+                for (int64_t v = v0; v < v1; v++) {
+                    while (v >= c->noff[gi + 1]) gi++;
+                    xadj_store[v] += eoff[gi];
+                }
+            });
+            xadj_store[n] = m;
+        }
+    }
     int64_t cmax = 1;
     for (int32_t i = 0; i < ng; i++) {
         const upr_graph *g = &gs[i];
-        const int64_t gn = g->n, v0 = c->noff[i], e0 = eoff[i];
-        c->noff[i + 1] = v0 + gn;
-        eoff[i + 1] = e0 + g->m;
-        if (gn > 0) {
-            UPR_CUDA(cudaMemcpy(xadj_h.data() + v0, g->xadj, sizeof(int64_t) * (gn + 1),
-                                mem_kind(g->xadj) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-            if (xadj_h[v0] != 0 || xadj_h[v0 + gn] != g->m) return UPR_ERR_INVALID;
-            for (int64_t v = v0; v < v0 + gn; v++)
-                if (xadj_h[v + 1] < xadj_h[v]) return UPR_ERR_INVALID;
-            for (int64_t v = v0; v <= v0 + gn; v++) xadj_h[v] += e0;
-        }
-        xadj_h[v0 + gn] = e0 + g->m;
+        const int64_t gn = g->n;
         int64_t total = gn;
         if (g->vwgt && gn > 0) {
             std::vector<int32_t> vw(gn);
-            UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * gn,
-                                mem_kind(g->vwgt) == kDevice ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+            if (mem_kind(g->vwgt) == kDevice)
+                UPR_CUDA(cudaMemcpy(vw.data(), g->vwgt, sizeof(int32_t) * gn, cudaMemcpyDeviceToHost));
+            else
+                memcpy(vw.data(), g->vwgt, sizeof(int32_t) * gn);
             total = 0;
             for (int32_t w : vw) {
                 if (w <= 0) return UPR_ERR_INVALID;
@@ -1147,34 +1255,42 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     }
     c->Lmax = c->Lmax_g[0];
     c->cbits = bit_length((uint64_t)cmax);
-    std::vector<HubChunk> chunks;
-    for (int64_t v = 0; v < n; v++) {
-        const int64_t d = xadj_h[v + 1] - xadj_h[v];
-        if (d > kHubDegree)
-            for (int64_t b = xadj_h[v]; b < xadj_h[v + 1]; b += 8192)
-                chunks.push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
-    }
-    // static schedule of the tiled table build: runs of consecutive nodes
-    // with at most tile_nodes rows (<= 32 KB of shared memory) and at most
-    // kTileEntries non-hub adjacency entries; a hub closes its tile.  Rows
-    // are independent, so a tile may span two graphs of a batch.
-    std::vector<TableTile> tiles;
-    int32_t tile_nodes = 0;
-    if (k % 4 == 0) {
-        const int64_t kTileEntries = 4096;
-        tile_nodes = (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k));
-        int64_t v = 0;
-        while (v < n) {
-            TableTile t{xadj_h[v], xadj_h[v], (int32_t)v, (int32_t)v};
-            while (v < n && t.v1 - t.v0 < tile_nodes) {
-                const int64_t d = xadj_h[v + 1] - xadj_h[v];
-                if (d > kHubDegree) { t.v1 = (int32_t)(++v); break; }     // hub: row zero here, last in tile
-                if (t.e1 + d - t.e0 > kTileEntries && t.v1 > t.v0) break;
-                t.e1 += d;
-                t.v1 = (int32_t)(++v);
-            }
-            tiles.push_back(t);
+    // static schedules, built segment by segment (a segment boundary also
+    // ends a tile): hub chunks of 8192 entries of one node of degree >
+    // kHubDegree, and the tiles of the table build, runs of consecutive
+    // nodes with at most tile_nodes rows (<= 32 KB of shared memory) and at
+    // most kTileEntries non-hub adjacency entries; a hub closes its tile.
+    // Rows are independent, so a tile may span two graphs of a batch.
+    const int32_t tile_nodes = k % 4 == 0 ? (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k)) : 0;
+    std::vector<std::vector<HubChunk>> seg_chunks(nthreads);
+    std::vector<std::vector<TableTile>> seg_tiles(nthreads);
+    parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
+        for (int64_t v = v0; v < v1; v++) {
+            const int64_t d = xadj_h[v + 1] - xadj_h[v];
+            if (d > kHubDegree)
+                for (int64_t b = xadj_h[v]; b < xadj_h[v + 1]; b += 8192)
+                    seg_chunks[t].push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
         }
+        if (!tile_nodes) return;
+        const int64_t kTileEntries = 4096;
+        int64_t v = v0;
+        while (v < v1) {
+            TableTile tl{xadj_h[v], xadj_h[v], (int32_t)v, (int32_t)v};
+            while (v < v1 && tl.v1 - tl.v0 < tile_nodes) {
+                const int64_t d = xadj_h[v + 1] - xadj_h[v];
+                if (d > kHubDegree) { tl.v1 = (int32_t)(++v); break; }     // hub: row zero here, last in tile
+                if (tl.e1 + d - tl.e0 > kTileEntries && tl.v1 > tl.v0) break;
+                tl.e1 += d;
+                tl.v1 = (int32_t)(++v);
+            }
+            seg_tiles[t].push_back(tl);
+        }
+    });
+    std::vector<HubChunk> chunks;
+    std::vector<TableTile> tiles;
+    for (int t = 0; t < nthreads; t++) {
+        chunks.insert(chunks.end(), seg_chunks[t].begin(), seg_chunks[t].end());
+        tiles.insert(tiles.end(), seg_tiles[t].begin(), seg_tiles[t].end());
     }
     // sparse rows: a power of two >= min(k, 2 deg(v)) + 1 slots per row (mode 3:
     // min(k, deg(v)) + 1); chosen by size (mode 0) when k >= 128 and the rows
@@ -1185,15 +1301,34 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         int64_t total = 0, buf_cap = 1;
         if (k % 4 == 0 && k <= kSparseRowMax / 2 && (mode >= 2 || (mode == 0 && k >= 128))) {
             sp_off_h.assign(n + 1, 0);
-            for (int64_t v = 0; v < n; v++) {
+            std::vector<int64_t> seg_total(nthreads, 0), seg_cap(nthreads, 1);
+            auto cap_of = [&](int64_t v) {
                 const int64_t d = xadj_h[v + 1] - xadj_h[v];
                 const int64_t want = std::min<int64_t>(k, mode == 3 ? d : 2 * d) + 1;
                 int64_t cap = 1;
                 while (cap < want) cap <<= 1;
-                sp_off_h[v] = total;
-                total += cap;
-                if (d <= kHubDegree) buf_cap = std::max<int64_t>(buf_cap, cap);
+                return cap;
+            };
+            parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
+                int64_t tot = 0, bc = 1;
+                for (int64_t v = v0; v < v1; v++) {
+                    const int64_t cap = cap_of(v);
+                    sp_off_h[v] = tot;              // local offset for now
+                    tot += cap;
+                    if (xadj_h[v + 1] - xadj_h[v] <= kHubDegree) bc = std::max(bc, cap);
+                }
+                seg_total[t] = tot;
+                seg_cap[t] = bc;
+            });
+            std::vector<int64_t> seg_base(nthreads + 1, 0);
+            for (int t = 0; t < nthreads; t++) {
+                seg_base[t + 1] = seg_base[t] + seg_total[t];
+                buf_cap = std::max(buf_cap, seg_cap[t]);
             }
+            parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
+                for (int64_t v = v0; v < v1; v++) sp_off_h[v] += seg_base[t];
+            });
+            total = seg_base[nthreads];
             sp_off_h[n] = total;
             if (mode == 0 && total * (int64_t)sizeof(int2) * 2 > n * (int64_t)k * (int64_t)sizeof(int32_t))
                 total = 0, buf_cap = 1, sp_off_h.clear();
@@ -1201,6 +1336,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         c->sp_slots = total;
         c->sp_buf_cap = (int32_t)buf_cap;
     }
+    const auto t_sched = std::chrono::steady_clock::now();
     c->m = m; c->k = k;
     c->n = n;                       // layout needs the sizes
     c->n_chunks = (int64_t)chunks.size();
@@ -1218,6 +1354,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     }
     A.base = (char *)c->mem; A.off = 0;
     layout(c, A);
+    const auto t_alloc = std::chrono::steady_clock::now();
     // pinned buffers and events are sized for kMaxK blocks, so a context
     // re-bound to another graph keeps them
     if (!c->h) {
@@ -1239,9 +1376,10 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->sel_pending = c->prop_pending = 0;
     cudaStream_t s = c->s;
     if (ng == 1) {
-        copy_in(c->xadj, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
+        if (n > 0) copy_in(c->xadj, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
+        else UPR_CUDA(cudaMemsetAsync(c->xadj, 0, sizeof(int64_t), s));
     } else {
-        UPR_CUDA(cudaMemcpyAsync(c->xadj, xadj_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+        UPR_CUDA(cudaMemcpyAsync(c->xadj, xadj_store.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
     }
     for (int32_t i = 0; i < ng; i++) {
         const upr_graph *g = &gs[i];
@@ -1272,6 +1410,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->G = GraphDev{n,      m,        k,       ng,   kmask, c->xadj, c->adj, any_adjw ? c->adjw : nullptr,
                     any_vwgt ? c->vwgt : nullptr, c->wI, c->Lb, c->gid,
                     SparseRows{c->sp_off, c->sparse_on ? c->sp_slot : nullptr, c->sp_over, c->sp_buf_cap}};
+    if (prm.autotune) recall_tuning(c);
     if (ng > 1) {
         // node -> graph, and graph-local neighbour ids made global
         UPR_CUDA(cudaMemcpyAsync(c->noff_d, c->noff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
@@ -1286,6 +1425,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         UPR_CUDA(cudaStreamSynchronize(s));
         if (flags != 0 || acc[0] != acc[1]) { c->n = -1; return UPR_ERR_INVALID; }
     }
+    const auto t_valid = std::chrono::steady_clock::now();
     incident_weights(c->G, c->wI, c->scal, s);
     read_i64(c, c->scal, 1, &c->wmax);
     if (c->wmax > 0x7fffffffLL) { c->n = -1; return UPR_ERR_INVALID; }
@@ -1304,6 +1444,14 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     fill_i32(c->m_pos, n, -1, s);
     fill_i32(c->r_to, n, -1, s);
     UPR_CUDA(cudaStreamSynchronize(s));
+    if (log_enabled()) {
+        const auto t_end = std::chrono::steady_clock::now();
+        auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+        fprintf(stderr, "upr bind: %lld nodes, %d host threads: schedules %.2f ms, arena %.2f ms (%.2f GB), "
+                        "upload and checks %.2f ms, incident weights and clears %.2f ms\n",
+                (long long)n, nthreads, ms(t_bind0, t_sched), ms(t_sched, t_alloc), A.off / 1e9,
+                ms(t_alloc, t_valid), ms(t_valid, t_end));
+    }
     return UPR_OK;
 }
 
