@@ -346,6 +346,21 @@ def test_rebalancing_graph_same_results(upr):
             assert (st.rebalance_graphs > 0) == (graphs == 1)
 
 
+def test_tuned_schedules_shared_between_contexts(upr):
+    """A context bound to a graph of the same shape as one tuned before starts
+    with the schedules found then (no candidates timed again); results equal."""
+    w = synth.cached(synth.plain_large, 2)          # R-MAT, 2^20 nodes, k = 64
+    runs = []
+    for _ in range(2):
+        ctx = upr.create_from_workload(w)
+        p = w.part.copy()
+        runs.append((p, upr.upr_refine(ctx, p, 2)))
+        del ctx
+    (p1, s1), (p2, s2) = runs
+    assert np.array_equal(p1, p2) and s1.cut_out == s2.cut_out
+    assert (s2.select_lanes, s2.propose_lanes) == (s1.select_lanes, s1.propose_lanes)
+
+
 def test_sparse_table_chosen_by_size(upr):
     """Auto layout: hashed rows for k >= 128 when they take at most half the
     dense table's bytes (sparse graphs), the dense table otherwise."""
