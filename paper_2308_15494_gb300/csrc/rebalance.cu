@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
         const bool src = i < n1 && (BATCH ? st.over[ag] : s_over[a]);
         const int4 zero = make_int4(0, 0, 0, 0);
         int4 r[CH];
-        if (src) {
+        // an isolated node's row is zero: not read
+        if (src && g.wI[v] > 0) {
             const int4 *row4 = reinterpret_cast<const int4 *>(W + (int64_t)v * k);
 #pragma unroll
             for (int j = 0; j < CH; j++) {

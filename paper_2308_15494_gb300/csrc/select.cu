@@ -90,10 +90,14 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
     long long out_w = 0;      // weight of the edges leaving v's block, summed over this thread's nodes
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = part[v];
-        const int64_t own = sp.on() ? sp_get(sp, v, blk_local(a, k, kmask)) : W[v * (int64_t)k + blk_local(a, k, kmask)];
+        const int32_t wIv = wI[v];
+        // an isolated node's row is zero: no gather
+        const int64_t own = wIv == 0 ? 0
+                            : sp.on() ? sp_get(sp, v, blk_local(a, k, kmask))
+                                      : W[v * (int64_t)k + blk_local(a, k, kmask)];
         const int64_t c = vwgt ? vwgt[v] : 1;
-        const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wI[v];
-        out_w += (long long)wI[v] - own;
+        const bool av = (int64_t)t_den * own >= (int64_t)t_num * (int64_t)wIv;
+        out_w += (long long)wIv - own;
         const int s = slot_of((uint64_t)own, (uint64_t)c, s_p3);
         if (av) {
             unsigned long long *dst = use_shared ? s_bw : BW;
@@ -250,6 +254,9 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
         int4 r[CH];
         int32_t a = 0, b0 = 0;
         const int4 zero = make_int4(0, 0, 0, 0);
+        // (rows are loaded without waiting for omega(I(v)): skipping the zero
+        // rows of isolated nodes behind that load measured slower)
+        const int32_t wIv = active ? g.wI[v] : 0;
         if (active) {
             const int32_t ag = part[v];
             a = BATCH ? blk_local(g, ag) : ag;
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
         // skipped and every score kept lies in [1, 2^31).
         int32_t best = 0;
         int32_t bt = -1, bg = 0;
-        if (active && own < g.wI[v]) {
+        if (active && own < wIv) {
             const int32_t c = g.vwgt ? g.vwgt[v] : 1;
 #pragma unroll
             for (int j = 0; j < CH; j++) {
