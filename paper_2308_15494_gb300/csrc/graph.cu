@@ -40,39 +40,60 @@ __global__ void k_edge_cut(const int64_t *__restrict__ xadj, const int32_t *__re
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t e0 = warp * kChunk, e1 = min(m, e0 + kChunk);
-    if (e0 >= m) return;                          // whole warp: e0 is warp-uniform
-    int64_t e = e0 + lane;
-    int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
-    const int32_t g0 = gid ? gid[owner_of(xadj, n, e0)] : 0;
-    const int32_t g1 = gid ? gid[owner_of(xadj, n, e1 - 1)] : 0;
     long long acc = 0;
-    for (; e < e1; e += 32) {
-        while (xadj[v + 1] <= e) v++;
-        const int32_t u = adj[e];
-        if (v < u && part[v] != part[u]) {        // each undirected edge once
-            const long long w = adjw ? adjw[e] : 1;
-            if (g0 == g1) acc += w;
-            else atomicAdd(&out[gid[v]], (unsigned long long)w);
+    int32_t g0 = 0, g1 = 0;
+    if (e0 < m) {                                 // warp-uniform
+        int64_t e = e0 + lane;
+        int64_t v = e < e1 ? owner_of(xadj, n, e) : 0;
+        g0 = gid ? gid[owner_of(xadj, n, e0)] : 0;
+        g1 = gid ? gid[owner_of(xadj, n, e1 - 1)] : 0;
+        for (; e < e1; e += 32) {
+            while (xadj[v + 1] <= e) v++;
+            const int32_t u = adj[e];
+            if (v < u && part[v] != part[u]) {    // each undirected edge once
+                const long long w = adjw ? adjw[e] : 1;
+                if (g0 == g1) acc += w;
+                else atomicAdd(&out[gid[v]], (unsigned long long)w);
+            }
         }
     }
-    if (g0 == g1) {
-        acc = warp_sum(acc);
-        if (lane == 0 && acc) atomicAdd(&out[g0], (unsigned long long)acc);
+    acc = warp_sum(acc);
+    if (gid) {
+        if (lane == 0 && acc && g0 == g1) atomicAdd(&out[g0], (unsigned long long)acc);
+        return;
+    }
+    // one graph: one atomic per CTA (one per warp would queue on the word)
+    __shared__ long long s_acc[8];
+    if (lane == 0) s_acc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) acc += s_acc[w];
+        if (acc) atomicAdd(&out[0], (unsigned long long)acc);
     }
 }
 
 // omega(I(v)) per node (warp per node); records the maximum and overflow.
-__global__ void k_incident(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adjw, int64_t n,
-                           int32_t *__restrict__ wI, unsigned long long *__restrict__ wmax) {
-    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// omega(I(v)) per node (warp per node, grid-stride) and its maximum: one
+// atomic per CTA (one per node would queue on the single word).
+__global__ void __launch_bounds__(256) k_incident(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adjw,
+                                                  int64_t n, int32_t *__restrict__ wI,
+                                                  unsigned long long *__restrict__ wmax) {
+    __shared__ unsigned long long s_max[8];
     const int lane = threadIdx.x & 31;
-    if (v >= n) return;
-    long long acc = 0;
-    for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) acc += adjw ? adjw[e] : 1;
-    acc = warp_sum(acc);
-    if (lane == 0) {
-        wI[v] = acc > 0x7fffffffLL ? 0x7fffffff : (int32_t)acc;
-        atomicMax(wmax, (unsigned long long)acc);
+    unsigned long long mx = 0;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n;
+         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        long long acc = 0;
+        for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) acc += adjw ? adjw[e] : 1;
+        acc = warp_sum(acc);
+        if (lane == 0) wI[v] = acc > 0x7fffffffLL ? 0x7fffffff : (int32_t)acc;
+        mx = (unsigned long long)acc > mx ? (unsigned long long)acc : mx;
+    }
+    if (lane == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = s_max[w] > mx ? s_max[w] : mx;
+        if (mx) atomicMax(wmax, mx);
     }
 }
 
@@ -114,7 +135,21 @@ __global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32
     h1 = warp_sum(h1);
     h2 = warp_sum(h2);
     for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, o);
+    // one set of atomics per CTA (the sums wrap modulo 2^64 in any order)
+    __shared__ unsigned long long s_h[2][8];
+    __shared__ int32_t s_f[8];
     if (lane == 0) {
+        s_h[0][threadIdx.x >> 5] = h1;
+        s_h[1][threadIdx.x >> 5] = h2;
+        s_f[threadIdx.x >> 5] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            h1 += s_h[0][w];
+            h2 += s_h[1][w];
+            f |= s_f[w];
+        }
         if (h1) atomicAdd(&acc[0], h1);
         if (h2) atomicAdd(&acc[1], h2);
         if (f) atomicOr(flags, f);
@@ -473,7 +508,8 @@ void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t
 void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_t s) {
     UPR_CUDA(cudaMemsetAsync(wmax, 0, sizeof(int64_t), s));
     if (g.n == 0) return;
-    k_incident<<<(unsigned)ceil_div(g.n * 32, 256), 256, 0, s>>>(g.xadj, g.adjw, g.n, wI, (unsigned long long *)wmax);
+    k_incident<<<wave_grid((const void *)k_incident, 256, 0, ceil_div(g.n * 32, 256)), 256, 0, s>>>(
+        g.xadj, g.adjw, g.n, wI, (unsigned long long *)wmax);
     UPR_LAUNCH_CHECK();
 }
 
