@@ -254,6 +254,12 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
     int64_t *s_x = reinterpret_cast<int64_t *>(s_raw);           // nn + 1 row starts
     int *rows = reinterpret_cast<int *>(s_x + ((nn + 2) & ~1));    // nn * k
     for (int i = threadIdx.x; i <= nn; i += blockDim.x) s_x[i] = xadj[t.v0 + i];
+    // hashed rows: the tile's row offsets, fetched now so that the write-out
+    // does not wait for them row by row
+    int64_t *s_off = sp.on() ? reinterpret_cast<int64_t *>(reinterpret_cast<int2 *>(rows + nn * k) + 8 * sp.buf_cap)
+                             : nullptr;
+    if (sp.on())
+        for (int i = threadIdx.x; i <= nn; i += blockDim.x) s_off[i] = sp.off[t.v0 + i];
     const int words4 = nn * k / 4;
     const int4 z = make_int4(0, 0, 0, 0);
     for (int i = threadIdx.x; i < words4; i += blockDim.x) reinterpret_cast<int4 *>(rows)[i] = z;
@@ -311,9 +317,8 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         int2 *buf = reinterpret_cast<int2 *>(rows + nn * k) + warp * sp.buf_cap;
         for (int r = warp; r < nn; r += (int)(blockDim.x >> 5)) {
-            const int64_t v = t.v0 + r;
-            const int64_t o = sp.off[v];
-            const uint32_t cap = (uint32_t)(sp.off[v + 1] - o);
+            const int64_t o = s_off[r];
+            const uint32_t cap = (uint32_t)(s_off[r + 1] - o);
             if (cap > (uint32_t)sp.buf_cap) {
                 // a hub: its row is empty here, the chunk pass fills it
                 for (uint32_t i = lane; i < cap; i += 32) sp.slot[o + i] = make_int2(kEmpty, 0);
@@ -544,7 +549,10 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaSt
 
 size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap) {
     const size_t rows = sizeof(int64_t) * (size_t)((nodes + 2) & ~1) + sizeof(int) * (size_t)nodes * k;
-    return sparse_buf_cap > 0 ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * (size_t)sparse_buf_cap : rows;
+    // hashed rows: 8 warps' staging buffers and the tile's nodes + 1 row offsets
+    return sparse_buf_cap > 0 ? ((rows + 15) & ~(size_t)15) + 8 * sizeof(int2) * (size_t)sparse_buf_cap +
+                                    sizeof(int64_t) * (size_t)(nodes + 1)
+                              : rows;
 }
 
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
