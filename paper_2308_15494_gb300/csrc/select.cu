@@ -594,7 +594,10 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
         if (cfg.G <= 0) cfg = cands[0];
         const int G = cfg.G, CH = cfg.CH;
         const bool exact = k == 4 * G * CH;
-        const int smem_pw = !batch && (size_t)k * kSlots * 8 <= 40 * 1024;
+        // the slot prefixes are read only for an excess x > 1, i.e. a node
+        // weight c >= 2: with unit node weights they stay in global memory
+        // and the smaller shared footprint lets more CTAs run
+        const int smem_pw = !batch && g.vwgt && (size_t)k * kSlots * 8 <= 40 * 1024;
         const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) +
                            (batch ? 0 : (sizeof(int32_t) + 1) * k);
         const int64_t groups = 256 / G;
