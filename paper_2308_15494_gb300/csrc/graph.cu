@@ -240,16 +240,11 @@ __device__ __forceinline__ int tile_owner(const int64_t *s_x, int nn, int64_t e)
 }
 
 template <bool WEIGHTED, int LOCAL, int UNROLL>
-__global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict__ tiles,
-                                                        const int64_t *__restrict__ xadj,
-                                                        const int32_t *__restrict__ adj,
-                                                        const int32_t *__restrict__ adjw,
-                                                        const int32_t *__restrict__ part, int32_t k, int32_t kmask,
-                                                        int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
-                                                        int64_t m, SparseRows sp) {
-    if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
+__device__ __forceinline__ void table_tile(const TableTile t, const int64_t *__restrict__ xadj,
+                                           const int32_t *__restrict__ adj, const int32_t *__restrict__ adjw,
+                                           const int32_t *__restrict__ part, int32_t k, int32_t kmask,
+                                           int32_t *__restrict__ W, const SparseRows &sp) {
     extern __shared__ int4 s_raw[];
-    const TableTile t = tiles[blockIdx.x];
     const int nn = t.v1 - t.v0;
     int64_t *s_x = reinterpret_cast<int64_t *>(s_raw);           // nn + 1 row starts
     int *rows = reinterpret_cast<int *>(s_x + ((nn + 2) & ~1));    // nn * k
@@ -343,6 +338,24 @@ __global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict
     }
     int4 *dst = reinterpret_cast<int4 *>(W + (int64_t)t.v0 * k);
     for (int i = threadIdx.x; i < words4; i += blockDim.x) __stcs(dst + i, reinterpret_cast<const int4 *>(rows)[i]);
+}
+
+// One tile per CTA for a build (grid = tiles); the rebuild alternatives,
+// which usually return at once, run on one wave of CTAs that loop over the
+// tiles, so that their early return costs a wave, not tens of thousands of CTAs.
+template <bool WEIGHTED, int LOCAL, int UNROLL>
+__global__ void __launch_bounds__(256) k_table_tiles(const TableTile *__restrict__ tiles, int64_t n_tiles,
+                                                        const int64_t *__restrict__ xadj,
+                                                        const int32_t *__restrict__ adj,
+                                                        const int32_t *__restrict__ adjw,
+                                                        const int32_t *__restrict__ part, int32_t k, int32_t kmask,
+                                                        int32_t *__restrict__ W, const int64_t *__restrict__ deg_sum,
+                                                        int64_t m, SparseRows sp) {
+    if (deg_sum && *deg_sum * 4 < m) return;      // the delta update handles this case
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        table_tile<WEIGHTED, LOCAL, UNROLL>(tiles[ti], xadj, adj, adjw, part, k, kmask, W, sp);
+        __syncthreads();                          // the next tile reuses the shared memory
+    }
 }
 
 // Hub rows: one CTA per chunk of a hub's adjacency, shared-memory row, then
@@ -565,8 +578,9 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
             // about four tiles per SM and the rest of the unified memory as L1:
             // the gathers of part[] need the L1 more than extra CTAs
             kernel_setup((const void *)kern, 64);
-            kern<<<(unsigned)n_tiles, 256, shm, s>>>(tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum,
-                                                     g.m, g.sp);
+            const unsigned grid = deg_sum ? wave_grid((const void *)kern, 256, shm, n_tiles) : (unsigned)n_tiles;
+            kern<<<grid, 256, shm, s>>>(tiles, n_tiles, g.xadj, g.adj, g.adjw, part, g.k, g.kmask, W, deg_sum, g.m,
+                                        g.sp);
         };
         // 16 entries in flight per thread (8 with weights); the default
         // shared/L1 split: a smaller L1 slows the gathers of part[] down
