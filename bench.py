@@ -319,17 +319,20 @@ def other_configs_leg(args, upr):
     """The two other single-graph workloads, timed like the main one (graph and
     partition resident, CUDA events around upr_refine): the Chung-Lu graph
     with 16,384 nodes (k = 8, 4 rounds) and the weighted random geometric
-    graph with 2^22 nodes (k = 256, 8 rounds)."""
+    graph with 2^22 nodes (k = 256, 8 rounds; also with each table layout
+    forced), and the R-MAT workload under the round driver of Sec. 6.2."""
     import torch
     peak, _ = _peaks()
     out = {}
-    legs = (("chung_lu_n16384_k8", "plain_tiny", 20, 0), ("rgg_2^22_weighted_k256", "plain_weighted", 3, 0),
-            ("rgg_2^22_weighted_k256_dense_table", "plain_weighted", 3, 1),
-            ("rgg_2^22_weighted_k256_hashed_table", "plain_weighted", 3, 2))
-    for name, builder, steps, table in legs:
+    legs = (("chung_lu_n16384_k8", "plain_tiny", 20, 0, 0), ("rgg_2^22_weighted_k256", "plain_weighted", 3, 0, 0),
+            ("rgg_2^22_weighted_k256_dense_table", "plain_weighted", 3, 1, 0),
+            ("rgg_2^22_weighted_k256_hashed_table", "plain_weighted", 3, 2, 0),
+            ("rmat_s22_k64_round_driver", "plain_large", 3, 0, 1))
+    for name, builder, steps, table, schedule in legs:
         w = synth.cached(getattr(synth, builder))
         prm = upr.upr_params_default()
         prm.table = table
+        prm.schedule = schedule
         ctx = upr.create_from_workload(w, params=prm, device=True)
         init = torch.from_numpy(w.part.copy()).cuda()
         part = torch.empty_like(init)
@@ -354,6 +357,9 @@ def other_configs_leg(args, upr):
                      "cut_in": st.cut_in, "cut_out": st.cut_out,
                      "table": ("hashed rows" if st.sparse_table else "dense n x k")
                               + (" (chosen by size)" if table == 0 else ""),
+                     "schedule": ["every round unconstrained", "round driver of Sec. 6.2",
+                                  "every round constrained"][schedule],
+                     "constrained_rounds": st.constrained_rounds,
                      "gain_table_ms": t_build, "gain_table_gbs": st.gain_table_bytes / (t_build / 1e3) / 1e9,
                      "gain_table_frac": st.gain_table_bytes / (t_build / 1e3) / 1e9 / peak}
         del ctx

@@ -99,6 +99,18 @@ typedef struct {
                                     node over one sub-round, the stop test on the device);
                                     0: the host launches every sub-round and reads its stop
                                     flag.  Results never depend on it. 1                     */
+    int32_t schedule;            /* round driver (Sec. 6.2): 0 every round unconstrained
+                                    with the tau schedule; 1 the paper's integration:
+                                    round 1 constrained, round 2 unconstrained with
+                                    tau = 1/2, then rounds 3..R-1 unconstrained (tau
+                                    schedule over them) if round 2 improved the cut more
+                                    than round 1, switching to constrained once a round
+                                    improves it by less than 0.002 of the cut, else
+                                    constrained; round R constrained; 2 every round
+                                    constrained.  A constrained round is the same round
+                                    with every move that would leave its target above
+                                    L_max forbidden.  1 and 2 need one graph,
+                                    round_offset = 0 and total_rounds = 0. 0                */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 
@@ -129,6 +141,7 @@ typedef struct {
     int32_t propose_lanes;       /* lanes per node of the proposal kernel (0: scalar)   */
     int32_t sparse_table;        /* 1: the rounds ran on the sparse gain table            */
     int32_t rebalance_graphs;    /* rounds whose rebalancing loop ran as one graph launch */
+    int32_t constrained_rounds;  /* constrained rounds (schedule 1 or 2)                 */
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */

@@ -100,6 +100,10 @@ def _load():
         lib.upro_round.restype = ctypes.c_int
         lib.upro_refine.argtypes = [GP, I32, I64, PP, P, I32, I32, I32, P, P]
         lib.upro_refine.restype = ctypes.c_int
+        lib.upro_refine_schedule.argtypes = [GP, I32, I64, PP, P, I32, I32, P, P, P]
+        lib.upro_round_kind.argtypes = [GP, I32, I64, PP, I32, I64, I64, P, P, TP]
+        lib.upro_round_kind.restype = ctypes.c_int
+        lib.upro_refine_schedule.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -174,8 +178,11 @@ def penalty_sequence(w, part, block: int, nodes, r: int = 1, R: int = 1,
     return pen, lvl
 
 
-def run_round(w, part, r: int, R: int, rebalance_only: bool = False, p: Optional[Params] = None):
-    """One round on a copy of part.  Returns (rc, new_part, cut, trace dict)."""
+def run_round(w, part, r: int, R: int, rebalance_only: bool = False, p: Optional[Params] = None,
+              kind: Optional[tuple] = None):
+    """One round on a copy of part.  Returns (rc, new_part, cut, trace dict).
+    kind (Sec. 6.2): ("constrained",) or ("tau", num, den) instead of the
+    schedule's tau_r."""
     n, k = w.n, w.k
     g = _G(w)
     part = np.array(part, dtype=np.int32, copy=True)
@@ -192,8 +199,14 @@ def run_round(w, part, r: int, R: int, rebalance_only: bool = False, p: Optional
         I_node=np.zeros(n, np.int32), I_from=np.zeros(n, np.int32), I_to=np.zeros(n, np.int32),
         I_gain=np.zeros(n, np.int64), I_eligible=np.zeros(n + 1, np.int8))
     t = Trace(**{key: _ptr(v) for key, v in a.items()})
-    rc = _load().upro_round(ctypes.byref(g.s), k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
-                            r, R, int(rebalance_only), _ptr(part), ctypes.byref(c), ctypes.byref(t))
+    if kind is None:
+        rc = _load().upro_round(ctypes.byref(g.s), k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
+                                r, R, int(rebalance_only), _ptr(part), ctypes.byref(c), ctypes.byref(t))
+    else:
+        con = kind[0] == "constrained"
+        num, den = (0, 0) if con else (kind[1], kind[2])
+        rc = _load().upro_round_kind(ctypes.byref(g.s), k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
+                                     int(con), num, den, _ptr(part), ctypes.byref(c), ctypes.byref(t))
     tr = {"n_cand": t.n_cand, "n_moves": t.n_moves, "n_rebal": t.n_rebal, "subrounds": t.subrounds,
           "n_inter": t.n_inter, "n_seq": t.n_seq, "best_len": t.best_len, "best_gain": t.best_gain,
           "cut_before": t.cut_before, "cut_after": t.cut_after}
@@ -223,3 +236,24 @@ def refine(w, part, rounds: Optional[int] = None, round_offset: int = 0,
     rc = _load().upro_refine(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
                              _ptr(part), rounds, round_offset, total_rounds, ctypes.byref(c), _ptr(rcuts))
     return rc, part, int(c.value), rcuts
+
+
+# Round kinds reported by refine_schedule (the round driver of Sec. 6.2).
+UNCONSTRAINED, CONSTRAINED, UNCONSTRAINED_HALF = 0, 1, 2
+
+
+def refine_schedule(w, part, rounds: int, schedule: int, p: Optional[Params] = None):
+    """The round driver of Sec. 6.2: schedule 0 = every round unconstrained
+    (tau schedule over the rounds), 1 = the paper's integration (constrained
+    round, unconstrained round with tau = 1/2, then unconstrained or
+    constrained rounds by the improvements, constrained last round), 2 =
+    every round constrained.  Returns (rc, new_part, cut, per-round cuts
+    [rounds+1], kind of each round [rounds])."""
+    g = _G(w)
+    part = np.array(part, dtype=np.int32, copy=True)
+    c = ctypes.c_int64(0)
+    rcuts = np.zeros(rounds + 1, np.int64)
+    kinds = np.zeros(max(rounds, 1), np.int8)
+    rc = _load().upro_refine_schedule(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
+                                      _ptr(part), rounds, schedule, ctypes.byref(c), _ptr(rcuts), _ptr(kinds))
+    return rc, part, int(c.value), rcuts, kinds[:rounds]

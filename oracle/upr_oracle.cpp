@@ -238,9 +238,19 @@ struct RoundOut {
  * (steps 2-5 skipped, M empty).  Returns UPRO_ERR_INFEASIBLE (part unchanged)
  * if no prefix of the sequence is balanced.
  */
+/* The kind of a round in the round driver of Sec. 6.2 ("integration"):
+ * an unconstrained round whose penalty factor is tau_r of the schedule
+ * (tau_den == 0) or a given tau, or a constrained round, read as the same
+ * round in which no move may leave its target above L_max (an infinite
+ * penalty, so such a move is never a candidate and never kept in M). */
+struct RoundKind {
+    bool constrained = false;
+    int64_t tau_num = 0, tau_den = 0;
+};
+
 int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, int32_t r,
                int32_t R, bool rebalance_only, int32_t *part, int64_t *cut, upro_trace *tr,
-               RoundOut *out) {
+               RoundOut *out, const RoundKind &kind = RoundKind()) {
     const int64_t n = g.n;
 
     /* ---- step 0: block weights c(V_b) (Sec. 2) ---- */
@@ -268,8 +278,15 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
             if (tr && tr->slot) tr->slot[v] = s;
         }
         int64_t tnum, tden, F[NSLOT];
-        tau_of(r, R, p, &tnum, &tden);
+        if (kind.tau_den > 0) { tnum = kind.tau_num; tden = kind.tau_den; }
+        else tau_of(r, R, p, &tnum, &tden);
         factors_of(tnum, tden, F);
+        /* the penalty of a move that leaves b exceeding L_max by x */
+        auto pen_of = [&](int32_t b, int64_t x, int64_t cu) -> int64_t {
+            int lvl;
+            if (kind.constrained) return x > 0 ? FORBID : 0;
+            return penalty(BW, b, x, cu, F, &lvl);
+        };
         if (tr && tr->bucket) memcpy(tr->bucket, BW.data(), sizeof(int64_t) * BW.size());
         if (tr && tr->factor) memcpy(tr->factor, F, sizeof(F));
 
@@ -284,8 +301,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
             for (int32_t b = 0; b < k; b++) {
                 if (b == part[v] || T.at(v, b) <= 0) continue;
                 int64_t gv = (int64_t)T.at(v, b) - own;
-                int lvl;
-                int64_t pen = penalty(BW, b, C[b] + g.c(v) - Lmax, g.c(v), F, &lvl);
+                int64_t pen = pen_of(b, C[b] + g.c(v) - Lmax, g.c(v));
                 if (pen == FORBID) continue;
                 int64_t sc = gv - pen;
                 if (!have || sc > best) { have = true; best = sc; bt = b; bestg = gv; }
@@ -309,8 +325,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
             });
             int64_t inflow = 0;                          /* c(U^{i-1}) of Lemma 1 */
             for (int32_t v : L) {
-                int lvl;
-                int64_t pen = penalty(BW, t, C[t] + inflow + g.c(v) - Lmax, g.c(v), F, &lvl);
+                int64_t pen = pen_of(t, C[t] + inflow + g.c(v) - Lmax, g.c(v));
                 inflow += g.c(v);
                 if (pen == FORBID) continue;
                 int64_t sc = gain[v] - pen;
@@ -604,6 +619,28 @@ int upro_round(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_para
     return rc;
 }
 
+/* One round of a given kind (Sec. 6.2): constrained != 0, or unconstrained
+ * with tau = tau_num / tau_den.  Otherwise as upro_round with r = R = 1. */
+int upro_round_kind(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t constrained,
+                    int64_t tau_num, int64_t tau_den, int32_t *part, int64_t *cut, upro_trace *tr) {
+    upro_params p = pp ? *pp : defaults();
+    if (!params_ok(p) || k < 2 || (!constrained && (tau_den <= 0 || tau_num < 0 || tau_num > tau_den ||
+                                                    tau_den > 65536)))
+        return UPRO_ERR_INVALID;
+    Graph g = wrap(gg);
+    int64_t tot = 0;
+    for (int64_t v = 0; v < g.n; v++) tot += g.c(v);
+    RoundOut o;
+    RoundKind kind;
+    kind.constrained = constrained != 0;
+    kind.tau_num = constrained ? 0 : tau_num;
+    kind.tau_den = constrained ? 0 : tau_den;
+    std::vector<int32_t> backup(part, part + g.n);
+    int rc = round_impl(g, k, lmax_of(tot, k, eps_ppm), p, 1, 1, false, part, cut, tr, &o, kind);
+    if (rc != UPRO_OK) memcpy(part, backup.data(), sizeof(int32_t) * g.n);
+    return rc;
+}
+
 /* Rounds round_offset+1 .. round_offset+rounds of a total_rounds schedule,
  * preceded by the round-0 repair if part is imbalanced.  part is changed
  * only on success.  cut_out and per-round stats are optional. */
@@ -635,6 +672,74 @@ int upro_refine(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_par
         int rc = round_impl(g, k, Lmax, p, round_offset + i, total_rounds, false, P.data(), &cut, nullptr, &o);
         if (rc != UPRO_OK) return rc;
         if (round_cuts) round_cuts[i] = cut;
+    }
+    memcpy(part, P.data(), sizeof(int32_t) * g.n);
+    if (cut_out) *cut_out = cut;
+    return UPRO_OK;
+}
+
+/* The round driver of Sec. 6.2 over `rounds` rounds.  schedule 0: every
+ * round unconstrained with tau_r of the rounds' schedule (as upro_refine);
+ * 2: every round constrained; 1: the paper's integration, read as
+ *   round 1 constrained, round 2 unconstrained with tau = 1/2; if round 2
+ *   improved the cut by more than round 1, rounds 3..R-1 are unconstrained
+ *   with tau_i of a schedule over those R-3 rounds (i = 1, 2, ...), and once
+ *   such a round improves the cut by less than 0.002 of the cut before it,
+ *   the remaining ones are constrained; otherwise rounds 3..R-1 are
+ *   constrained; round R (R >= 3) is constrained.
+ * kinds[i-1] (may be NULL) receives round i's kind: 0 unconstrained (tau of
+ * the schedule), 1 constrained, 2 unconstrained with tau = 1/2. */
+int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t *part,
+                         int32_t rounds, int32_t schedule, int64_t *cut_out, int64_t *round_cuts, int8_t *kinds) {
+    upro_params p = pp ? *pp : defaults();
+    Graph g = wrap(gg);
+    if (!params_ok(p) || k < 2 || rounds < 0 || rounds > 65536 || schedule < 0 || schedule > 2)
+        return UPRO_ERR_INVALID;
+    for (int64_t v = 0; v < g.n; v++) if (part[v] < 0 || part[v] >= k) return UPRO_ERR_INVALID;
+    int64_t tot = 0;
+    for (int64_t v = 0; v < g.n; v++) tot += g.c(v);
+    int64_t Lmax = lmax_of(tot, k, eps_ppm);
+    std::vector<int32_t> P(part, part + g.n);
+    int64_t cut = cut_of(g, P.data());
+    std::vector<int64_t> C(k, 0);
+    for (int64_t v = 0; v < g.n; v++) C[P[v]] += g.c(v);
+    bool bal = true;
+    for (int32_t b = 0; b < k; b++) bal = bal && C[b] <= Lmax;
+    RoundOut o;
+    if (!bal) {
+        int rc = round_impl(g, k, Lmax, p, 0, rounds > 0 ? rounds : 1, true, P.data(), &cut, nullptr, &o);
+        if (rc != UPRO_OK) return rc;
+    }
+    if (round_cuts) round_cuts[0] = cut;
+    bool unconstrained_rest = false, switched = false;
+    int64_t imp1 = 0;
+    const int32_t U = rounds - 3;            /* unconstrained rounds 3..R-1 of schedule 1 */
+    for (int32_t i = 1; i <= rounds; i++) {
+        RoundKind kind;
+        int8_t code = 0;
+        int32_t r = i, R = rounds;
+        if (schedule == 2) {
+            kind.constrained = true; code = 1;
+        } else if (schedule == 1) {
+            if (i == 1 || (rounds >= 3 && i == rounds) || (i >= 3 && (!unconstrained_rest || switched))) {
+                kind.constrained = true; code = 1;
+            } else if (i == 2) {
+                kind.tau_num = 1; kind.tau_den = 2; code = 2;
+            } else {
+                r = i - 2; R = U;              /* tau_{i-2} of the U unconstrained rounds */
+            }
+        }
+        const int64_t before = cut;
+        int rc = round_impl(g, k, Lmax, p, r, R, false, P.data(), &cut, nullptr, &o, kind);
+        if (rc != UPRO_OK) return rc;
+        if (round_cuts) round_cuts[i] = cut;
+        if (kinds) kinds[i - 1] = code;
+        const int64_t imp = before - cut;
+        if (schedule == 1) {
+            if (i == 1) imp1 = imp;
+            if (i == 2) unconstrained_rest = imp > imp1;
+            if (i >= 3 && code == 0 && 500 * imp < before) switched = true;
+        }
     }
     memcpy(part, P.data(), sizeof(int32_t) * g.n);
     if (cut_out) *cut_out = cut;

@@ -60,10 +60,8 @@ struct SortBuf {
 };
 
 // Host-side F_r[l] = floor(tau_r * (3/2)^l * 2^Q), tau_r = tau_1 + (1 - tau_1)(r-1)/max(R-1,1)
-void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F) {
-    const int64_t D = R > 1 ? (int64_t)R - 1 : 1;
-    const u128 num = (u128)(t1n * D + (t1d - t1n) * (int64_t)(r - 1));
-    const u128 den = (u128)(t1d * D);
+// F[l] = floor(tau * (3/2)^l * 2^Q) for tau = num / den
+void factors_tau(u128 num, u128 den, int64_t *F) {
     for (int l = kSlotLo; l <= kSlotHi; l++) {
         u128 p3 = 1, p2 = 1;
         for (int i = 0; i < (l >= 0 ? l : -l); i++) { p3 *= 3; p2 *= 2; }
@@ -72,6 +70,24 @@ void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F)
         F[l - kSlotLo] = (int64_t)((a << kQ) / b);
     }
 }
+
+void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F) {
+    const int64_t D = R > 1 ? (int64_t)R - 1 : 1;
+    factors_tau((u128)(t1n * D + (t1d - t1n) * (int64_t)(r - 1)), (u128)(t1d * D), F);
+}
+
+// The kind of a round (Sec. 6.2): unconstrained with tau_r of the schedule
+// (tau_den = 0) or a given tau, or constrained: no move may leave its target
+// above L_max.  A constrained round uses the factor 2^51 in every slot: the
+// penalty of any move that overfills its target is then at least 2^31, more
+// than any gain (omega(I(v)) < 2^31), so such a move is never a candidate
+// and never kept, exactly as if it were forbidden; moves that do not
+// overfill pay nothing, as in every round.
+struct RoundKind {
+    bool constrained = false;
+    int64_t tau_num = 0, tau_den = 0;
+};
+constexpr int64_t kConstrainedF = (int64_t)1 << 51;
 
 }  // namespace
 
@@ -336,6 +352,7 @@ struct RoundInfo {
     float ms_table = 0, ms_select = 0, ms_rebalance = 0, ms_sequence = 0;
     int tables = 0;
     bool graph = false;         // the rebalancing loop ran as one graph launch
+    bool constrained = false;   // a constrained round (Sec. 6.2)
 };
 
 // Trace destinations on the host (debug entry only).
@@ -567,7 +584,8 @@ bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
 constexpr upr_status kRedoDense = 100;     // internal: run the round again on the dense table
 constexpr upr_status kRedoFresh = 101;     // internal: run the round again on freshly built sparse rows
 
-upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
+upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr,
+                          const RoundKind &kind) {
     cudaStream_t s = c->s;
     const GraphDev &G = c->G;
     const int64_t n = c->n;
@@ -600,7 +618,12 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
                 tr ? tr->avail_d : nullptr, tr ? tr->slot_d : nullptr, s, c->cut_pending ? c->cut_parts : nullptr,
                 c->cut);
         c->cut_pending = false;
-        penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
+        if (kind.constrained)
+            for (int l = 0; l < kSlots; l++) c->hF[l] = kConstrainedF;
+        else if (kind.tau_den > 0)
+            factors_tau((u128)kind.tau_num, (u128)kind.tau_den, c->hF);
+        else
+            penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
         UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
         Penalty pen{c->PW, c->F, c->C0, c->Lb, c->first_slot};
         // ---- (b2) best move per boundary node
@@ -879,10 +902,11 @@ void ensure_dense(upr_ctx *c) {
 
 // A round; when a sparse row overflows, the round runs again from the same
 // state on rows built afresh, and when fresh rows overflow, on the dense table.
-upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr) {
+upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, RoundInfo &ri, TraceSink *tr,
+                     const RoundKind &kind = RoundKind()) {
     for (;;) {
         ri = RoundInfo{};
-        const upr_status rc = run_round_once(c, r, R, rebalance_only, ri, tr);
+        const upr_status rc = run_round_once(c, r, R, rebalance_only, ri, tr, kind);
         if (rc == kRedoFresh) {
             c->table_valid = false;
             continue;
@@ -974,6 +998,7 @@ void add_round(upr_stats &st, const RoundInfo &ri, bool repair) {
     st.ms_gain_table += ri.ms_table; st.gain_table_builds += ri.tables;
     st.n_rebalance_moves += ri.n_rebal; st.subrounds += ri.subrounds; st.n_sequence += ri.n_seq;
     st.rebalance_graphs += ri.graph ? 1 : 0;
+    st.constrained_rounds += ri.constrained ? 1 : 0;
     st.n_applied += ri.best_len;
     if (repair) return;
     st.rounds_run++;
@@ -992,6 +1017,10 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
     if (c->prm.round_offset + rounds > total) return UPR_ERR_INVALID;
     const int32_t ng = c->ng, K = c->G.K();
+    // the round driver of Sec. 6.2 decides round by round from one graph's
+    // cut, over a whole schedule in one call
+    const int sch = c->prm.schedule;
+    if (sch != 0 && (ng != 1 || c->prm.round_offset != 0 || c->prm.total_rounds != 0)) return UPR_ERR_INVALID;
     upr_stats st{};
     const auto t_host0 = std::chrono::steady_clock::now();
     const long long launches0 = g_upr_launches.load();
@@ -999,7 +1028,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     // one graph with a balanced input: the first round's bucket pass, which
     // reads omega(v, V_P(v)) and omega(I(v)) of every node anyway, gives the
     // cut, instead of a pass over the edges
-    bool defer_cut = ng == 1 && rounds >= 1;
+    bool defer_cut = ng == 1 && rounds >= 1 && sch == 0;
     upr_status rc = load_part(c, part, !defer_cut);
     if (rc != UPR_OK) return rc;
     std::vector<int64_t> cin(ng), cout(ng), C0h(K);
@@ -1019,6 +1048,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     bool balanced = true;
     for (int32_t b = 0; b < K; b++) balanced = balanced && C0h[b] <= c->Lmax_g[b / c->k];
     std::vector<int32_t> keep(ng, 0);
+    int64_t repair_gain = 0;
     if (!balanced) {
         RoundInfo ri;
         rc = run_round(c, 0, total, true, ri, nullptr);
@@ -1026,12 +1056,43 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
         if (rc != UPR_OK) return rc;
         if (ng > 1) read_i32(c, c->infeas_g, ng, keep.data());
         st.repaired_input = 1;
+        repair_gain = ri.best_gain;
     }
+    // schedule 1 (Sec. 6.2): round 1 constrained, round 2 unconstrained with
+    // tau = 1/2; rounds 3..R-1 unconstrained (tau_i of a schedule over those
+    // R-3 rounds) if round 2 improved the cut more than round 1, until one of
+    // them improves it by less than 0.002 of the cut before it, constrained
+    // otherwise; round R constrained.  Schedule 2: every round constrained.
+    bool unconstrained_rest = false, switched = false;
+    int64_t imp1 = 0, cut_now = st.cut_in - repair_gain;
     for (int32_t i = 1; i <= rounds; i++) {
         RoundInfo ri;
-        rc = run_round(c, c->prm.round_offset + i, total, false, ri, nullptr);
+        RoundKind kind;
+        int32_t r = c->prm.round_offset + i, R = total;
+        if (sch == 2) {
+            kind.constrained = true;
+        } else if (sch == 1) {
+            if (i == 1 || (rounds >= 3 && i == rounds) || (i >= 3 && (!unconstrained_rest || switched))) {
+                kind.constrained = true;
+            } else if (i == 2) {
+                kind.tau_num = 1;
+                kind.tau_den = 2;
+            } else {
+                r = i - 2;
+                R = rounds - 3;
+            }
+        }
+        rc = run_round(c, r, R, false, ri, nullptr, kind);
         if (rc != UPR_OK) return rc;
+        ri.constrained = kind.constrained;
         add_round(st, ri, false);
+        const int64_t imp = ri.best_gain, before = cut_now;
+        cut_now -= imp;
+        if (sch == 1) {
+            if (i == 1) imp1 = imp;
+            if (i == 2) unconstrained_rest = imp > imp1;
+            if (i >= 3 && !kind.constrained && 500 * imp < before) switched = true;
+        }
     }
     store_part(c, part, keep);
     read_i64(c, c->cut, ng, cout.data());
@@ -1087,6 +1148,7 @@ void upr_params_default(upr_params *p) {
     p->autotune = 1;
     p->table = 0;
     p->graphs = 1;
+    p->schedule = 0;
     p->stream = nullptr;
 }
 
@@ -1109,7 +1171,7 @@ static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
-           p.table >= 0 && p.table <= 3;
+           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 2;
 }
 
 }  // extern "C"

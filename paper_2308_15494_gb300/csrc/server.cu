@@ -74,7 +74,10 @@ struct upr_server {
     bool stop = false;
     int device = 0;
 
-    bool small(const Job &j) const { return p.batch_max_jobs > 1 && j.n <= p.batch_max_nodes; }
+    // batches need the plain round schedule (the round driver decides per graph)
+    bool small(const Job &j) const {
+        return p.batch_max_jobs > 1 && p.params.schedule == 0 && j.n <= p.batch_max_nodes;
+    }
 
     // Extra bytes slot i must reserve to run work of footprint f.
     size_t extra(int i, size_t f) const { return f > held[i] ? f - held[i] : 0; }

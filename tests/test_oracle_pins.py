@@ -451,3 +451,121 @@ def test_round_pins_on_skewed_and_weighted_graphs(name):
     assert rc == oracle.OK and cutv == brute.cut(w, newp)
     assert np.all(np.diff(rcuts) <= 0)
     assert np.all(brute.block_weights(w, newp) <= brute.lmax(w))
+
+
+# ---------------------------------------------------------------- Sec. 6.2: constrained rounds, round driver
+def test_constrained_selection_bruteforce(w):
+    """A constrained round (Sec. 6.2, read as: no move may leave its target
+    above L_max): the best target by gain among the blocks the node fits into,
+    by brute-force cut differences; no penalty otherwise."""
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 1, kind=("constrained",))
+    assert rc == oracle.OK
+    edges = brute.coo(w)
+    c = brute.node_w(w)
+    C = brute.block_weights(w, w.part)
+    L = brute.lmax(w)
+    W = brute.table(w, w.part)
+    cut0 = brute.cut(w, w.part, edges)
+    for v in range(w.n):
+        a = w.part[v]
+        best = None
+        if W[v, a] < W[v].sum():
+            for b in range(w.k):
+                if b == a or W[v, b] == 0 or C[b] + c[v] > L:
+                    continue
+                gain = cut0 - brute.cut(w, brute.apply(w.part, [v], b), edges)
+                if best is None or gain > best[0]:
+                    best = (gain, b)
+        if best is not None and best[0] > 0:
+            assert (tr["cand_target"][v], tr["cand_s0"][v], tr["cand_gain"][v]) == (best[1], best[0], best[0])
+        else:
+            assert tr["cand_target"][v] == -1
+
+
+def test_constrained_round_keeps_every_block_within_lmax(w):
+    """M of a constrained round: per target, candidates by (s0 desc, id) are
+    kept while the inflow still fits; after M no block exceeds L_max, so the
+    rebalancing has nothing to do."""
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 1, kind=("constrained",))
+    c = brute.node_w(w)
+    C = brute.block_weights(w, w.part)
+    L = brute.lmax(w)
+    tgt, s0, g = tr["cand_target"], tr["cand_s0"], tr["cand_gain"]
+    expect = {}
+    for t in range(w.k):
+        inflow = 0
+        for v in sorted([v for v in range(w.n) if tgt[v] == t], key=lambda v: (-s0[v], v)):
+            if C[t] + inflow + c[v] <= L and g[v] > 0:
+                expect[v] = (t, int(g[v]))
+            inflow += int(c[v])
+    Mn, Mt, Ms = tr["M"]
+    assert {int(v): (int(t), int(s)) for v, t, s in zip(Mn, Mt, Ms)} == expect
+    C1 = brute.block_weights(w, _after_M(w, tr))
+    assert np.all(C1 <= L) or np.any(C > L)
+    if np.all(C <= L):
+        assert tr["n_rebal"] == 0
+
+
+def test_constrained_round_on_a_tight_case_differs_from_unconstrained():
+    """The reading matters on a tight case: the unconstrained round overfills
+    blocks (rebalancing moves follow), the constrained one does not."""
+    w = synth.random_small(11, 400, 8, 8, weighted=True, max_vw=20)
+    w.eps = 0.005
+    rc0, _, _, tu = oracle.run_round(w, w.part, 1, 1, p=oracle.params(tau1=(1, 4)))
+    rc1, _, _, tc = oracle.run_round(w, w.part, 1, 1, kind=("constrained",))
+    assert rc0 == rc1 == oracle.OK
+    if np.all(brute.block_weights(w, w.part) <= brute.lmax(w)):
+        assert tu["n_rebal"] > 0 and tc["n_rebal"] == 0
+        assert tc["n_moves"] > 0
+
+
+@pytest.mark.parametrize("num,den", [(1, 2), (3, 5)])
+def test_given_tau_equals_schedule_tau(num, den):
+    """An unconstrained round with a given tau is the schedule's round 1 of 1
+    with tau_1 = tau (Sec. 4.4)."""
+    for i in (0, 3, 5):
+        w = small(i)
+        a = oracle.run_round(w, w.part, 1, 1, kind=("tau", num, den))
+        b = oracle.run_round(w, w.part, 1, 1, p=oracle.params(tau1=(num, den)))
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
+        assert np.array_equal(a[3]["factor"], b[3]["factor"])
+
+
+def _expected_kinds(cuts, rounds):
+    """The Sec. 6.2 rule restated on the cuts the rounds produced."""
+    kinds, unc_rest, switched = [], False, False
+    for i in range(1, rounds + 1):
+        if i == 1 or (rounds >= 3 and i == rounds) or (i >= 3 and (not unc_rest or switched)):
+            kind = oracle.CONSTRAINED
+        elif i == 2:
+            kind = oracle.UNCONSTRAINED_HALF
+        else:
+            kind = oracle.UNCONSTRAINED
+        kinds.append(kind)
+        imp, before = int(cuts[i - 1] - cuts[i]), int(cuts[i - 1])
+        if i == 2:
+            unc_rest = imp > int(cuts[0] - cuts[1])
+        if i >= 3 and kind == oracle.UNCONSTRAINED and Fraction(imp, max(before, 1)) < Fraction(2, 1000):
+            switched = True
+    return kinds
+
+
+@pytest.mark.parametrize("rounds", [1, 2, 3, 6, 10])
+def test_round_driver_follows_the_rule(rounds):
+    seen = set()
+    for i in range(len(SMALL)):
+        w = small(i)
+        rc, p, cut, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, 1)
+        assert rc == oracle.OK
+        assert list(kinds) == _expected_kinds(cuts, rounds)
+        assert cut == cuts[-1] == oracle.cut(w, p)[0]
+        assert all(cuts[j + 1] <= cuts[j] for j in range(rounds))
+        assert np.all(brute.block_weights(w, p) <= brute.lmax(w))
+        seen.add(tuple(kinds))
+        # schedule 0 is the plain refinement, schedule 2 only constrained rounds
+        r0 = oracle.refine_schedule(w, w.part, rounds, 0)
+        r1 = oracle.refine(w, w.part, rounds=rounds)
+        assert np.array_equal(r0[1], r1[1]) and r0[2] == r1[2]
+        assert list(oracle.refine_schedule(w, w.part, rounds, 2)[4]) == [oracle.CONSTRAINED] * rounds
+    if rounds >= 6:
+        assert len(seen) > 1        # both branches of the decision are exercised

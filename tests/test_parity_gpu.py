@@ -361,6 +361,57 @@ def test_tuned_schedules_shared_between_contexts(upr):
     assert (s2.select_lanes, s2.propose_lanes) == (s1.select_lanes, s1.propose_lanes)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "chung_lu_1k", "rmat_s12_k64",
+                                  "heavy_weights", "isolated"])
+def test_round_driver_same_results(upr, name, schedule):
+    """The round driver of Sec. 6.2 (1: constrained / tau = 1/2 decision,
+    unconstrained rounds until the improvement drops below 0.002 of the cut,
+    constrained last round; 2: constrained rounds only) equals the oracle's."""
+    w = CASES[name]()
+    rounds = 7
+    rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, schedule)
+    prm = upr.upr_params_default()
+    prm.schedule = schedule
+    ctx = upr.create_from_workload(w, params=prm)
+    p = w.part.copy()
+    if rc != oracle.OK:
+        with pytest.raises(upr.UprError):
+            upr.upr_refine(ctx, p, rounds)
+        return
+    st = upr.upr_refine(ctx, p, rounds)
+    assert np.array_equal(p, p0), name
+    assert st.cut_out == c0
+    assert st.constrained_rounds == int((kinds == oracle.CONSTRAINED).sum())
+
+
+def test_round_driver_on_a_tight_case(upr):
+    w = synth.random_small(11, 4000, 8, 16, weighted=True, max_vw=20)
+    w.eps = 0.005
+    for schedule in (1, 2):
+        rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 6, schedule)
+        prm = upr.upr_params_default()
+        prm.schedule = schedule
+        ctx = upr.create_from_workload(w, params=prm)
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, 6)
+        assert np.array_equal(p, p0) and st.cut_out == c0
+
+
+def test_round_driver_needs_one_graph_and_a_whole_schedule(upr):
+    prm = upr.upr_params_default()
+    prm.schedule = 1
+    ws = [synth.random_small(60 + i, 100, 4, 4) for i in range(3)]
+    ctx = upr.create_batch_from_workloads(ws, params=prm)
+    with pytest.raises(upr.UprError):
+        upr.upr_batch_refine(ctx, np.concatenate([w.part for w in ws]).astype(np.int32), 3)
+    w = ws[0]
+    prm.round_offset = 1
+    ctx = upr.create_from_workload(w, params=prm)
+    with pytest.raises(upr.UprError):
+        upr.upr_refine(ctx, w.part.copy(), 3)
+
+
 def test_sparse_table_chosen_by_size(upr):
     """Auto layout: hashed rows for k >= 128 when they take at most half the
     dense table's bytes (sparse graphs), the dense table otherwise."""
