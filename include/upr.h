@@ -109,8 +109,14 @@ typedef struct {
                                     constrained; round R constrained; 2 every round
                                     constrained.  A constrained round is the same round
                                     with every move that would leave its target above
-                                    L_max forbidden.  1 and 2 need one graph,
-                                    round_offset = 0 and total_rounds = 0. 0                */
+                                    L_max forbidden.  The variants of Sec. 7.2, each with
+                                    the same switch to constrained rounds and a
+                                    constrained last round: 3 constant penalty (tau =
+                                    tau_1 every round), 4 fully unconstrained (no penalty,
+                                    nothing forbidden), 5 limited imbalance (no penalty,
+                                    no block above alpha * L_max, alpha from 2 to 1.1).
+                                    1..5 need one graph, round_offset = 0 and
+                                    total_rounds = 0. 0                                     */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 

@@ -101,7 +101,7 @@ def _load():
         lib.upro_refine.argtypes = [GP, I32, I64, PP, P, I32, I32, I32, P, P]
         lib.upro_refine.restype = ctypes.c_int
         lib.upro_refine_schedule.argtypes = [GP, I32, I64, PP, P, I32, I32, P, P, P]
-        lib.upro_round_kind.argtypes = [GP, I32, I64, PP, I32, I64, I64, P, P, TP]
+        lib.upro_round_kind.argtypes = [GP, I32, I64, PP, I32, I64, I64, I64, P, P, TP]
         lib.upro_round_kind.restype = ctypes.c_int
         lib.upro_refine_schedule.restype = ctypes.c_int
         _lib = lib
@@ -181,8 +181,8 @@ def penalty_sequence(w, part, block: int, nodes, r: int = 1, R: int = 1,
 def run_round(w, part, r: int, R: int, rebalance_only: bool = False, p: Optional[Params] = None,
               kind: Optional[tuple] = None):
     """One round on a copy of part.  Returns (rc, new_part, cut, trace dict).
-    kind (Sec. 6.2): ("constrained",) or ("tau", num, den) instead of the
-    schedule's tau_r."""
+    kind (Sec. 6.2, 7.2): ("constrained",), ("tau", num, den) or ("limit",
+    L) (no penalty, no block above L) instead of the schedule's tau_r."""
     n, k = w.n, w.k
     g = _G(w)
     part = np.array(part, dtype=np.int32, copy=True)
@@ -204,9 +204,10 @@ def run_round(w, part, r: int, R: int, rebalance_only: bool = False, p: Optional
                                 r, R, int(rebalance_only), _ptr(part), ctypes.byref(c), ctypes.byref(t))
     else:
         con = kind[0] == "constrained"
-        num, den = (0, 0) if con else (kind[1], kind[2])
+        num, den = (kind[1], kind[2]) if kind[0] == "tau" else (0, 0)
+        limit = kind[1] if kind[0] == "limit" else 0
         rc = _load().upro_round_kind(ctypes.byref(g.s), k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
-                                     int(con), num, den, _ptr(part), ctypes.byref(c), ctypes.byref(t))
+                                     int(con), num, den, limit, _ptr(part), ctypes.byref(c), ctypes.byref(t))
     tr = {"n_cand": t.n_cand, "n_moves": t.n_moves, "n_rebal": t.n_rebal, "subrounds": t.subrounds,
           "n_inter": t.n_inter, "n_seq": t.n_seq, "best_len": t.best_len, "best_gain": t.best_gain,
           "cut_before": t.cut_before, "cut_after": t.cut_after}
@@ -238,8 +239,9 @@ def refine(w, part, rounds: Optional[int] = None, round_offset: int = 0,
     return rc, part, int(c.value), rcuts
 
 
-# Round kinds reported by refine_schedule (the round driver of Sec. 6.2).
-UNCONSTRAINED, CONSTRAINED, UNCONSTRAINED_HALF = 0, 1, 2
+# Round kinds reported by refine_schedule (the round driver of Sec. 6.2 and
+# the variants of Sec. 7.2).
+UNCONSTRAINED, CONSTRAINED, UNCONSTRAINED_HALF, CONSTANT_TAU, NO_PENALTY, LIMITED = 0, 1, 2, 3, 4, 5
 
 
 def refine_schedule(w, part, rounds: int, schedule: int, p: Optional[Params] = None):
@@ -247,7 +249,9 @@ def refine_schedule(w, part, rounds: int, schedule: int, p: Optional[Params] = N
     (tau schedule over the rounds), 1 = the paper's integration (constrained
     round, unconstrained round with tau = 1/2, then unconstrained or
     constrained rounds by the improvements, constrained last round), 2 =
-    every round constrained.  Returns (rc, new_part, cut, per-round cuts
+    every round constrained; the variants of Sec. 7.2 (3 constant tau =
+    tau_1, 4 fully unconstrained, 5 limited imbalance 2 -> 1.1), each with
+    the switch to constrained rounds and a constrained last round.  Returns (rc, new_part, cut, per-round cuts
     [rounds+1], kind of each round [rounds])."""
     g = _G(w)
     part = np.array(part, dtype=np.int32, copy=True)

@@ -246,6 +246,11 @@ struct RoundOut {
 struct RoundKind {
     bool constrained = false;
     int64_t tau_num = 0, tau_den = 0;
+    /* the variants of Sec. 7.2: limit > 0 replaces the penalty by a block
+     * limit: a move that would leave its target above `limit` (with the
+     * inflow of better-ranked candidates) is forbidden, every other move
+     * pays nothing.  A constrained round is limit = L_max. */
+    int64_t limit = 0;
 };
 
 int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, int32_t r,
@@ -285,6 +290,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
         auto pen_of = [&](int32_t b, int64_t x, int64_t cu) -> int64_t {
             int lvl;
             if (kind.constrained) return x > 0 ? FORBID : 0;
+            if (kind.limit > 0) return x + Lmax > kind.limit ? FORBID : 0;   /* x + L_max: the new weight */
             return penalty(BW, b, x, cu, F, &lvl);
         };
         if (tr && tr->bucket) memcpy(tr->bucket, BW.data(), sizeof(int64_t) * BW.size());
@@ -622,10 +628,10 @@ int upro_round(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_para
 /* One round of a given kind (Sec. 6.2): constrained != 0, or unconstrained
  * with tau = tau_num / tau_den.  Otherwise as upro_round with r = R = 1. */
 int upro_round_kind(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t constrained,
-                    int64_t tau_num, int64_t tau_den, int32_t *part, int64_t *cut, upro_trace *tr) {
+                    int64_t tau_num, int64_t tau_den, int64_t limit, int32_t *part, int64_t *cut, upro_trace *tr) {
     upro_params p = pp ? *pp : defaults();
-    if (!params_ok(p) || k < 2 || (!constrained && (tau_den <= 0 || tau_num < 0 || tau_num > tau_den ||
-                                                    tau_den > 65536)))
+    if (!params_ok(p) || k < 2 || limit < 0 ||
+        (!constrained && limit == 0 && (tau_den <= 0 || tau_num < 0 || tau_num > tau_den || tau_den > 65536)))
         return UPRO_ERR_INVALID;
     Graph g = wrap(gg);
     int64_t tot = 0;
@@ -635,6 +641,7 @@ int upro_round_kind(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro
     kind.constrained = constrained != 0;
     kind.tau_num = constrained ? 0 : tau_num;
     kind.tau_den = constrained ? 0 : tau_den;
+    kind.limit = constrained ? 0 : limit;
     std::vector<int32_t> backup(part, part + g.n);
     int rc = round_impl(g, k, lmax_of(tot, k, eps_ppm), p, 1, 1, false, part, cut, tr, &o, kind);
     if (rc != UPRO_OK) memcpy(part, backup.data(), sizeof(int32_t) * g.n);
@@ -687,13 +694,21 @@ int upro_refine(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_par
  *   such a round improves the cut by less than 0.002 of the cut before it,
  *   the remaining ones are constrained; otherwise rounds 3..R-1 are
  *   constrained; round R (R >= 3) is constrained.
+ * The variants of Sec. 7.2 (schedules 3-5) run rounds 1..R-1 of their kind
+ * and round R constrained (R >= 2); as in the paper's experiments, once a
+ * variant round improves the cut by less than 0.002 of the cut before it,
+ * the remaining rounds are constrained.  3: constant penalty, tau = tau_1 in
+ * every round; 4: fully unconstrained, no penalty and nothing forbidden;
+ * 5: limited imbalance, no penalty but no block above alpha_i * L_max, alpha
+ * going linearly from 2 (round 1) to 1.1 (round R-1), limit rounded down.
  * kinds[i-1] (may be NULL) receives round i's kind: 0 unconstrained (tau of
- * the schedule), 1 constrained, 2 unconstrained with tau = 1/2. */
+ * the schedule), 1 constrained, 2 unconstrained with tau = 1/2, 3 constant
+ * tau, 4 no penalty, 5 limited imbalance. */
 int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t *part,
                          int32_t rounds, int32_t schedule, int64_t *cut_out, int64_t *round_cuts, int8_t *kinds) {
     upro_params p = pp ? *pp : defaults();
     Graph g = wrap(gg);
-    if (!params_ok(p) || k < 2 || rounds < 0 || rounds > 65536 || schedule < 0 || schedule > 2)
+    if (!params_ok(p) || k < 2 || rounds < 0 || rounds > 65536 || schedule < 0 || schedule > 5)
         return UPRO_ERR_INVALID;
     for (int64_t v = 0; v < g.n; v++) if (part[v] < 0 || part[v] >= k) return UPRO_ERR_INVALID;
     int64_t tot = 0;
@@ -718,8 +733,16 @@ int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const
         RoundKind kind;
         int8_t code = 0;
         int32_t r = i, R = rounds;
-        if (schedule == 2) {
+        if (schedule == 2 || (schedule >= 3 && ((rounds >= 2 && i == rounds) || switched))) {
             kind.constrained = true; code = 1;
+        } else if (schedule == 3) {
+            kind.tau_num = p.tau1_num; kind.tau_den = p.tau1_den; code = 3;
+        } else if (schedule == 4) {
+            kind.limit = INT64_MAX; code = 4;
+        } else if (schedule == 5) {
+            const int64_t D = rounds > 2 ? rounds - 2 : 1;            /* alpha over rounds 1..R-1 */
+            kind.limit = (int64_t)(((i128)Lmax * (20 * D - 9 * (int64_t)(i - 1))) / (10 * D));
+            code = 5;
         } else if (schedule == 1) {
             if (i == 1 || (rounds >= 3 && i == rounds) || (i >= 3 && (!unconstrained_rest || switched))) {
                 kind.constrained = true; code = 1;
@@ -740,6 +763,7 @@ int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const
             if (i == 2) unconstrained_rest = imp > imp1;
             if (i >= 3 && code == 0 && 500 * imp < before) switched = true;
         }
+        if (schedule >= 3 && code != 1 && 500 * imp < before) switched = true;
     }
     memcpy(part, P.data(), sizeof(int32_t) * g.n);
     if (cut_out) *cut_out = cut;

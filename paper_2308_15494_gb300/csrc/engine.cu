@@ -86,8 +86,17 @@ void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F)
 struct RoundKind {
     bool constrained = false;
     int64_t tau_num = 0, tau_den = 0;
+    // the variants of Sec. 7.2: limit > 0 replaces the penalty by a block
+    // limit (no move may leave its target above it, every other move pays
+    // nothing): the selection sees L = limit and the factor 2^51 as above.
+    int64_t limit = 0;
 };
 constexpr int64_t kConstrainedF = (int64_t)1 << 51;
+
+__global__ void k_fill_i64(int64_t *a, int64_t n, int64_t v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
 
 }  // namespace
 
@@ -172,6 +181,7 @@ struct upr_ctx {
     HubChunk *hub_chunks; int64_t n_chunks = 0;
     TableTile *tiles = nullptr; int64_t n_tiles = 0; int32_t tile_nodes = 0;
     int64_t *Lb; int32_t *gid;          // [K] L_max per block; [n] graph of each node (batches)
+    int64_t *Lsel;                      // [K] the selection's block limit in a limited round (Sec. 7.2)
     int32_t *seg_beg, *seg_end, *over0_g, *light_g, *infeas_g, *inf0_g; long long *best_g, *best_j; int64_t *tot;
     int32_t *part_in;                   // batches: the input partition (global ids)
     int64_t *noff_d;                    // batches: [ng + 1] first node of each graph
@@ -223,6 +233,7 @@ void layout(upr_ctx *c, Arena &A) {
     const size_t ng = (size_t)c->ng;
     const size_t n2 = 2 * n;
     c->Lb = A.take<int64_t>(k);
+    c->Lsel = A.take<int64_t>(k);
     c->gid = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
     c->part_in = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
     c->noff_d = A.take<int64_t>(ng + 1);
@@ -618,14 +629,18 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
                 tr ? tr->avail_d : nullptr, tr ? tr->slot_d : nullptr, s, c->cut_pending ? c->cut_parts : nullptr,
                 c->cut);
         c->cut_pending = false;
-        if (kind.constrained)
+        if (kind.constrained || kind.limit > 0)
             for (int l = 0; l < kSlots; l++) c->hF[l] = kConstrainedF;
         else if (kind.tau_den > 0)
             factors_tau((u128)kind.tau_num, (u128)kind.tau_den, c->hF);
         else
             penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
         UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
-        Penalty pen{c->PW, c->F, c->C0, c->Lb, c->first_slot};
+        if (kind.limit > 0) {
+            k_fill_i64<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(c->Lsel, K, kind.limit);
+            UPR_LAUNCH_CHECK();
+        }
+        Penalty pen{c->PW, c->F, c->C0, kind.limit > 0 ? c->Lsel : c->Lb, c->first_slot};
         // ---- (b2) best move per boundary node
         run_tuned(c, c->sel_tuned, c->sel_cfg, c->sel_cands, &c->sel_pending, c->ev_tune, [&](LaneCfg cfg) {
             select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, cfg, s);
@@ -1069,8 +1084,16 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
         RoundInfo ri;
         RoundKind kind;
         int32_t r = c->prm.round_offset + i, R = total;
-        if (sch == 2) {
+        if (sch == 2 || (sch >= 3 && ((rounds >= 2 && i == rounds) || switched))) {
             kind.constrained = true;
+        } else if (sch == 3) {                       // constant penalty, tau = tau_1
+            kind.tau_num = c->prm.tau1_num;
+            kind.tau_den = c->prm.tau1_den;
+        } else if (sch == 4) {                       // fully unconstrained
+            kind.limit = INT64_MAX;
+        } else if (sch == 5) {                       // limited imbalance, alpha 2 -> 1.1
+            const int64_t D = rounds > 2 ? rounds - 2 : 1;
+            kind.limit = (int64_t)(((i128)c->Lmax * (20 * D - 9 * (int64_t)(i - 1))) / (10 * D));
         } else if (sch == 1) {
             if (i == 1 || (rounds >= 3 && i == rounds) || (i >= 3 && (!unconstrained_rest || switched))) {
                 kind.constrained = true;
@@ -1093,6 +1116,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
             if (i == 2) unconstrained_rest = imp > imp1;
             if (i >= 3 && !kind.constrained && 500 * imp < before) switched = true;
         }
+        if (sch >= 3 && !kind.constrained && 500 * imp < before) switched = true;
     }
     store_part(c, part, keep);
     read_i64(c, c->cut, ng, cout.data());
@@ -1171,7 +1195,7 @@ static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
-           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 2;
+           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5;
 }
 
 }  // extern "C"

@@ -569,3 +569,84 @@ def test_round_driver_follows_the_rule(rounds):
         assert list(oracle.refine_schedule(w, w.part, rounds, 2)[4]) == [oracle.CONSTRAINED] * rounds
     if rounds >= 6:
         assert len(seen) > 1        # both branches of the decision are exercised
+
+
+@pytest.mark.parametrize("factor", [(11, 10), (3, 2), (2, 1), None])
+def test_limited_round_selection_bruteforce(w, factor):
+    """The variants of Sec. 7.2 without a penalty: the best target by gain
+    among the blocks whose weight with the node stays within the limit
+    (alpha * L_max, or no limit at all: fully unconstrained)."""
+    L = brute.lmax(w)
+    limit = (2 ** 62) if factor is None else L * factor[0] // factor[1]
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 1, kind=("limit", limit))
+    assert rc == oracle.OK
+    edges = brute.coo(w)
+    c = brute.node_w(w)
+    C = brute.block_weights(w, w.part)
+    W = brute.table(w, w.part)
+    cut0 = brute.cut(w, w.part, edges)
+    for v in range(w.n):
+        a = w.part[v]
+        best = None
+        if W[v, a] < W[v].sum():
+            for b in range(w.k):
+                if b == a or W[v, b] == 0 or C[b] + c[v] > limit:
+                    continue
+                gain = cut0 - brute.cut(w, brute.apply(w.part, [v], b), edges)
+                if best is None or gain > best[0]:
+                    best = (gain, b)
+        if best is not None and best[0] > 0:
+            assert (tr["cand_target"][v], tr["cand_s0"][v], tr["cand_gain"][v]) == (best[1], best[0], best[0])
+        else:
+            assert tr["cand_target"][v] == -1
+    # M: per target, kept while the inflow fits under the limit
+    tgt, s0, g = tr["cand_target"], tr["cand_s0"], tr["cand_gain"]
+    expect = {}
+    for t in range(w.k):
+        inflow = 0
+        for v in sorted([v for v in range(w.n) if tgt[v] == t], key=lambda v: (-s0[v], v)):
+            if C[t] + inflow + c[v] <= limit and g[v] > 0:
+                expect[v] = (t, int(g[v]))
+            inflow += int(c[v])
+    Mn, Mt, Ms = tr["M"]
+    assert {int(v): (int(t), int(s)) for v, t, s in zip(Mn, Mt, Ms)} == expect
+
+
+def _expected_variant_kinds(cuts, rounds, schedule, Lmax):
+    """Sec. 7.2 variants: their kind until a round improves the cut by less
+    than 0.002 of it, then constrained; the last round constrained."""
+    kinds, limits, switched = [], [], False
+    D = max(rounds - 2, 1)
+    for i in range(1, rounds + 1):
+        if (rounds >= 2 and i == rounds) or switched:
+            kind, lim = oracle.CONSTRAINED, None
+        else:
+            kind = {3: oracle.CONSTANT_TAU, 4: oracle.NO_PENALTY, 5: oracle.LIMITED}[schedule]
+            lim = int(Fraction(Lmax) * (2 - Fraction(9, 10) * Fraction(i - 1, D))) if schedule == 5 else None
+        kinds.append(kind)
+        limits.append(lim)
+        imp, before = int(cuts[i - 1] - cuts[i]), int(cuts[i - 1])
+        if kind != oracle.CONSTRAINED and Fraction(imp, max(before, 1)) < Fraction(2, 1000):
+            switched = True
+    return kinds, limits
+
+
+@pytest.mark.parametrize("schedule", [3, 4, 5])
+def test_variant_schedules_follow_the_rule(schedule):
+    for i in (0, 1, 3, 5):
+        w = small(i)
+        rounds = 6
+        p = oracle.params(tau1=(1, 2))
+        rc, part, cut, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, schedule, p=p)
+        assert rc == oracle.OK
+        kinds_e, limits = _expected_variant_kinds(cuts, rounds, schedule, brute.lmax(w))
+        assert list(kinds) == kinds_e
+        assert cut == oracle.cut(w, part)[0] and np.all(brute.block_weights(w, part) <= brute.lmax(w))
+        # replaying the rounds one by one with the kinds found gives the same cuts
+        P = np.array(w.part, np.int32)
+        for r, (kd, lim) in enumerate(zip(kinds_e, limits), start=1):
+            kind = (("constrained",) if kd == oracle.CONSTRAINED else
+                    ("tau", 1, 2) if kd == oracle.CONSTANT_TAU else
+                    ("limit", 2 ** 62) if kd == oracle.NO_PENALTY else ("limit", lim))
+            _, P, c, _ = oracle.run_round(w, P, 1, 1, kind=kind)
+            assert c == cuts[r]

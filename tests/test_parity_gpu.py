@@ -361,18 +361,23 @@ def test_tuned_schedules_shared_between_contexts(upr):
     assert (s2.select_lanes, s2.propose_lanes) == (s1.select_lanes, s1.propose_lanes)
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "chung_lu_1k", "rmat_s12_k64",
                                   "heavy_weights", "isolated"])
 def test_round_driver_same_results(upr, name, schedule):
     """The round driver of Sec. 6.2 (1: constrained / tau = 1/2 decision,
     unconstrained rounds until the improvement drops below 0.002 of the cut,
-    constrained last round; 2: constrained rounds only) equals the oracle's."""
+    constrained last round; 2: constrained rounds only) and the variants of
+    Sec. 7.2 (3: constant tau = 1/2, 4: fully unconstrained, 5: limited
+    imbalance 2 -> 1.1) equal the oracle's."""
     w = CASES[name]()
     rounds = 7
-    rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, schedule)
+    op = oracle.params(tau1=(1, 2)) if schedule == 3 else None
+    rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, schedule, p=op)
     prm = upr.upr_params_default()
     prm.schedule = schedule
+    if schedule == 3:
+        prm.tau1_num, prm.tau1_den = 1, 2
     ctx = upr.create_from_workload(w, params=prm)
     p = w.part.copy()
     if rc != oracle.OK:
@@ -388,7 +393,7 @@ def test_round_driver_same_results(upr, name, schedule):
 def test_round_driver_on_a_tight_case(upr):
     w = synth.random_small(11, 4000, 8, 16, weighted=True, max_vw=20)
     w.eps = 0.005
-    for schedule in (1, 2):
+    for schedule in (1, 2, 4, 5):
         rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 6, schedule)
         prm = upr.upr_params_default()
         prm.schedule = schedule
