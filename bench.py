@@ -324,20 +324,21 @@ def other_configs_leg(args, upr):
     import torch
     peak, _ = _peaks()
     out = {}
-    legs = (("chung_lu_n16384_k8", "plain_tiny", 20, 0, 0), ("rgg_2^22_weighted_k256", "plain_weighted", 3, 0, 0),
-            ("rgg_2^22_weighted_k256_dense_table", "plain_weighted", 3, 1, 0),
-            ("rgg_2^22_weighted_k256_hashed_table", "plain_weighted", 3, 2, 0),
-            ("rmat_s22_k64_round_driver", "plain_large", 3, 0, 1),
-            ("rmat_s22_k64_constant_tau_half", "plain_large", 3, 0, 3),
-            ("rmat_s22_k64_fully_unconstrained", "plain_large", 3, 0, 4),
-            ("rmat_s22_k64_limited_imbalance", "plain_large", 3, 0, 5))
-    for name, builder, steps, table, schedule in legs:
+    legs = (("chung_lu_n16384_k8", "plain_tiny", 20, {}), ("rgg_2^22_weighted_k256", "plain_weighted", 3, {}),
+            ("rgg_2^22_weighted_k256_dense_table", "plain_weighted", 3, {"table": 1}),
+            ("rgg_2^22_weighted_k256_hashed_table", "plain_weighted", 3, {"table": 2}),
+            ("rgg_2^22_weighted_k256_gain_priority", "plain_weighted", 3, {"gain_priority": 1}),
+            ("rmat_s22_k64_round_driver", "plain_large", 3, {"schedule": 1}),
+            ("rmat_s22_k64_constant_tau_half", "plain_large", 3, {"schedule": 3, "tau1_num": 1, "tau1_den": 2}),
+            ("rmat_s22_k64_fully_unconstrained", "plain_large", 3, {"schedule": 4}),
+            ("rmat_s22_k64_limited_imbalance", "plain_large", 3, {"schedule": 5}),
+            ("rmat_s22_k64_appended_sequence", "plain_large", 3, {"append": 1}))
+    for name, builder, steps, over in legs:
         w = synth.cached(getattr(synth, builder))
         prm = upr.upr_params_default()
-        prm.table = table
-        prm.schedule = schedule
-        if schedule == 3:
-            prm.tau1_num, prm.tau1_den = 1, 2         # the paper's constant penalty tau = 0.5
+        for key, val in over.items():
+            setattr(prm, key, val)
+        table, schedule = prm.table, prm.schedule
         ctx = upr.create_from_workload(w, params=prm, device=True)
         init = torch.from_numpy(w.part.copy()).cuda()
         part = torch.empty_like(init)
@@ -365,6 +366,8 @@ def other_configs_leg(args, upr):
                      "schedule": ["every round unconstrained", "round driver of Sec. 6.2",
                                   "every round constrained", "constant penalty tau = 0.5 (Sec. 7.2)",
                                   "fully unconstrained (Sec. 7.2)", "limited imbalance 2 -> 1.1 (Sec. 7.2)"][schedule],
+                     "rebalancing_priority": "gain alone (Sec. 7.2)" if prm.gain_priority else "g/c, g*c (Sec. 6.1)",
+                     "sequence": "appended (Sec. 7.2)" if prm.append else "interleaved (Sec. 4.4)",
                      "constrained_rounds": st.constrained_rounds,
                      "gain_table_ms": t_build, "gain_table_gbs": st.gain_table_bytes / (t_build / 1e3) / 1e9,
                      "gain_table_frac": st.gain_table_bytes / (t_build / 1e3) / 1e9 / peak}

@@ -117,6 +117,12 @@ typedef struct {
                                     no block above alpha * L_max, alpha from 2 to 1.1).
                                     1..5 need one graph, round_offset = 0 and
                                     total_rounds = 0. 0                                     */
+    int32_t gain_priority;       /* rebalancing priority: 0 g/c(u) for g < 0 and g*c(u)
+                                    for g >= 0 (Sec. 6.1); 1 the gain alone (the variant
+                                    of Sec. 7.2), ties by node id either way. 0             */
+    int32_t append;              /* move sequence: 0 the rebalancing moves interleaved with
+                                    M (Sec. 4.4); 1 appended after M in their order (the
+                                    variant of Sec. 7.2). 0                                  */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 

@@ -66,7 +66,7 @@ class Graph(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("t_num", ctypes.c_int32), ("t_den", ctypes.c_int32),
                 ("tau1_num", ctypes.c_int32), ("tau1_den", ctypes.c_int32),
-                ("max_subrounds", ctypes.c_int32)]
+                ("max_subrounds", ctypes.c_int32), ("gain_priority", ctypes.c_int32), ("append", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -128,8 +128,8 @@ class _G:
         self.s = Graph(w.n, _ptr(xa), _ptr(ad), _ptr(aw), _ptr(vw))
 
 
-def params(t=(7, 10), tau1=(1, 4), max_subrounds=64) -> Params:
-    return Params(t[0], t[1], tau1[0], tau1[1], max_subrounds)
+def params(t=(7, 10), tau1=(1, 4), max_subrounds=64, gain_priority=0, append=0) -> Params:
+    return Params(t[0], t[1], tau1[0], tau1[1], max_subrounds, gain_priority, append)
 
 
 def lmax(total_weight: int, k: int, eps: float) -> int:

@@ -53,6 +53,9 @@ typedef struct {
     int32_t t_num, t_den;       /* availability threshold t (Sec. 4.3); 7/10 */
     int32_t tau1_num, tau1_den; /* tau_1 of the penalty schedule (Sec. 4.4); 1/4 */
     int32_t max_subrounds;      /* rebalancing sub-round limit; 64 */
+    int32_t gain_priority;      /* 1: rebalancing priority = gain alone (the variant of Sec. 7.2); 0 */
+    int32_t append;             /* 1: the rebalancing moves appended after M instead of
+                                   interleaved (the variant of Sec. 7.2); 0 */
 } upro_params;
 
 /* Optional per-round trace; every pointer may be NULL.  Node-sized arrays
@@ -390,7 +393,12 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
             }
             if (have) props.push_back(Proposal{(int32_t)u, a, bt, bg, cu});
         }
-        std::sort(props.begin(), props.end(), higher_priority);
+        if (p.gain_priority)      /* Sec. 7.2 variant: the gain alone, higher first, then smaller id */
+            std::sort(props.begin(), props.end(), [](const Proposal &a, const Proposal &b) {
+                return a.g != b.g ? a.g > b.g : a.u < b.u;
+            });
+        else
+            std::sort(props.begin(), props.end(), higher_priority);
         /* per source: the minimal prefix that removes the excess */
         std::vector<int64_t> taken(k, 0);
         std::vector<Proposal> sel;
@@ -432,7 +440,10 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
     std::vector<std::vector<Move>> Rb(k);
     for (const Move &mv : Rseq) Rb[mv.from].push_back(mv);
     std::vector<Move> X;
-    {
+    if (p.append) {             /* Sec. 7.2 variant: M, then the rebalancing moves in their order */
+        X = M;
+        X.insert(X.end(), Rseq.begin(), Rseq.end());
+    } else {
         std::vector<int64_t> Xw(C);
         std::vector<size_t> q(k, 0);
         for (const Move &mv : M) {
@@ -530,10 +541,11 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
 
 bool params_ok(const upro_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_num >= 0 &&
-           p.tau1_num <= p.tau1_den && p.tau1_den <= 65536 && p.max_subrounds >= 1;
+           p.tau1_num <= p.tau1_den && p.tau1_den <= 65536 && p.max_subrounds >= 1 &&
+           (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
 }
 
-upro_params defaults() { return upro_params{7, 10, 1, 4, 64}; }
+upro_params defaults() { return upro_params{7, 10, 1, 4, 64, 0, 0}; }
 
 } /* namespace */
 

@@ -487,7 +487,7 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     int32_t *dP = cnt + CNT_L1;
     if (c->prio_hist) {
         rebalance_prefilter(G, c->idxA, cnt + CNT_L1, n, nullptr, c->prop_gain, c->part, c->over_d, c->C, c->gbits,
-                            c->cbits, c->prio_hist, c->prio_cut, c->flags2, s);
+                            c->cbits, c->prm.gain_priority, c->prio_hist, c->prio_cut, c->flags2, s);
         select_flags(c->flags2, c->idxD, cnt + CNT_P, Count{cnt + CNT_L1, n}, c->tmp, s);
         rebalance_gather_list(c->idxA, c->idxD, cnt + CNT_P, c->Pq, n, s);
         Pn = c->Pq;
@@ -495,7 +495,8 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     }
     const Count cP{dP, n};
     uint64_t *kA; uint32_t *A;
-    rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->sb[0].k, c->sb[0].v, n, s);
+    rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->prm.gain_priority, c->sb[0].k, c->sb[0].v,
+                        n, s);
     c->sb[0].run(cP, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
     // per source: the minimal prefix covering the excess
     uint64_t *kB; uint32_t *B;
@@ -712,10 +713,14 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     }
     UPR_CUDA(cudaEventRecord(c->ev[6], s));
 
-    // ---- (c1) interleave M and R_1..R_k
+    // ---- (c1) interleave M and R_1..R_k (or append R after M: a variant of Sec. 7.2)
     const int32_t *dM = cnt + CNT_M, *dR = &ctl->nR;
     count_affine(dM, 2, nullptr, 0, cnt + CNT_EVM, s);
     count_affine(dM, 1, dR, 0, cnt + CNT_X, s);
+    if (c->prm.append) {
+        seq_append(c->M_node, c->M_from, c->M_to, dM, c->R_node, c->R_from, c->R_to, dR, 2 * n, c->X_node, c->X_from,
+                   c->X_to, c->X_isr, s);
+    } else {
     UPR_CUDA(cudaMemsetAsync(c->rbeg, 0, sizeof(int32_t) * K, s));
     UPR_CUDA(cudaMemsetAsync(c->rend, 0, sizeof(int32_t) * K, s));
     UPR_CUDA(cudaMemsetAsync(c->ebeg, 0, sizeof(int32_t) * K, s));
@@ -742,6 +747,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
                 s);
     seq_place_r(c->R_node, c->R_from, c->R_to, RB, dR, n, c->rbeg, EV, c->ebeg, c->eend, c->qmax, c->pos_m, c->qfin,
                 c->left_excl, c->em_excl, c->emit, dM, c->X_node, c->X_from, c->X_to, c->X_isr, s);
+    }
 
     // ---- (c1) merge double moves
     const Count cX{cnt + CNT_X, 2 * n};
@@ -1173,6 +1179,8 @@ void upr_params_default(upr_params *p) {
     p->table = 0;
     p->graphs = 1;
     p->schedule = 0;
+    p->gain_priority = 0;
+    p->append = 0;
     p->stream = nullptr;
 }
 
@@ -1195,7 +1203,8 @@ static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
-           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5;
+           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5 &&
+           (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
 }
 
 }  // extern "C"

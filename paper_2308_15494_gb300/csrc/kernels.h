@@ -281,10 +281,13 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
 constexpr int kPrioBins = 256;
 void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                          const int32_t *flags, const int32_t *prop_gain, const int32_t *part, const int8_t *over,
-                         const int64_t *C, int gbits, int cbits, unsigned long long *hist, int32_t *cut,
-                         int32_t *keep, cudaStream_t s);
+                         const int64_t *C, int gbits, int cbits, int gain_only, unsigned long long *hist,
+                         int32_t *cut, int32_t *keep, cudaStream_t s);
+// gain_only: the priority is the gain alone (a variant of Sec. 7.2), else g/c
+// for g < 0 and g*c for g >= 0 (Sec. 6.1)
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
-                         int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s);
+                         int gbits, int cbits, int gain_only, uint64_t *keys, uint32_t *vals, int64_t np_max,
+                         cudaStream_t s);
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,
                           const int32_t *blk_of_node, uint64_t *keys, uint32_t *vals, int64_t cnt_max, cudaStream_t s);
 void rebalance_seg_weights(const GraphDev &g, const int32_t *P, const uint32_t *A, const int32_t *S,
@@ -336,6 +339,11 @@ void seq_block_final(int32_t K, const int32_t *ebeg, const int32_t *eend, const 
 void seq_place_m(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM, int64_t max,
                  const int32_t *em_excl, int32_t *pos_m, int32_t *X_node, int32_t *X_from, int32_t *X_to,
                  int8_t *X_isr, cudaStream_t s);
+// X = M followed by R (the appended sequence, a variant of Sec. 7.2); max
+// bounds |M| + |R|
+void seq_append(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM,
+                const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const int32_t *d_nR, int64_t max,
+                int32_t *X_node, int32_t *X_from, int32_t *X_to, int8_t *X_isr, cudaStream_t s);
 void seq_place_r(const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const uint32_t *RB,
                  const int32_t *d_nR, int64_t max, const int32_t *rbeg, const uint32_t *EV, const int32_t *ebeg,
                  const int32_t *eend, const uint64_t *qmax, const int32_t *pos_m, const int32_t *qfin,

@@ -431,13 +431,15 @@ __device__ __forceinline__ uint64_t prio_key(int64_t g, uint64_t c, int gbits, i
     return (1ull << (gbits + S)) | (c == 1 ? num : num / c);     // unit weights need no division
 }
 
+// gain_only (the variant of Sec. 7.2): the priority is the gain alone, the
+// key of weight 1 (g >= 0 first by g, then g < 0 by |g|: g descending).
 __global__ void k_prio_keys(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
                             const int32_t *__restrict__ prop_gain, const int32_t *__restrict__ vwgt, int gbits,
-                            int cbits, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                            int cbits, int gain_only, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t cnt = *d_np;
     UPR_FOR(i, cnt) {
         const int32_t u = P[i];
-        keys[i] = prio_key(prop_gain[u], vwgt ? (uint64_t)vwgt[u] : 1ull, gbits, cbits);
+        keys[i] = prio_key(prop_gain[u], (vwgt && !gain_only) ? (uint64_t)vwgt[u] : 1ull, gbits, cbits);
         vals[i] = (uint32_t)i;
     }
 }
@@ -471,7 +473,8 @@ __global__ void __launch_bounds__(256) k_prio_hist(const int32_t *__restrict__ l
                                                    const int32_t *__restrict__ flags,
                                                    const int32_t *__restrict__ prop_gain,
                                                    const int32_t *__restrict__ vwgt, const int32_t *__restrict__ part,
-                                                   int gbits, int cbits, unsigned long long *__restrict__ hist) {
+                                                   int gbits, int cbits, int gain_only,
+                                                   unsigned long long *__restrict__ hist) {
     __shared__ uint32_t s_key[kHistSlots];
     __shared__ unsigned long long s_val[kHistSlots];
     for (int i = threadIdx.x; i < kHistSlots; i += blockDim.x) { s_key[i] = kHistEmpty; s_val[i] = 0; }
@@ -481,7 +484,8 @@ __global__ void __launch_bounds__(256) k_prio_hist(const int32_t *__restrict__ l
         if (flags && !flags[i]) continue;
         const int32_t u = list[i];
         const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
-        const uint32_t key = (uint32_t)part[u] * kPrioBins + prio_bin(prio_key(prop_gain[u], c, gbits, cbits), gbits, cbits);
+        const uint32_t key = (uint32_t)part[u] * kPrioBins +
+                             prio_bin(prio_key(prop_gain[u], gain_only ? 1ull : c, gbits, cbits), gbits, cbits);
         uint32_t h = (key * 0x9E3779B1u) >> 21;          // 11 bits: kHistSlots
         bool done = false;
         for (int probe = 0; probe < 32 && !done; probe++) {
@@ -539,14 +543,16 @@ __global__ void __launch_bounds__(kPrioBins) k_prio_cut(int32_t K, const int8_t 
 __global__ void k_prio_keep(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n1,
                             const int32_t *__restrict__ flags, const int32_t *__restrict__ prop_gain,
                             const int32_t *__restrict__ vwgt, const int32_t *__restrict__ part,
-                            const int32_t *__restrict__ cut, int gbits, int cbits, int32_t *__restrict__ keep) {
+                            const int32_t *__restrict__ cut, int gbits, int cbits, int gain_only,
+                            int32_t *__restrict__ keep) {
     const int64_t n1 = *d_n1;
     UPR_FOR(i, n1) {
         int32_t k = 0;
         if (!flags || flags[i]) {
             const int32_t u = list[i];
             const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
-            k = prio_bin(prio_key(prop_gain[u], c, gbits, cbits), gbits, cbits) <= cut[part[u]] ? 1 : 0;
+            k = prio_bin(prio_key(prop_gain[u], gain_only ? 1ull : c, gbits, cbits), gbits, cbits) <= cut[part[u]]
+                    ? 1 : 0;
         }
         keep[i] = k;
     }
@@ -764,22 +770,25 @@ void rebalance_propose_list(const GraphDev &g, const int32_t *list, const int32_
 
 void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                          const int32_t *flags, const int32_t *prop_gain, const int32_t *part, const int8_t *over,
-                         const int64_t *C, int gbits, int cbits, unsigned long long *hist, int32_t *cut,
-                         int32_t *keep, cudaStream_t s) {
+                         const int64_t *C, int gbits, int cbits, int gain_only, unsigned long long *hist,
+                         int32_t *cut, int32_t *keep, cudaStream_t s) {
     if (n1_max <= 0) return;
     const unsigned hist_grid = (unsigned)std::min<int64_t>(ceil_div(n1_max, 256), (int64_t)device_sm_count() * 4);
-    k_prio_hist<<<hist_grid, 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, gbits, cbits, hist);
+    k_prio_hist<<<hist_grid, 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, gbits, cbits, gain_only,
+                                          hist);
     UPR_LAUNCH_CHECK();
     k_prio_cut<<<(unsigned)std::min<int64_t>(g.K(), 4096), kPrioBins, 0, s>>>(g.K(), over, C, g.Lb, hist, cut);
     UPR_LAUNCH_CHECK();
-    k_prio_keep<<<grid_for(n1_max), 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, cut, gbits, cbits, keep);
+    k_prio_keep<<<grid_for(n1_max), 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, cut, gbits, cbits,
+                                                 gain_only, keep);
     UPR_LAUNCH_CHECK();
 }
 
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
-                         int gbits, int cbits, uint64_t *keys, uint32_t *vals, int64_t np_max, cudaStream_t s) {
+                         int gbits, int cbits, int gain_only, uint64_t *keys, uint32_t *vals, int64_t np_max,
+                         cudaStream_t s) {
     if (np_max <= 0) return;
-    k_prio_keys<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, gbits, cbits, keys, vals);
+    k_prio_keys<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, gbits, cbits, gain_only, keys, vals);
     UPR_LAUNCH_CHECK();
 }
 

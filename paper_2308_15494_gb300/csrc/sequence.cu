@@ -701,6 +701,24 @@ __global__ void __launch_bounds__(512) k_table_rollback_hubs(Rollback rb, const 
     }
 }
 
+// The variant of Sec. 7.2 without interleaving: X = M, then R in its order.
+__global__ void k_seq_append(const int32_t *__restrict__ M_node, const int32_t *__restrict__ M_from,
+                             const int32_t *__restrict__ M_to, const int32_t *__restrict__ d_nM,
+                             const int32_t *__restrict__ R_node, const int32_t *__restrict__ R_from,
+                             const int32_t *__restrict__ R_to, const int32_t *__restrict__ d_nR,
+                             int32_t *__restrict__ X_node, int32_t *__restrict__ X_from, int32_t *__restrict__ X_to,
+                             int8_t *__restrict__ X_isr) {
+    const int64_t nM = *d_nM, nR = *d_nR;
+    UPR_FOR(i, nM + nR) {
+        const bool r = i >= nM;
+        const int64_t j = r ? i - nM : i;
+        X_node[i] = r ? R_node[j] : M_node[j];
+        X_from[i] = r ? R_from[j] : M_from[j];
+        X_to[i] = r ? R_to[j] : M_to[j];
+        X_isr[i] = r ? 1 : 0;
+    }
+}
+
 __global__ void k_reset_nodes(const int32_t *__restrict__ nodes, const int32_t *__restrict__ d_cnt,
                               int32_t *__restrict__ arr, int32_t val) {
     const int64_t cnt = *d_cnt;
@@ -893,6 +911,15 @@ void table_rollback(const GraphDev &g, const Rollback &rb, int64_t max, const in
                                                                  deg_sum, g.m, g.sp);
         UPR_LAUNCH_CHECK();
     }
+}
+
+void seq_append(const int32_t *M_node, const int32_t *M_from, const int32_t *M_to, const int32_t *d_nM,
+                const int32_t *R_node, const int32_t *R_from, const int32_t *R_to, const int32_t *d_nR, int64_t max,
+                int32_t *X_node, int32_t *X_from, int32_t *X_to, int8_t *X_isr, cudaStream_t s) {
+    if (max <= 0) return;
+    k_seq_append<<<grid_for(max), 256, 0, s>>>(M_node, M_from, M_to, d_nM, R_node, R_from, R_to, d_nR, X_node, X_from,
+                                              X_to, X_isr);
+    UPR_LAUNCH_CHECK();
 }
 
 void seq_sort_by_graph(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,

@@ -650,3 +650,75 @@ def test_variant_schedules_follow_the_rule(schedule):
                     ("limit", 2 ** 62) if kd == oracle.NO_PENALTY else ("limit", lim))
             _, P, c, _ = oracle.run_round(w, P, 1, 1, kind=kind)
             assert c == cuts[r]
+
+
+def test_gain_priority_reduces_to_the_paper_rule_for_unit_weights():
+    """With unit node weights g/c(u) and g*c(u) are g itself, so the gain-only
+    rebalancing priority (the variant of Sec. 7.2) gives the same rounds; with
+    node weights it orders the proposals differently."""
+    for seed in (21, 22, 23):
+        w = synth.random_small(seed, 300, 6, 8, max_vw=1)
+        w.eps = 0.01
+        a = oracle.refine(w, w.part, rounds=4)
+        b = oracle.refine(w, w.part, rounds=4, p=oracle.params(gain_priority=1))
+        assert np.array_equal(a[1], b[1]) and a[2] == b[2]
+    differ = False
+    for seed in (31, 32, 33, 34):
+        w = synth.random_small(seed, 400, 6, 8, max_vw=40)
+        w.eps = 0.01
+        a = oracle.run_round(w, w.part, 1, 1)
+        b = oracle.run_round(w, w.part, 1, 1, p=oracle.params(gain_priority=1))
+        assert a[0] == b[0] == oracle.OK
+        assert np.all(brute.block_weights(w, b[1]) <= brute.lmax(w))
+        differ = differ or not np.array_equal(np.stack(a[3]["R"][:3]), np.stack(b[3]["R"][:3])) \
+            if len(a[3]["R"][0]) == len(b[3]["R"][0]) else True
+    assert differ
+
+
+def test_gain_priority_orders_rebalancing_by_gain():
+    """Gain-only priority: within a sub-round, each source's moves taken in
+    order of the gain of the move at the time (higher first, then id) — a
+    node of lower gain is never moved out of a source while one of higher gain
+    that fits its target stays; checked on the first sub-round by brute force."""
+    w = synth.random_small(41, 300, 6, 6, max_vw=30)
+    w.eps = 0.01
+    rc, _, _, tr = oracle.run_round(w, w.part, 1, 1, p=oracle.params(gain_priority=1))
+    assert rc == oracle.OK
+    Rn, Rf, Rt, Rs = tr["R"]
+    first = [i for i in range(len(Rn)) if Rs[i] == 1]
+    if not first:
+        pytest.skip("no rebalancing in this round")
+    P1 = _after_M(w, tr)
+    edges = brute.coo(w)
+    cut1 = brute.cut(w, P1, edges)
+    gains = [cut1 - brute.cut(w, brute.apply(P1, [int(Rn[i])], int(Rt[i])), edges) for i in first]
+    for src in set(int(Rf[i]) for i in first):
+        seq = [(g, int(Rn[i])) for g, i in zip(gains, first) if int(Rf[i]) == src]
+        # the sources' moves appear in the sequence in admission order, which
+        # is the priority order restricted to the admitted proposals
+        assert seq == sorted(seq, key=lambda x: (-x[0], x[1]))
+
+
+@pytest.mark.parametrize("i", [0, 3, 5])
+def test_appended_sequence_is_M_then_R(i):
+    """The variant of Sec. 7.2 without interleaving: the sequence before the
+    merge is M in its order followed by R in its order; M and R themselves are
+    those of the interleaving round, and the result is balanced."""
+    w = small(i)
+    w.eps = 0.01
+    a = oracle.run_round(w, w.part, 1, 1)
+    b = oracle.run_round(w, w.part, 1, 1, p=oracle.params(append=1))
+    assert a[0] == b[0] == oracle.OK
+    ta, tb = a[3], b[3]
+    for key in ("M", "R"):
+        for x, y in zip(ta[key], tb[key]):
+            assert np.array_equal(x, y)
+    Mn, Mt, _ = tb["M"]
+    Rn, Rf, Rt, _ = tb["R"]
+    Xn, Xf, Xt = tb["X"]
+    assert np.array_equal(Xn, np.concatenate([Mn, Rn])) and np.array_equal(Xt, np.concatenate([Mt, Rt]))
+    assert np.array_equal(Xf, np.concatenate([np.asarray(w.part)[Mn], Rf]))
+    # the interleaved X is a reordering of the same moves
+    key = lambda X: sorted(zip(X[0].tolist(), X[1].tolist(), X[2].tolist()))
+    assert key(ta["X"]) == key(tb["X"])
+    assert np.all(brute.block_weights(w, b[1]) <= brute.lmax(w))

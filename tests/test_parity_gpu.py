@@ -390,6 +390,50 @@ def test_round_driver_same_results(upr, name, schedule):
     assert st.constrained_rounds == int((kinds == oracle.CONSTRAINED).sum())
 
 
+@pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "heavy_weights", "rmat_s12_k64"])
+def test_gain_priority_same_results(upr, name):
+    """Rebalancing by the gain alone (the variant of Sec. 7.2) equals the oracle."""
+    w = CASES[name]()
+    w.eps = 0.01
+    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=4, p=oracle.params(gain_priority=1))
+    prm = upr.upr_params_default()
+    prm.gain_priority = 1
+    ctx = upr.create_from_workload(w, params=prm)
+    p = w.part.copy()
+    if rc != oracle.OK:
+        with pytest.raises(upr.UprError):
+            upr.upr_refine(ctx, p, 4)
+        return
+    st = upr.upr_refine(ctx, p, 4)
+    assert np.array_equal(p, p0) and st.cut_out == c0
+
+
+@pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "heavy_weights", "rmat_s12_k64"])
+def test_appended_sequence_same_results(upr, name):
+    """The rebalancing moves appended after M (the variant of Sec. 7.2): the
+    round's lists and the refinement equal the oracle's."""
+    w = CASES[name]()
+    w.eps = 0.01
+    prm = upr.upr_params_default()
+    prm.append = 1
+    ctx = upr.create_from_workload(w, params=prm)
+    op = oracle.params(append=1)
+    rc, p, t = upr.upr_debug_round(ctx, w.part, 1, 3)
+    rc0, p0, c0, o = oracle.run_round(w, w.part, 1, 3, p=op)
+    assert rc == rc0
+    if rc0 == oracle.OK:
+        _compare_traces(t, o)
+        assert np.array_equal(p, p0)
+    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=4, p=op)
+    p = w.part.copy()
+    if rc != oracle.OK:
+        with pytest.raises(upr.UprError):
+            upr.upr_refine(ctx, p, 4)
+        return
+    st = upr.upr_refine(ctx, p, 4)
+    assert np.array_equal(p, p0) and st.cut_out == c0
+
+
 def test_round_driver_on_a_tight_case(upr):
     w = synth.random_small(11, 4000, 8, 16, weighted=True, max_vw=20)
     w.eps = 0.005
