@@ -66,7 +66,8 @@ class Graph(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("t_num", ctypes.c_int32), ("t_den", ctypes.c_int32),
                 ("tau1_num", ctypes.c_int32), ("tau1_den", ctypes.c_int32),
-                ("max_subrounds", ctypes.c_int32), ("gain_priority", ctypes.c_int32), ("append", ctypes.c_int32)]
+                ("max_subrounds", ctypes.c_int32), ("gain_priority", ctypes.c_int32), ("append", ctypes.c_int32),
+                ("lp_rounds", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -103,6 +104,10 @@ def _load():
         lib.upro_refine_schedule.argtypes = [GP, I32, I64, PP, P, I32, I32, P, P, P]
         lib.upro_round_kind.argtypes = [GP, I32, I64, PP, I32, I64, I64, I64, P, P, TP]
         lib.upro_round_kind.restype = ctypes.c_int
+        lib.upro_lp_round.argtypes = [GP, I32, I64, PP, P, P, P, P, TP]
+        lib.upro_lp_round.restype = ctypes.c_int
+        lib.upro_label_propagation.argtypes = [GP, I32, I64, PP, P, I32, P]
+        lib.upro_label_propagation.restype = ctypes.c_int
         lib.upro_refine_schedule.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -128,8 +133,8 @@ class _G:
         self.s = Graph(w.n, _ptr(xa), _ptr(ad), _ptr(aw), _ptr(vw))
 
 
-def params(t=(7, 10), tau1=(1, 4), max_subrounds=64, gain_priority=0, append=0) -> Params:
-    return Params(t[0], t[1], tau1[0], tau1[1], max_subrounds, gain_priority, append)
+def params(t=(7, 10), tau1=(1, 4), max_subrounds=64, gain_priority=0, append=0, lp_rounds=0) -> Params:
+    return Params(t[0], t[1], tau1[0], tau1[1], max_subrounds, gain_priority, append, lp_rounds)
 
 
 def lmax(total_weight: int, k: int, eps: float) -> int:
@@ -261,3 +266,37 @@ def refine_schedule(w, part, rounds: int, schedule: int, p: Optional[Params] = N
     rc = _load().upro_refine_schedule(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
                                       _ptr(part), rounds, schedule, ctypes.byref(c), _ptr(rcuts), _ptr(kinds))
     return rc, part, int(c.value), rcuts, kinds[:rounds]
+
+
+def lp_round(w, part, active, p: Optional[Params] = None):
+    """One round of unconstrained label propagation (Sec. 5) on a copy of part
+    over the active nodes.  Returns (rc, kept, new_part, cut, trace dict with
+    the moves "M" = (node, to, gain) and the rebalancing "R")."""
+    n = w.n
+    g = _G(w)
+    part = np.array(part, dtype=np.int32, copy=True)
+    active = np.ascontiguousarray(active, np.int8)
+    c = ctypes.c_int64(cut(w, part)[0])
+    kept = ctypes.c_int32(0)
+    a = dict(M_node=np.zeros(n, np.int32), M_to=np.zeros(n, np.int32), M_score=np.zeros(n, np.int64),
+             R_node=np.zeros(n, np.int32), R_from=np.zeros(n, np.int32), R_to=np.zeros(n, np.int32),
+             R_subround=np.zeros(n, np.int32))
+    t = Trace(**{key: _ptr(v) for key, v in a.items()})
+    rc = _load().upro_lp_round(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None, _ptr(active),
+                               _ptr(part), ctypes.byref(c), ctypes.byref(kept), ctypes.byref(t))
+    nm, nr = t.n_moves, t.n_rebal
+    tr = {"M": (a["M_node"][:nm], a["M_to"][:nm], a["M_score"][:nm]),
+          "R": (a["R_node"][:nr], a["R_from"][:nr], a["R_to"][:nr], a["R_subround"][:nr]),
+          "cut_before": t.cut_before, "cut_after": t.cut_after}
+    return rc, bool(kept.value), part, int(c.value), tr
+
+
+def label_propagation(w, part, max_rounds: int = 5, p: Optional[Params] = None):
+    """Unconstrained label propagation alone (Sec. 5).  Returns (rounds kept
+    or an error code, new_part, cut)."""
+    g = _G(w)
+    part = np.array(part, dtype=np.int32, copy=True)
+    c = ctypes.c_int64(0)
+    kept = _load().upro_label_propagation(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
+                                          _ptr(part), max_rounds, ctypes.byref(c))
+    return kept, part, int(c.value)

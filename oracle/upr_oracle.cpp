@@ -56,6 +56,8 @@ typedef struct {
     int32_t gain_priority;      /* 1: rebalancing priority = gain alone (the variant of Sec. 7.2); 0 */
     int32_t append;             /* 1: the rebalancing moves appended after M instead of
                                    interleaved (the variant of Sec. 7.2); 0 */
+    int32_t lp_rounds;          /* rounds of unconstrained label propagation before the
+                                   FM rounds (Sec. 5; the paper uses 5); 0 */
 } upro_params;
 
 /* Optional per-round trace; every pointer may be NULL.  Node-sized arrays
@@ -234,6 +236,7 @@ int64_t cut_of(const Graph &g, const int32_t *part) {
 struct RoundOut {
     int64_t n_cand = 0, n_moves = 0, n_rebal = 0, n_seq = 0, best_len = 0, best_gain = 0;
     int32_t subrounds = 0;
+    bool lp_kept = false;     /* label propagation: the round's result was kept */
 };
 
 /*
@@ -254,6 +257,10 @@ struct RoundKind {
      * inflow of better-ranked candidates) is forbidden, every other move
      * pays nothing.  A constrained round is limit = L_max. */
     int64_t limit = 0;
+    /* unconstrained label propagation (Sec. 5): active[v] != 0 marks V_a;
+     * the round moves every active node to its best positive-gain block,
+     * rebalances, and keeps the result only if it is balanced and cuts less */
+    const int8_t *lp_active = nullptr;
 };
 
 int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, int32_t r,
@@ -274,7 +281,32 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
     std::vector<int32_t> Pp(part, part + n);  /* P' = P o M */
     std::vector<int64_t> Cp(C);
 
-    if (!rebalance_only) {
+    if (kind.lp_active) {
+        /* ---- label propagation (Sec. 5): every active node to the
+         * neighbouring block of the highest positive gain (ties to the smaller
+         * block), all against the round-start partition, balance ignored ---- */
+        for (int64_t v = 0; v < n; v++) {
+            if (!kind.lp_active[v]) continue;
+            const int64_t own = T.at(v, part[v]);
+            int64_t best = 0; int32_t bt = -1;
+            for (int32_t b = 0; b < k; b++) {
+                if (b == part[v] || T.at(v, b) <= 0) continue;
+                const int64_t gv = (int64_t)T.at(v, b) - own;
+                if (gv > best) { best = gv; bt = b; }
+            }
+            if (bt >= 0) {
+                M.push_back(Move{(int32_t)v, part[v], bt, 0});
+                if (tr && tr->M_node) { tr->M_node[M.size() - 1] = (int32_t)v; tr->M_to[M.size() - 1] = bt; tr->M_score[M.size() - 1] = best; }
+            }
+        }
+        out->n_moves = (int64_t)M.size();
+        for (const Move &mv : M) {
+            Pp[mv.v] = mv.to;
+            Cp[mv.from] -= g.c(mv.v);
+            Cp[mv.to] += g.c(mv.v);
+            table_move(g, T, mv.v, mv.from, mv.to);
+        }
+    } else if (!rebalance_only) {
         /* ---- step 2: V_r, slots, buckets B_{i,j} (Alg. 1, Sec. 4.3) ---- */
         std::vector<int64_t> BW((size_t)k * NSLOT, 0);
         for (int64_t v = 0; v < n; v++) {
@@ -435,6 +467,25 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
             tr->R_node[i] = Rseq[i].v; tr->R_from[i] = Rseq[i].from;
             tr->R_to[i] = Rseq[i].to; tr->R_subround[i] = Rsub[i];
         }
+    if (kind.lp_active) {
+        /* label propagation: keep the moved and rebalanced partition only if
+         * it is balanced and cuts strictly less (Sec. 5: the net improvement
+         * check, else the rollback) */
+        bool bal = true;
+        for (int32_t b = 0; b < k; b++) bal = bal && Cp[b] <= Lmax;
+        const int64_t cut1 = cut_of(g, Pp.data());
+        out->lp_kept = bal && cut1 < cut0;
+        if (tr) {
+            tr->n_cand = out->n_moves; tr->n_moves = out->n_moves; tr->n_rebal = out->n_rebal;
+            tr->subrounds = out->subrounds; tr->cut_before = cut0;
+        }
+        if (out->lp_kept) {
+            memcpy(part, Pp.data(), sizeof(int32_t) * n);
+            *cut = cut1;
+        }
+        if (tr) tr->cut_after = *cut;
+        return UPRO_OK;
+    }
 
     /* ---- step 7: interleaved sequence I (Sec. 4.4) ---- */
     std::vector<std::vector<Move>> Rb(k);
@@ -539,13 +590,58 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
     return UPRO_OK;
 }
 
+/* V_a after a kept label-propagation round (Sec. 5): the neighbours of the
+ * nodes whose block changed that did not change block themselves. */
+void lp_next_active(const Graph &g, const int32_t *before, const int32_t *after, std::vector<int8_t> &active) {
+    std::fill(active.begin(), active.end(), 0);
+    for (int64_t v = 0; v < g.n; v++) {
+        if (before[v] == after[v]) continue;
+        for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; e++) {
+            const int32_t u = g.adj[e];
+            if (before[u] == after[u]) active[u] = 1;
+        }
+    }
+}
+
+/* Unconstrained label propagation before the FM rounds (Sec. 5): V_a starts
+ * as the boundary nodes; a round that is not kept ends it, as do
+ * max_rounds rounds, an empty V_a, or a kept round whose improvement is below
+ * 0.001 of the cut before it.  Returns the rounds kept. */
+int32_t label_propagation(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, int32_t max_rounds,
+                          int32_t *P, int64_t *cut) {
+    std::vector<int8_t> active(g.n, 0);
+    {
+        Table T;
+        build_table(g, k, P, T);
+        for (int64_t v = 0; v < g.n; v++) active[v] = T.at(v, P[v]) < T.wI[v];   /* boundary nodes */
+    }
+    int32_t kept = 0;
+    for (int32_t r = 1; r <= max_rounds; r++) {
+        bool any = false;
+        for (int8_t a : active) any = any || a;
+        if (!any) break;
+        std::vector<int32_t> before(P, P + g.n);
+        const int64_t cut_before = *cut;
+        RoundKind kind;
+        kind.lp_active = active.data();
+        RoundOut o;
+        round_impl(g, k, Lmax, p, 1, 1, false, P, cut, nullptr, &o, kind);
+        if (!o.lp_kept) break;
+        kept++;
+        if (1000 * (cut_before - *cut) < cut_before) break;
+        lp_next_active(g, before.data(), P, active);
+    }
+    return kept;
+}
+
 bool params_ok(const upro_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_num >= 0 &&
            p.tau1_num <= p.tau1_den && p.tau1_den <= 65536 && p.max_subrounds >= 1 &&
-           (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
+           (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1) &&
+           p.lp_rounds >= 0 && p.lp_rounds <= 64;
 }
 
-upro_params defaults() { return upro_params{7, 10, 1, 4, 64, 0, 0}; }
+upro_params defaults() { return upro_params{7, 10, 1, 4, 64, 0, 0, 0}; }
 
 } /* namespace */
 
@@ -637,6 +733,40 @@ int upro_round(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_para
     return rc;
 }
 
+/* One round of unconstrained label propagation (Sec. 5) over the active
+ * nodes (active[v] != 0); *kept = 1 when its result was kept (part and cut
+ * updated), 0 when it was rolled back.  The trace's M holds the label
+ * propagation moves (M_score = their gain), R the rebalancing. */
+int upro_lp_round(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, const int8_t *active,
+                  int32_t *part, int64_t *cut, int32_t *kept, upro_trace *tr) {
+    upro_params p = pp ? *pp : defaults();
+    if (!params_ok(p) || k < 2 || !active) return UPRO_ERR_INVALID;
+    Graph g = wrap(gg);
+    int64_t tot = 0;
+    for (int64_t v = 0; v < g.n; v++) tot += g.c(v);
+    RoundOut o;
+    RoundKind kind;
+    kind.lp_active = active;
+    int rc = round_impl(g, k, lmax_of(tot, k, eps_ppm), p, 1, 1, false, part, cut, tr, &o, kind);
+    if (kept) *kept = o.lp_kept ? 1 : 0;
+    return rc;
+}
+
+/* Unconstrained label propagation alone (Sec. 5) on a balanced partition:
+ * returns the number of rounds kept, or an error. */
+int upro_label_propagation(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t *part,
+                           int32_t max_rounds, int64_t *cut_out) {
+    upro_params p = pp ? *pp : defaults();
+    if (!params_ok(p) || k < 2 || max_rounds < 0) return UPRO_ERR_INVALID;
+    Graph g = wrap(gg);
+    int64_t tot = 0;
+    for (int64_t v = 0; v < g.n; v++) tot += g.c(v);
+    int64_t cut = cut_of(g, part);
+    const int32_t kept = label_propagation(g, k, lmax_of(tot, k, eps_ppm), p, max_rounds, part, &cut);
+    if (cut_out) *cut_out = cut;
+    return kept;
+}
+
 /* One round of a given kind (Sec. 6.2): constrained != 0, or unconstrained
  * with tau = tau_num / tau_den.  Otherwise as upro_round with r = R = 1. */
 int upro_round_kind(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t constrained,
@@ -686,6 +816,7 @@ int upro_refine(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_par
         int rc = round_impl(g, k, Lmax, p, 0, total_rounds, true, P.data(), &cut, nullptr, &o);
         if (rc != UPRO_OK) return rc;
     }
+    if (p.lp_rounds > 0) label_propagation(g, k, Lmax, p, p.lp_rounds, P.data(), &cut);
     if (round_cuts) round_cuts[0] = cut;
     for (int32_t i = 1; i <= rounds; i++) {
         int rc = round_impl(g, k, Lmax, p, round_offset + i, total_rounds, false, P.data(), &cut, nullptr, &o);
@@ -737,6 +868,7 @@ int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const
         int rc = round_impl(g, k, Lmax, p, 0, rounds > 0 ? rounds : 1, true, P.data(), &cut, nullptr, &o);
         if (rc != UPRO_OK) return rc;
     }
+    if (p.lp_rounds > 0) label_propagation(g, k, Lmax, p, p.lp_rounds, P.data(), &cut);
     if (round_cuts) round_cuts[0] = cut;
     bool unconstrained_rest = false, switched = false;
     int64_t imp1 = 0;

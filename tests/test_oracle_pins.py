@@ -722,3 +722,82 @@ def test_appended_sequence_is_M_then_R(i):
     key = lambda X: sorted(zip(X[0].tolist(), X[1].tolist(), X[2].tolist()))
     assert key(ta["X"]) == key(tb["X"])
     assert np.all(brute.block_weights(w, b[1]) <= brute.lmax(w))
+
+
+# ---------------------------------------------------------------- Sec. 5: unconstrained label propagation
+def _boundary(w, part):
+    W = brute.table(w, part)
+    return np.array([W[v, part[v]] < W[v].sum() for v in range(w.n)], np.int8)
+
+
+def test_lp_round_moves_bruteforce(w):
+    """Every active node moves to the neighbouring block of the highest
+    positive gain (brute-force cut differences, ties to the smaller block),
+    all against the round-start partition."""
+    active = _boundary(w, w.part)
+    rc, kept, part, cut, tr = oracle.lp_round(w, w.part, active)
+    assert rc == oracle.OK
+    edges = brute.coo(w)
+    W = brute.table(w, w.part)
+    cut0 = brute.cut(w, w.part, edges)
+    expect = {}
+    for v in range(w.n):
+        if not active[v]:
+            continue
+        best = None
+        for b in range(w.k):
+            if b == w.part[v] or W[v, b] == 0:
+                continue
+            gain = cut0 - brute.cut(w, brute.apply(w.part, [v], b), edges)
+            if gain > 0 and (best is None or gain > best[0]):
+                best = (gain, b)
+        if best is not None:
+            expect[v] = (best[1], best[0])
+    Mn, Mt, Ms = tr["M"]
+    assert {int(v): (int(t), int(s)) for v, t, s in zip(Mn, Mt, Ms)} == expect
+
+
+def test_lp_round_keeps_only_a_balanced_improvement(w):
+    rc, kept, part, cut, tr = oracle.lp_round(w, w.part, _boundary(w, w.part))
+    cut0 = oracle.cut(w, w.part)[0]
+    if kept:
+        assert cut < cut0 and cut == oracle.cut(w, part)[0]
+        assert np.all(brute.block_weights(w, part) <= brute.lmax(w))
+        # the kept partition is the moves, then the rebalancing moves
+        Mn, Mt, _ = tr["M"]
+        Rn, Rf, Rt, _ = tr["R"]
+        P = brute.apply(w.part, Mn, Mt)
+        assert np.array_equal(brute.apply(P, Rn, Rt), part)
+    else:
+        assert np.array_equal(part, w.part) and cut == cut0
+
+
+def test_lp_rounds_compose_with_the_active_set_rule():
+    """Rounds after the first run on the unmoved neighbours of the moved nodes;
+    the driver stops at a rolled-back round or below 0.001 improvement."""
+    for seed in (1, 2, 3, 4, 5, 6):
+        w = synth.random_small(seed, 400, 6, 8)
+        P = np.array(w.part, np.int32)
+        active = _boundary(w, P)
+        rounds, cuts = 0, [oracle.cut(w, P)[0]]
+        adj = [w.adj[w.xadj[v]:w.xadj[v + 1]] for v in range(w.n)]
+        for r in range(5):
+            if not active.any():
+                break
+            rc, kept, P1, c1, _ = oracle.lp_round(w, P, active)
+            if not kept:
+                break
+            rounds += 1
+            moved = P1 != P
+            nxt = np.zeros(w.n, np.int8)
+            for v in np.nonzero(moved)[0]:
+                for u in adj[v]:
+                    if not moved[u]:
+                        nxt[u] = 1
+            improvement = cuts[-1] - c1
+            P, active = P1, nxt
+            cuts.append(c1)
+            if 1000 * improvement < cuts[-2]:
+                break
+        kept, Q, c = oracle.label_propagation(w, w.part, 5)
+        assert kept == rounds and np.array_equal(Q, P) and c == cuts[-1]
