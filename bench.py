@@ -332,7 +332,9 @@ def other_configs_leg(args, upr):
             ("rmat_s22_k64_constant_tau_half", "plain_large", 3, {"schedule": 3, "tau1_num": 1, "tau1_den": 2}),
             ("rmat_s22_k64_fully_unconstrained", "plain_large", 3, {"schedule": 4}),
             ("rmat_s22_k64_limited_imbalance", "plain_large", 3, {"schedule": 5}),
-            ("rmat_s22_k64_appended_sequence", "plain_large", 3, {"append": 1}))
+            ("rmat_s22_k64_appended_sequence", "plain_large", 3, {"append": 1}),
+            ("rmat_s22_k64_label_propagation", "plain_large", 3, {"lp_rounds": 5}),
+            ("rmat_s22_k64_label_propagation_round_driver", "plain_large", 3, {"lp_rounds": 5, "schedule": 1}))
     for name, builder, steps, over in legs:
         w = synth.cached(getattr(synth, builder))
         prm = upr.upr_params_default()
@@ -368,9 +370,11 @@ def other_configs_leg(args, upr):
                                   "fully unconstrained (Sec. 7.2)", "limited imbalance 2 -> 1.1 (Sec. 7.2)"][schedule],
                      "rebalancing_priority": "gain alone (Sec. 7.2)" if prm.gain_priority else "g/c, g*c (Sec. 6.1)",
                      "sequence": "appended (Sec. 7.2)" if prm.append else "interleaved (Sec. 4.4)",
+                     "label_propagation_rounds_kept": st.lp_rounds,
                      "constrained_rounds": st.constrained_rounds,
-                     "gain_table_ms": t_build, "gain_table_gbs": st.gain_table_bytes / (t_build / 1e3) / 1e9,
-                     "gain_table_frac": st.gain_table_bytes / (t_build / 1e3) / 1e9 / peak}
+                     "gain_table_ms": t_build or None,
+                     "gain_table_gbs": st.gain_table_bytes / (t_build / 1e3) / 1e9 if t_build else None,
+                     "gain_table_frac": st.gain_table_bytes / (t_build / 1e3) / 1e9 / peak if t_build else None}
         del ctx
     return out
 

@@ -123,6 +123,13 @@ typedef struct {
     int32_t append;              /* move sequence: 0 the rebalancing moves interleaved with
                                     M (Sec. 4.4); 1 appended after M in their order (the
                                     variant of Sec. 7.2). 0                                  */
+    int32_t lp_rounds;           /* rounds of unconstrained label propagation before the
+                                    FM rounds (Sec. 5; the paper uses 5): every active node
+                                    to its best positive-gain block, rebalancing, the round
+                                    kept only if balanced and cutting less; next active set
+                                    = the unmoved neighbours of moved nodes; stops at a
+                                    round not kept, an empty active set or an improvement
+                                    below 0.001 of the cut.  One graph only. 0 = off        */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 
@@ -154,6 +161,7 @@ typedef struct {
     int32_t sparse_table;        /* 1: the rounds ran on the sparse gain table            */
     int32_t rebalance_graphs;    /* rounds whose rebalancing loop ran as one graph launch */
     int32_t constrained_rounds;  /* constrained rounds (schedule 1 or 2)                 */
+    int32_t lp_rounds;           /* label propagation rounds kept (Sec. 5)               */
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */

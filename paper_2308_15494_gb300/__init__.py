@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
     _fields_ = [("t_num", I32), ("t_den", I32), ("tau1_num", I32), ("tau1_den", I32), ("max_subrounds", I32),
                 ("validate", I32), ("round_offset", I32), ("total_rounds", I32), ("autotune", I32), ("table", I32),
                 ("graphs", I32), ("schedule", I32), ("gain_priority", I32), ("append", I32),
-                ("stream", P)]
+                ("lp_rounds", I32), ("stream", P)]
 
 
 class Stats(ctypes.Structure):
@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
                 ("ms_gain_table", D), ("gain_table_builds", I32), ("gain_table_bytes", I64),
                 ("ms_select", D), ("ms_rebalance", D), ("ms_sequence", D), ("ms_host", D),
                 ("batch_graphs", I32), ("select_lanes", I32), ("propose_lanes", I32),
-                ("sparse_table", I32), ("rebalance_graphs", I32), ("constrained_rounds", I32)]
+                ("sparse_table", I32), ("rebalance_graphs", I32), ("constrained_rounds", I32),
+                ("lp_rounds", I32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -182,6 +182,7 @@ struct upr_ctx {
     TableTile *tiles = nullptr; int64_t n_tiles = 0; int32_t tile_nodes = 0;
     int64_t *Lb; int32_t *gid;          // [K] L_max per block; [n] graph of each node (batches)
     int64_t *Lsel;                      // [K] the selection's block limit in a limited round (Sec. 7.2)
+    int8_t *lp_active, *lp_next;        // [n] label propagation: V_a and the next V_a (Sec. 5)
     int32_t *seg_beg, *seg_end, *over0_g, *light_g, *infeas_g, *inf0_g; long long *best_g, *best_j; int64_t *tot;
     int32_t *part_in;                   // batches: the input partition (global ids)
     int64_t *noff_d;                    // batches: [ng + 1] first node of each graph
@@ -234,6 +235,8 @@ void layout(upr_ctx *c, Arena &A) {
     const size_t n2 = 2 * n;
     c->Lb = A.take<int64_t>(k);
     c->Lsel = A.take<int64_t>(k);
+    c->lp_active = A.take<int8_t>(n);
+    c->lp_next = A.take<int8_t>(n);
     c->gid = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
     c->part_in = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
     c->noff_d = A.take<int64_t>(ng + 1);
@@ -586,6 +589,57 @@ bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
     return c->reb_exec != nullptr;
 }
 
+// Step (d): the rebalancing sub-rounds (Sec. 6) on c->part / c->C / the table,
+// host-driven or as one graph launch.  r: the round (for the log).
+void rebalance_phase(upr_ctx *c, int32_t r, RoundInfo &ri, TraceSink *tr) {
+    cudaStream_t s = c->s;
+    const GraphDev &G = c->G;
+    const int64_t n = c->n;
+    const int32_t K = G.K();
+    const bool batch = c->ng > 1;
+    int32_t *cnt = c->counts;
+    RebalCtl *ctl = c->ctl;
+    const Count cN{nullptr, n};
+    if (c->prio_hist)
+        UPR_CUDA(cudaMemsetAsync(c->prio_hist, 0, sizeof(unsigned long long) * K * kPrioBins, s));
+    rebalance_init(G, c->C, c->excl_d, ctl, s);
+    rebalance_flag_in_blocks(c->part, n, c->excl_d, c->flags, s);
+    select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
+    int32_t *light = batch ? c->light_g : &ctl->light;
+    const RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
+    auto t_sub = std::chrono::steady_clock::now();
+    // the loop runs on the device as one graph once the proposal schedule is
+    // settled (the host-driven form times the schedules, logs and traces);
+    // a small binding first has to run a few rounds to pay for the capture
+    const bool tuning = !c->prop_tuned && worth_tuning(c);
+    const bool pays = (int64_t)n * c->k >= ((int64_t)1 << 22) || c->rounds_bound >= 8;
+    c->rounds_bound++;
+    if (c->prm.graphs && pays && !tuning && !tr && !log_enabled() && rebalance_graph(c, st, light)) {
+        UPR_CUDA(cudaGraphLaunch(c->reb_exec, s));
+        ri.graph = true;
+    } else for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
+        enqueue_subround(c, st, light, h == 1, s);
+        UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
+        UPR_CUDA(cudaStreamSynchronize(s));
+        if (c->prop_pending) {
+            settle_tuning(&c->prop_cfg, &c->prop_tuned, &c->prop_pending, c->prop_cands, c->ev_tune + 6, 0.02f);
+            if (c->prop_tuned) remember_tuning(c, 1, c->prop_cfg);
+        }
+        if (log_enabled()) {
+            int32_t hc[CNT_SLOTS];
+            UPR_CUDA(cudaMemcpy(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost));
+            const auto t1 = std::chrono::steady_clock::now();
+            fprintf(stderr, "upr round %d sub-round %d: listed %d proposals %d kept %d selected %d "
+                            "admitted %d (%.3f ms)\n",
+                    r, h, c->hctl->n1_active, hc[CNT_L1], c->prio_hist ? hc[CNT_P] : hc[CNT_L1], hc[CNT_S],
+                    hc[CNT_A],
+                    std::chrono::duration<double, std::milli>(t1 - t_sub).count());
+            t_sub = std::chrono::steady_clock::now();
+        }
+        if (c->hctl->stopped) break;
+    }
+}
+
 /*
  * One round on c->part0 / c->C0 / c->cut (device state).  Every step is
  * enqueued on c->s with its list lengths in device memory; the host waits
@@ -673,44 +727,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     UPR_CUDA(cudaEventRecord(c->ev[5], s));
 
     // ---- (d) rebalancing sub-rounds
-    if (c->prio_hist)
-        UPR_CUDA(cudaMemsetAsync(c->prio_hist, 0, sizeof(unsigned long long) * K * kPrioBins, s));
-    rebalance_init(G, c->C, c->excl_d, ctl, s);
-    rebalance_flag_in_blocks(c->part, n, c->excl_d, c->flags, s);
-    select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
-    int32_t *light = batch ? c->light_g : &ctl->light;
-    const RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
-    auto t_sub = std::chrono::steady_clock::now();
-    // the loop runs on the device as one graph once the proposal schedule is
-    // settled (the host-driven form times the schedules, logs and traces);
-    // a small binding first has to run a few rounds to pay for the capture
-    const bool tuning = !c->prop_tuned && worth_tuning(c);
-    const bool pays = (int64_t)n * c->k >= ((int64_t)1 << 22) || c->rounds_bound >= 8;
-    c->rounds_bound++;
-    if (c->prm.graphs && pays && !tuning && !tr && !log_enabled() && rebalance_graph(c, st, light)) {
-        UPR_CUDA(cudaGraphLaunch(c->reb_exec, s));
-        ri.graph = true;
-    } else for (int32_t h = 1; h <= c->prm.max_subrounds; h++) {
-        enqueue_subround(c, st, light, h == 1, s);
-        UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
-        UPR_CUDA(cudaStreamSynchronize(s));
-        if (c->prop_pending) {
-            settle_tuning(&c->prop_cfg, &c->prop_tuned, &c->prop_pending, c->prop_cands, c->ev_tune + 6, 0.02f);
-            if (c->prop_tuned) remember_tuning(c, 1, c->prop_cfg);
-        }
-        if (log_enabled()) {
-            int32_t hc[CNT_SLOTS];
-            UPR_CUDA(cudaMemcpy(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost));
-            const auto t1 = std::chrono::steady_clock::now();
-            fprintf(stderr, "upr round %d sub-round %d: listed %d proposals %d kept %d selected %d "
-                            "admitted %d (%.3f ms)\n",
-                    r, h, c->hctl->n1_active, hc[CNT_L1], c->prio_hist ? hc[CNT_P] : hc[CNT_L1], hc[CNT_S],
-                    hc[CNT_A],
-                    std::chrono::duration<double, std::milli>(t1 - t_sub).count());
-            t_sub = std::chrono::steady_clock::now();
-        }
-        if (c->hctl->stopped) break;
-    }
+    rebalance_phase(c, r, ri, tr);
     UPR_CUDA(cudaEventRecord(c->ev[6], s));
 
     // ---- (c1) interleave M and R_1..R_k (or append R after M: a variant of Sec. 7.2)
@@ -1033,6 +1050,137 @@ void add_round(upr_stats &st, const RoundInfo &ri, bool repair) {
  * keeps its input partition and cut, the others go on.  cut_in / cut_out /
  * status (nullable) have ng entries.
  */
+// One round of unconstrained label propagation (Sec. 5) on one graph, from
+// part0 (round start) with V_a = c->lp_active: every active node to its best
+// positive-gain block (the selection with no penalty and no limit), all moves
+// at once, then the rebalancing; the result is kept only if it is balanced and
+// cuts less than *cut (then part0, C0, the cut and the table follow it and
+// c->lp_active becomes the next V_a), else everything stays as it was.
+// Returns whether the round was kept; *active_next = |next V_a|.
+constexpr int kLpRedo = 2;     // internal: a hashed row ran out of slots, nothing was kept
+
+int lp_round_once(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri) {
+    cudaStream_t s = c->s;
+    const GraphDev &G = c->G;
+    const int64_t n = c->n;
+    const int32_t K = G.K();
+    int32_t *cnt = c->counts;
+    RebalCtl *ctl = c->ctl;
+    const Count cN{nullptr, n};
+    UPR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * CNT_SLOTS, s));
+    UPR_CUDA(cudaMemcpyAsync(c->part, c->part0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
+    if (!c->table_valid)
+        gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, nullptr, s);
+    c->table_valid = false;
+    // selection without a penalty: no block limit, so no move pays anything
+    for (int l = 0; l < kSlots; l++) c->hF[l] = kConstrainedF;
+    UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
+    k_fill_i64<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(c->Lsel, K, INT64_MAX);
+    UPR_LAUNCH_CHECK();
+    const Penalty pen{c->PW, c->F, c->C0, c->Lsel, c->first_slot};
+    select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, c->sel_cfg, s);
+    lp_filter(c->flags, c->lp_active, n, s);
+    select_flags(c->flags, c->idxA, cnt + CNT_M, cN, c->tmp, s);
+    lp_apply(G, c->idxA, cnt + CNT_M, c->cand_tgt, c->cand_gain, c->part0, c->part, c->C, c->M_node, c->M_from,
+             c->M_to, c->M_score, c->m_pos, c->scal + 1, n, s);
+    table_move(G, c->W, c->M_node, c->M_from, c->M_to, cnt + CNT_M, nullptr, c->scal + 1, n, c->hub_chunks,
+               c->n_chunks, HubMoves{c->m_pos, nullptr, nullptr, nullptr, nullptr, c->M_from, c->M_to}, s);
+    gain_table(G, c->part, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+               c->tile_nodes, c->scal + 1, s);
+    UPR_CUDA(cudaEventRecord(c->ev[5], s));
+    rebalance_phase(c, 0, ri, nullptr);
+    // balanced, and the cut after
+    count_over(G, c->C, cnt + CNT_OVER0, s);
+    edge_cut(G, c->part, c->tot, s);
+    int64_t cut1 = 0;
+    UPR_CUDA(cudaMemcpyAsync(c->hcnt, cnt, sizeof(int32_t) * CNT_SLOTS, cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaMemcpyAsync(c->hcut, c->tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
+    if (G.sp.on()) UPR_CUDA(cudaMemcpyAsync(c->hcnt + 41, c->sp_over, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    cut1 = *c->hcut;
+    ri.n_moves = c->hcnt[CNT_M];
+    ri.n_rebal = c->hctl->nR;
+    ri.subrounds = c->hctl->subrounds;
+    const int32_t *dM = cnt + CNT_M, *dR = &ctl->nR;
+    if (G.sp.on() && c->hcnt[41] != 0) {
+        // a hashed row ran out of slots: the proposals may have read a wrong
+        // row, so nothing of the round is kept; the caller runs it again
+        reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
+        reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
+        UPR_CUDA(cudaMemsetAsync(c->sp_over, 0, sizeof(int32_t), s));
+        UPR_CUDA(cudaStreamSynchronize(s));
+        return kLpRedo;
+    }
+    const bool kept = c->hcnt[CNT_OVER0] == 0 && cut1 < *cut;
+    if (kept) {
+        lp_next(G, c->part0, c->part, c->lp_next, cnt + CNT_L1, s);
+        std::swap(c->lp_active, c->lp_next);
+        UPR_CUDA(cudaMemcpyAsync(c->part0, c->part, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        UPR_CUDA(cudaMemcpyAsync(c->C0, c->C, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
+        UPR_CUDA(cudaMemcpyAsync(c->cut, c->tot, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        c->table_valid = true;              // W follows every move and rebalancing move
+        ri.best_gain = *cut - cut1;
+        *cut = cut1;
+    }
+    reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
+    reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
+    UPR_CUDA(cudaMemcpyAsync(c->hcnt + 40, c->tmp.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaMemcpyAsync(c->hcnt + CNT_L1, cnt + CNT_L1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    if (c->hcnt[40] != 0) { c->table_valid = false; throw CudaError{cudaErrorLaunchTimeout, "primitive wait"}; }
+    *active_next = kept ? c->hcnt[CNT_L1] : 0;
+    return kept ? 1 : 0;
+}
+
+// A label propagation round; when hashed rows run out of slots, the round
+// runs again on rows built afresh, and then on the dense table.
+bool lp_round(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri) {
+    for (int attempt = 0;; attempt++) {
+        ri = RoundInfo{};
+        const int rc = lp_round_once(c, cut, active_next, ri);
+        if (rc != kLpRedo) return rc == 1;
+        c->table_valid = false;
+        if (attempt >= 1) {
+            ensure_dense(c);
+            c->sparse_on = false;
+            c->G.sp.slot = nullptr;
+            c->gen++;
+        }
+    }
+}
+
+// Label propagation before the FM rounds (Sec. 5): V_a starts as the boundary
+// nodes; stops after max_rounds rounds, at a round that is not kept, at an
+// empty V_a, or after a kept round improving the cut by less than 0.001 of
+// it.  Returns the rounds kept.
+int32_t label_propagation(upr_ctx *c, int32_t max_rounds, int64_t *cut, upr_stats &st) {
+    cudaStream_t s = c->s;
+    if (!c->table_valid)
+        gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, nullptr, s);
+    c->table_valid = true;
+    lp_boundary(c->G, c->part0, c->W, c->lp_active, s);
+    lp_count(c->lp_active, c->n, c->counts + CNT_L1, s);
+    UPR_CUDA(cudaMemcpyAsync(c->hcnt + CNT_L1, c->counts + CNT_L1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    int64_t active = c->hcnt[CNT_L1];
+    int32_t kept = 0;
+    for (int32_t r = 1; r <= max_rounds && active > 0; r++) {
+        const int64_t before = *cut;
+        RoundInfo ri;
+        if (!lp_round(c, cut, &active, ri)) break;
+        kept++;
+        st.n_moves += ri.n_moves;
+        st.n_rebalance_moves += ri.n_rebal;
+        st.subrounds += ri.subrounds;
+        if (1000 * (before - *cut) < before) break;
+    }
+    return kept;
+}
+
 upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *stats, upr_status *status,
                        int64_t *cut_in, int64_t *cut_out) {
     const int32_t total = c->prm.total_rounds > 0 ? c->prm.total_rounds : c->prm.round_offset + rounds;
@@ -1042,6 +1190,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     // cut, over a whole schedule in one call
     const int sch = c->prm.schedule;
     if (sch != 0 && (ng != 1 || c->prm.round_offset != 0 || c->prm.total_rounds != 0)) return UPR_ERR_INVALID;
+    if (c->prm.lp_rounds > 0 && ng != 1) return UPR_ERR_INVALID;     // label propagation: one graph
     upr_stats st{};
     const auto t_host0 = std::chrono::steady_clock::now();
     const long long launches0 = g_upr_launches.load();
@@ -1049,7 +1198,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     // one graph with a balanced input: the first round's bucket pass, which
     // reads omega(v, V_P(v)) and omega(I(v)) of every node anyway, gives the
     // cut, instead of a pass over the edges
-    bool defer_cut = ng == 1 && rounds >= 1 && sch == 0;
+    bool defer_cut = ng == 1 && rounds >= 1 && sch == 0 && c->prm.lp_rounds == 0;
     upr_status rc = load_part(c, part, !defer_cut);
     if (rc != UPR_OK) return rc;
     std::vector<int64_t> cin(ng), cout(ng), C0h(K);
@@ -1078,6 +1227,12 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
         if (ng > 1) read_i32(c, c->infeas_g, ng, keep.data());
         st.repaired_input = 1;
         repair_gain = ri.best_gain;
+    }
+    // unconstrained label propagation before the FM rounds (Sec. 5)
+    if (c->prm.lp_rounds > 0) {
+        int64_t cut_lp = st.cut_in - repair_gain;
+        st.lp_rounds = label_propagation(c, c->prm.lp_rounds, &cut_lp, st);
+        repair_gain = st.cut_in - cut_lp;       // the rounds below start from this cut
     }
     // schedule 1 (Sec. 6.2): round 1 constrained, round 2 unconstrained with
     // tau = 1/2; rounds 3..R-1 unconstrained (tau_i of a schedule over those
@@ -1181,6 +1336,7 @@ void upr_params_default(upr_params *p) {
     p->schedule = 0;
     p->gain_priority = 0;
     p->append = 0;
+    p->lp_rounds = 0;
     p->stream = nullptr;
 }
 
@@ -1203,7 +1359,7 @@ static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
-           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5 &&
+           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5 && p.lp_rounds >= 0 && p.lp_rounds <= 64 &&
            (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
 }
 

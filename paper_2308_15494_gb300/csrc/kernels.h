@@ -401,4 +401,22 @@ void seq_apply_prefix_seg(const GraphDev &g, const int32_t *I_node, const int32_
                           const int32_t *d_nI, int64_t max, const int32_t *seg_beg, const long long *best_j,
                           int32_t *part0, int64_t *C0, cudaStream_t s);
 
+// ---- lp.cu: unconstrained label propagation (Sec. 5)
+// active[v] = 1 for the boundary nodes of part (table W of part)
+void lp_boundary(const GraphDev &g, const int32_t *part, const int32_t *W, int8_t *active, cudaStream_t s);
+// flags[v] = 0 where active[v] = 0
+void lp_filter(int32_t *flags, const int8_t *active, int64_t n, cudaStream_t s);
+// the listed movers (d_cnt of them, node order) to cand_tgt: part (a copy of
+// part0), C, the move list, m_pos markers and the movers' degree sum
+void lp_apply(const GraphDev &g, const int32_t *movers, const int32_t *d_cnt, const int32_t *cand_tgt,
+              const int32_t *cand_gain, const int32_t *part0, int32_t *part, int64_t *C, int32_t *M_node,
+              int32_t *M_from, int32_t *M_to, int64_t *M_score, int32_t *m_pos, int64_t *deg_sum, int64_t max_count,
+              cudaStream_t s);
+// next[u] = 1 for the unmoved neighbours u of the nodes whose block changed
+// from before to after; *d_count = their number
+void lp_next(const GraphDev &g, const int32_t *before, const int32_t *after, int8_t *next, int32_t *d_count,
+             cudaStream_t s);
+// *d_count = the number of non-zero entries of active
+void lp_count(const int8_t *active, int64_t n, int32_t *d_count, cudaStream_t s);
+
 }  // namespace upr

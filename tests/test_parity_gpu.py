@@ -434,6 +434,56 @@ def test_appended_sequence_same_results(upr, name):
     assert np.array_equal(p, p0) and st.cut_out == c0
 
 
+@pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "chung_lu_1k", "rmat_s12_k64",
+                                  "heavy_weights", "isolated", "star_hub"])
+def test_label_propagation_same_results(upr, name):
+    """Unconstrained label propagation (Sec. 5) before the FM rounds, alone
+    (no FM round) and followed by FM rounds, equals the oracle."""
+    w = CASES[name]()
+    prm = upr.upr_params_default()
+    prm.lp_rounds = 5
+    ctx = upr.create_from_workload(w, params=prm)
+    if np.all(brute.block_weights(w, w.part) <= brute.lmax(w)):
+        kept, q, c = oracle.label_propagation(w, w.part, 5)      # label propagation alone
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, 0)
+        assert st.lp_rounds == kept and np.array_equal(p, q) and st.cut_out == c
+    rc, p0, c0, _ = oracle.refine(w, w.part, rounds=3, p=oracle.params(lp_rounds=5))
+    p = w.part.copy()
+    if rc != oracle.OK:
+        with pytest.raises(upr.UprError):
+            upr.upr_refine(ctx, p, 3)
+        return
+    st = upr.upr_refine(ctx, p, 3)
+    assert np.array_equal(p, p0), name
+    assert st.cut_out == c0
+
+
+@pytest.mark.parametrize("table", [2, 3])
+def test_label_propagation_on_hashed_rows(upr, table):
+    for w in (CASES["rmat_s12_k64"](), synth.random_small(23, 4000, 9, 256, weighted=True, hubs=2)):
+        rc, p0, c0, _ = oracle.refine(w, w.part, rounds=2, p=oracle.params(lp_rounds=5))
+        prm = upr.upr_params_default()
+        prm.lp_rounds = 5
+        prm.table = table
+        ctx = upr.create_from_workload(w, params=prm)
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, 2)
+        assert np.array_equal(p, p0) and st.cut_out == c0
+
+
+def test_label_propagation_with_the_round_driver(upr):
+    w = CASES["chung_lu_1k"]()
+    rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 6, 1, p=oracle.params(lp_rounds=5))
+    prm = upr.upr_params_default()
+    prm.lp_rounds = 5
+    prm.schedule = 1
+    ctx = upr.create_from_workload(w, params=prm)
+    p = w.part.copy()
+    st = upr.upr_refine(ctx, p, 6)
+    assert np.array_equal(p, p0) and st.cut_out == c0
+
+
 def test_round_driver_on_a_tight_case(upr):
     w = synth.random_small(11, 4000, 8, 16, weighted=True, max_vw=20)
     w.eps = 0.005
