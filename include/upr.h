@@ -130,6 +130,9 @@ typedef struct {
                                     = the unmoved neighbours of moved nodes; stops at a
                                     round not kept, an empty active set or an improvement
                                     below 0.001 of the cut.  One graph only. 0 = off        */
+    int32_t lock_rebalanced;     /* 1: the oscillation guard of Sec. 2: a node whose applied
+                                    move in a round came from rebalancing alone is not a
+                                    candidate in the next round of the call. 0              */
     void   *stream;              /* cudaStream_t for all device work; NULL = default stream   */
 } upr_params;
 

@@ -67,7 +67,7 @@ class Params(ctypes.Structure):
     _fields_ = [("t_num", ctypes.c_int32), ("t_den", ctypes.c_int32),
                 ("tau1_num", ctypes.c_int32), ("tau1_den", ctypes.c_int32),
                 ("max_subrounds", ctypes.c_int32), ("gain_priority", ctypes.c_int32), ("append", ctypes.c_int32),
-                ("lp_rounds", ctypes.c_int32)]
+                ("lp_rounds", ctypes.c_int32), ("lock_rebalanced", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -104,6 +104,8 @@ def _load():
         lib.upro_refine_schedule.argtypes = [GP, I32, I64, PP, P, I32, I32, P, P, P]
         lib.upro_round_kind.argtypes = [GP, I32, I64, PP, I32, I64, I64, I64, P, P, TP]
         lib.upro_round_kind.restype = ctypes.c_int
+        lib.upro_round_guard.argtypes = [GP, I32, I64, PP, I32, I32, I64, P, P, P, P, TP]
+        lib.upro_round_guard.restype = ctypes.c_int
         lib.upro_lp_round.argtypes = [GP, I32, I64, PP, P, P, P, P, TP]
         lib.upro_lp_round.restype = ctypes.c_int
         lib.upro_label_propagation.argtypes = [GP, I32, I64, PP, P, I32, P]
@@ -133,8 +135,9 @@ class _G:
         self.s = Graph(w.n, _ptr(xa), _ptr(ad), _ptr(aw), _ptr(vw))
 
 
-def params(t=(7, 10), tau1=(1, 4), max_subrounds=64, gain_priority=0, append=0, lp_rounds=0) -> Params:
-    return Params(t[0], t[1], tau1[0], tau1[1], max_subrounds, gain_priority, append, lp_rounds)
+def params(t=(7, 10), tau1=(1, 4), max_subrounds=64, gain_priority=0, append=0, lp_rounds=0,
+           lock_rebalanced=0) -> Params:
+    return Params(t[0], t[1], tau1[0], tau1[1], max_subrounds, gain_priority, append, lp_rounds, lock_rebalanced)
 
 
 def lmax(total_weight: int, k: int, eps: float) -> int:
@@ -300,3 +303,28 @@ def label_propagation(w, part, max_rounds: int = 5, p: Optional[Params] = None):
     kept = _load().upro_label_propagation(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None,
                                           _ptr(part), max_rounds, ctypes.byref(c))
     return kept, part, int(c.value)
+
+
+def round_guard(w, part, r: int, R: int, locked, limit: int = 0, p: Optional[Params] = None):
+    """One round under the oscillation guard of Sec. 2 (locked nodes are no
+    candidates).  Returns (rc, new_part, cut, locked_out, trace dict with
+    cand_target, M, R, I, best_len)."""
+    n = w.n
+    g = _G(w)
+    part = np.array(part, dtype=np.int32, copy=True)
+    locked = np.ascontiguousarray(locked, np.int8)
+    out = np.zeros(n, np.int8)
+    c = ctypes.c_int64(cut(w, part)[0])
+    a = dict(cand_target=np.zeros(n, np.int32), cand_s0=np.zeros(n, np.int64), cand_gain=np.zeros(n, np.int64),
+             M_node=np.zeros(n, np.int32), M_to=np.zeros(n, np.int32), M_score=np.zeros(n, np.int64),
+             R_node=np.zeros(n, np.int32), R_from=np.zeros(n, np.int32), R_to=np.zeros(n, np.int32),
+             R_subround=np.zeros(n, np.int32), I_node=np.zeros(n, np.int32), I_from=np.zeros(n, np.int32),
+             I_to=np.zeros(n, np.int32), I_gain=np.zeros(n, np.int64))
+    t = Trace(**{key: _ptr(v) for key, v in a.items()})
+    rc = _load().upro_round_guard(ctypes.byref(g.s), w.k, eps_ppm(w.eps), ctypes.byref(p) if p else None, r, R, limit,
+                                  _ptr(locked), _ptr(out), _ptr(part), ctypes.byref(c), ctypes.byref(t))
+    nm, nr, ns = t.n_moves, t.n_rebal, t.n_seq
+    tr = {"cand_target": a["cand_target"], "M": (a["M_node"][:nm], a["M_to"][:nm]),
+          "R": (a["R_node"][:nr], a["R_from"][:nr], a["R_to"][:nr]),
+          "I": (a["I_node"][:ns], a["I_from"][:ns], a["I_to"][:ns]), "best_len": t.best_len}
+    return rc, part, int(c.value), out, tr

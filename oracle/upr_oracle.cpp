@@ -58,6 +58,9 @@ typedef struct {
                                    interleaved (the variant of Sec. 7.2); 0 */
     int32_t lp_rounds;          /* rounds of unconstrained label propagation before the
                                    FM rounds (Sec. 5; the paper uses 5); 0 */
+    int32_t lock_rebalanced;    /* 1: the oscillation guard of Sec. 2: a node whose applied
+                                   move in a round came from rebalancing alone is not a
+                                   candidate in the next round; 0 */
 } upro_params;
 
 /* Optional per-round trace; every pointer may be NULL.  Node-sized arrays
@@ -261,6 +264,11 @@ struct RoundKind {
      * the round moves every active node to its best positive-gain block,
      * rebalances, and keeps the result only if it is balanced and cuts less */
     const int8_t *lp_active = nullptr;
+    /* the oscillation guard (Sec. 2): locked[v] != 0 keeps v out of the
+     * selection of this round (rebalancing may still move it); locked_out
+     * receives the nodes whose applied move came from rebalancing alone */
+    const int8_t *locked = nullptr;
+    int8_t *locked_out = nullptr;
 };
 
 int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, int32_t r,
@@ -337,6 +345,7 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
         for (int64_t v = 0; v < n; v++) {
             int64_t own = T.at(v, part[v]);
             if (own >= T.wI[v]) continue;              /* not a boundary node (Sec. 2) */
+            if (kind.locked && kind.locked[v]) continue; /* locked by the oscillation guard */
             bool have = false;
             int64_t best = 0, bestg = 0; int32_t bt = -1;
             for (int32_t b = 0; b < k; b++) {
@@ -584,6 +593,11 @@ int round_impl(const Graph &g, int32_t k, int64_t Lmax, const upro_params &p, in
     out->n_seq = (int64_t)I.size();
     if (!have_best) return UPRO_ERR_INFEASIBLE;
     for (int64_t j = 0; j < best_len; j++) part[I[j].v] = I[j].to;
+    if (kind.locked_out) {
+        memset(kind.locked_out, 0, (size_t)n);
+        for (int64_t j = 0; j < best_len; j++)
+            if (I[j].rebal) kind.locked_out[I[j].v] = 1;
+    }
     *cut = cut0 - best_gain;
     out->best_len = best_len; out->best_gain = best_gain;
     if (tr) { tr->best_len = best_len; tr->best_gain = best_gain; tr->cut_after = *cut; }
@@ -638,10 +652,10 @@ bool params_ok(const upro_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_num >= 0 &&
            p.tau1_num <= p.tau1_den && p.tau1_den <= 65536 && p.max_subrounds >= 1 &&
            (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1) &&
-           p.lp_rounds >= 0 && p.lp_rounds <= 64;
+           p.lp_rounds >= 0 && p.lp_rounds <= 64 && (p.lock_rebalanced == 0 || p.lock_rebalanced == 1);
 }
 
-upro_params defaults() { return upro_params{7, 10, 1, 4, 64, 0, 0, 0}; }
+upro_params defaults() { return upro_params{7, 10, 1, 4, 64, 0, 0, 0, 0}; }
 
 } /* namespace */
 
@@ -767,6 +781,30 @@ int upro_label_propagation(const upro_graph *gg, int32_t k, int64_t eps_ppm, con
     return kept;
 }
 
+/* One round r of R (as upro_round) under the oscillation guard of Sec. 2:
+ * nodes with locked[v] != 0 are not candidates; locked_out[v] = 1 for the
+ * nodes whose applied move came from rebalancing alone (the next round's
+ * locks).  limit > 0: the fully unconstrained / limited variant instead of
+ * the penalty (as in upro_round_kind). */
+int upro_round_guard(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t r, int32_t R,
+                     int64_t limit, const int8_t *locked, int8_t *locked_out, int32_t *part, int64_t *cut,
+                     upro_trace *tr) {
+    upro_params p = pp ? *pp : defaults();
+    if (!params_ok(p) || k < 2 || R < 1 || R > 65536 || r < 1 || r > R || limit < 0) return UPRO_ERR_INVALID;
+    Graph g = wrap(gg);
+    int64_t tot = 0;
+    for (int64_t v = 0; v < g.n; v++) tot += g.c(v);
+    RoundOut o;
+    RoundKind kind;
+    kind.limit = limit;
+    kind.locked = locked;
+    kind.locked_out = locked_out;
+    std::vector<int32_t> backup(part, part + g.n);
+    int rc = round_impl(g, k, lmax_of(tot, k, eps_ppm), p, r, R, false, part, cut, tr, &o, kind);
+    if (rc != UPRO_OK) memcpy(part, backup.data(), sizeof(int32_t) * g.n);
+    return rc;
+}
+
 /* One round of a given kind (Sec. 6.2): constrained != 0, or unconstrained
  * with tau = tau_num / tau_den.  Otherwise as upro_round with r = R = 1. */
 int upro_round_kind(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t constrained,
@@ -818,10 +856,14 @@ int upro_refine(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_par
     }
     if (p.lp_rounds > 0) label_propagation(g, k, Lmax, p, p.lp_rounds, P.data(), &cut);
     if (round_cuts) round_cuts[0] = cut;
+    std::vector<int8_t> locked(p.lock_rebalanced ? g.n : 0, 0), locked_next(locked);
     for (int32_t i = 1; i <= rounds; i++) {
-        int rc = round_impl(g, k, Lmax, p, round_offset + i, total_rounds, false, P.data(), &cut, nullptr, &o);
+        RoundKind kind;
+        if (p.lock_rebalanced) { kind.locked = locked.data(); kind.locked_out = locked_next.data(); }
+        int rc = round_impl(g, k, Lmax, p, round_offset + i, total_rounds, false, P.data(), &cut, nullptr, &o, kind);
         if (rc != UPRO_OK) return rc;
         if (round_cuts) round_cuts[i] = cut;
+        locked.swap(locked_next);
     }
     memcpy(part, P.data(), sizeof(int32_t) * g.n);
     if (cut_out) *cut_out = cut;
@@ -873,6 +915,7 @@ int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const
     bool unconstrained_rest = false, switched = false;
     int64_t imp1 = 0;
     const int32_t U = rounds - 3;            /* unconstrained rounds 3..R-1 of schedule 1 */
+    std::vector<int8_t> locked(p.lock_rebalanced ? g.n : 0, 0), locked_next(locked);
     for (int32_t i = 1; i <= rounds; i++) {
         RoundKind kind;
         int8_t code = 0;
@@ -897,7 +940,9 @@ int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const
             }
         }
         const int64_t before = cut;
+        if (p.lock_rebalanced) { kind.locked = locked.data(); kind.locked_out = locked_next.data(); }
         int rc = round_impl(g, k, Lmax, p, r, R, false, P.data(), &cut, nullptr, &o, kind);
+        locked.swap(locked_next);
         if (rc != UPRO_OK) return rc;
         if (round_cuts) round_cuts[i] = cut;
         if (kinds) kinds[i - 1] = code;

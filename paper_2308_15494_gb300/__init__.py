@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
     _fields_ = [("t_num", I32), ("t_den", I32), ("tau1_num", I32), ("tau1_den", I32), ("max_subrounds", I32),
                 ("validate", I32), ("round_offset", I32), ("total_rounds", I32), ("autotune", I32), ("table", I32),
                 ("graphs", I32), ("schedule", I32), ("gain_priority", I32), ("append", I32),
-                ("lp_rounds", I32), ("stream", P)]
+                ("lp_rounds", I32), ("lock_rebalanced", I32), ("stream", P)]
 
 
 class Stats(ctypes.Structure):

@@ -183,6 +183,7 @@ struct upr_ctx {
     int64_t *Lb; int32_t *gid;          // [K] L_max per block; [n] graph of each node (batches)
     int64_t *Lsel;                      // [K] the selection's block limit in a limited round (Sec. 7.2)
     int8_t *lp_active, *lp_next;        // [n] label propagation: V_a and the next V_a (Sec. 5)
+    int8_t *locked;                     // [n] the oscillation guard's locks for the next round (Sec. 2)
     int32_t *seg_beg, *seg_end, *over0_g, *light_g, *infeas_g, *inf0_g; long long *best_g, *best_j; int64_t *tot;
     int32_t *part_in;                   // batches: the input partition (global ids)
     int64_t *noff_d;                    // batches: [ng + 1] first node of each graph
@@ -236,6 +237,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->Lb = A.take<int64_t>(k);
     c->Lsel = A.take<int64_t>(k);
     c->lp_active = A.take<int8_t>(n);
+    c->locked = A.take<int8_t>(n);
     c->lp_next = A.take<int8_t>(n);
     c->gid = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
     c->part_in = c->ng > 1 ? A.take<int32_t>(n) : nullptr;
@@ -700,6 +702,8 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
         run_tuned(c, c->sel_tuned, c->sel_cfg, c->sel_cands, &c->sel_pending, c->ev_tune, [&](LaneCfg cfg) {
             select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, cfg, s);
         });
+        if (c->prm.lock_rebalanced)        // the oscillation guard (Sec. 2)
+            guard_filter(c->locked, n, c->flags, c->cand_tgt, c->cand_s0, c->cand_gain, s);
         select_flags(c->flags, c->idxA, cnt + CNT_CAND, cN, c->tmp, s);
         const Count cC{cnt + CNT_CAND, n};
         // ---- (b3) inflow penalties: order by (target, s0 desc, id)
@@ -827,6 +831,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     // the table goes from W(P o I) to W(P o I^{j*}) for the next round
     {
         const Rollback rb{Iv, If, It, dI, c->best, batch ? G.gid : nullptr, c->seg_beg, c->best_j};
+        if (c->prm.lock_rebalanced && !rebalance_only) guard_locks(rb, n, n, c->m_pos, c->r_to, c->locked, s);
         table_rollback(G, rb, n, c->pos, c->W, c->hub_chunks, c->n_chunks, c->scal + 2, s);
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, c->scal + 2, s);
@@ -1228,6 +1233,7 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
         st.repaired_input = 1;
         repair_gain = ri.best_gain;
     }
+    if (c->prm.lock_rebalanced && c->n > 0) UPR_CUDA(cudaMemsetAsync(c->locked, 0, (size_t)c->n, c->s));
     // unconstrained label propagation before the FM rounds (Sec. 5)
     if (c->prm.lp_rounds > 0) {
         int64_t cut_lp = st.cut_in - repair_gain;
@@ -1337,6 +1343,7 @@ void upr_params_default(upr_params *p) {
     p->gain_priority = 0;
     p->append = 0;
     p->lp_rounds = 0;
+    p->lock_rebalanced = 0;
     p->stream = nullptr;
 }
 
@@ -1360,6 +1367,7 @@ static bool params_ok(const upr_params &p) {
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
            p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5 && p.lp_rounds >= 0 && p.lp_rounds <= 64 &&
+           (p.lock_rebalanced == 0 || p.lock_rebalanced == 1) &&
            (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
 }
 

@@ -379,6 +379,13 @@ struct Rollback {
     const int32_t *gid, *seg_beg;
     const long long *best_j;
 };
+// The oscillation guard of Sec. 2: locked[v] = 1 exactly for the nodes of the
+// applied prefix of I whose move came from rebalancing alone (m_pos < 0,
+// r_to >= 0); and no candidate among the locked nodes.
+void guard_locks(const struct Rollback &rb, int64_t max, int64_t n, const int32_t *m_pos, const int32_t *r_to,
+                 int8_t *locked, cudaStream_t s);
+void guard_filter(const int8_t *locked, int64_t n, int32_t *flags, int32_t *cand_tgt, int64_t *cand_s0,
+                  int32_t *cand_gain, cudaStream_t s);
 // W(P o I) -> W(P o I^{j*}): delta updates of the undone moves (pos = positions
 // in I), or nothing when 4 * (their degree sum, left in *deg_sum) >= m, in which
 // case the caller rebuilds with gain_table(..., deg_sum).

@@ -719,6 +719,31 @@ __global__ void k_seq_append(const int32_t *__restrict__ M_node, const int32_t *
     }
 }
 
+// The oscillation guard of Sec. 2: lock the nodes of the applied prefix whose
+// move comes from rebalancing alone (an R move and no M move).
+__global__ void k_guard_locks(Rollback rb, const int32_t *__restrict__ m_pos, const int32_t *__restrict__ r_to,
+                              int8_t *__restrict__ locked) {
+    const int64_t nI = *rb.d_nI;
+    UPR_FOR(i, nI) {
+        if (rolled_back(rb, i)) continue;
+        const int32_t v = rb.I_node[i];
+        if (m_pos[v] < 0 && r_to[v] >= 0) locked[v] = 1;
+    }
+}
+
+// no candidate among the locked nodes
+__global__ void k_guard_filter(const int8_t *__restrict__ locked, int64_t n, int32_t *__restrict__ flags,
+                               int32_t *__restrict__ cand_tgt, int64_t *__restrict__ cand_s0,
+                               int32_t *__restrict__ cand_gain) {
+    UPR_FOR(v, n) {
+        if (!locked[v]) continue;
+        flags[v] = 0;
+        cand_tgt[v] = -1;
+        cand_s0[v] = 0;
+        cand_gain[v] = 0;
+    }
+}
+
 __global__ void k_reset_nodes(const int32_t *__restrict__ nodes, const int32_t *__restrict__ d_cnt,
                               int32_t *__restrict__ arr, int32_t val) {
     const int64_t cnt = *d_cnt;
@@ -919,6 +944,21 @@ void seq_append(const int32_t *M_node, const int32_t *M_from, const int32_t *M_t
     if (max <= 0) return;
     k_seq_append<<<grid_for(max), 256, 0, s>>>(M_node, M_from, M_to, d_nM, R_node, R_from, R_to, d_nR, X_node, X_from,
                                               X_to, X_isr);
+    UPR_LAUNCH_CHECK();
+}
+
+void guard_locks(const Rollback &rb, int64_t max, int64_t n, const int32_t *m_pos, const int32_t *r_to,
+                 int8_t *locked, cudaStream_t s) {
+    if (n > 0) UPR_CUDA(cudaMemsetAsync(locked, 0, (size_t)n, s));
+    if (max <= 0) return;
+    k_guard_locks<<<grid_for(max), 256, 0, s>>>(rb, m_pos, r_to, locked);
+    UPR_LAUNCH_CHECK();
+}
+
+void guard_filter(const int8_t *locked, int64_t n, int32_t *flags, int32_t *cand_tgt, int64_t *cand_s0,
+                  int32_t *cand_gain, cudaStream_t s) {
+    if (n <= 0) return;
+    k_guard_filter<<<grid_for(n), 256, 0, s>>>(locked, n, flags, cand_tgt, cand_s0, cand_gain);
     UPR_LAUNCH_CHECK();
 }
 

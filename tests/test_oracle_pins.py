@@ -801,3 +801,59 @@ def test_lp_rounds_compose_with_the_active_set_rule():
                 break
         kept, Q, c = oracle.label_propagation(w, w.part, 5)
         assert kept == rounds and np.array_equal(Q, P) and c == cuts[-1]
+
+
+# ---------------------------------------------------------------- Sec. 2: the oscillation guard
+def test_locked_nodes_are_no_candidates():
+    """A locked node is no candidate; every other node's best move is the one
+    it has without locks (step b2 looks at each node alone)."""
+    for i in (0, 3, 5):
+        w = small(i)
+        rng = np.random.default_rng(i)
+        locked = (rng.random(w.n) < 0.3).astype(np.int8)
+        _, _, _, _, free = oracle.round_guard(w, w.part, 1, 3, np.zeros(w.n, np.int8))
+        _, _, _, _, lk = oracle.round_guard(w, w.part, 1, 3, locked)
+        expect = np.where(locked != 0, -1, free["cand_target"])
+        assert np.array_equal(lk["cand_target"], expect)
+        assert not np.any(locked[lk["M"][0]])
+
+
+def test_guard_locks_the_applied_pure_rebalancing_moves():
+    """The next round's locks: the nodes of the applied prefix whose move
+    comes from rebalancing alone (in R, not in M)."""
+    seen = 0
+    for seed in (41, 44, 45, 47):
+        w = synth.random_small(seed, 600, 8, 4, weighted=seed % 2 == 0)
+        w.eps = 0.01
+        rc, part, cut, out, tr = oracle.round_guard(w, w.part, 1, 1, np.zeros(w.n, np.int8), limit=2 ** 62)
+        assert rc == oracle.OK
+        Mset, Rset = set(tr["M"][0].tolist()), set(tr["R"][0].tolist())
+        In = tr["I"][0]
+        expect = np.zeros(w.n, np.int8)
+        for j in range(tr["best_len"]):
+            v = int(In[j])
+            if v in Rset and v not in Mset:
+                expect[v] = 1
+        assert np.array_equal(out, expect)
+        seen += int(expect.sum())
+    assert seen > 0
+
+
+def test_guard_changes_fully_unconstrained_refinement():
+    """With the fully unconstrained variant the locks change the outcome on
+    some inputs, and refine_schedule's rounds equal the rounds replayed with
+    the locks passed from round to round."""
+    differ = 0
+    for seed in (41, 44):
+        w = synth.random_small(seed, 600, 8, 4, weighted=seed % 2 == 0)
+        w.eps = 0.01
+        a = oracle.refine_schedule(w, w.part, 5, 4)
+        b = oracle.refine_schedule(w, w.part, 5, 4, p=oracle.params(lock_rebalanced=1))
+        differ += not np.array_equal(a[1], b[1])
+        # replay rounds 1..4 (fully unconstrained, no switch here) then the constrained last round
+        assert list(b[4]) == [oracle.NO_PENALTY] * 4 + [oracle.CONSTRAINED]
+        P, locked = np.array(w.part, np.int32), np.zeros(w.n, np.int8)
+        for r in range(4):
+            rc, P, c, locked, _ = oracle.round_guard(w, P, 1, 1, locked, limit=2 ** 62)
+            assert c == b[3][r + 1]
+    assert differ > 0

@@ -484,6 +484,27 @@ def test_label_propagation_with_the_round_driver(upr):
     assert np.array_equal(p, p0) and st.cut_out == c0
 
 
+@pytest.mark.parametrize("seed", [41, 44, 45, 47])
+def test_oscillation_guard_same_results(upr, seed):
+    """The oscillation guard of Sec. 2 (a node whose applied move came from
+    rebalancing alone is no candidate in the next round), with the plain
+    rounds and with the fully unconstrained variant (where it changes the
+    outcome), equals the oracle."""
+    w = synth.random_small(seed, 600, 8, 4, weighted=seed % 2 == 0)
+    w.eps = 0.01
+    for schedule in (0, 4):
+        rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 5, schedule,
+                                                         p=oracle.params(lock_rebalanced=1))
+        prm = upr.upr_params_default()
+        prm.schedule = schedule
+        prm.lock_rebalanced = 1
+        ctx = upr.create_from_workload(w, params=prm)
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, 5)
+        assert np.array_equal(p, p0), (seed, schedule)
+        assert st.cut_out == c0
+
+
 def test_round_driver_on_a_tight_case(upr):
     w = synth.random_small(11, 4000, 8, 16, weighted=True, max_vw=20)
     w.eps = 0.005
