@@ -483,18 +483,15 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     // node without a proposal has no block with room for it (the lightest
     // allowed block has the most room, and rooms only shrink), so it never
     // proposes again
-    select_flags(c->flags, c->idxD, cnt + CNT_L1, Count{&ctl->n1_active, n}, c->tmp, s);
-    rebalance_gather_list(c->L1, c->idxD, cnt + CNT_L1, c->idxA, n, s);
-    rebalance_copy_list(c->idxA, cnt + CNT_L1, c->L1, n, s);
+    select_values(c->flags, c->L1, c->L1, cnt + CNT_L1, Count{&ctl->n1_active, n}, c->tmp, s);
     // proposals that cannot be in their source's minimal prefix are dropped
     // before the ordering; P lists the others in node order
-    const int32_t *Pn = c->idxA;
+    const int32_t *Pn = c->L1;
     int32_t *dP = cnt + CNT_L1;
     if (c->prio_hist) {
-        rebalance_prefilter(G, c->idxA, cnt + CNT_L1, n, nullptr, c->prop_gain, c->part, c->over_d, c->C, c->gbits,
+        rebalance_prefilter(G, c->L1, cnt + CNT_L1, n, nullptr, c->prop_gain, c->part, c->over_d, c->C, c->gbits,
                             c->cbits, c->prm.gain_priority, c->prio_hist, c->prio_cut, c->flags2, s);
-        select_flags(c->flags2, c->idxD, cnt + CNT_P, Count{cnt + CNT_L1, n}, c->tmp, s);
-        rebalance_gather_list(c->idxA, c->idxD, cnt + CNT_P, c->Pq, n, s);
+        select_values(c->flags2, c->L1, c->Pq, cnt + CNT_P, Count{cnt + CNT_L1, n}, c->tmp, s);
         Pn = c->Pq;
         dP = cnt + CNT_P;
     }

@@ -384,76 +384,6 @@ __global__ void __launch_bounds__(512) k_table_hub_chunks(const HubChunk *__rest
         if (s_row[b]) atomicAdd(&dst[b], s_row[b]);
 }
 
-// Delta update: warp per moved node; hubs (degree > kHubDegree) are left to
-// k_table_move_hubs, which splits them into the static chunks.
-__global__ void k_table_move(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                             const int32_t *__restrict__ adjw, int32_t k, int32_t kmask, int32_t *__restrict__ W,
-                             const int32_t *__restrict__ nodes, const int32_t *__restrict__ from,
-                             const int32_t *__restrict__ to, const int32_t *__restrict__ d_count,
-                             const int32_t *__restrict__ d_offset, const int64_t *__restrict__ deg_sum, int64_t m,
-                             SparseRows sp) {
-    if (deg_sum && *deg_sum * 4 >= m) return;     // a rebuild handles this case
-    const int lane = threadIdx.x & 31;
-    const int64_t cnt = *d_count;
-    const int64_t off = d_offset ? *d_offset : 0;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt;
-         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int32_t v = nodes[off + j];
-        const int32_t a = blk_local(from[off + j], k, kmask), b = blk_local(to[off + j], k, kmask);
-        const int64_t e0 = xadj[v], e1 = xadj[v + 1];
-        if (e1 - e0 > kHubDegree) continue;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int32_t w = adjw ? adjw[e] : 1;
-            if (sp.on()) {
-                sp_sub(sp, adj[e], a, w);
-                sp_add(sp, adj[e], b, w);
-                continue;
-            }
-            int32_t *row = W + (int64_t)adj[e] * k;
-            atomicSub(&row[a], w);
-            atomicAdd(&row[b], w);
-        }
-    }
-}
-
-// Moved hubs, one CTA per static chunk.  A hub moved in M has m_pos >= 0 (from
-// its round-start block to its M target); a hub moved in the current
-// rebalancing sub-round has an R index in [*r_base, *r_base + *r_count).
-__global__ void __launch_bounds__(512) k_table_move_hubs(const HubChunk *__restrict__ chunks,
-                                                         const int32_t *__restrict__ adj,
-                                                         const int32_t *__restrict__ adjw, int32_t k,
-                                                         int32_t kmask, int32_t *__restrict__ W, HubMoves hm,
-                                                         const int64_t *__restrict__ deg_sum, int64_t m,
-                                                         SparseRows sp) {
-    if (deg_sum && *deg_sum * 4 >= m) return;
-    const HubChunk ch = chunks[blockIdx.x];
-    const int32_t v = ch.v;
-    int32_t a, b;
-    if (hm.m_pos) {
-        const int32_t p = hm.m_pos[v];
-        if (p < 0) return;
-        a = blk_local(hm.from[p], k, kmask);
-        b = blk_local(hm.to[p], k, kmask);
-    } else {
-        if (hm.r_to[v] < 0) return;
-        const int32_t ri = hm.r_at[v], base = *hm.r_base;
-        if (ri < base || ri >= base + *hm.r_count) return;
-        a = blk_local(hm.from[ri], k, kmask);
-        b = blk_local(hm.to[ri], k, kmask);
-    }
-    for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
-        const int32_t w = adjw ? adjw[e] : 1;
-        if (sp.on()) {
-            sp_sub(sp, adj[e], a, w);
-            sp_add(sp, adj[e], b, w);
-            continue;
-        }
-        int32_t *row = W + (int64_t)adj[e] * k;
-        atomicSub(&row[a], w);
-        atomicAdd(&row[b], w);
-    }
-}
-
 __global__ void k_node_graph(const int64_t *__restrict__ noff, int32_t ng, int64_t n, int32_t *__restrict__ gid) {
     UPR_FOR(v, n) {
         int32_t lo = 0, hi = ng - 1;            // last g with noff[g] <= v
@@ -621,21 +551,6 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
     if (n_chunks > 0) {
         k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k,
                                                                              g.kmask, W, deg_sum, g.m, g.sp);
-        UPR_LAUNCH_CHECK();
-    }
-}
-
-void table_move(const GraphDev &g, int32_t *W, const int32_t *nodes, const int32_t *from, const int32_t *to,
-                const int32_t *d_count, const int32_t *d_offset, const int64_t *deg_sum, int64_t max_count,
-                const HubChunk *hub_chunks, int64_t n_chunks, HubMoves hm, cudaStream_t s) {
-    if (max_count <= 0) return;
-    int64_t blocks = std::min<int64_t>(ceil_div(max_count * 32, 256), (int64_t)sm_count() * 16);
-    k_table_move<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.adjw, g.k, g.kmask, W, nodes, from, to, d_count,
-                                                  d_offset, deg_sum, g.m, g.sp);
-    UPR_LAUNCH_CHECK();
-    if (n_chunks > 0) {
-        k_table_move_hubs<<<(unsigned)n_chunks, 512, 0, s>>>(hub_chunks, g.adj, g.adjw, g.k, g.kmask, W, hm, deg_sum,
-                                                             g.m, g.sp);
         UPR_LAUNCH_CHECK();
     }
 }

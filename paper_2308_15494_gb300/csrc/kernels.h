@@ -160,6 +160,9 @@ bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
                       Scratch tmp, cudaStream_t s);
 // out_idx[0..*d_count) = indices i < n with flags[i] != 0, ascending.
 void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, Scratch tmp, cudaStream_t s);
+// out[j] = vals[i] for the j-th i with flags[i] != 0 (index order); out may be vals.
+void select_values(const int32_t *flags, const int32_t *vals, int32_t *out, int32_t *d_count, Count n, Scratch tmp,
+                   cudaStream_t s);
 
 // ---- graph.cu: step (e), step (a), create-time work
 struct HubChunk { int32_t v; int32_t pad; int64_t begin, end; };
@@ -262,10 +265,6 @@ struct RebalState {
 };
 // flags[v] = 1 for the nodes of the marked blocks
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s);
-// dst[i] = src[i] for i < *d_cnt
-void rebalance_copy_list(const int32_t *src, const int32_t *d_cnt, int32_t *dst, int64_t cnt_max, cudaStream_t s);
-void rebalance_gather_list(const int32_t *list, const int32_t *pos, const int32_t *d_cnt, int32_t *out, int64_t cnt_max,
-                           cudaStream_t s);
 // Proposals of the listed nodes in overloaded blocks: prop_tgt/prop_gain by node, flags by list position.
 void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
                                    const int32_t *part, const int32_t *W, RebalState st, int32_t *prop_tgt,

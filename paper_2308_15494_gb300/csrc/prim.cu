@@ -391,6 +391,63 @@ __global__ void __launch_bounds__(kThreads) k_compact(const int32_t *__restrict_
     finish_tiles(st, parts, epoch);
 }
 
+// Compaction of values: out[j] = vals[i] for the j-th set flag i, in index
+// order.  out may be vals itself: a tile loads its flags and values before it
+// publishes its count, writes only after its offset is known (so after every
+// earlier tile has published, hence loaded), and its output range
+// [offset, offset + count) ends within its own input range.
+__device__ __forceinline__ void compact_values_tile(const int32_t *flags, const int32_t *vals, int64_t n,
+                                                    int64_t tiles, int32_t *out, int32_t *d_count, int vec,
+                                                    const ScanState<int32_t> &st, uint32_t epoch, int64_t tile,
+                                                    bool alone, int32_t *s_warp, int32_t *s_excl) {
+    int32_t x[kItems], y[kItems];
+    load_items(flags, tile * kTile, n, (vec & 1) != 0, x);
+    load_items(vals, tile * kTile, n, (vec & 2) != 0, y);
+    int32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; j++) c += x[j] != 0;
+    int32_t total;
+    const int32_t pre = block_exclusive<OpSum>(c, s_warp, &total);
+    if (threadIdx.x < 32) {
+        const int32_t e = alone ? 0 : lookback<OpSum>(st, tile, total, epoch);
+        if (threadIdx.x == 0) {
+            *s_excl = e;
+            if (tile == tiles - 1) *d_count = e + total;
+        }
+    }
+    __syncthreads();
+    int32_t pos = *s_excl + pre;
+#pragma unroll
+    for (int j = 0; j < kItems; j++)
+        if (x[j]) out[pos++] = y[j];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_compact_values(const int32_t *__restrict__ flags, const int32_t *vals,
+                                                             const int32_t *__restrict__ d_n, int64_t n_max,
+                                                             int32_t *out, int32_t *__restrict__ d_count, int vec,
+                                                             ScanState<int32_t> st) {
+    __shared__ int32_t s_warp[kWarps];
+    __shared__ int32_t s_excl;
+    __shared__ uint32_t s_tile;
+    const int64_t n = count_of(d_n, n_max);
+    const int64_t tiles = tiles_of(n);
+    if (tiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_count = 0;
+    const unsigned parts = participants(tiles);
+    if (blockIdx.x >= parts) return;
+    if (tiles == 1) {
+        compact_values_tile(flags, vals, n, tiles, out, d_count, vec, st, 0u, 0, true, s_warp, &s_excl);
+        return;
+    }
+    const uint32_t epoch = call_epoch(st);
+    for (;;) {
+        const int64_t tile = next_tile(st.ctr, &s_tile);
+        if (tile >= tiles) break;
+        compact_values_tile(flags, vals, n, tiles, out, d_count, vec, st, epoch, tile, false, s_warp, &s_excl);
+    }
+    finish_tiles(st, parts, epoch);
+}
+
 // ------------------------------------------------------------------ radix sort
 constexpr int kBins = 256;
 
@@ -615,6 +672,16 @@ void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Coun
     const int64_t tiles_max = ceil_div(n.max, kTile);
     k_compact<<<tile_grid((const void *)k_compact, tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, out_idx, d_count, vec,
                                                         scan_state<int32_t>(tmp, tiles_max));
+    UPR_LAUNCH_CHECK();
+}
+
+void select_values(const int32_t *flags, const int32_t *vals, int32_t *out, int32_t *d_count, Count n, Scratch tmp,
+                   cudaStream_t s) {
+    if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
+    const int vec = (aligned16(flags) ? 1 : 0) | (aligned16(vals) ? 2 : 0);
+    const int64_t tiles_max = ceil_div(n.max, kTile);
+    k_compact_values<<<tile_grid((const void *)k_compact_values, tiles_max), kThreads, 0, s>>>(
+        flags, vals, n.d, n.max, out, d_count, vec, scan_state<int32_t>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
 }
 

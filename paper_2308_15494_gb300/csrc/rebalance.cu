@@ -223,12 +223,6 @@ __global__ void k_flag_in_blocks(const int32_t *__restrict__ part, int64_t n, co
     if (v < n) flags[v] = mark[part[v]] ? 1 : 0;
 }
 
-__global__ void k_gather_list(const int32_t *__restrict__ list, const int32_t *__restrict__ pos,
-                              const int32_t *__restrict__ d_cnt, int32_t *__restrict__ out) {
-    const int64_t cnt = *d_cnt;
-    UPR_FOR(i, cnt) out[i] = list[pos[i]];
-}
-
 // ---- loop control.  One graph: one CTA each (K = k <= 4096).  A batch: a
 // grid over the graphs, warp per graph; the last CTA to finish (ticket)
 // updates the control block.
@@ -686,25 +680,6 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
     k_flag_in_blocks<<<grid1(n), 256, 0, s>>>(part, n, mark, flags);
-    UPR_LAUNCH_CHECK();
-}
-
-__global__ void k_copy_list(const int32_t *__restrict__ src, const int32_t *__restrict__ d_cnt,
-                            int32_t *__restrict__ dst) {
-    const int64_t cnt = *d_cnt;
-    UPR_FOR(i, cnt) dst[i] = src[i];
-}
-
-void rebalance_copy_list(const int32_t *src, const int32_t *d_cnt, int32_t *dst, int64_t cnt_max, cudaStream_t s) {
-    if (cnt_max <= 0) return;
-    k_copy_list<<<grid_for(cnt_max), 256, 0, s>>>(src, d_cnt, dst);
-    UPR_LAUNCH_CHECK();
-}
-
-void rebalance_gather_list(const int32_t *list, const int32_t *pos, const int32_t *d_cnt, int32_t *out, int64_t cnt_max,
-                           cudaStream_t s) {
-    if (cnt_max <= 0) return;
-    k_gather_list<<<grid_for(cnt_max), 256, 0, s>>>(list, pos, d_cnt, out);
     UPR_LAUNCH_CHECK();
 }
 
