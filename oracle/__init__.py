@@ -16,11 +16,15 @@ What pins each step (tests/test_oracle_pins.py):
                                        constructive rebalancing costs <= (1/t) sum pen
   step 3  selection .................. brute-force argmax with gains from cut
                                        differences (parity of the definition only)
-  step 4  inflow / order of M ........ sortedness and inflow sums (parity unpinned
-                                       beyond these properties)
-  step 6  rebalancing ................ post-conditions: balanced when feasible, every
-                                       admitted move fits, minimal per-source prefixes
-                                       (sequence parity unpinned beyond these)
+  step 4  inflow / order of M ........ M re-derived per target from the candidates with
+                                       brute-force penalties of the cumulative inflow;
+                                       order (score desc, id asc)
+  step 6  rebalancing ................ the whole sequence (node, from, to, sub-round)
+                                       equals the sub-rounds of Sec. 6.1 evaluated from
+                                       the definitions (gains as cut differences,
+                                       priorities in exact rationals, prefixes by
+                                       search); post-conditions: balanced when
+                                       feasible, every admitted move fits
   step 7  interleave ................. independent re-derivation of the sequential rule
   step 9  exact gains ................ G(j) == cut(P) - cut(P o I^j) by brute force
   step 10 best prefix ................ brute-force max over balanced prefixes; cut never

@@ -6,6 +6,7 @@ interleaving, Alg. 1 best prefix) by brute force, exact rationals or an
 invariant -- never by re-calling the oracle's own routine."""
 from __future__ import annotations
 
+import dataclasses
 import itertools
 from fractions import Fraction
 
@@ -248,6 +249,63 @@ def test_rebalance_postconditions(w):
             assert Cn[a] + c[last] > L
     if tr["n_rebal"] or over1:
         assert np.all(brute.block_weights(w, P) <= L) or tr["subrounds"] > 0
+
+
+# Imbalanced inputs (half the nodes in block 0) for the repair round, whose
+# rebalancing starts from the input: several sub-rounds, rejected targets,
+# unconnected nodes sent to the lightest block, weighted and unit nodes.
+REBAL = [
+    dict(seed=51, n=40, avg_deg=3, k=4, balanced=False),
+    dict(seed=52, n=60, avg_deg=4, k=5, balanced=False, weighted=False),
+    dict(seed=53, n=80, avg_deg=2, k=6, balanced=False, isolated=8),
+    dict(seed=54, n=50, avg_deg=5, k=3, balanced=False, hubs=1, max_vw=20),
+    dict(seed=55, n=30, avg_deg=3, k=8, balanced=False, max_vw=3),
+]
+
+
+def _oracle_R(tr):
+    Rn, Rf, Rt, Rs = tr["R"]
+    return [(int(a), int(b), int(c), int(d)) for a, b, c, d in zip(Rn, Rf, Rt, Rs)]
+
+
+@pytest.mark.parametrize("gain_only", [0, 1])
+@pytest.mark.parametrize("i", range(len(REBAL)))
+def test_rebalancing_sequence_bruteforce(i, gain_only):
+    """The whole rebalancing sequence (node, from, to, sub-round) equals the
+    sub-rounds of Sec. 6.1 evaluated from the definitions (gains as cut
+    differences, priorities in exact rationals, prefixes by search)."""
+    w = synth.random_small(**REBAL[i])
+    L = brute.lmax(w)
+    assert np.any(brute.block_weights(w, w.part) > L)
+    _, _, _, tr = oracle.run_round(w, w.part, 0, 1, rebalance_only=True, p=oracle.params(gain_priority=gain_only))
+    expect = brute.rebalance_subrounds(w, w.part, L, gain_only=bool(gain_only))
+    assert len(expect) > 0 and _oracle_R(tr) == expect
+
+
+@pytest.mark.parametrize("seed,weighted", [(60, False), (61, False), (60, True), (62, True)])
+def test_rebalancing_sequence_with_room_to_spare(seed, weighted):
+    """With eps = 0.25 the targets have more room than the sources' excess, so
+    a source that selected one node too many would move it: the minimal
+    prefix per source is what the sequence shows."""
+    w = dataclasses.replace(synth.random_small(seed, 60, 3, 5, balanced=False, weighted=weighted, max_vw=2),
+                            eps=0.25)
+    L = brute.lmax(w)
+    _, _, _, tr = oracle.run_round(w, w.part, 0, 1, rebalance_only=True)
+    assert _oracle_R(tr) == brute.rebalance_subrounds(w, w.part, L)
+
+
+@pytest.mark.parametrize("limit", [1, 2])
+def test_rebalancing_sequence_stops_at_the_subround_limit(limit):
+    w = synth.random_small(**REBAL[0])
+    _, _, _, tr = oracle.run_round(w, w.part, 0, 1, rebalance_only=True, p=oracle.params(max_subrounds=limit))
+    assert _oracle_R(tr) == brute.rebalance_subrounds(w, w.part, brute.lmax(w), max_subrounds=limit)
+    assert tr["subrounds"] == limit
+
+
+def test_rebalancing_sequence_after_M_bruteforce(w):
+    """Inside a round the rebalancing starts from P o M."""
+    _, _, _, tr = oracle.run_round(w, w.part, 1, 2)
+    assert _oracle_R(tr) == brute.rebalance_subrounds(w, _after_M(w, tr), brute.lmax(w))
 
 
 def test_interleave_rule(w):
