@@ -1,7 +1,9 @@
 // The C ABI of include/upr.h: context creation, the round driver and the
 // inspection entry points.  The driver enqueues the kernels of one round on
-// the context's stream; it reads back a few counters per step (list lengths,
-// block weights between rebalancing sub-rounds) to size the next launches.
+// the context's stream.  List lengths stay in device memory (kernels read
+// them; grids are sized by static bounds), so the host reads back counters
+// once per round, and after every rebalancing sub-round only when it drives
+// that loop itself instead of launching it as one CUDA graph.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

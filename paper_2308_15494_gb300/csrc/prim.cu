@@ -1,6 +1,6 @@
 // Device-wide primitives written for this library: scans (sum / max),
-// stable LSD radix sort of (64-bit key, 32-bit value) pairs and stable flag
-// compaction.  Every ordered list the refinement produces comes out of these,
+// stable LSD radix sort of (64-bit key, 32-bit value) pairs and stable
+// compaction by flags (of the indices, or of values, in place if wanted).  Every ordered list the refinement produces comes out of these,
 // never out of the order of atomic operations, so results are deterministic.
 //
 // Element counts may live in device memory (Count::d) next to a static upper

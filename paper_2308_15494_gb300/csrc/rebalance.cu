@@ -4,7 +4,8 @@
 // proposals are ordered by the priority of Sec. 6.1 (g * c(u) for g >= 0,
 // g / c(u) for g < 0, higher first, ties by node id) through an exact integer
 // key; each source keeps the minimal prefix that removes its excess; each
-// target admits the longest prefix that fits.  The host drives the loop.
+// target admits the longest prefix that fits.  engine.cu runs the loop, from
+// the host or as one CUDA graph whose condition k_reb_continue sets.
 #include <cstddef>
 
 #include "kernels.h"
