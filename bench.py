@@ -114,15 +114,27 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def code_digest(path: str) -> str:
+    """First 16 hex digits of the sha256 of a C/CUDA source with its comments
+    removed and its blank space normalised: edits of comments keep the
+    digest, any change of the code changes it."""
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = " ".join(src.split())
+    src = re.sub(r"\s*([^\w\s])\s*", r"\1", src)     # no blank next to punctuation
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def _traffic(kernel_src: str, profile: str):
     """Per-launch DRAM bytes of the dominant kernel from a committed ncu summary,
-    only if it was taken on the current kernel source."""
+    only if it was taken on the current kernel source (same code digest)."""
     try:
         txt = open(os.path.join(ROOT, "profiles", profile)).read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
-    m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    sha = code_digest(os.path.join(ROOT, kernel_src))
+    m1 = re.search(r"code_sha256_16:\s*([0-9a-f]+)", txt)
     m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
     if not m1 or not m2 or m1.group(1) != sha:
         return None

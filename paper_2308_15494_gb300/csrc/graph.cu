@@ -1,6 +1,7 @@
 // Step (e): block weights and edge cut (Sec. 2); step (a): the gain table
-// omega(v, V_b) (Sec. 2, Sec. 6.1) and its delta update; create-time graph
-// checks and incident weights omega(I(v)).
+// omega(v, V_b) (Sec. 2, Sec. 6.1), built from the partition (its delta
+// update after moves is in delta.cu); create-time graph checks and incident
+// weights omega(I(v)).
 #include "kernels.h"
 
 namespace upr {

@@ -52,20 +52,27 @@ def fake_root(tmp_path, monkeypatch):
 
 
 def _profile(root, sha, traffic=123456):
-    (root / "profiles" / "p.md").write_text(f"source_sha256_16: {sha}\ntraffic_bytes_per_launch: {traffic}\n")
+    (root / "profiles" / "p.md").write_text(f"code_sha256_16: {sha}\ntraffic_bytes_per_launch: {traffic}\n")
 
 
-def test_traffic_reported_while_the_source_matches(fake_root):
-    sha = hashlib.sha256((fake_root / "k.cu").read_bytes()).hexdigest()[:16]
-    _profile(fake_root, sha)
+def test_traffic_reported_while_the_code_matches(fake_root):
+    _profile(fake_root, bench.code_digest(str(fake_root / "k.cu")))
+    assert bench._traffic("k.cu", "p.md") == 123456
+    # comments and layout are not code
+    (fake_root / "k.cu").write_bytes(b"// the kernel\n__global__   void k()\n{ /* empty */ }\n")
     assert bench._traffic("k.cu", "p.md") == 123456
 
 
-def test_traffic_dropped_once_the_source_changed(fake_root):
-    sha = hashlib.sha256((fake_root / "k.cu").read_bytes()).hexdigest()[:16]
-    _profile(fake_root, sha)
-    (fake_root / "k.cu").write_bytes(b"__global__ void k() { /* changed */ }\n")
+def test_traffic_dropped_once_the_code_changed(fake_root):
+    _profile(fake_root, bench.code_digest(str(fake_root / "k.cu")))
+    (fake_root / "k.cu").write_bytes(b"__global__ void k() { int x = 0; }\n")
     assert bench._traffic("k.cu", "p.md") is None
+
+
+def test_code_digest_is_sha256_of_the_normalised_code(tmp_path):
+    f = tmp_path / "a.cu"
+    f.write_text("int a; // note\n/* block\n comment */ int  b;\n")
+    assert bench.code_digest(str(f)) == hashlib.sha256(b"int a;int b;").hexdigest()[:16]
 
 
 def test_traffic_missing_profile(fake_root):
