@@ -302,6 +302,29 @@ def test_rebalancing_sequence_stops_at_the_subround_limit(limit):
     assert tr["subrounds"] == limit
 
 
+def test_rebalancing_sequence_random_sweep():
+    """Forty seeded imbalanced graphs (n 8..90, k 2..8, unit or weighted nodes,
+    isolated nodes, hubs, eps up to 0.25), both priorities."""
+    rng = np.random.default_rng(5)
+    checked = 0
+    for seed in range(100, 140):
+        n, k, deg = int(rng.integers(8, 90)), int(rng.integers(2, 9)), float(rng.uniform(1.5, 6))
+        w = synth.random_small(seed, n, deg, k, balanced=False, weighted=bool(seed % 2),
+                               max_vw=int(rng.integers(1, 12)), isolated=int(rng.integers(0, 4)),
+                               hubs=int(seed % 5 == 0))
+        if seed % 3 == 0:
+            w = dataclasses.replace(w, eps=float(rng.choice([0.03, 0.1, 0.25])))
+        L = brute.lmax(w)
+        if not np.any(brute.block_weights(w, w.part) > L):
+            continue
+        for gain_only in (0, 1):
+            _, _, _, tr = oracle.run_round(w, w.part, 0, 1, rebalance_only=True,
+                                           p=oracle.params(gain_priority=gain_only))
+            assert _oracle_R(tr) == brute.rebalance_subrounds(w, w.part, L, gain_only=bool(gain_only)), seed
+            checked += 1
+    assert checked >= 60
+
+
 def test_rebalancing_sequence_after_M_bruteforce(w):
     """Inside a round the rebalancing starts from P o M."""
     _, _, _, tr = oracle.run_round(w, w.part, 1, 2)
