@@ -32,9 +32,24 @@ def small(i):
     return synth.random_small(**SMALL[i])
 
 
-@pytest.fixture(params=range(len(SMALL)))
+def _random_specs(count=24, seed=11):
+    """Seeded random small graphs next to the hand-picked ones: n 6..69,
+    k 2..6, unit or weighted nodes, isolated nodes, a hub in every fourth."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for s in range(200, 200 + count):
+        specs.append(dict(seed=s, n=int(rng.integers(6, 70)), avg_deg=float(rng.uniform(1.5, 6)),
+                          k=int(rng.integers(2, 7)), weighted=bool(s % 2), max_vw=int(rng.integers(1, 10)),
+                          isolated=int(rng.integers(0, 3)), hubs=int(s % 4 == 0)))
+    return specs
+
+
+CASES = SMALL + _random_specs()
+
+
+@pytest.fixture(params=range(len(CASES)), ids=lambda i: f"case{i}")
 def w(request):
-    return small(request.param)
+    return synth.random_small(**CASES[request.param])
 
 
 # ---------------------------------------------------------------- step 0/1
