@@ -667,6 +667,28 @@ def test_round_driver_follows_the_rule(rounds):
         assert len(seen) > 1        # both branches of the decision are exercised
 
 
+@pytest.mark.parametrize("rounds", [3, 6, 10])
+def test_round_driver_replays_round_by_round(rounds):
+    """The driver's rounds equal single rounds of the kind it reports: round 1
+    constrained, round 2 unconstrained with tau = 1/2, an unconstrained round
+    i >= 3 with tau of round i - 2 of a schedule over rounds - 3 rounds, and
+    constrained rounds; the cut after every round and the final partition."""
+    for i in range(len(SMALL)):
+        w = small(i)
+        rc, p, cut, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, 1)
+        P = np.array(w.part, np.int32)
+        for j, code in enumerate(kinds, start=1):
+            if code == oracle.CONSTRAINED:
+                rc, P, c, _ = oracle.run_round(w, P, 1, 1, kind=("constrained",))
+            elif code == oracle.UNCONSTRAINED_HALF:
+                rc, P, c, _ = oracle.run_round(w, P, 1, 1, kind=("tau", 1, 2))
+            else:
+                assert code == oracle.UNCONSTRAINED and j >= 3
+                rc, P, c, _ = oracle.run_round(w, P, j - 2, rounds - 3)
+            assert rc == oracle.OK and c == cuts[j], (i, j)
+        assert np.array_equal(P, p)
+
+
 @pytest.mark.parametrize("factor", [(11, 10), (3, 2), (2, 1), None])
 def test_limited_round_selection_bruteforce(w, factor):
     """The variants of Sec. 7.2 without a penalty: the best target by gain
@@ -871,8 +893,10 @@ def test_lp_round_keeps_only_a_balanced_improvement(w):
 def test_lp_rounds_compose_with_the_active_set_rule():
     """Rounds after the first run on the unmoved neighbours of the moved nodes;
     the driver stops at a rolled-back round or below 0.001 improvement."""
-    for seed in (1, 2, 3, 4, 5, 6):
-        w = synth.random_small(seed, 400, 6, 8)
+    # the last four have a kept round whose improvement lies between 0.001
+    # and 0.01 of the cut, so the threshold itself decides whether they go on
+    for seed, n, deg, k in [(s, 400, 6, 8) for s in range(1, 7)] + [(s, 300, 10, 4) for s in (19, 28, 63, 65)]:
+        w = synth.random_small(seed, n, deg, k)
         P = np.array(w.part, np.int32)
         active = _boundary(w, P)
         rounds, cuts = 0, [oracle.cut(w, P)[0]]
