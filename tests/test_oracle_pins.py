@@ -770,6 +770,22 @@ def test_variant_schedules_follow_the_rule(schedule):
             assert c == cuts[r]
 
 
+@pytest.mark.parametrize("tau1", [(3, 10), (1, 4)])
+def test_constant_tau_variant_uses_tau_1(tau1):
+    """Schedule 3 keeps tau_1 in every unconstrained round, whatever tau_1 is."""
+    for i in (0, 1, 3, 5):
+        w = small(i)
+        rounds = 5
+        rc, part, cut, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, 3, p=oracle.params(tau1=tau1))
+        assert rc == oracle.OK
+        P = np.array(w.part, np.int32)
+        for r, kd in enumerate(kinds, start=1):
+            kind = ("constrained",) if kd == oracle.CONSTRAINED else ("tau",) + tau1
+            _, P, c, _ = oracle.run_round(w, P, 1, 1, kind=kind)
+            assert c == cuts[r], (i, r)
+        assert np.array_equal(P, part)
+
+
 def test_gain_priority_reduces_to_the_paper_rule_for_unit_weights():
     """With unit node weights g/c(u) and g*c(u) are g itself, so the gain-only
     rebalancing priority (the variant of Sec. 7.2) gives the same rounds; with
