@@ -105,6 +105,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+HBM_NOMINAL_GBS = 7900.0      # GB300 HBM3e, nominal
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -560,7 +563,8 @@ def run_gpu(args):
     achieved = bytes_build / t_build / 1e9
     roofline = {"bound": "hbm", "kernel": "gain table build (k_table_tiles + k_table_hub_chunks)",
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": achieved / peak, "bytes_per_launch": bytes_build, "ms_per_launch": t_build * 1e3,
+                "frac": achieved / peak, "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": achieved / HBM_NOMINAL_GBS,
+                "bytes_per_launch": bytes_build, "ms_per_launch": t_build * 1e3,
                 "traffic": _traffic("paper_2308_15494_gb300/csrc/graph.cu", "gain_table_rmat_s22_k64.md")}
 
     # end to end through the C ABI from pinned host buffers
