@@ -8,7 +8,7 @@
  * Partitioning Irregular Graphs", arXiv 2308.15494).  One round is the
  * deterministic synchronous form of Algorithm 1:
  *   (a) gain table omega(v, V_b) (Sec. 6.1),
- *   (b) selection of moves that may violate the balance constraint, scored by
+ *   (b) selection of moves that ignore the balance constraint, scored by
  *       gain minus the rebalancing-cost penalty of Sec. 4.3, scaled by the
  *       tau schedule of Sec. 4.4,
  *   (d) rebalancing by gain-per-weight priority (Sec. 6),
