@@ -335,7 +335,9 @@ def other_configs_leg(args, upr):
     partition resident, CUDA events around upr_refine): the Chung-Lu graph
     with 16,384 nodes (k = 8, 4 rounds) and the weighted random geometric
     graph with 2^22 nodes (k = 256, 8 rounds; also with each table layout
-    forced), and the R-MAT workload under the round driver of Sec. 6.2."""
+    forced), and the R-MAT workload under the round drivers of Sec. 4.4 / 6.2
+    (the paper's final configuration also with the paper's ten rounds) and
+    the variants of Sec. 7.2."""
     import torch
     peak, _ = _peaks()
     out = {}
@@ -343,16 +345,21 @@ def other_configs_leg(args, upr):
             ("rgg_2^22_weighted_k256_dense_table", "plain_weighted", 3, {"table": 1}),
             ("rgg_2^22_weighted_k256_hashed_table", "plain_weighted", 3, {"table": 2}),
             ("rgg_2^22_weighted_k256_gain_priority", "plain_weighted", 3, {"gain_priority": 1}),
-            ("rmat_s22_k64_round_driver", "plain_large", 3, {"schedule": 1}),
+            ("rmat_s22_k64_final_configuration_10_rounds", "plain_large", 3, {"schedule": 6, "rounds": 10}),
+            ("rmat_s22_k64_final_configuration", "plain_large", 3, {"schedule": 6}),
+            ("rmat_s22_k64_dynamic_activation", "plain_large", 3, {"schedule": 1}),
             ("rmat_s22_k64_constant_tau_half", "plain_large", 3, {"schedule": 3, "tau1_num": 1, "tau1_den": 2}),
             ("rmat_s22_k64_fully_unconstrained", "plain_large", 3, {"schedule": 4}),
             ("rmat_s22_k64_limited_imbalance", "plain_large", 3, {"schedule": 5}),
             ("rmat_s22_k64_appended_sequence", "plain_large", 3, {"append": 1}),
             ("rmat_s22_k64_label_propagation", "plain_large", 3, {"lp_rounds": 5}),
-            ("rmat_s22_k64_label_propagation_round_driver", "plain_large", 3, {"lp_rounds": 5, "schedule": 1}))
+            ("rmat_s22_k64_label_propagation_final_configuration_10_rounds", "plain_large", 3,
+             {"lp_rounds": 5, "schedule": 6, "rounds": 10}))
     for name, builder, steps, over in legs:
         w = synth.cached(getattr(synth, builder))
         prm = upr.upr_params_default()
+        over = dict(over)
+        rounds = over.pop("rounds", w.rounds)
         for key, val in over.items():
             setattr(prm, key, val)
         table, schedule = prm.table, prm.schedule
@@ -361,7 +368,7 @@ def other_configs_leg(args, upr):
         part = torch.empty_like(init)
         for _ in range(2):
             part.copy_(init)
-            upr.upr_refine(ctx, part, w.rounds)
+            upr.upr_refine(ctx, part, rounds)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -369,20 +376,22 @@ def other_configs_leg(args, upr):
         e0.record()
         for _ in range(steps):
             part.copy_(init)
-            sts.append(upr.upr_refine(ctx, part, w.rounds))
+            sts.append(upr.upr_refine(ctx, part, rounds))
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         st = sts[-1]
         t_build = sum(x.ms_gain_table for x in sts) / max(1, sum(x.gain_table_builds for x in sts))
-        out[name] = {"n": w.n, "m": w.m, "k": w.k, "rounds": w.rounds, "weighted": w.adjw is not None,
-                     "ms_per_refine": ms, "edges_per_s": w.rounds * (w.m // 2) / (ms / 1e3),
+        out[name] = {"n": w.n, "m": w.m, "k": w.k, "rounds": rounds, "weighted": w.adjw is not None,
+                     "ms_per_refine": ms, "edges_per_s": rounds * (w.m // 2) / (ms / 1e3),
                      "cut_in": st.cut_in, "cut_out": st.cut_out,
                      "table": ("hashed rows" if st.sparse_table else "dense n x k")
                               + (" (chosen by size)" if table == 0 else ""),
-                     "schedule": ["every round unconstrained", "round driver of Sec. 6.2",
+                     "schedule": ["every round unconstrained",
+                                  "dynamic activation (Sec. 4.4; not in the paper's final configuration)",
                                   "every round constrained", "constant penalty tau = 0.5 (Sec. 7.2)",
-                                  "fully unconstrained (Sec. 7.2)", "limited imbalance 2 -> 1.1 (Sec. 7.2)"][schedule],
+                                  "fully unconstrained (Sec. 7.2)", "limited imbalance 2 -> 1.1 (Sec. 7.2)",
+                                  "the paper's final configuration (Sec. 4.4, Sec. 7.2)"][schedule],
                      "rebalancing_priority": "gain alone (Sec. 7.2)" if prm.gain_priority else "g/c, g*c (Sec. 6.1)",
                      "sequence": "appended (Sec. 7.2)" if prm.append else "interleaved (Sec. 4.4)",
                      "label_propagation_rounds_kept": st.lp_rounds,

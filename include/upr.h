@@ -57,14 +57,16 @@ typedef struct upr_ctx upr_ctx;
 typedef struct upr_server upr_server;
 
 /* An undirected graph in CSR form (Sec. 2).  Every edge {u,v} appears twice,
- * as v in u's list and u in v's list, with equal weight.  n < 2^31, m < 2^31.
+ * as v in u's list and u in v's list, with equal weight, and a list holds each
+ * neighbour once (E is a set of pairs).  n < 2^31, m < 2^31.
  * on_device: ignored (the library inspects the pointers); kept for callers
  * that want to state it. */
 typedef struct {
     int64_t        n;        /* number of nodes                                      */
     int64_t        m;        /* number of adjacency entries (= 2|E|)                 */
     const int64_t *xadj;     /* [n+1], xadj[0] = 0, non-decreasing, xadj[n] = m      */
-    const int32_t *adjncy;   /* [m], neighbour ids in [0, n), no self loops          */
+    const int32_t *adjncy;   /* [m], neighbour ids in [0, n), no self loops, no
+                                duplicates within a row                              */
     const int32_t *vwgt;     /* [n] node weights c(v) > 0, or NULL for unit weights  */
     const int32_t *adjwgt;   /* [m] edge weights omega > 0, or NULL for unit weights */
     int32_t        on_device;
@@ -76,8 +78,13 @@ typedef struct {
     int32_t tau1_num, tau1_den;  /* tau_1, the penalty factor of round 1 (Sec. 4.4); rounds
                                     interpolate linearly to 1. 1/4; tau1_den <= 65536       */
     int32_t max_subrounds;       /* rebalancing sub-rounds per round. 64                      */
-    int32_t validate;            /* 1: check the graph in upr_create (symmetry by a 64-bit
-                                    multiset hash, ranges, weights). 1                      */
+    int32_t validate;            /* 1: check the graph in upr_create: offsets, neighbour
+                                    ranges, self loops, weights and duplicate neighbours
+                                    exactly; symmetry with equal weights by a 64-bit
+                                    multiset hash (an asymmetric graph is rejected with
+                                    probability 1 - 2^-64 unless built against the hash).
+                                    0: the caller guarantees all of it (a duplicate then
+                                    counts as a second edge of the same pair). 1            */
     int32_t round_offset;        /* rounds already run of a longer schedule (resume). 0       */
     int32_t total_rounds;        /* length of the tau schedule; 0 = the rounds of each call   */
     int32_t autotune;            /* 1: on a context's first large calls, time the lane
@@ -99,24 +106,28 @@ typedef struct {
                                     node over one sub-round, the stop test on the device);
                                     0: the host launches every sub-round and reads its stop
                                     flag.  Results never depend on it. 1                     */
-    int32_t schedule;            /* round driver (Sec. 6.2): 0 every round unconstrained
-                                    with the tau schedule; 1 the paper's integration:
-                                    round 1 constrained, round 2 unconstrained with
-                                    tau = 1/2, then rounds 3..R-1 unconstrained (tau
-                                    schedule over them) if round 2 improved the cut more
-                                    than round 1, switching to constrained once a round
-                                    improves it by less than 0.002 of the cut, else
-                                    constrained; round R constrained; 2 every round
-                                    constrained.  A constrained round is the same round
-                                    with every move that would leave its target above
-                                    L_max forbidden.  The variants of Sec. 7.2, each with
-                                    the same switch to constrained rounds and a
-                                    constrained last round: 3 constant penalty (tau =
+    int32_t schedule;            /* round driver (Sec. 4.4, Sec. 6.2): 0 every round
+                                    unconstrained with the tau schedule.  6 the paper's
+                                    final configuration: the first U rounds unconstrained
+                                    with tau from tau_1 to 1 over them, the rest
+                                    constrained (U = R - 2 for R >= 3, the paper's eight
+                                    and two of ten; U = 1 for R = 2; U = 0 for R = 1), and
+                                    every round after one that improves the cut by less
+                                    than 0.002 of it constrained.  The variants of
+                                    Sec. 7.2 in the same frame: 3 constant penalty (tau =
                                     tau_1 every round), 4 fully unconstrained (no penalty,
                                     nothing forbidden), 5 limited imbalance (no penalty,
                                     no block above alpha * L_max, alpha from 2 to 1.1).
-                                    1..5 need one graph, round_offset = 0 and
-                                    total_rounds = 0. 0                                     */
+                                    1 dynamic activation (Sec. 4.4, which Sec. 7.2 leaves
+                                    out of the final configuration): round 1 constrained,
+                                    round 2 unconstrained with tau = 1/2, rounds 3..R-1
+                                    unconstrained (tau schedule over them, with the same
+                                    switch) if round 2 improved the cut more than round
+                                    1, else constrained; round R constrained.  2 every
+                                    round constrained.  A constrained round is the same
+                                    round with every move that would leave its target
+                                    above L_max forbidden.  1..6 need one graph,
+                                    round_offset = 0 and total_rounds = 0. 0             */
     int32_t gain_priority;       /* rebalancing priority: 0 g/c(u) for g < 0 and g*c(u)
                                     for g >= 0 (Sec. 6.1); 1 the gain alone (the variant
                                     of Sec. 7.2), ties by node id either way. 0             */
@@ -163,7 +174,7 @@ typedef struct {
     int32_t propose_lanes;       /* lanes per node of the proposal kernel (0: scalar)   */
     int32_t sparse_table;        /* 1: the rounds ran on the sparse gain table            */
     int32_t rebalance_graphs;    /* rounds whose rebalancing loop ran as one graph launch */
-    int32_t constrained_rounds;  /* constrained rounds (schedule 1 or 2)                 */
+    int32_t constrained_rounds;  /* constrained rounds (schedules 1-6)                   */
     int32_t lp_rounds;           /* label propagation rounds kept (Sec. 5)               */
 } upr_stats;
 
@@ -216,15 +227,20 @@ void upr_destroy(upr_ctx *ctx);
  * caller's); cut (one int64) and block_weights (k int64, may be NULL) may be
  * host or device memory.  The kernels' scratch is one static device array of
  * 4096 + 8 int64 that every GPU loading the library holds until exit, so
- * k must be in [2, 4096] (UPR_ERR_INVALID otherwise).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * it before any stream capture.  Every call on a device shares the one
- * array and clears what it accumulates into, so calls whose work overlaps on
- * the GPU (other streams, other host threads) race and must be serialised by
- * the caller.  The call runs on `stream` (cudaStream_t, NULL = default) and
- * returns after synchronising it.  Errors: UPR_ERR_INVALID (sizes, k, host
- * graph pointers, part values outside [0, k)), UPR_ERR_CUDA.  The graph is
- * not validated beyond that (see upr_create's validate). */
+ * k must be in [2, 4096] (UPR_ERR_INVALID otherwise).  Every call looks up
+ * that array's device address (cudaGetSymbolAddress, which allocates
+ * nothing); the first call on a device may load the library's device code,
+ * so make it before any stream capture.  Every call on a device shares the
+ * one array and clears what it accumulates into, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The call runs on `stream` (cudaStream_t, NULL =
+ * default) and returns after synchronising it.  Before any kernel indexes
+ * with them it checks, on the device, that part is in [0, k), that xadj[0] =
+ * 0, xadj[n] = m and xadj is non-decreasing, and that every neighbour id is
+ * in [0, n).  Errors: UPR_ERR_INVALID (sizes, k, pointers that are not
+ * device memory of the current device, a failed check above), UPR_ERR_CUDA.
+ * Symmetry, self loops and weights are not checked (see upr_create's
+ * validate). */
 upr_status upr_cut_noalloc(const upr_graph *g, int32_t k, const int32_t *part, void *stream, int64_t *cut,
                            int64_t *block_weights);
 

@@ -251,20 +251,24 @@ def refine(w, part, rounds: Optional[int] = None, round_offset: int = 0,
     return rc, part, int(c.value), rcuts
 
 
-# Round kinds reported by refine_schedule (the round driver of Sec. 6.2 and
-# the variants of Sec. 7.2).
+# Round kinds reported by refine_schedule (the round driver of Sec. 4.4 / 6.2
+# and the variants of Sec. 7.2).
 UNCONSTRAINED, CONSTRAINED, UNCONSTRAINED_HALF, CONSTANT_TAU, NO_PENALTY, LIMITED = 0, 1, 2, 3, 4, 5
 
 
 def refine_schedule(w, part, rounds: int, schedule: int, p: Optional[Params] = None):
-    """The round driver of Sec. 6.2: schedule 0 = every round unconstrained
-    (tau schedule over the rounds), 1 = the paper's integration (constrained
-    round, unconstrained round with tau = 1/2, then unconstrained or
-    constrained rounds by the improvements, constrained last round), 2 =
-    every round constrained; the variants of Sec. 7.2 (3 constant tau =
-    tau_1, 4 fully unconstrained, 5 limited imbalance 2 -> 1.1), each with
-    the switch to constrained rounds and a constrained last round.  Returns (rc, new_part, cut, per-round cuts
-    [rounds+1], kind of each round [rounds])."""
+    """The round driver of Sec. 4.4 / Sec. 6.2.  schedule 0 = every round
+    unconstrained (tau schedule over the rounds); 6 = the paper's final
+    configuration (unconstrained rounds with tau annealed from tau_1 to 1
+    over the first U rounds, U = R - 2 for R >= 3, 1 for R = 2, 0 for R = 1,
+    the switch to constrained rounds below an improvement of 0.002 of the
+    cut, constrained rounds after them); 3-5 = the variants of Sec. 7.2 in
+    the same frame (3 constant tau = tau_1, 4 fully unconstrained, 5 limited
+    imbalance 2 -> 1.1); 1 = dynamic activation (Sec. 4.4, not in the
+    paper's final configuration: constrained round, unconstrained round with
+    tau = 1/2, then unconstrained or constrained rounds by the improvements,
+    constrained last round); 2 = every round constrained.  Returns (rc,
+    new_part, cut, per-round cuts [rounds+1], kind of each round [rounds])."""
     g = _G(w)
     part = np.array(part, dtype=np.int32, copy=True)
     c = ctypes.c_int64(0)

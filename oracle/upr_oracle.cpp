@@ -870,30 +870,47 @@ int upro_refine(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_par
     return UPRO_OK;
 }
 
-/* The round driver of Sec. 6.2 over `rounds` rounds.  schedule 0: every
- * round unconstrained with tau_r of the rounds' schedule (as upro_refine);
- * 2: every round constrained; 1: the paper's integration, read as
- *   round 1 constrained, round 2 unconstrained with tau = 1/2; if round 2
- *   improved the cut by more than round 1, rounds 3..R-1 are unconstrained
- *   with tau_i of a schedule over those R-3 rounds (i = 1, 2, ...), and once
- *   such a round improves the cut by less than 0.002 of the cut before it,
- *   the remaining ones are constrained; otherwise rounds 3..R-1 are
- *   constrained; round R (R >= 3) is constrained.
- * The variants of Sec. 7.2 (schedules 3-5) run rounds 1..R-1 of their kind
- * and round R constrained (R >= 2); as in the paper's experiments, once a
- * variant round improves the cut by less than 0.002 of the cut before it,
- * the remaining rounds are constrained.  3: constant penalty, tau = tau_1 in
- * every round; 4: fully unconstrained, no penalty and nothing forbidden;
- * 5: limited imbalance, no penalty but no block above alpha_i * L_max, alpha
- * going linearly from 2 (round 1) to 1.1 (round R-1), limit rounded down.
+/* The round driver of Sec. 4.4 / Sec. 6.2 over R = `rounds` rounds.
+ *
+ * The frame of the paper's final configuration (Sec. 4.4, "Integration into
+ * the Overall Algorithm", with the parameters of Sec. 7.2): the first U
+ * rounds are unconstrained, the others constrained, where U = R - 2 for
+ * R >= 3 (ten rounds: eight unconstrained and two constrained, the split
+ * Sec. 7.2 compares the switch against), U = 1 for R = 2 and U = 0 for
+ * R = 1, so at least one constrained round follows the unconstrained ones;
+ * once an unconstrained round improves the cut by less than 0.002 of the
+ * cut before it, every later round is constrained.
+ *
+ * schedule 0: every round unconstrained with tau_r of the rounds' schedule
+ *   (as upro_refine; no switch, no constrained round).
+ * schedule 6: the paper's final configuration: the frame above with tau_i
+ *   of a schedule over the U unconstrained rounds (tau_1 in round 1, 1 in
+ *   round U).
+ * schedules 3-5, the variants of Sec. 7.2 in the same frame (every variant
+ *   there starts unconstrained and switches at 0.002): 3 constant penalty,
+ *   tau = tau_1 in every unconstrained round; 4 fully unconstrained, no
+ *   penalty and nothing forbidden; 5 limited imbalance, no penalty but no
+ *   block above alpha_i * L_max, alpha going linearly from 2 (round 1) to
+ *   1.1 (round U), the limit rounded down.
+ * schedule 1: dynamic activation (Sec. 4.4, last paragraph), which Sec. 7.2
+ *   tested and left out of the final configuration: round 1 constrained,
+ *   round 2 unconstrained with tau = 1/2; if round 2 improved the cut by
+ *   more than round 1, rounds 3..R-1 are unconstrained with tau_i of a
+ *   schedule over those R-3 rounds (i = 1, 2, ...) until one of them
+ *   improves the cut by less than 0.002 of the cut before it, the remaining
+ *   ones constrained; otherwise rounds 3..R-1 are constrained; round R
+ *   (R >= 3) is constrained.
+ * schedule 2: every round constrained.
  * kinds[i-1] (may be NULL) receives round i's kind: 0 unconstrained (tau of
  * the schedule), 1 constrained, 2 unconstrained with tau = 1/2, 3 constant
  * tau, 4 no penalty, 5 limited imbalance. */
+static int32_t unconstrained_rounds(int32_t R) { return R >= 3 ? R - 2 : R == 2 ? 1 : 0; }
+
 int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const upro_params *pp, int32_t *part,
                          int32_t rounds, int32_t schedule, int64_t *cut_out, int64_t *round_cuts, int8_t *kinds) {
     upro_params p = pp ? *pp : defaults();
     Graph g = wrap(gg);
-    if (!params_ok(p) || k < 2 || rounds < 0 || rounds > 65536 || schedule < 0 || schedule > 5)
+    if (!params_ok(p) || k < 2 || rounds < 0 || rounds > 65536 || schedule < 0 || schedule > 6)
         return UPRO_ERR_INVALID;
     for (int64_t v = 0; v < g.n; v++) if (part[v] < 0 || part[v] >= k) return UPRO_ERR_INVALID;
     int64_t tot = 0;
@@ -914,29 +931,32 @@ int upro_refine_schedule(const upro_graph *gg, int32_t k, int64_t eps_ppm, const
     if (round_cuts) round_cuts[0] = cut;
     bool unconstrained_rest = false, switched = false;
     int64_t imp1 = 0;
-    const int32_t U = rounds - 3;            /* unconstrained rounds 3..R-1 of schedule 1 */
+    const int32_t U1 = rounds - 3;                      /* unconstrained rounds 3..R-1 of schedule 1 */
+    const int32_t U = unconstrained_rounds(rounds);     /* unconstrained rounds of schedules 3-6 */
     std::vector<int8_t> locked(p.lock_rebalanced ? g.n : 0, 0), locked_next(locked);
     for (int32_t i = 1; i <= rounds; i++) {
         RoundKind kind;
         int8_t code = 0;
         int32_t r = i, R = rounds;
-        if (schedule == 2 || (schedule >= 3 && ((rounds >= 2 && i == rounds) || switched))) {
+        if (schedule == 2 || (schedule >= 3 && (i > U || switched))) {
             kind.constrained = true; code = 1;
         } else if (schedule == 3) {
             kind.tau_num = p.tau1_num; kind.tau_den = p.tau1_den; code = 3;
         } else if (schedule == 4) {
             kind.limit = INT64_MAX; code = 4;
         } else if (schedule == 5) {
-            const int64_t D = rounds > 2 ? rounds - 2 : 1;            /* alpha over rounds 1..R-1 */
+            const int64_t D = U > 1 ? U - 1 : 1;                    /* alpha over rounds 1..U */
             kind.limit = (int64_t)(((i128)Lmax * (20 * D - 9 * (int64_t)(i - 1))) / (10 * D));
             code = 5;
+        } else if (schedule == 6) {
+            r = i; R = U;                                             /* tau_i of the U unconstrained rounds */
         } else if (schedule == 1) {
             if (i == 1 || (rounds >= 3 && i == rounds) || (i >= 3 && (!unconstrained_rest || switched))) {
                 kind.constrained = true; code = 1;
             } else if (i == 2) {
                 kind.tau_num = 1; kind.tau_den = 2; code = 2;
             } else {
-                r = i - 2; R = U;              /* tau_{i-2} of the U unconstrained rounds */
+                r = i - 2; R = U1;             /* tau_{i-2} of the U1 unconstrained rounds */
             }
         }
         const int64_t before = cut;

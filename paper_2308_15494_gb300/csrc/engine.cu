@@ -78,7 +78,7 @@ void penalty_factors(int32_t r, int32_t R, int64_t t1n, int64_t t1d, int64_t *F)
     factors_tau((u128)(t1n * D + (t1d - t1n) * (int64_t)(r - 1)), (u128)(t1d * D), F);
 }
 
-// The kind of a round (Sec. 6.2): unconstrained with tau_r of the schedule
+// The kind of a round (Sec. 4.4, Sec. 6.2): unconstrained with tau_r of the schedule
 // (tau_den = 0) or a given tau, or constrained: no move may leave its target
 // above L_max.  A constrained round uses the factor 2^51 in every slot: the
 // penalty of any move that overfills its target is then at least 2^31, more
@@ -499,9 +499,15 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     }
     const Count cP{dP, n};
     uint64_t *kA; uint32_t *A;
-    rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->prm.gain_priority, c->sb[0].k, c->sb[0].v,
-                        n, s);
-    c->sb[0].run(cP, 1 + c->gbits + 2 * c->cbits, c->tmp, s, &kA, &A);
+    const int key_bits = 1 + c->gbits + 2 * c->cbits;
+    if (key_bits <= 63) {
+        rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->prm.gain_priority, c->sb[0].k,
+                            c->sb[0].v, n, s);
+        c->sb[0].run(cP, key_bits, c->tmp, s, &kA, &A);
+    } else {                // a 128-bit key: two stable sorts in sb[0]'s buffers
+        rebalance_prio_sort_wide(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->prm.gain_priority,
+                                 SortPairs{c->sb[0].k, c->sb[0].ka, c->sb[0].v, c->sb[0].va}, n, c->tmp, s, &A);
+    }
     // per source: the minimal prefix covering the excess
     uint64_t *kB; uint32_t *B;
     rebalance_block_keys(Pn, A, nullptr, dP, c->part, c->sb[1].k, c->sb[1].v, n, s);
@@ -1239,27 +1245,40 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
         st.lp_rounds = label_propagation(c, c->prm.lp_rounds, &cut_lp, st);
         repair_gain = st.cut_in - cut_lp;       // the rounds below start from this cut
     }
-    // schedule 1 (Sec. 6.2): round 1 constrained, round 2 unconstrained with
-    // tau = 1/2; rounds 3..R-1 unconstrained (tau_i of a schedule over those
-    // R-3 rounds) if round 2 improved the cut more than round 1, until one of
-    // them improves it by less than 0.002 of the cut before it, constrained
-    // otherwise; round R constrained.  Schedule 2: every round constrained.
+    // The frame of the paper's final configuration (Sec. 4.4, with Sec. 7.2's
+    // split of ten rounds into eight unconstrained and two constrained): the
+    // first U rounds unconstrained (U = R - 2 for R >= 3, 1 for R = 2, 0 for
+    // R = 1), the others constrained, and once an unconstrained round improves
+    // the cut by less than 0.002 of the cut before it, every later round is
+    // constrained.  Schedule 6 runs its unconstrained rounds with tau_i of a
+    // schedule over the U rounds; the variants of Sec. 7.2 (3-5) run theirs
+    // in the same frame.  Schedule 1 is dynamic activation (Sec. 4.4, left out
+    // of the final configuration in Sec. 7.2): round 1 constrained, round 2
+    // unconstrained with tau = 1/2; rounds 3..R-1 unconstrained (tau_i of a
+    // schedule over those R-3 rounds) if round 2 improved the cut more than
+    // round 1, until one of them improves it by less than 0.002 of the cut
+    // before it, constrained otherwise; round R constrained.  Schedule 2:
+    // every round constrained.
+    const int32_t U = rounds >= 3 ? rounds - 2 : rounds == 2 ? 1 : 0;
     bool unconstrained_rest = false, switched = false;
     int64_t imp1 = 0, cut_now = st.cut_in - repair_gain;
     for (int32_t i = 1; i <= rounds; i++) {
         RoundInfo ri;
         RoundKind kind;
         int32_t r = c->prm.round_offset + i, R = total;
-        if (sch == 2 || (sch >= 3 && ((rounds >= 2 && i == rounds) || switched))) {
+        if (sch == 2 || (sch >= 3 && (i > U || switched))) {
             kind.constrained = true;
         } else if (sch == 3) {                       // constant penalty, tau = tau_1
             kind.tau_num = c->prm.tau1_num;
             kind.tau_den = c->prm.tau1_den;
         } else if (sch == 4) {                       // fully unconstrained
             kind.limit = INT64_MAX;
-        } else if (sch == 5) {                       // limited imbalance, alpha 2 -> 1.1
-            const int64_t D = rounds > 2 ? rounds - 2 : 1;
+        } else if (sch == 5) {                       // limited imbalance, alpha 2 -> 1.1 over rounds 1..U
+            const int64_t D = U > 1 ? U - 1 : 1;
             kind.limit = (int64_t)(((i128)c->Lmax * (20 * D - 9 * (int64_t)(i - 1))) / (10 * D));
+        } else if (sch == 6) {                       // tau_i of the U unconstrained rounds
+            r = i;
+            R = U;
         } else if (sch == 1) {
             if (i == 1 || (rounds >= 3 && i == rounds) || (i >= 3 && (!unconstrained_rest || switched))) {
                 kind.constrained = true;
@@ -1365,7 +1384,7 @@ static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
-           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 5 && p.lp_rounds >= 0 && p.lp_rounds <= 64 &&
+           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 6 && p.lp_rounds >= 0 && p.lp_rounds <= 64 &&
            (p.lock_rebalanced == 0 || p.lock_rebalanced == 1) &&
            (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
 }
@@ -1676,7 +1695,14 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         UPR_CUDA(cudaStreamSynchronize(s));     // noff is host memory that may be re-assigned
     }
     if (prm.validate) {
-        validate_graph(c->G, c->vacc, c->vflags, s);
+        // the hub list goes to a sort buffer, free until the first round
+        std::vector<int32_t> hubs;
+        for (size_t i = 0; i < chunks.size(); i++)
+            if (i == 0 || chunks[i].v != chunks[i - 1].v) hubs.push_back(chunks[i].v);
+        int32_t *hubs_d = reinterpret_cast<int32_t *>(c->sb[0].v);
+        if (!hubs.empty())
+            UPR_CUDA(cudaMemcpyAsync(hubs_d, hubs.data(), sizeof(int32_t) * hubs.size(), cudaMemcpyHostToDevice, s));
+        validate_graph(c->G, c->vacc, c->vflags, hubs_d, (int64_t)hubs.size(), c->noff_d, s);
         uint64_t acc[2]; int32_t flags;
         UPR_CUDA(cudaMemcpyAsync(acc, c->vacc, sizeof(acc), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
@@ -1688,7 +1714,6 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     read_i64(c, c->scal, 1, &c->wmax);
     if (c->wmax > 0x7fffffffLL) { c->n = -1; return UPR_ERR_INVALID; }
     c->gbits = std::max(1, bit_length((uint64_t)c->wmax));
-    if (1 + c->gbits + 2 * c->cbits > 63) { c->n = -1; return UPR_ERR_INVALID; }
     // the arena may hold another binding's data: clear every word a kernel
     // reads before writing it
     UPR_CUDA(cudaMemsetAsync(c->tmp.ticket, 0, 64 * sizeof(unsigned int), s));

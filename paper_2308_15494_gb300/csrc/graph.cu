@@ -109,8 +109,10 @@ __device__ __forceinline__ uint64_t entry_hash(uint64_t a, uint64_t b, uint64_t 
 }
 
 // Validation bits: 1 xadj, 2 neighbour range (or, in a batch, a neighbour in
-// another graph), 4 self loop, 8 edge weight, 16 node weight, 64 asymmetric
-// (sum of hash(v,u,w) over entries != sum of hash(u,v,w)).
+// another graph), 4 self loop, 8 edge weight, 16 node weight, 32 duplicate
+// neighbour in a row; asymmetry shows as differing sums of hash(v,u,w) and
+// hash(u,v,w) over the entries (an asymmetric graph whose sums agree passes:
+// probability about 2^-64 for a graph not built against the hash).
 __global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
                                    const int32_t *__restrict__ adjw, const int32_t *__restrict__ gid, int64_t n,
                                    int64_t m, unsigned long long *__restrict__ acc, int32_t *__restrict__ flags) {
@@ -167,6 +169,101 @@ __global__ void k_validate_nodes(const int64_t *__restrict__ xadj, const int32_t
     if (v < n && xadj[v + 1] < xadj[v]) f |= 1;
     if (v < n && vwgt && vwgt[v] <= 0) f |= 16;
     if (f) atomicOr(flags, f);
+}
+
+// Duplicate adjacency entries (E is a set of pairs {v, u}, Sec. 2, so a row
+// lists each neighbour once).  Rows of degree <= kHubDegree: a CTA takes the
+// rows that start in a chunk of kDupChunk entries (they may run into the
+// next chunk, by less than kHubDegree entries) and inserts (row, neighbour)
+// into a hash set in shared memory: kDupSlots 64-bit keys, linear probing, a
+// key that meets itself is a duplicate.  Keys carry the CTA's iteration
+// number, so a slot holding another iteration's key counts as empty and the
+// set is never cleared between chunks.  Hub rows: k_dup_hubs.  Both set
+// validation bit 32.
+constexpr int kDupChunk = 4096;
+constexpr int kDupSlots = 4 * kDupChunk;             // >= 2 x the entries of one chunk's rows (< 2 kDupChunk)
+constexpr int64_t kDupRange = (int64_t)1 << 20;     // neighbour ids per bitmap of k_dup_hubs
+static_assert(kHubDegree <= kDupChunk, "a row of a chunk ends within the next chunk");
+static_assert((kDupSlots & (kDupSlots - 1)) == 0, "power of two");
+
+__device__ __forceinline__ uint64_t dup_key(uint64_t iter, int64_t row, int32_t u) {
+    // iteration: 20 bits; row: its first entry's offset from the chunk's first
+    // row start, 13 bits (< kDupChunk + kHubDegree); neighbour: 31 bits
+    return (iter << 44) | ((uint64_t)row << 31) | (uint64_t)(uint32_t)u;
+}
+
+__global__ void __launch_bounds__(512) k_dup_rows(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                                                  int64_t n, int64_t m, int32_t *__restrict__ flags) {
+    extern __shared__ unsigned long long s_set[];
+    __shared__ int64_t s_v[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < kDupSlots; i += blockDim.x) s_set[i] = ~0ull;     // iteration field all ones
+    bool dup = false;
+    const int64_t chunks = (m + kDupChunk - 1) / kDupChunk;
+    uint64_t iter = 0;
+    for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x, iter = (iter + 1) & 0xFFFFF) {
+        const int64_t e0 = c * kDupChunk, e1 = min(m, e0 + kDupChunk);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // the rows that start in [e0, e1): first row starting at or after
+            // e0, first row starting at or after e1
+            int64_t lo = 0, hi = n;
+            while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (xadj[mid] < e0) lo = mid + 1; else hi = mid; }
+            s_v[0] = lo;
+            hi = n;
+            while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (xadj[mid] < e1) lo = mid + 1; else hi = mid; }
+            s_v[1] = lo;
+        }
+        __syncthreads();
+        const int64_t va = s_v[0], vb = s_v[1];
+        if (va >= vb) continue;
+        const int64_t f0 = xadj[va];
+        for (int64_t v = va + warp; v < vb; v += warps) {
+            const int64_t r0 = xadj[v], r1 = xadj[v + 1];
+            if (r1 - r0 < 2 || r1 - r0 > kHubDegree) continue;
+            for (int64_t e = r0 + lane; e < r1; e += 32) {
+                const uint64_t key = dup_key(iter, r0 - f0, adj[e]);
+                uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 50) & (kDupSlots - 1);
+                for (int probe = 0; probe < kDupSlots;) {
+                    const unsigned long long cur = s_set[h];
+                    if ((cur >> 44) != iter) {            // another iteration's key: empty
+                        if (atomicCAS(&s_set[h], cur, key) == cur) break;
+                        continue;                         // lost the slot: look at it again
+                    }
+                    if (cur == key) { dup = true; break; }
+                    h = (h + 1) & (kDupSlots - 1);
+                    probe++;
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(dup) && threadIdx.x == 0) atomicOr(flags, 32);
+}
+
+// Hub rows (degree > kHubDegree), one CTA each: the row's neighbours in
+// [lo, lo + kDupRange) set bits of a shared-memory bitmap, range after range
+// over the node ids of the hub's graph; a bit found set is a duplicate.
+__global__ void __launch_bounds__(256) k_dup_hubs(const int32_t *__restrict__ hubs, const int64_t *__restrict__ xadj,
+                                                  const int32_t *__restrict__ adj, int64_t n,
+                                                  const int32_t *__restrict__ gid, const int64_t *__restrict__ noff,
+                                                  int32_t *__restrict__ flags) {
+    extern __shared__ uint32_t s_bits[];
+    const int32_t v = hubs[blockIdx.x];
+    const int64_t e0 = xadj[v], e1 = xadj[v + 1];
+    const int64_t lo0 = noff ? noff[gid[v]] : 0, hi = noff ? noff[gid[v] + 1] : n;
+    bool dup = false;
+    for (int64_t lo = lo0; lo < hi; lo += kDupRange) {
+        for (int i = threadIdx.x; i < (int)(kDupRange / 32); i += blockDim.x) s_bits[i] = 0;
+        __syncthreads();
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int64_t x = (int64_t)adj[e] - lo;
+            if (x < 0 || x >= kDupRange) continue;
+            const uint32_t bit = 1u << (x & 31);
+            dup |= (atomicOr(&s_bits[x >> 5], bit) & bit) != 0;
+        }
+        __syncthreads();
+    }
+    if (__syncthreads_or(dup) && threadIdx.x == 0) atomicOr(flags, 32);
 }
 
 // Dense gain table: G lanes per node, a k-int row per group in shared memory,
@@ -478,7 +575,8 @@ void sparse_to_dense(const GraphDev &g, int32_t *W, cudaStream_t s) {
     UPR_LAUNCH_CHECK();
 }
 
-void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s) {
+void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, const int32_t *hubs, int64_t n_hubs,
+                    const int64_t *noff, cudaStream_t s) {
     UPR_CUDA(cudaMemsetAsync(d_acc, 0, 2 * sizeof(uint64_t), s));
     UPR_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int32_t), s));
     k_validate_nodes<<<(unsigned)ceil_div(g.n + 1, 256), 256, 0, s>>>(g.xadj, g.vwgt, g.n, g.m, d_flags);
@@ -488,6 +586,19 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaSt
         k_validate_entries<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(
             g.xadj, g.adj, g.adjw, g.gid, g.n, g.m, (unsigned long long *)d_acc, d_flags);
         UPR_LAUNCH_CHECK();
+        // duplicates: rows up to kHubDegree by warps, hub rows by CTAs
+        const size_t shm_rows = (size_t)kDupSlots * sizeof(unsigned long long);
+        const size_t shm_hubs = (size_t)(kDupRange / 32) * sizeof(uint32_t);
+        kernel_setup((const void *)k_dup_rows, -1);
+        kernel_setup((const void *)k_dup_hubs, -1);
+        const unsigned grid = wave_grid((const void *)k_dup_rows, 512, shm_rows, ceil_div(g.m, (int64_t)kDupChunk));
+        k_dup_rows<<<grid, 512, shm_rows, s>>>(g.xadj, g.adj, g.n, g.m, d_flags);
+        UPR_LAUNCH_CHECK();
+        if (n_hubs > 0) {
+            k_dup_hubs<<<(unsigned)n_hubs, 256, shm_hubs, s>>>(hubs, g.xadj, g.adj, g.n, g.gid,
+                                                              g.ng > 1 ? noff : nullptr, d_flags);
+            UPR_LAUNCH_CHECK();
+        }
     }
 }
 

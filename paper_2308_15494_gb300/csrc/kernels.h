@@ -204,7 +204,12 @@ void pack_batch(const GraphDev &g, const int64_t *noff, int32_t *gid, int32_t *a
 // W[v][b] = omega(v, V_b) from the sparse table (inspection only).
 void sparse_to_dense(const GraphDev &g, int32_t *W, cudaStream_t s);
 // Graph checks; writes a bitmask of violations into *d_flags (see engine.cu).
-void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s);
+// Checks the CSR on the device (bits of *d_flags, hash sums in d_acc[0..1]):
+// ranges, self loops, weights, symmetry by a multiset hash, and exactly
+// (no hash) duplicate neighbours; hubs lists the n_hubs nodes of degree >
+// kHubDegree, noff the batch's node offsets (ignored for one graph).
+void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, const int32_t *hubs, int64_t n_hubs,
+                    const int64_t *noff, cudaStream_t s);
 
 // ---- select.cu: step (b) and applying M
 struct Penalty {
@@ -284,6 +289,14 @@ void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *
                          int32_t *cut, int32_t *keep, cudaStream_t s);
 // gain_only: the priority is the gain alone (a variant of Sec. 7.2), else g/c
 // for g < 0 and g*c for g >= 0 (Sec. 6.1)
+// The four buffers of a two-array radix sort (keys and values, and their alternates).
+struct SortPairs { uint64_t *k, *ka; uint32_t *v, *va; };
+// A priority key wider than 63 bits (1 + gbits + 2 cbits > 63): the proposals
+// P[0..*d_np) ordered by their 128-bit keys, two stable sorts (low word, then
+// high word); *order receives the buffer holding the order (indices into P).
+void rebalance_prio_sort_wide(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
+                              int gbits, int cbits, int gain_only, SortPairs sp, int64_t np_max, Scratch tmp,
+                              cudaStream_t s, uint32_t **order);
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                          int gbits, int cbits, int gain_only, uint64_t *keys, uint32_t *vals, int64_t np_max,
                          cudaStream_t s);

@@ -5,47 +5,63 @@
 // needs no upr_create and no cudaMalloc.  Every GPU that loads the library
 // holds this array (kNoAllocMaxK + 8 int64, about 33 KB) until the process
 // exits.
-#include <mutex>
+#include <algorithm>
 
 #include "kernels.h"
 
 namespace {
 
 constexpr int kNoAllocMaxK = 4096;
-constexpr int kMaxDevices = 64;
 
-// [0, k): block weights, [k]: cut, [k+1]: partition-range flag.
+// [0, k): block weights, [k]: cut, [k+1]: input-check flag (partition range,
+// CSR offsets, neighbour ids).
 static __device__ __align__(256) int64_t g_noalloc_scratch[kNoAllocMaxK + 8];
 
-std::mutex g_setup_mu;
-int64_t *g_scratch_addr[kMaxDevices] = {};
-
-// The device address of g_noalloc_scratch on the current device, looked up
-// once per device (host code cannot use the symbol itself as an address).
-int64_t *scratch_address(int dev) {
-    if (dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        g_scratch_addr[dev] = static_cast<int64_t *>(p);
+// The device address of g_noalloc_scratch on the current device (host code
+// cannot use the symbol itself as an address).  Looked up on every call: the
+// lookup allocates nothing, and an address cached across a cudaDeviceReset
+// could point into a module that no longer exists.
+int64_t *scratch_address() {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_scratch_addr[dev];
+    return static_cast<int64_t *>(p);
+}
+
+__device__ __forceinline__ void set_flag(int32_t flag_slot) {
+    atomicOr(reinterpret_cast<unsigned long long *>(&g_noalloc_scratch[flag_slot]), 1ull);
 }
 
 __global__ void k_part_in_range(const int32_t *__restrict__ part, int64_t n, int32_t k, int32_t flag_slot) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n && (part[v] < 0 || part[v] >= k))
-        atomicOr(reinterpret_cast<unsigned long long *>(&g_noalloc_scratch[flag_slot]), 1ull);
+    if (v < n && (part[v] < 0 || part[v] >= k)) set_flag(flag_slot);
 }
 
-bool on_device(const void *p) {
+// The CSR offsets: xadj[0] = 0, xadj[n] = m, non-decreasing.  The cut kernels
+// find an entry's node by walking xadj, so they run only after this holds.
+__global__ void k_xadj_valid(const int64_t *__restrict__ xadj, int64_t n, int64_t m, int32_t flag_slot) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v > n) return;
+    const bool bad = (v == 0 && xadj[0] != 0) || (v == n && xadj[n] != m) || (v < n && xadj[v + 1] < xadj[v]);
+    if (bad) set_flag(flag_slot);
+}
+
+// Neighbour ids in [0, n): the cut kernels read part[] at every neighbour.
+__global__ void k_adj_in_range(const int32_t *__restrict__ adj, int64_t m, int64_t n, int32_t flag_slot) {
+    bool bad = false;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        bad |= adj[e] < 0 || adj[e] >= n;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) set_flag(flag_slot);
+}
+
+// Device memory of the current device (another GPU's memory would be read
+// through peer access, which may be off).
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -54,20 +70,29 @@ extern "C" upr_status upr_cut_noalloc(const upr_graph *g, int32_t k, const int32
                                       int64_t *cut, int64_t *block_weights) {
     if (!g || !cut || g->n < 0 || g->m < 0 || g->n >= (1LL << 31) || g->m >= (1LL << 31)) return UPR_ERR_INVALID;
     if (k < 2 || k > kNoAllocMaxK) return UPR_ERR_INVALID;      // the scratch holds at most 4096 blocks
-    if (g->n > 0 && (!part || !g->xadj || !on_device(part) || !on_device(g->xadj))) return UPR_ERR_INVALID;
-    if (g->m > 0 && (!g->adjncy || !on_device(g->adjncy))) return UPR_ERR_INVALID;
-    if ((g->vwgt && !on_device(g->vwgt)) || (g->adjwgt && !on_device(g->adjwgt))) return UPR_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return UPR_ERR_CUDA;
-    int64_t *scratch = scratch_address(dev);
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return UPR_ERR_CUDA; }
+    if (g->n > 0 && (!part || !g->xadj || !on_device(part, dev) || !on_device(g->xadj, dev))) return UPR_ERR_INVALID;
+    if (g->m > 0 && (!g->adjncy || !on_device(g->adjncy, dev))) return UPR_ERR_INVALID;
+    if ((g->vwgt && !on_device(g->vwgt, dev)) || (g->adjwgt && !on_device(g->adjwgt, dev))) return UPR_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t *scratch = scratch_address();
     if (!scratch) return UPR_ERR_CUDA;
     try {
         upr::GraphDev G{g->n, g->m, k, 1, -1, g->xadj, g->adjncy, g->adjwgt, g->vwgt, nullptr, nullptr, nullptr};
-        // the flag keeps the previous call's value: clear it first
+        // the flag keeps the previous call's value: clear it first; then the
+        // partition's range and the CSR's offsets and neighbour ids, all
+        // before any kernel that indexes with them
         UPR_CUDA(cudaMemsetAsync(scratch + k + 1, 0, sizeof(int64_t), s));
         if (g->n > 0) {
             k_part_in_range<<<(unsigned)upr::ceil_div(g->n, 256), 256, 0, s>>>(part, g->n, k, k + 1);
+            UPR_LAUNCH_CHECK();
+            k_xadj_valid<<<(unsigned)upr::ceil_div(g->n + 1, 256), 256, 0, s>>>(g->xadj, g->n, g->m, k + 1);
+            UPR_LAUNCH_CHECK();
+        }
+        if (g->m > 0) {
+            const int64_t blocks = std::min<int64_t>(upr::ceil_div(g->m, 256), 4096);
+            k_adj_in_range<<<(unsigned)blocks, 256, 0, s>>>(g->adjncy, g->m, g->n, k + 1);
             UPR_LAUNCH_CHECK();
         }
         int64_t bad = 0;

@@ -417,13 +417,23 @@ __global__ void k_reb_end_batch(const int64_t *__restrict__ C, const int64_t *__
 }
 
 // Ascending key = descending priority.  Class 0 (g >= 0): (2^(gb+cb) - 1) - g*c.
-// Class 1 (g < 0): floor(|g| * 2^(2cb) / c), exact for c < 2^cb.  Equal
-// priorities give equal keys; the stable sort then keeps node order.
+// Class 1 (g < 0): 2^(gb+2cb) + floor(|g| * 2^(2cb) / c), exact for c < 2^cb.
+// Equal priorities give equal keys; the stable sort then keeps node order.
+// The key has 1 + gb + 2cb bits; up to 63 it is one word (prio_key), above
+// it the 128-bit form (prio_key_wide) is sorted as two words, low word first.
 __device__ __forceinline__ uint64_t prio_key(int64_t g, uint64_t c, int gbits, int cbits) {
     const int S = 2 * cbits;
     if (g >= 0) return ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
     const uint64_t num = ((uint64_t)(-g)) << S;
     return (1ull << (gbits + S)) | (c == 1 ? num : num / c);     // unit weights need no division
+}
+
+__device__ __forceinline__ unsigned __int128 prio_key_wide(int64_t g, uint64_t c, int gbits, int cbits) {
+    typedef unsigned __int128 u128;
+    const int S = 2 * cbits;
+    if (g >= 0) return (u128)(((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c);     // gb + cb <= 62
+    const u128 num = ((u128)(uint64_t)(-g)) << S;
+    return ((u128)1 << (gbits + S)) | (c == 1 ? num : num / (u128)c);
 }
 
 // gain_only (the variant of Sec. 7.2): the priority is the gain alone, the
@@ -439,6 +449,34 @@ __global__ void k_prio_keys(const int32_t *__restrict__ P, const int32_t *__rest
     }
 }
 
+// The two words of a wide key: the low words of the proposals in list order
+// (sorted first), then the high words in the order of that sort (A0), whose
+// stable sort completes the order.
+__global__ void k_prio_keys_lo(const int32_t *__restrict__ P, const int32_t *__restrict__ d_np,
+                               const int32_t *__restrict__ prop_gain, const int32_t *__restrict__ vwgt, int gbits,
+                               int cbits, int gain_only, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t cnt = *d_np;
+    UPR_FOR(i, cnt) {
+        const int32_t u = P[i];
+        keys[i] = (uint64_t)prio_key_wide(prop_gain[u], (vwgt && !gain_only) ? (uint64_t)vwgt[u] : 1ull, gbits, cbits);
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_prio_keys_hi(const int32_t *__restrict__ P, const uint32_t *__restrict__ A0,
+                               const int32_t *__restrict__ d_np, const int32_t *__restrict__ prop_gain,
+                               const int32_t *__restrict__ vwgt, int gbits, int cbits, int gain_only,
+                               uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t cnt = *d_np;
+    UPR_FOR(j, cnt) {
+        const uint32_t i = A0[j];
+        const int32_t u = P[i];
+        keys[j] = (uint64_t)(prio_key_wide(prop_gain[u], (vwgt && !gain_only) ? (uint64_t)vwgt[u] : 1ull, gbits,
+                                           cbits) >> 64);
+        vals[j] = i;
+    }
+}
+
 // ---- prefilter of the proposals.  A source keeps the minimal prefix of its
 // proposals (priority order) that covers its excess; that prefix is usually a
 // few percent of them.  A coarse bin, non-decreasing in the key, splits each
@@ -447,13 +485,17 @@ __global__ void k_prio_keys(const int32_t *__restrict__ P, const int32_t *__rest
 // above it is, so only the proposals up to that bin need the exact ordering.
 // Keeping them (in their order) and dropping the rest leaves every kept
 // proposal with the same weight before it in its source's order.
-__device__ __forceinline__ int prio_bin(uint64_t key, int gbits, int cbits) {
-    const uint64_t top = 1ull << (gbits + 2 * cbits);
-    if (key < top) {      // g >= 0: g*c from 127 down, larger values share bin 0
-        const uint64_t v = ((1ull << (gbits + cbits)) - 1ull) - key;
+// The bin of a proposal of gain g and weight c (c = 1 for the gain-only
+// priority), from g and c directly so that it needs no key of any width.  It
+// equals the bin of the key: class 0 keys bin by g*c (127 - g*c, larger values
+// all in bin 0), class 1 keys by floor(|g| * 2^cb / c), the key's class-1
+// part shifted right by cb (128 + that value, larger values all in bin 255).
+__device__ __forceinline__ int prio_bin(int64_t g, uint64_t c, int cbits) {
+    if (g >= 0) {
+        const uint64_t v = (uint64_t)g * c;
         return 127 - (int)(v < 127ull ? v : 127ull);
     }
-    const uint64_t r = (key - top) >> cbits;      // about |g| * 2^cb / c
+    const uint64_t r = (((uint64_t)(-g)) << cbits) / c;     // |g| < 2^31, cb <= 31
     return 128 + (int)(r < 127ull ? r : 127ull);
 }
 
@@ -479,8 +521,7 @@ __global__ void __launch_bounds__(256) k_prio_hist(const int32_t *__restrict__ l
         if (flags && !flags[i]) continue;
         const int32_t u = list[i];
         const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
-        const uint32_t key = (uint32_t)part[u] * kPrioBins +
-                             prio_bin(prio_key(prop_gain[u], gain_only ? 1ull : c, gbits, cbits), gbits, cbits);
+        const uint32_t key = (uint32_t)part[u] * kPrioBins + prio_bin(prop_gain[u], gain_only ? 1ull : c, cbits);
         uint32_t h = (key * 0x9E3779B1u) >> 21;          // 11 bits: kHistSlots
         bool done = false;
         for (int probe = 0; probe < 32 && !done; probe++) {
@@ -546,8 +587,7 @@ __global__ void k_prio_keep(const int32_t *__restrict__ list, const int32_t *__r
         if (!flags || flags[i]) {
             const int32_t u = list[i];
             const uint64_t c = vwgt ? (uint64_t)vwgt[u] : 1ull;
-            k = prio_bin(prio_key(prop_gain[u], gain_only ? 1ull : c, gbits, cbits), gbits, cbits) <= cut[part[u]]
-                    ? 1 : 0;
+            k = prio_bin(prop_gain[u], gain_only ? 1ull : c, cbits) <= cut[part[u]] ? 1 : 0;
         }
         keep[i] = k;
     }
@@ -766,6 +806,22 @@ void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_n
     if (np_max <= 0) return;
     k_prio_keys<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, gbits, cbits, gain_only, keys, vals);
     UPR_LAUNCH_CHECK();
+}
+
+void rebalance_prio_sort_wide(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
+                              int gbits, int cbits, int gain_only, SortPairs sp, int64_t np_max, Scratch tmp,
+                              cudaStream_t s, uint32_t **order) {
+    if (np_max <= 0) { *order = sp.v; return; }
+    const Count cnt{d_np, np_max};
+    k_prio_keys_lo<<<grid_for(np_max), 256, 0, s>>>(P, d_np, prop_gain, g.vwgt, gbits, cbits, gain_only, sp.k, sp.v);
+    UPR_LAUNCH_CHECK();
+    // 64 bits = 8 passes, an even number: the result is back in (k, v)
+    radix_sort_pairs(sp.k, sp.v, sp.ka, sp.va, cnt, 64, tmp, s);
+    k_prio_keys_hi<<<grid_for(np_max), 256, 0, s>>>(P, sp.v, d_np, prop_gain, g.vwgt, gbits, cbits, gain_only, sp.ka,
+                                                    sp.va);
+    UPR_LAUNCH_CHECK();
+    const bool alt = radix_sort_pairs(sp.ka, sp.va, sp.k, sp.v, cnt, 1 + gbits + 2 * cbits - 64, tmp, s);
+    *order = alt ? sp.v : sp.va;
 }
 
 void rebalance_block_keys(const int32_t *P, const uint32_t *A, const int32_t *S, const int32_t *d_cnt,

@@ -628,7 +628,8 @@ def test_given_tau_equals_schedule_tau(num, den):
 
 
 def _expected_kinds(cuts, rounds):
-    """The Sec. 6.2 rule restated on the cuts the rounds produced."""
+    """Dynamic activation (Sec. 4.4, last paragraph; Sec. 7.2 leaves it out of
+    the final configuration) restated on the cuts the rounds produced."""
     kinds, unc_rest, switched = [], False, False
     for i in range(1, rounds + 1):
         if i == 1 or (rounds >= 3 and i == rounds) or (i >= 3 and (not unc_rest or switched)):
@@ -730,13 +731,22 @@ def test_limited_round_selection_bruteforce(w, factor):
     assert {int(v): (int(t), int(s)) for v, t, s in zip(Mn, Mt, Ms)} == expect
 
 
+def _frame_unconstrained(rounds):
+    """Unconstrained rounds of the final configuration's frame (Sec. 4.4 with
+    Sec. 7.2's split of ten rounds into eight unconstrained and two
+    constrained): R - 2 for R >= 3, one for R = 2, none for R = 1."""
+    return rounds - 2 if rounds >= 3 else 1 if rounds == 2 else 0
+
+
 def _expected_variant_kinds(cuts, rounds, schedule, Lmax):
-    """Sec. 7.2 variants: their kind until a round improves the cut by less
-    than 0.002 of it, then constrained; the last round constrained."""
+    """Sec. 7.2 variants in the final configuration's frame: their kind in the
+    first U rounds until a round improves the cut by less than 0.002 of it,
+    constrained from then on and in every round after the first U."""
     kinds, limits, switched = [], [], False
-    D = max(rounds - 2, 1)
+    U = _frame_unconstrained(rounds)
+    D = max(U - 1, 1)
     for i in range(1, rounds + 1):
-        if (rounds >= 2 and i == rounds) or switched:
+        if i > U or switched:
             kind, lim = oracle.CONSTRAINED, None
         else:
             kind = {3: oracle.CONSTANT_TAU, 4: oracle.NO_PENALTY, 5: oracle.LIMITED}[schedule]
@@ -747,6 +757,104 @@ def _expected_variant_kinds(cuts, rounds, schedule, Lmax):
         if kind != oracle.CONSTRAINED and Fraction(imp, max(before, 1)) < Fraction(2, 1000):
             switched = True
     return kinds, limits
+
+
+def _expected_final_kinds(cuts, rounds):
+    """The paper's final configuration (Sec. 4.4, Sec. 7.2) restated on the
+    cuts the rounds produced: unconstrained rounds 1..U, constrained from the
+    round after one whose improvement is below 0.002 of the cut before it,
+    and constrained after round U."""
+    kinds, switched = [], False
+    U = _frame_unconstrained(rounds)
+    for i in range(1, rounds + 1):
+        kind = oracle.CONSTRAINED if (i > U or switched) else oracle.UNCONSTRAINED
+        kinds.append(kind)
+        imp, before = int(cuts[i - 1] - cuts[i]), int(cuts[i - 1])
+        if kind == oracle.UNCONSTRAINED and Fraction(imp, max(before, 1)) < Fraction(2, 1000):
+            switched = True
+    return kinds
+
+
+# graphs on which unconstrained rounds keep improving for a while (tight
+# balance, many boundary nodes), next to the small hand-picked ones
+FINAL_CASES = [dict(seed=41, n=600, avg_deg=6, k=4), dict(seed=42, n=800, avg_deg=8, k=8, hubs=2),
+               dict(seed=43, n=500, avg_deg=5, k=6, weighted=True, max_vw=12),
+               dict(seed=44, n=1000, avg_deg=10, k=16, hubs=1)]
+
+
+def _final_graphs():
+    out = [small(i) for i in range(len(SMALL))]
+    for spec in FINAL_CASES:
+        g = synth.random_small(**spec)
+        g.eps = 0.01
+        out.append(g)
+    return out
+
+
+@pytest.mark.parametrize("rounds", [1, 2, 3, 6, 10])
+def test_final_configuration_follows_the_rule(rounds):
+    """Schedule 6, the paper's final configuration: the kinds restated on the
+    per-round cuts, the cut never worse, the result balanced; across the
+    graphs both a switch below 0.002 and constrained closing rounds reached
+    without a switch occur (so a switch threshold of 0.02, or a frame without
+    the closing constrained rounds, changes some kind sequence)."""
+    seen_switch = seen_plain = False
+    for w in _final_graphs():
+        rc, p, cut, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, 6)
+        assert rc == oracle.OK
+        expect = _expected_final_kinds(cuts, rounds)
+        assert list(kinds) == expect
+        assert cut == cuts[-1] == oracle.cut(w, p)[0]
+        assert all(cuts[j + 1] <= cuts[j] for j in range(rounds))
+        assert np.all(brute.block_weights(w, p) <= brute.lmax(w))
+        U = _frame_unconstrained(rounds)
+        assert all(k == oracle.CONSTRAINED for k in kinds[U:])
+        assert rounds == 1 or kinds[0] == oracle.UNCONSTRAINED
+        if U >= 2 and oracle.CONSTRAINED in list(kinds[:U]):
+            seen_switch = True
+        if U >= 2 and oracle.CONSTRAINED not in list(kinds[:U]):
+            seen_plain = True
+        # an improvement in [0.002, 0.02) of the cut by an unconstrained round
+        # that is followed by another unconstrained round pins the threshold
+    if rounds >= 6:
+        assert seen_switch and seen_plain
+
+
+def test_final_configuration_threshold_is_two_per_mille():
+    """Some unconstrained round that is followed by an unconstrained round
+    improves the cut by at least 0.002 but less than 0.02 of it: a switch
+    at 0.02 would have made the next round constrained."""
+    found = False
+    for w in _final_graphs():
+        rc, p, cut, cuts, kinds = oracle.refine_schedule(w, w.part, 10, 6)
+        for i in range(1, 10):
+            if kinds[i - 1] == oracle.UNCONSTRAINED and kinds[i] == oracle.UNCONSTRAINED:
+                f = Fraction(int(cuts[i - 1] - cuts[i]), int(cuts[i - 1]))
+                found = found or Fraction(2, 1000) <= f < Fraction(2, 100)
+    assert found
+
+
+@pytest.mark.parametrize("rounds", [2, 3, 6, 10])
+def test_final_configuration_replays_round_by_round(rounds):
+    """Schedule 6's rounds equal single rounds of the kind it reports: the
+    unconstrained round i with tau_i of a schedule over the U unconstrained
+    rounds (tau_1 in round 1, 1 in round U), constrained rounds; the cut
+    after every round and the final partition."""
+    U = _frame_unconstrained(rounds)
+    for w in _final_graphs():
+        rc, p, cut, cuts, kinds = oracle.refine_schedule(w, w.part, rounds, 6)
+        P = np.array(w.part, np.int32)
+        for j, code in enumerate(kinds, start=1):
+            if code == oracle.CONSTRAINED:
+                rc, P, c, _ = oracle.run_round(w, P, 1, 1, kind=("constrained",))
+            else:
+                assert code == oracle.UNCONSTRAINED and j <= U
+                rc, P, c, tr = oracle.run_round(w, P, j, U)
+                # tau_j of the U rounds: tau_1 = 1/4 first, 1 in round U
+                tau = Fraction(1, 4) + Fraction(3, 4) * Fraction(j - 1, max(U - 1, 1))
+                assert tr["factor"][0 - oracle.SLOT_LO] == int(tau * (1 << 20))
+            assert rc == oracle.OK and c == cuts[j], (j,)
+        assert np.array_equal(P, p)
 
 
 @pytest.mark.parametrize("schedule", [3, 4, 5])
@@ -983,11 +1091,11 @@ def test_guard_changes_fully_unconstrained_refinement():
     for seed in (41, 44):
         w = synth.random_small(seed, 600, 8, 4, weighted=seed % 2 == 0)
         w.eps = 0.01
-        a = oracle.refine_schedule(w, w.part, 5, 4)
-        b = oracle.refine_schedule(w, w.part, 5, 4, p=oracle.params(lock_rebalanced=1))
+        a = oracle.refine_schedule(w, w.part, 6, 4)
+        b = oracle.refine_schedule(w, w.part, 6, 4, p=oracle.params(lock_rebalanced=1))
         differ += not np.array_equal(a[1], b[1])
-        # replay rounds 1..4 (fully unconstrained, no switch here) then the constrained last round
-        assert list(b[4]) == [oracle.NO_PENALTY] * 4 + [oracle.CONSTRAINED]
+        # replay rounds 1..4 (fully unconstrained, no switch here) before the two constrained closing rounds
+        assert list(b[4]) == [oracle.NO_PENALTY] * 4 + [oracle.CONSTRAINED] * 2
         P, locked = np.array(w.part, np.int32), np.zeros(w.n, np.int8)
         for r in range(4):
             rc, P, c, locked, _ = oracle.round_guard(w, P, 1, 1, locked, limit=2 ** 62)

@@ -222,6 +222,104 @@ def test_invalid_inputs_rejected(upr):
         upr.upr_create(w.xadj, w.adj, 1, 0.03)            # k < 2
 
 
+def _with_duplicate(xadj, adj, v, u):
+    """The CSR with the pair {v, u} listed a second time in both rows (still
+    symmetric, so only the duplicate check can refuse it)."""
+    rows = [list(adj[xadj[i]:xadj[i + 1]]) for i in range(len(xadj) - 1)]
+    rows[v].append(u)
+    rows[u].append(v)
+    x = np.zeros(len(rows) + 1, np.int64)
+    x[1:] = np.cumsum([len(r) for r in rows])
+    return x, np.array([a for r in rows for a in r], np.int32)
+
+
+def test_duplicate_entries_rejected(upr):
+    """E is a set of pairs (Sec. 2): a row that lists a neighbour twice is
+    refused with UPR_ERR_INVALID, in a short row, a row of a few hundred
+    entries (the shared-memory hash set) and a hub row of more than 4096
+    entries (the bitmap pass), one graph and in a batch; the same graphs
+    without the duplicate are accepted."""
+    w = synth.random_small(44, 300, 6.0, 4)
+    v = 7
+    u = int(w.adj[w.xadj[v]])
+    x, a = _with_duplicate(w.xadj, w.adj, v, u)
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_create(x, a, w.k, w.eps)
+    assert e.value.status == upr.UPR_ERR_INVALID
+    # a row of a few hundred entries: node 0 joined to every third node
+    n = 900
+    src = np.array([0] * (n // 3 - 1), np.int32)
+    dst = np.arange(3, n, 3, dtype=np.int32)[:len(src)]
+    ring_s = np.arange(1, n - 1, dtype=np.int32)
+    xadj, adj = synth.csr_from_edges(n, np.concatenate([src, ring_s]), np.concatenate([dst, ring_s + 1]))
+    upr.upr_destroy(upr.upr_create(xadj, adj, 4, 0.03))
+    x, a = _with_duplicate(xadj, adj, 0, 3)
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_create(x, a, 4, 0.03)
+    assert e.value.status == upr.UPR_ERR_INVALID
+    # a hub: node 0 joined to all 5999 others, plus a ring
+    n = 6000
+    src = np.concatenate([np.zeros(n - 1, np.int32), np.arange(1, n - 1, dtype=np.int32)])
+    dst = np.concatenate([np.arange(1, n, dtype=np.int32), np.arange(2, n, dtype=np.int32)])
+    xadj, adj = synth.csr_from_edges(n, src, dst)
+    assert xadj[1] - xadj[0] > 4096
+    upr.upr_destroy(upr.upr_create(xadj, adj, 8, 0.03))
+    x, a = _with_duplicate(xadj, adj, 0, 4321)
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_create(x, a, 8, 0.03)
+    assert e.value.status == upr.UPR_ERR_INVALID
+    # in a batch: one graph with a duplicate makes the call fail
+    ws = [synth.random_small(45 + i, 200, 5.0, 4) for i in range(3)]
+    xd, ad = _with_duplicate(ws[1].xadj, ws[1].adj, 5, int(ws[1].adj[ws[1].xadj[5]]))
+    graphs = [(g.xadj, g.adj, None, None) for g in ws]
+    graphs[1] = (xd, ad, None, None)
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_batch_create(graphs, 4, 0.03)
+    assert e.value.status == upr.UPR_ERR_INVALID
+
+
+@pytest.mark.parametrize("seed", [71, 72, 73])
+def test_wide_rebalancing_key_same_results(upr, seed):
+    """Node weights near 2^24 with heavy edges: the exact rebalancing key
+    (class bit, g*c or floor(|g| 2^(2 cb) / c)) needs 1 + gb + 2 cb > 63 bits
+    and is sorted as two words.  Round traces (with the rebalancing sequence
+    and its sub-rounds), a repair of an imbalanced input and whole
+    refinements equal the oracle's, for the g/c priority and the gain-only
+    variant."""
+    w = synth.random_small(seed, 1500, 6.0, 8, max_vw=(1 << 24) - 1, max_ew=1 << 20)
+    w.eps = 0.01
+    wI = np.add.reduceat(w.adjw.astype(np.int64), w.xadj[:-1]) if w.m else np.zeros(1)
+    gb, cb = int(wI.max()).bit_length(), int(w.vwgt.max()).bit_length()
+    assert 1 + gb + 2 * cb > 63 and wI.max() < 2 ** 31
+    ctx = upr.create_from_workload(w)
+    for r, R in ((1, 4), (3, 4)):
+        rc, p, t = upr.upr_debug_round(ctx, w.part, r, R)
+        rc0, p0, c0, o = oracle.run_round(w, w.part, r, R)
+        assert rc == rc0
+        _compare_traces(t, o)
+        assert np.array_equal(p, p0)
+    for gp in (0, 1):
+        prm = upr.upr_params_default()
+        prm.gain_priority = gp
+        ctx = upr.create_from_workload(w, params=prm)
+        p = w.part.copy()
+        st = upr.upr_refine(ctx, p, 4)
+        rc0, p0, c0, _ = oracle.refine(w, w.part, rounds=4, p=oracle.params(gain_priority=gp))
+        assert np.array_equal(p, p0) and st.cut_out == c0, gp
+    # an imbalanced input: everything of block 0 moved to block 1 first
+    bad = w.part.copy()
+    bad[bad == 0] = 1
+    ctx = upr.create_from_workload(w)
+    rc0, p0, c0, _ = oracle.refine(w, bad, rounds=2)
+    p = bad.copy()
+    if rc0 == oracle.OK:
+        st = upr.upr_refine(ctx, p, 2)
+        assert st.repaired_input == 1 and np.array_equal(p, p0) and st.cut_out == c0
+    else:
+        with pytest.raises(upr.UprError):
+            upr.upr_refine(ctx, p, 2)
+
+
 def test_split_resume_and_seed_independence(upr):
     w = synth.plain_tiny(3)
     full = upr.create_from_workload(w)
@@ -361,15 +459,17 @@ def test_tuned_schedules_shared_between_contexts(upr):
     assert (s2.select_lanes, s2.propose_lanes) == (s1.select_lanes, s1.propose_lanes)
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("schedule", [6, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("name", ["small4_hubs", "small6_wide", "k11_odd", "chung_lu_1k", "rmat_s12_k64",
                                   "heavy_weights", "isolated"])
 def test_round_driver_same_results(upr, name, schedule):
-    """The round driver of Sec. 6.2 (1: constrained / tau = 1/2 decision,
-    unconstrained rounds until the improvement drops below 0.002 of the cut,
-    constrained last round; 2: constrained rounds only) and the variants of
-    Sec. 7.2 (3: constant tau = 1/2, 4: fully unconstrained, 5: limited
-    imbalance 2 -> 1.1) equal the oracle's."""
+    """The round driver of Sec. 4.4 / 6.2 (6: the paper's final
+    configuration, unconstrained rounds with tau annealed to 1 and the
+    switch below 0.002 of the cut, two closing constrained rounds; 1: dynamic
+    activation, the constrained / tau = 1/2 decision of the first two rounds;
+    2: constrained rounds only) and the variants of Sec. 7.2 in the final
+    configuration's frame (3: constant tau = 1/2, 4: fully unconstrained, 5:
+    limited imbalance 2 -> 1.1) equal the oracle's."""
     w = CASES[name]()
     rounds = 7
     op = oracle.params(tau1=(1, 2)) if schedule == 3 else None
@@ -472,12 +572,15 @@ def test_label_propagation_on_hashed_rows(upr, table):
         assert np.array_equal(p, p0) and st.cut_out == c0
 
 
-def test_label_propagation_with_the_round_driver(upr):
+@pytest.mark.parametrize("schedule", [6, 1])
+def test_label_propagation_with_the_round_driver(upr, schedule):
+    """Label propagation (Sec. 5) before the FM rounds of the paper's final
+    configuration (6) and of dynamic activation (1)."""
     w = CASES["chung_lu_1k"]()
-    rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 6, 1, p=oracle.params(lp_rounds=5))
+    rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 6, schedule, p=oracle.params(lp_rounds=5))
     prm = upr.upr_params_default()
     prm.lp_rounds = 5
-    prm.schedule = 1
+    prm.schedule = schedule
     ctx = upr.create_from_workload(w, params=prm)
     p = w.part.copy()
     st = upr.upr_refine(ctx, p, 6)
@@ -508,7 +611,7 @@ def test_oscillation_guard_same_results(upr, seed):
 def test_round_driver_on_a_tight_case(upr):
     w = synth.random_small(11, 4000, 8, 16, weighted=True, max_vw=20)
     w.eps = 0.005
-    for schedule in (1, 2, 4, 5):
+    for schedule in (6, 1, 2, 4, 5):
         rc, p0, c0, cuts, kinds = oracle.refine_schedule(w, w.part, 6, schedule)
         prm = upr.upr_params_default()
         prm.schedule = schedule
@@ -518,9 +621,10 @@ def test_round_driver_on_a_tight_case(upr):
         assert np.array_equal(p, p0) and st.cut_out == c0
 
 
-def test_round_driver_needs_one_graph_and_a_whole_schedule(upr):
+@pytest.mark.parametrize("schedule", [6, 1])
+def test_round_driver_needs_one_graph_and_a_whole_schedule(upr, schedule):
     prm = upr.upr_params_default()
-    prm.schedule = 1
+    prm.schedule = schedule
     ws = [synth.random_small(60 + i, 100, 4, 4) for i in range(3)]
     ctx = upr.create_batch_from_workloads(ws, params=prm)
     with pytest.raises(upr.UprError):
