@@ -129,6 +129,21 @@ def code_digest(path: str) -> str:
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
+def _dominant_kernel(profile: str):
+    """The first row of a committed ncu launch-list summary (kernels by total
+    device time in one step): name, launches and share of the step's kernel
+    time."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    m = re.search(r"^\| `([^`]+)` \| (\d+) \| (\d+) \| ([\d.]+)%", txt, flags=re.M)
+    if not m:
+        return None
+    return {"kernel": m.group(1), "launches": int(m.group(2)), "us_total": int(m.group(3)),
+            "share": float(m.group(4)) / 100, "source": f"profiles/{profile}"}
+
+
 def _traffic(kernel_src: str, profile: str):
     """Per-launch DRAM bytes of the dominant kernel from a committed ncu summary,
     only if it was taken on the current kernel source (same code digest)."""
@@ -214,64 +229,46 @@ def cpu_baseline(w):
 
 
 def batched_leg(args, upr, rank, ws, local, graphs):
-    """The 4096-graph Chung-Lu batch: graphs grouped by k, one batch context per
-    group on its own stream (the groups run concurrently from host threads),
-    every graph refined for its 4 rounds per step; against the plain
-    one-graph-per-call form (upr_refine per graph, graph resident) on a sample
-    of the same graphs, whose cuts must be identical."""
-    import concurrent.futures as cf
+    """The 4096-graph Chung-Lu batch refined by one context
+    (upr_batch_create_mixed: the graphs of each k form one batch, the batches
+    run concurrently, and from the second call on each batch's rounds are one
+    CUDA graph launch, params.graphs = 2), every graph for its 4 rounds per
+    step; against the plain one-graph-per-call form (upr_refine per graph,
+    graph resident) on a sample of the same graphs, whose cuts must be
+    identical; end to end from pinned host arrays."""
     import torch
-    by_k = {}
-    for i, w in enumerate(graphs):
-        by_k.setdefault(w.k, []).append(i)
     rounds = graphs[0].rounds
-    groups = []
-    for k, idx in sorted(by_k.items()):
-        st = torch.cuda.Stream()
-        ctx = upr.upr_batch_create([(graphs[i].xadj, graphs[i].adj, graphs[i].vwgt, graphs[i].adjw) for i in idx], k,
-                                   [graphs[i].eps for i in idx], stream=ctypes.c_void_p(st.cuda_stream))
-        init = torch.from_numpy(np.concatenate([graphs[i].part for i in idx]).astype(np.int32)).cuda()
-        groups.append({"k": k, "idx": idx, "stream": st, "ctx": ctx, "init": init, "part": torch.empty_like(init)})
-    torch.cuda.synchronize()
-    pool = cf.ThreadPoolExecutor(len(groups), initializer=torch.cuda.set_device, initargs=(local,))
-
-    def run_group(gr):
-        with torch.cuda.stream(gr["stream"]):
-            gr["part"].copy_(gr["init"])
-        return upr.upr_batch_refine(gr["ctx"], gr["part"], rounds)
+    ng = len(graphs)
+    ks = [w.k for w in graphs]
+    prm = upr.upr_params_default()
+    prm.graphs = 2
+    main = torch.cuda.current_stream()
+    ctx = upr.upr_batch_create_mixed([(w.xadj, w.adj, w.vwgt, w.adjw) for w in graphs], ks,
+                                     [w.eps for w in graphs], params=prm)
+    init = torch.from_numpy(np.concatenate([w.part for w in graphs]).astype(np.int32)).cuda()
+    part = torch.empty_like(init)
 
     def step():
-        return list(pool.map(run_group, groups))
+        part.copy_(init)
+        return upr.upr_batch_refine(ctx, part, rounds)
 
-    for _ in range(max(1, min(args.warmup, 2))):
+    for _ in range(max(2, min(args.warmup, 3))):        # the second call builds the batches' step graphs
         res = step()
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 5))
-    main = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    ends = [torch.cuda.Event() for _ in groups]
     torch.cuda.synchronize()
     e0.record(main)
-    for gr in groups:
-        gr["stream"].wait_event(e0)
     for _ in range(steps):
         res = step()
-    for gr, ev in zip(groups, ends):
-        ev.record(gr["stream"])
-        main.wait_event(ev)
     e1.record(main)
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3 / steps
-    ng = len(graphs)
-    cut_b = np.zeros(ng, np.int64)
-    stat_b = np.zeros(ng, np.int32)
-    launches = 0
-    for gr, (status, cin, cout, st) in zip(groups, res):
-        cut_b[gr["idx"]] = cout
-        stat_b[gr["idx"]] = status
-        launches += st.kernel_launches
+    stat_b, _, cut_b, st_b = res
+    cut_b = np.asarray(cut_b).copy()
     E = sum(w.m // 2 for w in graphs)
+    n_batches = len(set(ks))
 
     # the plain form on a sample: one context and one upr_refine per graph
     sample = list(range(0, ng, max(1, ng // args.plain_sample)))[: args.plain_sample]
@@ -296,36 +293,58 @@ def batched_leg(args, upr, rank, ws, local, graphs):
     identical = all(cut_p[i] == cut_b[i] for i in sample)
     del plain, work
 
-    # end to end: upload from host arrays, refine, read back (one step)
-    t0 = time.perf_counter()
-    outs = []
-    for k, idx in sorted(by_k.items()):
-        ctx = upr.upr_batch_create([(graphs[i].xadj, graphs[i].adj, graphs[i].vwgt, graphs[i].adjw) for i in idx],
-                                   k, [graphs[i].eps for i in idx])
-        part = np.concatenate([graphs[i].part for i in idx]).astype(np.int32)
-        outs.append(upr.upr_batch_refine(ctx, part, rounds))
-        upr.upr_destroy(ctx)
+    # end to end from pinned host arrays: one context created (upload and
+    # checks), refined, partition read back
+    def _pinned_views(arrays):
+        # one pinned buffer per array kind, one view per graph
+        buf = torch.from_numpy(np.concatenate(arrays)).pin_memory().numpy()
+        ends = np.cumsum([len(a) for a in arrays])
+        return [buf[e - len(a):e] for e, a in zip(ends, arrays)]
+
+    xs = _pinned_views([w.xadj for w in graphs])
+    adjs = _pinned_views([w.adj for w in graphs])
+    assert all(w.vwgt is None and w.adjw is None for w in graphs)       # unit weights
+    pinned = [(x, a, None, None) for x, a in zip(xs, adjs)]
+    part_h = torch.from_numpy(np.concatenate([w.part for w in graphs]).astype(np.int32)).pin_memory().numpy()
+    work_h = torch.empty(len(part_h), dtype=torch.int32).pin_memory().numpy()
+    prm1 = upr.upr_params_default()
+    prm1.graphs = 2
+
+    def e2e_step():
+        c = upr.upr_batch_create_mixed(pinned, ks, [w.eps for w in graphs], params=prm1)
+        work_h[:] = part_h
+        out = upr.upr_batch_refine(c, work_h, rounds)
+        upr.upr_destroy(c)
+        return out
+
+    e2e_step()
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    h2d = sum(w.xadj.nbytes + w.adj.nbytes + w.part.nbytes for w in graphs)
-    d2h = sum(w.part.nbytes for w in graphs)
-    for gr in groups:
-        upr.upr_destroy(gr["ctx"])
-    pool.shutdown()
+    t0 = time.perf_counter()
+    e2e_steps = 2
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(sum(x.nbytes for x in t if x is not None) for t in pinned) + part_h.nbytes
+    d2h = part_h.nbytes
+    upr.upr_destroy(ctx)
     return {
         "workload": f"{ng} Chung-Lu graphs, n log-uniform in [2^10, 2^16], avg degree U[4,32], exponent U[2.0,2.8], "
-                    f"k from {{2,4,8,16,32}}, eps 0.03, unit weights, {rounds} rounds; grouped by k into "
-                    f"{len(groups)} batch contexts on concurrent streams",
+                    f"k from {{2,4,8,16,32}}, eps 0.03, unit weights, {rounds} rounds; one context "
+                    f"(upr_batch_create_mixed: {n_batches} batches by k, run concurrently)",
         "graphs": ng, "nodes": int(sum(w.n for w in graphs)), "edges": int(E),
         "graphs_per_s": ng / t_batch, "edges_per_s": rounds * E / t_batch, "ms_per_step": t_batch * 1e3,
-        "steps": steps, "gpu_launches_per_step": int(launches),
+        "steps": steps, "gpu_launches_per_step": int(st_b.kernel_launches),
+        "graph_launches_per_step": n_batches if st_b.rebalance_graphs == n_batches * rounds else None,
+        "rounds_in_graphs_per_step": int(st_b.rebalance_graphs),
         "infeasible_graphs": int((stat_b != 0).sum()),
         "plain": {"form": "one upr_refine per graph, graph resident on the device", "graphs": len(sample),
                   "graphs_per_s": len(sample) / t_plain, "ms_per_graph": t_plain * 1e3 / len(sample)},
         "speedup_vs_plain": (ng / t_batch) / (len(sample) / t_plain),
         "identical_cuts_on_sample": bool(identical),
         "e2e": {"graphs_per_s": ng / t_e2e, "ms": t_e2e * 1e3, "h2d_bytes": int(h2d), "d2h_bytes": int(d2h),
-                "includes": "batch creation from host arrays, refinement, partition read-back"},
+                "includes": "context creation from pinned host arrays (upload, checks), refinement, partition "
+                            "read-back"},
         "_cuts": cut_b,
     }
 
@@ -556,8 +575,13 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     if args.profile:
         if rank == 0:
+            st = stats[-1]
             print(json.dumps({"profile": True, "ms_per_step": ms / args.steps,
-                              "launches_per_step": stats[-1].kernel_launches}))
+                              "launches_per_step": st.kernel_launches,
+                              "rebalance_graph_rounds": st.rebalance_graphs, "subrounds": st.subrounds,
+                              "cut_out": st.cut_out,
+                              "phases_ms": {"gain_table": st.ms_gain_table, "select": st.ms_select,
+                                            "rebalance": st.ms_rebalance, "sequence": st.ms_sequence}}))
         return 0
     ms = allreduce_max(ms, ws)
     ms_step = ms / args.steps
@@ -575,6 +599,27 @@ def run_gpu(args):
                 "frac": achieved / peak, "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": achieved / HBM_NOMINAL_GBS,
                 "bytes_per_launch": bytes_build, "ms_per_launch": t_build * 1e3,
                 "traffic": _traffic("paper_2308_15494_gb300/csrc/graph.cu", "gain_table_rmat_s22_k64.md")}
+
+    # the whole step against the same peak: the rounds' algorithmic bytes
+    # (SURVEY's per-round formula, counted by the library) over the call's
+    # device time, and the same per round
+    s_last = stats[-1]
+    step_bytes = s_last.bytes_algorithmic
+    step_ms = statistics.median(x.ms_device for x in stats)
+    roofline["step"] = {"bytes_algorithmic": step_bytes, "ms_device": step_ms,
+                        "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
+                        "frac": step_bytes / (step_ms / 1e3) / 1e9 / peak,
+                        "seq_degree_sum": s_last.seq_degree_sum,
+                        "gain_table_builds": s_last.gain_table_builds,
+                        "kernel_launches": s_last.kernel_launches}
+    roofline["per_round"] = {"rounds": w.rounds, "bytes": step_bytes / w.rounds, "ms": step_ms / w.rounds,
+                             "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
+                             "frac": step_bytes / (step_ms / 1e3) / 1e9 / peak,
+                             "phases_ms": {"gain_table": s_last.ms_gain_table / w.rounds,
+                                           "select": s_last.ms_select / w.rounds,
+                                           "rebalance": s_last.ms_rebalance / w.rounds,
+                                           "sequence": s_last.ms_sequence / w.rounds}}
+    roofline["dominant_kernel_by_time"] = _dominant_kernel("launches_rmat_s22_k64.md")
 
     # end to end through the C ABI from pinned host buffers
     pinned = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

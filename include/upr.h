@@ -104,8 +104,12 @@ typedef struct {
     int32_t graphs;              /* 1: once the proposal schedule is settled, each round's
                                     rebalancing loop runs as one CUDA graph launch (a while
                                     node over one sub-round, the stop test on the device);
-                                    0: the host launches every sub-round and reads its stop
-                                    flag.  Results never depend on it. 1                     */
+                                    2: also, from a binding's second call on, all rounds
+                                    of a call run as one graph launch (schedule 0, no
+                                    label propagation, dense table; round 1's table build
+                                    precedes the graph; the per-phase times of the stats
+                                    are then 0); 0: the host launches every sub-round and
+                                    reads its stop flag.  Results never depend on it. 1    */
     int32_t schedule;            /* round driver (Sec. 4.4, Sec. 6.2): 0 every round
                                     unconstrained with the tau schedule.  6 the paper's
                                     final configuration: the first U rounds unconstrained
@@ -176,6 +180,15 @@ typedef struct {
     int32_t rebalance_graphs;    /* rounds whose rebalancing loop ran as one graph launch */
     int32_t constrained_rounds;  /* constrained rounds (schedules 1-6)                   */
     int32_t lp_rounds;           /* label propagation rounds kept (Sec. 5)               */
+    int32_t lp_table_builds;     /* full gain-table builds of label propagation (also in
+                                    gain_table_builds)                                  */
+    int64_t seq_degree_sum;      /* sum over rounds of the degrees of the nodes of the
+                                    move sequence I (the adjacency its exact gains read)  */
+    int64_t bytes_algorithmic;   /* the rounds' algorithmic DRAM bytes: every full table
+                                    build, per round one read of the table (dense n*k*4
+                                    or the hashed rows' slots * 8) and 16 bytes per node,
+                                    16 bytes per adjacency entry of a node of I, 48
+                                    bytes per candidate, move and rebalancing move       */
 } upr_stats;
 
 /* Fills *p with the defaults documented in upr_params. */
@@ -263,6 +276,22 @@ upr_status upr_cut_noalloc(const upr_graph *g, int32_t k, const int32_t *part, v
  * CSR makes the whole call fail). */
 upr_status upr_batch_create(const upr_graph *graphs, int32_t n_graphs, int32_t k, const double *eps,
                             const upr_params *params, upr_ctx **out);
+
+/* Creates one context for n_graphs graphs whose block counts may differ:
+ * k[i] (2 <= k[i] <= 4096) is graph i's k, eps[i] its imbalance.  A row of
+ * the gain table keeps exactly k columns, so the graphs with the same k form
+ * one batch (as upr_batch_create) with its own stream, created with params
+ * (params.stream is the caller's stream); upr_batch_refine refines the
+ * batches concurrently and returns every graph's result in the caller's
+ * graph order, each equal to upr_refine on that graph alone.  part holds
+ * the graphs' partitions back to back in the caller's order (graph-local
+ * block ids), host or device.  upr_batch_cut's block_weights then holds
+ * sum(k[i]) entries, graph i's k[i] weights after those of graphs < i;
+ * upr_batch_info is as for a batch.  upr_refine, upr_cut and the inspection
+ * entry points refuse the context (UPR_ERR_INVALID).  Errors as
+ * upr_batch_create. */
+upr_status upr_batch_create_mixed(const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
+                                  const upr_params *params, upr_ctx **out);
 
 /* Refines all graphs of a batch context.  part holds every graph's
  * partition back to back (graph i at node offset sum of n of graphs < i,

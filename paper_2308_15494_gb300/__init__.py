@@ -46,7 +46,7 @@ class Stats(ctypes.Structure):
                 ("ms_select", D), ("ms_rebalance", D), ("ms_sequence", D), ("ms_host", D),
                 ("batch_graphs", I32), ("select_lanes", I32), ("propose_lanes", I32),
                 ("sparse_table", I32), ("rebalance_graphs", I32), ("constrained_rounds", I32),
-                ("lp_rounds", I32)]
+                ("lp_rounds", I32), ("lp_table_builds", I32), ("seq_degree_sum", I64), ("bytes_algorithmic", I64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -87,6 +87,7 @@ SIGNATURES = {
     "upr_debug_gain_table": (I32, [P, P, P, P]),
     "upr_debug_round": (I32, [P, P, I32, I32, I32, ctypes.POINTER(Trace)]),
     "upr_batch_create": (I32, [ctypes.POINTER(Graph), I32, I32, P, ctypes.POINTER(Params), ctypes.POINTER(P)]),
+    "upr_batch_create_mixed": (I32, [ctypes.POINTER(Graph), I32, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]),
     "upr_batch_refine": (I32, [P, P, I32, U64, P, P, P, ctypes.POINTER(Stats)]),
     "upr_batch_cut": (I32, [P, P, P, P]),
     "upr_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),
@@ -280,9 +281,10 @@ def upr_debug_round(ctx: Context, part: np.ndarray, r: int, R: int, rebalance_on
 class BatchContext:
     handle: ctypes.c_void_p
     n_graphs: int
-    k: int
+    k: int                       # the graphs' k (0: a mixed context, see ks)
     offsets: np.ndarray          # node offsets, n_graphs + 1
     lmax: np.ndarray             # L_max per graph
+    ks: Optional[np.ndarray] = None   # per graph k of a mixed context
 
     @property
     def n(self) -> int:
@@ -319,10 +321,35 @@ def upr_batch_create(graphs, k: int, eps, params: Optional[Params] = None, strea
     return BatchContext(h, ng, k, off, lm[:ng])
 
 
+def upr_batch_create_mixed(graphs, ks, eps, params: Optional[Params] = None, stream=None) -> BatchContext:
+    """upr_batch_create_mixed: graphs as upr_batch_create, ks[i] = graph i's k."""
+    lib = load()
+    ng = len(graphs)
+    arr = (Graph * max(ng, 1))()
+    for i, (xa, ad, vw, aw) in enumerate(graphs):
+        arr[i], _, _ = _graph_struct(xa, ad, vw, aw)
+    kk = np.ascontiguousarray(np.asarray(ks, np.int32))
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (ng,)))
+    p = params if params is not None else upr_params_default()
+    if stream is not None:
+        p.stream = stream
+    elif not p.stream:
+        p.stream = _current_stream()
+    h = ctypes.c_void_p()
+    st = lib.upr_batch_create_mixed(arr, ng, _ptr(kk), _ptr(e), ctypes.byref(p), ctypes.byref(h))
+    if st != UPR_OK:
+        raise UprError(st, "upr_batch_create_mixed")
+    cnt = I32()
+    off = np.zeros(ng + 1, np.int64)
+    lm = np.zeros(max(ng, 1), np.int64)
+    lib.upr_batch_info(h, ctypes.byref(cnt), _ptr(off), _ptr(lm))
+    return BatchContext(h, ng, 0, off, lm[:ng], kk.copy())
+
+
 def create_batch_from_workloads(ws, params: Optional[Params] = None, device: bool = False) -> BatchContext:
-    """One batch context for workloads that share k (their own eps each)."""
+    """One batch context for the workloads (their own eps each): upr_batch_create
+    when they share k, upr_batch_create_mixed otherwise."""
     ks = {w.k for w in ws}
-    assert len(ks) == 1, "a batch holds graphs with one k"
     graphs = []
     for w in ws:
         arrs = [w.xadj, w.adj, w.vwgt, w.adjw]
@@ -330,6 +357,8 @@ def create_batch_from_workloads(ws, params: Optional[Params] = None, device: boo
             import torch
             arrs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
         graphs.append(tuple(arrs))
+    if len(ks) > 1:
+        return upr_batch_create_mixed(graphs, [w.k for w in ws], [w.eps for w in ws], params=params)
     return upr_batch_create(graphs, ws[0].k, [w.eps for w in ws], params=params)
 
 
@@ -347,12 +376,18 @@ def upr_batch_refine(ctx: BatchContext, part, rounds: int, seed: int = 0):
     return status[:ng], cin[:ng], cout[:ng], st
 
 
-def upr_batch_cut(ctx: BatchContext, part) -> tuple[np.ndarray, np.ndarray]:
+def upr_batch_cut(ctx: BatchContext, part):
+    """Per-graph cuts and block weights: an (n_graphs, k) array, or for a mixed
+    context a list with graph i's k_i weights."""
     cut = np.zeros(max(ctx.n_graphs, 1), np.int64)
-    bw = np.zeros(max(ctx.n_graphs * ctx.k, 1), np.int64)
+    total = int(ctx.ks.sum()) if ctx.ks is not None else ctx.n_graphs * ctx.k
+    bw = np.zeros(max(total, 1), np.int64)
     rc = load().upr_batch_cut(ctx.handle, _ptr(part), _ptr(cut), _ptr(bw))
     if rc != UPR_OK:
         raise UprError(rc, "upr_batch_cut")
+    if ctx.ks is not None:
+        ends = np.cumsum(ctx.ks)
+        return cut[: ctx.n_graphs], [bw[e - k:e] for e, k in zip(ends, ctx.ks)]
     return cut[: ctx.n_graphs], bw[: ctx.n_graphs * ctx.k].reshape(ctx.n_graphs, ctx.k)
 
 

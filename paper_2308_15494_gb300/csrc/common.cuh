@@ -32,10 +32,10 @@ struct CudaError { cudaError_t e; const char *what; };
     } while (0)
 
 // Counts kernel launches of this library (reported in upr_stats).
-extern std::atomic<long long> g_upr_launches;
+extern thread_local long long g_upr_launches;
 #define UPR_LAUNCH_CHECK()                                                 \
     do {                                                                   \
-        ::upr::g_upr_launches.fetch_add(1, std::memory_order_relaxed);     \
+        ::upr::g_upr_launches++;     \
         UPR_CUDA(cudaGetLastError());                                      \
     } while (0)
 

@@ -102,7 +102,37 @@ __global__ void k_fill_i64(int64_t *a, int64_t n, int64_t v) {
 
 }  // namespace
 
-std::atomic<long long> upr::g_upr_launches{0};
+namespace {
+// Slots of the device counters (upr_ctx::counts).
+enum {
+    CNT_CAND = 0, CNT_M, CNT_P, CNT_S, CNT_A, CNT_I, CNT_HUB, CNT_BADPART, CNT_L1, CNT_X, CNT_EVM, CNT_EVI,
+    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_HIST, CNT_EXACT, CNT_SLOTS = 32
+};
+
+// Per-call sums of the step graph's rounds (upr_ctx::dstats): candidates,
+// moves, rebalancing moves, sub-rounds, sequence length, applied moves, the
+// primitives' error word, infeasible rounds, interleaved length.
+__global__ void k_round_stats(const int32_t *__restrict__ cnt, const RebalCtl *__restrict__ ctl,
+                              const long long *__restrict__ best, const int64_t *__restrict__ tot, int batch,
+                              const int32_t *__restrict__ err, long long *__restrict__ d) {
+    if (threadIdx.x != 0) return;
+    const bool infeasible = !batch && cnt[CNT_INFEAS] != 0;
+    d[0] += cnt[CNT_CAND];
+    d[1] += cnt[CNT_M];
+    d[2] += ctl->nR;
+    d[3] += ctl->subrounds;
+    d[4] += cnt[CNT_I];
+    d[5] += infeasible ? 0 : batch ? tot[0] : best[1];
+    d[6] |= *err;
+    d[7] += infeasible ? 1 : 0;
+    d[8] += cnt[CNT_X];
+}
+}  // namespace
+
+// kernels launched by this host thread (a call runs on one thread, so the
+// difference over a call counts that call's launches even when other
+// threads refine other contexts meanwhile)
+thread_local long long upr::g_upr_launches = 0;
 
 int upr::resident_ctas(const void *func, int threads, size_t shm) {
     static std::mutex mu;
@@ -140,6 +170,7 @@ void upr::kernel_setup(const void *func, int carveout_percent) {
 
 struct upr_ctx {
     int device = 0;
+    MixedBatch *mix = nullptr;        // a context over graphs of different k (mixed.cu); nothing else is used
     int64_t n = 0, m = 0;
     int32_t k = 0;
     int32_t ng = 1;                   // graphs bound (a batch when > 1)
@@ -168,7 +199,21 @@ struct upr_ctx {
     int reb_body_kernels = 0;
     int64_t rounds_bound = 0;         // rounds run since the binding
     bool cut_pending = false;         // the next build also computes the cut of part0 (load_part skipped it)
+    int32_t lp_attempts = 0;          // label propagation rounds run by the current call (kept or not)
     bool reb_failed = false;          // capture or instantiation failed: host-driven loop
+    // the whole refinement after round 1's table build as one CUDA graph
+    // (params.graphs == 2): every round's launches, each rebalancing loop a
+    // while node; built on a binding's second call of the same shape
+    cudaGraphExec_t step_exec = nullptr;
+    cudaStream_t s_body = nullptr;    // captures the while nodes' bodies
+    uint64_t step_gen = ~0ull;
+    int32_t step_rounds = -1, step_off = -1, step_total = -1, step_lock = -1;
+    LaneCfg step_sel{}, step_prop{};
+    bool step_failed = false, capturing = false;
+    int32_t cap_round = 0;            // while capturing: index of the round in the call (0-based)
+    long long step_kernels = 0;       // kernels of the step graph outside the while bodies
+    int64_t *F_all = nullptr; int64_t *hF_all = nullptr; int32_t F_all_cap = 0;   // [rounds][kSlots]
+    int64_t calls_bound = 0;          // refinement calls since the binding
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -211,10 +256,12 @@ struct upr_ctx {
     int32_t *seg_first, *rbeg, *rend, *ebeg, *eend, *qfin, *left, *left_excl;
     long long *best_parts, *best;
     int8_t *over_d, *excl_d, *reject_d;
+    long long *Cd;                   // [K] block-weight changes of a fused rebalancing sub-round
     unsigned long long *prio_hist;   // [K][kPrioBins] proposal prefilter (null: K too large, no prefilter)
     int32_t *prio_cut;               // [K]
     int32_t *counts;          // device counters (CNT_* slots)
     RebalCtl *ctl;            // rebalancing loop control block
+    long long *dstats;        // [16] per-call sums of the step graph's rounds
     uint64_t *vacc; int32_t *vflags; int64_t *scal, *cut_parts;
     int2 *pk;                 // exact gains: position in I and blocks before/after, per node
     Scratch tmp;              // scan / sort temporaries
@@ -303,11 +350,13 @@ void layout(upr_ctx *c, Arena &A) {
     c->over_d = A.take<int8_t>(k);
     c->excl_d = A.take<int8_t>(k);
     c->reject_d = A.take<int8_t>(k);
+    c->Cd = A.take<long long>(k);
     const bool prefilter = k * (size_t)kPrioBins <= ((size_t)1 << 22);
     c->prio_hist = prefilter ? A.take<unsigned long long>(k * kPrioBins) : nullptr;
     c->prio_cut = prefilter ? A.take<int32_t>(k) : nullptr;
     c->counts = A.take<int32_t>(64);
     c->ctl = A.take<RebalCtl>(1);
+    c->dstats = A.take<long long>(16);
     c->vacc = A.take<uint64_t>(2);
     c->vflags = A.take<int32_t>(2);
     c->scal = A.take<int64_t>(4);    // [0] wmax, [1] degree sum of M, [2] degree sum of undone moves
@@ -379,12 +428,6 @@ struct TraceSink { upr_trace *t; int8_t *avail_d; int32_t *slot_d; };
 void d2h(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (dst && bytes) UPR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
 }
-
-// Slots of the device counters (upr_ctx::counts).
-enum {
-    CNT_CAND = 0, CNT_M, CNT_P, CNT_S, CNT_A, CNT_I, CNT_HUB, CNT_BADPART, CNT_L1, CNT_X, CNT_EVM, CNT_EVI,
-    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_SLOTS = 32
-};
 
 // ---- lane-schedule tuning.  A kernel whose schedule is not chosen yet runs
 // every candidate back to back on the same inputs (each run rewrites the
@@ -459,6 +502,18 @@ void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands
     *pending = 0;
 }
 
+// The fused form of a rebalancing sub-round applies: one graph, K <= 256, a
+// one-word key, the prefilter, and per-(block, tile) sums that fit the
+// 2n-entry buffers they use (UPR_FUSED=0 in the environment turns it off:
+// the general form computes the same sub-round).
+bool fused_rebalance(const upr_ctx *c, int key_bits) {
+    static int env = -1;
+    if (env < 0) { const char *v = getenv("UPR_FUSED"); env = (v && *v == '0') ? 0 : 1; }
+    const int64_t n = std::max<int64_t>(c->n, 1);
+    return env == 1 && rebalance_fused_ok(c->G, key_bits, c->prio_hist != nullptr) &&
+           (int64_t)c->G.K() * ceil_div(n, (int64_t)2048) <= 2 * n;
+}
+
 // One rebalancing sub-round (Sec. 6), enqueued on s.  Every argument is fixed
 // for the binding (the sub-round number and every list length live in device
 // memory), so the same launches can be captured once and replayed.  first:
@@ -485,6 +540,32 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     // node without a proposal has no block with room for it (the lightest
     // allowed block has the most room, and rooms only shrink), so it never
     // proposes again
+    const int key_bits = 1 + c->gbits + 2 * c->cbits;
+    if (fused_rebalance(c, key_bits)) {
+        // the same sub-round in fused passes (reb_fused.cu): the proposers
+        // with the prefilter histogram, the cut bins, the kept proposals as
+        // (key, node), one sort by key, selection and admission from
+        // per-tile block sums, R appended and the moves applied
+        uint64_t *rep = reinterpret_cast<uint64_t *>(c->qmax);       // kPrioBins keys (free during rebalancing)
+        int32_t *exact = cnt + CNT_EXACT;
+        rebalance_fused_compact_hist(G, c->flags, c->L1, &ctl->n1_active, n, cnt + CNT_L1, st.lgain, st.lsrc,
+                                     c->gbits, c->cbits, c->prm.gain_priority, c->prio_hist, rep, exact, c->tmp, s);
+        rebalance_prio_cut(G, c->over_d, c->C, c->prio_hist, c->prio_cut, s);
+        rebalance_fused_keep_keys(G, c->L1, cnt + CNT_L1, n, st.lgain, st.lsrc, c->prio_cut, c->gbits, c->cbits,
+                                  c->prm.gain_priority, c->sb[0].k, c->sb[0].v, cnt + CNT_P, rep, exact, c->tmp, s);
+        rebalance_fused_sort(c->sb[0].k, c->sb[0].v, c->sb[0].ka, c->sb[0].va, cnt + CNT_P, n, key_bits, c->gbits,
+                             c->cbits, exact, c->tmp, s);
+        const uint32_t *U = c->sb[0].va;
+        rebalance_fused_select_admit(G, U, cnt + CNT_P, n, c->part, c->prop_tgt, c->C,
+                                     reinterpret_cast<int8_t *>(c->flags2), reinterpret_cast<long long *>(c->c_sorted),
+                                     reinterpret_cast<long long *>(c->c_excl), cnt + CNT_HIST, c->reject_d, ctl,
+                                     c->R_node, c->R_from, c->R_to, c->R_sub, c->r_to, c->r_at, c->Cd, cnt + CNT_A,
+                                     c->tmp, s);
+        table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
+                   c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
+        rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
+        return;
+    }
     select_values(c->flags, c->L1, c->L1, cnt + CNT_L1, Count{&ctl->n1_active, n}, c->tmp, s);
     // proposals that cannot be in their source's minimal prefix are dropped
     // before the ordering; P lists the others in node order
@@ -499,7 +580,6 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     }
     const Count cP{dP, n};
     uint64_t *kA; uint32_t *A;
-    const int key_bits = 1 + c->gbits + 2 * c->cbits;
     if (key_bits <= 63) {
         rebalance_prio_keys(G, Pn, dP, c->prop_gain, c->gbits, c->cbits, c->prm.gain_priority, c->sb[0].k,
                             c->sb[0].v, n, s);
@@ -569,10 +649,10 @@ bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         capturing = true;
-        const long long b0 = g_upr_launches.load();
+        const long long b0 = g_upr_launches;
         enqueue_subround(c, st, light, false, c->s_cap);
         rebalance_continue(c->ctl, c->prm.max_subrounds, cond, c->s_cap);
-        c->reb_body_kernels = (int)(g_upr_launches.load() - b0);
+        c->reb_body_kernels = (int)(g_upr_launches - b0);
         captured += c->reb_body_kernels;
         capturing = false;
         UPR_CUDA(cudaStreamEndCapture(c->s_cap, &out));
@@ -590,7 +670,7 @@ bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
         c->reb_exec = nullptr;
         c->reb_failed = true;
     }
-    g_upr_launches.fetch_sub(captured);     // captured, not launched: counted when the graph runs
+    g_upr_launches -= (captured);     // captured, not launched: counted when the graph runs
     c->reb_gen = c->gen;
     c->reb_cfg = c->prop_cfg;
     return c->reb_exec != nullptr;
@@ -613,7 +693,44 @@ void rebalance_phase(upr_ctx *c, int32_t r, RoundInfo &ri, TraceSink *tr) {
     rebalance_flag_in_blocks(c->part, n, c->excl_d, c->flags, s);
     select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
     int32_t *light = batch ? c->light_g : &ctl->light;
-    const RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
+    RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
+    if (fused_rebalance(c, 1 + c->gbits + 2 * c->cbits)) {
+        st.lsrc = c->emit;          // list-indexed proposal blocks and gains (sequence-phase arrays, free here)
+        st.lgain = c->qbefore;
+    }
+    if (c->capturing) {
+        // inside the step graph: the loop as a while node whose body is one
+        // sub-round followed by the condition kernel (captured on a side
+        // stream into the node's body graph)
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        UPR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle cond;
+        UPR_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+        rebalance_continue(ctl, c->prm.max_subrounds, cond, s);
+        UPR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop;
+        UPR_CUDA(cudaGraphAddNode(&loop, g, deps, nullptr, nd, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (!c->s_body) UPR_CUDA(cudaStreamCreateWithFlags(&c->s_body, cudaStreamNonBlocking));
+        UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const long long b0 = g_upr_launches;
+        enqueue_subround(c, st, light, false, c->s_body);
+        rebalance_continue(ctl, c->prm.max_subrounds, cond, c->s_body);
+        c->reb_body_kernels = (int)(g_upr_launches - b0);
+        cudaGraph_t out = nullptr;
+        UPR_CUDA(cudaStreamEndCapture(c->s_body, &out));
+        UPR_CUDA(cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
+        ri.graph = true;
+        return;
+    }
     auto t_sub = std::chrono::steady_clock::now();
     // the loop runs on the device as one graph once the proposal schedule is
     // settled (the host-driven form times the schedules, logs and traces);
@@ -676,14 +793,18 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
     // ---- (a) gain table of the round-start partition (kept from the previous
     // round of this call when it is valid)
-    const bool build = !c->table_valid || tr;
+    // (in the step graph the table is always carried: round 1's build runs before it)
+    const bool cap = c->capturing;
+    const bool build = !cap && (!c->table_valid || tr);
     c->table_valid = false;
-    UPR_CUDA(cudaEventRecord(c->ev[0], s));
+    if (!cap) UPR_CUDA(cudaEventRecord(c->ev[0], s));
     if (build)
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, nullptr, s);
-    UPR_CUDA(cudaEventRecord(c->ev[1], s));
-    UPR_CUDA(cudaEventRecord(c->ev[4], s));
+    if (!cap) {
+        UPR_CUDA(cudaEventRecord(c->ev[1], s));
+        UPR_CUDA(cudaEventRecord(c->ev[4], s));
+    }
     if (!rebalance_only) {
         // ---- (b1) availability, slots, bucket weights; F_r
         // (the first round of a call also sums the input cut here)
@@ -691,18 +812,22 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
                 tr ? tr->avail_d : nullptr, tr ? tr->slot_d : nullptr, s, c->cut_pending ? c->cut_parts : nullptr,
                 c->cut);
         c->cut_pending = false;
-        if (kind.constrained || kind.limit > 0)
-            for (int l = 0; l < kSlots; l++) c->hF[l] = kConstrainedF;
-        else if (kind.tau_den > 0)
-            factors_tau((u128)kind.tau_num, (u128)kind.tau_den, c->hF);
-        else
-            penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
-        UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
+        // the step graph reads round i's factors from the per-call table F_all
+        const int64_t *F = cap ? c->F_all + (int64_t)c->cap_round * kSlots : c->F;
+        if (!cap) {
+            if (kind.constrained || kind.limit > 0)
+                for (int l = 0; l < kSlots; l++) c->hF[l] = kConstrainedF;
+            else if (kind.tau_den > 0)
+                factors_tau((u128)kind.tau_num, (u128)kind.tau_den, c->hF);
+            else
+                penalty_factors(r, R, c->prm.tau1_num, c->prm.tau1_den, c->hF);
+            UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
+        }
         if (kind.limit > 0) {
             k_fill_i64<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(c->Lsel, K, kind.limit);
             UPR_LAUNCH_CHECK();
         }
-        Penalty pen{c->PW, c->F, c->C0, kind.limit > 0 ? c->Lsel : c->Lb, c->first_slot};
+        Penalty pen{c->PW, F, c->C0, kind.limit > 0 ? c->Lsel : c->Lb, c->first_slot};
         // ---- (b2) best move per boundary node
         run_tuned(c, c->sel_tuned, c->sel_cfg, c->sel_cands, &c->sel_pending, c->ev_tune, [&](LaneCfg cfg) {
             select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, cfg, s);
@@ -733,11 +858,11 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
         gain_table(G, c->part, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, c->scal + 1, s);
     }
-    UPR_CUDA(cudaEventRecord(c->ev[5], s));
+    if (!cap) UPR_CUDA(cudaEventRecord(c->ev[5], s));
 
     // ---- (d) rebalancing sub-rounds
     rebalance_phase(c, r, ri, tr);
-    UPR_CUDA(cudaEventRecord(c->ev[6], s));
+    if (!cap) UPR_CUDA(cudaEventRecord(c->ev[6], s));
 
     // ---- (c1) interleave M and R_1..R_k (or append R after M: a variant of Sec. 7.2)
     const int32_t *dM = cnt + CNT_M, *dR = &ctl->nR;
@@ -792,7 +917,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     }
 
     // ---- (c2) exact gains, balanced prefixes, best prefix
-    seq_gains(G, Iv, If, It, dI, n, c->part0, c->pk, c->I_gain, c->hub_chunks, c->n_chunks, s);
+    seq_gains(G, Iv, If, It, dI, n, c->part0, c->pk, c->I_gain, c->hub_chunks, c->n_chunks, c->scal + 3, s);
     inclusive_sum_i64(c->I_gain, c->Gsum, Count{dI, n}, c->tmp, s);
     count_affine(dI, 2, nullptr, 0, cnt + CNT_EVI, s);
     count_affine(dI, 1, nullptr, 1, cnt + CNT_I1, s);
@@ -806,7 +931,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     clear_count(c->diff, dI, 1, n, s);
     seq_iev_transitions(E, kE, dI, n, c->delta, c->d_excl, c->ebeg, c->C0, c->Lb, c->diff, s);
     exclusive_sum_i32(c->diff, c->diff_excl, Count{cnt + CNT_I1, n + 1}, c->tmp, s);
-    UPR_CUDA(cudaMemcpyAsync(c->hcut, c->cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));   // cut before the round
+    if (!cap) UPR_CUDA(cudaMemcpyAsync(c->hcut, c->cut, sizeof(int64_t), cudaMemcpyDeviceToHost, s));   // cut before the round
     if (!batch) {
         count_over(G, c->C0, cnt + CNT_OVER0, s);
         seq_best(c->Gsum, c->diff, c->diff_excl, dI, n, cnt + CNT_OVER0, c->best_parts, c->best, cnt + CNT_INFEAS, s);
@@ -815,7 +940,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
         seq_best_seg(G, Iv, dI, n, c->seg_beg, c->Gsum, c->diff, c->diff_excl, c->over0_g, c->best_g, c->best_j, c->cut,
                      c->infeas_g, c->tot, s);
     }
-    if (G.sp.on()) {
+    if (G.sp.on() && !cap) {
         // a sparse row without room for a new block: nothing of the round is
         // applied yet; the caller runs it again on rows built afresh (which
         // drop the blocks whose weight went back to zero) or, if these were
@@ -845,6 +970,12 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     reset_nodes(c->I_node, dI, n, c->pos, INT32_MAX, s);
     reset_nodes(c->M_node, dM, n, c->m_pos, -1, s);
     reset_nodes(c->R_node, dR, n, c->r_to, -1, s);
+    if (cap) {                  // the step graph: the round's counts go to the device sums
+        k_round_stats<<<1, 32, 0, s>>>(cnt, ctl, c->best, c->tot, batch ? 1 : 0, c->tmp.err, c->dstats);
+        UPR_LAUNCH_CHECK();
+        c->table_valid = true;
+        return UPR_OK;
+    }
     UPR_CUDA(cudaEventRecord(c->ev[7], s));
     UPR_CUDA(cudaMemcpyAsync(c->hcnt, cnt, sizeof(int32_t) * CNT_SLOTS, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaMemcpyAsync(c->hctl, ctl, sizeof(RebalCtl), cudaMemcpyDeviceToHost, s));
@@ -872,7 +1003,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     ri.n_moves = hc[CNT_M];
     ri.n_rebal = c->hctl->nR;
     ri.subrounds = c->hctl->subrounds;
-    if (ri.graph) g_upr_launches.fetch_add(1 + (long long)c->reb_body_kernels * ri.subrounds);
+    if (ri.graph) g_upr_launches += (1 + (long long)c->reb_body_kernels * ri.subrounds);
     ri.n_inter = hc[CNT_X];
     ri.n_seq = hc[CNT_I];
     // one graph: an infeasible round applies nothing and is an error; a
@@ -970,10 +1101,15 @@ upr_status run_round(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only, Roun
 
 void free_ctx(upr_ctx *c) {
     if (!c) return;
+    if (c->mix) mixed_destroy(c->mix);
     if (c->mem) cudaFree(c->mem);
     if (c->W_own) cudaFree(c->W_own);
     if (c->reb_exec) cudaGraphExecDestroy(c->reb_exec);
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
     if (c->s_cap) cudaStreamDestroy(c->s_cap);
+    if (c->s_body) cudaStreamDestroy(c->s_body);
+    if (c->F_all) cudaFree(c->F_all);
+    if (c->hF_all) cudaFreeHost(c->hF_all);
     if (c->h) cudaFreeHost(c->h);
     if (c->h8) cudaFreeHost(c->h8);
     for (auto &e : c->ev) if (e) cudaEventDestroy(e);
@@ -1080,9 +1216,12 @@ int lp_round_once(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri)
     UPR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * CNT_SLOTS, s));
     UPR_CUDA(cudaMemcpyAsync(c->part, c->part0, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     UPR_CUDA(cudaMemcpyAsync(c->C, c->C0, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
-    if (!c->table_valid)
+    const bool build = !c->table_valid;
+    UPR_CUDA(cudaEventRecord(c->ev[0], s));
+    if (build)
         gain_table(G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, nullptr, s);
+    UPR_CUDA(cudaEventRecord(c->ev[1], s));
     c->table_valid = false;
     // selection without a penalty: no block limit, so no move pays anything
     for (int l = 0; l < kSlots; l++) c->hF[l] = kConstrainedF;
@@ -1101,9 +1240,10 @@ int lp_round_once(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri)
                c->tile_nodes, c->scal + 1, s);
     UPR_CUDA(cudaEventRecord(c->ev[5], s));
     rebalance_phase(c, 0, ri, nullptr);
-    // balanced, and the cut after
+    // balanced, and the cut after: the table follows every move and
+    // rebalancing move, so the cut comes from it in a pass over the nodes
     count_over(G, c->C, cnt + CNT_OVER0, s);
-    edge_cut(G, c->part, c->tot, s);
+    cut_from_table(G, c->part, c->W, c->tot, s);
     int64_t cut1 = 0;
     UPR_CUDA(cudaMemcpyAsync(c->hcnt, cnt, sizeof(int32_t) * CNT_SLOTS, cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaMemcpyAsync(c->hcut, c->tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1111,6 +1251,12 @@ int lp_round_once(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri)
     if (G.sp.on()) UPR_CUDA(cudaMemcpyAsync(c->hcnt + 41, c->sp_over, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     UPR_CUDA(cudaStreamSynchronize(s));
     cut1 = *c->hcut;
+    if (build) {
+        float t = 0;
+        UPR_CUDA(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+        ri.ms_table += t;
+        ri.tables++;
+    }
     ri.n_moves = c->hcnt[CNT_M];
     ri.n_rebal = c->hctl->nR;
     ri.subrounds = c->hctl->subrounds;
@@ -1168,9 +1314,18 @@ bool lp_round(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri) {
 // it.  Returns the rounds kept.
 int32_t label_propagation(upr_ctx *c, int32_t max_rounds, int64_t *cut, upr_stats &st) {
     cudaStream_t s = c->s;
-    if (!c->table_valid)
+    if (!c->table_valid) {
+        UPR_CUDA(cudaEventRecord(c->ev[0], s));
         gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
                    c->tile_nodes, nullptr, s);
+        UPR_CUDA(cudaEventRecord(c->ev[1], s));
+        UPR_CUDA(cudaEventSynchronize(c->ev[1]));
+        float t = 0;
+        UPR_CUDA(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+        st.ms_gain_table += t;
+        st.gain_table_builds++;
+        st.lp_table_builds++;
+    }
     c->table_valid = true;
     lp_boundary(c->G, c->part0, c->W, c->lp_active, s);
     lp_count(c->lp_active, c->n, c->counts + CNT_L1, s);
@@ -1181,7 +1336,12 @@ int32_t label_propagation(upr_ctx *c, int32_t max_rounds, int64_t *cut, upr_stat
     for (int32_t r = 1; r <= max_rounds && active > 0; r++) {
         const int64_t before = *cut;
         RoundInfo ri;
-        if (!lp_round(c, cut, &active, ri)) break;
+        const bool keep = lp_round(c, cut, &active, ri);
+        st.ms_gain_table += ri.ms_table;
+        st.gain_table_builds += ri.tables;
+        st.lp_table_builds += ri.tables;
+        c->lp_attempts++;
+        if (!keep) break;
         kept++;
         st.n_moves += ri.n_moves;
         st.n_rebalance_moves += ri.n_rebal;
@@ -1189,6 +1349,119 @@ int32_t label_propagation(upr_ctx *c, int32_t max_rounds, int64_t *cut, upr_stat
         if (1000 * (before - *cut) < before) break;
     }
     return kept;
+}
+
+// The step graph of `rounds` rounds (round_offset+1 .. of total): every
+// round of run_round_once captured on s_cap with the rebalancing loops as
+// while nodes.  False if it cannot be built (the host-driven rounds run).
+bool build_step_graph(upr_ctx *c, int32_t rounds, int32_t total) {
+    if (c->step_exec) { cudaGraphExecDestroy(c->step_exec); c->step_exec = nullptr; }
+    cudaStream_t saved = c->s;
+    cudaGraph_t g = nullptr;
+    bool capturing = false;
+    const long long l0 = g_upr_launches;
+    try {
+        if (!c->s_cap) UPR_CUDA(cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
+        UPR_CUDA(cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeRelaxed));
+        capturing = true;
+        c->s = c->s_cap;
+        c->capturing = true;
+        for (int32_t i = 1; i <= rounds; i++) {
+            c->cap_round = i - 1;
+            RoundInfo ri;
+            run_round_once(c, c->prm.round_offset + i, total, false, ri, nullptr, RoundKind());
+        }
+        c->capturing = false;
+        c->s = saved;
+        capturing = false;
+        UPR_CUDA(cudaStreamEndCapture(c->s_cap, &g));
+        UPR_CUDA(cudaGraphInstantiate(&c->step_exec, g, 0));
+        cudaGraphDestroy(g);
+    } catch (const CudaError &e) {
+        c->capturing = false;
+        c->s = saved;
+        if (capturing) {
+            cudaGraph_t out = nullptr;
+            cudaStreamEndCapture(c->s_cap, &out);
+            if (out) cudaGraphDestroy(out);
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (log_enabled()) fprintf(stderr, "upr: step graph not built (%s: %s)\n", e.what, cudaGetErrorString(e.e));
+        c->step_exec = nullptr;
+        c->step_failed = true;
+    }
+    const long long captured = g_upr_launches - l0;
+    g_upr_launches -= (captured);     // captured, not launched: counted when the graph runs
+    c->step_kernels = captured - (long long)rounds * c->reb_body_kernels;
+    c->step_gen = c->gen;
+    c->step_rounds = rounds;
+    c->step_off = c->prm.round_offset;
+    c->step_total = total;
+    c->step_lock = c->prm.lock_rebalanced;
+    c->step_sel = c->sel_cfg;
+    c->step_prop = c->prop_cfg;
+    return c->step_exec != nullptr;
+}
+
+// Rounds 1..rounds of a call as one graph launch (params.graphs == 2, the
+// plain tau schedule, dense table, lane schedules settled): round 1's table
+// build runs (timed) before the graph, the rounds' penalty factors are copied
+// in one piece, and the rounds' counts are read once at the end.  False: not
+// applicable (nothing enqueued but the build); the caller runs the rounds.
+bool run_step_graph(upr_ctx *c, int32_t rounds, int32_t total, upr_stats &st) {
+    cudaStream_t s = c->s;
+    if (c->step_failed) return false;
+    const bool same = c->step_exec && c->step_gen == c->gen && c->step_rounds == rounds &&
+                      c->step_off == c->prm.round_offset && c->step_total == total &&
+                      c->step_lock == c->prm.lock_rebalanced && c->step_sel.G == c->sel_cfg.G &&
+                      c->step_sel.CH == c->sel_cfg.CH && c->step_prop.G == c->prop_cfg.G &&
+                      c->step_prop.CH == c->prop_cfg.CH;
+    if (!c->table_valid) {
+        UPR_CUDA(cudaEventRecord(c->ev[0], s));
+        gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                   c->tile_nodes, nullptr, s);
+        UPR_CUDA(cudaEventRecord(c->ev[1], s));
+        UPR_CUDA(cudaEventSynchronize(c->ev[1]));
+        float t = 0;
+        UPR_CUDA(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+        st.ms_gain_table += t;
+        st.gain_table_builds++;
+        c->table_valid = true;
+    }
+    if (c->F_all_cap < rounds) {
+        if (c->F_all) cudaFree(c->F_all);
+        if (c->hF_all) cudaFreeHost(c->hF_all);
+        c->F_all = nullptr;
+        c->hF_all = nullptr;
+        c->F_all_cap = 0;
+        UPR_CUDA(cudaMalloc(&c->F_all, sizeof(int64_t) * kSlots * (size_t)rounds));
+        UPR_CUDA(cudaMallocHost(&c->hF_all, sizeof(int64_t) * kSlots * (size_t)rounds));
+        c->F_all_cap = rounds;
+    }
+    UPR_CUDA(cudaStreamSynchronize(s));          // hF_all may still be read by the previous call's copy
+    for (int32_t i = 1; i <= rounds; i++)
+        penalty_factors(c->prm.round_offset + i, total, c->prm.tau1_num, c->prm.tau1_den,
+                        c->hF_all + (size_t)(i - 1) * kSlots);
+    if (!same && !build_step_graph(c, rounds, total)) return false;
+    UPR_CUDA(cudaMemcpyAsync(c->F_all, c->hF_all, sizeof(int64_t) * kSlots * rounds, cudaMemcpyHostToDevice, s));
+    UPR_CUDA(cudaMemsetAsync(c->dstats, 0, sizeof(long long) * 16, s));
+    UPR_CUDA(cudaGraphLaunch(c->step_exec, s));
+    long long d[16];
+    UPR_CUDA(cudaMemcpyAsync(d, c->dstats, sizeof(d), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    if (d[6] != 0) { c->table_valid = false; throw CudaError{cudaErrorLaunchTimeout, "primitive wait"}; }
+    if (d[7] != 0) { c->table_valid = false; throw CudaError{cudaErrorInvalidValue, "step graph: infeasible round"}; }
+    st.rounds_run += rounds;
+    st.n_candidates += d[0];
+    st.n_moves += d[1];
+    st.n_rebalance_moves += d[2];
+    st.subrounds += (int32_t)d[3];
+    st.n_sequence += d[4];
+    st.n_applied += d[5];
+    st.rebalance_graphs += rounds;
+    g_upr_launches += (c->step_kernels + (long long)c->reb_body_kernels * d[3]);
+    return true;
 }
 
 upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *stats, upr_status *status,
@@ -1203,8 +1476,10 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     if (c->prm.lp_rounds > 0 && ng != 1) return UPR_ERR_INVALID;     // label propagation: one graph
     upr_stats st{};
     const auto t_host0 = std::chrono::steady_clock::now();
-    const long long launches0 = g_upr_launches.load();
+    const long long launches0 = g_upr_launches;
+    c->lp_attempts = 0;
     UPR_CUDA(cudaEventRecord(c->ev[2], c->s));
+    UPR_CUDA(cudaMemsetAsync(c->scal + 3, 0, sizeof(int64_t), c->s));     // degrees of the sequences' nodes
     // one graph with a balanced input: the first round's bucket pass, which
     // reads omega(v, V_P(v)) and omega(I(v)) of every node anyway, gives the
     // cut, instead of a pass over the edges
@@ -1262,7 +1537,16 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     const int32_t U = rounds >= 3 ? rounds - 2 : rounds == 2 ? 1 : 0;
     bool unconstrained_rest = false, switched = false;
     int64_t imp1 = 0, cut_now = st.cut_in - repair_gain;
-    for (int32_t i = 1; i <= rounds; i++) {
+    // params.graphs == 2: from a binding's second call on, the plain schedule's
+    // rounds run as one graph launch
+    c->calls_bound++;
+    LaneCfg lc[3];
+    const bool no_choice = lane_candidates(c->k, lc) <= 1;      // nothing to time: the schedule is fixed
+    const bool settled = no_choice || !worth_tuning(c) || (c->sel_tuned && c->prop_tuned);
+    const bool step = c->prm.graphs == 2 && sch == 0 && c->prm.lp_rounds == 0 && !c->G.sp.on() && rounds >= 1 &&
+                      !log_enabled() && settled && c->calls_bound >= 2;
+    const int32_t first_round = step && run_step_graph(c, rounds, total, st) ? rounds + 1 : 1;
+    for (int32_t i = first_round; i <= rounds; i++) {
         RoundInfo ri;
         RoundKind kind;
         int32_t r = c->prm.round_offset + i, R = total;
@@ -1323,10 +1607,20 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     float ms = 0;
     UPR_CUDA(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
     st.ms_device = ms;
-    st.kernel_launches = (int32_t)(g_upr_launches.load() - launches0);
+    st.kernel_launches = (int32_t)(g_upr_launches - launches0);
     st.ms_host = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
-    st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n +
-                          4 * c->n * (int64_t)c->k;
+    // the rows written by a build: the dense table, or every slot of the hashed rows
+    const int64_t table_bytes = c->G.sp.on() ? 8 * c->sp_slots : 4 * c->n * (int64_t)c->k;
+    st.gain_table_bytes = 8 * (c->n + 1) + 4 * c->m + (c->G.adjw ? 4 * c->m : 0) + 4 * c->n + table_bytes;
+    read_i64(c, c->scal + 3, 1, &st.seq_degree_sum);
+    // the rounds' algorithmic bytes (FM rounds and label propagation rounds):
+    // each build, per round a read of the table and 16 bytes per node (part,
+    // c, omega(I)), the exact gains and delta updates over the adjacency of
+    // the sequence's nodes, and one read and one write of 24-byte records per
+    // candidate, move and rebalancing move
+    st.bytes_algorithmic = (int64_t)st.gain_table_builds * st.gain_table_bytes +
+                           (int64_t)(st.rounds_run + c->lp_attempts) * (table_bytes + 16 * c->n) +
+                           16 * st.seq_degree_sum + 48 * (st.n_candidates + st.n_moves + st.n_rebalance_moves);
     st.batch_graphs = ng;
     {
         LaneCfg d[3];
@@ -1384,7 +1678,7 @@ static bool params_ok(const upr_params &p) {
     return p.t_den > 0 && p.t_num >= 0 && p.t_num <= p.t_den && p.tau1_den > 0 && p.tau1_den <= 65536 &&
            p.tau1_num >= 0 && p.tau1_num <= p.tau1_den && p.max_subrounds >= 1 && p.round_offset >= 0 &&
            p.total_rounds >= 0 && p.total_rounds <= 65536 && (p.autotune == 0 || p.autotune == 1) &&
-           p.table >= 0 && p.table <= 3 && (p.graphs == 0 || p.graphs == 1) && p.schedule >= 0 && p.schedule <= 6 && p.lp_rounds >= 0 && p.lp_rounds <= 64 &&
+           p.table >= 0 && p.table <= 3 && (p.graphs >= 0 && p.graphs <= 2) && p.schedule >= 0 && p.schedule <= 6 && p.lp_rounds >= 0 && p.lp_rounds <= 64 &&
            (p.lock_rebalanced == 0 || p.lock_rebalanced == 1) &&
            (p.gain_priority == 0 || p.gain_priority == 1) && (p.append == 0 || p.append == 1);
 }
@@ -1623,6 +1917,8 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     if (c->W_own) { cudaFree(c->W_own); c->W_own = nullptr; c->W_own_bytes = 0; }
     c->gen++;                       // kernels captured for the previous binding are stale
     c->rounds_bound = 0;
+    c->calls_bound = 0;
+    c->step_failed = false;
     layout(c, A);
     if (!c->mem || c->mem_bytes < A.off) {
         if (c->mem) { cudaFree(c->mem); c->mem = nullptr; c->mem_bytes = 0; }
@@ -1723,6 +2019,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     UPR_CUDA(cudaMemsetAsync(c->tmp.epoch, 0, sizeof(uint32_t), s));
     UPR_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(RebalCtl), s));
     UPR_CUDA(cudaMemsetAsync(c->counts, 0, 64 * sizeof(int32_t), s));
+    UPR_CUDA(cudaMemsetAsync(c->Cd, 0, sizeof(long long) * (size_t)c->G.K(), s));
     fill_i32(c->pos, n, INT32_MAX, s);
     fill_i32(c->m_pos, n, -1, s);
     fill_i32(c->r_to, n, -1, s);
@@ -1788,7 +2085,7 @@ upr_status upr_create(const upr_graph *g, int32_t k, double eps, const upr_param
 void upr_destroy(upr_ctx *c) { free_ctx(c); }
 
 upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
-    if (!c || c->n < 0 || c->ng != 1 || !part || !cut) return UPR_ERR_INVALID;
+    if (!c || c->mix || c->n < 0 || c->ng != 1 || !part || !cut) return UPR_ERR_INVALID;
     try {
         upr_status st = load_part(c, part);
         if (st != UPR_OK) return st;
@@ -1804,7 +2101,7 @@ upr_status upr_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block
 
 upr_status upr_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_stats *stats) {
     (void)seed;
-    if (!c || c->n < 0 || c->ng != 1 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
+    if (!c || c->mix || c->n < 0 || c->ng != 1 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
     try {
         return refine_impl(c, part, rounds, stats, nullptr, nullptr, nullptr);
     } catch (const CudaError &e) {
@@ -1823,9 +2120,23 @@ upr_status upr_batch_create(const upr_graph *graphs, int32_t n_graphs, int32_t k
     return UPR_OK;
 }
 
+upr_status upr_batch_create_mixed(const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
+                                  const upr_params *params, upr_ctx **out) {
+    if (!out || !graphs || !eps || !k || n_graphs < 1) return UPR_ERR_INVALID;
+    upr_ctx *c = new (std::nothrow) upr_ctx();
+    if (!c) return UPR_ERR_OOM;
+    const upr_status st = upr::mixed_create(graphs, n_graphs, k, eps, params, &c->mix);
+    if (st != UPR_OK) { delete c; return st; }
+    c->n = upr::mixed_nodes(c->mix);
+    c->ng = n_graphs;
+    *out = c;
+    return UPR_OK;
+}
+
 upr_status upr_batch_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_status *status,
                             int64_t *cut_in, int64_t *cut_out, upr_stats *stats) {
     (void)seed;
+    if (c && c->mix) return upr::mixed_refine(c->mix, part, rounds, seed, status, cut_in, cut_out, stats);
     if (!c || c->n < 0 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
     try {
         upr_status rc = refine_impl(c, part, rounds, stats, status, cut_in, cut_out);
@@ -1846,6 +2157,7 @@ upr_status upr_batch_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t 
 }
 
 upr_status upr_batch_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
+    if (c && c->mix) return upr::mixed_cut(c->mix, part, cut, block_weights_out);
     if (!c || c->n < 0 || !part || !cut) return UPR_ERR_INVALID;
     try {
         upr_status st = load_part(c, part);
@@ -1859,6 +2171,7 @@ upr_status upr_batch_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t 
 }
 
 upr_status upr_batch_info(const upr_ctx *c, int32_t *n_graphs, int64_t *node_offsets, int64_t *lmax) {
+    if (c && c->mix) return upr::mixed_info(c->mix, n_graphs, node_offsets, lmax);
     if (!c || c->n < 0) return UPR_ERR_INVALID;
     if (n_graphs) *n_graphs = c->ng;
     if (node_offsets) memcpy(node_offsets, c->noff.data(), sizeof(int64_t) * (c->ng + 1));
@@ -1867,7 +2180,7 @@ upr_status upr_batch_info(const upr_ctx *c, int32_t *n_graphs, int64_t *node_off
 }
 
 upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int64_t *wI) {
-    if (!c || c->n < 0 || c->ng != 1 || !part) return UPR_ERR_INVALID;
+    if (!c || c->mix || c->n < 0 || c->ng != 1 || !part) return UPR_ERR_INVALID;
     try {
         upr_status rc = load_part(c, part);
         if (rc != UPR_OK) return rc;
@@ -1890,7 +2203,7 @@ upr_status upr_debug_gain_table(upr_ctx *c, const int32_t *part, int32_t *W, int
 }
 
 upr_status upr_debug_round(upr_ctx *c, int32_t *part, int32_t r, int32_t R, int32_t rebalance_only, upr_trace *trace) {
-    if (!c || c->n < 0 || c->ng != 1 || !part || !trace || R < 1 || R > 65536 ||
+    if (!c || c->mix || c->n < 0 || c->ng != 1 || !part || !trace || R < 1 || R > 65536 ||
         (!rebalance_only && (r < 1 || r > R)))
         return UPR_ERR_INVALID;
     int8_t *avail_d = nullptr;

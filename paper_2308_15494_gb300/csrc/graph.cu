@@ -171,6 +171,31 @@ __global__ void k_validate_nodes(const int64_t *__restrict__ xadj, const int32_t
     if (f) atomicOr(flags, f);
 }
 
+// The cut of a partition from its gain table (Sec. 2): every edge leaving v
+// is counted once from each end, so cut = (sum of omega(I(v)) - sum of
+// omega(v, V_P(v))) / 2; one read of the own-block entry per node instead of
+// a pass over the edges.  One graph; *out (zero) receives twice the cut
+// first, halved by the last step below.
+__global__ void k_cut_from_table(const GraphDev g, const int32_t *__restrict__ part, const int32_t *__restrict__ W,
+                                 unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long s_w[8];
+    unsigned long long acc = 0;
+    UPR_FOR(v, g.n) {
+        const int32_t own = g.sp.on() ? sp_get(g.sp, v, part[v]) : W[(int64_t)v * g.k + part[v]];
+        acc += (unsigned long long)((int64_t)g.wI[v] - own);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+        if (t) atomicAdd(out, t);
+    }
+}
+
+__global__ void k_halve(int64_t *x) { *x /= 2; }
+
 // Duplicate adjacency entries (E is a set of pairs {v, u}, Sec. 2, so a row
 // lists each neighbour once).  Rows of degree <= kHubDegree: a CTA takes the
 // rows that start in a chunk of kDupChunk entries (they may run into the
@@ -548,6 +573,15 @@ void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t
     int64_t warps = ceil_div(g.m, kChunk);
     k_edge_cut<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(g.xadj, g.adj, g.adjw, part, g.gid, g.n, g.m,
                                                                    (unsigned long long *)cut);
+    UPR_LAUNCH_CHECK();
+}
+
+void cut_from_table(const GraphDev &g, const int32_t *part, const int32_t *W, int64_t *cut, cudaStream_t s) {
+    UPR_CUDA(cudaMemsetAsync(cut, 0, sizeof(int64_t), s));
+    if (g.n == 0) return;
+    k_cut_from_table<<<grid_for(g.n), 256, 0, s>>>(g, part, W, (unsigned long long *)cut);
+    UPR_LAUNCH_CHECK();
+    k_halve<<<1, 1, 0, s>>>(cut);
     UPR_LAUNCH_CHECK();
 }
 

@@ -171,6 +171,8 @@ void block_weights(const GraphDev &g, const int32_t *part, int64_t *C, cudaStrea
 // cut[0..ng) = edge cut of each graph.
 void edge_cut(const GraphDev &g, const int32_t *part, int64_t *cut, cudaStream_t s);
 void incident_weights(const GraphDev &g, int32_t *wI, int64_t *wmax, cudaStream_t s);
+// *cut = the cut of part (one graph) from the gain table W = W(part) (dense or hashed rows) and omega(I(v)).
+void cut_from_table(const GraphDev &g, const int32_t *part, const int32_t *W, int64_t *cut, cudaStream_t s);
 // A tile of the table build: nodes [v0, v1) and the adjacency entries [e0, e1)
 // of its non-hub nodes (a hub, if any, is the tile's last node).
 struct TableTile { int64_t e0, e1; int32_t v0, v1; };
@@ -267,6 +269,10 @@ struct RebalState {
     const int8_t *excl;   // [K] not a target: overloaded at the first sub-round, or rejected a move
     const int32_t *light; // [ng] lightest non-excluded block of each graph, or -1
     const int64_t *Lb;    // [K] L_max of each block's graph
+    // optional (null: not written): per listed node i with a proposal, its
+    // block and gain by list index, so that later passes over the list read
+    // them in order instead of gathering them by node
+    int32_t *lsrc = nullptr, *lgain = nullptr;
 };
 // flags[v] = 1 for the nodes of the marked blocks
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s);
@@ -287,8 +293,6 @@ void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *
                          const int32_t *flags, const int32_t *prop_gain, const int32_t *part, const int8_t *over,
                          const int64_t *C, int gbits, int cbits, int gain_only, unsigned long long *hist,
                          int32_t *cut, int32_t *keep, cudaStream_t s);
-// gain_only: the priority is the gain alone (a variant of Sec. 7.2), else g/c
-// for g < 0 and g*c for g >= 0 (Sec. 6.1)
 // The four buffers of a two-array radix sort (keys and values, and their alternates).
 struct SortPairs { uint64_t *k, *ka; uint32_t *v, *va; };
 // A priority key wider than 63 bits (1 + gbits + 2 cbits > 63): the proposals
@@ -297,6 +301,60 @@ struct SortPairs { uint64_t *k, *ka; uint32_t *v, *va; };
 void rebalance_prio_sort_wide(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                               int gbits, int cbits, int gain_only, SortPairs sp, int64_t np_max, Scratch tmp,
                               cudaStream_t s, uint32_t **order);
+// ---- mixed.cu: one context over batches of different k (one batch per k)
+struct MixedBatch;
+upr_status mixed_create(const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
+                        const upr_params *params, MixedBatch **out);
+void mixed_destroy(MixedBatch *mb);
+int64_t mixed_nodes(const MixedBatch *mb);
+upr_status mixed_refine(MixedBatch *mb, int32_t *part, int32_t rounds, uint64_t seed, upr_status *status,
+                        int64_t *cut_in, int64_t *cut_out, upr_stats *stats);
+upr_status mixed_cut(MixedBatch *mb, const int32_t *part, int64_t *cut, int64_t *block_weights);
+upr_status mixed_info(const MixedBatch *mb, int32_t *n_graphs, int64_t *node_offsets, int64_t *lmax);
+
+// ---- reb_fused.cu: one rebalancing sub-round in fused passes (one graph,
+// K <= 256, a key of at most 63 bits, the prefilter on); same results as the
+// general form.  K * ceil(n / 2048) must not exceed the histogram buffers.
+bool rebalance_fused_ok(const GraphDev &g, int key_bits, bool prefilter);
+// list[0..*d_out) = the listed nodes with flags set (in place, in order), and
+// the prefilter's (source, bin) weights added to hist
+// (rep: [kPrioBins] one key per bin; *exact set to 1 for k_fr_keep_keys to clear)
+// (lgain, lsrc: the proposals' gains and blocks by list index, compacted with the list)
+void rebalance_fused_compact_hist(const GraphDev &g, const int32_t *flags, int32_t *list, const int32_t *d_n,
+                                  int64_t n_max, int32_t *d_out, int32_t *lgain, int32_t *lsrc, int gbits, int cbits,
+                                  int gain_only, unsigned long long *hist, uint64_t *rep, int32_t *exact, Scratch tmp,
+                                  cudaStream_t s);
+// (keys, vals)[0..*d_out) = (priority key, node) of the proposals whose bin is
+// not after their source's cut; *exact cleared when a kept key differs from its bin's rep
+void rebalance_fused_keep_keys(const GraphDev &g, const int32_t *list, const int32_t *d_n, int64_t n_max,
+                               const int32_t *lgain, const int32_t *lsrc, const int32_t *cut, int gbits, int cbits,
+                               int gain_only, uint64_t *keys, uint32_t *vals, int32_t *d_out, const uint64_t *rep,
+                               int32_t *exact, Scratch tmp, cudaStream_t s);
+// Stable sort of (keys, vals)[0..*d_n) by key (key_bits, an odd number of
+// 8-bit passes), or by the key's prefilter bin alone when *exact; the result
+// is in the alternate buffers (returns true).
+bool rebalance_fused_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const int32_t *d_n,
+                          int64_t n_max, int key_bits, int gbits, int cbits, const int32_t *exact, Scratch tmp,
+                          cudaStream_t s);
+// U[0..*d_np): proposals (nodes) in priority order.  Minimal prefix per
+// source, longest fitting prefix per target, the admitted appended to R at
+// ctl->nR (count *d_na), part / r_to / r_at updated, block-weight changes
+// added to Cd; sel (np int8) and the two histograms (K * ceil(np / 2048)
+// int64 each) are scratch.
+void rebalance_fused_select_admit(const GraphDev &g, const uint32_t *U, const int32_t *d_np, int64_t np_max,
+                                  int32_t *part, const int32_t *prop_tgt, const int64_t *C, int8_t *sel,
+                                  long long *h0, long long *h1, int32_t *d_hist_n, int8_t *reject,
+                                  const RebalCtl *ctl, int32_t *R_node, int32_t *R_from, int32_t *R_to,
+                                  int32_t *R_sub, int32_t *r_to, int32_t *r_at, long long *Cd, int32_t *d_na,
+                                  Scratch tmp, cudaStream_t s);
+// C += Cd, Cd = 0; then k_reb_end's update of the excluded set and the stop flag
+void rebalance_fused_end(const GraphDev &g, int64_t *C, long long *Cd, int8_t *excl, const int8_t *reject,
+                         const int32_t *d_na, RebalCtl *ctl, cudaStream_t s);
+// The prefilter's cut bin of every overloaded source (hist rows read are cleared).
+void rebalance_prio_cut(const GraphDev &g, const int8_t *over, const int64_t *C, unsigned long long *hist, int32_t *cut,
+                        cudaStream_t s);
+// gain_only: the priority is the gain alone (a variant of Sec. 7.2), else g/c
+// for g < 0 and g*c for g >= 0 (Sec. 6.1)
 void rebalance_prio_keys(const GraphDev &g, const int32_t *P, const int32_t *d_np, const int32_t *prop_gain,
                          int gbits, int cbits, int gain_only, uint64_t *keys, uint32_t *vals, int64_t np_max,
                          cudaStream_t s);
@@ -370,7 +428,7 @@ void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int3
 // pk: n words of scratch (each node's position in I and blocks before/after)
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                const int32_t *d_nI, int64_t max, const int32_t *part0, int2 *pk, int64_t *gain,
-               const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s);
+               const HubChunk *hub_chunks, int64_t n_chunks, int64_t *deg_sum, cudaStream_t s);
 void seq_iev_keys(const int32_t *I_from, const int32_t *I_to, const int32_t *d_nI, int64_t max, uint64_t *keys,
                   uint32_t *vals, cudaStream_t s);
 void seq_iev_delta(const int32_t *I_node, const uint32_t *EV, const uint64_t *ekeys, const int32_t *d_nI, int64_t max,

@@ -254,5 +254,42 @@ inline ScanState<T> scan_state(const Scratch &tmp, int64_t tiles_max) {
     return st;
 }
 
+constexpr int kBins = 256;
+
+// Stable ranking of the 8 x 256 items of a tile by digit (0..255, 256 = no item).
+// Item (round r, thread t) precedes (r', t') iff r < r' or (r == r' and t < t').
+// s_cnt: [2][kWarps][kBins+1] zero-initialised; s_run: [kBins+1] tile-local
+// running counts (zero-initialised).  Returns the rank within the tile among
+// items of the same digit.
+__device__ __forceinline__ void tile_rank(const int (&dig)[kItems], int (&rank)[kItems], int *s_cnt, int *s_run) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    constexpr int kStride = kWarps * (kBins + 1);
+#pragma unroll
+    for (int r = 0; r < kItems; r++) {
+        int *cnt = s_cnt + (r & 1) * kStride;
+        const int d = dig[r];
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int within = __popc(peers & lt);
+        if (within == 0) cnt[warp * (kBins + 1) + d] = __popc(peers);
+        __syncthreads();
+        // thread t owns digit t (t < 256); digit 256 (padding) is owned by thread 0 as well
+        for (int dd = threadIdx.x; dd <= kBins; dd += kThreads) {
+            int run = s_run[dd];
+            for (int w = 0; w < kWarps; w++) {
+                int c = cnt[w * (kBins + 1) + dd];
+                cnt[w * (kBins + 1) + dd] = run;
+                run += c;
+            }
+            s_run[dd] = run;
+            // clear the other buffer (used two rounds ago, read by everyone before the barrier above)
+            int *old = s_cnt + ((r + 1) & 1) * kStride;
+            for (int w = 0; w < kWarps; w++) old[w * (kBins + 1) + dd] = 0;
+        }
+        __syncthreads();
+        rank[r] = cnt[warp * (kBins + 1) + d] + within;
+    }
+}
+
 }  // namespace prim
 }  // namespace upr

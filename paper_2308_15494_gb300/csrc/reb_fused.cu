@@ -1,0 +1,775 @@
+// Step (d), one rebalancing sub-round (Sec. 6.1) in fewer, fused passes, for
+// one graph with K <= kFuseMaxK blocks, a one-word priority key and the
+// proposal prefilter.  It computes exactly what the general form in
+// rebalance.cu computes (the same proposals, the same minimal prefix per
+// source, the same longest fitting prefix per target, R in priority order),
+// but instead of sorting the kept proposals three times (by key, then by
+// source, then by target) it sorts them once by key and finds each
+// proposal's weight before it among the proposals of its source (then of its
+// target) from per-tile, per-block weight sums:
+//   1. compaction of the proposers (in place, node order) fused with the
+//      prefilter's (source, bin) weight histogram;
+//   2. the prefilter's cut bin per source (rebalance.cu, k_prio_cut);
+//   3. the kept proposals as (key, node) pairs, in node order;
+//   4. one stable radix sort by key;
+//   5. weights per (source, tile) of the sorted list, scanned;
+//   6. selection: weight before the proposal in its source = the scanned sum
+//      of earlier tiles + the weight of earlier items of the tile with the
+//      same source; selected iff that is below the source's excess; weights
+//      of the selected per (target, tile), scanned;
+//   7. admission in the same way per target (the inclusive weight fits the
+//      target's room), compaction of the admitted into R (look-back) and the
+//      moves applied; block-weight changes go to a delta array that the
+//      sub-round's end folds in, because C is read for admission meanwhile.
+#include "prim.cuh"
+
+namespace upr {
+namespace {
+
+using namespace prim;
+
+constexpr int kFuseMaxK = 256;
+constexpr int kDigits = kFuseMaxK + 1;          // blocks, and one digit for "no item"
+constexpr int kHistSlots = 2048;
+constexpr uint32_t kHistEmpty = 0xffffffffu;
+
+// The bin of a proposal: the same function as rebalance.cu's prefilter bins.
+__device__ __forceinline__ int prio_bin_f(int64_t g, uint64_t c, int cbits) {
+    if (g >= 0) {
+        const uint64_t v = (uint64_t)g * c;
+        return 127 - (int)(v < 127ull ? v : 127ull);
+    }
+    const uint64_t r = (((uint64_t)(-g)) << cbits) / c;
+    return 128 + (int)(r < 127ull ? r : 127ull);
+}
+
+// The one-word priority key (ascending = higher priority first): class 0
+// (g >= 0) (2^(gb+cb) - 1) - g*c, class 1 (g < 0) 2^(gb+2cb) + floor(|g|
+// 2^(2cb) / c); the same function as rebalance.cu's prio_key.
+__device__ __forceinline__ uint64_t prio_key_f(int64_t g, uint64_t c, int gbits, int cbits) {
+    const int S = 2 * cbits;
+    if (g >= 0) return ((1ull << (gbits + cbits)) - 1ull) - (uint64_t)g * c;
+    const uint64_t num = ((uint64_t)(-g)) << S;
+    return (1ull << (gbits + S)) | (c == 1 ? num : num / c);
+}
+
+// Weighted ranks inside a tile: before[r] = the weight of the earlier items
+// of the tile (item (r, t) precedes (r', t') iff r < r' or r == r' and
+// t < t') with the same digit; digit K = no item.  s_cnt: [2][kWarps][K+1]
+// and s_run: [K+1], zero on entry, zero again on return.
+template <bool UNIT>
+__device__ __forceinline__ void tile_wprefix(const int (&dig)[kItems], const int64_t (&w)[kItems],
+                                             int64_t (&before)[kItems], int64_t *s_cnt, int64_t *s_run, int K) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int stride = kWarps * (K + 1);
+#pragma unroll
+    for (int r = 0; r < kItems; r++) {
+        int64_t *cnt = s_cnt + (r & 1) * stride;
+        const int d = dig[r];
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        int64_t within;
+        if (UNIT) {
+            within = __popc(peers & lt);
+            if ((peers & lt) == 0) cnt[warp * (K + 1) + d] = __popc(peers);
+        } else {
+            within = 0;
+            for (int j = 0; j < 32; j++) {
+                const int dj = __shfl_sync(0xffffffffu, d, j);
+                const int64_t wj = __shfl_sync(0xffffffffu, w[r], j);
+                if (j < lane && dj == d) within += wj;
+            }
+            if (lane == 31 - __clz(peers)) cnt[warp * (K + 1) + d] = within + w[r];     // last of the group
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd <= K; dd += kThreads) {
+            int64_t run = s_run[dd];
+            for (int q = 0; q < kWarps; q++) {
+                const int64_t c = cnt[q * (K + 1) + dd];
+                cnt[q * (K + 1) + dd] = run;
+                run += c;
+            }
+            s_run[dd] = run;
+            int64_t *old = s_cnt + ((r + 1) & 1) * stride;     // read by everyone before the barrier above
+            for (int q = 0; q < kWarps; q++) old[q * (K + 1) + dd] = 0;
+        }
+        __syncthreads();
+        before[r] = cnt[warp * (K + 1) + d] + within;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < stride; i += kThreads) s_cnt[((kItems - 1) & 1) * stride + i] = 0;
+    for (int dd = threadIdx.x; dd <= K; dd += kThreads) s_run[dd] = 0;
+    __syncthreads();
+}
+
+// Per-warp accumulation without atomics: the lanes holding the same digit
+// form a group (__match_any_sync); the group's first lane adds the group's
+// weight to the warp's own slot of that digit.  Items of a tile sorted by
+// priority often share their block, so shared-memory atomics would queue on
+// one address.  acc: this warp's K slots; valid = false: no item.
+template <bool UNIT>
+__device__ __forceinline__ void warp_acc(int d, int64_t w, bool valid, int64_t *acc) {
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : -1);
+    int64_t tot;
+    if (UNIT) {
+        tot = (int64_t)__popc(peers) * w;        // the group's items share w (+1 or -1)
+    } else {
+        tot = 0;
+        for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, w, __ffs(m) - 1);
+    }
+    if (valid && lane == __ffs(peers) - 1) acc[d] += tot;
+}
+
+// Sum of the warps' slots of digit i (threads i < K), then the slots cleared.
+__device__ __forceinline__ int64_t warps_total(int64_t *s_acc, int K, int i) {
+    int64_t t = 0;
+    for (int q = 0; q < kWarps; q++) {
+        t += s_acc[q * K + i];
+        s_acc[q * K + i] = 0;
+    }
+    return t;
+}
+
+// ---- 1. proposers compacted in place (node order) + prefilter histogram
+__global__ void __launch_bounds__(kThreads) k_fr_compact_hist(const int32_t *__restrict__ flags, int32_t *list,
+                                                              const int32_t *__restrict__ d_n, int32_t *__restrict__ d_out,
+                                                              int32_t *lgain, const int32_t *__restrict__ vwgt,
+                                                              int32_t *lsrc, int gbits, int cbits,
+                                                              int gain_only, unsigned long long *__restrict__ hist,
+                                                              uint64_t *__restrict__ rep, int32_t *__restrict__ exact,
+                                                              int vec, ScanState<int32_t> st) {
+    __shared__ int32_t s_warp[kWarps];
+    __shared__ int32_t s_excl;
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_key[kHistSlots];
+    __shared__ unsigned long long s_val[kHistSlots];
+    __shared__ uint64_t s_rep[kPrioBins];
+    __shared__ int s_has[kPrioBins];
+    const int64_t n = *d_n;
+    const int64_t tiles = tiles_of(n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *exact = 1;                              // until k_fr_keep_keys finds a bin holding two keys
+        if (tiles == 0) *d_out = 0;
+    }
+    const unsigned parts = participants(tiles);
+    if (blockIdx.x >= parts) return;
+    for (int i = threadIdx.x; i < kHistSlots; i += kThreads) { s_key[i] = kHistEmpty; s_val[i] = 0; }
+    for (int i = threadIdx.x; i < kPrioBins; i += kThreads) s_has[i] = 0;
+    __syncthreads();
+    const bool alone = tiles == 1;
+    const uint32_t epoch = alone ? 0u : call_epoch(st);
+    for (;;) {
+        const int64_t tile = alone ? (int64_t)blockIdx.x : next_tile(st.ctr, &s_tile);
+        if (tile >= tiles) break;
+        int32_t x[kItems], y[kItems], ya[kItems], yg[kItems];
+        load_items(flags, tile * kTile, n, (vec & 1) != 0, x);
+        load_items((const int32_t *)list, tile * kTile, n, (vec & 2) != 0, y);
+        load_items((const int32_t *)lsrc, tile * kTile, n, (vec & 2) != 0, ya);
+        load_items((const int32_t *)lgain, tile * kTile, n, (vec & 2) != 0, yg);
+        int32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) c += x[j] != 0;
+        int32_t total;
+        const int32_t pre = block_exclusive<OpSum>(c, s_warp, &total);
+        if (threadIdx.x < 32) {
+            const int32_t e = alone ? 0 : lookback<OpSum>(st, tile, total, epoch);
+            if (threadIdx.x == 0) {
+                s_excl = e;
+                if (tile == tiles - 1) *d_out = e + total;
+            }
+        }
+        __syncthreads();
+        int32_t pos = s_excl + pre;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            if (!x[j]) continue;
+            const int32_t u = y[j];
+            list[pos] = u;
+            lsrc[pos] = ya[j];
+            lgain[pos] = yg[j];
+            pos++;
+            const uint64_t cu = vwgt ? (uint64_t)vwgt[u] : 1ull;
+            const int64_t gu = yg[j];
+            const int bin = prio_bin_f(gu, gain_only ? 1ull : cu, cbits);
+            // some proposal's key per bin (any one: plain stores race, one
+            // wins), in shared memory first: one global store per bin and CTA
+            s_rep[bin] = prio_key_f(gu, gain_only ? 1ull : cu, gbits, cbits);
+            s_has[bin] = 1;
+            const uint32_t key = (uint32_t)ya[j] * kPrioBins + bin;
+            uint32_t h = (key * 0x9E3779B1u) >> 21;          // 11 bits: kHistSlots
+            bool done = false;
+            for (int probe = 0; probe < 32 && !done; probe++) {
+                uint32_t cur = s_key[h];
+                if (cur == kHistEmpty) {
+                    cur = atomicCAS(&s_key[h], kHistEmpty, key);
+                    if (cur == kHistEmpty) cur = key;
+                }
+                if (cur == key) {
+                    atomicAdd(&s_val[h], (unsigned long long)cu);
+                    done = true;
+                }
+                h = (h + 1) & (kHistSlots - 1);
+            }
+            if (!done) atomicAdd(&hist[key], (unsigned long long)cu);   // crowded table: straight to the histogram
+        }
+        __syncthreads();
+        if (alone) break;
+    }
+    if (!alone) finish_tiles(st, parts, epoch);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHistSlots; i += kThreads)
+        if (s_key[i] != kHistEmpty) atomicAdd(&hist[s_key[i]], s_val[i]);
+    for (int i = threadIdx.x; i < kPrioBins; i += kThreads)
+        if (s_has[i]) rep[i] = s_rep[i];
+}
+
+// ---- 3. kept proposals (bin not after their source's cut) as (key, node)
+__global__ void __launch_bounds__(kThreads) k_fr_keep_keys(const int32_t *__restrict__ list, const int32_t *__restrict__ d_n,
+                                                           const int32_t *__restrict__ lgain,
+                                                           const int32_t *__restrict__ vwgt,
+                                                           const int32_t *__restrict__ lsrc,
+                                                           const int32_t *__restrict__ cut, int gbits, int cbits,
+                                                           int gain_only, uint64_t *__restrict__ keys,
+                                                           uint32_t *__restrict__ vals, int32_t *__restrict__ d_out,
+                                                           const uint64_t *__restrict__ rep,
+                                                           int32_t *__restrict__ exact, ScanState<int32_t> st) {
+    __shared__ int32_t s_warp[kWarps];
+    __shared__ int32_t s_excl;
+    __shared__ uint32_t s_tile;
+    const int64_t n = *d_n;
+    const int64_t tiles = tiles_of(n);
+    if (tiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_out = 0;
+    const unsigned parts = participants(tiles);
+    if (blockIdx.x >= parts) return;
+    const bool alone = tiles == 1;
+    const uint32_t epoch = alone ? 0u : call_epoch(st);
+    for (;;) {
+        const int64_t tile = alone ? (int64_t)blockIdx.x : next_tile(st.ctr, &s_tile);
+        if (tile >= tiles) break;
+        const int64_t first = tile * kTile + (int64_t)threadIdx.x * kItems;
+        uint64_t key[kItems];
+        int32_t u[kItems];
+        int32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            u[j] = -1;
+            if (first + j < n) {
+                const int32_t v = list[first + j];
+                const uint64_t cv = (vwgt && !gain_only) ? (uint64_t)vwgt[v] : 1ull;
+                const int64_t g = lgain[first + j];
+                const int bin = prio_bin_f(g, cv, cbits);
+                if (bin <= cut[lsrc[first + j]]) {
+                    u[j] = v;
+                    key[j] = prio_key_f(g, cv, gbits, cbits);
+                    if (key[j] != rep[bin]) *exact = 0;
+                    c++;
+                }
+            }
+        }
+        int32_t total;
+        const int32_t pre = block_exclusive<OpSum>(c, s_warp, &total);
+        if (threadIdx.x < 32) {
+            const int32_t e = alone ? 0 : lookback<OpSum>(st, tile, total, epoch);
+            if (threadIdx.x == 0) {
+                s_excl = e;
+                if (tile == tiles - 1) *d_out = e + total;
+            }
+        }
+        __syncthreads();
+        int32_t pos = s_excl + pre;
+#pragma unroll
+        for (int j = 0; j < kItems; j++)
+            if (u[j] >= 0) { keys[pos] = key[j]; vals[pos] = (uint32_t)u[j]; pos++; }
+        __syncthreads();
+        if (alone) break;
+    }
+    if (!alone) finish_tiles(st, parts, epoch);
+}
+
+// ---- 4. the stable sort of the kept proposals by key.  The bin of a key is
+// non-decreasing in the key; when every bin holds one key value (the flag
+// `exact`, e.g. unit weights with small gains), sorting by the bin alone gives
+// the key order, so pass 0 sorts by the bin and the later passes do nothing.
+// With an odd number of passes the result lands in the same buffer either way.
+__device__ __forceinline__ int bin_of_key(uint64_t key, int gbits, int cbits) {
+    const uint64_t top = 1ull << (gbits + 2 * cbits);
+    if (key < top) {
+        const uint64_t v = ((1ull << (gbits + cbits)) - 1ull) - key;     // g * c
+        return 127 - (int)(v < 127ull ? v : 127ull);
+    }
+    const uint64_t r = (key - top) >> cbits;                            // floor(|g| 2^cb / c)
+    return 128 + (int)(r < 127ull ? r : 127ull);
+}
+
+__device__ __forceinline__ int sort_digit(uint64_t key, int pass, bool exact, int gbits, int cbits) {
+    return exact ? bin_of_key(key, gbits, cbits) : (int)((key >> (8 * pass)) & 0xFF);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fr_radix_hist(const uint64_t *__restrict__ keys,
+                                                            const int32_t *__restrict__ d_n, int pass, int gbits,
+                                                            int cbits, const int32_t *__restrict__ d_exact,
+                                                            int32_t *__restrict__ hist, int32_t *__restrict__ d_hist_n) {
+    __shared__ int s_h[kBins];
+    const int64_t n = *d_n;
+    const bool exact = *d_exact != 0;
+    const bool skip = n <= kTile || (exact && pass > 0);
+    const int64_t T = tiles_of(n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_hist_n = skip ? 0 : (int32_t)(kBins * T);
+    if (skip) return;
+    for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < kBins; i += kThreads) s_h[i] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int64_t g = tile * kTile + r * kThreads + threadIdx.x;
+            if (g < n) atomicAdd(&s_h[sort_digit(keys[g], pass, exact, gbits, cbits)], 1);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kBins; i += kThreads) hist[(int64_t)i * T + tile] = s_h[i];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fr_radix_scatter(const uint64_t *__restrict__ keys,
+                                                               const uint32_t *__restrict__ vals,
+                                                               uint64_t *__restrict__ okeys, uint32_t *__restrict__ ovals,
+                                                               const int32_t *__restrict__ d_n, int pass, int gbits,
+                                                               int cbits, const int32_t *__restrict__ d_exact,
+                                                               const int32_t *__restrict__ offs) {
+    __shared__ int s_cnt[2 * kWarps * (kBins + 1)];
+    __shared__ int s_run[kBins + 1];
+    __shared__ int s_off[kBins];
+    const int64_t n = *d_n;
+    const bool exact = *d_exact != 0;
+    if (n <= kTile || (exact && pass > 0)) return;
+    const int64_t T = tiles_of(n);
+    for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
+        for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
+        for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = offs[(int64_t)i * T + tile];
+        __syncthreads();
+        uint64_t k[kItems];
+        uint32_t v[kItems];
+        int dig[kItems], rank[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int64_t g = tile * kTile + r * kThreads + threadIdx.x;
+            if (g < n) { k[r] = keys[g]; v[r] = vals[g]; dig[r] = sort_digit(k[r], pass, exact, gbits, cbits); }
+            else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
+        }
+        tile_rank(dig, rank, s_cnt, s_run);
+#pragma unroll
+        for (int r = 0; r < kItems; r++)
+            if (dig[r] < kBins) {
+                const int64_t p = (int64_t)s_off[dig[r]] + rank[r];
+                okeys[p] = k[r];
+                ovals[p] = v[r];
+            }
+        __syncthreads();
+    }
+}
+
+// A list of at most one tile: every pass in one CTA (one pass by the bin when exact).
+__global__ void __launch_bounds__(kThreads) k_fr_radix_small(const uint64_t *__restrict__ keys,
+                                                             const uint32_t *__restrict__ vals, uint64_t *okeys,
+                                                             uint32_t *ovals, const int32_t *__restrict__ d_n,
+                                                             int passes, int gbits, int cbits,
+                                                             const int32_t *__restrict__ d_exact) {
+    __shared__ int s_cnt[2 * kWarps * (kBins + 1)];
+    __shared__ int s_run[kBins + 1];
+    __shared__ int s_off[kBins];
+    __shared__ int s_warp[kWarps];
+    __shared__ uint64_t s_k[kTile];
+    __shared__ uint32_t s_v[kTile];
+    const int64_t n64 = *d_n;
+    if (n64 > kTile || n64 <= 0) return;
+    const int n = (int)n64;
+    const bool exact = *d_exact != 0;
+    for (int i = threadIdx.x; i < n; i += kThreads) { s_k[i] = keys[i]; s_v[i] = vals[i]; }
+    for (int p = 0; p < (exact ? 1 : passes); p++) {
+        for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
+        for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
+        for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = 0;
+        __syncthreads();
+        uint64_t k[kItems];
+        uint32_t v[kItems];
+        int dig[kItems], rank[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int g = r * kThreads + threadIdx.x;
+            if (g < n) {
+                k[r] = s_k[g]; v[r] = s_v[g];
+                dig[r] = sort_digit(k[r], p, exact, gbits, cbits);
+                atomicAdd(&s_off[dig[r]], 1);
+            } else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
+        }
+        __syncthreads();
+        const int c = threadIdx.x < kBins ? s_off[threadIdx.x] : 0;
+        int total;
+        const int ex = block_exclusive<OpSum>(c, s_warp, &total);
+        if (threadIdx.x < kBins) s_off[threadIdx.x] = ex;
+        __syncthreads();
+        tile_rank(dig, rank, s_cnt, s_run);
+#pragma unroll
+        for (int r = 0; r < kItems; r++)
+            if (dig[r] < kBins) { const int q = s_off[dig[r]] + rank[r]; s_k[q] = k[r]; s_v[q] = v[r]; }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += kThreads) { okeys[i] = s_k[i]; ovals[i] = s_v[i]; }
+}
+
+// Item (r, t) of a tile: index base + r * kThreads + t (the radix order).
+__device__ __forceinline__ int64_t item_at(int64_t tile, int r) { return tile * kTile + r * kThreads + threadIdx.x; }
+
+// ---- 5. weight of the sorted proposals per (source, tile), block-major
+template <bool UNIT>
+__global__ void __launch_bounds__(kThreads) k_fr_src_hist(const uint32_t *__restrict__ U, const int32_t *__restrict__ d_n,
+                                                          const int32_t *__restrict__ part,
+                                                          const int32_t *__restrict__ vwgt, int K,
+                                                          long long *__restrict__ hw, int32_t *__restrict__ d_hist_n) {
+    __shared__ int64_t s_acc[kWarps * kFuseMaxK];
+    const int64_t n = *d_n;
+    const int64_t T = tiles_of(n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_hist_n = (int32_t)(K * T);
+    int64_t *acc = s_acc + (threadIdx.x >> 5) * K;
+    for (int i = threadIdx.x; i < kWarps * K; i += kThreads) s_acc[i] = 0;
+    __syncthreads();
+    for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int64_t g = item_at(tile, r);
+            const bool ok = g < n;
+            const uint32_t u = ok ? U[g] : 0;
+            warp_acc<UNIT>(ok ? part[u] : 0, (ok && vwgt) ? vwgt[u] : 1, ok, acc);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += kThreads) hw[(int64_t)i * T + tile] = warps_total(s_acc, K, i);
+        __syncthreads();
+    }
+}
+
+// ---- 6. selection per source; weights of the selected per (target, tile)
+template <bool UNIT>
+__global__ void __launch_bounds__(kThreads) k_fr_select(const uint32_t *__restrict__ U, const int32_t *__restrict__ d_n,
+                                                        const int32_t *__restrict__ part,
+                                                        const int32_t *__restrict__ vwgt,
+                                                        const int32_t *__restrict__ prop_tgt, int K,
+                                                        const int64_t *__restrict__ C, const int64_t *__restrict__ Lb,
+                                                        const long long *__restrict__ hw_ex, int8_t *__restrict__ sel,
+                                                        long long *__restrict__ ht, int32_t *__restrict__ d_hist_n) {
+    // the warps' accumulators share the ranks' counters: tile_wprefix leaves
+    // them zero, warps_total leaves them zero again
+    __shared__ int64_t s_cnt[2 * kWarps * kDigits];
+    __shared__ int64_t s_run[kDigits];
+    int64_t *s_acc = s_cnt;
+    const int64_t n = *d_n;
+    const int64_t T = tiles_of(n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_hist_n = (int32_t)(K * T);
+    for (int i = threadIdx.x; i < 2 * kWarps * (K + 1); i += kThreads) s_cnt[i] = 0;
+    for (int i = threadIdx.x; i <= K; i += kThreads) s_run[i] = 0;
+    int64_t *acc = s_acc + (threadIdx.x >> 5) * K;
+    __syncthreads();
+    for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
+        int dig[kItems];
+        int64_t w[kItems], before[kItems];
+        uint32_t u[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int64_t g = item_at(tile, r);
+            if (g < n) {
+                u[r] = U[g];
+                dig[r] = part[u[r]];
+                w[r] = vwgt ? vwgt[u[r]] : 1;
+            } else {
+                u[r] = 0;
+                dig[r] = K;
+                w[r] = 0;
+            }
+        }
+        tile_wprefix<UNIT>(dig, w, before, s_cnt, s_run, K);
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int64_t g = item_at(tile, r);
+            bool s = false;
+            if (g < n) {
+                const int a = dig[r];
+                const int64_t prior = hw_ex[(int64_t)a * T + tile] - hw_ex[(int64_t)a * T] + before[r];
+                s = prior < C[a] - Lb[a];
+                sel[g] = s ? 1 : 0;
+            }
+            warp_acc<UNIT>(s ? prop_tgt[u[r]] : 0, w[r], s, acc);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += kThreads) ht[(int64_t)i * T + tile] = warps_total(s_acc, K, i);
+        __syncthreads();
+    }
+}
+
+// ---- 7. admission per target, compaction of the admitted into R, moves applied
+template <bool UNIT>
+__global__ void __launch_bounds__(kThreads) k_fr_admit(const uint32_t *__restrict__ U, const int32_t *__restrict__ d_n,
+                                                       const int8_t *__restrict__ sel, int32_t *__restrict__ part,
+                                                       const int32_t *__restrict__ vwgt,
+                                                       const int32_t *__restrict__ prop_tgt, int K,
+                                                       const int64_t *__restrict__ C, const int64_t *__restrict__ Lb,
+                                                       const long long *__restrict__ ht_ex,
+                                                       int8_t *__restrict__ reject, const RebalCtl *__restrict__ ctl,
+                                                       int32_t *__restrict__ R_node, int32_t *__restrict__ R_from,
+                                                       int32_t *__restrict__ R_to, int32_t *__restrict__ R_sub,
+                                                       int32_t *__restrict__ r_to, int32_t *__restrict__ r_at,
+                                                       long long *__restrict__ Cd, int32_t *__restrict__ d_out,
+                                                       ScanState<int32_t> st) {
+    // the warps' accumulators share the ranks' counters (see k_fr_select)
+    __shared__ int64_t s_cnt[2 * kWarps * kDigits];
+    __shared__ int64_t s_run[kDigits];
+    int64_t *s_acc = s_cnt;
+    __shared__ uint64_t s_w64[kWarps];
+    __shared__ int32_t s_excl;
+    __shared__ uint32_t s_tile;
+    const int64_t n = *d_n;
+    const int64_t T = tiles_of(n);
+    if (T == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_out = 0;
+    const unsigned parts = participants(T);
+    if (blockIdx.x >= parts) return;
+    for (int i = threadIdx.x; i < 2 * kWarps * (K + 1); i += kThreads) s_cnt[i] = 0;
+    for (int i = threadIdx.x; i <= K; i += kThreads) s_run[i] = 0;
+    int64_t *acc = s_acc + (threadIdx.x >> 5) * K;
+    __syncthreads();
+    const int64_t off = ctl->nR;
+    const int32_t subround = ctl->subrounds;
+    const bool alone = T == 1;
+    const uint32_t epoch = alone ? 0u : call_epoch(st);
+    for (;;) {
+        const int64_t tile = alone ? (int64_t)blockIdx.x : next_tile(st.ctr, &s_tile);
+        if (tile >= T) break;
+        int dig[kItems];
+        int64_t w[kItems], before[kItems];
+        uint32_t u[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int64_t g = item_at(tile, r);
+            dig[r] = K;
+            w[r] = 0;
+            u[r] = 0;
+            if (g < n) {
+                u[r] = U[g];
+                if (sel[g]) {
+                    dig[r] = prop_tgt[u[r]];
+                    w[r] = vwgt ? vwgt[u[r]] : 1;
+                }
+            }
+        }
+        tile_wprefix<UNIT>(dig, w, before, s_cnt, s_run, K);
+        // admitted: the weight of the target's selected proposals up to this one fits
+        bool adm[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            adm[r] = false;
+            const int b = dig[r];
+            if (b == K) continue;
+            const int64_t incl = ht_ex[(int64_t)b * T + tile] - ht_ex[(int64_t)b * T] + before[r] + w[r];
+            adm[r] = C[b] + incl <= Lb[b];
+            if (!adm[r]) reject[b] = 1;
+        }
+        // R keeps the sorted (priority) order, which inside a tile is item
+        // order (round-major): per-round counts packed 16 bits each into two
+        // words, one block scan per word
+        uint64_t lo = 0, hi = 0;
+#pragma unroll
+        for (int r = 0; r < kItems; r++)
+            if (adm[r]) {
+                if (r < 4) lo += 1ull << (16 * r);
+                else hi += 1ull << (16 * (r - 4));
+            }
+        uint64_t tlo, thi;
+        const uint64_t plo = block_exclusive<OpSum>(lo, s_w64, &tlo);
+        const uint64_t phi = block_exclusive<OpSum>(hi, s_w64, &thi);
+        int32_t total = 0;
+#pragma unroll
+        for (int r = 0; r < kItems; r++) total += (int32_t)(((r < 4 ? tlo : thi) >> (16 * (r & 3))) & 0xFFFF);
+        if (threadIdx.x < 32) {
+            const int32_t e = alone ? 0 : lookback<OpSum>(st, tile, total, epoch);
+            if (threadIdx.x == 0) {
+                s_excl = e;
+                if (tile == T - 1) *d_out = e + total;
+            }
+        }
+        __syncthreads();
+        int32_t mine[kItems];
+        {
+            int32_t base = s_excl;
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int sh = 16 * (r & 3);
+                mine[r] = base + (int32_t)(((r < 4 ? plo : phi) >> sh) & 0xFFFF);
+                base += (int32_t)(((r < 4 ? tlo : thi) >> sh) & 0xFFFF);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            int32_t a = 0;
+            const int32_t b = dig[r];
+            if (adm[r]) {
+                const int32_t v = (int32_t)u[r];
+                a = part[v];
+                const int64_t p = off + mine[r];
+                R_node[p] = v;
+                R_from[p] = a;
+                R_to[p] = b;
+                R_sub[p] = subround;
+                r_to[v] = b;
+                r_at[v] = (int32_t)p;
+                part[v] = b;
+            }
+            warp_acc<UNIT>(a, -w[r], adm[r], acc);
+            __syncwarp();
+            warp_acc<UNIT>(b, w[r], adm[r], acc);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += kThreads) {
+            const int64_t d = warps_total(s_acc, K, i);
+            if (d) atomicAdd(reinterpret_cast<unsigned long long *>(&Cd[i]), (unsigned long long)d);
+        }
+        __syncthreads();
+        if (alone) break;
+    }
+    if (!alone) finish_tiles(st, parts, epoch);
+}
+
+// ---- end of the sub-round: the block-weight changes folded in, then the
+// targets that rejected a move excluded; stop when nothing was admitted and
+// no target was newly excluded, or when no block is overloaded any more.
+__global__ void k_fr_end(int64_t *__restrict__ C, long long *__restrict__ Cd, const int64_t *__restrict__ Lb, int32_t K,
+                         int8_t *__restrict__ excl, const int8_t *__restrict__ reject, const int32_t *__restrict__ d_na,
+                         RebalCtl *__restrict__ ctl) {
+    __shared__ int s_grew, s_over;
+    if (threadIdx.x == 0) s_grew = 0, s_over = 0;
+    __syncthreads();
+    const bool active = ctl->active != 0;
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
+        const int64_t c = C[b] + Cd[b];
+        C[b] = c;
+        Cd[b] = 0;
+        if (!active) continue;
+        if (reject[b] && !excl[b]) { excl[b] = 1; s_grew = 1; }
+        if (c > Lb[b]) s_over = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && active) {
+        const int32_t na = *d_na;
+        ctl->nR += na;
+        if ((na == 0 && !s_grew) || !s_over) ctl->stopped = 1;
+    }
+}
+
+}  // namespace
+
+bool rebalance_fused_ok(const GraphDev &g, int key_bits, bool prefilter) {
+    return g.ng == 1 && g.K() <= kFuseMaxK && key_bits <= 63 && prefilter && (((key_bits + 7) / 8) & 1);
+}
+
+void rebalance_fused_compact_hist(const GraphDev &g, const int32_t *flags, int32_t *list, const int32_t *d_n,
+                                  int64_t n_max, int32_t *d_out, int32_t *lgain, int32_t *lsrc, int gbits, int cbits,
+                                  int gain_only, unsigned long long *hist, uint64_t *rep, int32_t *exact, Scratch tmp,
+                                  cudaStream_t s) {
+    if (n_max <= 0) { UPR_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int32_t), s)); return; }
+    const int vec = (aligned16(flags) ? 1 : 0) |
+                    (aligned16(list) && aligned16(lgain) && aligned16(lsrc) ? 2 : 0);
+    const int64_t tiles_max = ceil_div(n_max, kTile);
+    k_fr_compact_hist<<<tile_grid((const void *)k_fr_compact_hist, tiles_max), kThreads, 0, s>>>(
+        flags, list, d_n, d_out, lgain, g.vwgt, lsrc, gbits, cbits, gain_only, hist, rep, exact, vec,
+        scan_state<int32_t>(tmp, tiles_max));
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_fused_keep_keys(const GraphDev &g, const int32_t *list, const int32_t *d_n, int64_t n_max,
+                               const int32_t *lgain, const int32_t *lsrc, const int32_t *cut, int gbits, int cbits,
+                               int gain_only, uint64_t *keys, uint32_t *vals, int32_t *d_out, const uint64_t *rep,
+                               int32_t *exact, Scratch tmp, cudaStream_t s) {
+    if (n_max <= 0) { UPR_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int32_t), s)); return; }
+    const int64_t tiles_max = ceil_div(n_max, kTile);
+    k_fr_keep_keys<<<tile_grid((const void *)k_fr_keep_keys, tiles_max), kThreads, 0, s>>>(
+        list, d_n, lgain, g.vwgt, lsrc, cut, gbits, cbits, gain_only, keys, vals, d_out, rep, exact,
+        scan_state<int32_t>(tmp, tiles_max));
+    UPR_LAUNCH_CHECK();
+}
+
+bool rebalance_fused_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const int32_t *d_n,
+                          int64_t n_max, int key_bits, int gbits, int cbits, const int32_t *exact, Scratch tmp,
+                          cudaStream_t s) {
+    const int passes = (key_bits + 7) / 8;
+    if (!(passes & 1)) throw CudaError{cudaErrorInvalidValue, "rebalance_fused_sort: even pass count"};
+    if (n_max <= 0) return true;
+    k_fr_radix_small<<<1, kThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, d_n, passes, gbits, cbits, exact);
+    UPR_LAUNCH_CHECK();
+    if (n_max <= kTile) return true;
+    const int64_t tiles_max = ceil_div(n_max, kTile);
+    if (tiles_max > tmp.tiles_cap) throw CudaError{cudaErrorInvalidValue, "sort longer than the scratch"};
+    int32_t *hist = reinterpret_cast<int32_t *>(tmp.mem);
+    int32_t *d_hist_n = hist + (size_t)kBins * tmp.tiles_cap;
+    const unsigned grid_h = wave_grid((const void *)k_fr_radix_hist, kThreads, 0, tiles_max);
+    const unsigned grid_s = wave_grid((const void *)k_fr_radix_scatter, kThreads, 0, tiles_max);
+    uint64_t *ka = keys, *kb = keys_alt;
+    uint32_t *va = vals, *vb = vals_alt;
+    for (int p = 0; p < passes; p++) {
+        k_fr_radix_hist<<<grid_h, kThreads, 0, s>>>(ka, d_n, p, gbits, cbits, exact, hist, d_hist_n);
+        UPR_LAUNCH_CHECK();
+        exclusive_sum_i32(hist, hist, Count{d_hist_n, (int64_t)kBins * tiles_max}, tmp, s);
+        k_fr_radix_scatter<<<grid_s, kThreads, 0, s>>>(ka, va, kb, vb, d_n, p, gbits, cbits, exact, hist);
+        UPR_LAUNCH_CHECK();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    return true;
+}
+
+void rebalance_fused_select_admit(const GraphDev &g, const uint32_t *U, const int32_t *d_np, int64_t np_max,
+                                  int32_t *part, const int32_t *prop_tgt, const int64_t *C, int8_t *sel,
+                                  long long *h0, long long *h1, int32_t *d_hist_n, int8_t *reject,
+                                  const RebalCtl *ctl, int32_t *R_node, int32_t *R_from, int32_t *R_to,
+                                  int32_t *R_sub, int32_t *r_to, int32_t *r_at, long long *Cd, int32_t *d_na,
+                                  Scratch tmp, cudaStream_t s) {
+    if (np_max <= 0) { UPR_CUDA(cudaMemsetAsync(d_na, 0, sizeof(int32_t), s)); return; }
+    const int K = g.K();
+    const int64_t tiles_max = ceil_div(np_max, kTile);
+    const Count ch{d_hist_n, (int64_t)K * tiles_max};
+    const bool unit = g.vwgt == nullptr;
+    if (unit) {
+        const unsigned gh = wave_grid((const void *)k_fr_src_hist<true>, kThreads, 0, tiles_max);
+        k_fr_src_hist<true><<<gh, kThreads, 0, s>>>(U, d_np, part, g.vwgt, K, h0, d_hist_n);
+    } else {
+        const unsigned gh = wave_grid((const void *)k_fr_src_hist<false>, kThreads, 0, tiles_max);
+        k_fr_src_hist<false><<<gh, kThreads, 0, s>>>(U, d_np, part, g.vwgt, K, h0, d_hist_n);
+    }
+    UPR_LAUNCH_CHECK();
+    exclusive_sum_i64((const int64_t *)h0, (int64_t *)h1, ch, tmp, s);
+    if (unit) {
+        const unsigned gs = wave_grid((const void *)k_fr_select<true>, kThreads, 0, tiles_max);
+        k_fr_select<true><<<gs, kThreads, 0, s>>>(U, d_np, part, g.vwgt, prop_tgt, K, C, g.Lb, h1, sel, h0, d_hist_n);
+    } else {
+        const unsigned gs = wave_grid((const void *)k_fr_select<false>, kThreads, 0, tiles_max);
+        k_fr_select<false><<<gs, kThreads, 0, s>>>(U, d_np, part, g.vwgt, prop_tgt, K, C, g.Lb, h1, sel, h0, d_hist_n);
+    }
+    UPR_LAUNCH_CHECK();
+    exclusive_sum_i64((const int64_t *)h0, (int64_t *)h1, ch, tmp, s);
+    auto launch = [&](auto kern) {
+        kern<<<tile_grid((const void *)kern, tiles_max), kThreads, 0, s>>>(
+            U, d_np, sel, part, g.vwgt, prop_tgt, K, C, g.Lb, h1, reject, ctl, R_node, R_from, R_to, R_sub, r_to, r_at,
+            Cd, d_na, scan_state<int32_t>(tmp, tiles_max));
+    };
+    if (unit) launch(k_fr_admit<true>);
+    else launch(k_fr_admit<false>);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_fused_end(const GraphDev &g, int64_t *C, long long *Cd, int8_t *excl, const int8_t *reject,
+                         const int32_t *d_na, RebalCtl *ctl, cudaStream_t s) {
+    k_fr_end<<<1, 256, 0, s>>>(C, Cd, g.Lb, g.K(), excl, reject, d_na, ctl);
+    UPR_LAUNCH_CHECK();
+}
+
+}  // namespace upr

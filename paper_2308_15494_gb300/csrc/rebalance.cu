@@ -63,7 +63,11 @@ __global__ void __launch_bounds__(256) k_propose(const GraphDev g, const int32_t
             int64_t gain = s;
             const int32_t light = src ? st.light[blk_graph(g, ag)] : -1;
             if (src && tgt < 0 && light >= 0 && st.C[light] + c <= st.Lb[light]) { tgt = light; gain = -(int64_t)own; }
-            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = (int32_t)gain; }
+            if (tgt >= 0) {
+                prop_tgt[v] = tgt;
+                prop_gain[v] = (int32_t)gain;
+                if (st.lgain) { st.lgain[i] = (int32_t)gain; st.lsrc[i] = ag; }
+            }
             flags[i] = tgt >= 0 ? 1 : 0;
         }
     }
@@ -166,7 +170,11 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
                     if ((int64_t)c <= lroom) { tgt = light; gain = -own; }
                 }
             }
-            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = gain; }
+            if (tgt >= 0) {
+                prop_tgt[v] = tgt;
+                prop_gain[v] = gain;
+                if (st.lgain) { st.lgain[i] = gain; st.lsrc[i] = ag; }
+            }
             flags[i] = tgt >= 0 ? 1 : 0;
         }
     }
@@ -211,7 +219,11 @@ __global__ void __launch_bounds__(256) k_propose_sparse(const GraphDev g, const 
                 const int32_t light = st.light[blk_graph(g, ag)];
                 if (light >= 0 && (int64_t)c <= st.Lb[light] - st.C[light]) { tgt = light; gain = -own; }
             }
-            if (tgt >= 0) { prop_tgt[v] = tgt; prop_gain[v] = gain; }
+            if (tgt >= 0) {
+                prop_tgt[v] = tgt;
+                prop_gain[v] = gain;
+                if (st.lgain) { st.lgain[i] = gain; st.lsrc[i] = ag; }
+            }
             flags[i] = tgt >= 0 ? 1 : 0;
         }
     }
@@ -797,6 +809,12 @@ void rebalance_prefilter(const GraphDev &g, const int32_t *list, const int32_t *
     UPR_LAUNCH_CHECK();
     k_prio_keep<<<grid_for(n1_max), 256, 0, s>>>(list, d_n1, flags, prop_gain, g.vwgt, part, cut, gbits, cbits,
                                                  gain_only, keep);
+    UPR_LAUNCH_CHECK();
+}
+
+void rebalance_prio_cut(const GraphDev &g, const int8_t *over, const int64_t *C, unsigned long long *hist, int32_t *cut,
+                        cudaStream_t s) {
+    k_prio_cut<<<(unsigned)std::min<int64_t>(g.K(), 4096), kPrioBins, 0, s>>>(g.K(), over, C, g.Lb, hist, cut);
     UPR_LAUNCH_CHECK();
 }
 

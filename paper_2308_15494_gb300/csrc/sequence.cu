@@ -251,14 +251,22 @@ __global__ void k_pk_fill(const int32_t *__restrict__ part0, int64_t n, int32_t 
     }
 }
 
+// Also adds the degrees of the moved nodes to *deg_sum (the adjacency the
+// exact gains read: the step's algorithmic bytes).
 __global__ void k_pk_moves(const int32_t *__restrict__ I_node, const int32_t *__restrict__ I_from,
                            const int32_t *__restrict__ I_to, const int32_t *__restrict__ d_nI, int32_t k,
-                           int32_t kmask, int2 *__restrict__ pk) {
+                           int32_t kmask, const int64_t *__restrict__ xadj, int2 *__restrict__ pk,
+                           unsigned long long *__restrict__ deg_sum) {
     const int64_t nI = *d_nI;
+    unsigned long long deg = 0;
     UPR_FOR(i, nI) {
+        const int32_t v = I_node[i];
         const uint32_t a = (uint32_t)blk_local(I_from[i], k, kmask), b = (uint32_t)blk_local(I_to[i], k, kmask);
-        pk[I_node[i]] = make_int2((int32_t)i, (int32_t)(a | (b << 16)));
+        pk[v] = make_int2((int32_t)i, (int32_t)(a | (b << 16)));
+        deg += (unsigned long long)(xadj[v + 1] - xadj[v]);
     }
+    deg = warp_sum(deg);
+    if ((threadIdx.x & 31) == 0 && deg) atomicAdd(deg_sum, deg);
 }
 
 __device__ __forceinline__ uint32_t block_before(int2 p, int64_t i) {
@@ -869,10 +877,11 @@ void seq_build_I(const int32_t *Ix, const int32_t *d_nI, int64_t max, const int3
 
 void seq_gains(const GraphDev &g, const int32_t *I_node, const int32_t *I_from, const int32_t *I_to,
                const int32_t *d_nI, int64_t max, const int32_t *part0, int2 *pk, int64_t *gain,
-               const HubChunk *hub_chunks, int64_t n_chunks, cudaStream_t s) {
+               const HubChunk *hub_chunks, int64_t n_chunks, int64_t *deg_sum, cudaStream_t s) {
     k_pk_fill<<<grid_for(g.n), 256, 0, s>>>(part0, g.n, g.k, g.kmask, pk);
     UPR_LAUNCH_CHECK();
-    k_pk_moves<<<grid_for(max), 256, 0, s>>>(I_node, I_from, I_to, d_nI, g.k, g.kmask, pk);
+    k_pk_moves<<<grid_for(max), 256, 0, s>>>(I_node, I_from, I_to, d_nI, g.k, g.kmask, g.xadj, pk,
+                                             reinterpret_cast<unsigned long long *>(deg_sum));
     UPR_LAUNCH_CHECK();
     // two waves of CTAs (moved nodes differ widely in degree)
     const unsigned blocks = (unsigned)std::max<int64_t>(

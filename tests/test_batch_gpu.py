@@ -162,3 +162,116 @@ def test_batch_repeated_calls_graph_loop(upr):
                 assert np.array_equal(part[off[i]:off[i + 1]], ref), i
                 assert cout[i] == cut
     assert used > 0
+
+
+@pytest.mark.parametrize("k", [4, 16, 64])
+def test_step_graph_equals_oracle(upr, k):
+    """params.graphs = 2: from a binding's second call on, all rounds of a
+    call run as one CUDA graph launch (every round's kernels, each
+    rebalancing loop a while node).  Calls 1-4 (host-driven, graph built,
+    graph replayed, a different round count) and an imbalanced input (its
+    repair round runs first, the graph after) equal the oracle graph by
+    graph; the graph calls report every round as a graph round."""
+    ws = _mixed(k, 8, 91 + k)
+    prm = upr.upr_params_default()
+    prm.graphs = 2
+    ctx = upr.create_batch_from_workloads(ws, params=prm)
+    off = ctx.offsets
+    seen_graph = 0
+    for call, rounds in enumerate((3, 3, 3, 5)):
+        part = _packed(ws)
+        status, cin, cout, st = upr.upr_batch_refine(ctx, part, rounds)
+        for i, w in enumerate(ws):
+            rc, ref, cut, _ = oracle.refine(w, w.part, rounds)
+            assert status[i] == rc, (call, i)
+            if rc == 0:
+                assert np.array_equal(part[off[i]:off[i + 1]], ref), (call, i)
+                assert cout[i] == cut, (call, i)
+        if call >= 1:
+            assert st.rebalance_graphs == rounds and st.rounds_run == rounds
+            seen_graph += 1
+    assert seen_graph == 3
+    # an imbalanced graph in the batch: repaired first, then the graph's rounds
+    bad = [synth.random_small(1234 + j, 300, 5.0, k, balanced=False) for j in range(2)]
+    ws2 = ws[:3] + bad
+    ctx2 = upr.create_batch_from_workloads(ws2, params=prm)
+    off2 = ctx2.offsets
+    for call in range(3):
+        part = _packed(ws2)
+        status, cin, cout, st = upr.upr_batch_refine(ctx2, part, 3)
+        for i, w in enumerate(ws2):
+            rc, ref, cut, _ = oracle.refine(w, w.part, 3)
+            assert status[i] == rc, (call, i)
+            if rc == 0:
+                assert np.array_equal(part[off2[i]:off2[i + 1]], ref), (call, i)
+
+
+@pytest.mark.parametrize("name", ["plain_tiny", "rmat_s12_k64", "weighted"])
+def test_step_graph_one_graph(upr, name):
+    """The same for one graph (plain tau schedule): partition and cut equal
+    the oracle on the host-driven first call and on the graph calls, also
+    with the oscillation guard."""
+    w = (synth.plain_tiny(3) if name == "plain_tiny" else
+         synth.random_small(5, 4000, 10.0, 64, weighted=False, hubs=2) if name == "rmat_s12_k64" else
+         synth.random_small(6, 3000, 6.0, 16, max_vw=40, max_ew=30))
+    for lock in (0, 1):
+        prm = upr.upr_params_default()
+        prm.graphs = 2
+        prm.lock_rebalanced = lock
+        ctx = upr.create_from_workload(w, params=prm)
+        rc, ref, cut, _ = oracle.refine_schedule(w, w.part, 4, 0, p=oracle.params(lock_rebalanced=lock))[:4]
+        for call in range(3):
+            p = w.part.copy()
+            st = upr.upr_refine(ctx, p, 4)
+            assert np.array_equal(p, ref) and st.cut_out == cut, (call, lock)
+            if call >= 1:
+                assert st.rebalance_graphs == 4
+
+
+@pytest.mark.parametrize("graphs_mode", [1, 2])
+def test_mixed_k_context_equals_oracle(upr, graphs_mode):
+    """One context over graphs of different k (upr_batch_create_mixed): the
+    graphs with the same k form one batch each, refined concurrently; every
+    graph's partition, status and cut equal the oracle's for that graph
+    alone, in the caller's graph order, over several calls (with
+    params.graphs = 2 the later calls run each batch's rounds as one graph
+    launch), from host and from device buffers; upr_batch_cut gives the
+    oracle's cut and k_i block weights per graph."""
+    import torch
+    ks = [2, 8, 4, 32, 8, 2, 16, 4, 64, 8, 6, 32]
+    ws = [synth.random_small(700 + i, [40, 300, 120, 900, 60, 500, 250, 33, 1200, 80, 400, 150][i],
+                             [3, 5, 4, 8, 3, 6, 5, 2, 9, 4, 5, 6][i], k, weighted=i % 3 != 1, hubs=1 if i % 4 == 2 else 0)
+          for i, k in enumerate(ks)]
+    ws.append(synth.random_small(799, 200, 5.0, 8, balanced=False))        # a repair in one of the batches
+    prm = upr.upr_params_default()
+    prm.graphs = graphs_mode
+    ctx = upr.create_batch_from_workloads(ws, params=prm)
+    assert ctx.k == 0 and list(ctx.ks) == [w.k for w in ws]
+    off = ctx.offsets
+    ref = [oracle.refine(w, w.part, 3) for w in ws]
+    for call in range(3):
+        part = _packed(ws)
+        buf = torch.from_numpy(part.copy()).cuda() if call == 1 else part
+        status, cin, cout, st = upr.upr_batch_refine(ctx, buf, 3)
+        got = buf.cpu().numpy() if call == 1 else buf
+        for i, (w, (rc, p0, c0, _)) in enumerate(zip(ws, ref)):
+            assert status[i] == rc, (call, i)
+            if rc == 0:
+                assert np.array_equal(got[off[i]:off[i + 1]], p0), (call, i)
+                assert cout[i] == c0, (call, i)
+    cuts, bws = upr.upr_batch_cut(ctx, got)
+    for i, w in enumerate(ws):
+        c, bw = oracle.cut(w, got[off[i]:off[i + 1]])
+        assert cuts[i] == c and np.array_equal(bws[i], bw), i
+
+
+def test_mixed_k_context_refuses_single_graph_calls(upr):
+    """upr_refine and upr_cut refuse a mixed context (it is not one graph)."""
+    import ctypes
+    ws = [synth.random_small(810, 100, 4.0, 4), synth.random_small(811, 100, 4.0, 8)]
+    ctx = upr.create_batch_from_workloads(ws)
+    part = _packed(ws)
+    lib = upr.load()
+    assert lib.upr_refine(ctx.handle, part.ctypes.data_as(ctypes.c_void_p), 1, 0, None) == upr.UPR_ERR_INVALID
+    cut = ctypes.c_int64()
+    assert lib.upr_cut(ctx.handle, part.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cut), None) == upr.UPR_ERR_INVALID

@@ -92,45 +92,35 @@ def _oracle_pool(jobs):
 
 
 def test_batch_4096_graphs_sampled(upr):
-    """The 4096-graph Chung-Lu batch in the bench's launch configuration (graphs
-    grouped by k, one batch context per group on its own stream, the groups
-    refined concurrently from host threads), every graph's status and cut
-    against its balance, and 32 graphs sampled across the groups against the
-    oracle bit for bit."""
-    import concurrent.futures as cf
+    """The 4096-graph Chung-Lu batch in the bench's launch configuration: one
+    context over all graphs (k from {2, 4, 8, 16, 32}: upr_batch_create_mixed,
+    one batch per k refined concurrently), params.graphs = 2 (from the second
+    call on each batch's rounds are one graph launch), refined twice; every
+    graph's status and cut against its balance, and 32 graphs sampled across
+    the k values against the oracle bit for bit, on both calls."""
     import torch
     graphs = synth.batch_graphs(4096)
-    by_k = {}
-    for i, w in enumerate(graphs):
-        by_k.setdefault(w.k, []).append(i)
-    groups = []
-    for k, idx in sorted(by_k.items()):
-        st = torch.cuda.Stream()
-        ctx = upr.upr_batch_create([(graphs[i].xadj, graphs[i].adj, graphs[i].vwgt, graphs[i].adjw) for i in idx], k,
-                                   [graphs[i].eps for i in idx], stream=upr.ctypes.c_void_p(st.cuda_stream))
-        part = torch.from_numpy(np.concatenate([graphs[i].part for i in idx]).astype(np.int32)).cuda()
-        groups.append((idx, st, ctx, part))
-    torch.cuda.synchronize()
-
-    def run(gr):
-        idx, st, ctx, part = gr
-        torch.cuda.set_device(0)
-        return upr.upr_batch_refine(ctx, part, graphs[idx[0]].rounds)
-
-    with cf.ThreadPoolExecutor(len(groups)) as ex:
-        results = list(ex.map(run, groups))
-    torch.cuda.synchronize()
-    parts = {}
-    for (idx, st, ctx, part), (status, cin, cout, stats) in zip(groups, results):
+    prm = upr.upr_params_default()
+    prm.graphs = 2
+    ctx = upr.upr_batch_create_mixed([(w.xadj, w.adj, w.vwgt, w.adjw) for w in graphs], [w.k for w in graphs],
+                                     [w.eps for w in graphs], params=prm)
+    init = np.concatenate([w.part for w in graphs]).astype(np.int32)
+    rounds = graphs[0].rounds
+    calls = []
+    for call in range(2):
+        part = torch.from_numpy(init.copy()).cuda()
+        status, cin, cout, stats = upr.upr_batch_refine(ctx, part, rounds)
+        torch.cuda.synchronize()
         assert (status == 0).all()
         assert (cout <= cin).all()
         host = part.cpu().numpy()
-        for j, i in enumerate(idx):
-            o0, o1 = ctx.offsets[j], ctx.offsets[j + 1]
-            parts[i] = (host[o0:o1], int(cout[j]))
-            w = graphs[i]
-            bw = np.bincount(parts[i][0], minlength=w.k)
-            assert bw.max() <= ctx.lmax[j]
+        calls.append((host, cout.copy(), stats))
+        for i, w in enumerate(graphs):
+            mine = host[ctx.offsets[i]:ctx.offsets[i + 1]]
+            assert np.bincount(mine, minlength=w.k).max() <= ctx.lmax[i], i
+    assert np.array_equal(calls[0][0], calls[1][0]) and np.array_equal(calls[0][1], calls[1][1])
+    assert calls[1][2].rebalance_graphs == 5 * rounds           # five batches, every round in the graph
+    parts = {i: (calls[1][0][ctx.offsets[i]:ctx.offsets[i + 1]], int(calls[1][1][i])) for i in range(len(graphs))}
     sample = sorted({int(x) for x in np.linspace(0, 4095, 32).round()})
     for i, (rc, p, c) in zip(sample, _oracle_pool([("batch", i) for i in sample])):
         assert rc == 0
