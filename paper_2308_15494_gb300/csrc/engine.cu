@@ -1991,19 +1991,31 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         UPR_CUDA(cudaStreamSynchronize(s));     // noff is host memory that may be re-assigned
     }
     if (prm.validate) {
-        // the hub list goes to a sort buffer, free until the first round
-        std::vector<int32_t> hubs;
-        for (size_t i = 0; i < chunks.size(); i++)
-            if (i == 0 || chunks[i].v != chunks[i - 1].v) hubs.push_back(chunks[i].v);
-        int32_t *hubs_d = reinterpret_cast<int32_t *>(c->sb[0].v);
-        if (!hubs.empty())
-            UPR_CUDA(cudaMemcpyAsync(hubs_d, hubs.data(), sizeof(int32_t) * hubs.size(), cudaMemcpyHostToDevice, s));
-        validate_graph(c->G, c->vacc, c->vflags, hubs_d, (int64_t)hubs.size(), c->noff_d, s);
+        validate_graph(c->G, c->vacc, c->vflags, s);
         uint64_t acc[2]; int32_t flags;
         UPR_CUDA(cudaMemcpyAsync(acc, c->vacc, sizeof(acc), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
         UPR_CUDA(cudaStreamSynchronize(s));
-        if (flags != 0 || acc[0] != acc[1]) { c->n = -1; return UPR_ERR_INVALID; }
+        if ((flags & ~128) != 0 || acc[0] != acc[1]) { c->n = -1; return UPR_ERR_INVALID; }
+        if (flags & 128) {
+            // a row that is not strictly increasing: the exact duplicate check
+            // (the hub list goes to a sort buffer, free until the first round)
+            std::vector<int32_t> hubs;
+            for (size_t i = 0; i < chunks.size(); i++)
+                if (i == 0 || chunks[i].v != chunks[i - 1].v) hubs.push_back(chunks[i].v);
+            int32_t *hubs_d = reinterpret_cast<int32_t *>(c->sb[0].v);
+            if (!hubs.empty())
+                UPR_CUDA(cudaMemcpyAsync(hubs_d, hubs.data(), sizeof(int32_t) * hubs.size(), cudaMemcpyHostToDevice,
+                                         s));
+            UPR_CUDA(cudaMemsetAsync(c->vflags, 0, sizeof(int32_t), s));
+            int64_t max_nodes = 0;
+            for (int32_t i = 0; i < ng; i++) max_nodes = std::max<int64_t>(max_nodes, c->noff[i + 1] - c->noff[i]);
+            validate_duplicates(c->G, c->vflags, hubs_d, (int64_t)hubs.size(), c->noff_d, max_nodes,
+                                reinterpret_cast<int32_t *>(c->sb[1].k), 4 * std::max<int64_t>(n, 1), s);
+            UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+            UPR_CUDA(cudaStreamSynchronize(s));
+            if (flags != 0) { c->n = -1; return UPR_ERR_INVALID; }
+        }
     }
     const auto t_valid = std::chrono::steady_clock::now();
     incident_weights(c->G, c->wI, c->scal, s);

@@ -110,7 +110,9 @@ __device__ __forceinline__ uint64_t entry_hash(uint64_t a, uint64_t b, uint64_t 
 
 // Validation bits: 1 xadj, 2 neighbour range (or, in a batch, a neighbour in
 // another graph), 4 self loop, 8 edge weight, 16 node weight, 32 duplicate
-// neighbour in a row; asymmetry shows as differing sums of hash(v,u,w) and
+// neighbour in a row, 128 a row not strictly increasing (no error: rows with
+// strictly increasing ids have no duplicates, others get the exact duplicate
+// check); asymmetry shows as differing sums of hash(v,u,w) and
 // hash(u,v,w) over the entries (an asymmetric graph whose sums agree passes:
 // probability about 2^-64 for a graph not built against the hash).
 __global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
@@ -128,6 +130,9 @@ __global__ void k_validate_entries(const int64_t *__restrict__ xadj, const int32
             while (xadj[v + 1] <= e) v++;
             int32_t u = adj[e];
             int32_t w = adjw ? adjw[e] : 1;
+            // a row whose next entry is not larger: unsorted, or a duplicate
+            // (bit 128, not an error by itself: the exact duplicate check runs)
+            if (e + 1 < xadj[v + 1] && adj[e + 1] <= u) f |= 128;
             if (u < 0 || u >= n || (gid && gid[u] != gid[v])) { f |= 2; continue; }
             if (u == v) f |= 4;
             if (w <= 0) f |= 8;
@@ -217,8 +222,23 @@ __device__ __forceinline__ uint64_t dup_key(uint64_t iter, int64_t row, int32_t 
     return (iter << 44) | ((uint64_t)row << 31) | (uint64_t)(uint32_t)u;
 }
 
+// first[c] = the first row starting at or after entry c * kDupChunk (n if
+// none), c = 0 .. chunks: one pass over the rows instead of a search per chunk.
+__global__ void k_dup_chunk_first(const int64_t *__restrict__ xadj, int64_t n, int64_t chunks,
+                                  int32_t *__restrict__ first) {
+    UPR_FOR(v, n + 1) {
+        // chunks c with xadj[v - 1] < c * kDupChunk <= xadj[v] start at row v
+        const int64_t hi = v < n ? xadj[v] : (int64_t)chunks * kDupChunk;
+        const int64_t lo = v > 0 ? xadj[v - 1] : -1;
+        const int64_t c0 = lo < 0 ? 0 : lo / kDupChunk + 1;
+        const int64_t c1 = v < n ? hi / kDupChunk : chunks;
+        for (int64_t c = c0; c <= c1 && c <= chunks; c++) first[c] = (int32_t)v;
+    }
+}
+
 __global__ void __launch_bounds__(512) k_dup_rows(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                                                  int64_t n, int64_t m, int32_t *__restrict__ flags) {
+                                                  int64_t n, int64_t m, const int32_t *__restrict__ chunk_first,
+                                                  int32_t *__restrict__ flags) {
     extern __shared__ unsigned long long s_set[];
     __shared__ int64_t s_v[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
@@ -229,7 +249,10 @@ __global__ void __launch_bounds__(512) k_dup_rows(const int64_t *__restrict__ xa
     for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x, iter = (iter + 1) & 0xFFFFF) {
         const int64_t e0 = c * kDupChunk, e1 = min(m, e0 + kDupChunk);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && chunk_first) {
+            s_v[0] = chunk_first[c];
+            s_v[1] = chunk_first[c + 1];
+        } else if (threadIdx.x == 0) {
             // the rows that start in [e0, e1): first row starting at or after
             // e0, first row starting at or after e1
             int64_t lo = 0, hi = n;
@@ -265,9 +288,10 @@ __global__ void __launch_bounds__(512) k_dup_rows(const int64_t *__restrict__ xa
     if (__syncthreads_or(dup) && threadIdx.x == 0) atomicOr(flags, 32);
 }
 
-// Hub rows (degree > kHubDegree), one CTA each: the row's neighbours in
-// [lo, lo + kDupRange) set bits of a shared-memory bitmap, range after range
-// over the node ids of the hub's graph; a bit found set is a duplicate.
+// Hub rows (degree > kHubDegree): CTA (h, r) takes hub h's neighbours in
+// [lo + r * kDupRange, lo + (r + 1) * kDupRange) over the node ids [lo, hi)
+// of the hub's graph, sets their bits in a shared-memory bitmap (8 loads in
+// flight per thread); a bit found set is a duplicate.
 __global__ void __launch_bounds__(256) k_dup_hubs(const int32_t *__restrict__ hubs, const int64_t *__restrict__ xadj,
                                                   const int32_t *__restrict__ adj, int64_t n,
                                                   const int32_t *__restrict__ gid, const int64_t *__restrict__ noff,
@@ -275,18 +299,27 @@ __global__ void __launch_bounds__(256) k_dup_hubs(const int32_t *__restrict__ hu
     extern __shared__ uint32_t s_bits[];
     const int32_t v = hubs[blockIdx.x];
     const int64_t e0 = xadj[v], e1 = xadj[v + 1];
-    const int64_t lo0 = noff ? noff[gid[v]] : 0, hi = noff ? noff[gid[v] + 1] : n;
+    const int64_t hi = noff ? noff[gid[v] + 1] : n;
+    const int64_t lo = (noff ? noff[gid[v]] : 0) + (int64_t)blockIdx.y * kDupRange;
+    if (lo >= hi) return;                                   // uniform over the CTA
+    for (int i = threadIdx.x; i < (int)(kDupRange / 32); i += blockDim.x) s_bits[i] = 0;
+    __syncthreads();
     bool dup = false;
-    for (int64_t lo = lo0; lo < hi; lo += kDupRange) {
-        for (int i = threadIdx.x; i < (int)(kDupRange / 32); i += blockDim.x) s_bits[i] = 0;
-        __syncthreads();
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int64_t x = (int64_t)adj[e] - lo;
-            if (x < 0 || x >= kDupRange) continue;
+    constexpr int kU = 8;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += (int64_t)blockDim.x * kU) {
+        int32_t u[kU];
+#pragma unroll
+        for (int j = 0; j < kU; j++) {
+            const int64_t x = e + (int64_t)j * blockDim.x;
+            u[j] = x < e1 ? adj[x] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < kU; j++) {
+            const int64_t x = (int64_t)u[j] - lo;
+            if (u[j] < 0 || x < 0 || x >= kDupRange) continue;
             const uint32_t bit = 1u << (x & 31);
             dup |= (atomicOr(&s_bits[x >> 5], bit) & bit) != 0;
         }
-        __syncthreads();
     }
     if (__syncthreads_or(dup) && threadIdx.x == 0) atomicOr(flags, 32);
 }
@@ -609,8 +642,7 @@ void sparse_to_dense(const GraphDev &g, int32_t *W, cudaStream_t s) {
     UPR_LAUNCH_CHECK();
 }
 
-void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, const int32_t *hubs, int64_t n_hubs,
-                    const int64_t *noff, cudaStream_t s) {
+void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s) {
     UPR_CUDA(cudaMemsetAsync(d_acc, 0, 2 * sizeof(uint64_t), s));
     UPR_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int32_t), s));
     k_validate_nodes<<<(unsigned)ceil_div(g.n + 1, 256), 256, 0, s>>>(g.xadj, g.vwgt, g.n, g.m, d_flags);
@@ -620,19 +652,33 @@ void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, const 
         k_validate_entries<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, s>>>(
             g.xadj, g.adj, g.adjw, g.gid, g.n, g.m, (unsigned long long *)d_acc, d_flags);
         UPR_LAUNCH_CHECK();
-        // duplicates: rows up to kHubDegree by warps, hub rows by CTAs
-        const size_t shm_rows = (size_t)kDupSlots * sizeof(unsigned long long);
-        const size_t shm_hubs = (size_t)(kDupRange / 32) * sizeof(uint32_t);
-        kernel_setup((const void *)k_dup_rows, -1);
-        kernel_setup((const void *)k_dup_hubs, -1);
-        const unsigned grid = wave_grid((const void *)k_dup_rows, 512, shm_rows, ceil_div(g.m, (int64_t)kDupChunk));
-        k_dup_rows<<<grid, 512, shm_rows, s>>>(g.xadj, g.adj, g.n, g.m, d_flags);
+    }
+}
+
+void validate_duplicates(const GraphDev &g, int32_t *d_flags, const int32_t *hubs, int64_t n_hubs,
+                         const int64_t *noff, int64_t max_graph_nodes, int32_t *scratch, int64_t scratch_ints,
+                         cudaStream_t s) {
+    if (g.m == 0 || g.n == 0) return;
+    // rows up to kHubDegree by chunks of entries, hub rows by CTAs
+    const size_t shm_rows = (size_t)kDupSlots * sizeof(unsigned long long);
+    const size_t shm_hubs = (size_t)(kDupRange / 32) * sizeof(uint32_t);
+    kernel_setup((const void *)k_dup_rows, -1);
+    kernel_setup((const void *)k_dup_hubs, -1);
+    const int64_t chunks = ceil_div(g.m, (int64_t)kDupChunk);
+    int32_t *first = chunks + 1 <= scratch_ints ? scratch : nullptr;
+    if (first) {
+        k_dup_chunk_first<<<grid_for(g.n + 1), 256, 0, s>>>(g.xadj, g.n, chunks, first);
         UPR_LAUNCH_CHECK();
-        if (n_hubs > 0) {
-            k_dup_hubs<<<(unsigned)n_hubs, 256, shm_hubs, s>>>(hubs, g.xadj, g.adj, g.n, g.gid,
-                                                              g.ng > 1 ? noff : nullptr, d_flags);
-            UPR_LAUNCH_CHECK();
-        }
+    }
+    const unsigned grid = wave_grid((const void *)k_dup_rows, 512, shm_rows, chunks);
+    k_dup_rows<<<grid, 512, shm_rows, s>>>(g.xadj, g.adj, g.n, g.m, first, d_flags);
+    UPR_LAUNCH_CHECK();
+    if (n_hubs > 0) {
+        // ranges of node ids per hub: those of the largest graph
+        const int64_t ranges = ceil_div(std::max<int64_t>(max_graph_nodes, 1), kDupRange);
+        k_dup_hubs<<<dim3((unsigned)n_hubs, (unsigned)ranges), 256, shm_hubs, s>>>(
+            hubs, g.xadj, g.adj, g.n, g.gid, g.ng > 1 ? noff : nullptr, d_flags);
+        UPR_LAUNCH_CHECK();
     }
 }
 

@@ -207,11 +207,16 @@ void pack_batch(const GraphDev &g, const int64_t *noff, int32_t *gid, int32_t *a
 void sparse_to_dense(const GraphDev &g, int32_t *W, cudaStream_t s);
 // Graph checks; writes a bitmask of violations into *d_flags (see engine.cu).
 // Checks the CSR on the device (bits of *d_flags, hash sums in d_acc[0..1]):
-// ranges, self loops, weights, symmetry by a multiset hash, and exactly
-// (no hash) duplicate neighbours; hubs lists the n_hubs nodes of degree >
-// kHubDegree, noff the batch's node offsets (ignored for one graph).
-void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, const int32_t *hubs, int64_t n_hubs,
-                    const int64_t *noff, cudaStream_t s);
+// ranges, self loops, weights, symmetry by a multiset hash, and bit 128 for a
+// row whose ids are not strictly increasing.
+void validate_graph(const GraphDev &g, uint64_t *d_acc, int32_t *d_flags, cudaStream_t s);
+// Exact duplicate check (bit 32 of *d_flags) for graphs with an unsorted row:
+// hubs lists the n_hubs nodes of degree > kHubDegree, noff the batch's node
+// offsets (ignored for one graph), max_graph_nodes the largest graph's node
+// count, scratch: scratch_ints free ints.
+void validate_duplicates(const GraphDev &g, int32_t *d_flags, const int32_t *hubs, int64_t n_hubs,
+                         const int64_t *noff, int64_t max_graph_nodes, int32_t *scratch, int64_t scratch_ints,
+                         cudaStream_t s);
 
 // ---- select.cu: step (b) and applying M
 struct Penalty {

@@ -118,26 +118,37 @@ upr_status mixed_create(const upr_graph *graphs, int32_t n_graphs, const int32_t
         mb->gnodes.assign(G, 0);
         mb->lmax.assign(n_graphs, 0);
         std::vector<int64_t> map(mb->n);
+        std::vector<std::vector<upr_graph>> gs(G);
+        std::vector<std::vector<double>> es(G);
         for (size_t g = 0; g < G; g++) {
             UPR_CUDA(cudaStreamCreateWithFlags(&mb->streams[g], cudaStreamNonBlocking));
-            std::vector<upr_graph> gs;
-            std::vector<double> es;
             int64_t pos = 0;
             for (int32_t i : mb->idx[g]) {
-                gs.push_back(graphs[i]);
-                es.push_back(eps[i]);
+                gs[g].push_back(graphs[i]);
+                es[g].push_back(eps[i]);
                 for (int64_t v = 0; v < graphs[i].n; v++) map[mb->noff[i] + v] = ((int64_t)g << kPosBits) | (pos + v);
                 pos += graphs[i].n;
             }
             mb->gnodes[g] = pos;
-            upr_params p = prm;
-            p.stream = mb->streams[g];
-            rc = upr_batch_create(gs.data(), (int32_t)gs.size(), ks[g], es.data(), &p, &mb->sub[g]);
-            if (rc != UPR_OK) { free_mixed(mb); return rc; }
-            std::vector<int64_t> lm(gs.size());
+        }
+        // the batches are bound concurrently, one host thread each
+        std::vector<upr_status> grc(G, UPR_OK);
+        std::vector<std::thread> th;
+        for (size_t g = 0; g < G; g++)
+            th.emplace_back([&, g] {
+                cudaSetDevice(mb->device);
+                upr_params p = prm;
+                p.stream = mb->streams[g];
+                grc[g] = upr_batch_create(gs[g].data(), (int32_t)gs[g].size(), ks[g], es[g].data(), &p, &mb->sub[g]);
+            });
+        for (auto &t : th) t.join();
+        for (size_t g = 0; g < G; g++)
+            if (grc[g] != UPR_OK) { rc = grc[g]; free_mixed(mb); return rc; }
+        for (size_t g = 0; g < G; g++) {
+            std::vector<int64_t> lm(gs[g].size());
             upr_batch_info(mb->sub[g], nullptr, nullptr, lm.data());
-            for (size_t j = 0; j < gs.size(); j++) mb->lmax[mb->idx[g][j]] = lm[j];
-            if (pos > 0) UPR_CUDA(cudaMalloc(&mb->d_sub[g], sizeof(int32_t) * pos));
+            for (size_t j = 0; j < gs[g].size(); j++) mb->lmax[mb->idx[g][j]] = lm[j];
+            if (mb->gnodes[g] > 0) UPR_CUDA(cudaMalloc(&mb->d_sub[g], sizeof(int32_t) * mb->gnodes[g]));
         }
         if (mb->n > 0) {
             UPR_CUDA(cudaMalloc(&mb->d_part, sizeof(int32_t) * mb->n));

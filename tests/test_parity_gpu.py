@@ -320,6 +320,25 @@ def test_wide_rebalancing_key_same_results(upr, seed):
             upr.upr_refine(ctx, p, 2)
 
 
+def test_unsorted_rows_without_duplicates_accepted(upr):
+    """Rows need not be sorted: with every row reversed (so the exact
+    duplicate check runs, on short rows, long rows and a hub row) the graph
+    is accepted and refines to the oracle's result for the same graph."""
+    n = 6000
+    src = np.concatenate([np.zeros(n - 1, np.int32), np.arange(1, n - 1, dtype=np.int32),
+                          np.arange(0, n - 3, 7, dtype=np.int32)])
+    dst = np.concatenate([np.arange(1, n, dtype=np.int32), np.arange(2, n, dtype=np.int32),
+                          (np.arange(0, n - 3, 7, dtype=np.int32) * 13 + 5) % n])
+    xadj, adj = synth.csr_from_edges(n, src, dst)
+    rev = np.concatenate([adj[xadj[v]:xadj[v + 1]][::-1] for v in range(n)]).astype(np.int32)
+    w = synth.Workload("rows_reversed", n, xadj, adj, None, None, 8, 0.03, synth.part_random_balanced(n, 8, 5), 3)
+    rc0, p0, c0, _ = oracle.refine(w, w.part, 3)
+    ctx = upr.upr_create(xadj, rev, 8, 0.03)
+    p = w.part.copy()
+    st = upr.upr_refine(ctx, p, 3)
+    assert np.array_equal(p, p0) and st.cut_out == c0
+
+
 def test_split_resume_and_seed_independence(upr):
     w = synth.plain_tiny(3)
     full = upr.create_from_workload(w)
