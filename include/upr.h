@@ -293,6 +293,21 @@ upr_status upr_batch_create(const upr_graph *graphs, int32_t n_graphs, int32_t k
 upr_status upr_batch_create_mixed(const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
                                   const upr_params *params, upr_ctx **out);
 
+/* Binds other graphs to an existing context, with the parameters it was
+ * created with, as upr_create / upr_batch_create / upr_batch_create_mixed
+ * would create it, reusing its device memory where it is large enough (a
+ * context rebound to graphs no larger than before allocates nothing new on
+ * the device).  k and eps have n_graphs entries.  A context of
+ * upr_create or upr_batch_create takes graphs of one k (k[i] all equal,
+ * else UPR_ERR_INVALID with the context unchanged); a mixed context takes
+ * any k (batches of a k it already had are reused, new k get new batches,
+ * batches of k no longer present are freed).  The graphs are read as in
+ * upr_create and may be freed on return.  Any other error leaves the
+ * context unusable (every call returns UPR_ERR_INVALID) until a rebind
+ * succeeds. */
+upr_status upr_batch_rebind(upr_ctx *ctx, const upr_graph *graphs, int32_t n_graphs, const int32_t *k,
+                            const double *eps);
+
 /* Refines all graphs of a batch context.  part holds every graph's
  * partition back to back (graph i at node offset sum of n of graphs < i,
  * graph-local block ids in [0, k)), host or device, refined in place.

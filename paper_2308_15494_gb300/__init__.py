@@ -88,6 +88,7 @@ SIGNATURES = {
     "upr_debug_round": (I32, [P, P, I32, I32, I32, ctypes.POINTER(Trace)]),
     "upr_batch_create": (I32, [ctypes.POINTER(Graph), I32, I32, P, ctypes.POINTER(Params), ctypes.POINTER(P)]),
     "upr_batch_create_mixed": (I32, [ctypes.POINTER(Graph), I32, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]),
+    "upr_batch_rebind": (I32, [P, ctypes.POINTER(Graph), I32, P, P]),
     "upr_batch_refine": (I32, [P, P, I32, U64, P, P, P, ctypes.POINTER(Stats)]),
     "upr_batch_cut": (I32, [P, P, P, P]),
     "upr_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),
@@ -344,6 +345,46 @@ def upr_batch_create_mixed(graphs, ks, eps, params: Optional[Params] = None, str
     lm = np.zeros(max(ng, 1), np.int64)
     lib.upr_batch_info(h, ctypes.byref(cnt), _ptr(off), _ptr(lm))
     return BatchContext(h, ng, 0, off, lm[:ng], kk.copy())
+
+
+def upr_rebind(ctx: Context, xadj, adj, k: int, eps: float, vwgt=None, adjw=None) -> Context:
+    """upr_batch_rebind of a one-graph context to another graph (its device
+    memory reused where it is large enough)."""
+    g, n, m = _graph_struct(xadj, adj, vwgt, adjw)
+    kk = np.array([k], np.int32)
+    e = np.array([eps], np.float64)
+    st = load().upr_batch_rebind(ctx.handle, ctypes.byref(g), 1, _ptr(kk), _ptr(e))
+    if st != UPR_OK:
+        raise UprError(st, "upr_batch_rebind")
+    ctx.n, ctx.m, ctx.k = n, m, k
+    ctx._keep = (xadj, adj, vwgt, adjw)
+    return ctx
+
+
+def upr_batch_rebind(ctx: BatchContext, graphs, ks, eps) -> BatchContext:
+    """upr_batch_rebind: the context bound to other graphs (reusing its device
+    memory where it is large enough); returns ctx with its offsets, L_max and
+    k updated."""
+    lib = load()
+    ng = len(graphs)
+    arr = (Graph * max(ng, 1))()
+    for i, (xa, ad, vw, aw) in enumerate(graphs):
+        arr[i], _, _ = _graph_struct(xa, ad, vw, aw)
+    kk = np.ascontiguousarray(np.asarray(ks, np.int32))
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (ng,)))
+    st = lib.upr_batch_rebind(ctx.handle, arr, ng, _ptr(kk), _ptr(e))
+    if st != UPR_OK:
+        raise UprError(st, "upr_batch_rebind")
+    cnt = I32()
+    off = np.zeros(ng + 1, np.int64)
+    lm = np.zeros(max(ng, 1), np.int64)
+    lib.upr_batch_info(ctx.handle, ctypes.byref(cnt), _ptr(off), _ptr(lm))
+    ctx.n_graphs, ctx.offsets, ctx.lmax = ng, off, lm[:ng]
+    if ctx.ks is not None:
+        ctx.ks = kk.copy()
+    else:
+        ctx.k = int(kk[0])
+    return ctx
 
 
 def create_batch_from_workloads(ws, params: Optional[Params] = None, device: bool = False) -> BatchContext:

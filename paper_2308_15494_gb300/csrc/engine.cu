@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <set>
@@ -273,6 +274,7 @@ struct upr_ctx {
     long long *hbest = nullptr;
     RebalCtl *hctl = nullptr;
     cudaEvent_t ev[8] = {};
+    int64_t *hx = nullptr; int64_t hx_cap = 0;   // pinned staging of a batch's packed xadj (kept across bindings)
 };
 
 namespace {
@@ -1112,6 +1114,7 @@ void free_ctx(upr_ctx *c) {
     if (c->hF_all) cudaFreeHost(c->hF_all);
     if (c->h) cudaFreeHost(c->h);
     if (c->h8) cudaFreeHost(c->h8);
+    if (c->hx) cudaFreeHost(c->hx);
     for (auto &e : c->ev) if (e) cudaEventDestroy(e);
     for (auto &e : c->ev_tune) if (e) cudaEventDestroy(e);
     delete c;
@@ -1747,59 +1750,82 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         c->noff[i + 1] = c->noff[i] + gs[i].n;
         eoff[i + 1] = eoff[i] + gs[i].m;
     }
-    std::vector<int64_t> xadj_store;
+    // the packed xadj of a batch (or of a graph whose xadj is device
+    // memory) goes to the context's pinned staging buffer, kept across
+    // bindings, so that its upload is a DMA from pinned memory
+    int64_t *xadj_store = nullptr;
     const int64_t *xadj_h;
+    const int nthreads = host_threads(n);
     if (ng == 1 && (n == 0 || mem_kind(gs[0].xadj) == kHost)) {
         static const int64_t zero = 0;
         xadj_h = n > 0 ? gs[0].xadj : &zero;
         if (n > 0 && (xadj_h[0] != 0 || xadj_h[n] != m)) return UPR_ERR_INVALID;
-    } else {
-        xadj_store.assign(n + 1, 0);
-        for (int32_t i = 0; i < ng; i++) {
-            const upr_graph *g = &gs[i];
-            const int64_t gn = g->n, v0 = c->noff[i];
-            if (gn == 0) continue;
-            if (mem_kind(g->xadj) == kDevice)
-                UPR_CUDA(cudaMemcpy(xadj_store.data() + v0, g->xadj, sizeof(int64_t) * (gn + 1), cudaMemcpyDeviceToHost));
-            else
-                memcpy(xadj_store.data() + v0, g->xadj, sizeof(int64_t) * (gn + 1));
-            if (xadj_store[v0] != 0 || xadj_store[v0 + gn] != g->m) return UPR_ERR_INVALID;
-        }
-        xadj_store[n] = m;
-        xadj_h = xadj_store.data();
-    }
-    const int nthreads = host_threads(n);
-    // monotone rows; batches: graph-local offsets made global
-    {
         std::vector<char> bad(nthreads, 0);
         parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
-            if (ng == 1) {
-                for (int64_t v = v0; v < v1; v++)
-                    if (xadj_h[v + 1] < xadj_h[v]) { bad[t] = 1; return; }
-                return;
+            for (int64_t v = v0; v < v1; v++)
+                if (xadj_h[v + 1] < xadj_h[v]) { bad[t] = 1; return; }
+        });
+        for (char x : bad)
+            if (x) return UPR_ERR_INVALID;
+    } else {
+        if (c->hx_cap < n + 1) {
+            if (c->hx) cudaFreeHost(c->hx);
+            c->hx = nullptr;
+            c->hx_cap = 0;
+            if (cudaMallocHost((void **)&c->hx, sizeof(int64_t) * (n + 1)) != cudaSuccess) {
+                cudaGetLastError();
+                return UPR_ERR_OOM;
             }
-            // v in [v0, v1): graph of v by search, then its offset
-            int32_t gi = (int32_t)(std::upper_bound(c->noff.begin(), c->noff.end(), v0) - c->noff.begin()) - 1;
-            for (int64_t v = v0; v < v1; v++) {
-                while (v >= c->noff[gi + 1]) gi++;
-                const bool last = v + 1 == c->noff[gi + 1];
-                const int64_t nxt = last ? gs[gi].m : xadj_store[v + 1];
-                if (nxt < xadj_store[v]) { bad[t] = 1; return; }
+            c->hx_cap = n + 1;
+        }
+        xadj_store = c->hx;
+    }
+    if (ng == 1 && xadj_store) {
+        // one graph whose xadj is device memory: read back, checked on several threads
+        UPR_CUDA(cudaMemcpy(xadj_store, gs[0].xadj, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+        if (xadj_store[0] != 0 || xadj_store[n] != m) return UPR_ERR_INVALID;
+        std::vector<char> bad(nthreads, 0);
+        parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
+            for (int64_t v = v0; v < v1; v++)
+                if (xadj_store[v + 1] < xadj_store[v]) { bad[t] = 1; return; }
+        });
+        for (char x : bad)
+            if (x) return UPR_ERR_INVALID;
+        xadj_h = xadj_store;
+    } else if (xadj_store) {
+        // graph i's offsets shifted by the entries of the graphs before it,
+        // checked on the way (starts at 0, non-decreasing, ends at m_i), one
+        // pass per graph on several threads; device graphs are read back first
+        std::vector<char> dev(ng, 0);
+        std::vector<std::vector<int64_t>> dev_x(ng);
+        for (int32_t i = 0; i < ng; i++) {
+            dev[i] = gs[i].n > 0 && mem_kind(gs[i].xadj) == kDevice;
+            if (dev[i]) {
+                dev_x[i].resize(gs[i].n + 1);
+                UPR_CUDA(cudaMemcpy(dev_x[i].data(), gs[i].xadj, sizeof(int64_t) * (gs[i].n + 1),
+                                    cudaMemcpyDeviceToHost));
+            }
+        }
+        std::vector<char> bad(nthreads, 0);
+        parallel_segments(ng, nthreads, [&](int t, int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; i++) {
+                const int64_t gn = gs[i].n;
+                if (gn == 0) continue;
+                const int64_t *src = dev[i] ? dev_x[i].data() : gs[i].xadj;
+                int64_t *dst = xadj_store + c->noff[i];
+                const int64_t off = eoff[i];
+                bool ok = src[0] == 0 && src[gn] == gs[i].m;
+                for (int64_t v = 0; v < gn; v++) {
+                    ok = ok && src[v] <= src[v + 1];
+                    dst[v] = src[v] + off;
+                }
+                if (!ok) bad[t] = 1;
             }
         });
         for (char x : bad)
             if (x) return UPR_ERR_INVALID;
-        if (ng > 1) {
-            // every entry of graph g gains eoff[g] (the last one of a graph is the next graph's 0 + its offset)
-            parallel_segments(n, nthreads, [&](int, int64_t v0, int64_t v1) {
-                int32_t gi = (int32_t)(std::upper_bound(c->noff.begin(), c->noff.end(), v0) - c->noff.begin()) - 1;
-                for (int64_t v = v0; v < v1; v++) {
-                    while (v >= c->noff[gi + 1]) gi++;
-                    xadj_store[v] += eoff[gi];
-                }
-            });
-            xadj_store[n] = m;
-        }
+        xadj_store[n] = m;
+        xadj_h = xadj_store;
     }
     int64_t cmax = 1;
     for (int32_t i = 0; i < ng; i++) {
@@ -1952,7 +1978,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         if (n > 0) copy_in(c->xadj, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
         else UPR_CUDA(cudaMemsetAsync(c->xadj, 0, sizeof(int64_t), s));
     } else {
-        UPR_CUDA(cudaMemcpyAsync(c->xadj, xadj_store.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+        UPR_CUDA(cudaMemcpyAsync(c->xadj, xadj_store, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
     }
     for (int32_t i = 0; i < ng; i++) {
         const upr_graph *g = &gs[i];
@@ -2145,10 +2171,28 @@ upr_status upr_batch_create_mixed(const upr_graph *graphs, int32_t n_graphs, con
     return UPR_OK;
 }
 
+upr_status upr_batch_rebind(upr_ctx *c, const upr_graph *graphs, int32_t n_graphs, const int32_t *k,
+                            const double *eps) {
+    if (!c || !graphs || !k || !eps || n_graphs < 1) return UPR_ERR_INVALID;
+    if (c->mix) {
+        const upr_status st = upr::mixed_rebind(c->mix, graphs, n_graphs, k, eps);
+        c->n = st == UPR_OK ? upr::mixed_nodes(c->mix) : -1;
+        c->ng = n_graphs;
+        return st;
+    }
+    for (int32_t i = 1; i < n_graphs; i++)
+        if (k[i] != k[0]) return UPR_ERR_INVALID;        // one k: a mixed context takes several
+    if (n_graphs == 1) return upr::ctx_rebind(c, graphs, k[0], eps[0], &c->prm);
+    return upr::ctx_rebind_batch(c, graphs, n_graphs, k[0], eps, &c->prm);
+}
+
 upr_status upr_batch_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t seed, upr_status *status,
                             int64_t *cut_in, int64_t *cut_out, upr_stats *stats) {
     (void)seed;
-    if (c && c->mix) return upr::mixed_refine(c->mix, part, rounds, seed, status, cut_in, cut_out, stats);
+    if (c && c->mix) {
+        if (c->n < 0) return UPR_ERR_INVALID;
+        return upr::mixed_refine(c->mix, part, rounds, seed, status, cut_in, cut_out, stats);
+    }
     if (!c || c->n < 0 || (!part && c->n > 0) || rounds < 0) return UPR_ERR_INVALID;
     try {
         upr_status rc = refine_impl(c, part, rounds, stats, status, cut_in, cut_out);
@@ -2169,7 +2213,7 @@ upr_status upr_batch_refine(upr_ctx *c, int32_t *part, int32_t rounds, uint64_t 
 }
 
 upr_status upr_batch_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t *block_weights_out) {
-    if (c && c->mix) return upr::mixed_cut(c->mix, part, cut, block_weights_out);
+    if (c && c->mix) return c->n < 0 ? UPR_ERR_INVALID : upr::mixed_cut(c->mix, part, cut, block_weights_out);
     if (!c || c->n < 0 || !part || !cut) return UPR_ERR_INVALID;
     try {
         upr_status st = load_part(c, part);
@@ -2183,7 +2227,7 @@ upr_status upr_batch_cut(upr_ctx *c, const int32_t *part, int64_t *cut, int64_t 
 }
 
 upr_status upr_batch_info(const upr_ctx *c, int32_t *n_graphs, int64_t *node_offsets, int64_t *lmax) {
-    if (c && c->mix) return upr::mixed_info(c->mix, n_graphs, node_offsets, lmax);
+    if (c && c->mix) return c->n < 0 ? UPR_ERR_INVALID : upr::mixed_info(c->mix, n_graphs, node_offsets, lmax);
     if (!c || c->n < 0) return UPR_ERR_INVALID;
     if (n_graphs) *n_graphs = c->ng;
     if (node_offsets) memcpy(node_offsets, c->noff.data(), sizeof(int64_t) * (c->ng + 1));

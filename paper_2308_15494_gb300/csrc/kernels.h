@@ -310,7 +310,13 @@ void rebalance_prio_sort_wide(const GraphDev &g, const int32_t *P, const int32_t
 struct MixedBatch;
 upr_status mixed_create(const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
                         const upr_params *params, MixedBatch **out);
+upr_status mixed_rebind(MixedBatch *mb, const upr_graph *graphs, int32_t n_graphs, const int32_t *k,
+                        const double *eps);
 void mixed_destroy(MixedBatch *mb);
+// engine.cu: a context bound to other graphs (its arena reused when large enough)
+upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, const upr_params *params);
+upr_status ctx_rebind_batch(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
+                            const upr_params *params);
 int64_t mixed_nodes(const MixedBatch *mb);
 upr_status mixed_refine(MixedBatch *mb, int32_t *part, int32_t rounds, uint64_t seed, upr_status *status,
                         int64_t *cut_in, int64_t *cut_out, upr_stats *stats);

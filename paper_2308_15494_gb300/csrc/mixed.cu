@@ -28,10 +28,13 @@ struct MixedBatch {
     std::vector<int64_t> boff;                    // caller offsets of the graphs' block weights [ng + 1]
     std::vector<int64_t> lmax;                    // L_max of each caller graph
     std::vector<int64_t> gnodes;                  // nodes of each group
+    upr_params prm{};                             // the parameters every batch is bound with
     int32_t *d_part = nullptr;                    // [n] the partition in caller order
     std::vector<int32_t *> d_sub;                 // [nodes of group g] the group's packed partition
+    std::vector<size_t> d_cap;                    // capacity of d_sub[g]
     int32_t **d_ptrs = nullptr;                   // device copy of d_sub
     int64_t *d_map = nullptr;                     // [n] caller node -> (group << 40) | position in the group
+    size_t part_cap = 0, map_cap = 0, ptrs_cap = 0;
     cudaEvent_t ev_fork = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
 };
 
@@ -81,94 +84,150 @@ void gather_part(MixedBatch *mb, const int32_t *part) {
 
 }  // namespace
 
+namespace {
+
+// Device buffer of at least `count` elements (grown, never shrunk).
+template <typename T>
+void reserve(T **p, size_t *cap, size_t count) {
+    if (*cap >= count) return;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    UPR_CUDA(cudaMalloc(p, sizeof(T) * std::max<size_t>(count, 1)));
+    *cap = count;
+}
+
+// Binds the graphs: one batch per k.  A batch of a k the previous binding
+// had reuses that batch's context (and its device memory when large
+// enough); new k get new contexts; contexts of k no longer present are freed.
+upr_status mixed_bind(MixedBatch *mb, const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
+                      const upr_params &prm) {
+    mb->noff.assign(n_graphs + 1, 0);
+    mb->boff.assign(n_graphs + 1, 0);
+    for (int32_t i = 0; i < n_graphs; i++) {
+        if (k[i] < 2 || k[i] > kMaxK || graphs[i].n < 0) return UPR_ERR_INVALID;
+        mb->noff[i + 1] = mb->noff[i] + graphs[i].n;
+        mb->boff[i + 1] = mb->boff[i] + k[i];
+    }
+    if (mb->noff[n_graphs] >= (1ll << 31)) return UPR_ERR_INVALID;
+    mb->ng = n_graphs;
+    mb->n = mb->noff[n_graphs];
+    // groups by k, in increasing k, graphs in caller order within a group
+    std::vector<int32_t> ks(k, k + n_graphs);
+    std::sort(ks.begin(), ks.end());
+    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+    const size_t G = ks.size();
+    // the previous binding's contexts, streams and buffers by k
+    std::vector<upr_ctx *> sub(G, nullptr);
+    std::vector<cudaStream_t> streams(G, nullptr);
+    std::vector<int32_t *> d_sub(G, nullptr);
+    std::vector<size_t> d_cap(G, 0);
+    for (size_t j = 0; j < mb->k_of.size(); j++) {
+        const auto it = std::lower_bound(ks.begin(), ks.end(), mb->k_of[j]);
+        if (it != ks.end() && *it == mb->k_of[j]) {
+            const size_t g = it - ks.begin();
+            sub[g] = mb->sub[j];
+            streams[g] = mb->streams[j];
+            d_sub[g] = mb->d_sub[j];
+            d_cap[g] = mb->d_cap[j];
+        } else {
+            upr_destroy(mb->sub[j]);
+            if (mb->streams[j]) cudaStreamDestroy(mb->streams[j]);
+            if (mb->d_sub[j]) cudaFree(mb->d_sub[j]);
+        }
+    }
+    mb->k_of = ks;
+    mb->sub = sub;
+    mb->streams = streams;
+    mb->d_sub = d_sub;
+    mb->d_cap = d_cap;
+    mb->idx.assign(G, {});
+    for (int32_t i = 0; i < n_graphs; i++)
+        mb->idx[std::lower_bound(ks.begin(), ks.end(), k[i]) - ks.begin()].push_back(i);
+    mb->gnodes.assign(G, 0);
+    mb->lmax.assign(n_graphs, 0);
+    std::vector<int64_t> map(mb->n);
+    std::vector<std::vector<upr_graph>> gs(G);
+    std::vector<std::vector<double>> es(G);
+    for (size_t g = 0; g < G; g++) {
+        if (!mb->streams[g]) UPR_CUDA(cudaStreamCreateWithFlags(&mb->streams[g], cudaStreamNonBlocking));
+        int64_t pos = 0;
+        for (int32_t i : mb->idx[g]) {
+            gs[g].push_back(graphs[i]);
+            es[g].push_back(eps[i]);
+            for (int64_t v = 0; v < graphs[i].n; v++) map[mb->noff[i] + v] = ((int64_t)g << kPosBits) | (pos + v);
+            pos += graphs[i].n;
+        }
+        mb->gnodes[g] = pos;
+    }
+    // the batches are bound concurrently, one host thread each
+    std::vector<upr_status> grc(G, UPR_OK);
+    std::vector<std::thread> th;
+    for (size_t g = 0; g < G; g++)
+        th.emplace_back([&, g] {
+            cudaSetDevice(mb->device);
+            upr_params p = prm;
+            p.stream = mb->streams[g];
+            grc[g] = mb->sub[g] ? ctx_rebind_batch(mb->sub[g], gs[g].data(), (int32_t)gs[g].size(), ks[g],
+                                                   es[g].data(), &p)
+                                : upr_batch_create(gs[g].data(), (int32_t)gs[g].size(), ks[g], es[g].data(), &p,
+                                                   &mb->sub[g]);
+        });
+    for (auto &t : th) t.join();
+    for (size_t g = 0; g < G; g++)
+        if (grc[g] != UPR_OK) return grc[g];
+    for (size_t g = 0; g < G; g++) {
+        std::vector<int64_t> lm(gs[g].size());
+        upr_batch_info(mb->sub[g], nullptr, nullptr, lm.data());
+        for (size_t j = 0; j < gs[g].size(); j++) mb->lmax[mb->idx[g][j]] = lm[j];
+        reserve(&mb->d_sub[g], &mb->d_cap[g], (size_t)mb->gnodes[g]);
+    }
+    reserve(&mb->d_part, &mb->part_cap, (size_t)mb->n);
+    reserve(&mb->d_map, &mb->map_cap, (size_t)mb->n);
+    reserve(&mb->d_ptrs, &mb->ptrs_cap, G);
+    if (mb->n > 0) UPR_CUDA(cudaMemcpy(mb->d_map, map.data(), sizeof(int64_t) * mb->n, cudaMemcpyHostToDevice));
+    UPR_CUDA(cudaMemcpy(mb->d_ptrs, mb->d_sub.data(), sizeof(int32_t *) * G, cudaMemcpyHostToDevice));
+    return UPR_OK;
+}
+
+}  // namespace
+
 upr_status mixed_create(const upr_graph *graphs, int32_t n_graphs, const int32_t *k, const double *eps,
                         const upr_params *params, MixedBatch **out) {
     if (!graphs || !k || !eps || n_graphs < 1 || !out) return UPR_ERR_INVALID;
     MixedBatch *mb = new (std::nothrow) MixedBatch();
     if (!mb) return UPR_ERR_OOM;
-    upr_params prm;
-    upr_params_default(&prm);
-    if (params) prm = *params;
-    mb->s = (cudaStream_t)prm.stream;
-    mb->ng = n_graphs;
+    upr_params_default(&mb->prm);
+    if (params) mb->prm = *params;
+    mb->s = (cudaStream_t)mb->prm.stream;
     upr_status rc = UPR_OK;
     try {
         UPR_CUDA(cudaGetDevice(&mb->device));
-        mb->noff.assign(n_graphs + 1, 0);
-        mb->boff.assign(n_graphs + 1, 0);
-        for (int32_t i = 0; i < n_graphs; i++) {
-            if (k[i] < 2 || k[i] > kMaxK || graphs[i].n < 0) { free_mixed(mb); return UPR_ERR_INVALID; }
-            mb->noff[i + 1] = mb->noff[i] + graphs[i].n;
-            mb->boff[i + 1] = mb->boff[i] + k[i];
-        }
-        mb->n = mb->noff[n_graphs];
-        if (mb->n >= (1ll << 31)) { free_mixed(mb); return UPR_ERR_INVALID; }
-        // groups by k, in increasing k, graphs in caller order within a group
-        std::vector<int32_t> ks(k, k + n_graphs);
-        std::sort(ks.begin(), ks.end());
-        ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
-        mb->k_of = ks;
-        mb->idx.assign(ks.size(), {});
-        for (int32_t i = 0; i < n_graphs; i++)
-            mb->idx[std::lower_bound(ks.begin(), ks.end(), k[i]) - ks.begin()].push_back(i);
-        const size_t G = ks.size();
-        mb->sub.assign(G, nullptr);
-        mb->streams.assign(G, nullptr);
-        mb->d_sub.assign(G, nullptr);
-        mb->gnodes.assign(G, 0);
-        mb->lmax.assign(n_graphs, 0);
-        std::vector<int64_t> map(mb->n);
-        std::vector<std::vector<upr_graph>> gs(G);
-        std::vector<std::vector<double>> es(G);
-        for (size_t g = 0; g < G; g++) {
-            UPR_CUDA(cudaStreamCreateWithFlags(&mb->streams[g], cudaStreamNonBlocking));
-            int64_t pos = 0;
-            for (int32_t i : mb->idx[g]) {
-                gs[g].push_back(graphs[i]);
-                es[g].push_back(eps[i]);
-                for (int64_t v = 0; v < graphs[i].n; v++) map[mb->noff[i] + v] = ((int64_t)g << kPosBits) | (pos + v);
-                pos += graphs[i].n;
-            }
-            mb->gnodes[g] = pos;
-        }
-        // the batches are bound concurrently, one host thread each
-        std::vector<upr_status> grc(G, UPR_OK);
-        std::vector<std::thread> th;
-        for (size_t g = 0; g < G; g++)
-            th.emplace_back([&, g] {
-                cudaSetDevice(mb->device);
-                upr_params p = prm;
-                p.stream = mb->streams[g];
-                grc[g] = upr_batch_create(gs[g].data(), (int32_t)gs[g].size(), ks[g], es[g].data(), &p, &mb->sub[g]);
-            });
-        for (auto &t : th) t.join();
-        for (size_t g = 0; g < G; g++)
-            if (grc[g] != UPR_OK) { rc = grc[g]; free_mixed(mb); return rc; }
-        for (size_t g = 0; g < G; g++) {
-            std::vector<int64_t> lm(gs[g].size());
-            upr_batch_info(mb->sub[g], nullptr, nullptr, lm.data());
-            for (size_t j = 0; j < gs[g].size(); j++) mb->lmax[mb->idx[g][j]] = lm[j];
-            if (mb->gnodes[g] > 0) UPR_CUDA(cudaMalloc(&mb->d_sub[g], sizeof(int32_t) * mb->gnodes[g]));
-        }
-        if (mb->n > 0) {
-            UPR_CUDA(cudaMalloc(&mb->d_part, sizeof(int32_t) * mb->n));
-            UPR_CUDA(cudaMalloc(&mb->d_map, sizeof(int64_t) * mb->n));
-            UPR_CUDA(cudaMemcpy(mb->d_map, map.data(), sizeof(int64_t) * mb->n, cudaMemcpyHostToDevice));
-        }
-        UPR_CUDA(cudaMalloc(&mb->d_ptrs, sizeof(int32_t *) * G));
-        UPR_CUDA(cudaMemcpy(mb->d_ptrs, mb->d_sub.data(), sizeof(int32_t *) * G, cudaMemcpyHostToDevice));
         UPR_CUDA(cudaEventCreateWithFlags(&mb->ev_fork, cudaEventDisableTiming));
         UPR_CUDA(cudaEventCreate(&mb->ev_t0));
         UPR_CUDA(cudaEventCreate(&mb->ev_t1));
+        rc = mixed_bind(mb, graphs, n_graphs, k, eps, mb->prm);
     } catch (const CudaError &e) {
-        free_mixed(mb);
-        return e.e == cudaErrorMemoryAllocation ? UPR_ERR_OOM : UPR_ERR_CUDA;
+        rc = e.e == cudaErrorMemoryAllocation ? UPR_ERR_OOM : UPR_ERR_CUDA;
     } catch (const std::bad_alloc &) {
-        free_mixed(mb);
-        return UPR_ERR_OOM;
+        rc = UPR_ERR_OOM;
     }
+    if (rc != UPR_OK) { free_mixed(mb); return rc; }
     *out = mb;
     return UPR_OK;
+}
+
+upr_status mixed_rebind(MixedBatch *mb, const upr_graph *graphs, int32_t n_graphs, const int32_t *k,
+                        const double *eps) {
+    if (!graphs || !k || !eps || n_graphs < 1) return UPR_ERR_INVALID;
+    try {
+        UPR_CUDA(cudaSetDevice(mb->device));
+        return mixed_bind(mb, graphs, n_graphs, k, eps, mb->prm);
+    } catch (const CudaError &e) {
+        return e.e == cudaErrorMemoryAllocation ? UPR_ERR_OOM : UPR_ERR_CUDA;
+    } catch (const std::bad_alloc &) {
+        return UPR_ERR_OOM;
+    }
 }
 
 void mixed_destroy(MixedBatch *mb) { free_mixed(mb); }

@@ -109,53 +109,26 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
-    const int4 zero = make_int4(0, 0, 0, 0);
-    const int64_t stride = (int64_t)gridDim.x * kGroups;
-    // Software pipeline over a group's list entries i, i + stride, ...: the
-    // next entry's row is in flight while the current one is evaluated, and
-    // the entry after it has its node, block and omega(I) loaded (an isolated
-    // node's row is zero: not read; a node no longer in an overloaded block
-    // proposes nothing: not read either).
-    int64_t i = (int64_t)blockIdx.x * kGroups + gid;
-    int32_t v_nxt = i < n1 ? list[i] : 0;
-    int32_t ag_nxt = i < n1 ? part[v_nxt] : 0;
-    bool rd_nxt = i < n1 && g.wI[v_nxt] > 0;
-    int4 r_nxt[CH];
-    {
-        const bool src = i < n1 && (BATCH ? st.over[ag_nxt] : s_over[BATCH ? 0 : ag_nxt]);
-        const int4 *row4 = reinterpret_cast<const int4 *>(W + (int64_t)v_nxt * k);
-#pragma unroll
-        for (int j = 0; j < CH; j++) {
-            const int q = gl + G * j;
-            r_nxt[j] = (src && rd_nxt && (EXACT || 4 * q < k)) ? row4[q] : zero;
-        }
-    }
-    int32_t v_2 = i + stride < n1 ? list[i + stride] : 0;
-    int32_t ag_2 = i + stride < n1 ? part[v_2] : 0;
-    bool rd_2 = i + stride < n1 && g.wI[v_2] > 0;
-    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += stride, i += stride) {
-        const int32_t v = v_nxt, ag = ag_nxt;
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t i = base + gid;
+        const int32_t v = i < n1 ? list[i] : 0;
+        const int32_t ag = i < n1 ? part[v] : 0;
         const int32_t a = BATCH ? blk_local(g, ag) : ag, b0 = ag - a;
         const bool src = i < n1 && (BATCH ? st.over[ag] : s_over[a]);
+        const int4 zero = make_int4(0, 0, 0, 0);
         int4 r[CH];
-#pragma unroll
-        for (int j = 0; j < CH; j++) r[j] = r_nxt[j];
-        // the next entry's row; the node, block and omega(I) of the one after
-        {
-            const bool src2 = i + stride < n1 && (BATCH ? st.over[ag_2] : s_over[BATCH ? 0 : ag_2]);
-            const int4 *row4 = reinterpret_cast<const int4 *>(W + (int64_t)v_2 * k);
+        // an isolated node's row is zero: not read
+        if (src && g.wI[v] > 0) {
+            const int4 *row4 = reinterpret_cast<const int4 *>(W + (int64_t)v * k);
 #pragma unroll
             for (int j = 0; j < CH; j++) {
                 const int q = gl + G * j;
-                r_nxt[j] = (src2 && rd_2 && (EXACT || 4 * q < k)) ? row4[q] : zero;
+                r[j] = (EXACT || 4 * q < k) ? row4[q] : zero;
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CH; j++) r[j] = zero;
         }
-        v_nxt = v_2;
-        ag_nxt = ag_2;
-        rd_nxt = rd_2;
-        v_2 = i + 2 * stride < n1 ? list[i + 2 * stride] : 0;
-        ag_2 = i + 2 * stride < n1 ? part[v_2] : 0;
-        rd_2 = i + 2 * stride < n1 && g.wI[v_2] > 0;
         const int q4 = a >> 2;
         int32_t mine = 0;
 #pragma unroll

@@ -248,49 +248,28 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
-    const int64_t stride = (int64_t)gridDim.x * kGroups;
-    const int4 zero = make_int4(0, 0, 0, 0);
-    // Software pipeline over a group's nodes v, v + stride, ...: the row of
-    // the next node is in flight while the current one is scored, and
-    // omega(I) one node further ahead decides whether that row is read at all
-    // (an isolated node's row is zero: not read).
-    int64_t v = (int64_t)blockIdx.x * kGroups + gid;
-    int32_t wI_cur = v < n ? g.wI[v] : 0;
-    int32_t part_cur = v < n ? part[v] : 0;
-    int4 r_nxt[CH];
-    {
-        const int4 *row4 = reinterpret_cast<const int4 *>(W + v * (int64_t)k);
-#pragma unroll
-        for (int j = 0; j < CH; j++) {
-            const int q = gl + G * j;
-            r_nxt[j] = (wI_cur > 0 && (EXACT || 4 * q < k)) ? __ldcs(row4 + q) : zero;
-        }
-    }
-    int32_t wI_nxt = v + stride < n ? g.wI[v + stride] : 0;
-    int32_t part_nxt = v + stride < n ? part[v + stride] : 0;
-    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += stride, v += stride) {
+    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
+        const int64_t v = base + gid;
         const bool active = v < n;
         int4 r[CH];
-#pragma unroll
-        for (int j = 0; j < CH; j++) r[j] = r_nxt[j];
-        const int32_t wIv = wI_cur, ag = part_cur;
-        // next node's row, and omega(I) and block of the node after it
-        {
-            const int4 *row4 = reinterpret_cast<const int4 *>(W + (v + stride) * (int64_t)k);
+        int32_t a = 0, b0 = 0;
+        const int4 zero = make_int4(0, 0, 0, 0);
+        // (rows are loaded without waiting for omega(I(v)): skipping the zero
+        // rows of isolated nodes behind that load measured slower)
+        const int32_t wIv = active ? g.wI[v] : 0;
+        if (active) {
+            const int32_t ag = part[v];
+            a = BATCH ? blk_local(g, ag) : ag;
+            b0 = ag - a;
+            const int4 *row4 = reinterpret_cast<const int4 *>(W + v * (int64_t)k);
 #pragma unroll
             for (int j = 0; j < CH; j++) {
                 const int q = gl + G * j;
-                r_nxt[j] = (wI_nxt > 0 && (EXACT || 4 * q < k)) ? __ldcs(row4 + q) : zero;
+                r[j] = (EXACT || 4 * q < k) ? __ldcs(row4 + q) : zero;
             }
-        }
-        wI_cur = wI_nxt;
-        part_cur = part_nxt;
-        wI_nxt = v + 2 * stride < n ? g.wI[v + 2 * stride] : 0;
-        part_nxt = v + 2 * stride < n ? part[v + 2 * stride] : 0;
-        int32_t a = 0, b0 = 0;
-        if (active) {
-            a = BATCH ? blk_local(g, ag) : ag;
-            b0 = ag - a;
+        } else {
+#pragma unroll
+            for (int j = 0; j < CH; j++) r[j] = zero;
         }
         const int q4 = a >> 2;
         int32_t mine = 0;

@@ -275,3 +275,50 @@ def test_mixed_k_context_refuses_single_graph_calls(upr):
     assert lib.upr_refine(ctx.handle, part.ctypes.data_as(ctypes.c_void_p), 1, 0, None) == upr.UPR_ERR_INVALID
     cut = ctypes.c_int64()
     assert lib.upr_cut(ctx.handle, part.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cut), None) == upr.UPR_ERR_INVALID
+
+
+def _check_ctx(upr, ctx, ws, rounds=3):
+    part = _packed(ws)
+    status, cin, cout, st = upr.upr_batch_refine(ctx, part, rounds)
+    off = ctx.offsets
+    for i, w in enumerate(ws):
+        rc, ref, cut, _ = oracle.refine(w, w.part, rounds)
+        assert status[i] == rc, i
+        if rc == 0:
+            assert np.array_equal(part[off[i]:off[i + 1]], ref), i
+            assert cout[i] == cut, i
+
+
+@pytest.mark.parametrize("graphs_mode", [1, 2])
+def test_rebind_contexts(upr, graphs_mode):
+    """upr_batch_rebind: a mixed context bound to graphs of other k (a k it
+    had reused, a new one added, one dropped) and back, a same-k batch bound
+    to other graphs, a one-graph context bound to another graph (smaller:
+    its memory reused); every result equals the oracle's; a same-k context
+    refuses graphs of several k and stays usable."""
+    prm = upr.upr_params_default()
+    prm.graphs = graphs_mode
+    a = [synth.random_small(900 + i, 150 + 50 * i, 5.0, [4, 8, 4, 8][i]) for i in range(4)]
+    b = [synth.random_small(950 + i, 300 + 40 * i, 4.0, [8, 16, 16, 8, 16][i]) for i in range(5)]
+    ctx = upr.create_batch_from_workloads(a, params=prm)
+    for ws in (a, b, a, b):
+        upr.upr_batch_rebind(ctx, [(w.xadj, w.adj, w.vwgt, w.adjw) for w in ws], [w.k for w in ws],
+                             [w.eps for w in ws])
+        for _ in range(2):
+            _check_ctx(upr, ctx, ws)
+    same = [synth.random_small(980 + i, 200 + 30 * i, 5.0, 8) for i in range(3)]
+    other = [synth.random_small(990 + i, 120 + 30 * i, 6.0, 8) for i in range(4)]
+    bctx = upr.create_batch_from_workloads(same, params=prm)
+    _check_ctx(upr, bctx, same)
+    upr.upr_batch_rebind(bctx, [(w.xadj, w.adj, w.vwgt, w.adjw) for w in other], [8] * 4, [w.eps for w in other])
+    _check_ctx(upr, bctx, other)
+    with pytest.raises(upr.UprError) as e:
+        upr.upr_batch_rebind(bctx, [(w.xadj, w.adj, w.vwgt, w.adjw) for w in b], [w.k for w in b],
+                             [w.eps for w in b])
+    assert e.value.status == upr.UPR_ERR_INVALID
+    _check_ctx(upr, bctx, other)                # unchanged and usable
+    big, small = synth.random_small(1001, 3000, 6.0, 16), synth.random_small(1002, 1000, 5.0, 16)
+    one = upr.create_batch_from_workloads([big], params=prm)
+    _check_ctx(upr, one, [big])
+    upr.upr_batch_rebind(one, [(small.xadj, small.adj, small.vwgt, small.adjw)], [16], [small.eps])
+    _check_ctx(upr, one, [small])
