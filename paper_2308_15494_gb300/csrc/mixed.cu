@@ -35,6 +35,9 @@ struct MixedBatch {
     int32_t **d_ptrs = nullptr;                   // device copy of d_sub
     int64_t *d_map = nullptr;                     // [n] caller node -> (group << 40) | position in the group
     size_t part_cap = 0, map_cap = 0, ptrs_cap = 0;
+    int64_t *d_noff = nullptr, *d_gpos = nullptr;  // per caller graph: node offset, first position in its batch
+    int32_t *d_grp = nullptr;                     // per caller graph: its batch
+    size_t noff_cap = 0, gpos_cap = 0, grp_cap = 0;
     cudaEvent_t ev_fork = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
 };
 
@@ -58,6 +61,21 @@ __global__ void k_mix_scatter(int32_t *__restrict__ part, const int64_t *__restr
     }
 }
 
+// map[j] for every caller node j: its batch (group) and its position in the
+// batch's packed order, from per-graph node offsets (caller order), groups
+// and first positions in their batches.
+__global__ void k_mix_map(const int64_t *__restrict__ noff, const int32_t *__restrict__ grp,
+                          const int64_t *__restrict__ gpos, int32_t ng, int64_t n, int64_t *__restrict__ map) {
+    UPR_FOR(j, n) {
+        int32_t lo = 0, hi = ng - 1;            // last graph i with noff[i] <= j
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (noff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        map[j] = ((int64_t)grp[lo] << kPosBits) | (gpos[lo] + (j - noff[lo]));
+    }
+}
+
 void free_mixed(MixedBatch *mb) {
     if (!mb) return;
     for (upr_ctx *c : mb->sub) upr_destroy(c);
@@ -68,6 +86,9 @@ void free_mixed(MixedBatch *mb) {
     if (mb->d_part) cudaFree(mb->d_part);
     if (mb->d_ptrs) cudaFree(mb->d_ptrs);
     if (mb->d_map) cudaFree(mb->d_map);
+    if (mb->d_noff) cudaFree(mb->d_noff);
+    if (mb->d_gpos) cudaFree(mb->d_gpos);
+    if (mb->d_grp) cudaFree(mb->d_grp);
     if (mb->ev_fork) cudaEventDestroy(mb->ev_fork);
     if (mb->ev_t0) cudaEventDestroy(mb->ev_t0);
     if (mb->ev_t1) cudaEventDestroy(mb->ev_t1);
@@ -146,7 +167,8 @@ upr_status mixed_bind(MixedBatch *mb, const upr_graph *graphs, int32_t n_graphs,
         mb->idx[std::lower_bound(ks.begin(), ks.end(), k[i]) - ks.begin()].push_back(i);
     mb->gnodes.assign(G, 0);
     mb->lmax.assign(n_graphs, 0);
-    std::vector<int64_t> map(mb->n);
+    std::vector<int32_t> grp(n_graphs);
+    std::vector<int64_t> gpos(n_graphs);
     std::vector<std::vector<upr_graph>> gs(G);
     std::vector<std::vector<double>> es(G);
     for (size_t g = 0; g < G; g++) {
@@ -155,7 +177,8 @@ upr_status mixed_bind(MixedBatch *mb, const upr_graph *graphs, int32_t n_graphs,
         for (int32_t i : mb->idx[g]) {
             gs[g].push_back(graphs[i]);
             es[g].push_back(eps[i]);
-            for (int64_t v = 0; v < graphs[i].n; v++) map[mb->noff[i] + v] = ((int64_t)g << kPosBits) | (pos + v);
+            grp[i] = (int32_t)g;
+            gpos[i] = pos;
             pos += graphs[i].n;
         }
         mb->gnodes[g] = pos;
@@ -185,8 +208,20 @@ upr_status mixed_bind(MixedBatch *mb, const upr_graph *graphs, int32_t n_graphs,
     reserve(&mb->d_part, &mb->part_cap, (size_t)mb->n);
     reserve(&mb->d_map, &mb->map_cap, (size_t)mb->n);
     reserve(&mb->d_ptrs, &mb->ptrs_cap, G);
-    if (mb->n > 0) UPR_CUDA(cudaMemcpy(mb->d_map, map.data(), sizeof(int64_t) * mb->n, cudaMemcpyHostToDevice));
     UPR_CUDA(cudaMemcpy(mb->d_ptrs, mb->d_sub.data(), sizeof(int32_t *) * G, cudaMemcpyHostToDevice));
+    if (mb->n > 0) {
+        // the node map on the device, from per-graph offsets, batches and
+        // first positions (in buffers kept across bindings)
+        reserve(&mb->d_noff, &mb->noff_cap, (size_t)n_graphs + 1);
+        reserve(&mb->d_gpos, &mb->gpos_cap, (size_t)n_graphs);
+        reserve(&mb->d_grp, &mb->grp_cap, (size_t)n_graphs);
+        UPR_CUDA(cudaMemcpy(mb->d_noff, mb->noff.data(), sizeof(int64_t) * (n_graphs + 1), cudaMemcpyHostToDevice));
+        UPR_CUDA(cudaMemcpy(mb->d_gpos, gpos.data(), sizeof(int64_t) * n_graphs, cudaMemcpyHostToDevice));
+        UPR_CUDA(cudaMemcpy(mb->d_grp, grp.data(), sizeof(int32_t) * n_graphs, cudaMemcpyHostToDevice));
+        k_mix_map<<<grid_for(mb->n), 256, 0, mb->s>>>(mb->d_noff, mb->d_grp, mb->d_gpos, n_graphs, mb->n, mb->d_map);
+        UPR_LAUNCH_CHECK();
+        UPR_CUDA(cudaStreamSynchronize(mb->s));
+    }
     return UPR_OK;
 }
 
