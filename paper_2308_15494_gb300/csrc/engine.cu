@@ -107,12 +107,13 @@ namespace {
 // Slots of the device counters (upr_ctx::counts).
 enum {
     CNT_CAND = 0, CNT_M, CNT_P, CNT_S, CNT_A, CNT_I, CNT_HUB, CNT_BADPART, CNT_L1, CNT_X, CNT_EVM, CNT_EVI,
-    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_HIST, CNT_EXACT, CNT_SLOTS = 32
+    CNT_I1, CNT_OVER0, CNT_INFEAS, CNT_HIST, CNT_EXACT, CNT_SORTP, CNT_SLOTS = 32
 };
 
 // Per-call sums of the step graph's rounds (upr_ctx::dstats): candidates,
 // moves, rebalancing moves, sub-rounds, sequence length, applied moves, the
-// primitives' error word, infeasible rounds, interleaved length.
+// primitives' error word, infeasible rounds, interleaved length, runs of the
+// sub-rounds' conditional sort passes.
 __global__ void k_round_stats(const int32_t *__restrict__ cnt, const RebalCtl *__restrict__ ctl,
                               const long long *__restrict__ best, const int64_t *__restrict__ tot, int batch,
                               const int32_t *__restrict__ err, long long *__restrict__ d) {
@@ -127,6 +128,7 @@ __global__ void k_round_stats(const int32_t *__restrict__ cnt, const RebalCtl *_
     d[6] |= *err;
     d[7] += infeasible ? 1 : 0;
     d[8] += cnt[CNT_X];
+    d[9] += cnt[CNT_SORTP];
 }
 }  // namespace
 
@@ -198,6 +200,8 @@ struct upr_ctx {
     uint64_t gen = 0, reb_gen = ~0ull;  // binding generation; the one reb_exec belongs to
     LaneCfg reb_cfg{};
     int reb_body_kernels = 0;
+    int reb_if_kernels = 0;           // kernels of the conditional sort passes in the sub-round body
+    cudaStream_t s_if = nullptr;      // capture stream of that conditional body
     int64_t rounds_bound = 0;         // rounds run since the binding
     bool cut_pending = false;         // the next build also computes the cut of part0 (load_part skipped it)
     int32_t lp_attempts = 0;          // label propagation rounds run by the current call (kept or not)
@@ -251,6 +255,7 @@ struct upr_ctx {
     SortBuf sb[3];
     int64_t *c_sorted, *c_excl, *delta, *d_excl;
     uint64_t *packed, *qmax;
+    uint64_t *prio_rep;                 // [2 * kPrioBins] rebalancing: a key per prefilter bin
     int32_t *emit, *qbefore, *em_excl, *pos_m;
     int32_t *diff, *diff_excl;
     int32_t *hub_flag, *hub_excl, *hubs;
@@ -345,6 +350,7 @@ void layout(upr_ctx *c, Arena &A) {
     c->d_excl = A.take<int64_t>(n2);
     c->packed = A.take<uint64_t>(n2);
     c->qmax = A.take<uint64_t>(n2);
+    c->prio_rep = A.take<uint64_t>(2 * (size_t)kPrioBins);
     for (int32_t **p : {&c->seg_first, &c->rbeg, &c->rend, &c->ebeg, &c->eend, &c->qfin, &c->left, &c->left_excl})
         *p = A.take<int32_t>(k);
     c->best_parts = A.take<long long>(2048);
@@ -516,12 +522,29 @@ bool fused_rebalance(const upr_ctx *c, int key_bits) {
            (int64_t)c->G.K() * ceil_div(n, (int64_t)2048) <= 2 * n;
 }
 
+// The fused sub-round's steps after the proposals in one cooperative launch
+// (UPR_MEGA=0 in the environment: one launch per step, the same results).
+bool mega_rebalance() {
+    static int env = -1;
+    if (env < 0) {
+        const char *v = getenv("UPR_MEGA");
+        int coop = 0, dev = 0;
+        UPR_CUDA(cudaGetDevice(&dev));
+        UPR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        env = (v && *v == '0') || !coop ? 0 : 1;
+    }
+    return env == 1;
+}
+
 // One rebalancing sub-round (Sec. 6), enqueued on s.  Every argument is fixed
 // for the binding (the sub-round number and every list length live in device
 // memory), so the same launches can be captured once and replayed.  first:
 // the round's first sub-round, which may time the proposal kernel's lane
-// schedules (host-driven loop only).
-void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool first, cudaStream_t s) {
+// schedules (host-driven loop only).  cond: the condition of a graph-resident
+// loop; returns true when the sub-round's last kernel has set it (else the
+// caller adds rebalance_continue).
+bool enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool first, cudaStream_t s,
+                      cudaGraphConditionalHandle cond = 0) {
     const GraphDev &G = c->G;
     const int64_t n = c->n;
     const int kbits = std::max(1, bit_length((uint64_t)(G.K() - 1)));
@@ -548,15 +571,68 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
         // with the prefilter histogram, the cut bins, the kept proposals as
         // (key, node), one sort by key, selection and admission from
         // per-tile block sums, R appended and the moves applied
-        uint64_t *rep = reinterpret_cast<uint64_t *>(c->qmax);       // kPrioBins keys (free during rebalancing)
+        uint64_t *rep = c->prio_rep;
         int32_t *exact = cnt + CNT_EXACT;
+        if (mega_rebalance()) {
+            // steps 1 and 3-7 in one cooperative launch (the sort buffers of
+            // sb[1] and sb[2] hold the compacted proposers: free here)
+            RebalMega m{};
+            m.flags = c->flags;
+            m.list = c->L1;
+            m.lsrc = st.lsrc;
+            m.lgain = st.lgain;
+            m.d_n1 = &ctl->n1_active;
+            m.list2 = reinterpret_cast<int32_t *>(c->sb[1].v);
+            m.lsrc2 = reinterpret_cast<int32_t *>(c->sb[1].va);
+            m.lgain2 = reinterpret_cast<int32_t *>(c->sb[2].v);
+            m.gbits = c->gbits;
+            m.cbits = c->cbits;
+            m.gain_only = c->prm.gain_priority;
+            m.hist = c->prio_hist;
+            m.rep = rep;
+            m.cut = c->prio_cut;
+            m.over = c->over_d;
+            m.C = c->C;
+            m.keys = c->sb[0].k;
+            m.keys_alt = c->sb[0].ka;
+            m.vals = c->sb[0].v;
+            m.vals_alt = c->sb[0].va;
+            m.part = c->part;
+            m.prop_tgt = c->prop_tgt;
+            m.sel = reinterpret_cast<int8_t *>(c->flags2);
+            m.h0 = reinterpret_cast<long long *>(c->c_sorted);
+            m.h1 = reinterpret_cast<long long *>(c->c_excl);
+            m.reject = c->reject_d;
+            m.ctl = ctl;
+            m.R_node = c->R_node; m.R_from = c->R_from; m.R_to = c->R_to; m.R_sub = c->R_sub;
+            m.r_to = c->r_to; m.r_at = c->r_at;
+            m.Cd = c->Cd;
+            m.d_np = cnt + CNT_L1;
+            m.d_nk = cnt + CNT_P;
+            m.d_na = cnt + CNT_A;
+            m.exact = exact;
+            rebalance_fused_mega(G, m, key_bits, n, c->tmp, s);
+            table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
+                       c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
+            rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s, cond,
+                                c->prm.max_subrounds);
+            return cond != 0;
+        }
         rebalance_fused_compact_hist(G, c->flags, c->L1, &ctl->n1_active, n, cnt + CNT_L1, st.lgain, st.lsrc,
                                      c->gbits, c->cbits, c->prm.gain_priority, c->prio_hist, rep, exact, c->tmp, s);
         rebalance_prio_cut(G, c->over_d, c->C, c->prio_hist, c->prio_cut, s);
         rebalance_fused_keep_keys(G, c->L1, cnt + CNT_L1, n, st.lgain, st.lsrc, c->prio_cut, c->gbits, c->cbits,
                                   c->prm.gain_priority, c->sb[0].k, c->sb[0].v, cnt + CNT_P, rep, exact, c->tmp, s);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        static int if_env = -1;
+        if (if_env < 0) { const char *v = getenv("UPR_SORT_IF"); if_env = (v && *v == '0') ? 0 : 1; }
+        if (if_env) UPR_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusActive && !c->s_if)
+            UPR_CUDA(cudaStreamCreateWithFlags(&c->s_if, cudaStreamNonBlocking));
+        int if_kernels = 0;
         rebalance_fused_sort(c->sb[0].k, c->sb[0].v, c->sb[0].ka, c->sb[0].va, cnt + CNT_P, n, key_bits, c->gbits,
-                             c->cbits, exact, c->tmp, s);
+                             c->cbits, exact, c->tmp, s, c->s_if, cnt + CNT_SORTP, &if_kernels);
+        if (cs == cudaStreamCaptureStatusActive) c->reb_if_kernels = if_kernels;
         const uint32_t *U = c->sb[0].va;
         rebalance_fused_select_admit(G, U, cnt + CNT_P, n, c->part, c->prop_tgt, c->C,
                                      reinterpret_cast<int8_t *>(c->flags2), reinterpret_cast<long long *>(c->c_sorted),
@@ -565,8 +641,8 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
                                      c->tmp, s);
         table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
                    c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
-        rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
-        return;
+        rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s, cond, c->prm.max_subrounds);
+        return cond != 0;
     }
     select_values(c->flags, c->L1, c->L1, cnt + CNT_L1, Count{&ctl->n1_active, n}, c->tmp, s);
     // proposals that cannot be in their source's minimal prefix are dropped
@@ -612,6 +688,7 @@ void enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
                c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
     rebalance_end(G, c->C, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s);
+    return false;
 }
 
 // The rebalancing loop as a graph: a kernel sets the condition of a while
@@ -652,8 +729,8 @@ bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
         UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         capturing = true;
         const long long b0 = g_upr_launches;
-        enqueue_subround(c, st, light, false, c->s_cap);
-        rebalance_continue(c->ctl, c->prm.max_subrounds, cond, c->s_cap);
+        if (!enqueue_subround(c, st, light, false, c->s_cap, cond))
+            rebalance_continue(c->ctl, c->prm.max_subrounds, cond, c->s_cap);
         c->reb_body_kernels = (int)(g_upr_launches - b0);
         captured += c->reb_body_kernels;
         capturing = false;
@@ -724,8 +801,8 @@ void rebalance_phase(upr_ctx *c, int32_t r, RoundInfo &ri, TraceSink *tr) {
         if (!c->s_body) UPR_CUDA(cudaStreamCreateWithFlags(&c->s_body, cudaStreamNonBlocking));
         UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         const long long b0 = g_upr_launches;
-        enqueue_subround(c, st, light, false, c->s_body);
-        rebalance_continue(ctl, c->prm.max_subrounds, cond, c->s_body);
+        if (!enqueue_subround(c, st, light, false, c->s_body, cond))
+            rebalance_continue(ctl, c->prm.max_subrounds, cond, c->s_body);
         c->reb_body_kernels = (int)(g_upr_launches - b0);
         cudaGraph_t out = nullptr;
         UPR_CUDA(cudaStreamEndCapture(c->s_body, &out));
@@ -1005,7 +1082,9 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
     ri.n_moves = hc[CNT_M];
     ri.n_rebal = c->hctl->nR;
     ri.subrounds = c->hctl->subrounds;
-    if (ri.graph) g_upr_launches += (1 + (long long)c->reb_body_kernels * ri.subrounds);
+    if (ri.graph)
+        g_upr_launches += (1 + (long long)c->reb_body_kernels * ri.subrounds +
+                           (long long)c->reb_if_kernels * hc[CNT_SORTP]);
     ri.n_inter = hc[CNT_X];
     ri.n_seq = hc[CNT_I];
     // one graph: an infeasible round applies nothing and is an error; a
@@ -1110,6 +1189,7 @@ void free_ctx(upr_ctx *c) {
     if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
     if (c->s_cap) cudaStreamDestroy(c->s_cap);
     if (c->s_body) cudaStreamDestroy(c->s_body);
+    if (c->s_if) cudaStreamDestroy(c->s_if);
     if (c->F_all) cudaFree(c->F_all);
     if (c->hF_all) cudaFreeHost(c->hF_all);
     if (c->h) cudaFreeHost(c->h);
@@ -1463,7 +1543,7 @@ bool run_step_graph(upr_ctx *c, int32_t rounds, int32_t total, upr_stats &st) {
     st.n_sequence += d[4];
     st.n_applied += d[5];
     st.rebalance_graphs += rounds;
-    g_upr_launches += (c->step_kernels + (long long)c->reb_body_kernels * d[3]);
+    g_upr_launches += (c->step_kernels + (long long)c->reb_body_kernels * d[3] + (long long)c->reb_if_kernels * d[9]);
     return true;
 }
 

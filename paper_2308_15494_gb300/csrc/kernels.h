@@ -341,12 +341,54 @@ void rebalance_fused_keep_keys(const GraphDev &g, const int32_t *list, const int
                                const int32_t *lgain, const int32_t *lsrc, const int32_t *cut, int gbits, int cbits,
                                int gain_only, uint64_t *keys, uint32_t *vals, int32_t *d_out, const uint64_t *rep,
                                int32_t *exact, Scratch tmp, cudaStream_t s);
+// Steps 1 and 3-7 of the fused sub-round (compaction with the prefilter
+// histogram, cut bins, kept keys, the sort, selection, admission and the
+// moves) in one cooperative launch with grid barriers: the same results as
+// the separate fused kernels.  The wrapper sets the fields after `exact`.
+struct RebalMega {
+    const int32_t *flags;                    // [n1] proposer flags by list index
+    int32_t *list, *lsrc, *lgain;            // [n1] the list (becomes the proposers), their blocks and gains
+    const int32_t *d_n1;                     // n1
+    int32_t *list2, *lsrc2, *lgain2;         // [n] the compacted proposers, their blocks and gains
+    int gbits, cbits, gain_only;
+    unsigned long long *hist;                // [K * kPrioBins] prefilter weights (rows of overloaded sources cleared)
+    uint64_t *rep;                           // [kPrioBins] some proposal's key per bin
+    int32_t *cut;                            // [K] cut bin per source
+    const int8_t *over;
+    const int64_t *C;
+    uint64_t *keys, *keys_alt;               // [n] kept keys; the sorted keys
+    uint32_t *vals, *vals_alt;               // [n] kept nodes; the sorted nodes
+    int32_t *part;
+    const int32_t *prop_tgt;
+    int8_t *sel;                             // [n] per sorted proposal: 1 selected, 2 admitted
+    long long *h0, *h1;                      // [K * tiles] per-(block, tile) weights and their row prefixes
+    int8_t *reject;
+    const RebalCtl *ctl;
+    int32_t *R_node, *R_from, *R_to, *R_sub, *r_to, *r_at;
+    long long *Cd;
+    int32_t *d_np, *d_nk, *d_na;             // proposers, kept, admitted
+    int32_t *exact;
+    // set by rebalance_fused_mega
+    const int32_t *vwgt = nullptr;
+    const int64_t *Lb = nullptr;
+    int K = 0, passes = 0, vec = 0;
+    int32_t *tab = nullptr;                  // tile counts 3 x [tcap], digit totals [256], digit counts [256 * tcap]
+    int64_t tcap = 0;
+    unsigned long long *bar = nullptr;       // the grid barrier's arrival counter
+    int32_t *err = nullptr;
+};
+void rebalance_fused_mega(const GraphDev &g, RebalMega m, int key_bits, int64_t n_max, Scratch tmp, cudaStream_t s);
 // Stable sort of (keys, vals)[0..*d_n) by key (key_bits, an odd number of
 // 8-bit passes), or by the key's prefilter bin alone when *exact; the result
-// is in the alternate buffers (returns true).
+// is in the alternate buffers (returns true).  While s is being captured and
+// s_aux and later_runs are given, the passes after the first are captured on
+// s_aux as the body of a conditional node that runs only when they sort
+// anything; each run adds 1 to *later_runs, and *later_kernels = the body's
+// kernels (0 when no such node was made).
 bool rebalance_fused_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const int32_t *d_n,
                           int64_t n_max, int key_bits, int gbits, int cbits, const int32_t *exact, Scratch tmp,
-                          cudaStream_t s);
+                          cudaStream_t s, cudaStream_t s_aux = nullptr, int32_t *later_runs = nullptr,
+                          int *later_kernels = nullptr);
 // U[0..*d_np): proposals (nodes) in priority order.  Minimal prefix per
 // source, longest fitting prefix per target, the admitted appended to R at
 // ctl->nR (count *d_na), part / r_to / r_at updated, block-weight changes
@@ -358,9 +400,12 @@ void rebalance_fused_select_admit(const GraphDev &g, const uint32_t *U, const in
                                   const RebalCtl *ctl, int32_t *R_node, int32_t *R_from, int32_t *R_to,
                                   int32_t *R_sub, int32_t *r_to, int32_t *r_at, long long *Cd, int32_t *d_na,
                                   Scratch tmp, cudaStream_t s);
-// C += Cd, Cd = 0; then k_reb_end's update of the excluded set and the stop flag
+// C += Cd, Cd = 0; then k_reb_end's update of the excluded set and the stop
+// flag; with cond (a graph-resident loop) also the loop's condition, as
+// rebalance_continue sets it
 void rebalance_fused_end(const GraphDev &g, int64_t *C, long long *Cd, int8_t *excl, const int8_t *reject,
-                         const int32_t *d_na, RebalCtl *ctl, cudaStream_t s);
+                         const int32_t *d_na, RebalCtl *ctl, cudaStream_t s, cudaGraphConditionalHandle cond = 0,
+                         int32_t max_subrounds = 0);
 // The prefilter's cut bin of every overloaded source (hist rows read are cleared).
 void rebalance_prio_cut(const GraphDev &g, const int8_t *over, const int64_t *C, unsigned long long *hist, int32_t *cut,
                         cudaStream_t s);

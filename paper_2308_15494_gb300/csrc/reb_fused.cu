@@ -181,22 +181,38 @@ __global__ void __launch_bounds__(kThreads) k_fr_compact_hist(const int32_t *__r
         }
         __syncthreads();
         int32_t pos = s_excl + pre;
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int j = 0; j < kItems; j++) {
-            if (!x[j]) continue;
-            const int32_t u = y[j];
-            list[pos] = u;
-            lsrc[pos] = ya[j];
-            lgain[pos] = yg[j];
-            pos++;
-            const uint64_t cu = vwgt ? (uint64_t)vwgt[u] : 1ull;
-            const int64_t gu = yg[j];
-            const int bin = prio_bin_f(gu, gain_only ? 1ull : cu, cbits);
-            // some proposal's key per bin (any one: plain stores race, one
-            // wins), in shared memory first: one global store per bin and CTA
-            s_rep[bin] = prio_key_f(gu, gain_only ? 1ull : cu, gbits, cbits);
-            s_has[bin] = 1;
-            const uint32_t key = (uint32_t)ya[j] * kPrioBins + bin;
+            uint32_t key = kHistEmpty;
+            uint64_t cu = 0;
+            if (x[j]) {
+                const int32_t u = y[j];
+                list[pos] = u;
+                lsrc[pos] = ya[j];
+                lgain[pos] = yg[j];
+                pos++;
+                cu = vwgt ? (uint64_t)vwgt[u] : 1ull;
+                const int64_t gu = yg[j];
+                const int bin = prio_bin_f(gu, gain_only ? 1ull : cu, cbits);
+                // some proposal's key per bin (any one: plain stores race, one
+                // wins), in shared memory first: one global store per bin and CTA
+                s_rep[bin] = prio_key_f(gu, gain_only ? 1ull : cu, gbits, cbits);
+                s_has[bin] = 1;
+                key = (uint32_t)ya[j] * kPrioBins + bin;
+            }
+            // the lanes holding the same (source, bin) add their weights
+            // first, so that one lane per group updates the table (many
+            // proposals share their source and bin)
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            unsigned long long tot;
+            if (vwgt) {
+                tot = 0;
+                for (unsigned mm = peers; mm; mm &= mm - 1) tot += __shfl_sync(peers, cu, __ffs(mm) - 1);
+            } else {
+                tot = (unsigned long long)__popc(peers);
+            }
+            if (key == kHistEmpty || lane != __ffs(peers) - 1) continue;
             uint32_t h = (key * 0x9E3779B1u) >> 21;          // 11 bits: kHistSlots
             bool done = false;
             for (int probe = 0; probe < 32 && !done; probe++) {
@@ -206,12 +222,12 @@ __global__ void __launch_bounds__(kThreads) k_fr_compact_hist(const int32_t *__r
                     if (cur == kHistEmpty) cur = key;
                 }
                 if (cur == key) {
-                    atomicAdd(&s_val[h], (unsigned long long)cu);
+                    atomicAdd(&s_val[h], tot);
                     done = true;
                 }
                 h = (h + 1) & (kHistSlots - 1);
             }
-            if (!done) atomicAdd(&hist[key], (unsigned long long)cu);   // crowded table: straight to the histogram
+            if (!done) atomicAdd(&hist[key], tot);   // crowded table: straight to the histogram
         }
         __syncthreads();
         if (alone) break;
@@ -336,12 +352,21 @@ __global__ void __launch_bounds__(kThreads) k_fr_radix_scatter(const uint64_t *_
                                                                uint64_t *__restrict__ okeys, uint32_t *__restrict__ ovals,
                                                                const int32_t *__restrict__ d_n, int pass, int gbits,
                                                                int cbits, const int32_t *__restrict__ d_exact,
-                                                               const int32_t *__restrict__ offs) {
+                                                               const int32_t *__restrict__ offs,
+                                                               cudaGraphConditionalHandle later,
+                                                               int32_t *__restrict__ later_runs) {
     __shared__ int s_cnt[2 * kWarps * (kBins + 1)];
     __shared__ int s_run[kBins + 1];
     __shared__ int s_off[kBins];
     const int64_t n = *d_n;
     const bool exact = *d_exact != 0;
+    if (later_runs && blockIdx.x == 0 && threadIdx.x == 0) {
+        // captured form: the later passes are the body of a conditional node,
+        // run only when they sort anything
+        const bool run = n > kTile && !exact;
+        cudaGraphSetConditional(later, run ? 1u : 0u);
+        if (run) *later_runs += 1;
+    }
     if (n <= kTile || (exact && pass > 0)) return;
     const int64_t T = tiles_of(n);
     for (int64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
@@ -643,9 +668,11 @@ __global__ void __launch_bounds__(kThreads) k_fr_admit(const uint32_t *__restric
 // ---- end of the sub-round: the block-weight changes folded in, then the
 // targets that rejected a move excluded; stop when nothing was admitted and
 // no target was newly excluded, or when no block is overloaded any more.
+// In a graph-resident loop (cond != 0) it also sets the loop's condition:
+// another sub-round while the loop has not stopped and sub-rounds are left.
 __global__ void k_fr_end(int64_t *__restrict__ C, long long *__restrict__ Cd, const int64_t *__restrict__ Lb, int32_t K,
                          int8_t *__restrict__ excl, const int8_t *__restrict__ reject, const int32_t *__restrict__ d_na,
-                         RebalCtl *__restrict__ ctl) {
+                         RebalCtl *__restrict__ ctl, cudaGraphConditionalHandle cond, int32_t max_subrounds) {
     __shared__ int s_grew, s_over;
     if (threadIdx.x == 0) s_grew = 0, s_over = 0;
     __syncthreads();
@@ -663,6 +690,560 @@ __global__ void k_fr_end(int64_t *__restrict__ C, long long *__restrict__ Cd, co
         const int32_t na = *d_na;
         ctl->nR += na;
         if ((na == 0 && !s_grew) || !s_over) ctl->stopped = 1;
+    }
+    if (threadIdx.x == 0 && cond)
+        cudaGraphSetConditional(cond, (!ctl->stopped && ctl->subrounds < max_subrounds) ? 1u : 0u);
+}
+
+
+// ---- steps 1 and 3-7 of the sub-round in one cooperative launch.  The
+// same tiles and the same per-tile code as the kernels above; the prefix of
+// a tile over the tiles before it comes from per-tile totals read after a
+// grid barrier instead of the look-back, and the per-(block, tile) weight
+// sums are scanned row by row (one row per CTA).  Every CTA passes every
+// barrier (no early return), and every wait is bounded: a wait that gives up
+// sets the error word and the launch runs to its end.
+
+// Grid barrier on a 64-bit arrival counter that only grows: the barrier that
+// a CTA reaches with arrival number `old` ends when the count reaches the
+// next multiple of the grid size.
+__device__ __forceinline__ void grid_sync(unsigned long long *count, int32_t *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long old = atomicAdd(count, 1ull);
+        const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
+        for (int it = 0;; it++) {
+            unsigned long long v;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            if (it >= kMaxSpin || ((it & 1023) == 1023 && gave_up(err))) { atomicOr(err, 2); break; }
+            if (it >= 16) __nanosleep(32);
+        }
+    }
+    __syncthreads();
+}
+
+// Sum of tc[0..t) (all threads get it).
+__device__ __forceinline__ int32_t tiles_before(const int32_t *tc, int64_t t, int32_t *s_warp) {
+    int32_t v = 0;
+    for (int64_t i = threadIdx.x; i < t; i += kThreads) v += tc[i];
+    int32_t total;
+    block_exclusive<OpSum>(v, s_warp, &total);
+    return total;
+}
+
+// Row-wise exclusive scan in place: row[0..T) becomes the sum of the entries
+// before each one; returns the row's total (all threads).
+template <typename T>
+__device__ __forceinline__ T scan_row(T *row, int64_t len, T *s_warp) {
+    T carry = 0;
+    for (int64_t base = 0; base < len; base += kTile) {
+        T x[kItems];
+        load_items(row, base, len, false, x);
+        T c = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) c += x[j];
+        T total;
+        const T pre = block_exclusive<OpSum>(c, s_warp, &total);
+        T run = carry + pre;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const T v = x[j];
+            x[j] = run;
+            run += v;
+        }
+        store_items(row, base, len, false, x);
+        carry += total;
+    }
+    return carry;
+}
+
+using MegaArgs = RebalMega;
+
+constexpr int kMegaSmem = 43136;
+
+template <bool UNIT>
+__global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
+    __shared__ __align__(16) unsigned char s_raw[kMegaSmem];
+    __shared__ int32_t s_warp[kWarps];
+    __shared__ int64_t s_w64s[kWarps];
+    __shared__ uint64_t s_w64[kWarps];
+    __shared__ int32_t s_excl;
+    const int64_t P = gridDim.x;
+    const int K = a.K;
+    int32_t *tc1 = a.tab, *tc2 = tc1 + a.tcap, *tc3 = tc2 + a.tcap;
+    int32_t *dtot = tc3 + a.tcap, *tbl = dtot + kBins;     // (digits: only with more than one tile)
+
+    // ---- 1. proposers compacted (node order) with the prefilter histogram
+    const int64_t n1 = *a.d_n1;
+    const int64_t T1 = tiles_of(n1);
+    for (int64_t t = blockIdx.x; t < T1; t += P) {
+        int32_t x[kItems];
+        load_items(a.flags, t * kTile, n1, (a.vec & 1) != 0, x);
+        int32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; j++) c += x[j] != 0;
+        int32_t total;
+        block_exclusive<OpSum>(c, s_warp, &total);
+        if (threadIdx.x == 0) tc1[t] = total;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.exact = 1;
+    grid_sync(a.bar, a.err);
+    {
+        uint32_t *s_key = reinterpret_cast<uint32_t *>(s_raw);
+        unsigned long long *s_val = reinterpret_cast<unsigned long long *>(s_raw + 8192);
+        uint64_t *s_rep = reinterpret_cast<uint64_t *>(s_raw + 24576);
+        int *s_has = reinterpret_cast<int *>(s_raw + 26624);
+        for (int i = threadIdx.x; i < kHistSlots; i += kThreads) { s_key[i] = kHistEmpty; s_val[i] = 0; }
+        for (int i = threadIdx.x; i < kPrioBins; i += kThreads) s_has[i] = 0;
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        for (int64_t t = blockIdx.x; t < T1; t += P) {
+            const int32_t before = tiles_before(tc1, t, s_warp);
+            int32_t x[kItems], y[kItems], ya[kItems], yg[kItems];
+            load_items(a.flags, t * kTile, n1, (a.vec & 1) != 0, x);
+            load_items((const int32_t *)a.list, t * kTile, n1, (a.vec & 2) != 0, y);
+            load_items((const int32_t *)a.lsrc, t * kTile, n1, (a.vec & 2) != 0, ya);
+            load_items((const int32_t *)a.lgain, t * kTile, n1, (a.vec & 2) != 0, yg);
+            int32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < kItems; j++) c += x[j] != 0;
+            int32_t total;
+            int32_t pos = before + block_exclusive<OpSum>(c, s_warp, &total);
+#pragma unroll
+            for (int j = 0; j < kItems; j++) {
+                uint32_t key = kHistEmpty;
+                uint64_t cu = 0;
+                if (x[j]) {
+                    const int32_t u = y[j];
+                    a.list2[pos] = u;
+                    a.lsrc2[pos] = ya[j];
+                    a.lgain2[pos] = yg[j];
+                    pos++;
+                    cu = a.vwgt ? (uint64_t)a.vwgt[u] : 1ull;
+                    const int64_t gu = yg[j];
+                    const int bin = prio_bin_f(gu, a.gain_only ? 1ull : cu, a.cbits);
+                    s_rep[bin] = prio_key_f(gu, a.gain_only ? 1ull : cu, a.gbits, a.cbits);
+                    s_has[bin] = 1;
+                    key = (uint32_t)ya[j] * kPrioBins + bin;
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                unsigned long long tot;
+                if (a.vwgt) {
+                    tot = 0;
+                    for (unsigned mm = peers; mm; mm &= mm - 1) tot += __shfl_sync(peers, cu, __ffs(mm) - 1);
+                } else {
+                    tot = (unsigned long long)__popc(peers);
+                }
+                if (key == kHistEmpty || lane != __ffs(peers) - 1) continue;
+                uint32_t h = (key * 0x9E3779B1u) >> 21;
+                bool done = false;
+                for (int probe = 0; probe < 32 && !done; probe++) {
+                    uint32_t cur = s_key[h];
+                    if (cur == kHistEmpty) {
+                        cur = atomicCAS(&s_key[h], kHistEmpty, key);
+                        if (cur == kHistEmpty) cur = key;
+                    }
+                    if (cur == key) {
+                        atomicAdd(&s_val[h], tot);
+                        done = true;
+                    }
+                    h = (h + 1) & (kHistSlots - 1);
+                }
+                if (!done) atomicAdd(&a.hist[key], tot);
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kHistSlots; i += kThreads)
+            if (s_key[i] != kHistEmpty) atomicAdd(&a.hist[s_key[i]], s_val[i]);
+        for (int i = threadIdx.x; i < kPrioBins; i += kThreads)
+            if (s_has[i]) a.rep[i] = s_rep[i];
+    }
+    grid_sync(a.bar, a.err);
+    const int64_t np = tiles_before(tc1, T1, s_warp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_np = (int32_t)np;
+
+    // ---- 2. the prefilter's cut bin per overloaded source (one CTA per source)
+    {
+        unsigned long long *s_pw = reinterpret_cast<unsigned long long *>(s_raw);
+        int *s_cut = reinterpret_cast<int *>(s_raw + 64);
+        const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+        for (int64_t src = blockIdx.x; src < K; src += P) {
+            if (!a.over[src]) continue;                       // uniform over the CTA
+            unsigned long long *row = a.hist + src * kPrioBins;
+            const unsigned long long v = row[t];
+            unsigned long long inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_pw[warp] = inc;
+            if (t == 0) *s_cut = kPrioBins - 1;
+            __syncthreads();
+            for (int w = 0; w < warp; w++) inc += s_pw[w];
+            const unsigned long long excess = (unsigned long long)(a.C[src] - a.Lb[src]);
+            if (inc >= excess) atomicMin(s_cut, t);
+            row[t] = 0;
+            __syncthreads();
+            if (t == 0) a.cut[src] = *s_cut;
+            __syncthreads();
+        }
+    }
+    grid_sync(a.bar, a.err);
+
+    // ---- 3. kept proposals as (key, node), node order; the list becomes the proposers
+    const int64_t Tp = tiles_of(np);
+    for (int pass = 0; pass < 2; pass++) {
+        for (int64_t t = blockIdx.x; t < Tp; t += P) {
+            const int64_t first = t * kTile + (int64_t)threadIdx.x * kItems;
+            uint64_t key[kItems];
+            int32_t u[kItems];
+            int32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < kItems; j++) {
+                u[j] = -1;
+                if (first + j < np) {
+                    const int32_t v = a.list2[first + j];
+                    if (pass == 0) a.list[first + j] = v;
+                    const uint64_t cv = (a.vwgt && !a.gain_only) ? (uint64_t)a.vwgt[v] : 1ull;
+                    const int64_t g = a.lgain2[first + j];
+                    const int bin = prio_bin_f(g, cv, a.cbits);
+                    if (bin <= a.cut[a.lsrc2[first + j]]) {
+                        u[j] = v;
+                        key[j] = prio_key_f(g, cv, a.gbits, a.cbits);
+                        if (pass == 0 && key[j] != a.rep[bin]) *a.exact = 0;
+                        c++;
+                    }
+                }
+            }
+            if (pass == 0) {
+                int32_t total;
+                block_exclusive<OpSum>(c, s_warp, &total);
+                if (threadIdx.x == 0) tc2[t] = total;
+                continue;
+            }
+            const int32_t before = tiles_before(tc2, t, s_warp);
+            int32_t total;
+            int32_t pos = before + block_exclusive<OpSum>(c, s_warp, &total);
+#pragma unroll
+            for (int j = 0; j < kItems; j++)
+                if (u[j] >= 0) { a.keys[pos] = key[j]; a.vals[pos] = (uint32_t)u[j]; pos++; }
+        }
+        grid_sync(a.bar, a.err);
+    }
+    const int64_t nk = tiles_before(tc2, Tp, s_warp);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_nk = (int32_t)nk;
+
+    // ---- 4. stable sort of the kept proposals by key (by the bin when exact)
+    const bool exact = *(volatile const int32_t *)a.exact != 0;
+    const int64_t Tk = tiles_of(nk);
+    if (nk <= kTile) {
+        if (blockIdx.x == 0 && nk > 0) {
+            int *s_cnt = reinterpret_cast<int *>(s_raw);
+            int *s_run = reinterpret_cast<int *>(s_raw + 16448);
+            int *s_off = reinterpret_cast<int *>(s_raw + 17488);
+            uint64_t *s_k = reinterpret_cast<uint64_t *>(s_raw + 18512);
+            uint32_t *s_v = reinterpret_cast<uint32_t *>(s_raw + 34896);
+            const int n = (int)nk;
+            for (int i = threadIdx.x; i < n; i += kThreads) { s_k[i] = a.keys[i]; s_v[i] = a.vals[i]; }
+            for (int p = 0; p < (exact ? 1 : a.passes); p++) {
+                for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
+                for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
+                for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = 0;
+                __syncthreads();
+                uint64_t k[kItems];
+                uint32_t v[kItems];
+                int dig[kItems], rank[kItems];
+#pragma unroll
+                for (int r = 0; r < kItems; r++) {
+                    const int g = r * kThreads + threadIdx.x;
+                    if (g < n) {
+                        k[r] = s_k[g]; v[r] = s_v[g];
+                        dig[r] = sort_digit(k[r], p, exact, a.gbits, a.cbits);
+                        atomicAdd(&s_off[dig[r]], 1);
+                    } else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
+                }
+                __syncthreads();
+                const int c = threadIdx.x < kBins ? s_off[threadIdx.x] : 0;
+                int total;
+                const int ex = block_exclusive<OpSum>(c, s_warp, &total);
+                if (threadIdx.x < kBins) s_off[threadIdx.x] = ex;
+                __syncthreads();
+                tile_rank(dig, rank, s_cnt, s_run);
+#pragma unroll
+                for (int r = 0; r < kItems; r++)
+                    if (dig[r] < kBins) { const int q = s_off[dig[r]] + rank[r]; s_k[q] = k[r]; s_v[q] = v[r]; }
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < n; i += kThreads) { a.keys_alt[i] = s_k[i]; a.vals_alt[i] = s_v[i]; }
+        }
+    } else {
+        uint64_t *ka = a.keys, *kb = a.keys_alt;
+        uint32_t *va = a.vals, *vb = a.vals_alt;
+        const int passes = exact ? 1 : a.passes;
+        for (int p = 0; p < passes; p++) {
+            {
+                int *s_h = reinterpret_cast<int *>(s_raw);
+                for (int64_t t = blockIdx.x; t < Tk; t += P) {
+                    for (int i = threadIdx.x; i < kBins; i += kThreads) s_h[i] = 0;
+                    __syncthreads();
+#pragma unroll
+                    for (int r = 0; r < kItems; r++) {
+                        const int64_t g = t * kTile + r * kThreads + threadIdx.x;
+                        if (g < nk) atomicAdd(&s_h[sort_digit(ka[g], p, exact, a.gbits, a.cbits)], 1);
+                    }
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < kBins; i += kThreads) tbl[(int64_t)i * Tk + t] = s_h[i];
+                    __syncthreads();
+                }
+            }
+            grid_sync(a.bar, a.err);
+            for (int64_t d = blockIdx.x; d < kBins; d += P) {
+                const int32_t tot = scan_row(tbl + d * Tk, Tk, s_warp);
+                if (threadIdx.x == 0) dtot[d] = tot;
+            }
+            grid_sync(a.bar, a.err);
+            {
+                int *s_cnt = reinterpret_cast<int *>(s_raw);
+                int *s_run = reinterpret_cast<int *>(s_raw + 16448);
+                int *s_off = reinterpret_cast<int *>(s_raw + 17488);
+                int *s_base = reinterpret_cast<int *>(s_raw + 18512);
+                {
+                    const int c = dtot[threadIdx.x];       // kThreads == kBins
+                    int total;
+                    s_base[threadIdx.x] = block_exclusive<OpSum>(c, s_warp, &total);
+                }
+                for (int64_t t = blockIdx.x; t < Tk; t += P) {
+                    for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
+                    for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
+                    for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = s_base[i] + tbl[(int64_t)i * Tk + t];
+                    __syncthreads();
+                    uint64_t k[kItems];
+                    uint32_t v[kItems];
+                    int dig[kItems], rank[kItems];
+#pragma unroll
+                    for (int r = 0; r < kItems; r++) {
+                        const int64_t g = t * kTile + r * kThreads + threadIdx.x;
+                        if (g < nk) { k[r] = ka[g]; v[r] = va[g]; dig[r] = sort_digit(k[r], p, exact, a.gbits, a.cbits); }
+                        else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
+                    }
+                    tile_rank(dig, rank, s_cnt, s_run);
+#pragma unroll
+                    for (int r = 0; r < kItems; r++)
+                        if (dig[r] < kBins) {
+                            const int64_t q = (int64_t)s_off[dig[r]] + rank[r];
+                            kb[q] = k[r];
+                            vb[q] = v[r];
+                        }
+                    __syncthreads();
+                }
+            }
+            grid_sync(a.bar, a.err);
+            uint64_t *tk = ka; ka = kb; kb = tk;
+            uint32_t *tv = va; va = vb; vb = tv;
+        }
+    }
+    grid_sync(a.bar, a.err);
+    const uint32_t *U = a.vals_alt;
+
+    // ---- 5. weight of the sorted proposals per (source, tile), row prefixes
+    {
+        int64_t *s_acc = reinterpret_cast<int64_t *>(s_raw);
+        int64_t *acc = s_acc + (threadIdx.x >> 5) * K;
+        for (int i = threadIdx.x; i < kWarps * K; i += kThreads) s_acc[i] = 0;
+        __syncthreads();
+        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int64_t g = item_at(t, r);
+                const bool ok = g < nk;
+                const uint32_t u = ok ? U[g] : 0;
+                warp_acc<UNIT>(ok ? a.part[u] : 0, (ok && a.vwgt) ? a.vwgt[u] : 1, ok, acc);
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < K; i += kThreads) a.h0[(int64_t)i * Tk + t] = warps_total(s_acc, K, i);
+            __syncthreads();
+        }
+    }
+    grid_sync(a.bar, a.err);
+    for (int64_t b = blockIdx.x; b < K; b += P) {
+        long long *row = a.h0 + b * Tk;
+        long long *out = a.h1 + b * Tk;
+        for (int64_t i = threadIdx.x; i < Tk; i += kThreads) out[i] = row[i];
+        __syncthreads();
+        scan_row(out, Tk, reinterpret_cast<long long *>(s_w64s));
+    }
+    grid_sync(a.bar, a.err);
+
+    // ---- 6. selection per source; weights of the selected per (target, tile)
+    int64_t *s_cnt = reinterpret_cast<int64_t *>(s_raw);
+    int64_t *s_run = reinterpret_cast<int64_t *>(s_raw + 32896);
+    {
+        for (int i = threadIdx.x; i < 2 * kWarps * (K + 1); i += kThreads) s_cnt[i] = 0;
+        for (int i = threadIdx.x; i <= K; i += kThreads) s_run[i] = 0;
+        int64_t *acc = s_cnt + (threadIdx.x >> 5) * K;
+        __syncthreads();
+        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+            int dig[kItems];
+            int64_t w[kItems], before[kItems];
+            uint32_t u[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int64_t g = item_at(t, r);
+                if (g < nk) {
+                    u[r] = U[g];
+                    dig[r] = a.part[u[r]];
+                    w[r] = a.vwgt ? a.vwgt[u[r]] : 1;
+                } else {
+                    u[r] = 0;
+                    dig[r] = K;
+                    w[r] = 0;
+                }
+            }
+            tile_wprefix<UNIT>(dig, w, before, s_cnt, s_run, K);
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int64_t g = item_at(t, r);
+                bool sl = false;
+                if (g < nk) {
+                    const int src = dig[r];
+                    const int64_t prior = a.h1[(int64_t)src * Tk + t] + before[r];
+                    sl = prior < a.C[src] - a.Lb[src];
+                    a.sel[g] = sl ? 1 : 0;
+                }
+                warp_acc<UNIT>(sl ? a.prop_tgt[u[r]] : 0, w[r], sl, acc);
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < K; i += kThreads) a.h0[(int64_t)i * Tk + t] = warps_total(s_cnt, K, i);
+            __syncthreads();
+        }
+    }
+    grid_sync(a.bar, a.err);
+    for (int64_t b = blockIdx.x; b < K; b += P) {
+        long long *row = a.h0 + b * Tk;
+        long long *out = a.h1 + b * Tk;
+        for (int64_t i = threadIdx.x; i < Tk; i += kThreads) out[i] = row[i];
+        __syncthreads();
+        scan_row(out, Tk, reinterpret_cast<long long *>(s_w64s));
+    }
+    grid_sync(a.bar, a.err);
+
+    // ---- 7. admission per target (sel = 2), then R in priority order and the moves applied
+    {
+        for (int i = threadIdx.x; i < 2 * kWarps * (K + 1); i += kThreads) s_cnt[i] = 0;
+        for (int i = threadIdx.x; i <= K; i += kThreads) s_run[i] = 0;
+        __syncthreads();
+        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+            int dig[kItems];
+            int64_t w[kItems], before[kItems];
+            uint32_t u[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int64_t g = item_at(t, r);
+                dig[r] = K;
+                w[r] = 0;
+                u[r] = 0;
+                if (g < nk) {
+                    u[r] = U[g];
+                    if (a.sel[g]) {
+                        dig[r] = a.prop_tgt[u[r]];
+                        w[r] = a.vwgt ? a.vwgt[u[r]] : 1;
+                    }
+                }
+            }
+            tile_wprefix<UNIT>(dig, w, before, s_cnt, s_run, K);
+            int32_t c = 0;
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int b = dig[r];
+                if (b == K) continue;
+                const int64_t incl = a.h1[(int64_t)b * Tk + t] + before[r] + w[r];
+                const bool adm = a.C[b] + incl <= a.Lb[b];
+                if (!adm) a.reject[b] = 1;
+                else { a.sel[item_at(t, r)] = 2; c++; }
+            }
+            int32_t total;
+            block_exclusive<OpSum>(c, s_warp, &total);
+            if (threadIdx.x == 0) tc3[t] = total;
+        }
+    }
+    grid_sync(a.bar, a.err);
+    {
+        int64_t *acc = s_cnt + (threadIdx.x >> 5) * K;
+        for (int i = threadIdx.x; i < kWarps * K; i += kThreads) s_cnt[i] = 0;
+        __syncthreads();
+        const int64_t off = a.ctl->nR;
+        const int32_t subround = a.ctl->subrounds;
+        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+            const int32_t tbefore = tiles_before(tc3, t, s_warp);
+            bool adm[kItems];
+            int32_t b8[kItems];
+            int64_t w[kItems];
+            uint32_t u[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                const int64_t g = item_at(t, r);
+                adm[r] = g < nk && a.sel[g] == 2;
+                u[r] = adm[r] ? U[g] : 0;
+                b8[r] = adm[r] ? a.prop_tgt[u[r]] : 0;
+                w[r] = adm[r] ? (a.vwgt ? a.vwgt[u[r]] : 1) : 0;
+            }
+            // R keeps the sorted (priority) order, which inside a tile is item
+            // order (round-major): per-round counts packed 16 bits each
+            uint64_t lo = 0, hi = 0;
+#pragma unroll
+            for (int r = 0; r < kItems; r++)
+                if (adm[r]) {
+                    if (r < 4) lo += 1ull << (16 * r);
+                    else hi += 1ull << (16 * (r - 4));
+                }
+            uint64_t tlo, thi;
+            const uint64_t plo = block_exclusive<OpSum>(lo, s_w64, &tlo);
+            const uint64_t phi = block_exclusive<OpSum>(hi, s_w64, &thi);
+            int32_t mine[kItems];
+            {
+                int32_t base = tbefore;
+#pragma unroll
+                for (int r = 0; r < kItems; r++) {
+                    const int sh = 16 * (r & 3);
+                    mine[r] = base + (int32_t)(((r < 4 ? plo : phi) >> sh) & 0xFFFF);
+                    base += (int32_t)(((r < 4 ? tlo : thi) >> sh) & 0xFFFF);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kItems; r++) {
+                int32_t from = 0;
+                const int32_t b = b8[r];
+                if (adm[r]) {
+                    const int32_t v = (int32_t)u[r];
+                    from = a.part[v];
+                    const int64_t p = off + mine[r];
+                    a.R_node[p] = v;
+                    a.R_from[p] = from;
+                    a.R_to[p] = b;
+                    a.R_sub[p] = subround;
+                    a.r_to[v] = b;
+                    a.r_at[v] = (int32_t)p;
+                    a.part[v] = b;
+                }
+                warp_acc<UNIT>(from, -w[r], adm[r], acc);
+                __syncwarp();
+                warp_acc<UNIT>(b, w[r], adm[r], acc);
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < K; i += kThreads) {
+                const int64_t d = warps_total(s_cnt, K, i);
+                if (d) atomicAdd(reinterpret_cast<unsigned long long *>(&a.Cd[i]), (unsigned long long)d);
+            }
+            __syncthreads();
+        }
+        const int32_t na = tiles_before(tc3, Tk, s_warp);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_na = na;
     }
 }
 
@@ -700,9 +1281,10 @@ void rebalance_fused_keep_keys(const GraphDev &g, const int32_t *list, const int
 
 bool rebalance_fused_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, const int32_t *d_n,
                           int64_t n_max, int key_bits, int gbits, int cbits, const int32_t *exact, Scratch tmp,
-                          cudaStream_t s) {
+                          cudaStream_t s, cudaStream_t s_aux, int32_t *later_runs, int *later_kernels) {
     const int passes = (key_bits + 7) / 8;
     if (!(passes & 1)) throw CudaError{cudaErrorInvalidValue, "rebalance_fused_sort: even pass count"};
+    if (later_kernels) *later_kernels = 0;
     if (n_max <= 0) return true;
     k_fr_radix_small<<<1, kThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, d_n, passes, gbits, cbits, exact);
     UPR_LAUNCH_CHECK();
@@ -713,17 +1295,59 @@ bool rebalance_fused_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, ui
     int32_t *d_hist_n = hist + (size_t)kBins * tmp.tiles_cap;
     const unsigned grid_h = wave_grid((const void *)k_fr_radix_hist, kThreads, 0, tiles_max);
     const unsigned grid_s = wave_grid((const void *)k_fr_radix_scatter, kThreads, 0, tiles_max);
+    // while s is being captured (and s_aux is given), passes 1.. become the
+    // body of a conditional node that pass 0 sets: an exact-bin sort, or a
+    // list of one tile, skips them without launching their kernels
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    if (s_aux && later_runs && passes > 1) UPR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    const bool cond = cs == cudaStreamCaptureStatusActive;
+    cudaGraphConditionalHandle later = 0;
+    if (cond) UPR_CUDA(cudaGraphConditionalHandleCreate(&later, g, 0, 0));
     uint64_t *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
-    for (int p = 0; p < passes; p++) {
-        k_fr_radix_hist<<<grid_h, kThreads, 0, s>>>(ka, d_n, p, gbits, cbits, exact, hist, d_hist_n);
+    auto pass = [&](int p, cudaStream_t st) {
+        k_fr_radix_hist<<<grid_h, kThreads, 0, st>>>(ka, d_n, p, gbits, cbits, exact, hist, d_hist_n);
         UPR_LAUNCH_CHECK();
-        exclusive_sum_i32(hist, hist, Count{d_hist_n, (int64_t)kBins * tiles_max}, tmp, s);
-        k_fr_radix_scatter<<<grid_s, kThreads, 0, s>>>(ka, va, kb, vb, d_n, p, gbits, cbits, exact, hist);
+        exclusive_sum_i32(hist, hist, Count{d_hist_n, (int64_t)kBins * tiles_max}, tmp, st);
+        k_fr_radix_scatter<<<grid_s, kThreads, 0, st>>>(ka, va, kb, vb, d_n, p, gbits, cbits, exact, hist, later,
+                                                         p == 0 && cond ? later_runs : nullptr);
         UPR_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
+    };
+    pass(0, s);
+    if (!cond) {
+        for (int p = 1; p < passes; p++) pass(p, s);
+        return true;
     }
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    UPR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = later;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    UPR_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    UPR_CUDA(cudaStreamBeginCaptureToGraph(s_aux, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+    const long long l0 = g_upr_launches;
+    try {
+        for (int p = 1; p < passes; p++) pass(p, s_aux);
+    } catch (...) {
+        cudaGraph_t out = nullptr;
+        cudaStreamEndCapture(s_aux, &out);
+        throw;
+    }
+    // counted when the node runs (later_runs), not with the enclosing graph
+    const long long body = g_upr_launches - l0;
+    g_upr_launches -= body;
+    if (later_kernels) *later_kernels = (int)body;
+    cudaGraph_t out = nullptr;
+    UPR_CUDA(cudaStreamEndCapture(s_aux, &out));
+    UPR_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     return true;
 }
 
@@ -766,9 +1390,44 @@ void rebalance_fused_select_admit(const GraphDev &g, const uint32_t *U, const in
     UPR_LAUNCH_CHECK();
 }
 
+void rebalance_fused_mega(const GraphDev &g, RebalMega m, int key_bits, int64_t n_max, Scratch tmp,
+                          cudaStream_t s) {
+    m.K = g.K();
+    m.vwgt = g.vwgt;
+    m.Lb = g.Lb;
+    m.passes = (key_bits + 7) / 8;
+    if (!(m.passes & 1)) throw CudaError{cudaErrorInvalidValue, "rebalance_fused_mega: even pass count"};
+    m.tcap = std::max<int64_t>(1, ceil_div(std::max<int64_t>(n_max, 1), kTile));
+    // tile counts 3 x [tcap], then (a sort of more than one tile) digit totals and counts
+    const int64_t need = m.tcap == 1 ? 3 : 3 * m.tcap + kBins + (int64_t)kBins * m.tcap;
+    if ((size_t)need * sizeof(int32_t) > tmp.mem_bytes)
+        throw CudaError{cudaErrorInvalidValue, "rebalance_fused_mega: scratch too small"};
+    m.tab = reinterpret_cast<int32_t *>(tmp.mem);
+    m.bar = reinterpret_cast<unsigned long long *>(tmp.ticket + 8);
+    m.err = tmp.err;
+    m.vec = (aligned16(m.flags) ? 1 : 0) | (aligned16(m.list) && aligned16(m.lsrc) && aligned16(m.lgain) ? 2 : 0);
+    const bool unit = g.vwgt == nullptr;
+    const void *fn = unit ? (const void *)k_fr_mega<true> : (const void *)k_fr_mega<false>;
+    const int per_sm = std::min(2, resident_ctas(fn, kThreads, 0));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(device_sm_count() * per_sm));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (unit) UPR_CUDA(cudaLaunchKernelEx(&cfg, k_fr_mega<true>, m));
+    else UPR_CUDA(cudaLaunchKernelEx(&cfg, k_fr_mega<false>, m));
+    UPR_LAUNCH_CHECK();
+}
+
 void rebalance_fused_end(const GraphDev &g, int64_t *C, long long *Cd, int8_t *excl, const int8_t *reject,
-                         const int32_t *d_na, RebalCtl *ctl, cudaStream_t s) {
-    k_fr_end<<<1, 256, 0, s>>>(C, Cd, g.Lb, g.K(), excl, reject, d_na, ctl);
+                         const int32_t *d_na, RebalCtl *ctl, cudaStream_t s, cudaGraphConditionalHandle cond,
+                         int32_t max_subrounds) {
+    k_fr_end<<<1, 256, 0, s>>>(C, Cd, g.Lb, g.K(), excl, reject, d_na, ctl, cond, max_subrounds);
     UPR_LAUNCH_CHECK();
 }
 
