@@ -21,6 +21,8 @@
 //      target's room), compaction of the admitted into R (look-back) and the
 //      moves applied; block-weight changes go to a delta array that the
 //      sub-round's end folds in, because C is read for admission meanwhile.
+#include <type_traits>
+
 #include "prim.cuh"
 
 namespace upr {
@@ -57,14 +59,14 @@ __device__ __forceinline__ uint64_t prio_key_f(int64_t g, uint64_t c, int gbits,
 // of the tile (item (r, t) precedes (r', t') iff r < r' or r == r' and
 // t < t') with the same digit; digit K = no item.  s_cnt: [2][kWarps][K+1]
 // and s_run: [K+1], zero on entry, zero again on return.
-template <bool UNIT>
-__device__ __forceinline__ void tile_wprefix(const int (&dig)[kItems], const int64_t (&w)[kItems],
-                                             int64_t (&before)[kItems], int64_t *s_cnt, int64_t *s_run, int K) {
+template <bool UNIT, int N = kItems>
+__device__ __forceinline__ void tile_wprefix(const int (&dig)[N], const int64_t (&w)[N], int64_t (&before)[N],
+                                             int64_t *s_cnt, int64_t *s_run, int K) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int stride = kWarps * (K + 1);
 #pragma unroll
-    for (int r = 0; r < kItems; r++) {
+    for (int r = 0; r < N; r++) {
         int64_t *cnt = s_cnt + (r & 1) * stride;
         const int d = dig[r];
         const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -97,7 +99,7 @@ __device__ __forceinline__ void tile_wprefix(const int (&dig)[kItems], const int
         before[r] = cnt[warp * (K + 1) + d] + within;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < stride; i += kThreads) s_cnt[((kItems - 1) & 1) * stride + i] = 0;
+    for (int i = threadIdx.x; i < stride; i += kThreads) s_cnt[((N - 1) & 1) * stride + i] = 0;
     for (int dd = threadIdx.x; dd <= K; dd += kThreads) s_run[dd] = 0;
     __syncthreads();
 }
@@ -762,6 +764,61 @@ __device__ __forceinline__ T scan_row(T *row, int64_t len, T *s_warp) {
 using MegaArgs = RebalMega;
 
 constexpr int kMegaSmem = 43136;
+constexpr int kMI = 4;                       // items per thread in steps 5-7
+constexpr int kMT = kThreads * kMI;          // their tiles: 1024 sorted proposals
+constexpr uint64_t kNoKey = ~0ull;           // (keys have at most 63 bits)
+
+__device__ __forceinline__ int64_t item_m(int64_t tile, int r) { return tile * kMT + r * kThreads + threadIdx.x; }
+__device__ __forceinline__ int64_t tiles_m(int64_t n) { return (n + kMT - 1) / kMT; }
+
+// The proposal at index i of the compacted proposers: kept (its bin not after
+// its source's cut), with its key and node; the list takes the node.
+__device__ __forceinline__ bool kept_key(const MegaArgs &a, int64_t i, bool copy, uint64_t *key, int32_t *node) {
+    const int32_t v = a.list2[i];
+    if (copy) a.list[i] = v;
+    const uint64_t cv = (a.vwgt && !a.gain_only) ? (uint64_t)a.vwgt[v] : 1ull;
+    const int64_t g = a.lgain2[i];
+    const int bin = prio_bin_f(g, cv, a.cbits);
+    *node = v;
+    if (bin > a.cut[a.lsrc2[i]]) return false;
+    *key = prio_key_f(g, cv, a.gbits, a.cbits);
+    return true;
+}
+
+// Sort passes [p0, p1) of n <= kTile (key, node) pairs held in shared memory
+// (one CTA; the radix order of the kernels above).
+__device__ __forceinline__ void smem_sort(uint64_t *s_k, uint32_t *s_v, int *s_cnt, int *s_run, int *s_off,
+                                          int32_t *s_warp, int n, int p0, int p1, bool exact, int gbits, int cbits) {
+    for (int p = p0; p < p1; p++) {
+        for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
+        for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
+        for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = 0;
+        __syncthreads();
+        uint64_t k[kItems];
+        uint32_t v[kItems];
+        int dig[kItems], rank[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; r++) {
+            const int g = r * kThreads + threadIdx.x;
+            if (g < n) {
+                k[r] = s_k[g]; v[r] = s_v[g];
+                dig[r] = sort_digit(k[r], p, exact, gbits, cbits);
+                atomicAdd(&s_off[dig[r]], 1);
+            } else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
+        }
+        __syncthreads();
+        const int c = threadIdx.x < kBins ? s_off[threadIdx.x] : 0;
+        int total;
+        const int ex = block_exclusive<OpSum>(c, s_warp, &total);
+        if (threadIdx.x < kBins) s_off[threadIdx.x] = ex;
+        __syncthreads();
+        tile_rank(dig, rank, s_cnt, s_run);
+#pragma unroll
+        for (int r = 0; r < kItems; r++)
+            if (dig[r] < kBins) { const int q = s_off[dig[r]] + rank[r]; s_k[q] = k[r]; s_v[q] = v[r]; }
+        __syncthreads();
+    }
+}
 
 template <bool UNIT>
 __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
@@ -769,13 +826,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
     __shared__ int32_t s_warp[kWarps];
     __shared__ int64_t s_w64s[kWarps];
     __shared__ uint64_t s_w64[kWarps];
-    __shared__ int32_t s_excl;
+    __shared__ int s_inexact;
     const int64_t P = gridDim.x;
     const int K = a.K;
-    int32_t *tc1 = a.tab, *tc2 = tc1 + a.tcap, *tc3 = tc2 + a.tcap;
-    int32_t *dtot = tc3 + a.tcap, *tbl = dtot + kBins;     // (digits: only with more than one tile)
+    int32_t *tc1 = a.tab, *tc2 = tc1 + a.tcap, *tc3 = tc2 + a.tcap;       // tc3: 2 * tcap tiles of kMT
+    int32_t *dtot = tc3 + 2 * a.tcap, *tbl = dtot + kBins;                 // (digits: more than one tile only)
+    uint64_t *grep = a.rep;
 
-    // ---- 1. proposers compacted (node order) with the prefilter histogram
+    // ---- 1. proposers compacted (node order) with the prefilter histogram;
+    // a key per bin, to learn whether every bin holds one key value
     const int64_t n1 = *a.d_n1;
     const int64_t T1 = tiles_of(n1);
     for (int64_t t = blockIdx.x; t < T1; t += P) {
@@ -788,17 +847,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
         block_exclusive<OpSum>(c, s_warp, &total);
         if (threadIdx.x == 0) tc1[t] = total;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.exact = 1;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < kPrioBins; i += kThreads) grep[i] = kNoKey;
+        if (threadIdx.x == 0) *a.exact = 1;
+    }
     grid_sync(a.bar, a.err);
     {
+        // the (source, bin) weights in a shared-memory hash table: 32-bit
+        // values with unit weights (a CTA's proposals fit), 64-bit otherwise
+        using HV = typename std::conditional<UNIT, unsigned int, unsigned long long>::type;
         uint32_t *s_key = reinterpret_cast<uint32_t *>(s_raw);
-        unsigned long long *s_val = reinterpret_cast<unsigned long long *>(s_raw + 8192);
-        uint64_t *s_rep = reinterpret_cast<uint64_t *>(s_raw + 24576);
-        int *s_has = reinterpret_cast<int *>(s_raw + 26624);
+        HV *s_val = reinterpret_cast<HV *>(s_raw + 8192);
         for (int i = threadIdx.x; i < kHistSlots; i += kThreads) { s_key[i] = kHistEmpty; s_val[i] = 0; }
-        for (int i = threadIdx.x; i < kPrioBins; i += kThreads) s_has[i] = 0;
         __syncthreads();
-        const int lane = threadIdx.x & 31;
         for (int64_t t = blockIdx.x; t < T1; t += P) {
             const int32_t before = tiles_before(tc1, t, s_warp);
             int32_t x[kItems], y[kItems], ya[kItems], yg[kItems];
@@ -813,30 +874,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
             int32_t pos = before + block_exclusive<OpSum>(c, s_warp, &total);
 #pragma unroll
             for (int j = 0; j < kItems; j++) {
-                uint32_t key = kHistEmpty;
-                uint64_t cu = 0;
-                if (x[j]) {
-                    const int32_t u = y[j];
-                    a.list2[pos] = u;
-                    a.lsrc2[pos] = ya[j];
-                    a.lgain2[pos] = yg[j];
-                    pos++;
-                    cu = a.vwgt ? (uint64_t)a.vwgt[u] : 1ull;
-                    const int64_t gu = yg[j];
-                    const int bin = prio_bin_f(gu, a.gain_only ? 1ull : cu, a.cbits);
-                    s_rep[bin] = prio_key_f(gu, a.gain_only ? 1ull : cu, a.gbits, a.cbits);
-                    s_has[bin] = 1;
-                    key = (uint32_t)ya[j] * kPrioBins + bin;
-                }
-                const unsigned peers = __match_any_sync(0xffffffffu, key);
-                unsigned long long tot;
-                if (a.vwgt) {
-                    tot = 0;
-                    for (unsigned mm = peers; mm; mm &= mm - 1) tot += __shfl_sync(peers, cu, __ffs(mm) - 1);
-                } else {
-                    tot = (unsigned long long)__popc(peers);
-                }
-                if (key == kHistEmpty || lane != __ffs(peers) - 1) continue;
+                if (!x[j]) continue;
+                const int32_t u = y[j];
+                a.list2[pos] = u;
+                a.lsrc2[pos] = ya[j];
+                a.lgain2[pos] = yg[j];
+                pos++;
+                const uint64_t cu = a.vwgt ? (uint64_t)a.vwgt[u] : 1ull;
+                const int64_t gu = yg[j];
+                const int bin = prio_bin_f(gu, a.gain_only ? 1ull : cu, a.cbits);
+                const uint32_t key = (uint32_t)ya[j] * kPrioBins + bin;
+                const HV tot = (HV)cu;
                 uint32_t h = (key * 0x9E3779B1u) >> 21;
                 bool done = false;
                 for (int probe = 0; probe < 32 && !done; probe++) {
@@ -851,15 +899,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
                     }
                     h = (h + 1) & (kHistSlots - 1);
                 }
-                if (!done) atomicAdd(&a.hist[key], tot);
+                if (!done) atomicAdd(&a.hist[key], (unsigned long long)tot);
             }
             __syncthreads();
         }
         __syncthreads();
         for (int i = threadIdx.x; i < kHistSlots; i += kThreads)
-            if (s_key[i] != kHistEmpty) atomicAdd(&a.hist[s_key[i]], s_val[i]);
-        for (int i = threadIdx.x; i < kPrioBins; i += kThreads)
-            if (s_has[i]) a.rep[i] = s_rep[i];
+            if (s_key[i] != kHistEmpty) atomicAdd(&a.hist[s_key[i]], (unsigned long long)s_val[i]);
     }
     grid_sync(a.bar, a.err);
     const int64_t np = tiles_before(tc1, T1, s_warp);
@@ -893,160 +939,256 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
     }
     grid_sync(a.bar, a.err);
 
-    // ---- 3. kept proposals as (key, node), node order; the list becomes the proposers
+    // ---- 3-4. the kept proposals (node order) sorted stably by key, or by
+    // the bin alone when every bin holds one key value; the list becomes the
+    // proposers
     const int64_t Tp = tiles_of(np);
-    for (int pass = 0; pass < 2; pass++) {
-        for (int64_t t = blockIdx.x; t < Tp; t += P) {
-            const int64_t first = t * kTile + (int64_t)threadIdx.x * kItems;
-            uint64_t key[kItems];
-            int32_t u[kItems];
-            int32_t c = 0;
-#pragma unroll
-            for (int j = 0; j < kItems; j++) {
-                u[j] = -1;
-                if (first + j < np) {
-                    const int32_t v = a.list2[first + j];
-                    if (pass == 0) a.list[first + j] = v;
-                    const uint64_t cv = (a.vwgt && !a.gain_only) ? (uint64_t)a.vwgt[v] : 1ull;
-                    const int64_t g = a.lgain2[first + j];
-                    const int bin = prio_bin_f(g, cv, a.cbits);
-                    if (bin <= a.cut[a.lsrc2[first + j]]) {
-                        u[j] = v;
-                        key[j] = prio_key_f(g, cv, a.gbits, a.cbits);
-                        if (pass == 0 && key[j] != a.rep[bin]) *a.exact = 0;
-                        c++;
-                    }
-                }
-            }
-            if (pass == 0) {
-                int32_t total;
-                block_exclusive<OpSum>(c, s_warp, &total);
-                if (threadIdx.x == 0) tc2[t] = total;
-                continue;
-            }
-            const int32_t before = tiles_before(tc2, t, s_warp);
-            int32_t total;
-            int32_t pos = before + block_exclusive<OpSum>(c, s_warp, &total);
-#pragma unroll
-            for (int j = 0; j < kItems; j++)
-                if (u[j] >= 0) { a.keys[pos] = key[j]; a.vals[pos] = (uint32_t)u[j]; pos++; }
-        }
-        grid_sync(a.bar, a.err);
-    }
-    const int64_t nk = tiles_before(tc2, Tp, s_warp);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_nk = (int32_t)nk;
-
-    // ---- 4. stable sort of the kept proposals by key (by the bin when exact)
-    const bool exact = *(volatile const int32_t *)a.exact != 0;
-    const int64_t Tk = tiles_of(nk);
-    if (nk <= kTile) {
-        if (blockIdx.x == 0 && nk > 0) {
+    int64_t nk = 0;
+    if (Tp <= 1) {
+        // one tile of proposals: kept keys and the whole sort in one CTA
+        if (blockIdx.x == 0) {
             int *s_cnt = reinterpret_cast<int *>(s_raw);
             int *s_run = reinterpret_cast<int *>(s_raw + 16448);
             int *s_off = reinterpret_cast<int *>(s_raw + 17488);
             uint64_t *s_k = reinterpret_cast<uint64_t *>(s_raw + 18512);
             uint32_t *s_v = reinterpret_cast<uint32_t *>(s_raw + 34896);
-            const int n = (int)nk;
-            for (int i = threadIdx.x; i < n; i += kThreads) { s_k[i] = a.keys[i]; s_v[i] = a.vals[i]; }
-            for (int p = 0; p < (exact ? 1 : a.passes); p++) {
+            const int64_t first = (int64_t)threadIdx.x * kItems;
+            uint64_t key[kItems];
+            int32_t u[kItems];
+            bool kp[kItems];
+            int32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < kItems; j++) {
+                kp[j] = first + j < np && kept_key(a, first + j, true, &key[j], &u[j]);
+                c += kp[j];
+            }
+            int32_t total;
+            int32_t pos = block_exclusive<OpSum>(c, s_warp, &total);
+#pragma unroll
+            for (int j = 0; j < kItems; j++)
+                if (kp[j]) { s_k[pos] = key[j]; s_v[pos] = (uint32_t)u[j]; pos++; }
+            // whether every bin of the kept keys holds one key value
+            uint64_t *s_rep = reinterpret_cast<uint64_t *>(s_raw);      // (free until the sort)
+            for (int i = threadIdx.x; i < kPrioBins; i += kThreads) s_rep[i] = kNoKey;
+            if (threadIdx.x == 0) s_inexact = 0;
+            __syncthreads();
+            for (int i = threadIdx.x; i < total; i += kThreads) {
+                const uint64_t k = s_k[i];
+                const int bin = bin_of_key(k, a.gbits, a.cbits);
+                unsigned long long r = atomicCAS(reinterpret_cast<unsigned long long *>(&s_rep[bin]), kNoKey, k);
+                if (r != kNoKey && r != k) s_inexact = 1;
+            }
+            __syncthreads();
+            const bool exact = s_inexact == 0;
+            if (threadIdx.x == 0) *a.exact = exact ? 1 : 0;
+            smem_sort(s_k, s_v, s_cnt, s_run, s_off, s_warp, total, 0, exact ? 1 : a.passes, exact, a.gbits, a.cbits);
+            for (int i = threadIdx.x; i < total; i += kThreads) { a.keys_alt[i] = s_k[i]; a.vals_alt[i] = s_v[i]; }
+            if (threadIdx.x == 0) tc2[0] = total;
+        }
+        grid_sync(a.bar, a.err);
+        nk = Tp == 1 ? tc2[0] : 0;
+    } else {
+        // (a) per tile of proposals: the kept ones staged in node order at the
+        // tile's start, the counts of both candidates for their first sort
+        // digit (the bin, or the key's low byte), and whether every bin of
+        // the kept keys holds one key value
+        int32_t *tbl_b = reinterpret_cast<int32_t *>(a.h1);       // (free until step 5)
+        {
+            int *s_h = reinterpret_cast<int *>(s_raw);
+            int *s_h2 = s_h + kBins;
+            uint64_t *s_rep = reinterpret_cast<uint64_t *>(s_raw + 2048);
+            for (int i = threadIdx.x; i < kPrioBins; i += kThreads) s_rep[i] = kNoKey;
+            if (threadIdx.x == 0) s_inexact = 0;
+            for (int64_t t = blockIdx.x; t < Tp; t += P) {
+                for (int i = threadIdx.x; i < kBins; i += kThreads) { s_h[i] = 0; s_h2[i] = 0; }
+                __syncthreads();
+                const int64_t first = t * kTile + (int64_t)threadIdx.x * kItems;
+                uint64_t key[kItems];
+                int32_t yv[kItems];
+                bool kp[kItems];
+                int32_t c = 0;
+#pragma unroll
+                for (int j = 0; j < kItems; j++) {
+                    kp[j] = first + j < np && kept_key(a, first + j, true, &key[j], &yv[j]);
+                    c += kp[j];
+                }
+                int32_t total;
+                int32_t pos = block_exclusive<OpSum>(c, s_warp, &total);
+#pragma unroll
+                for (int j = 0; j < kItems; j++)
+                    if (kp[j]) {
+                        a.keys[t * kTile + pos] = key[j];
+                        a.vals[t * kTile + pos] = (uint32_t)yv[j];
+                        pos++;
+                        const int bin = bin_of_key(key[j], a.gbits, a.cbits);
+                        atomicAdd(&s_h[bin], 1);
+                        atomicAdd(&s_h2[(int)(key[j] & 0xFF)], 1);
+                        uint64_t r = s_rep[bin];
+                        if (r == kNoKey) {
+                            r = atomicCAS(reinterpret_cast<unsigned long long *>(&s_rep[bin]), kNoKey, key[j]);
+                            if (r == kNoKey) r = key[j];
+                        }
+                        if (r != key[j]) s_inexact = 1;
+                    }
+                __syncthreads();
+                for (int i = threadIdx.x; i < kBins; i += kThreads) {
+                    tbl[(int64_t)i * Tp + t] = s_h[i];
+                    tbl_b[(int64_t)i * Tp + t] = s_h2[i];
+                }
+                if (threadIdx.x == 0) tc2[t] = total;
+                __syncthreads();
+            }
+            bool differs = false;
+            for (int i = threadIdx.x; i < kPrioBins; i += kThreads)
+                if (s_rep[i] != kNoKey) {
+                    const unsigned long long g =
+                        atomicCAS(reinterpret_cast<unsigned long long *>(&grep[i]), kNoKey, s_rep[i]);
+                    if (g != kNoKey && g != s_rep[i]) differs = true;
+                }
+            if (differs) s_inexact = 1;
+            __syncthreads();
+            if (threadIdx.x == 0 && s_inexact) *a.exact = 0;
+        }
+        grid_sync(a.bar, a.err);
+        const bool exact = *(volatile const int32_t *)a.exact != 0;
+        const int passes = exact ? 1 : a.passes;
+        int32_t *tsel = exact ? tbl : tbl_b;
+        for (int64_t d = blockIdx.x; d < kBins; d += P) {
+            const int32_t tot = scan_row(tsel + d * Tp, Tp, s_warp);
+            if (threadIdx.x == 0) dtot[d] = tot;
+        }
+        grid_sync(a.bar, a.err);
+        // (b) the first pass from the staged tiles into the alternate buffers
+        {
+            int *s_cnt = reinterpret_cast<int *>(s_raw);
+            int *s_run = reinterpret_cast<int *>(s_raw + 16448);
+            int *s_off = reinterpret_cast<int *>(s_raw + 17488);
+            int *s_base = reinterpret_cast<int *>(s_raw + 18512);
+            {
+                const int c = dtot[threadIdx.x];       // kThreads == kBins
+                int total;
+                s_base[threadIdx.x] = block_exclusive<OpSum>(c, s_warp, &total);
+            }
+            for (int64_t t = blockIdx.x; t < Tp; t += P) {
+                const int cnt = tc2[t];
                 for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
                 for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
-                for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = 0;
+                for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = s_base[i] + tsel[(int64_t)i * Tp + t];
                 __syncthreads();
                 uint64_t k[kItems];
                 uint32_t v[kItems];
                 int dig[kItems], rank[kItems];
 #pragma unroll
                 for (int r = 0; r < kItems; r++) {
-                    const int g = r * kThreads + threadIdx.x;
-                    if (g < n) {
-                        k[r] = s_k[g]; v[r] = s_v[g];
-                        dig[r] = sort_digit(k[r], p, exact, a.gbits, a.cbits);
-                        atomicAdd(&s_off[dig[r]], 1);
+                    const int j = r * kThreads + threadIdx.x;
+                    if (j < cnt) {
+                        k[r] = a.keys[t * kTile + j];
+                        v[r] = a.vals[t * kTile + j];
+                        dig[r] = sort_digit(k[r], 0, exact, a.gbits, a.cbits);
                     } else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
                 }
-                __syncthreads();
-                const int c = threadIdx.x < kBins ? s_off[threadIdx.x] : 0;
-                int total;
-                const int ex = block_exclusive<OpSum>(c, s_warp, &total);
-                if (threadIdx.x < kBins) s_off[threadIdx.x] = ex;
-                __syncthreads();
                 tile_rank(dig, rank, s_cnt, s_run);
 #pragma unroll
                 for (int r = 0; r < kItems; r++)
-                    if (dig[r] < kBins) { const int q = s_off[dig[r]] + rank[r]; s_k[q] = k[r]; s_v[q] = v[r]; }
+                    if (dig[r] < kBins) {
+                        const int64_t q = (int64_t)s_off[dig[r]] + rank[r];
+                        a.keys_alt[q] = k[r];
+                        a.vals_alt[q] = v[r];
+                    }
                 __syncthreads();
             }
-            for (int i = threadIdx.x; i < n; i += kThreads) { a.keys_alt[i] = s_k[i]; a.vals_alt[i] = s_v[i]; }
         }
-    } else {
-        uint64_t *ka = a.keys, *kb = a.keys_alt;
-        uint32_t *va = a.vals, *vb = a.vals_alt;
-        const int passes = exact ? 1 : a.passes;
-        for (int p = 0; p < passes; p++) {
-            {
-                int *s_h = reinterpret_cast<int *>(s_raw);
-                for (int64_t t = blockIdx.x; t < Tk; t += P) {
-                    for (int i = threadIdx.x; i < kBins; i += kThreads) s_h[i] = 0;
+        grid_sync(a.bar, a.err);
+        nk = tiles_before(tc2, Tp, s_warp);
+        // (c) the other passes (none when exact), alternate -> main -> ... ->
+        // alternate (an odd number of passes in all)
+        if (passes > 1) {
+            if (nk <= kTile) {
+                if (blockIdx.x == 0 && nk > 0) {
+                    int *s_cnt = reinterpret_cast<int *>(s_raw);
+                    int *s_run = reinterpret_cast<int *>(s_raw + 16448);
+                    int *s_off = reinterpret_cast<int *>(s_raw + 17488);
+                    uint64_t *s_k = reinterpret_cast<uint64_t *>(s_raw + 18512);
+                    uint32_t *s_v = reinterpret_cast<uint32_t *>(s_raw + 34896);
+                    const int n = (int)nk;
+                    for (int i = threadIdx.x; i < n; i += kThreads) { s_k[i] = a.keys_alt[i]; s_v[i] = a.vals_alt[i]; }
                     __syncthreads();
-#pragma unroll
-                    for (int r = 0; r < kItems; r++) {
-                        const int64_t g = t * kTile + r * kThreads + threadIdx.x;
-                        if (g < nk) atomicAdd(&s_h[sort_digit(ka[g], p, exact, a.gbits, a.cbits)], 1);
-                    }
-                    __syncthreads();
-                    for (int i = threadIdx.x; i < kBins; i += kThreads) tbl[(int64_t)i * Tk + t] = s_h[i];
-                    __syncthreads();
+                    smem_sort(s_k, s_v, s_cnt, s_run, s_off, s_warp, n, 1, passes, false, a.gbits, a.cbits);
+                    for (int i = threadIdx.x; i < n; i += kThreads) { a.keys_alt[i] = s_k[i]; a.vals_alt[i] = s_v[i]; }
                 }
-            }
-            grid_sync(a.bar, a.err);
-            for (int64_t d = blockIdx.x; d < kBins; d += P) {
-                const int32_t tot = scan_row(tbl + d * Tk, Tk, s_warp);
-                if (threadIdx.x == 0) dtot[d] = tot;
-            }
-            grid_sync(a.bar, a.err);
-            {
-                int *s_cnt = reinterpret_cast<int *>(s_raw);
-                int *s_run = reinterpret_cast<int *>(s_raw + 16448);
-                int *s_off = reinterpret_cast<int *>(s_raw + 17488);
-                int *s_base = reinterpret_cast<int *>(s_raw + 18512);
-                {
-                    const int c = dtot[threadIdx.x];       // kThreads == kBins
-                    int total;
-                    s_base[threadIdx.x] = block_exclusive<OpSum>(c, s_warp, &total);
-                }
-                for (int64_t t = blockIdx.x; t < Tk; t += P) {
-                    for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
-                    for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
-                    for (int i = threadIdx.x; i < kBins; i += kThreads) s_off[i] = s_base[i] + tbl[(int64_t)i * Tk + t];
-                    __syncthreads();
-                    uint64_t k[kItems];
-                    uint32_t v[kItems];
-                    int dig[kItems], rank[kItems];
+            } else {
+                const int64_t Tk = tiles_of(nk);
+                uint64_t *ka = a.keys_alt, *kb = a.keys;
+                uint32_t *va = a.vals_alt, *vb = a.vals;
+                for (int p = 1; p < passes; p++) {
+                    {
+                        int *s_h = reinterpret_cast<int *>(s_raw);
+                        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+                            for (int i = threadIdx.x; i < kBins; i += kThreads) s_h[i] = 0;
+                            __syncthreads();
 #pragma unroll
-                    for (int r = 0; r < kItems; r++) {
-                        const int64_t g = t * kTile + r * kThreads + threadIdx.x;
-                        if (g < nk) { k[r] = ka[g]; v[r] = va[g]; dig[r] = sort_digit(k[r], p, exact, a.gbits, a.cbits); }
-                        else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
-                    }
-                    tile_rank(dig, rank, s_cnt, s_run);
-#pragma unroll
-                    for (int r = 0; r < kItems; r++)
-                        if (dig[r] < kBins) {
-                            const int64_t q = (int64_t)s_off[dig[r]] + rank[r];
-                            kb[q] = k[r];
-                            vb[q] = v[r];
+                            for (int r = 0; r < kItems; r++) {
+                                const int64_t g = t * kTile + r * kThreads + threadIdx.x;
+                                if (g < nk) atomicAdd(&s_h[sort_digit(ka[g], p, false, a.gbits, a.cbits)], 1);
+                            }
+                            __syncthreads();
+                            for (int i = threadIdx.x; i < kBins; i += kThreads) tbl[(int64_t)i * Tk + t] = s_h[i];
+                            __syncthreads();
                         }
-                    __syncthreads();
+                    }
+                    grid_sync(a.bar, a.err);
+                    for (int64_t d = blockIdx.x; d < kBins; d += P) {
+                        const int32_t tot = scan_row(tbl + d * Tk, Tk, s_warp);
+                        if (threadIdx.x == 0) dtot[d] = tot;
+                    }
+                    grid_sync(a.bar, a.err);
+                    {
+                        int *s_cnt = reinterpret_cast<int *>(s_raw);
+                        int *s_run = reinterpret_cast<int *>(s_raw + 16448);
+                        int *s_off = reinterpret_cast<int *>(s_raw + 17488);
+                        int *s_base = reinterpret_cast<int *>(s_raw + 18512);
+                        {
+                            const int c = dtot[threadIdx.x];
+                            int total;
+                            s_base[threadIdx.x] = block_exclusive<OpSum>(c, s_warp, &total);
+                        }
+                        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+                            for (int i = threadIdx.x; i < 2 * kWarps * (kBins + 1); i += kThreads) s_cnt[i] = 0;
+                            for (int i = threadIdx.x; i <= kBins; i += kThreads) s_run[i] = 0;
+                            for (int i = threadIdx.x; i < kBins; i += kThreads)
+                                s_off[i] = s_base[i] + tbl[(int64_t)i * Tk + t];
+                            __syncthreads();
+                            uint64_t k[kItems];
+                            uint32_t v[kItems];
+                            int dig[kItems], rank[kItems];
+#pragma unroll
+                            for (int r = 0; r < kItems; r++) {
+                                const int64_t g = t * kTile + r * kThreads + threadIdx.x;
+                                if (g < nk) { k[r] = ka[g]; v[r] = va[g]; dig[r] = sort_digit(k[r], p, false, a.gbits, a.cbits); }
+                                else { k[r] = 0; v[r] = 0; dig[r] = kBins; }
+                            }
+                            tile_rank(dig, rank, s_cnt, s_run);
+#pragma unroll
+                            for (int r = 0; r < kItems; r++)
+                                if (dig[r] < kBins) {
+                                    const int64_t q = (int64_t)s_off[dig[r]] + rank[r];
+                                    kb[q] = k[r];
+                                    vb[q] = v[r];
+                                }
+                            __syncthreads();
+                        }
+                    }
+                    grid_sync(a.bar, a.err);
+                    uint64_t *tk = ka; ka = kb; kb = tk;
+                    uint32_t *tv = va; va = vb; vb = tv;
                 }
             }
-            grid_sync(a.bar, a.err);
-            uint64_t *tk = ka; ka = kb; kb = tk;
-            uint32_t *tv = va; va = vb; vb = tv;
         }
+        grid_sync(a.bar, a.err);
     }
-    grid_sync(a.bar, a.err);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_nk = (int32_t)nk;
     const uint32_t *U = a.vals_alt;
+    const int64_t T2 = tiles_m(nk);
 
     // ---- 5. weight of the sorted proposals per (source, tile), row prefixes
     {
@@ -1054,27 +1196,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
         int64_t *acc = s_acc + (threadIdx.x >> 5) * K;
         for (int i = threadIdx.x; i < kWarps * K; i += kThreads) s_acc[i] = 0;
         __syncthreads();
-        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+        for (int64_t t = blockIdx.x; t < T2; t += P) {
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
-                const int64_t g = item_at(t, r);
+            for (int r = 0; r < kMI; r++) {
+                const int64_t g = item_m(t, r);
                 const bool ok = g < nk;
                 const uint32_t u = ok ? U[g] : 0;
                 warp_acc<UNIT>(ok ? a.part[u] : 0, (ok && a.vwgt) ? a.vwgt[u] : 1, ok, acc);
                 __syncwarp();
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < K; i += kThreads) a.h0[(int64_t)i * Tk + t] = warps_total(s_acc, K, i);
+            for (int i = threadIdx.x; i < K; i += kThreads) a.h0[(int64_t)i * T2 + t] = warps_total(s_acc, K, i);
             __syncthreads();
         }
     }
     grid_sync(a.bar, a.err);
     for (int64_t b = blockIdx.x; b < K; b += P) {
-        long long *row = a.h0 + b * Tk;
-        long long *out = a.h1 + b * Tk;
-        for (int64_t i = threadIdx.x; i < Tk; i += kThreads) out[i] = row[i];
+        long long *row = a.h0 + b * T2;
+        long long *out = a.h1 + b * T2;
+        for (int64_t i = threadIdx.x; i < T2; i += kThreads) out[i] = row[i];
         __syncthreads();
-        scan_row(out, Tk, reinterpret_cast<long long *>(s_w64s));
+        scan_row(out, T2, reinterpret_cast<long long *>(s_w64s));
     }
     grid_sync(a.bar, a.err);
 
@@ -1086,13 +1228,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
         for (int i = threadIdx.x; i <= K; i += kThreads) s_run[i] = 0;
         int64_t *acc = s_cnt + (threadIdx.x >> 5) * K;
         __syncthreads();
-        for (int64_t t = blockIdx.x; t < Tk; t += P) {
-            int dig[kItems];
-            int64_t w[kItems], before[kItems];
-            uint32_t u[kItems];
+        for (int64_t t = blockIdx.x; t < T2; t += P) {
+            int dig[kMI];
+            int64_t w[kMI], before[kMI];
+            uint32_t u[kMI];
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
-                const int64_t g = item_at(t, r);
+            for (int r = 0; r < kMI; r++) {
+                const int64_t g = item_m(t, r);
                 if (g < nk) {
                     u[r] = U[g];
                     dig[r] = a.part[u[r]];
@@ -1103,14 +1245,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
                     w[r] = 0;
                 }
             }
-            tile_wprefix<UNIT>(dig, w, before, s_cnt, s_run, K);
+            tile_wprefix<UNIT, kMI>(dig, w, before, s_cnt, s_run, K);
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
-                const int64_t g = item_at(t, r);
+            for (int r = 0; r < kMI; r++) {
+                const int64_t g = item_m(t, r);
                 bool sl = false;
                 if (g < nk) {
                     const int src = dig[r];
-                    const int64_t prior = a.h1[(int64_t)src * Tk + t] + before[r];
+                    const int64_t prior = a.h1[(int64_t)src * T2 + t] + before[r];
                     sl = prior < a.C[src] - a.Lb[src];
                     a.sel[g] = sl ? 1 : 0;
                 }
@@ -1118,17 +1260,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
                 __syncwarp();
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < K; i += kThreads) a.h0[(int64_t)i * Tk + t] = warps_total(s_cnt, K, i);
+            for (int i = threadIdx.x; i < K; i += kThreads) a.h0[(int64_t)i * T2 + t] = warps_total(s_cnt, K, i);
             __syncthreads();
         }
     }
     grid_sync(a.bar, a.err);
     for (int64_t b = blockIdx.x; b < K; b += P) {
-        long long *row = a.h0 + b * Tk;
-        long long *out = a.h1 + b * Tk;
-        for (int64_t i = threadIdx.x; i < Tk; i += kThreads) out[i] = row[i];
+        long long *row = a.h0 + b * T2;
+        long long *out = a.h1 + b * T2;
+        for (int64_t i = threadIdx.x; i < T2; i += kThreads) out[i] = row[i];
         __syncthreads();
-        scan_row(out, Tk, reinterpret_cast<long long *>(s_w64s));
+        scan_row(out, T2, reinterpret_cast<long long *>(s_w64s));
     }
     grid_sync(a.bar, a.err);
 
@@ -1137,13 +1279,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
         for (int i = threadIdx.x; i < 2 * kWarps * (K + 1); i += kThreads) s_cnt[i] = 0;
         for (int i = threadIdx.x; i <= K; i += kThreads) s_run[i] = 0;
         __syncthreads();
-        for (int64_t t = blockIdx.x; t < Tk; t += P) {
-            int dig[kItems];
-            int64_t w[kItems], before[kItems];
-            uint32_t u[kItems];
+        for (int64_t t = blockIdx.x; t < T2; t += P) {
+            int dig[kMI];
+            int64_t w[kMI], before[kMI];
+            uint32_t u[kMI];
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
-                const int64_t g = item_at(t, r);
+            for (int r = 0; r < kMI; r++) {
+                const int64_t g = item_m(t, r);
                 dig[r] = K;
                 w[r] = 0;
                 u[r] = 0;
@@ -1155,16 +1297,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
                     }
                 }
             }
-            tile_wprefix<UNIT>(dig, w, before, s_cnt, s_run, K);
+            tile_wprefix<UNIT, kMI>(dig, w, before, s_cnt, s_run, K);
             int32_t c = 0;
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
+            for (int r = 0; r < kMI; r++) {
                 const int b = dig[r];
                 if (b == K) continue;
-                const int64_t incl = a.h1[(int64_t)b * Tk + t] + before[r] + w[r];
+                const int64_t incl = a.h1[(int64_t)b * T2 + t] + before[r] + w[r];
                 const bool adm = a.C[b] + incl <= a.Lb[b];
                 if (!adm) a.reject[b] = 1;
-                else { a.sel[item_at(t, r)] = 2; c++; }
+                else { a.sel[item_m(t, r)] = 2; c++; }
             }
             int32_t total;
             block_exclusive<OpSum>(c, s_warp, &total);
@@ -1178,15 +1320,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
         __syncthreads();
         const int64_t off = a.ctl->nR;
         const int32_t subround = a.ctl->subrounds;
-        for (int64_t t = blockIdx.x; t < Tk; t += P) {
+        for (int64_t t = blockIdx.x; t < T2; t += P) {
             const int32_t tbefore = tiles_before(tc3, t, s_warp);
-            bool adm[kItems];
-            int32_t b8[kItems];
-            int64_t w[kItems];
-            uint32_t u[kItems];
+            bool adm[kMI];
+            int32_t b8[kMI];
+            int64_t w[kMI];
+            uint32_t u[kMI];
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
-                const int64_t g = item_at(t, r);
+            for (int r = 0; r < kMI; r++) {
+                const int64_t g = item_m(t, r);
                 adm[r] = g < nk && a.sel[g] == 2;
                 u[r] = adm[r] ? U[g] : 0;
                 b8[r] = adm[r] ? a.prop_tgt[u[r]] : 0;
@@ -1194,28 +1336,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
             }
             // R keeps the sorted (priority) order, which inside a tile is item
             // order (round-major): per-round counts packed 16 bits each
-            uint64_t lo = 0, hi = 0;
+            uint64_t lo = 0;
 #pragma unroll
-            for (int r = 0; r < kItems; r++)
-                if (adm[r]) {
-                    if (r < 4) lo += 1ull << (16 * r);
-                    else hi += 1ull << (16 * (r - 4));
-                }
-            uint64_t tlo, thi;
+            for (int r = 0; r < kMI; r++)
+                if (adm[r]) lo += 1ull << (16 * r);
+            uint64_t tlo;
             const uint64_t plo = block_exclusive<OpSum>(lo, s_w64, &tlo);
-            const uint64_t phi = block_exclusive<OpSum>(hi, s_w64, &thi);
-            int32_t mine[kItems];
+            int32_t mine[kMI];
             {
                 int32_t base = tbefore;
 #pragma unroll
-                for (int r = 0; r < kItems; r++) {
-                    const int sh = 16 * (r & 3);
-                    mine[r] = base + (int32_t)(((r < 4 ? plo : phi) >> sh) & 0xFFFF);
-                    base += (int32_t)(((r < 4 ? tlo : thi) >> sh) & 0xFFFF);
+                for (int r = 0; r < kMI; r++) {
+                    const int sh = 16 * r;
+                    mine[r] = base + (int32_t)((plo >> sh) & 0xFFFF);
+                    base += (int32_t)((tlo >> sh) & 0xFFFF);
                 }
             }
 #pragma unroll
-            for (int r = 0; r < kItems; r++) {
+            for (int r = 0; r < kMI; r++) {
                 int32_t from = 0;
                 const int32_t b = b8[r];
                 if (adm[r]) {
@@ -1242,7 +1380,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fr_mega(const MegaArgs a) {
             }
             __syncthreads();
         }
-        const int32_t na = tiles_before(tc3, Tk, s_warp);
+        const int32_t na = tiles_before(tc3, T2, s_warp);
         if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_na = na;
     }
 }
@@ -1398,8 +1536,9 @@ void rebalance_fused_mega(const GraphDev &g, RebalMega m, int key_bits, int64_t 
     m.passes = (key_bits + 7) / 8;
     if (!(m.passes & 1)) throw CudaError{cudaErrorInvalidValue, "rebalance_fused_mega: even pass count"};
     m.tcap = std::max<int64_t>(1, ceil_div(std::max<int64_t>(n_max, 1), kTile));
-    // tile counts 3 x [tcap], then (a sort of more than one tile) digit totals and counts
-    const int64_t need = m.tcap == 1 ? 3 : 3 * m.tcap + kBins + (int64_t)kBins * m.tcap;
+    // tile counts [tcap] x 2 and [2 tcap], then (more than one tile of
+    // proposals) digit totals and counts
+    const int64_t need = m.tcap == 1 ? 4 : 4 * m.tcap + kBins + (int64_t)kBins * m.tcap;
     if ((size_t)need * sizeof(int32_t) > tmp.mem_bytes)
         throw CudaError{cudaErrorInvalidValue, "rebalance_fused_mega: scratch too small"};
     m.tab = reinterpret_cast<int32_t *>(tmp.mem);
