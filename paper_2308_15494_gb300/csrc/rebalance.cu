@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
         const bool src = i < n1 && (BATCH ? st.over[ag] : s_over[a]);
         const int4 zero = make_int4(0, 0, 0, 0);
         int4 r[CH];
-        // an isolated node's row is zero: not read
-        if (src && g.wI[v] > 0) {
+        // the row is loaded as soon as v is known, beside its block (a
+        // listed node that is no longer a source ignores it)
+        if (i < n1) {
             const int4 *row4 = reinterpret_cast<const int4 *>(W + (int64_t)v * k);
 #pragma unroll
             for (int j = 0; j < CH; j++) {
