@@ -773,6 +773,10 @@ void rebalance_phase(upr_ctx *c, int32_t r, RoundInfo &ri, TraceSink *tr) {
     select_flags(c->flags, c->L1, cnt + CNT_L1, cN, c->tmp, s);
     int32_t *light = batch ? c->light_g : &ctl->light;
     RebalState st{c->C, c->over_d, c->excl_d, light, c->Lb};
+    {
+        const int kb = std::max(1, bit_length((uint64_t)(G.k - 1)));
+        if (!batch && !G.vwgt && c->gbits + kb <= 31) st.pack_bits = kb;
+    }
     if (fused_rebalance(c, 1 + c->gbits + 2 * c->cbits)) {
         st.lsrc = c->emit;          // list-indexed proposal blocks and gains (sequence-phase arrays, free here)
         st.lgain = c->qbefore;

@@ -278,6 +278,10 @@ struct RebalState {
     // block and gain by list index, so that later passes over the list read
     // them in order instead of gathering them by node
     int32_t *lsrc = nullptr, *lgain = nullptr;
+    // > 0 (unit node weights, one graph, 1 + gb + pack_bits <= 32): the dense
+    // proposal kernel scores a column as one integer, (omega << pack_bits) +
+    // (2^pack_bits - 1 - b), pack_bits = the bits of a column index
+    int pack_bits = 0;
 };
 // flags[v] = 1 for the nodes of the marked blocks
 void rebalance_flag_in_blocks(const int32_t *part, int64_t n, const int8_t *mark, int32_t *flags, cudaStream_t s);

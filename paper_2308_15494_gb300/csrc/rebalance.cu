@@ -83,7 +83,7 @@ __device__ __forceinline__ int32_t int4_at(const int4 &x, int c) {
 // excluded one, so one comparison c <= room(b) tests validity.  With one
 // graph the rooms are staged in shared memory; in a batch each node reads its
 // graph's blocks from global memory.
-template <int G, int CH, bool EXACT, bool BATCH>
+template <int G, int CH, bool EXACT, bool BATCH, bool PACK = false>
 __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int32_t *__restrict__ list,
                                                      const int32_t *__restrict__ d_n1,
                                                      const int32_t *__restrict__ part, const int32_t *__restrict__ W,
@@ -109,6 +109,22 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    // PACK (unit weights, one graph): the lane's columns that have room for a
+    // node of weight 1, as a bit mask fixed for the launch, and a column's
+    // score as one integer whose maximum is the largest omega, ties to the
+    // smaller block
+    uint32_t okm = 0;
+    const int kb = st.pack_bits;
+    const int32_t kmask = (1 << kb) - 1, lbase = kmask - 4 * gl;
+    if (PACK) {
+#pragma unroll
+        for (int j = 0; j < CH; j++)
+#pragma unroll
+            for (int cc = 0; cc < 4; cc++) {
+                const int b = 4 * (gl + G * j) + cc;
+                if ((EXACT || b < k) && s_room[b] >= 1) okm |= 1u << (4 * j + cc);
+            }
+    }
     for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n1; base += (int64_t)gridDim.x * kGroups) {
         const int64_t i = base + gid;
         const int32_t v = i < n1 ? list[i] : 0;
@@ -139,7 +155,21 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
         const int32_t c = src ? (g.vwgt ? g.vwgt[v] : 1) : 1;
         // best valid block: the largest omega(v, V_b) (gain = omega - own), ties to the smaller b
         int32_t bw = 0, bt = -1;
-        if (src) {
+        if (PACK) {
+            int32_t best = 0;
+#pragma unroll
+            for (int j = 0; j < CH; j++) {
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) {
+                    const int32_t w = int4_at(r[j], cc);
+                    const int32_t key = (w << kb) + (lbase - 4 * G * j - cc);
+                    const bool ok = ((okm >> (4 * j + cc)) & 1u) && w > 0;
+                    best = max(best, ok ? key : 0);
+                }
+            }
+            for (int o = G / 2; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (src && best > 0) { bw = best >> kb; bt = kmask - (best & kmask); }
+        } else if (src) {
 #pragma unroll
             for (int j = 0; j < CH; j++) {
 #pragma unroll
@@ -160,7 +190,7 @@ __global__ void __launch_bounds__(256) k_propose_vec(const GraphDev g, const int
             }
         }
         int32_t id = bt;
-        group_argmax32<G>(bw, id);
+        if (!PACK) group_argmax32<G>(bw, id);
         if (i < n1 && gl == 0) {
             int32_t tgt = src && id >= 0 ? b0 + id : -1;
             int32_t gain = bw - own;
@@ -748,14 +778,17 @@ void launch_propose_vec(bool exact, bool batch, unsigned blocks, size_t shm, cud
         kern<<<wave_grid((const void *)kern, 256, shm, blocks), 256, shm, s>>>(g, list, d_n1, part, W, st, prop_tgt,
                                                                              prop_gain, flags);
     };
+    const bool pack = !batch && st.pack_bits > 0 && g.vwgt == nullptr;
     if constexpr (CH == 1 || (G == 32 && CH == 2)) {
         if (!exact) {
             if (batch) go(k_propose_vec<G, CH, false, true>);
+            else if (pack) go(k_propose_vec<G, CH, false, false, true>);
             else go(k_propose_vec<G, CH, false, false>);
             return;
         }
     }
     if (batch) go(k_propose_vec<G, CH, true, true>);
+    else if (pack) go(k_propose_vec<G, CH, true, false, true>);
     else go(k_propose_vec<G, CH, true, false>);
 }
 
