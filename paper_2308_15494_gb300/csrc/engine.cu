@@ -510,6 +510,16 @@ void settle_tuning(LaneCfg *cfg, bool *tuned, int *pending, const LaneCfg *cands
     *pending = 0;
 }
 
+// The selection's one-integer column scores (unit node weights, one graph,
+// gains and column bits within 30 bits).
+void set_pack(const upr_ctx *c, Penalty &pen) {
+    const int kb = std::max(1, bit_length((uint64_t)(c->G.k - 1)));
+    if (c->ng == 1 && !c->G.vwgt && c->gbits + kb <= 30) {
+        pen.pack_bits = kb;
+        pen.gbits = c->gbits;
+    }
+}
+
 // The fused form of a rebalancing sub-round applies: one graph, K <= 256, a
 // one-word key, the prefilter, and per-(block, tile) sums that fit the
 // 2n-entry buffers they use (UPR_FUSED=0 in the environment turns it off:
@@ -911,6 +921,7 @@ upr_status run_round_once(upr_ctx *c, int32_t r, int32_t R, bool rebalance_only,
             UPR_LAUNCH_CHECK();
         }
         Penalty pen{c->PW, F, c->C0, kind.limit > 0 ? c->Lsel : c->Lb, c->first_slot};
+        set_pack(c, pen);
         // ---- (b2) best move per boundary node
         run_tuned(c, c->sel_tuned, c->sel_cfg, c->sel_cands, &c->sel_pending, c->ev_tune, [&](LaneCfg cfg) {
             select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, cfg, s);
@@ -1315,7 +1326,8 @@ int lp_round_once(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri)
     UPR_CUDA(cudaMemcpyAsync(c->F, c->hF, sizeof(int64_t) * kSlots, cudaMemcpyHostToDevice, s));
     k_fill_i64<<<(unsigned)ceil_div(K, 256), 256, 0, s>>>(c->Lsel, K, INT64_MAX);
     UPR_LAUNCH_CHECK();
-    const Penalty pen{c->PW, c->F, c->C0, c->Lsel, c->first_slot};
+    Penalty pen{c->PW, c->F, c->C0, c->Lsel, c->first_slot};
+    set_pack(c, pen);
     select_moves(G, c->part0, c->W, pen, c->cand_tgt, c->cand_s0, c->cand_gain, c->flags, c->sel_cfg, s);
     lp_filter(c->flags, c->lp_active, n, s);
     select_flags(c->flags, c->idxA, cnt + CNT_M, cN, c->tmp, s);

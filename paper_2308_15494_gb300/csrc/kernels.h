@@ -225,6 +225,11 @@ struct Penalty {
     const int64_t *C;     // [K] round-start block weights
     const int64_t *Lb;    // [K] L_max of each block's graph
     const int8_t *first;  // [K] smallest slot l with PW[b][l] >= 1, -1 if none (the excess-1 case)
+    // > 0 (unit node weights, one graph, gb + pack_bits <= 30): the dense
+    // selection kernel scores a column as one integer, ((gain - penalty) <<
+    // pack_bits) + (2^pack_bits - 1 - b), pack_bits = the bits of a column index
+    int pack_bits = 0;
+    int gbits = 0;
 };
 // With cut2 (kCutParts + 1 words; one graph): also sums twice the cut of part
 // (Sec. 2: the sum over v of omega(I(v)) - omega(v, V_P(v))) into

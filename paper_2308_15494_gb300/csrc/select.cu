@@ -219,7 +219,7 @@ __device__ __forceinline__ int32_t int4_get(const int4 &x, int c) {
 // memory; in a batch each node reads its own graph's blocks from global
 // memory.  A move into a block with room for it costs no penalty and needs no
 // search.
-template <int G, int CH, bool EXACT, bool BATCH>
+template <int G, int CH, bool EXACT, bool BATCH, bool PACK = false>
 __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int32_t *__restrict__ part,
                                                     const int32_t *__restrict__ W, Penalty pen, int smem_pw,
                                                     int32_t *__restrict__ cand_tgt, int64_t *__restrict__ cand_s0,
@@ -248,6 +248,58 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
     constexpr int kGroups = 256 / G;
     const int gid = threadIdx.x / G, gl = threadIdx.x % G;
     const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    // PACK (unit weights, one graph): a node of weight 1 pays the same
+    // penalty p(b) into block b wherever it comes from, so p(b) (-1:
+    // forbidden) is fixed for the launch; the lane keeps, per column it
+    // scores, a bit "allowed" and the constant (2^kb - 1 - b) - (p(b) << kb)
+    const int kb = PACK ? pen.pack_bits : 0;
+    const int32_t kmask = (1 << kb) - 1;
+    int32_t *s_pen = reinterpret_cast<int32_t *>(s_first + ((k + 3) & ~3));
+    uint32_t okm = 0;
+    int32_t cst[CH][4];
+    if (PACK) {
+        for (int b = threadIdx.x; b < k; b += blockDim.x) {
+            const int32_t sl = s_slack[b];
+            int32_t p = 0;
+            if (sl < 1) {
+                const int64_t x = 1 - (int64_t)sl;
+                int lo;
+                if (x == 1) {
+                    lo = s_first[b];
+                } else {
+                    const int64_t *row = PW + (int64_t)b * kSlots;
+                    if (row[kSlots - 1] < x) {
+                        lo = -1;
+                    } else {
+                        lo = 0;
+                        int hi = kSlots - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (row[mid] >= x) hi = mid; else lo = mid + 1;
+                        }
+                    }
+                }
+                if (lo < 0) {
+                    p = -1;
+                } else {
+                    // floor(1 * F / 2^Q); a penalty of at least 2^gb exceeds every gain
+                    const uint64_t pp = (uint64_t)s_F[lo] >> kQ;
+                    p = pp >= (1ull << pen.gbits) ? -1 : (int32_t)pp;
+                }
+            }
+            s_pen[b] = p;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < CH; j++)
+#pragma unroll
+            for (int cc = 0; cc < 4; cc++) {
+                const int b = 4 * (gl + G * j) + cc;
+                const int32_t p = (EXACT || b < k) ? s_pen[b] : -1;
+                if (p >= 0) okm |= 1u << (4 * j + cc);
+                cst[j][cc] = (kmask - b) - (p >= 0 ? (p << kb) : 0);
+            }
+    }
     for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
         const int64_t v = base + gid;
         const bool active = v < n;
@@ -277,6 +329,31 @@ __global__ void __launch_bounds__(256) k_select_vec(const GraphDev g, const int3
         for (int j = 0; j < CH; j++)
             if (j == q4 / G) mine = int4_get(r[j], a & 3);
         const int32_t own = __shfl_sync(0xffffffffu, mine, gbase + (q4 % G));
+        if (PACK) {
+            int32_t pbest = 0;
+            if (active && own < wIv) {
+                const int32_t ownk = own << kb;
+#pragma unroll
+                for (int j = 0; j < CH; j++)
+#pragma unroll
+                    for (int cc = 0; cc < 4; cc++) {
+                        const int32_t key = (int4_get(r[j], cc) << kb) - ownk + cst[j][cc];
+                        pbest = max(pbest, ((okm >> (4 * j + cc)) & 1u) ? key : 0);
+                    }
+            }
+            for (int o = G / 2; o > 0; o >>= 1) pbest = max(pbest, __shfl_xor_sync(0xffffffffu, pbest, o));
+            if (active && gl == 0) {
+                // a score >= 1 (key >= 2^kb) makes a candidate
+                const bool cand = pbest >= (1 << kb);
+                const int32_t b = kmask - (pbest & kmask);
+                const int32_t sc = pbest >> kb;
+                cand_tgt[v] = cand ? b0 + b : -1;
+                cand_s0[v] = cand ? sc : 0;
+                cand_gain[v] = cand ? sc + s_pen[b] : 0;
+                flags[v] = cand ? 1 : 0;
+            }
+            continue;
+        }
         // Only a positive score makes a candidate and the penalty is never
         // negative, so blocks with gain <= 0 (the own block among them) are
         // skipped and every score kept lies in [1, 2^31).
@@ -565,14 +642,17 @@ void launch_select_vec(bool exact, bool batch, unsigned blocks, size_t shm, cuda
         kern<<<wave_grid((const void *)kern, 256, shm, blocks), 256, shm, s>>>(g, part, W, pen, smem_pw, cand_tgt,
                                                                              cand_s0, cand_gain, flags);
     };
+    const bool pack = !batch && pen.pack_bits > 0 && g.vwgt == nullptr;
     if constexpr (CH == 1 || (G == 32 && CH == 2)) {
         if (!exact) {
             if (batch) go(k_select_vec<G, CH, false, true>);
+            else if (pack) go(k_select_vec<G, CH, false, false, true>);
             else go(k_select_vec<G, CH, false, false>);
             return;
         }
     }
     if (batch) go(k_select_vec<G, CH, true, true>);
+    else if (pack) go(k_select_vec<G, CH, true, false, true>);
     else go(k_select_vec<G, CH, true, false>);
 }
 
@@ -599,7 +679,7 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
         // and the smaller shared footprint lets more CTAs run
         const int smem_pw = !batch && g.vwgt && (size_t)k * kSlots * 8 <= 40 * 1024;
         const size_t shm = sizeof(int64_t) * ((size_t)kSlots + (smem_pw ? (size_t)k * kSlots : 0)) +
-                           (batch ? 0 : (sizeof(int32_t) + 1) * k);
+                           (batch ? 0 : (sizeof(int32_t) + 1) * k + sizeof(int32_t) * (k + 4));
         const int64_t groups = 256 / G;
         const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 8);
 #define UPR_SELC(GG, CC)                                                                                       \
