@@ -84,7 +84,9 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
     const int bins = K * kSlots;
     __syncthreads();
     if (use_shared) {
-        for (int i = threadIdx.x; i < bins; i += blockDim.x) s_bw[i] = 0;
+        // (unit weights: 32-bit counts, half the words)
+        unsigned int *s_w32 = reinterpret_cast<unsigned int *>(s_bw);
+        for (int i = threadIdx.x; i < (vwgt ? 2 : 1) * bins; i += blockDim.x) s_w32[i] = 0;
         __syncthreads();
     }
     long long out_w = 0;      // weight of the edges leaving v's block, summed over this thread's nodes
@@ -100,16 +102,24 @@ __global__ void k_buckets(const int32_t *__restrict__ part, const int32_t *__res
         out_w += (long long)wIv - own;
         const int s = slot_of((uint64_t)own, (uint64_t)c, s_p3);
         if (av) {
-            unsigned long long *dst = use_shared ? s_bw : BW;
-            atomicAdd(&dst[a * kSlots + (s - kSlotLo)], (unsigned long long)c);
+            if (use_shared && !vwgt)      // unit weights: a CTA's counts fit 32-bit shared-memory atomics
+                atomicAdd(reinterpret_cast<unsigned int *>(s_bw) + a * kSlots + (s - kSlotLo), 1u);
+            else
+                atomicAdd(&(use_shared ? s_bw : BW)[a * kSlots + (s - kSlotLo)], (unsigned long long)c);
         }
         if (avail_out) avail_out[v] = av ? 1 : 0;
         if (slot_out) slot_out[v] = s;
     }
     if (use_shared) {
         __syncthreads();
-        for (int i = threadIdx.x; i < bins; i += blockDim.x)
-            if (s_bw[i]) atomicAdd(&BW[i], s_bw[i]);
+        if (!vwgt) {
+            const unsigned int *s_bw32 = reinterpret_cast<const unsigned int *>(s_bw);
+            for (int i = threadIdx.x; i < bins; i += blockDim.x)
+                if (s_bw32[i]) atomicAdd(&BW[i], (unsigned long long)s_bw32[i]);
+        } else {
+            for (int i = threadIdx.x; i < bins; i += blockDim.x)
+                if (s_bw[i]) atomicAdd(&BW[i], s_bw[i]);
+        }
     }
     if (cut2) {
         __shared__ long long s_cw[8];
@@ -592,7 +602,7 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
         c2 = reinterpret_cast<unsigned long long *>(cut2);
     }
     if (g.n > 0) {
-        const size_t shm = sizeof(unsigned long long) * (size_t)K * kSlots;
+        const size_t shm = (g.vwgt ? sizeof(unsigned long long) : sizeof(unsigned int)) * (size_t)K * kSlots;
         const int use_shared = shm <= 200 * 1024;
         if (use_shared && shm > 48 * 1024)
             kernel_setup((const void *)k_buckets, -1);
