@@ -200,6 +200,8 @@ struct upr_ctx {
     uint64_t gen = 0, reb_gen = ~0ull;  // binding generation; the one reb_exec belongs to
     LaneCfg reb_cfg{};
     int reb_body_kernels = 0;
+    int64_t *xs = nullptr;            // binding: the packed offsets and the schedule counts (bind.cu), kept
+    int64_t xs_cap = 0;
     int reb_if_kernels = 0;           // kernels of the conditional sort passes in the sub-round body
     cudaStream_t s_if = nullptr;      // capture stream of that conditional body
     int64_t rounds_bound = 0;         // rounds run since the binding
@@ -1205,6 +1207,7 @@ void free_ctx(upr_ctx *c) {
     if (c->s_cap) cudaStreamDestroy(c->s_cap);
     if (c->s_body) cudaStreamDestroy(c->s_body);
     if (c->s_if) cudaStreamDestroy(c->s_if);
+    if (c->xs) cudaFree(c->xs);
     if (c->F_all) cudaFree(c->F_all);
     if (c->hF_all) cudaFreeHost(c->hF_all);
     if (c->h) cudaFreeHost(c->h);
@@ -1849,80 +1852,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     // the packed xadj of a batch (or of a graph whose xadj is device
     // memory) goes to the context's pinned staging buffer, kept across
     // bindings, so that its upload is a DMA from pinned memory
-    int64_t *xadj_store = nullptr;
-    const int64_t *xadj_h;
     const int nthreads = host_threads(n);
-    if (ng == 1 && (n == 0 || mem_kind(gs[0].xadj) == kHost)) {
-        static const int64_t zero = 0;
-        xadj_h = n > 0 ? gs[0].xadj : &zero;
-        if (n > 0 && (xadj_h[0] != 0 || xadj_h[n] != m)) return UPR_ERR_INVALID;
-        std::vector<char> bad(nthreads, 0);
-        parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
-            for (int64_t v = v0; v < v1; v++)
-                if (xadj_h[v + 1] < xadj_h[v]) { bad[t] = 1; return; }
-        });
-        for (char x : bad)
-            if (x) return UPR_ERR_INVALID;
-    } else {
-        if (c->hx_cap < n + 1) {
-            if (c->hx) cudaFreeHost(c->hx);
-            c->hx = nullptr;
-            c->hx_cap = 0;
-            if (cudaMallocHost((void **)&c->hx, sizeof(int64_t) * (n + 1)) != cudaSuccess) {
-                cudaGetLastError();
-                return UPR_ERR_OOM;
-            }
-            c->hx_cap = n + 1;
-        }
-        xadj_store = c->hx;
-    }
-    if (ng == 1 && xadj_store) {
-        // one graph whose xadj is device memory: read back, checked on several threads
-        UPR_CUDA(cudaMemcpy(xadj_store, gs[0].xadj, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
-        if (xadj_store[0] != 0 || xadj_store[n] != m) return UPR_ERR_INVALID;
-        std::vector<char> bad(nthreads, 0);
-        parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
-            for (int64_t v = v0; v < v1; v++)
-                if (xadj_store[v + 1] < xadj_store[v]) { bad[t] = 1; return; }
-        });
-        for (char x : bad)
-            if (x) return UPR_ERR_INVALID;
-        xadj_h = xadj_store;
-    } else if (xadj_store) {
-        // graph i's offsets shifted by the entries of the graphs before it,
-        // checked on the way (starts at 0, non-decreasing, ends at m_i), one
-        // pass per graph on several threads; device graphs are read back first
-        std::vector<char> dev(ng, 0);
-        std::vector<std::vector<int64_t>> dev_x(ng);
-        for (int32_t i = 0; i < ng; i++) {
-            dev[i] = gs[i].n > 0 && mem_kind(gs[i].xadj) == kDevice;
-            if (dev[i]) {
-                dev_x[i].resize(gs[i].n + 1);
-                UPR_CUDA(cudaMemcpy(dev_x[i].data(), gs[i].xadj, sizeof(int64_t) * (gs[i].n + 1),
-                                    cudaMemcpyDeviceToHost));
-            }
-        }
-        std::vector<char> bad(nthreads, 0);
-        parallel_segments(ng, nthreads, [&](int t, int64_t i0, int64_t i1) {
-            for (int64_t i = i0; i < i1; i++) {
-                const int64_t gn = gs[i].n;
-                if (gn == 0) continue;
-                const int64_t *src = dev[i] ? dev_x[i].data() : gs[i].xadj;
-                int64_t *dst = xadj_store + c->noff[i];
-                const int64_t off = eoff[i];
-                bool ok = src[0] == 0 && src[gn] == gs[i].m;
-                for (int64_t v = 0; v < gn; v++) {
-                    ok = ok && src[v] <= src[v + 1];
-                    dst[v] = src[v] + off;
-                }
-                if (!ok) bad[t] = 1;
-            }
-        });
-        for (char x : bad)
-            if (x) return UPR_ERR_INVALID;
-        xadj_store[n] = m;
-        xadj_h = xadj_store;
-    }
     int64_t cmax = 1;
     for (int32_t i = 0; i < ng; i++) {
         const upr_graph *g = &gs[i];
@@ -1948,92 +1878,78 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     }
     c->Lmax = c->Lmax_g[0];
     c->cbits = bit_length((uint64_t)cmax);
-    // static schedules, built segment by segment (a segment boundary also
-    // ends a tile): hub chunks of 8192 entries of one node of degree >
-    // kHubDegree, and the tiles of the table build, runs of consecutive
-    // nodes with at most tile_nodes rows (<= 32 KB of shared memory) and at
-    // most kTileEntries non-hub adjacency entries; a hub closes its tile.
-    // Rows are independent, so a tile may span two graphs of a batch.
-    const int32_t tile_nodes = k % 4 == 0 ? (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k)) : 0;
-    std::vector<std::vector<HubChunk>> seg_chunks(nthreads);
-    std::vector<std::vector<TableTile>> seg_tiles(nthreads);
-    parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
-        for (int64_t v = v0; v < v1; v++) {
-            const int64_t d = xadj_h[v + 1] - xadj_h[v];
-            if (d > kHubDegree)
-                for (int64_t b = xadj_h[v]; b < xadj_h[v + 1]; b += 8192)
-                    seg_chunks[t].push_back(HubChunk{(int32_t)v, 0, b, std::min(b + 8192, xadj_h[v + 1])});
-        }
-        if (!tile_nodes) return;
-        const int64_t kTileEntries = 4096;
-        int64_t v = v0;
-        while (v < v1) {
-            TableTile tl{xadj_h[v], xadj_h[v], (int32_t)v, (int32_t)v};
-            while (v < v1 && tl.v1 - tl.v0 < tile_nodes) {
-                const int64_t d = xadj_h[v + 1] - xadj_h[v];
-                if (d > kHubDegree) { tl.v1 = (int32_t)(++v); break; }     // hub: row zero here, last in tile
-                if (tl.e1 + d - tl.e0 > kTileEntries && tl.v1 > tl.v0) break;
-                tl.e1 += d;
-                tl.v1 = (int32_t)(++v);
-            }
-            seg_tiles[t].push_back(tl);
-        }
-    });
-    std::vector<HubChunk> chunks;
-    std::vector<TableTile> tiles;
-    for (int t = 0; t < nthreads; t++) {
-        chunks.insert(chunks.end(), seg_chunks[t].begin(), seg_chunks[t].end());
-        tiles.insert(tiles.end(), seg_tiles[t].begin(), seg_tiles[t].end());
+    // the packed offsets on the device (a staging buffer kept across
+    // bindings), checked there for one graph, and the static schedules
+    // counted (bind.cu): hub chunks of 8192 entries of one node of degree >
+    // kHubDegree, the table build's tiles (at most tile_nodes rows, <= 32 KB
+    // of shared memory), the hashed rows' slots, the hubs
+    cudaStream_t s = c->s;
+    if (!c->h) {
+        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * (4 * (int64_t)kMaxK + 256)));
+        int64_t *hb = c->h + 4 * (int64_t)kMaxK;
+        c->hF = hb;                                             // 73
+        c->hcut = hb + 80;                                      // 1
+        c->hbest = reinterpret_cast<long long *>(hb + 88);      // 3
+        c->hctl = reinterpret_cast<RebalCtl *>(hb + 96);        // 4
+        c->hcnt = reinterpret_cast<int32_t *>(hb + 112);        // 64 ints
     }
+    // staging layout: packed offsets [n + 1], schedule counts [4 nseg], 8
+    // words (totals, largest row, check flag); a batch adds each graph's own
+    // offsets [n + ng] and the graphs' node and entry offsets [ng + 1] x 2
+    const int64_t nseg = sched_segments(n);
+    const int64_t xs_need = n + 1 + 4 * nseg + 8 + (ng > 1 ? n + ng + 2 * (ng + 1) : 0);
+    if (c->xs_cap < xs_need) {
+        if (c->xs) cudaFree(c->xs);
+        c->xs = nullptr;
+        c->xs_cap = 0;
+        if (cudaMalloc(&c->xs, sizeof(int64_t) * (size_t)xs_need) != cudaSuccess) {
+            cudaGetLastError();
+            return UPR_ERR_OOM;
+        }
+        c->xs_cap = xs_need;
+    }
+    int64_t *sx = c->xs, *scnt = c->xs + n + 1, *stot = scnt + 4 * nseg;   // stot: 4 totals, cap, check flag
+    UPR_CUDA(cudaMemsetAsync(stot, 0, 8 * sizeof(int64_t), s));
+    if (ng == 1) {
+        if (n > 0) copy_in(sx, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
+        else UPR_CUDA(cudaMemsetAsync(sx, 0, sizeof(int64_t), s));
+        xadj_check(sx, n, m, reinterpret_cast<int32_t *>(stot + 5), s);
+    } else {
+        // each graph's offsets as given, then packed (shifted by the entries of
+        // the graphs before it) and checked on the device
+        int64_t *raw = stot + 8, *d_noff = raw + n + ng, *d_eoff = d_noff + ng + 1;
+        for (int32_t i = 0; i < ng; i++)
+            if (gs[i].n > 0) copy_in(raw + c->noff[i] + i, gs[i].xadj, sizeof(int64_t) * (gs[i].n + 1), s);
+        UPR_CUDA(cudaMemcpyAsync(d_noff, c->noff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
+        UPR_CUDA(cudaMemcpyAsync(d_eoff, eoff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
+        xadj_pack(raw, d_noff, d_eoff, ng, n, sx, reinterpret_cast<int32_t *>(stot + 5), s);
+    }
+    const int32_t tile_nodes = k % 4 == 0 ? (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k)) : 0;
     // sparse rows: a power of two >= min(k, 2 deg(v)) + 1 slots per row (mode 3:
     // min(k, deg(v)) + 1); chosen by size (mode 0) when k >= 128 and the rows
     // take at most half the bytes of the dense table
-    std::vector<int64_t> sp_off_h;
+    const int mode = prm.table;
+    const int sp_mode = (k % 4 == 0 && k <= kSparseRowMax / 2 && (mode >= 2 || (mode == 0 && k >= 128)))
+                            ? (mode == 3 ? 3 : 1) : 0;
+    sched_count(sx, n, m, tile_nodes, sp_mode, k, scnt, stot, reinterpret_cast<unsigned long long *>(stot + 4), s);
+    int64_t *ht = c->h;                      // (the pinned block's first words: free outside a call)
+    UPR_CUDA(cudaMemcpyAsync(ht, stot, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    UPR_CUDA(cudaStreamSynchronize(s));
+    if ((int32_t)ht[5] != 0) return UPR_ERR_INVALID;
+    const int64_t n_hubs = ht[3];
     {
-        const int mode = prm.table;
-        int64_t total = 0, buf_cap = 1;
-        if (k % 4 == 0 && k <= kSparseRowMax / 2 && (mode >= 2 || (mode == 0 && k >= 128))) {
-            sp_off_h.assign(n + 1, 0);
-            std::vector<int64_t> seg_total(nthreads, 0), seg_cap(nthreads, 1);
-            auto cap_of = [&](int64_t v) {
-                const int64_t d = xadj_h[v + 1] - xadj_h[v];
-                const int64_t want = std::min<int64_t>(k, mode == 3 ? d : 2 * d) + 1;
-                int64_t cap = 1;
-                while (cap < want) cap <<= 1;
-                return cap;
-            };
-            parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
-                int64_t tot = 0, bc = 1;
-                for (int64_t v = v0; v < v1; v++) {
-                    const int64_t cap = cap_of(v);
-                    sp_off_h[v] = tot;              // local offset for now
-                    tot += cap;
-                    if (xadj_h[v + 1] - xadj_h[v] <= kHubDegree) bc = std::max(bc, cap);
-                }
-                seg_total[t] = tot;
-                seg_cap[t] = bc;
-            });
-            std::vector<int64_t> seg_base(nthreads + 1, 0);
-            for (int t = 0; t < nthreads; t++) {
-                seg_base[t + 1] = seg_base[t] + seg_total[t];
-                buf_cap = std::max(buf_cap, seg_cap[t]);
-            }
-            parallel_segments(n, nthreads, [&](int t, int64_t v0, int64_t v1) {
-                for (int64_t v = v0; v < v1; v++) sp_off_h[v] += seg_base[t];
-            });
-            total = seg_base[nthreads];
-            sp_off_h[n] = total;
-            if (mode == 0 && total * (int64_t)sizeof(int2) * 2 > n * (int64_t)k * (int64_t)sizeof(int32_t))
-                total = 0, buf_cap = 1, sp_off_h.clear();
-        }
+        int64_t total = sp_mode ? ht[2] : 0, buf_cap = sp_mode ? std::max<int64_t>(1, ht[4]) : 1;
+        if (sp_mode && mode == 0 && total * (int64_t)sizeof(int2) * 2 > n * (int64_t)k * (int64_t)sizeof(int32_t))
+            total = 0, buf_cap = 1;
         c->sp_slots = total;
         c->sp_buf_cap = (int32_t)buf_cap;
     }
+    const int sp_write = c->sp_slots > 0 ? sp_mode : 0;
     const auto t_sched = std::chrono::steady_clock::now();
     c->m = m; c->k = k;
     c->n = n;                       // layout needs the sizes
-    c->n_chunks = (int64_t)chunks.size();
-    c->n_tiles = (int64_t)tiles.size();
+    c->n_chunks = ht[0];
+    c->n_tiles = tile_nodes ? ht[1] : 0;
     c->tile_nodes = tile_nodes;
     Arena A;
     if (c->W_own) { cudaFree(c->W_own); c->W_own = nullptr; c->W_own_bytes = 0; }
@@ -2052,15 +1968,6 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     const auto t_alloc = std::chrono::steady_clock::now();
     // pinned buffers and events are sized for kMaxK blocks, so a context
     // re-bound to another graph keeps them
-    if (!c->h) {
-        UPR_CUDA(cudaMallocHost((void **)&c->h, sizeof(int64_t) * (4 * (int64_t)kMaxK + 256)));
-        int64_t *base = c->h + 4 * (int64_t)kMaxK;
-        c->hF = base;                                           // 73
-        c->hcut = base + 80;                                    // 1
-        c->hbest = reinterpret_cast<long long *>(base + 88);    // 3
-        c->hctl = reinterpret_cast<RebalCtl *>(base + 96);      // 4
-        c->hcnt = reinterpret_cast<int32_t *>(base + 112);      // 64 ints
-    }
     if (!c->h8) UPR_CUDA(cudaMallocHost((void **)&c->h8, 2 * (size_t)kMaxK + 64));
     for (auto &ev : c->ev)
         if (!ev) UPR_CUDA(cudaEventCreate(&ev));
@@ -2069,13 +1976,11 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->sel_cfg = c->prop_cfg = LaneCfg{0, 0};
     c->sel_tuned = c->prop_tuned = false;
     c->sel_pending = c->prop_pending = 0;
-    cudaStream_t s = c->s;
-    if (ng == 1) {
-        if (n > 0) copy_in(c->xadj, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
-        else UPR_CUDA(cudaMemsetAsync(c->xadj, 0, sizeof(int64_t), s));
-    } else {
-        UPR_CUDA(cudaMemcpyAsync(c->xadj, xadj_store, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
-    }
+    UPR_CUDA(cudaMemcpyAsync(c->xadj, sx, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
+    // the schedules written (the hub list into a sort buffer, free until the
+    // first round, for the duplicate check)
+    int32_t *hubs_d = reinterpret_cast<int32_t *>(c->sb[0].v);
+    sched_write(c->xadj, n, m, tile_nodes, sp_write, k, scnt, c->hub_chunks, c->tiles, c->sp_off, hubs_d, s);
     for (int32_t i = 0; i < ng; i++) {
         const upr_graph *g = &gs[i];
         const int64_t v0 = c->noff[i], e0 = eoff[i];
@@ -2092,15 +1997,9 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         UPR_CUDA(cudaMemcpyAsync(c->Lb, Lb.data(), sizeof(int64_t) * Lb.size(), cudaMemcpyHostToDevice, s));
         UPR_CUDA(cudaStreamSynchronize(s));     // Lb is a local vector
     }
-    if (!chunks.empty())
-        UPR_CUDA(cudaMemcpyAsync(c->hub_chunks, chunks.data(), sizeof(HubChunk) * chunks.size(), cudaMemcpyHostToDevice,
-                                 s));
-    if (!tiles.empty())
-        UPR_CUDA(cudaMemcpyAsync(c->tiles, tiles.data(), sizeof(TableTile) * tiles.size(), cudaMemcpyHostToDevice, s));
+
     const int32_t kmask = ng == 1 ? -1 : ((k & (k - 1)) == 0 ? k - 1 : 0);
     c->sparse_on = c->sp_slots > 0;
-    if (c->sparse_on)
-        UPR_CUDA(cudaMemcpyAsync(c->sp_off, sp_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
     UPR_CUDA(cudaMemsetAsync(c->sp_over, 0, sizeof(int32_t), s));
     c->G = GraphDev{n,      m,        k,       ng,   kmask, c->xadj, c->adj, any_adjw ? c->adjw : nullptr,
                     any_vwgt ? c->vwgt : nullptr, c->wI, c->Lb, c->gid,
@@ -2122,17 +2021,10 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         if (flags & 128) {
             // a row that is not strictly increasing: the exact duplicate check
             // (the hub list goes to a sort buffer, free until the first round)
-            std::vector<int32_t> hubs;
-            for (size_t i = 0; i < chunks.size(); i++)
-                if (i == 0 || chunks[i].v != chunks[i - 1].v) hubs.push_back(chunks[i].v);
-            int32_t *hubs_d = reinterpret_cast<int32_t *>(c->sb[0].v);
-            if (!hubs.empty())
-                UPR_CUDA(cudaMemcpyAsync(hubs_d, hubs.data(), sizeof(int32_t) * hubs.size(), cudaMemcpyHostToDevice,
-                                         s));
             UPR_CUDA(cudaMemsetAsync(c->vflags, 0, sizeof(int32_t), s));
             int64_t max_nodes = 0;
             for (int32_t i = 0; i < ng; i++) max_nodes = std::max<int64_t>(max_nodes, c->noff[i + 1] - c->noff[i]);
-            validate_duplicates(c->G, c->vflags, hubs_d, (int64_t)hubs.size(), c->noff_d, max_nodes,
+            validate_duplicates(c->G, c->vflags, hubs_d, n_hubs, c->noff_d, max_nodes,
                                 reinterpret_cast<int32_t *>(c->sb[1].k), 4 * std::max<int64_t>(n, 1), s);
             UPR_CUDA(cudaMemcpyAsync(&flags, c->vflags, sizeof(flags), cudaMemcpyDeviceToHost, s));
             UPR_CUDA(cudaStreamSynchronize(s));
@@ -2192,7 +2084,7 @@ upr_status ctx_rebind(upr_ctx *c, const upr_graph *g, int32_t k, double eps, con
 }
 
 // Device bytes of the context's arena.
-size_t ctx_arena_bytes(const upr_ctx *c) { return c ? c->mem_bytes : 0; }
+size_t ctx_arena_bytes(const upr_ctx *c) { return c ? c->mem_bytes + sizeof(int64_t) * (size_t)c->xs_cap : 0; }
 
 upr_status ctx_rebind_batch(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
                             const upr_params *params) {
@@ -2391,5 +2283,6 @@ size_t upr_ctx_footprint(int64_t n, int64_t m, int32_t k, int32_t ng) {
     c.sp_slots = 0;     // the dense layout bounds the sparse one (rows chosen by size take half as many bytes)
     Arena A;
     layout(&c, A);
-    return A.off + ((size_t)1 << 20);
+    // plus the staging buffer of the offsets and schedule counts
+    return A.off + sizeof(int64_t) * (size_t)(n + 1 + 4 * sched_segments(n) + 8) + ((size_t)1 << 20);
 }

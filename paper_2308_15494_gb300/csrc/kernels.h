@@ -176,6 +176,26 @@ void cut_from_table(const GraphDev &g, const int32_t *part, const int32_t *W, in
 // A tile of the table build: nodes [v0, v1) and the adjacency entries [e0, e1)
 // of its non-hub nodes (a hub, if any, is the tile's last node).
 struct TableTile { int64_t e0, e1; int32_t v0, v1; };
+// Static schedules from the packed offsets (bind.cu), over segments of
+// kSchedSegment nodes.  sched_count: cnt[4 s + 0..3] = exclusive offsets of
+// segment s's hub chunks, tiles, hashed-row slots and hubs; tot[0..3] = the
+// totals; *cap_max = the largest hashed row of a non-hub node.  sp_mode 0:
+// no hashed rows, 1: min(k, 2 deg) + 1 slots rounded up to a power of two,
+// 3: min(k, deg) + 1.  sched_write fills the arrays (nullptr: not written).
+constexpr int64_t kSchedSegment = 1024;
+int64_t sched_segments(int64_t n);
+void sched_count(const int64_t *xadj, int64_t n, int64_t m, int tile_nodes, int sp_mode, int32_t k, int64_t *cnt,
+                 int64_t *tot, unsigned long long *cap_max, cudaStream_t s);
+void sched_write(const int64_t *xadj, int64_t n, int64_t m, int tile_nodes, int sp_mode, int32_t k,
+                 const int64_t *off, HubChunk *chunks, TableTile *tiles, int64_t *sp_off, int32_t *hubs,
+                 cudaStream_t s);
+// *bad = 1 unless xadj[0] = 0, xadj[n] = m and xadj is non-decreasing
+void xadj_check(const int64_t *xadj, int64_t n, int64_t m, int32_t *bad, cudaStream_t s);
+// A batch's packed offsets from each graph's own (graph i's n_i + 1 offsets at
+// raw + noff[i] + i), shifted by the entries before it (eoff), checked as
+// xadj_check checks one graph
+void xadj_pack(const int64_t *raw, const int64_t *noff, const int64_t *eoff, int32_t ng, int64_t n, int64_t *out,
+               int32_t *bad, cudaStream_t s);
 // Shared memory of one tile of `nodes` rows (plus per-warp row buffers for the sparse table).
 size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
