@@ -563,7 +563,12 @@ bool enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     int32_t *cnt = c->counts;
     RebalCtl *ctl = c->ctl;
     const Count cS{cnt + CNT_S, n};
-    rebalance_begin(G, c->C, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, c->prm.max_subrounds, ctl, light, s);
+    // a graph-resident loop in the fused form begins each sub-round at the
+    // end of the one before (and the first before the loop, merged_loop_head)
+    const bool merged = cond && fused_rebalance(c, 1 + c->gbits + 2 * c->cbits);
+    if (!merged)
+        rebalance_begin(G, c->C, c->excl_d, c->over_d, c->reject_d, cnt + CNT_L1, c->prm.max_subrounds, ctl, light,
+                        s);
     if (first)
         run_tuned(c, c->prop_tuned, c->prop_cfg, c->prop_cands, &c->prop_pending, c->ev_tune + 6,
                   [&](LaneCfg cfg) {
@@ -627,7 +632,7 @@ bool enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
             table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
                        c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
             rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s, cond,
-                                c->prm.max_subrounds);
+                                c->prm.max_subrounds, merged ? c->over_d : nullptr, c->reject_d, cnt + CNT_L1);
             return cond != 0;
         }
         rebalance_fused_compact_hist(G, c->flags, c->L1, &ctl->n1_active, n, cnt + CNT_L1, st.lgain, st.lsrc,
@@ -653,7 +658,8 @@ bool enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
                                      c->tmp, s);
         table_move(G, c->W, c->R_node, c->R_from, c->R_to, cnt + CNT_A, &ctl->nR, nullptr, n, c->hub_chunks,
                    c->n_chunks, HubMoves{nullptr, c->r_to, c->r_at, &ctl->nR, cnt + CNT_A, c->R_from, c->R_to}, s);
-        rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s, cond, c->prm.max_subrounds);
+        rebalance_fused_end(G, c->C, c->Cd, c->excl_d, c->reject_d, cnt + CNT_A, ctl, s, cond, c->prm.max_subrounds,
+                            merged ? c->over_d : nullptr, c->reject_d, cnt + CNT_L1);
         return cond != 0;
     }
     select_values(c->flags, c->L1, c->L1, cnt + CNT_L1, Count{&ctl->n1_active, n}, c->tmp, s);
@@ -703,6 +709,17 @@ bool enqueue_subround(upr_ctx *c, const RebalState &st, int32_t *light, bool fir
     return false;
 }
 
+// The kernel before a graph-resident loop: the fused form begins the first
+// sub-round there (setting the condition), the general form only sets the
+// condition (its body begins each sub-round itself).
+void loop_head(upr_ctx *c, int32_t *light, cudaGraphConditionalHandle cond, cudaStream_t s) {
+    if (fused_rebalance(c, 1 + c->gbits + 2 * c->cbits))
+        rebalance_begin(c->G, c->C, c->excl_d, c->over_d, c->reject_d, c->counts + CNT_L1, c->prm.max_subrounds,
+                        c->ctl, light, s, cond);
+    else
+        rebalance_continue(c->ctl, c->prm.max_subrounds, cond, s);
+}
+
 // The rebalancing loop as a graph: a kernel sets the condition of a while
 // node whose body is one sub-round followed by the same kernel.  Built on
 // first use for the binding and the proposal schedule, then replayed; false
@@ -722,7 +739,7 @@ bool rebalance_graph(upr_ctx *c, const RebalState &st, int32_t *light) {
         UPR_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
         UPR_CUDA(cudaStreamBeginCaptureToGraph(c->s_cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         capturing = true;
-        rebalance_continue(c->ctl, c->prm.max_subrounds, cond, c->s_cap);
+        loop_head(c, light, cond, c->s_cap);
         captured++;
         cudaGraph_t out = nullptr;
         capturing = false;
@@ -804,7 +821,7 @@ void rebalance_phase(upr_ctx *c, int32_t r, RoundInfo &ri, TraceSink *tr) {
         UPR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle cond;
         UPR_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
-        rebalance_continue(ctl, c->prm.max_subrounds, cond, s);
+        loop_head(c, light, cond, s);
         UPR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
         cudaGraphNodeParams cp = {};
         cp.type = cudaGraphNodeTypeConditional;

@@ -431,10 +431,13 @@ void rebalance_fused_select_admit(const GraphDev &g, const uint32_t *U, const in
                                   Scratch tmp, cudaStream_t s);
 // C += Cd, Cd = 0; then k_reb_end's update of the excluded set and the stop
 // flag; with cond (a graph-resident loop) also the loop's condition, as
-// rebalance_continue sets it
+// rebalance_continue sets it.  With begin_next (over, reject and d_n1
+// given) the next sub-round's begin follows in the same kernel (as
+// rebalance_begin) and the condition is "that sub-round runs".
 void rebalance_fused_end(const GraphDev &g, int64_t *C, long long *Cd, int8_t *excl, const int8_t *reject,
                          const int32_t *d_na, RebalCtl *ctl, cudaStream_t s, cudaGraphConditionalHandle cond = 0,
-                         int32_t max_subrounds = 0);
+                         int32_t max_subrounds = 0, int8_t *over = nullptr, int8_t *reject_next = nullptr,
+                         const int32_t *d_n1 = nullptr);
 // The prefilter's cut bin of every overloaded source (hist rows read are cleared).
 void rebalance_prio_cut(const GraphDev &g, const int8_t *over, const int64_t *C, unsigned long long *hist, int32_t *cut,
                         cudaStream_t s);
@@ -460,8 +463,11 @@ void rebalance_apply(const GraphDev &g, const int32_t *P, const uint32_t *A, con
 // Loop control over the K blocks of g (C = current block weights).  light
 // receives each graph's lightest non-excluded block (&ctl->light for one graph).
 void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl *ctl, cudaStream_t s);
+// cond (one graph, a graph-resident loop whose body does not begin with this
+// kernel): also sets the loop's condition to "this sub-round runs"
 void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
-                     const int32_t *d_n1, int32_t max_subrounds, RebalCtl *ctl, int32_t *light, cudaStream_t s);
+                     const int32_t *d_n1, int32_t max_subrounds, RebalCtl *ctl, int32_t *light, cudaStream_t s,
+                     cudaGraphConditionalHandle cond = 0);
 // Sets the condition of a graph's while node: another sub-round is due.
 void rebalance_continue(const RebalCtl *ctl, int32_t max_subrounds, cudaGraphConditionalHandle handle,
                         cudaStream_t s);

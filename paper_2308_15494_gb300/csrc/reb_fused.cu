@@ -673,8 +673,9 @@ __global__ void __launch_bounds__(kThreads) k_fr_admit(const uint32_t *__restric
 // In a graph-resident loop (cond != 0) it also sets the loop's condition:
 // another sub-round while the loop has not stopped and sub-rounds are left.
 __global__ void k_fr_end(int64_t *__restrict__ C, long long *__restrict__ Cd, const int64_t *__restrict__ Lb, int32_t K,
-                         int8_t *__restrict__ excl, const int8_t *__restrict__ reject, const int32_t *__restrict__ d_na,
-                         RebalCtl *__restrict__ ctl, cudaGraphConditionalHandle cond, int32_t max_subrounds) {
+                         int8_t *__restrict__ excl, int8_t *reject, const int32_t *__restrict__ d_na,
+                         RebalCtl *__restrict__ ctl, cudaGraphConditionalHandle cond, int32_t max_subrounds,
+                         int8_t *__restrict__ over, const int32_t *__restrict__ d_n1) {
     __shared__ int s_grew, s_over;
     if (threadIdx.x == 0) s_grew = 0, s_over = 0;
     __syncthreads();
@@ -693,8 +694,52 @@ __global__ void k_fr_end(int64_t *__restrict__ C, long long *__restrict__ Cd, co
         ctl->nR += na;
         if ((na == 0 && !s_grew) || !s_over) ctl->stopped = 1;
     }
-    if (threadIdx.x == 0 && cond)
-        cudaGraphSetConditional(cond, (!ctl->stopped && ctl->subrounds < max_subrounds) ? 1u : 0u);
+    if (!over) {
+        if (threadIdx.x == 0 && cond)
+            cudaGraphSetConditional(cond, (!ctl->stopped && ctl->subrounds < max_subrounds) ? 1u : 0u);
+        return;
+    }
+    // the next sub-round's begin (k_reb_begin's steps) on the updated weights
+    // and exclusions: overloaded set, lightest allowed block, activity
+    __shared__ int s_any;
+    __shared__ long long s_w[256];
+    __shared__ int s_b[256];
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    long long bw = 0;
+    int bb = -1;
+    for (int b = threadIdx.x; b < K; b += blockDim.x) {
+        const bool o = C[b] > Lb[b];
+        over[b] = o ? 1 : 0;
+        reject[b] = 0;
+        if (o) s_any = 1;
+        if (!excl[b] && (bb < 0 || C[b] < bw)) { bw = C[b]; bb = b; }
+    }
+    s_w[threadIdx.x] = bw;
+    s_b[threadIdx.x] = bb;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const int b2 = s_b[threadIdx.x + o];
+            const long long w2 = s_w[threadIdx.x + o];
+            const int b1 = s_b[threadIdx.x];
+            if (b2 >= 0 && (b1 < 0 || w2 < s_w[threadIdx.x] || (w2 == s_w[threadIdx.x] && b2 < b1))) {
+                s_b[threadIdx.x] = b2;
+                s_w[threadIdx.x] = w2;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int32_t h = ctl->subrounds + 1;
+        const bool run = !ctl->stopped && s_any && h <= max_subrounds;
+        ctl->active = run ? 1 : 0;
+        if (!run) ctl->stopped = 1;
+        if (run) ctl->subrounds = h;
+        ctl->light = s_b[0];
+        ctl->n1_active = run ? *d_n1 : 0;
+        if (cond) cudaGraphSetConditional(cond, run ? 1u : 0u);
+    }
 }
 
 
@@ -1565,8 +1610,11 @@ void rebalance_fused_mega(const GraphDev &g, RebalMega m, int key_bits, int64_t 
 
 void rebalance_fused_end(const GraphDev &g, int64_t *C, long long *Cd, int8_t *excl, const int8_t *reject,
                          const int32_t *d_na, RebalCtl *ctl, cudaStream_t s, cudaGraphConditionalHandle cond,
-                         int32_t max_subrounds) {
-    k_fr_end<<<1, 256, 0, s>>>(C, Cd, g.Lb, g.K(), excl, reject, d_na, ctl, cond, max_subrounds);
+                         int32_t max_subrounds, int8_t *over, int8_t *reject_next, const int32_t *d_n1) {
+    if (over && (!reject_next || reject_next != reject || !d_n1 || g.K() > 256))
+        throw CudaError{cudaErrorInvalidValue, "rebalance_fused_end: begin_next needs reject and d_n1, K <= 256"};
+    k_fr_end<<<1, 256, 0, s>>>(C, Cd, g.Lb, g.K(), excl, const_cast<int8_t *>(reject), d_na, ctl, cond, max_subrounds,
+                               over, d_n1);
     UPR_LAUNCH_CHECK();
 }
 

@@ -336,7 +336,8 @@ __global__ void k_reb_init_batch(const int64_t *__restrict__ C, const int64_t *_
 // set, lightest allowed block, activity.
 __global__ void k_reb_begin(const int64_t *__restrict__ C, const int64_t *__restrict__ Lb, int32_t k,
                             const int8_t *__restrict__ excl, int8_t *__restrict__ over, int8_t *__restrict__ reject,
-                            const int32_t *__restrict__ d_n1, int32_t max_subrounds, RebalCtl *__restrict__ ctl) {
+                            const int32_t *__restrict__ d_n1, int32_t max_subrounds, RebalCtl *__restrict__ ctl,
+                            cudaGraphConditionalHandle cond) {
     __shared__ int s_any;
     __shared__ long long s_w[256];
     __shared__ int s_b[256];
@@ -374,6 +375,8 @@ __global__ void k_reb_begin(const int64_t *__restrict__ C, const int64_t *__rest
         if (run) ctl->subrounds = h;
         ctl->light = s_b[0];
         ctl->n1_active = run ? *d_n1 : 0;
+        // a graph-resident loop whose body starts without this kernel: its condition
+        if (cond) cudaGraphSetConditional(cond, run ? 1u : 0u);
     }
 }
 
@@ -942,9 +945,10 @@ void rebalance_init(const GraphDev &g, const int64_t *C, int8_t *excl, RebalCtl 
 }
 
 void rebalance_begin(const GraphDev &g, const int64_t *C, const int8_t *excl, int8_t *over, int8_t *reject,
-                     const int32_t *d_n1, int32_t max_subrounds, RebalCtl *ctl, int32_t *light, cudaStream_t s) {
+                     const int32_t *d_n1, int32_t max_subrounds, RebalCtl *ctl, int32_t *light, cudaStream_t s,
+                     cudaGraphConditionalHandle cond) {
     if (g.ng == 1) {
-        k_reb_begin<<<1, 256, 0, s>>>(C, g.Lb, g.k, excl, over, reject, d_n1, max_subrounds, ctl);
+        k_reb_begin<<<1, 256, 0, s>>>(C, g.Lb, g.k, excl, over, reject, d_n1, max_subrounds, ctl, cond);
     } else {
         clear_ticket(ctl, s);
         k_reb_begin_batch<<<ctl_grid((int64_t)g.ng * 32), 256, 0, s>>>(C, g.Lb, g.k, g.ng, excl, over, reject, d_n1,
