@@ -200,6 +200,8 @@ struct upr_ctx {
     uint64_t gen = 0, reb_gen = ~0ull;  // binding generation; the one reb_exec belongs to
     LaneCfg reb_cfg{};
     int reb_body_kernels = 0;
+    cudaStream_t s_up = nullptr;      // binding: the early upload of the adjacency
+    cudaEvent_t ev_up = nullptr, ev_prev = nullptr;
     int64_t *xs = nullptr;            // binding: the packed offsets and the schedule counts (bind.cu), kept
     int64_t xs_cap = 0;
     int reb_if_kernels = 0;           // kernels of the conditional sort passes in the sub-round body
@@ -1225,6 +1227,9 @@ void free_ctx(upr_ctx *c) {
     if (c->s_body) cudaStreamDestroy(c->s_body);
     if (c->s_if) cudaStreamDestroy(c->s_if);
     if (c->xs) cudaFree(c->xs);
+    if (c->s_up) cudaStreamDestroy(c->s_up);
+    if (c->ev_up) cudaEventDestroy(c->ev_up);
+    if (c->ev_prev) cudaEventDestroy(c->ev_prev);
     if (c->F_all) cudaFree(c->F_all);
     if (c->hF_all) cudaFreeHost(c->hF_all);
     if (c->h) cudaFreeHost(c->h);
@@ -1910,6 +1915,33 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         c->hctl = reinterpret_cast<RebalCtl *>(hb + 96);        // 4
         c->hcnt = reinterpret_cast<int32_t *>(hb + 112);        // 64 ints
     }
+    // one graph rebound to an arena that already has room for its adjacency
+    // at the adjacency's offset (which depends only on n, m, k and ng): the
+    // adjacency upload starts now on a side stream, beside the offsets'
+    // checks and the schedules, after the work already queued on s
+    bool early = false;
+    size_t adj_off = 0;
+    // whatever way the binding ends, the early copy has landed before the
+    // arena can be freed or written again
+    struct UpGuard {
+        upr_ctx *c;
+        bool on = false;
+        ~UpGuard() { if (on) cudaEventSynchronize(c->ev_up); }
+    } up_guard{c};
+    if (ng == 1 && m > 0 && c->mem) {
+        upr_ctx dry;
+        dry.n = n; dry.m = m; dry.k = k; dry.ng = ng;
+        Arena D;
+        D.base = reinterpret_cast<char *>((uintptr_t)1 << 20);
+        layout(&dry, D);
+        adj_off = (size_t)(reinterpret_cast<char *>(dry.adj) - D.base);
+        if (c->mem_bytes >= adj_off + sizeof(int32_t) * (size_t)m) {
+            if (!c->s_up) UPR_CUDA(cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking));
+            if (!c->ev_up) UPR_CUDA(cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming));
+            if (!c->ev_prev) UPR_CUDA(cudaEventCreateWithFlags(&c->ev_prev, cudaEventDisableTiming));
+            early = true;           // (issued below, after the offsets' copy, which the schedules wait for)
+        }
+    }
     // staging layout: packed offsets [n + 1], schedule counts [4 nseg], 8
     // words (totals, largest row, check flag); a batch adds each graph's own
     // offsets [n + ng] and the graphs' node and entry offsets [ng + 1] x 2
@@ -1930,6 +1962,13 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     if (ng == 1) {
         if (n > 0) copy_in(sx, gs[0].xadj, sizeof(int64_t) * (n + 1), s);
         else UPR_CUDA(cudaMemsetAsync(sx, 0, sizeof(int64_t), s));
+        if (early) {
+            UPR_CUDA(cudaEventRecord(c->ev_prev, s));
+            UPR_CUDA(cudaStreamWaitEvent(c->s_up, c->ev_prev, 0));
+            copy_in(static_cast<char *>(c->mem) + adj_off, gs[0].adjncy, sizeof(int32_t) * m, c->s_up);
+            UPR_CUDA(cudaEventRecord(c->ev_up, c->s_up));
+            up_guard.on = true;
+        }
         xadj_check(sx, n, m, reinterpret_cast<int32_t *>(stot + 5), s);
     } else {
         // each graph's offsets as given, then packed (shifted by the entries of
@@ -1976,6 +2015,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     c->step_failed = false;
     layout(c, A);
     if (!c->mem || c->mem_bytes < A.off) {
+        if (early) { UPR_CUDA(cudaEventSynchronize(c->ev_up)); early = false; }     // (its target is freed)
         if (c->mem) { cudaFree(c->mem); c->mem = nullptr; c->mem_bytes = 0; }
         if (cudaMalloc(&c->mem, A.off) != cudaSuccess) { cudaGetLastError(); c->n = -1; return UPR_ERR_OOM; }
         c->mem_bytes = A.off;
@@ -1998,10 +2038,15 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     // first round, for the duplicate check)
     int32_t *hubs_d = reinterpret_cast<int32_t *>(c->sb[0].v);
     sched_write(c->xadj, n, m, tile_nodes, sp_write, k, scnt, c->hub_chunks, c->tiles, c->sp_off, hubs_d, s);
+    if (early && reinterpret_cast<char *>(c->adj) != static_cast<char *>(c->mem) + adj_off) {
+        UPR_CUDA(cudaEventSynchronize(c->ev_up));       // (not where the layout put it: copied again)
+        early = false;
+    }
+    if (early) UPR_CUDA(cudaStreamWaitEvent(s, c->ev_up, 0));
     for (int32_t i = 0; i < ng; i++) {
         const upr_graph *g = &gs[i];
         const int64_t v0 = c->noff[i], e0 = eoff[i];
-        copy_in(c->adj + e0, g->adjncy, sizeof(int32_t) * g->m, s);
+        if (!early) copy_in(c->adj + e0, g->adjncy, sizeof(int32_t) * g->m, s);
         if (g->adjwgt) copy_in(c->adjw + e0, g->adjwgt, sizeof(int32_t) * g->m, s);
         else if (any_adjw) fill_i32(c->adjw + e0, g->m, 1, s);
         if (g->vwgt) copy_in(c->vwgt + v0, g->vwgt, sizeof(int32_t) * g->n, s);
