@@ -217,12 +217,19 @@ struct upr_ctx {
     cudaStream_t s_body = nullptr;    // captures the while nodes' bodies
     uint64_t step_gen = ~0ull;
     int32_t step_rounds = -1, step_off = -1, step_total = -1, step_lock = -1;
+    bool step_cut = false;            // captured with round 1 summing the input cut (cut_pending)
     LaneCfg step_sel{}, step_prop{};
     bool step_failed = false, capturing = false;
     int32_t cap_round = 0;            // while capturing: index of the round in the call (0-based)
     long long step_kernels = 0;       // kernels of the step graph outside the while bodies
     int64_t *F_all = nullptr; int64_t *hF_all = nullptr; int32_t F_all_cap = 0;   // [rounds][kSlots]
     int64_t calls_bound = 0;          // refinement calls since the binding
+    // every host value of a binding that a captured launch can depend on (the
+    // sizes, the schedules' counts, the key widths, the arena, the parameters,
+    // the graphs' offsets and limits): a rebinding to a graph with the same
+    // key, with nothing invalidated since, keeps the captured graphs
+    std::vector<int64_t> bkey;
+    uint64_t bkey_gen = ~0ull;        // gen when bkey was taken
     int64_t eps_ppm = 0, total_w = 0, Lmax = 0, wmax = 0;   // one graph: its eps, c(V), L_max
     std::vector<int64_t> noff, Lmax_g;                        // per graph: first node, L_max
     int gbits = 1, cbits = 1;
@@ -1396,7 +1403,8 @@ int lp_round_once(upr_ctx *c, int64_t *cut, int64_t *active_next, RoundInfo &ri)
     }
     const bool kept = c->hcnt[CNT_OVER0] == 0 && cut1 < *cut;
     if (kept) {
-        lp_next(G, c->part0, c->part, c->lp_next, cnt + CNT_L1, s);
+        lp_next(G, c->part0, c->part, c->M_node, dM, c->R_node, dR, c->hub_chunks, c->n_chunks, c->lp_next,
+                cnt + CNT_L1, s);
         std::swap(c->lp_active, c->lp_next);
         UPR_CUDA(cudaMemcpyAsync(c->part0, c->part, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
         UPR_CUDA(cudaMemcpyAsync(c->C0, c->C, sizeof(int64_t) * K, cudaMemcpyDeviceToDevice, s));
@@ -1490,6 +1498,7 @@ bool build_step_graph(upr_ctx *c, int32_t rounds, int32_t total) {
         capturing = true;
         c->s = c->s_cap;
         c->capturing = true;
+        c->step_cut = c->cut_pending;
         for (int32_t i = 1; i <= rounds; i++) {
             c->cap_round = i - 1;
             RoundInfo ri;
@@ -1538,7 +1547,8 @@ bool run_step_graph(upr_ctx *c, int32_t rounds, int32_t total, upr_stats &st) {
     if (c->step_failed) return false;
     const bool same = c->step_exec && c->step_gen == c->gen && c->step_rounds == rounds &&
                       c->step_off == c->prm.round_offset && c->step_total == total &&
-                      c->step_lock == c->prm.lock_rebalanced && c->step_sel.G == c->sel_cfg.G &&
+                      c->step_lock == c->prm.lock_rebalanced && c->step_cut == c->cut_pending &&
+                      c->step_sel.G == c->sel_cfg.G &&
                       c->step_sel.CH == c->sel_cfg.CH && c->step_prop.G == c->prop_cfg.G &&
                       c->step_prop.CH == c->prop_cfg.CH;
     if (!c->table_valid) {
@@ -1608,24 +1618,42 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     // reads omega(v, V_P(v)) and omega(I(v)) of every node anyway, gives the
     // cut, instead of a pass over the edges
     bool defer_cut = ng == 1 && rounds >= 1 && sch == 0 && c->prm.lp_rounds == 0;
-    upr_status rc = load_part(c, part, !defer_cut);
+    // label propagation on the dense table: its first build gives the cut
+    const bool lp_cut = ng == 1 && c->prm.lp_rounds > 0 && !c->G.sp.on();
+    upr_status rc = load_part(c, part, !defer_cut && !lp_cut);
     if (rc != UPR_OK) return rc;
     std::vector<int64_t> cin(ng), cout(ng), C0h(K);
     read_i64(c, c->C0, K, C0h.data());
-    if (defer_cut) {
-        bool bal = true;
-        for (int32_t b = 0; b < K; b++) bal = bal && C0h[b] <= c->Lmax_g[b / c->k];
-        if (!bal) {             // the repair round comes first and has no bucket pass
+    bool bal_in = true;
+    for (int32_t b = 0; b < K; b++) bal_in = bal_in && C0h[b] <= c->Lmax_g[b / c->k];
+    if (defer_cut && !bal_in) {     // the repair round comes first and has no bucket pass
+        edge_cut(c->G, c->part0, c->cut, c->s);
+        c->cut_pending = false;
+        defer_cut = false;
+    }
+    if (lp_cut) {
+        if (bal_in) {
+            UPR_CUDA(cudaEventRecord(c->ev[0], c->s));
+            gain_table(c->G, c->part0, c->W, c->hub_chunks, c->n_chunks, c->n_tiles ? c->tiles : nullptr, c->n_tiles,
+                       c->tile_nodes, nullptr, c->s);
+            UPR_CUDA(cudaEventRecord(c->ev[1], c->s));
+            cut_from_table(c->G, c->part0, c->W, c->cut, c->s);
+            UPR_CUDA(cudaEventSynchronize(c->ev[1]));
+            float t = 0;
+            UPR_CUDA(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+            st.ms_gain_table += t;
+            st.gain_table_builds++;
+            st.lp_table_builds++;
+            c->table_valid = true;
+        } else {                    // the repair round comes first
             edge_cut(c->G, c->part0, c->cut, c->s);
-            c->cut_pending = false;
-            defer_cut = false;
         }
+        c->cut_pending = false;
     }
     if (!defer_cut) read_i64(c, c->cut, ng, cin.data());
     st.cut_in = 0;
     for (int64_t x : cin) st.cut_in += x;
-    bool balanced = true;
-    for (int32_t b = 0; b < K; b++) balanced = balanced && C0h[b] <= c->Lmax_g[b / c->k];
+    const bool balanced = bal_in;
     std::vector<int32_t> keep(ng, 0);
     int64_t repair_gain = 0;
     if (!balanced) {
@@ -1667,8 +1695,8 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     LaneCfg lc[3];
     const bool no_choice = lane_candidates(c->k, lc) <= 1;      // nothing to time: the schedule is fixed
     const bool settled = no_choice || !worth_tuning(c) || (c->sel_tuned && c->prop_tuned);
-    const bool step = c->prm.graphs == 2 && sch == 0 && c->prm.lp_rounds == 0 && !c->G.sp.on() && rounds >= 1 &&
-                      !log_enabled() && settled && c->calls_bound >= 2;
+    const bool step = c->prm.graphs == 2 && sch == 0 && !c->G.sp.on() && rounds >= 1 && !log_enabled() && settled &&
+                      c->calls_bound >= 2;
     const int32_t first_round = step && run_step_graph(c, rounds, total, st) ? rounds + 1 : 1;
     for (int32_t i = first_round; i <= rounds; i++) {
         RoundInfo ri;
@@ -1836,6 +1864,23 @@ void parallel_segments(int64_t n, int parts, F fn) {
     for (auto &x : th) x.join();
 }
 
+// The binding's key (upr_ctx::bkey): the host values the captured graphs'
+// launches were built from.  Everything else they read is device data that
+// a binding rewrites in full.
+std::vector<int64_t> bind_key(const upr_ctx *c) {
+    static_assert(sizeof(upr_params) % sizeof(int64_t) == 0, "parameters as whole words");
+    std::vector<int64_t> key = {c->n, c->m, c->k, c->ng, c->G.kmask, c->G.adjw != nullptr, c->G.vwgt != nullptr,
+                                c->sp_slots, c->sp_buf_cap, c->sparse_on, c->n_chunks, c->n_tiles, c->tile_nodes,
+                                c->gbits, c->cbits, c->wmax, c->Lmax, c->total_w, c->eps_ppm,
+                                (int64_t)(uintptr_t)c->mem, (int64_t)c->mem_bytes, (int64_t)(uintptr_t)c->W};
+    const size_t words = sizeof(upr_params) / sizeof(int64_t);
+    key.resize(key.size() + words);
+    memcpy(key.data() + key.size() - words, &c->prm, sizeof(upr_params));
+    key.insert(key.end(), c->noff.begin(), c->noff.end());
+    key.insert(key.end(), c->Lmax_g.begin(), c->Lmax_g.end());
+    return key;
+}
+
 upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, const double *eps,
                        const upr_params &prm) {
     if (!gs || !eps || ng < 1 || k < 2 || k > kMaxK || (int64_t)ng * k >= (1LL << 30) || !params_ok(prm))
@@ -1854,6 +1899,13 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     }
     if (n >= (1LL << 31) || m >= (1LL << 31)) return UPR_ERR_INVALID;
     const auto t_bind0 = std::chrono::steady_clock::now();
+    // the previous binding's key, if nothing invalidated its graphs since
+    const bool kept_ok = c->n >= 0 && c->bkey_gen == c->gen;
+    const uint64_t gen0 = c->gen;
+    const int64_t calls0 = c->calls_bound, rounds0 = c->rounds_bound;
+    std::vector<int64_t> key0;
+    key0.swap(c->bkey);
+    c->bkey_gen = ~0ull;
     c->n = -1;
     c->table_valid = false;
     UPR_CUDA(cudaGetDevice(&c->device));
@@ -2112,6 +2164,15 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
     fill_i32(c->m_pos, n, -1, s);
     fill_i32(c->r_to, n, -1, s);
     UPR_CUDA(cudaStreamSynchronize(s));
+    c->bkey = bind_key(c);
+    if (kept_ok && c->bkey == key0) {
+        // the same key: the graphs captured for the previous binding launch
+        // the same kernels with the same arguments on this one
+        c->gen = gen0;
+        c->calls_bound = calls0;
+        c->rounds_bound = rounds0;
+    }
+    c->bkey_gen = c->gen;
     if (log_enabled()) {
         const auto t_end = std::chrono::steady_clock::now();
         auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };

@@ -581,9 +581,11 @@ void lp_apply(const GraphDev &g, const int32_t *movers, const int32_t *d_cnt, co
               int32_t *M_from, int32_t *M_to, int64_t *M_score, int32_t *m_pos, int64_t *deg_sum, int64_t max_count,
               cudaStream_t s);
 // next[u] = 1 for the unmoved neighbours u of the nodes whose block changed
-// from before to after; *d_count = their number
-void lp_next(const GraphDev &g, const int32_t *before, const int32_t *after, int8_t *next, int32_t *d_count,
-             cudaStream_t s);
+// from before to after, every such node being in nodes1[0..*d_cnt1) or
+// nodes2[0..*d_cnt2) (the hubs' rows by their chunks); *d_count = their number
+void lp_next(const GraphDev &g, const int32_t *before, const int32_t *after, const int32_t *nodes1,
+             const int32_t *d_cnt1, const int32_t *nodes2, const int32_t *d_cnt2, const HubChunk *hub_chunks,
+             int64_t n_chunks, int8_t *next, int32_t *d_count, cudaStream_t s);
 // *d_count = the number of non-zero entries of active
 void lp_count(const int8_t *active, int64_t n, int32_t *d_count, cudaStream_t s);
 

@@ -63,18 +63,115 @@ __global__ void k_lp_apply(const int32_t *__restrict__ movers, const int32_t *__
 }
 
 // V_a of the next round: the neighbours of the nodes whose block changed that
-// did not change block themselves (warp per node).
-__global__ void k_lp_next(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                          const int32_t *__restrict__ before, const int32_t *__restrict__ after, int64_t n,
-                          int8_t *__restrict__ next) {
+// did not change block themselves.  One byte per node holds the state: 2
+// moved, 1 unmoved with a moved neighbour, 0 otherwise; then the bytes
+// become the 0/1 markers.  With few moved nodes the moved nodes push (their
+// rows, from the round's two move lists: a node in both, or moved back, is
+// looked at twice or skipped); with more than a quarter of the nodes moved
+// the unmoved nodes pull (their rows until the first moved neighbour).  Hubs'
+// rows go by their chunks, a CTA each.
+__global__ void k_lp_state(const int32_t *__restrict__ before, const int32_t *__restrict__ after, int64_t n,
+                           int8_t *__restrict__ state, int32_t *__restrict__ d_moved) {
+    int32_t c = 0;
+    UPR_FOR(v, n) {
+        const bool moved = before[v] != after[v];
+        state[v] = moved ? 2 : 0;
+        c += moved;
+    }
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(d_moved, c);
+}
+
+__global__ void __launch_bounds__(256) k_lp_mark(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
+                                                 int64_t n, const int32_t *__restrict__ nodes1,
+                                                 const int32_t *__restrict__ d_cnt1,
+                                                 const int32_t *__restrict__ nodes2,
+                                                 const int32_t *__restrict__ d_cnt2,
+                                                 const HubChunk *__restrict__ chunks, int64_t n_chunks,
+                                                 const int32_t *__restrict__ d_moved, int8_t *state) {
+    const bool pull = 4 * (int64_t)*d_moved > n;           // uniform over the grid
     const int lane = threadIdx.x & 31;
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n;
-         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        if (before[v] == after[v]) continue;          // warp-uniform
-        for (int64_t e = xadj[v] + lane; e < xadj[v + 1]; e += 32) {
+    __shared__ int s_hit;
+    for (int64_t ci = blockIdx.x; ci < n_chunks; ci += gridDim.x) {
+        const HubChunk ch = chunks[ci];
+        const int8_t sh = state[ch.v];
+        if (pull ? sh == 2 : sh != 2) continue;            // uniform over the CTA
+        if (threadIdx.x == 0) s_hit = 0;
+        __syncthreads();
+        int hit = 0;
+        for (int64_t e = ch.begin + threadIdx.x; e < ch.end; e += blockDim.x) {
             const int32_t u = adj[e];
-            if (before[u] == after[u]) next[u] = 1;
+            const int8_t su = state[u];
+            if (pull) hit |= su == 2;
+            else if (su == 0) state[u] = 1;
         }
+        if (pull && hit) s_hit = 1;
+        __syncthreads();
+        if (pull && threadIdx.x == 0 && s_hit && state[ch.v] == 0) state[ch.v] = 1;
+    }
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pull) {
+        // 32 consecutive nodes per warp; the unmoved ones scan their rows in turn
+        for (int64_t base = w0 * 32; base < n; base += warps * 32) {
+            const int64_t v = base + lane;
+            uint32_t todo = __ballot_sync(0xffffffffu, v < n && state[v] == 0);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t x = base + src;
+                const int64_t e0 = xadj[x], e1 = xadj[x + 1];
+                if (e1 - e0 > kHubDegree) continue;         // its chunks above
+                bool found = false;
+                for (int64_t e = e0; e < e1 && !found; e += 32)
+                    found = __any_sync(0xffffffffu, e + lane < e1 && state[adj[e + lane]] == 2);
+                if (found && lane == 0) state[x] = 1;
+            }
+        }
+        return;
+    }
+    // 32 listed nodes per warp, spread over the list (neighbouring ids can
+    // share high degrees), their rows (non-hub, moved) in turn
+    const int64_t c1 = *d_cnt1, c2 = *d_cnt2;
+    for (int64_t base = w0; base < c1 + c2; base += warps * 32) {
+        const int64_t j = base + lane * warps;
+        int64_t e0 = 0, e1 = 0;
+        if (j < c1 + c2) {
+            const int32_t v = j < c1 ? nodes1[j] : nodes2[j - c1];
+            if (state[v] == 2) {
+                e0 = xadj[v];
+                e1 = xadj[v + 1];
+                if (e1 - e0 > kHubDegree) e1 = e0;          // its chunks above
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, e1 > e0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t a = __shfl_sync(0xffffffffu, e0, src), b = __shfl_sync(0xffffffffu, e1, src);
+            for (int64_t e = a + lane; e < b; e += 32) {
+                const int32_t u = adj[e];
+                if (state[u] == 0) state[u] = 1;
+            }
+        }
+    }
+}
+
+// The states become the markers (1 for state 1, else 0); *out += their number.
+__global__ void k_lp_final(int8_t *__restrict__ state, int64_t n, int32_t *__restrict__ out) {
+    __shared__ int32_t s_c[8];
+    int32_t c = 0;
+    UPR_FOR(i, n) {
+        const int8_t m = state[i] == 1 ? 1 : 0;
+        state[i] = m;
+        c += m;
+    }
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) c += s_c[w];
+        if (c) atomicAdd(out, c);
     }
 }
 
@@ -121,15 +218,20 @@ void lp_apply(const GraphDev &g, const int32_t *movers, const int32_t *d_cnt, co
     UPR_LAUNCH_CHECK();
 }
 
-void lp_next(const GraphDev &g, const int32_t *before, const int32_t *after, int8_t *next, int32_t *d_count,
-             cudaStream_t s) {
+void lp_next(const GraphDev &g, const int32_t *before, const int32_t *after, const int32_t *nodes1,
+             const int32_t *d_cnt1, const int32_t *nodes2, const int32_t *d_cnt2, const HubChunk *hub_chunks,
+             int64_t n_chunks, int8_t *next, int32_t *d_count, cudaStream_t s) {
     UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s));
     if (g.n == 0) return;
-    UPR_CUDA(cudaMemsetAsync(next, 0, (size_t)g.n, s));
-    const int64_t blocks = std::min<int64_t>(ceil_div(g.n * 32, 256), (int64_t)device_sm_count() * 16);
-    k_lp_next<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, before, after, g.n, next);
+    k_lp_state<<<grid_for(g.n), 256, 0, s>>>(before, after, g.n, next, d_count);
     UPR_LAUNCH_CHECK();
-    k_count_i8<<<grid_for(g.n), 256, 0, s>>>(next, g.n, d_count);
+    const int64_t blocks = std::max<int64_t>(std::min<int64_t>(ceil_div(g.n, 256), (int64_t)device_sm_count() * 8),
+                                             std::min<int64_t>(n_chunks, (int64_t)device_sm_count() * 8));
+    k_lp_mark<<<(unsigned)blocks, 256, 0, s>>>(g.xadj, g.adj, g.n, nodes1, d_cnt1, nodes2, d_cnt2, hub_chunks,
+                                               n_chunks, d_count, next);
+    UPR_LAUNCH_CHECK();
+    UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s));
+    k_lp_final<<<grid_for(g.n), 256, 0, s>>>(next, g.n, d_count);
     UPR_LAUNCH_CHECK();
 }
 
