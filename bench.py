@@ -561,6 +561,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     prm = upr.upr_params_default()
     prm.graphs = 0 if args.no_graphs else args.graphs
+    if args.profile and args.lp_rounds > 0:
+        prm.lp_rounds = args.lp_rounds
     ctx = upr.create_from_workload(w, params=prm, device=True)
     part_init = torch.from_numpy(w.part.copy()).cuda()
     part = torch.empty_like(part_init)
@@ -772,6 +774,8 @@ def main():
     ap.add_argument("--graphs", type=int, default=2, choices=[1, 2],
                     help="params.graphs of the headline workload: 1 each rebalancing loop as a CUDA graph, 2 also "
                          "all rounds of a call as one graph (from the context's second call on)")
+    ap.add_argument("--lp-rounds", type=int, default=0,
+                    help="with --profile: label propagation rounds before the FM rounds of the headline workload")
     ap.add_argument("--profile", action="store_true",
                     help="device loop only (for ncu launch lists): no e2e, no CPU baseline")
     args = ap.parse_args()
