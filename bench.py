@@ -305,8 +305,9 @@ def batched_leg(args, upr, rank, ws, local, graphs):
     adjs = _pinned_views([w.adj for w in graphs])
     assert all(w.vwgt is None and w.adjw is None for w in graphs)       # unit weights
     pinned = [(x, a, None, None) for x, a in zip(xs, adjs)]
-    part_h = torch.from_numpy(np.concatenate([w.part for w in graphs]).astype(np.int32)).pin_memory().numpy()
-    work_h = torch.empty(len(part_h), dtype=torch.int32).pin_memory().numpy()
+    part_t = torch.from_numpy(np.concatenate([w.part for w in graphs]).astype(np.int32)).pin_memory()
+    work_t = torch.empty(len(part_t), dtype=torch.int32).pin_memory()
+    part_h, work_h = part_t.numpy(), work_t.numpy()
     prm1 = upr.upr_params_default()
     prm1.graphs = 2
     eps_all = [w.eps for w in graphs]
@@ -317,7 +318,7 @@ def batched_leg(args, upr, rank, ws, local, graphs):
 
     def e2e_step():
         upr.upr_batch_rebind(c_e2e, pinned, ks, eps_all)
-        work_h[:] = part_h
+        work_t.copy_(part_t)         # the step's input partition (a host copy on several threads)
         return upr.upr_batch_refine(c_e2e, work_h, rounds)
 
     for _ in range(2):          # the second call captures the batches' step graphs
@@ -333,7 +334,7 @@ def batched_leg(args, upr, rank, ws, local, graphs):
     # the same with the context created and destroyed inside the step
     t0 = time.perf_counter()
     c1 = upr.upr_batch_create_mixed(pinned, ks, eps_all, params=prm1)
-    work_h[:] = part_h
+    work_t.copy_(part_t)
     upr.upr_batch_refine(c1, work_h, rounds)
     upr.upr_destroy(c1)
     torch.cuda.synchronize()
@@ -658,12 +659,12 @@ def run_gpu(args):
 
     def e2e_step():
         upr.upr_rebind(c_e2e, pin["xadj"], pin["adj"], w.k, w.eps)
-        pin["work"][:] = pin["part"]
+        pinned["work"].copy_(pinned["part"])     # the step's input partition (a host copy)
         return upr.upr_refine(c_e2e, pin["work"], w.rounds)
 
     def e2e_step_create():
         c = upr.upr_create(pin["xadj"], pin["adj"], w.k, w.eps)
-        pin["work"][:] = pin["part"]
+        pinned["work"].copy_(pinned["part"])
         st = upr.upr_refine(c, pin["work"], w.rounds)
         upr.upr_destroy(c)
         return st

@@ -155,7 +155,42 @@ __global__ void k_xadj_pack(const int64_t *__restrict__ raw, const int64_t *__re
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = eoff[ng];
 }
 
+// Copies of many host arrays in one launch: the arrays are page-locked host
+// memory, which the GPU reads directly; segment i moves len elements from
+// src to dst + off (segments of at most kGatherChunk elements, one per CTA
+// at a time, eight loads in flight per thread).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_host(const HostSeg *__restrict__ segs, int64_t nseg,
+                                                     T *__restrict__ dst) {
+    for (int64_t i = blockIdx.x; i < nseg; i += gridDim.x) {
+        const HostSeg sg = segs[i];
+        const T *src = static_cast<const T *>(sg.src);
+        T *out = dst + sg.off;
+        for (int64_t b = 0; b < sg.len; b += 8 * 256) {
+            T x[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int64_t e = b + u * 256 + threadIdx.x;
+                if (e < sg.len) x[u] = src[e];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int64_t e = b + u * 256 + threadIdx.x;
+                if (e < sg.len) out[e] = x[u];
+            }
+        }
+    }
+}
+
 }  // namespace
+
+void gather_host(const HostSeg *d_segs, int64_t nseg, size_t elem, void *dst, cudaStream_t s) {
+    if (nseg <= 0) return;
+    const unsigned grid = (unsigned)std::min<int64_t>(nseg, (int64_t)device_sm_count() * 8);
+    if (elem == 8) k_gather_host<int64_t><<<grid, 256, 0, s>>>(d_segs, nseg, static_cast<int64_t *>(dst));
+    else k_gather_host<int32_t><<<grid, 256, 0, s>>>(d_segs, nseg, static_cast<int32_t *>(dst));
+    UPR_LAUNCH_CHECK();
+}
 
 void xadj_pack(const int64_t *raw, const int64_t *noff, const int64_t *eoff, int32_t ng, int64_t n, int64_t *out,
                int32_t *bad, cudaStream_t s) {

@@ -204,6 +204,8 @@ struct upr_ctx {
     cudaEvent_t ev_up = nullptr, ev_prev = nullptr;
     int64_t *xs = nullptr;            // binding: the packed offsets and the schedule counts (bind.cu), kept
     int64_t xs_cap = 0;
+    HostSeg *segs_d = nullptr;        // binding a batch: the segments of a gather of host arrays, kept
+    int64_t segs_cap = 0;
     int reb_if_kernels = 0;           // kernels of the conditional sort passes in the sub-round body
     cudaStream_t s_if = nullptr;      // capture stream of that conditional body
     int64_t rounds_bound = 0;         // rounds run since the binding
@@ -408,6 +410,46 @@ void copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
 void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (bytes == 0) return;
     UPR_CUDA(cudaMemcpyAsync(dst, src, bytes, mem_kind(dst) == kDevice ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+// Page-locked host memory that kernels read at the same address.
+bool host_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
+// The copies dst[off_i .. off_i + len_i) <- src_i (elements of `elem` bytes):
+// one gather launch that reads the sources where they are when every one is
+// page-locked host memory (a batch's thousands of small arrays would
+// otherwise be as many DMA transfers), one copy each otherwise.
+void copy_many(upr_ctx *c, const std::vector<const void *> &src, const std::vector<int64_t> &off,
+               const std::vector<int64_t> &len, size_t elem, void *dst, cudaStream_t s) {
+    bool locked = src.size() > 1;                    // (one array: one DMA transfer)
+    for (size_t i = 0; i < src.size() && locked; i++) locked = len[i] <= 0 || host_locked(src[i]);
+    if (!locked) {
+        for (size_t i = 0; i < src.size(); i++)
+            if (len[i] > 0) copy_in(static_cast<char *>(dst) + off[i] * elem, src[i], len[i] * elem, s);
+        return;
+    }
+    std::vector<HostSeg> segs;
+    for (size_t i = 0; i < src.size(); i++)
+        for (int64_t b = 0; b < len[i]; b += kGatherChunk)
+            segs.push_back(HostSeg{static_cast<const char *>(src[i]) + b * elem, off[i] + b,
+                                   std::min<int64_t>(kGatherChunk, len[i] - b)});
+    if (segs.empty()) return;
+    if (c->segs_cap < (int64_t)segs.size()) {
+        UPR_CUDA(cudaStreamSynchronize(s));          // (a gather queued earlier may still read them)
+        if (c->segs_d) cudaFree(c->segs_d);
+        c->segs_d = nullptr;
+        c->segs_cap = 0;
+        UPR_CUDA(cudaMalloc(&c->segs_d, sizeof(HostSeg) * segs.size()));
+        c->segs_cap = (int64_t)segs.size();
+    }
+    // (from pageable memory: the copy waits for the work queued on s, so an
+    // earlier gather has read its segments by then)
+    UPR_CUDA(cudaMemcpyAsync(c->segs_d, segs.data(), sizeof(HostSeg) * segs.size(), cudaMemcpyHostToDevice, s));
+    gather_host(c->segs_d, (int64_t)segs.size(), elem, dst, s);
 }
 
 int32_t read_count(upr_ctx *c, int slot) {
@@ -1234,6 +1276,7 @@ void free_ctx(upr_ctx *c) {
     if (c->s_body) cudaStreamDestroy(c->s_body);
     if (c->s_if) cudaStreamDestroy(c->s_if);
     if (c->xs) cudaFree(c->xs);
+    if (c->segs_d) cudaFree(c->segs_d);
     if (c->s_up) cudaStreamDestroy(c->s_up);
     if (c->ev_up) cudaEventDestroy(c->ev_up);
     if (c->ev_prev) cudaEventDestroy(c->ev_prev);
@@ -1692,6 +1735,12 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     // params.graphs == 2: from a binding's second call on, the plain schedule's
     // rounds run as one graph launch
     c->calls_bound++;
+    // a lane schedule still open after two calls had too little work to time
+    // (e.g. no rebalancing sub-round ran): it keeps the default
+    if (c->calls_bound >= 3) {
+        c->sel_tuned = true;
+        c->prop_tuned = true;
+    }
     LaneCfg lc[3];
     const bool no_choice = lane_candidates(c->k, lc) <= 1;      // nothing to time: the schedule is fixed
     const bool settled = no_choice || !worth_tuning(c) || (c->sel_tuned && c->prop_tuned);
@@ -2026,8 +2075,14 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         // each graph's offsets as given, then packed (shifted by the entries of
         // the graphs before it) and checked on the device
         int64_t *raw = stot + 8, *d_noff = raw + n + ng, *d_eoff = d_noff + ng + 1;
-        for (int32_t i = 0; i < ng; i++)
-            if (gs[i].n > 0) copy_in(raw + c->noff[i] + i, gs[i].xadj, sizeof(int64_t) * (gs[i].n + 1), s);
+        std::vector<const void *> src(ng);
+        std::vector<int64_t> off(ng), len(ng);
+        for (int32_t i = 0; i < ng; i++) {
+            src[i] = gs[i].xadj;
+            off[i] = c->noff[i] + i;
+            len[i] = gs[i].n > 0 ? gs[i].n + 1 : 0;
+        }
+        copy_many(c, src, off, len, sizeof(int64_t), raw, s);
         UPR_CUDA(cudaMemcpyAsync(d_noff, c->noff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
         UPR_CUDA(cudaMemcpyAsync(d_eoff, eoff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
         xadj_pack(raw, d_noff, d_eoff, ng, n, sx, reinterpret_cast<int32_t *>(stot + 5), s);
@@ -2095,14 +2150,23 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         early = false;
     }
     if (early) UPR_CUDA(cudaStreamWaitEvent(s, c->ev_up, 0));
-    for (int32_t i = 0; i < ng; i++) {
-        const upr_graph *g = &gs[i];
-        const int64_t v0 = c->noff[i], e0 = eoff[i];
-        if (!early) copy_in(c->adj + e0, g->adjncy, sizeof(int32_t) * g->m, s);
-        if (g->adjwgt) copy_in(c->adjw + e0, g->adjwgt, sizeof(int32_t) * g->m, s);
-        else if (any_adjw) fill_i32(c->adjw + e0, g->m, 1, s);
-        if (g->vwgt) copy_in(c->vwgt + v0, g->vwgt, sizeof(int32_t) * g->n, s);
-        else if (any_vwgt) fill_i32(c->vwgt + v0, g->n, 1, s);
+    {
+        // the graphs' arrays (a batch's as one gather each where they are
+        // page-locked host memory); unit weights where a graph has none
+        std::vector<const void *> sa, sw, sv;
+        std::vector<int64_t> oa, la, ow, lw, ov, lv;
+        for (int32_t i = 0; i < ng; i++) {
+            const upr_graph *g = &gs[i];
+            const int64_t v0 = c->noff[i], e0 = eoff[i];
+            if (!early) { sa.push_back(g->adjncy); oa.push_back(e0); la.push_back(g->m); }
+            if (g->adjwgt) { sw.push_back(g->adjwgt); ow.push_back(e0); lw.push_back(g->m); }
+            else if (any_adjw) fill_i32(c->adjw + e0, g->m, 1, s);
+            if (g->vwgt) { sv.push_back(g->vwgt); ov.push_back(v0); lv.push_back(g->n); }
+            else if (any_vwgt) fill_i32(c->vwgt + v0, g->n, 1, s);
+        }
+        copy_many(c, sa, oa, la, sizeof(int32_t), c->adj, s);
+        copy_many(c, sw, ow, lw, sizeof(int32_t), c->adjw, s);
+        copy_many(c, sv, ov, lv, sizeof(int32_t), c->vwgt, s);
     }
     {
         std::vector<int64_t> Lb((size_t)ng * k);

@@ -194,6 +194,15 @@ void xadj_check(const int64_t *xadj, int64_t n, int64_t m, int32_t *bad, cudaStr
 // A batch's packed offsets from each graph's own (graph i's n_i + 1 offsets at
 // raw + noff[i] + i), shifted by the entries before it (eoff), checked as
 // xadj_check checks one graph
+// One segment of a gather of host arrays: len elements from src (page-locked
+// host memory, read by the GPU directly) to the destination + off.
+struct HostSeg {
+    const void *src;
+    int64_t off, len;
+};
+constexpr int64_t kGatherChunk = 1 << 16;
+// d_segs (device memory): the segments; elem: 4 or 8 bytes per element
+void gather_host(const HostSeg *d_segs, int64_t nseg, size_t elem, void *dst, cudaStream_t s);
 void xadj_pack(const int64_t *raw, const int64_t *noff, const int64_t *eoff, int32_t ng, int64_t n, int64_t *out,
                int32_t *bad, cudaStream_t s);
 // Shared memory of one tile of `nodes` rows (plus per-warp row buffers for the sparse table).

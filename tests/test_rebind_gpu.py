@@ -9,7 +9,9 @@ on the new graph's data.  The cases below rebind to graphs with the same
 offsets but other neighbours (nodes relabelled within their degree class),
 and then to a graph of another shape; every call must give the oracle's
 partition and cut, and the calls after a same-shape rebinding must run the
-captured graph (no per-phase times: those come from host-driven rounds)."""
+captured graph (no per-phase times: those come from host-driven rounds).
+Batches bound from page-locked host arrays (one gather launch per array
+kind instead of a copy per graph) must give the oracle's results too."""
 from __future__ import annotations
 
 import numpy as np
@@ -133,3 +135,47 @@ def test_label_propagation_then_the_step_graph(upr, shrink):
         assert np.array_equal(p, p0) and st.cut_out == c0
         sts.append(st)
     assert sts[0].ms_select > 0 and sts[2].ms_select == 0
+
+
+def test_batches_from_page_locked_host_arrays(upr):
+    """A batch bound from page-locked host arrays (read by one gather launch
+    per array kind) and rebound to other graphs: weighted and unweighted
+    graphs, isolated nodes, one graph without edges, several k; every graph
+    equals the oracle."""
+    import torch
+
+    def pinned(a):
+        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    def graphs_of(seed, k_list):
+        ws = []
+        for i, k in enumerate(k_list):
+            n = [40, 700, 1500, 90, 3000, 12][i % 6]
+            ws.append(synth.random_small(seed + i, n, [3, 6, 4, 8, 5, 0.1][i % 6], k, weighted=i % 3 != 2,
+                                         hubs=2 if i % 4 == 1 else 0, isolated=4 if i % 5 == 3 else 0))
+        return ws
+
+    def check(ctx, ws, rounds=3):
+        part = np.concatenate([np.asarray(w.part, np.int32) for w in ws])
+        status, cin, cout, st = upr.upr_batch_refine(ctx, part, rounds)
+        off = ctx.offsets
+        for i, w in enumerate(ws):
+            rc, p0, c0, _ = oracle.refine(w, w.part, rounds)
+            assert status[i] == rc, (i, w.name)
+            if rc == oracle.OK:
+                assert np.array_equal(part[off[i]:off[i + 1]], p0), (i, w.name)
+                assert cout[i] == c0, (i, w.name)
+
+    for mixed in (False, True):
+        a = graphs_of(700, [8] * 7 if not mixed else [4, 8, 16, 8, 4, 16, 8])
+        b = graphs_of(800, [8] * 9 if not mixed else [16, 4, 8, 8, 16, 4, 8, 8, 4])
+        ga = [tuple(pinned(x) for x in (w.xadj, w.adj, w.vwgt, w.adjw)) for w in a]
+        gb = [tuple(pinned(x) for x in (w.xadj, w.adj, w.vwgt, w.adjw)) for w in b]
+        if mixed:
+            ctx = upr.upr_batch_create_mixed(ga, [w.k for w in a], [w.eps for w in a])
+        else:
+            ctx = upr.upr_batch_create(ga, 8, [w.eps for w in a])
+        check(ctx, a)
+        upr.upr_batch_rebind(ctx, gb, [w.k for w in b], [w.eps for w in b])
+        check(ctx, b)
+        upr.upr_destroy(ctx)
