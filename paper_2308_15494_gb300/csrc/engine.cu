@@ -2087,7 +2087,7 @@ upr_status bind_graphs(upr_ctx *c, const upr_graph *gs, int32_t ng, int32_t k, c
         UPR_CUDA(cudaMemcpyAsync(d_eoff, eoff.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
         xadj_pack(raw, d_noff, d_eoff, ng, n, sx, reinterpret_cast<int32_t *>(stot + 5), s);
     }
-    const int32_t tile_nodes = k % 4 == 0 ? (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k)) : 0;
+    const int32_t tile_nodes = (int32_t)std::max<int64_t>(4, std::min<int64_t>(512, 8192 / k));
     // sparse rows: a power of two >= min(k, 2 deg(v)) + 1 slots per row (mode 3:
     // min(k, deg(v)) + 1); chosen by size (mode 0) when k >= 128 and the rows
     // take at most half the bytes of the dense table

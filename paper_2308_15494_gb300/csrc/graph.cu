@@ -411,9 +411,14 @@ __device__ __forceinline__ void table_tile(const TableTile t, const int64_t *__r
                              : nullptr;
     if (sp.on())
         for (int i = threadIdx.x; i <= nn; i += blockDim.x) s_off[i] = sp.off[t.v0 + i];
+    // (k % 4 != 0: the rows' block is not a whole number of 16-byte words)
+    const bool quads = k % 4 == 0;
     const int words4 = nn * k / 4;
     const int4 z = make_int4(0, 0, 0, 0);
-    for (int i = threadIdx.x; i < words4; i += blockDim.x) reinterpret_cast<int4 *>(rows)[i] = z;
+    if (quads)
+        for (int i = threadIdx.x; i < words4; i += blockDim.x) reinterpret_cast<int4 *>(rows)[i] = z;
+    else
+        for (int i = threadIdx.x; i < nn * k; i += blockDim.x) rows[i] = 0;
     __syncthreads();
     // ragged head and tail (fewer than 4 entries each) element by element
     const int64_t qa = (t.e0 + 3) >> 2, qb = t.e1 >> 2;     // aligned quads [qa, qb)
@@ -490,6 +495,11 @@ __device__ __forceinline__ void table_tile(const TableTile t, const int64_t *__r
             for (uint32_t i = lane; i < cap; i += 32) sp.slot[o + i] = buf[i];
             __syncwarp();
         }
+        return;
+    }
+    if (!quads) {
+        int32_t *dst1 = W + (int64_t)t.v0 * k;
+        for (int i = threadIdx.x; i < nn * k; i += blockDim.x) __stcs(dst1 + i, rows[i]);
         return;
     }
     int4 *dst = reinterpret_cast<int4 *>(W + (int64_t)t.v0 * k);

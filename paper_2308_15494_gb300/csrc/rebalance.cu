@@ -742,7 +742,7 @@ inline unsigned grid1(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, 256)
 
 int rebalance_group(int k) {
     int G = k / 4;
-    return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
+    return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : k >= 4 ? 4 : 2;
 }
 
 void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const int32_t *d_n1, int64_t n1_max,
@@ -755,6 +755,7 @@ void rebalance_propose_scalar_list(const GraphDev &g, const int32_t *list, const
 #define UPR_PROP(GG) k_propose<GG><<<(unsigned)blocks, 256, 0, s>>>(g, list, d_n1, part, W, st, prop_tgt, prop_gain, \
                                                                     flags)
     switch (G) {
+        case 2: UPR_PROP(2); break;
         case 4: UPR_PROP(4); break;
         case 8: UPR_PROP(8); break;
         case 16: UPR_PROP(16); break;

@@ -622,7 +622,7 @@ void buckets(const GraphDev &g, const int32_t *part, const int32_t *W, int32_t t
 
 int select_group(int k) {
     int G = k / 4;
-    return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
+    return G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : k >= 4 ? 4 : 2;
 }
 
 int lane_candidates(int32_t k, LaneCfg *out) {
@@ -710,6 +710,7 @@ void select_moves(const GraphDev &g, const int32_t *part, const int32_t *W, Pena
     const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count_sel() * 16);
 #define UPR_SEL(GG) k_select<GG><<<(unsigned)blocks, 256, 0, s>>>(g, part, W, pen, cand_tgt, cand_s0, cand_gain, flags)
     switch (G) {
+        case 2: UPR_SEL(2); break;
         case 4: UPR_SEL(4); break;
         case 8: UPR_SEL(8); break;
         case 16: UPR_SEL(16); break;
