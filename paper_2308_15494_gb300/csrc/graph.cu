@@ -324,53 +324,6 @@ __global__ void __launch_bounds__(256) k_dup_hubs(const int32_t *__restrict__ hu
     if (__syncthreads_or(dup) && threadIdx.x == 0) atomicOr(flags, 32);
 }
 
-// Dense gain table: G lanes per node, a k-int row per group in shared memory,
-// shared atomics per adjacency entry, one coalesced row store (int4 when
-// k % 4 == 0).  Nodes of degree > kHubDegree get a zero row here; their rows
-// are accumulated by k_table_hub_chunks afterwards.
-template <int G>
-__global__ void __launch_bounds__(256) k_table_dense(const int64_t *__restrict__ xadj, const int32_t *__restrict__ adj,
-                                                     const int32_t *__restrict__ adjw, const int32_t *__restrict__ part,
-                                                     int64_t n, int32_t k, int32_t kmask, int32_t *__restrict__ W,
-                                                     const int64_t *__restrict__ deg_sum, int64_t m) {
-    if (deg_sum && *deg_sum * 4 < m) return;
-    extern __shared__ int s_rows[];
-    constexpr int kGroups = 256 / G;
-    const int gid = threadIdx.x / G, gl = threadIdx.x % G;
-    int *row = s_rows + gid * k;
-    const bool vec = (k & 3) == 0;
-    for (int64_t base = (int64_t)blockIdx.x * kGroups; base < n; base += (int64_t)gridDim.x * kGroups) {
-        const int64_t v = base + gid;
-        const bool active = v < n;
-        for (int b = gl; b < k; b += G) row[b] = 0;
-        __syncwarp();
-        if (active) {
-            const int64_t b0 = xadj[v], b1 = xadj[v + 1];
-            if (b1 - b0 <= kHubDegree) {
-                // adjacency is read once per build: stream it past L2 so the
-                // gathered partition array stays cached
-                if (adjw) {
-                    for (int64_t e = b0 + gl; e < b1; e += G)
-                        atomicAdd(&row[blk_local(part[__ldcs(adj + e)], k, kmask)], __ldcs(adjw + e));
-                } else {
-                    for (int64_t e = b0 + gl; e < b1; e += G) atomicAdd(&row[blk_local(part[__ldcs(adj + e)], k, kmask)], 1);
-                }
-            }
-        }
-        __syncwarp();
-        if (active) {
-            int32_t *dst = W + v * (int64_t)k;
-            if (vec) {
-                for (int b = gl * 4; b < k; b += G * 4)
-                    __stcs(reinterpret_cast<int4 *>(dst + b), *reinterpret_cast<const int4 *>(row + b));
-            } else {
-                for (int b = gl; b < k; b += G) dst[b] = row[b];
-            }
-        }
-        __syncwarp();
-    }
-}
-
 // Dense gain table, tiled: one CTA per tile of consecutive nodes whose
 // adjacency (without hubs) is one contiguous range of entries.  The CTA
 // streams that range with 16-byte loads (4 * UNROLL entries in flight per
@@ -753,28 +706,7 @@ void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChu
         }
         UPR_LAUNCH_CHECK();
     } else {
-        const int k = g.k;
-        int G = k / 4;
-        G = G < 4 ? 4 : (G > 32 ? 32 : G);
-        G = G >= 32 ? 32 : G >= 16 ? 16 : G >= 8 ? 8 : 4;
-        const size_t shm = (size_t)(256 / G) * k * sizeof(int);
-        const int64_t groups = 256 / G;
-        const int64_t blocks = std::min<int64_t>(ceil_div(g.n, groups), (int64_t)sm_count() * 16);
-        if (shm > 48 * 1024) {
-            kernel_setup((const void *)k_table_dense<4>, -1);
-            kernel_setup((const void *)k_table_dense<8>, -1);
-            kernel_setup((const void *)k_table_dense<16>, -1);
-            kernel_setup((const void *)k_table_dense<32>, -1);
-        }
-#define UPR_TD(GG) k_table_dense<GG><<<(unsigned)blocks, 256, shm, s>>>(g.xadj, g.adj, g.adjw, part, g.n, k, g.kmask, W, deg_sum, g.m)
-        switch (G) {
-            case 4: UPR_TD(4); break;
-            case 8: UPR_TD(8); break;
-            case 16: UPR_TD(16); break;
-            default: UPR_TD(32); break;
-        }
-#undef UPR_TD
-        UPR_LAUNCH_CHECK();
+        throw CudaError{cudaErrorInvalidValue, "gain_table: a binding without table tiles"};
     }
     if (n_chunks > 0) {
         k_table_hub_chunks<<<(unsigned)n_chunks, 512, sizeof(int) * g.k, s>>>(hub_chunks, g.adj, g.adjw, part, g.k,

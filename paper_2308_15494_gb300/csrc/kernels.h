@@ -208,7 +208,7 @@ void xadj_pack(const int64_t *raw, const int64_t *noff, const int64_t *eoff, int
 // Shared memory of one tile of `nodes` rows (plus per-warp row buffers for the sparse table).
 size_t table_tile_smem(int32_t k, int32_t nodes, int32_t sparse_buf_cap);
 // W must hold n*k ints.  Rows of hubs (degree > kHubDegree) are completed by the chunk pass.
-// With tiles (k % 4 == 0), the tiled kernel is used; otherwise the group-per-node kernel.
+// By the binding's tiles (every binding with nodes has them).
 // With deg_sum: runs only when 4 * (*deg_sum) >= m (the rebuild alternative to table_move).
 void gain_table(const GraphDev &g, const int32_t *part, int32_t *W, const HubChunk *hub_chunks, int64_t n_chunks,
                 const TableTile *tiles, int64_t n_tiles, int32_t tile_nodes, const int64_t *deg_sum, cudaStream_t s);
