@@ -8,9 +8,11 @@
 // actual count, so a step can be enqueued without the host knowing how long
 // the previous step's output was.
 //
-// Tiles are 2048 items (256 threads x 8 items).  Scans and compaction are
-// single-pass with decoupled look-back: a CTA takes the next tile index from
-// an atomic counter, publishes its tile total, then walks back over the
+// Scan and compaction tiles are 4096 items (256 threads x 16 items), radix
+// tiles 2048 (256 x 8; the tile ranking's shared memory grows with the
+// items).  Scans and compaction are single-pass with decoupled look-back: a
+// CTA takes the next tile index from an atomic counter, publishes its tile
+// total, then walks back over the
 // preceding tiles' published totals until it meets an inclusive prefix, and
 // publishes its own.  A tile only waits for tiles that running CTAs took
 // earlier, so the waits end whatever the scheduling; every wait is bounded
@@ -31,15 +33,20 @@ namespace {
 using namespace prim;
 // Single-pass scan (see the top of the file).  A one-tile list needs neither
 // the tile counters nor the look-back.
+// Items per thread of the scans and compactions (tiles of kThreads * kPI).
+constexpr int kPI = 16;
+constexpr int kPTile = kThreads * kPI;
+__device__ __forceinline__ int64_t ptiles_of(int64_t n) { return (n + kPTile - 1) / kPTile; }
+
 template <typename Op, typename T, typename TIn>
 __device__ __forceinline__ void scan_tile(const TIn *in, T *out, int64_t n, int inclusive, int vec,
                                           const ScanState<T> &st, uint32_t epoch, int64_t tile, bool alone,
                                           T *s_warp, T *s_excl) {
-    TIn x[kItems];
-    load_items(in, tile * kTile, n, (vec & 1) != 0, x);
+    TIn x[kPI];
+    load_items(in, tile * kPTile, n, (vec & 1) != 0, x);
     T acc = Op::template identity<T>();
 #pragma unroll
-    for (int j = 0; j < kItems; j++) acc = Op::template apply<T>(acc, (T)x[j]);
+    for (int j = 0; j < kPI; j++) acc = Op::template apply<T>(acc, (T)x[j]);
     T total;
     const T pre = block_exclusive<Op>(acc, s_warp, &total);
     if (alone) {
@@ -50,14 +57,14 @@ __device__ __forceinline__ void scan_tile(const TIn *in, T *out, int64_t n, int 
     }
     __syncthreads();
     T run = Op::template apply<T>(*s_excl, pre);
-    T y[kItems];
+    T y[kPI];
 #pragma unroll
-    for (int j = 0; j < kItems; j++) {
+    for (int j = 0; j < kPI; j++) {
         const T nxt = Op::template apply<T>(run, (T)x[j]);
         y[j] = inclusive ? nxt : run;
         run = nxt;
     }
-    store_items(out, tile * kTile, n, (vec & 2) != 0, y);
+    store_items(out, tile * kPTile, n, (vec & 2) != 0, y);
     __syncthreads();
 }
 
@@ -68,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const TIn *in, T *out, const 
     __shared__ T s_excl;
     __shared__ uint32_t s_tile;
     const int64_t n = count_of(d_n, n_max);
-    const int64_t tiles = tiles_of(n);
+    const int64_t tiles = ptiles_of(n);
     const unsigned parts = participants(tiles);
     if (blockIdx.x >= parts) return;
     if (tiles == 1) {
@@ -92,7 +99,7 @@ void scan_impl(const TIn *in, T *out, Count n, bool inclusive, Scratch tmp, cuda
     if (n.max <= 0) return;
     const int vin = aligned16(in) ? 1 : 0;
     const int vio = vin | (aligned16(out) ? 2 : 0);
-    const int64_t tiles_max = ceil_div(n.max, kTile);
+    const int64_t tiles_max = ceil_div(n.max, kPTile);
     k_scan<Op, T, TIn><<<tile_grid((const void *)k_scan<Op, T, TIn>, tiles_max), kThreads, 0, s>>>(in, out, n.d, n.max, inclusive ? 1 : 0, vio,
                                                                   scan_state<T>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
@@ -106,11 +113,11 @@ __device__ __forceinline__ void compact_tile(const int32_t *flags, int64_t n, in
                                              int32_t *d_count, int vec, const ScanState<int32_t> &st,
                                              uint32_t epoch, int64_t tile, bool alone, int32_t *s_warp,
                                              int32_t *s_excl) {
-    int32_t x[kItems];
-    load_items(flags, tile * kTile, n, vec != 0, x);
+    int32_t x[kPI];
+    load_items(flags, tile * kPTile, n, vec != 0, x);
     int32_t c = 0;
 #pragma unroll
-    for (int j = 0; j < kItems; j++) c += x[j] != 0;
+    for (int j = 0; j < kPI; j++) c += x[j] != 0;
     int32_t total;
     const int32_t pre = block_exclusive<OpSum>(c, s_warp, &total);
     if (threadIdx.x < 32) {
@@ -122,9 +129,9 @@ __device__ __forceinline__ void compact_tile(const int32_t *flags, int64_t n, in
     }
     __syncthreads();
     int32_t pos = *s_excl + pre;
-    const int64_t first = tile * kTile + (int64_t)threadIdx.x * kItems;
+    const int64_t first = tile * kPTile + (int64_t)threadIdx.x * kPI;
 #pragma unroll
-    for (int j = 0; j < kItems; j++)
+    for (int j = 0; j < kPI; j++)
         if (x[j]) out[pos++] = (int32_t)(first + j);
     __syncthreads();
 }
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(const int32_t *__restrict_
     __shared__ int32_t s_excl;
     __shared__ uint32_t s_tile;
     const int64_t n = count_of(d_n, n_max);
-    const int64_t tiles = tiles_of(n);
+    const int64_t tiles = ptiles_of(n);
     if (tiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_count = 0;
     const unsigned parts = participants(tiles);
     if (blockIdx.x >= parts) return;
@@ -162,12 +169,12 @@ __device__ __forceinline__ void compact_values_tile(const int32_t *flags, const 
                                                     int64_t tiles, int32_t *out, int32_t *d_count, int vec,
                                                     const ScanState<int32_t> &st, uint32_t epoch, int64_t tile,
                                                     bool alone, int32_t *s_warp, int32_t *s_excl) {
-    int32_t x[kItems], y[kItems];
-    load_items(flags, tile * kTile, n, (vec & 1) != 0, x);
-    load_items(vals, tile * kTile, n, (vec & 2) != 0, y);
+    int32_t x[kPI], y[kPI];
+    load_items(flags, tile * kPTile, n, (vec & 1) != 0, x);
+    load_items(vals, tile * kPTile, n, (vec & 2) != 0, y);
     int32_t c = 0;
 #pragma unroll
-    for (int j = 0; j < kItems; j++) c += x[j] != 0;
+    for (int j = 0; j < kPI; j++) c += x[j] != 0;
     int32_t total;
     const int32_t pre = block_exclusive<OpSum>(c, s_warp, &total);
     if (threadIdx.x < 32) {
@@ -180,7 +187,7 @@ __device__ __forceinline__ void compact_values_tile(const int32_t *flags, const 
     __syncthreads();
     int32_t pos = *s_excl + pre;
 #pragma unroll
-    for (int j = 0; j < kItems; j++)
+    for (int j = 0; j < kPI; j++)
         if (x[j]) out[pos++] = y[j];
     __syncthreads();
 }
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_values(const int32_t *__re
     __shared__ int32_t s_excl;
     __shared__ uint32_t s_tile;
     const int64_t n = count_of(d_n, n_max);
-    const int64_t tiles = tiles_of(n);
+    const int64_t tiles = ptiles_of(n);
     if (tiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *d_count = 0;
     const unsigned parts = participants(tiles);
     if (blockIdx.x >= parts) return;
@@ -395,7 +402,7 @@ bool radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
 void select_flags(const int32_t *flags, int32_t *out_idx, int32_t *d_count, Count n, Scratch tmp, cudaStream_t s) {
     if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
     const int vec = aligned16(flags) ? 1 : 0;
-    const int64_t tiles_max = ceil_div(n.max, kTile);
+    const int64_t tiles_max = ceil_div(n.max, kPTile);
     k_compact<<<tile_grid((const void *)k_compact, tiles_max), kThreads, 0, s>>>(flags, n.d, n.max, out_idx, d_count, vec,
                                                         scan_state<int32_t>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();
@@ -405,7 +412,7 @@ void select_values(const int32_t *flags, const int32_t *vals, int32_t *out, int3
                    cudaStream_t s) {
     if (n.max <= 0) { UPR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), s)); return; }
     const int vec = (aligned16(flags) ? 1 : 0) | (aligned16(vals) ? 2 : 0);
-    const int64_t tiles_max = ceil_div(n.max, kTile);
+    const int64_t tiles_max = ceil_div(n.max, kPTile);
     k_compact_values<<<tile_grid((const void *)k_compact_values, tiles_max), kThreads, 0, s>>>(
         flags, vals, n.d, n.max, out, d_count, vec, scan_state<int32_t>(tmp, tiles_max));
     UPR_LAUNCH_CHECK();

@@ -59,36 +59,38 @@ __device__ __forceinline__ T block_exclusive(T v, T *s_warp, T *total) {
 
 // Thread t of a tile owns items [8t, 8t + 8): loaded with 16-byte vector loads
 // when the tile is complete and the input aligned, element by element otherwise.
-template <typename T>
+// (N items per thread: kItems for the fused kernels' tiles, more for the
+// scans and compactions of prim.cu)
+template <typename T, int N>
 __device__ __forceinline__ void load_items(const T *__restrict__ in, int64_t base, int64_t n, bool vec,
-                                           T (&x)[kItems]) {
-    const int64_t first = base + (int64_t)threadIdx.x * kItems;
-    if (vec && first + kItems <= n) {
+                                           T (&x)[N]) {
+    const int64_t first = base + (int64_t)threadIdx.x * N;
+    if (vec && first + N <= n) {
         const int4 *p = reinterpret_cast<const int4 *>(in + first);
-        int4 tmp[kItems * sizeof(T) / 16];
+        int4 tmp[N * sizeof(T) / 16];
 #pragma unroll
-        for (int i = 0; i < (int)(kItems * sizeof(T) / 16); i++) tmp[i] = p[i];
+        for (int i = 0; i < (int)(N * sizeof(T) / 16); i++) tmp[i] = p[i];
         const T *t = reinterpret_cast<const T *>(tmp);
 #pragma unroll
-        for (int j = 0; j < kItems; j++) x[j] = t[j];
+        for (int j = 0; j < N; j++) x[j] = t[j];
     } else {
 #pragma unroll
-        for (int j = 0; j < kItems; j++) x[j] = first + j < n ? in[first + j] : T(0);
+        for (int j = 0; j < N; j++) x[j] = first + j < n ? in[first + j] : T(0);
     }
 }
 
-template <typename T>
+template <typename T, int N>
 __device__ __forceinline__ void store_items(T *__restrict__ out, int64_t base, int64_t n, bool vec,
-                                            const T (&x)[kItems]) {
-    const int64_t first = base + (int64_t)threadIdx.x * kItems;
-    if (vec && first + kItems <= n) {
+                                            const T (&x)[N]) {
+    const int64_t first = base + (int64_t)threadIdx.x * N;
+    if (vec && first + N <= n) {
         int4 *p = reinterpret_cast<int4 *>(out + first);
         const int4 *t = reinterpret_cast<const int4 *>(x);
 #pragma unroll
-        for (int i = 0; i < (int)(kItems * sizeof(T) / 16); i++) p[i] = t[i];
+        for (int i = 0; i < (int)(N * sizeof(T) / 16); i++) p[i] = t[i];
     } else {
 #pragma unroll
-        for (int j = 0; j < kItems; j++)
+        for (int j = 0; j < N; j++)
             if (first + j < n) out[first + j] = x[j];
     }
 }
