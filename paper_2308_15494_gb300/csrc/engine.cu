@@ -1735,9 +1735,12 @@ upr_status refine_impl(upr_ctx *c, int32_t *part, int32_t rounds, upr_stats *sta
     // params.graphs == 2: from a binding's second call on, the plain schedule's
     // rounds run as one graph launch
     c->calls_bound++;
-    // a lane schedule still open after two calls had too little work to time
-    // (e.g. no rebalancing sub-round ran): it keeps the default
-    if (c->calls_bound >= 3) {
+    // with graphs = 2, a lane schedule still open after two calls had too
+    // little work to time (e.g. no rebalancing sub-round ran): it keeps the
+    // default, so that the call can run as one graph (other contexts, the
+    // server's slots among them, go on timing: settling early there
+    // lengthened the served mix's tail latency, p99 87 -> 240-350 ms)
+    if (c->prm.graphs == 2 && c->calls_bound >= 3) {
         c->sel_tuned = true;
         c->prop_tuned = true;
     }
