@@ -104,12 +104,13 @@ typedef struct {
     int32_t graphs;              /* 1: once the proposal schedule is settled, each round's
                                     rebalancing loop runs as one CUDA graph launch (a while
                                     node over one sub-round, the stop test on the device);
-                                    2: also, from a binding's second call on, all rounds
-                                    of a call run as one graph launch (schedule 0, no
-                                    label propagation, dense table; round 1's table build
-                                    precedes the graph; the per-phase times of the stats
-                                    are then 0); 0: the host launches every sub-round and
-                                    reads its stop flag.  Results never depend on it. 1    */
+                                    2: also, from a binding's second call on, all FM
+                                    rounds of a call run as one graph launch (schedule 0,
+                                    dense table; after label propagation too; round 1's
+                                    table build precedes the graph; the per-phase times of
+                                    the stats are then 0); 0: the host launches every
+                                    sub-round and reads its stop flag.  Results never
+                                    depend on it. 1                                          */
     int32_t schedule;            /* round driver (Sec. 4.4, Sec. 6.2): 0 every round
                                     unconstrained with the tau schedule.  6 the paper's
                                     final configuration: the first U rounds unconstrained
@@ -302,9 +303,13 @@ upr_status upr_batch_create_mixed(const upr_graph *graphs, int32_t n_graphs, con
  * else UPR_ERR_INVALID with the context unchanged); a mixed context takes
  * any k (batches of a k it already had are reused, new k get new batches,
  * batches of k no longer present are freed).  The graphs are read as in
- * upr_create and may be freed on return.  Any other error leaves the
- * context unusable (every call returns UPR_ERR_INVALID) until a rebind
- * succeeds. */
+ * upr_create and may be freed on return; a batch's arrays in page-locked
+ * host memory are read in place by one gather launch per array kind.  A
+ * rebinding whose sizes, schedules, key widths, limits and device memory
+ * all equal the previous binding's (the same graph, or another of the same
+ * shape) keeps the graphs captured for it, so the next call does not
+ * capture again.  Any other error leaves the context unusable (every call
+ * returns UPR_ERR_INVALID) until a rebind succeeds. */
 upr_status upr_batch_rebind(upr_ctx *ctx, const upr_graph *graphs, int32_t n_graphs, const int32_t *k,
                             const double *eps);
 
