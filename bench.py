@@ -627,7 +627,7 @@ def run_gpu(args):
                 "traffic": _traffic("paper_2308_15494_gb300/csrc/graph.cu", "gain_table_rmat_s22_k64.md")}
 
     # the whole step against the same peak: the rounds' algorithmic bytes
-    # (SURVEY's per-round formula, counted by the library) over the call's
+    # (the per-round byte formula, counted by the library) over the call's
     # device time, and the same per round
     s_last = stats[-1]
     step_bytes = s_last.bytes_algorithmic
